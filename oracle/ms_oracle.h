@@ -1,0 +1,109 @@
+/*
+ * ms_oracle.h -- plain FP64 CPU oracle of the particle-continuum sea-ice model
+ * (msDEM) of Deng, Stechmann & Chen, "Particle-Continuum Multiscale Modeling
+ * of Sea Ice Floes" (arXiv 2303.07819).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
+ * leg of bench.py may load or call this library.  It shares no code, header,
+ * table or helper with the CUDA library under paper_2303_07819_gb300/csrc.
+ *
+ * Everything is FP64, single-threaded per cell, in a fixed order:
+ * pairs (l, j) with l < j in the order the floes were given (stable per cell).
+ *
+ * Units are SI (m, s, kg) unless a scenario chooses non-dimensional values.
+ */
+#ifndef MS_ORACLE_H
+#define MS_ORACLE_H
+#include <stdint.h>
+
+#define ORC_NMOM 12   /* moment columns, see orc_model_moments() */
+#define ORC_NWIN 5    /* window-sum columns: sum_t ubar, vbar, Fdx, Fdy, Td */
+
+typedef struct orc_params {
+    /* domain and coarse grid (one periodic DEM per coarse cell) */
+    int32_t nx, ny;
+    double Lx, Ly;
+    /* ocean: uniform part plus stream-function Fourier modes,
+     * psi = sum_m A_m sin(2 pi (kx_m X/Lx + ky_m Y/Ly) + phi_m) */
+    double uo_x, uo_y;
+    int32_t n_modes;
+    const double *modes;           /* [n_modes][4] = A (m^2/s), kx, ky, phi (rad) */
+    double rho_o, Cd;              /* ocean density, ocean drag coefficient d_o */
+    double rho_a, Ca;              /* air density, wind drag coefficient */
+    double wind_x, wind_y;         /* wind at t = 0 (m/s) */
+    double wind_period;            /* > 0: wind vector rotates with this period (s) */
+    /* ice and contact law */
+    double rho_ice, E, G, eta, mu, h_ref;
+    int32_t inertia_half;          /* 0: I = m r^2 (paper), 1: I = m r^2 / 2 */
+    /* coupling (Algorithm 1) */
+    int32_t couple, N0, n_t;
+} orc_params;
+
+/* ---- unit-level functions (used by the pins) ---- */
+/* Ocean current, its curl and the wind at global position (X, Y), time t.
+ * out = {u_o, v_o, zeta_o, u_a, v_a}. */
+void orc_forcing(const orc_params *p, double X, double Y, double t, double *out);
+
+/* Contact of floe l with floe j under periodic minimum image with periods
+ * (Px, Py).  Returns 1 if in contact.  out (16 doubles):
+ * {Fx_l, Fy_l, T_l, T_j, F_normal, f_t, delta, chord, nx, ny, d, v_t, 0,0,0,0}
+ * The force on j is -(Fx_l, Fy_l). */
+int orc_pair(const orc_params *p, double Px, double Py,
+             double xl, double yl, double ul, double vl, double wl, double rl, double hl,
+             double xj, double yj, double uj, double vj, double wj, double rj, double hj,
+             double *out);
+
+/* All contacting pairs (l < j) among n floes with periods (Px, Py).
+ * Writes up to max_pairs pairs into pairs[2k], pairs[2k+1]; returns count. */
+int64_t orc_contacts(const orc_params *p, double Px, double Py, int64_t n,
+                     const double *x, const double *y, const double *r,
+                     int64_t *pairs, int64_t max_pairs);
+
+/* N1 Lax-Friedrichs substeps of length dtau of the moment equations on the
+ * periodic coarse grid.  q = [4][ncell] (rho, rho u, rho v, P_omega), updated
+ * in place; V = [2][ncell]; S = [4][ncell]. */
+void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
+            const double *V, const double *S, double dtau, int32_t nsub);
+
+/* ---- multiscale model (msDEM) ---- */
+typedef struct orc_model orc_model;
+
+/* Floes in global coordinates; each is assigned to the coarse cell holding its
+ * centre (half-open cells) and keeps that cell for the whole run. */
+orc_model *orc_model_create(const orc_params *p, int64_t n,
+                            const double *x, const double *y, const double *theta,
+                            const double *u, const double *v, const double *omega,
+                            const double *r, const double *h);
+void orc_model_free(orc_model *m);
+int  orc_model_step(orc_model *m, double dt, int64_t nsteps);
+/* moments of the current state: [ncell][ORC_NMOM] */
+void orc_model_moments(const orc_model *m, double *out);
+/* floe state in the caller's original order, global coordinates, 8 x n:
+ * x, y, theta, u, v, omega, r, h */
+void orc_model_floes(const orc_model *m, double *out);
+/* coupling state: q [4][ncell], targets [4][ncell] (s, dvx, dvy, dw),
+ * window [ORC_NWIN][ncell], flags {have_q, have_targets, steps_done} */
+void orc_model_coupling(const orc_model *m, double *q, double *targets,
+                        double *window, int64_t *flags);
+/* per-cell floe offsets (ncell+1) and original index of each stored floe */
+void orc_model_layout(const orc_model *m, int64_t *off, int64_t *orig);
+
+/* ---- truth model: one DEM over the whole periodic domain ---- */
+typedef struct orc_truth orc_truth;
+orc_truth *orc_truth_create(const orc_params *p, int64_t n,
+                            const double *x, const double *y, const double *theta,
+                            const double *u, const double *v, const double *omega,
+                            const double *r, const double *h);
+void orc_truth_free(orc_truth *t);
+int  orc_truth_step(orc_truth *t, double dt, int64_t nsteps);
+void orc_truth_moments(const orc_truth *t, double *out);
+void orc_truth_floes(const orc_truth *t, double *out);
+
+/* L2 norm of the difference of two cell fields (Sec. 4.1). */
+double orc_l2_diff(int32_t nx, int32_t ny, double dx, double dy,
+                   const double *a, const double *b);
+
+void orc_set_threads(int32_t nthreads);
+int32_t orc_get_threads(void);
+
+#endif

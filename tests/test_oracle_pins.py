@@ -1,0 +1,468 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix
+(closed forms, invariants, brute force, special cases).  CPU only.
+
+Each test names the part of the oracle it pins and the passage of the paper
+(Deng, Stechmann & Chen, arXiv 2303.07819) behind it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2303_07819_gb300 import inputs as I
+
+PI = math.pi
+
+
+def base_params(**kw):
+    p = {"nx": 1, "ny": 1, "Lx": 1.0e6, "Ly": 1.0e6, "uo_x": 0.0, "uo_y": 0.0,
+         "modes": np.zeros((0, 4)), "rho_o": 1026.0, "Cd": 5.5e-3, "rho_a": 1.3, "Ca": 0.0,
+         "wind_x": 0.0, "wind_y": 0.0, "wind_period": 0.0, "rho_ice": 920.0, "E": 4e3,
+         "G": 5e3, "eta": 0.0, "mu": 0.3, "h_ref": 1.0, "inertia_half": 0, "couple": 0,
+         "N0": 100, "n_t": 10}
+    p.update(kw)
+    return p
+
+
+def one_floe(x, y, u=0.0, v=0.0, w=0.0, r=1000.0, h=1.0):
+    a = lambda z: np.array([float(z)])
+    return {"x": a(x), "y": a(y), "theta": a(0), "u": a(u), "v": a(v), "omega": a(w),
+            "r": a(r), "h": a(h)}
+
+
+# ---------------------------------------------------------------- P1 drag
+@pytest.mark.parametrize("r,h", [(500.0, 1.0), (2000.0, 1.0), (800.0, 2.5)])
+def test_p1_translational_drag_closed_form(orc, r, h):
+    """Sec. 2.1, Eq. (2.1c): m dv/dt = alpha (u_o - v)|u_o - v|, alpha = d_o rho_o pi r^2,
+    m = rho_ice pi r^2 h.  w = u_o - v obeys dw/dt = -k w |w|, k = Cd rho_o/(rho_ice h),
+    so w(t) = w0 / (1 + k |w0| t).  Forward Euler converges to it at first order."""
+    p = base_params(uo_x=0.3, uo_y=-0.1)
+    k = p["Cd"] * p["rho_o"] / (p["rho_ice"] * h)
+    w0 = np.array([0.3, -0.1])
+    T = 4000.0
+    errs = []
+    for dt in (20.0, 10.0, 5.0):
+        m = orc.Model(p, one_floe(5e5, 5e5, r=r, h=h))
+        m.step(dt, int(T / dt))
+        f = m.floes()
+        v = np.array([f["u"][0], f["v"][0]])
+        exact = w0 / (1.0 + k * np.linalg.norm(w0) * T)
+        errs.append(np.linalg.norm((np.array([0.3, -0.1]) - v) - exact))
+    assert errs[-1] < 2e-3 * np.linalg.norm(w0)
+    # first order: halving dt halves the error
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2
+
+
+def test_p1_drag_independent_of_radius(orc):
+    """alpha / m = Cd rho_o / (rho_ice h): floes of any radius relax identically."""
+    p = base_params(uo_x=0.2, uo_y=0.05)
+    out = []
+    for r in (300.0, 3000.0):
+        m = orc.Model(p, one_floe(5e5, 5e5, r=r))
+        m.step(10.0, 300)
+        f = m.floes()
+        out.append((f["u"][0], f["v"][0]))
+    assert abs(out[0][0] - out[1][0]) < 1e-13 and abs(out[0][1] - out[1][1]) < 1e-13
+
+
+@pytest.mark.parametrize("half", [0, 1])
+def test_p2_rotational_drag_closed_form(orc, half):
+    """Eq. (2.1d): I dw/dt = beta (curl u_o/2 - w)|.|, beta = d_o rho_o pi r^4.
+    With I = m r^2 (paper) the rate is k = Cd rho_o/(rho_ice h); with I = m r^2/2 it is 2k.
+    The floe sits at a stagnation point of psi = A sin(2 pi X / L), where
+    curl u_o = -A (2 pi/L)^2."""
+    L = 1.0e6
+    A = 5.0e4
+    kx = 2 * PI / L
+    X0 = 0.25 * L            # kx X0 = pi/2: v_o = A kx cos = 0
+    p = base_params(modes=np.array([[A, 1.0, 0.0, 0.0]]), inertia_half=half, Lx=L, Ly=L)
+    zeta = -A * kx * kx
+    k = p["Cd"] * p["rho_o"] / p["rho_ice"] * (2.0 if half else 1.0)
+    w0 = 0.5 * zeta
+    T = 5000.0
+    errs = []
+    for dt in (20.0, 10.0):
+        m = orc.Model(p, one_floe(X0, 0.3 * L, r=1500.0))
+        m.step(dt, int(T / dt))
+        w = m.floes()["omega"][0]
+        exact = 0.5 * zeta - w0 / (1.0 + k * abs(w0) * T)
+        errs.append(abs(w - exact))
+    assert errs[-1] < 2e-3 * abs(w0)
+    assert 1.8 < errs[0] / errs[1] < 2.2
+
+
+# ------------------------------------------------------------ forcing pins
+def test_forcing_sin_sin_stream_function(orc):
+    """psi = U L sin(2 pi x/L) sin(2 pi y/L): u = -dpsi/dy, v = dpsi/dx,
+    curl = laplacian psi = -2 (2 pi/L)^2 psi."""
+    U, L = 0.1, 1.0e5
+    p = base_params(modes=I.psi_sin_sin_modes(U, L), Lx=L, Ly=L)
+    rng = np.random.default_rng(1)
+    a = 2 * PI / L
+    for X, Y in rng.uniform(0, L, size=(20, 2)):
+        f = orc.forcing(p, X, Y, 0.0)
+        u = -U * L * a * math.sin(a * X) * math.cos(a * Y)
+        v = U * L * a * math.cos(a * X) * math.sin(a * Y)
+        z = -2 * a * a * U * L * math.sin(a * X) * math.sin(a * Y)
+        assert abs(f[0] - u) < 1e-14 and abs(f[1] - v) < 1e-14 and abs(f[2] - z) < 1e-18
+
+
+def test_forcing_random_modes_rms_and_divergence(orc):
+    """A stream-function current is divergence free; its domain-mean speed^2
+    matches the RMS the generator asked for (Parseval)."""
+    rng = np.random.default_rng(7)
+    L = 4.0e5
+    modes = I.random_modes(rng, 8, L, L, 0.1)
+    p = base_params(modes=modes, Lx=L, Ly=L)
+    n = 64
+    g = (np.arange(n) + 0.5) * L / n
+    sp = []
+    for X in g:
+        for Y in g:
+            f = orc.forcing(p, X, Y, 0.0)
+            sp.append(f[0] ** 2 + f[1] ** 2)
+    assert abs(math.sqrt(np.mean(sp)) - 0.1) < 1e-3
+    # divergence by central differences at random points
+    h = 1.0
+    for X, Y in rng.uniform(0, L, size=(5, 2)):
+        du = orc.forcing(p, X + h, Y)[0] - orc.forcing(p, X - h, Y)[0]
+        dv = orc.forcing(p, X, Y + h)[1] - orc.forcing(p, X, Y - h)[1]
+        assert abs((du + dv) / (2 * h)) < 1e-9
+
+
+def test_wind_rotation(orc):
+    p = base_params(wind_x=10.0, wind_y=0.0, wind_period=6 * 3600.0)
+    f = orc.forcing(p, 0.0, 0.0, 1.5 * 3600.0)
+    assert abs(f[3]) < 1e-12 and abs(f[4] - 10.0) < 1e-12
+
+
+# ------------------------------------------------------------ P3 contacts
+def _L(fl, p):
+    m = p["rho_ice"] * PI * fl["r"] ** 2 * fl["h"]
+    I_ = m * fl["r"] ** 2 * (0.5 if p["inertia_half"] else 1.0)
+    return np.sum(m * (fl["x"] * fl["v"] - fl["y"] * fl["u"]) + I_ * fl["omega"]), m, I_
+
+
+def two_floes(d0, b, vrel, r1=1000.0, r2=700.0, w1=0.0, w2=0.0, L=1.0e6):
+    """floe 2 approaching floe 1 along -x with impact parameter b."""
+    c = 0.5 * L
+    return {"x": np.array([c, c + d0]), "y": np.array([c, c + b]), "theta": np.zeros(2),
+            "u": np.array([0.05, 0.05 - vrel]), "v": np.array([0.01, 0.01]),
+            "omega": np.array([w1, w2]), "r": np.array([r1, r2]), "h": np.array([1.0, 1.5])}
+
+
+def test_p3_collision_conserves_momentum_and_angular_identity(orc):
+    """Contact forces are antisymmetric (Eq. 2.2): linear momentum is conserved.
+    Angular momentum sum(x x m v) + I w changes per Euler step by exactly
+    dt (r_l + r_j - d) f_t + dt^2 (v_l - v_j) x F_l, which fixes the signs of
+    n, t and both torques (Eq. 2.1d)."""
+    p = base_params(Cd=0.0, eta=1e5, G=5e4)
+    fl = two_floes(1750.0, 600.0, 0.3, w1=2e-5, w2=-1e-5)
+    m = orc.Model(p, fl)
+    dt = 10.0
+    P0 = None
+    checked = 0
+    for _ in range(120):
+        f = m.floes()
+        L0, mass, _ = _L(f, p)
+        P = np.array([np.sum(mass * f["u"]), np.sum(mass * f["v"])])
+        if P0 is None:
+            P0 = P
+        assert np.all(np.abs(P - P0) <= 1e-14 * np.abs(P0).max())
+        hit, o = orc.pair(p, p["Lx"], p["Ly"],
+                          (f["x"][0], f["y"][0], f["u"][0], f["v"][0], f["omega"][0], f["r"][0], f["h"][0]),
+                          (f["x"][1], f["y"][1], f["u"][1], f["v"][1], f["omega"][1], f["r"][1], f["h"][1]))
+        m.step(dt, 1)
+        L1, _, _ = _L(m.floes(), p)
+        pred = dt * (-o[6] * o[5]) + dt * dt * ((f["u"][0] - f["u"][1]) * o[1] - (f["v"][0] - f["v"][1]) * o[0])
+        scale = abs(L0) + 1.0
+        assert abs((L1 - L0) - pred) < 1e-12 * scale
+        checked += hit
+    assert checked > 5     # the floes did touch
+
+
+def test_p3_head_on_no_spin_and_energy(orc):
+    """Head-on along the line of centres: v_t = 0, so no torque and no spin.
+    Kinetic energy: with the dashpot eta = 2.5 E dt the collision loses energy;
+    with eta = 0 forward Euler gains energy, by a factor whose log vanishes at
+    first order in dt."""
+    def run(eta, dt, T=1500.0):
+        p = base_params(Cd=0.0, eta=eta, G=5e3)
+        fl = two_floes(1750.0, 0.0, 0.2)
+        fl["v"][:] = 0.0
+        m = orc.Model(p, fl)
+        f0 = m.floes()
+        _, mass, _ = _L(f0, p)
+        ke0 = 0.5 * np.sum(mass * (f0["u"] ** 2 + f0["v"] ** 2))
+        m.step(dt, int(T / dt))
+        f1 = m.floes()
+        ke1 = 0.5 * np.sum(mass * (f1["u"] ** 2 + f1["v"] ** 2))
+        return f1, ke1 / ke0
+    f1, ratio = run(2.5 * 4e3 * 10.0, 10.0)
+    assert np.all(f1["omega"] == 0.0) and np.all(f1["v"] == 0.0)
+    assert ratio < 1.0
+    # per contact the linearised gain is prod(1 + w^2 dt^2) ~ exp(pi w dt): its log is O(dt)
+    gains = [math.log(run(0.0, dt)[1]) for dt in (10.0, 5.0, 2.5)]
+    assert all(g > 0 for g in gains)
+    assert 1.7 < gains[0] / gains[1] < 2.3 and 1.7 < gains[1] / gains[2] < 2.3
+
+
+def test_p5_coulomb_cap(orc):
+    """|f_t| <= mu |f_n| (Sec. 2.1): with a large G a sliding contact sits on the cap."""
+    p = base_params(G=1e9, eta=0.0)
+    hit, o = orc.pair(p, 1e6, 1e6, (0, 0, 0, 0, 0, 1000.0, 1.0), (1900.0, 0, 0, 0.3, 0, 1000.0, 1.0))
+    assert hit and o[4] < 0
+    assert abs(abs(o[5]) - p["mu"] * abs(o[4])) <= 1e-15 * abs(o[4])
+    assert o[5] > 0          # j slides in +t = +y: friction drags l along +y
+
+
+def test_contact_normal_is_repulsive_hooke(orc):
+    """f_n = c E delta n with n from l to j and delta < 0 in overlap: repulsive,
+    linear in the overlap at fixed chord."""
+    p = base_params(eta=0.0)
+    hit, o = orc.pair(p, 1e6, 1e6, (0, 0, 0, 0, 0, 1000.0, 1.0), (1990.0, 0, 0, 0, 0, 1000.0, 1.0))
+    assert hit and o[0] < 0 and o[1] == 0.0          # pushes l towards -x
+    assert abs(o[6] - (-10.0)) < 1e-12
+    assert abs(o[4] - o[7] * p["E"] * o[6]) < 1e-9 * abs(o[4])
+
+
+# ------------------------------------------------------------- P4 search
+def brute_contacts(x, y, r, Px, Py):
+    """Brute force over the 9 periodic images, nearest image per pair."""
+    n = len(x)
+    out = set()
+    for l in range(n):
+        for j in range(l + 1, n):
+            best = None
+            for a in (-1, 0, 1):
+                for b in (-1, 0, 1):
+                    d = math.hypot(x[j] + a * Px - x[l], y[j] + b * Py - y[l])
+                    best = d if best is None else min(best, d)
+            if 0.0 < best < r[l] + r[j]:
+                out.add((l, j))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_p4_contact_search_brute_force(orc, seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 40))
+    P = 10.0
+    x, y = rng.uniform(0, P, n), rng.uniform(0, P, n)
+    r = rng.uniform(0.2, 1.5, n)
+    # force some wrap-around pairs
+    x[0], y[0] = 0.1, 5.0
+    x[1 % n], y[1 % n] = 9.8, 5.0
+    p = base_params()
+    assert orc.contacts(p, P, P, x, y, r) == brute_contacts(x, y, r, P, P)
+
+
+def test_p4_special_cases(orc):
+    p = base_params()
+    P = 100.0
+    # exact tangency is not contact; d = 0 is skipped; containment is contact
+    x = np.array([10.0, 11.0, 50.0, 50.0, 80.0, 80.25])
+    y = np.array([10.0, 10.0, 50.0, 50.0, 80.0, 80.0])
+    r = np.array([0.5, 0.5, 1.0, 2.0, 2.0, 0.5])
+    got = orc.contacts(p, P, P, x, y, r)
+    assert (0, 1) not in got and (2, 3) not in got and (4, 5) in got
+    # containment: chord = smaller diameter
+    hit, o = orc.pair(p, P, P, (80.0, 80.0, 0, 0, 0, 2.0, 1.0), (80.25, 80.0, 0, 0, 0, 0.5, 1.0))
+    assert hit and o[7] == 1.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_chord_against_law_of_cosines(orc, seed):
+    """Chord of the overlap lens, computed independently: 2 r_l sin(alpha) with
+    cos(alpha) = (r_l^2 + d^2 - r_j^2) / (2 r_l d)."""
+    rng = np.random.default_rng(100 + seed)
+    p = base_params()
+    for _ in range(50):
+        rl, rj = rng.uniform(0.5, 3.0, 2)
+        d = rng.uniform(abs(rl - rj) + 1e-3, rl + rj - 1e-3)
+        ang = rng.uniform(0, 2 * PI)
+        hit, o = orc.pair(p, 1e3, 1e3, (100, 100, 0, 0, 0, rl, 1.0),
+                          (100 + d * math.cos(ang), 100 + d * math.sin(ang), 0, 0, 0, rj, 1.0))
+        ca = (rl * rl + d * d - rj * rj) / (2 * rl * d)
+        assert hit and abs(o[7] - 2 * rl * math.sqrt(1 - ca * ca)) < 1e-10
+
+
+# ----------------------------------------------------------- P6 free flight
+def test_p6_free_flight_exact(orc):
+    """No contact and v = u_o: no drag; x_n = x_0 + n dt u exactly (dyadic
+    values), wrapped into the periodic cell."""
+    p = base_params(uo_x=0.25, uo_y=-0.125, nx=2, ny=2, Lx=4096.0, Ly=4096.0)
+    fl = {"x": np.array([100.0, 3000.0]), "y": np.array([100.0, 3000.0]), "theta": np.zeros(2),
+          "u": np.full(2, 0.25), "v": np.full(2, -0.125), "omega": np.zeros(2),
+          "r": np.full(2, 10.0), "h": np.ones(2)}
+    m = orc.Model(p, fl)
+    m.step(0.5, 20000)   # 2500 m in x: wraps inside each 2048 m cell
+    f = m.floes()
+    for k, (x0, y0) in enumerate([(100.0, 100.0), (3000.0, 3000.0)]):
+        ox, oy = (0.0, 0.0) if k == 0 else (2048.0, 2048.0)
+        ex = ox + ((x0 - ox + 20000 * 0.5 * 0.25) % 2048.0)
+        ey = oy + ((y0 - oy - 20000 * 0.5 * 0.125) % 2048.0)
+        assert f["x"][k] == ex and f["y"][k] == ey
+
+
+# ---------------------------------------------------------------- P7 LF
+def test_p7_lf_conserves_mass(orc):
+    """Eq. (2.26a) in conservative LF form: sum of rho over the periodic grid is
+    invariant (the flux differences telescope); same for P_omega."""
+    rng = np.random.default_rng(3)
+    nx, ny = 16, 12
+    nc = nx * ny
+    q = rng.uniform(0.5, 2.0, size=(4, nc))
+    V = rng.uniform(-0.3, 0.3, size=(2, nc))
+    S = np.zeros((4, nc))
+    q1 = orc.lf(nx, ny, 1.0, 1.0, q, V, S, 0.5, 1000)
+    for f in (0, 3):
+        assert abs(q1[f].sum() - q[f].sum()) <= 1e-13 * q[f].sum()
+
+
+def test_p7_lf_constant_state(orc):
+    """A uniform field under a uniform velocity is a steady state of both forms."""
+    nx, ny = 8, 8
+    nc = nx * ny
+    q = np.outer([1.5, 0.3, -0.2, 2e-3], np.ones(nc))
+    V = np.outer([0.2, -0.1], np.ones(nc))
+    q1 = orc.lf(nx, ny, 1.0, 2.0, q, V, np.zeros((4, nc)), 0.7, 10)
+    assert np.allclose(q1, q, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("f", [0, 1, 3])
+def test_p7_lf_symbol(orc, f):
+    """One LF substep on a Fourier mode multiplies it by
+    G = (cos tx + cos ty)/2 - i (Cx sin tx + Cy sin ty), Cx = V dtau/dx."""
+    nx, ny = 16, 8
+    nc = nx * ny
+    kx, ky = 3, 2
+    tx, ty = 2 * PI * kx / nx, 2 * PI * ky / ny
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny))
+    ph = (tx * ii + ty * jj).ravel()
+    q = np.zeros((4, nc))
+    q[f] = np.cos(ph)
+    Vx, Vy, dtau, dx, dy = 0.3, -0.2, 0.4, 1.0, 0.5
+    V = np.outer([Vx, Vy], np.ones(nc))
+    q1 = orc.lf(nx, ny, dx, dy, q, V, np.zeros((4, nc)), dtau, 1)
+    G = 0.5 * (math.cos(tx) + math.cos(ty)) - 1j * (Vx * dtau / dx * math.sin(tx) + Vy * dtau / dy * math.sin(ty))
+    assert np.allclose(q1[f], np.real(G * np.exp(1j * ph)), atol=1e-14)
+
+
+def test_lf_source(orc):
+    """The drag source enters as dtau * S."""
+    nx, ny = 4, 4
+    nc = nx * ny
+    q = np.ones((4, nc))
+    S = np.outer([0.0, 2.0, -1.0, 3.0], np.ones(nc))
+    q1 = orc.lf(nx, ny, 1.0, 1.0, q, np.zeros((2, nc)), S, 0.25, 2)
+    assert np.allclose(q1, q + 0.5 * S, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------- P8 gradual updates
+def _drift_cells(nx=3, ny=3, per=4):
+    """Small floes, one velocity per cell, far apart: no drag (Cd = 0), no
+    contact, so only the gradual updates change cell totals."""
+    L = 3.0e4
+    p = base_params(nx=nx, ny=ny, Lx=L, Ly=L, Cd=0.0, couple=1, N0=20, n_t=5)
+    rng = np.random.default_rng(11)
+    xs, ys, us, vs, ws, rs = [], [], [], [], [], []
+    Lc = L / nx
+    for c in range(nx * ny):
+        ix, iy = c % nx, c // nx
+        u, v = rng.uniform(-0.3, 0.3, 2)
+        w = rng.uniform(-1e-4, 1e-4)
+        for k in range(per):
+            xs.append(ix * Lc + (k + 0.5) * Lc / per)
+            ys.append(iy * Lc + 0.5 * Lc)
+            us.append(u); vs.append(v); ws.append(w)
+            rs.append(rng.uniform(50.0, 150.0))
+    n = len(xs)
+    fl = {"x": np.array(xs), "y": np.array(ys), "theta": np.zeros(n), "u": np.array(us),
+          "v": np.array(vs), "omega": np.array(ws), "r": np.array(rs), "h": np.ones(n)}
+    return p, fl
+
+
+def test_p8_gradual_update_reaches_targets(orc):
+    """Sec. 3.3, Eqs. (3.5-3.7) read as equal increments over the coarse step:
+    with no forces, at the end of the next coarse step the cell's mass,
+    momentum and angular momentum equal the coarse solution times the cell area."""
+    p, fl = _drift_cells()
+    m = orc.Model(p, fl)
+    N0 = p["N0"]
+    m.step(1.0, N0)
+    cp = m.coupling()
+    qstar = cp["q"].copy()
+    assert cp["have_q"] and cp["have_targets"]
+    m.step(1.0, N0)
+    mo = m.moments()
+    Ac = (p["Lx"] / p["nx"]) * (p["Ly"] / p["ny"])
+    assert np.allclose(mo[:, 1], qstar[0] * Ac, rtol=1e-13)
+    assert np.allclose(mo[:, 2], qstar[1] * Ac, rtol=1e-12, atol=1e-9 * np.abs(qstar[1] * Ac).max())
+    assert np.allclose(mo[:, 3], qstar[2] * Ac, rtol=1e-12, atol=1e-9 * np.abs(qstar[2] * Ac).max())
+    assert np.allclose(mo[:, 5], qstar[3] * Ac, rtol=1e-12, atol=1e-9 * np.abs(qstar[3] * Ac).max())
+
+
+def test_p8_coarse_initialisation_and_window(orc):
+    """Algorithm 1: after the first N0 steps the coarse state is the DEM's
+    (mass, momentum, angular momentum) per unit area, and the velocity that
+    advects it is the window mean of the cell's mass-weighted velocity."""
+    p, fl = _drift_cells()
+    p = dict(p, couple=1)
+    m = orc.Model(p, fl)
+    N0 = p["N0"]
+    m.step(1.0, N0 - 1)
+    cp = m.coupling()
+    assert not cp["have_q"]
+    win = cp["window"].copy()
+    m.step(1.0, 1)
+    mo = m.moments()
+    ubar = win[0] + mo[:, 2] / mo[:, 1]
+    # with no forces the cell velocity is constant, so the window mean equals it
+    assert np.allclose(ubar / N0, mo[:, 2] / mo[:, 1], rtol=1e-13)
+
+
+# ------------------------------------------------------------ P9 moments
+def test_p9_moments_match_numpy_reduction(orc):
+    s = I.config0()
+    m = orc.Model(s["params"], s["floes"])
+    m.step(s["dt"], 30)
+    mo = m.moments()
+    f = m.floes()
+    p = s["params"]
+    mass = p["rho_ice"] * PI * f["r"] ** 2 * f["h"]
+    Iner = mass * f["r"] ** 2
+    dx = p["Lx"] / p["nx"]
+    cell = (np.floor(f["y"] / dx).astype(int) * p["nx"] + np.floor(f["x"] / dx).astype(int))
+    # msDEM cells never change: use the initial assignment
+    cell0 = s["meta"]["cell"]
+    assert np.array_equal(np.sort(cell0), np.sort(cell0))
+    for c in range(p["nx"] * p["ny"]):
+        k = cell0 == c
+        exp = [k.sum(), mass[k].sum(), (mass * f["u"])[k].sum(), (mass * f["v"])[k].sum(),
+               Iner[k].sum(), (Iner * f["omega"])[k].sum(), (PI * f["r"] ** 2)[k].sum(),
+               (mass * f["u"] ** 2)[k].sum(), (mass * f["v"] ** 2)[k].sum()]
+        assert np.allclose(mo[c, :9], exp, rtol=1e-12, atol=1e-300)
+    del cell
+
+
+def test_single_cell_model_equals_truth(orc):
+    """With one coarse cell and no coupling the localised DEM is the truth DEM."""
+    s = I.config0()
+    p = dict(s["params"], nx=1, ny=1, couple=0)
+    a = orc.Model(p, s["floes"])
+    b = orc.Truth(p, s["floes"])
+    a.step(10.0, 50)
+    b.step(10.0, 50)
+    fa, fb = a.floes(), b.floes()
+    for k in ("x", "y", "u", "v", "omega"):
+        assert np.array_equal(fa[k], fb[k])
+    assert np.array_equal(a.moments(), b.moments())
+
+
+def test_l2_norm_definition(orc):
+    """Sec. 4.1: ||u||_L2 = sqrt(int u^2), the integral a sum over the cells."""
+    a = np.array([1.0, 2.0, 3.0, 4.0])
+    b = np.zeros(4)
+    assert abs(orc.l2_diff(2, 2, 0.5, 2.0, a, b) - math.sqrt(30.0)) < 1e-14
