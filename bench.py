@@ -1,0 +1,309 @@
+"""Benchmark of the msDEM hot path on GB300 (one JSON line on rank 0).
+
+Workload: the batched configuration of 128 x 128 coarse cells of 25 km with
+lognormal(median 96, sigma 0.69) floes per cell clipped to [8, 1024]
+(~1.98M floes), FP32 floe state with FP64 moments and coarse solve, seeded
+synthetic inputs.
+
+One bench step = one coarse interval of Algorithm 1: N0 = 100 fine steps of
+every cell's DEM (contact search, contact and drag forces, forward Euler,
+moment reduction, 10 gradual updates) plus the coarse Lax-Friedrichs step,
+i.e. one pass over every row of the hot path.  The state (64 MB) fits in L2,
+so L2 is flushed (a 512 MB write) before every timed step and each step is
+timed alone with CUDA events on the library's stream.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+BYTES_PER_FLOE_STEP = 56.0     # read x,y,theta,u,v,omega,r,h (8 x 4 B), write x,y,theta,u,v,omega (6 x 4 B)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured", d
+    return HBM_FALLBACK_GBS, "fallback", {}
+
+
+def load_scenario(cfg: int):
+    from paper_2303_07819_gb300 import inputs as I
+    cache = os.path.join(tempfile.gettempdir(), f"msdem_inputs_cfg{cfg}_{I.BASE_SEED}.npz")
+    if os.path.exists(cache):
+        z = np.load(cache, allow_pickle=True)
+        s = z["s"].item()
+        return s
+    s = I.CONFIGS[cfg]()
+    try:
+        np.savez(cache, s=np.array(s, dtype=object))
+    except OSError:
+        pass
+    return s
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"msdem_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample_rate(s, ncells: int, steps: int, seed: int = 0):
+    """Floe-steps/s of the FP64 oracle (all host cores) on `ncells` random
+    cells of the workload for `steps` fine steps."""
+    from oracle import oracle as O
+    O.build()
+    cores = len(os.sched_getaffinity(0))
+    O.set_threads(cores)
+    p = s["params"]
+    cell = s["meta"]["cell"]
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(p["nx"] * p["ny"], size=min(ncells, p["nx"] * p["ny"]), replace=False)
+    sel = np.isin(cell, pick)
+    sub = {k: v[sel] for k, v in s["floes"].items()}
+    m = O.Model(p, sub)
+    t0 = time.perf_counter()
+    m.step(s["dt"], steps)
+    dt = time.perf_counter() - t0
+    n = int(sel.sum())
+    m.close()
+    return n * steps / dt, n, dt, cores
+
+
+def calibrated_oracle(s, target_s: float, ncells: int = 4096):
+    """A sample of `ncells` random cells and the number of fine steps that
+    takes the oracle about target_s seconds on all host cores."""
+    p = s["params"]
+    ncells = min(ncells, p["nx"] * p["ny"])
+    rate, n, dt, cores = oracle_sample_rate(s, ncells, 1, seed=1)
+    steps = int(max(1, min(1000, round(target_s * rate / max(n, 1)))))
+    return ncells, steps
+
+
+def run_reference(args, s, rank):
+    if rank != 0:
+        return
+    from paper_2303_07819_gb300 import inputs as I  # noqa: F401
+    p = s["params"]
+    ncells, steps = calibrated_oracle(s, 8.0)
+    for w in range(args.warmup):
+        oracle_sample_rate(s, max(64, ncells // 8), 1, seed=100 + w)
+    tot_fs, tot_t, cores, nsum = 0.0, 0.0, 0, 0
+    for k in range(args.steps):
+        rate, n, dt, cores = oracle_sample_rate(s, ncells, steps, seed=k)
+        tot_fs += n * steps
+        tot_t += dt
+        nsum += n
+    value = tot_fs / tot_t
+    sample = (f"{ncells} random cells (~{nsum // args.steps} floes) of the workload, {steps} fine steps "
+              f"per bench step, FP64 oracle, OpenMP over cells")
+    line = {
+        "impl": "reference", "metric": "floe-steps/s", "value": value, "unit": "floe-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot_t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(s, "none (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "floe-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(s, l2):
+    p = s["params"]
+    return {"workload": "msDEM batched cells: 128x128 cells of 25 km, lognormal(96, 0.69) floes/cell "
+                        "clipped [8,1024], power-law radii 0.2-3 km, 8-mode ocean, rotating 6 h wind, "
+                        "dt 5 s, N0 100, n_t 10",
+            "floes": int(s["floes"]["x"].shape[0]), "cells": int(p["nx"] * p["ny"]),
+            "fine_steps_per_step": int(p["N0"]), "state": "FP32 floes, FP64 moments and coarse solve",
+            "l2": l2}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and autotune")
+    ap.add_argument("--variant", type=int, default=-1, help="force the cell-kernel variant (profiling)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    s = load_scenario(args.config)
+    if args.impl == "reference":
+        run_reference(args, s, rank)
+        return
+
+    import torch
+    from paper_2303_07819_gb300 import msdem
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    msdem.load()
+    p = s["params"]
+    dt = s["dt"]
+    N0 = int(p["N0"])
+    stream = torch.cuda.Stream()
+    model = msdem.Model(p, s["floes"], msdem.MS_FP32)
+    model.set_stream(stream.cuda_stream)
+    n_floes, ncell = model.n, model.ncell
+    if args.variant >= 0:
+        model.set_launch(args.variant, 128, 0)
+    elif not args.no_extras:
+        model.autotune(dt, reps=3)
+    info = model.info()
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        model.step(dt, N0)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        ev[k][0].record(stream)
+        model.step_async(dt, N0)
+        ev[k][1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    model.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    fine_steps = args.steps * N0
+    value = world * n_floes * fine_steps / (tot_ms / 1e3)
+    cell_rate = world * ncell * fine_steps / (tot_ms / 1e3)
+
+    hbm, peak_kind, _ = peaks()
+    kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
+    kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
+    achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
+
+    line = {
+        "metric": "floe-steps/s", "value": value, "unit": "floe-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "cell_steps_per_s": cell_rate,
+        "config": workload_config(s, "flushed before every timed step (512 MB write); state 64 MB"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "msd::k_cell_step32", "peak_source": peak_kind,
+                     "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
+                     "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso},
+        "clocks": clk,
+        "gpu_launches": args.steps * (N0 + (info["launches_per_coarse"])),
+        "launch": {"variant": info["variant"], "threads": info["threads"], "persistent": info["persistent"]},
+        "wall_s": t_wall,
+    }
+
+    if not args.no_extras and rank == 0:
+        # end to end through the public API with host buffers: upload the
+        # state, one coarse interval, read the moments back
+        host = model.floes()
+        ke = max(1, min(args.steps, 5))
+        model.set_floes(host)
+        model.step(dt, N0)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            model.set_floes(host)
+            model.step_async(dt, N0)
+            mom = model.moments()
+        te = time.perf_counter() - t0
+        line["e2e"] = {"value": world * n_floes * N0 * ke / te, "unit": "floe-steps/s",
+                       "h2d_bytes_per_step": int(32 * n_floes), "d2h_bytes_per_step": int(mom.nbytes)}
+        ncells, steps = calibrated_oracle(s, 15.0)
+        rate, n, tdt, cores = oracle_sample_rate(s, ncells, steps)
+        line["cpu_baseline"] = {"value": rate, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{ncells} random cells ({n} floes) x {steps} fine steps, "
+                                          f"{tdt:.1f} s wall, FP64, OpenMP over cells"}
+    model.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * msdem.h -- C-ABI of libmsdem.so, the GB300 (sm_103a) hot path of the
+ * particle-continuum sea-ice model "msDEM" of Deng, Stechmann & Chen
+ * (arXiv 2303.07819).
+ *
+ * The model: one doubly periodic discrete-element model (DEM) of disk floes
+ * per coarse cell (Sec. 3.1), whose per-cell moments drive a Lax-Friedrichs
+ * solution of the moment equations (Eq. 2.26 with the Oseen form Eq. 3.3,
+ * Sec. 3.2), fed back gradually into the floes (Sec. 3.3, Eqs. 3.4-3.7) on
+ * the schedule of Algorithm 1; beside it the un-localised full-domain DEM the
+ * paper compares against (Sec. 4).
+ *
+ * Conventions for every entry point
+ *  - Units are SI (m, s, kg) unless the caller picks consistent non-dimensional
+ *    values, as the paper's Sec. 4 scenarios do.
+ *  - Pointers marked "host" are ordinary CPU memory owned by the caller; the
+ *    library copies from or into them before returning.  The library never
+ *    keeps a caller pointer.
+ *  - Device memory is allocated by the library (cudaMalloc) in ms_init and
+ *    released by ms_free.  One model handle belongs to one host thread at a
+ *    time; calls on different handles are independent.
+ *  - Every call is synchronous: when it returns, its work on the model's
+ *    stream has finished and its outputs are valid.
+ *  - Return value: MS_OK (0) or a negative MS_ERR_* code; ms_last_error()
+ *    gives a message for the calling thread's last failure.
+ */
+#ifndef MSDEM_H
+#define MSDEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_NMOM 12   /* moment columns per cell, see ms_moments */
+#define MS_NWIN 5    /* accumulated-window columns, see ms_coupling */
+#define MS_MAX_MODES 16
+
+enum {
+    MS_OK = 0,
+    MS_ERR_ARG = -1,       /* invalid argument: sizes, NaN, overlap, call order of dt */
+    MS_ERR_CUDA = -2,      /* a CUDA call failed (message says which) */
+    MS_ERR_UNSTABLE = -3,  /* non-finite floe state, or an overlap deeper than r_min / 2 */
+    MS_ERR_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+    MS_ERR_STATE = -5      /* call not valid in the model's current state */
+};
+
+enum { MS_FP32 = 0, MS_FP64 = 1 };
+
+/* Coarse grid over the doubly periodic domain [0, Lx) x [0, Ly): nx x ny
+ * cells of side (Lx/nx, Ly/ny); cell c = iy * nx + ix.  Each cell carries its
+ * own periodic DEM (Sec. 3.1). */
+typedef struct ms_grid {
+    int32_t nx, ny;
+    double Lx, Ly;
+} ms_grid;
+
+/* Floe state (Sec. 2.1): centre (x, y) in domain coordinates, angle theta,
+ * velocity (u, v), spin omega, radius r, thickness h.  Host arrays of n
+ * doubles each.  A floe belongs to the cell holding its centre (half-open
+ * cells) for the whole msDEM run. */
+typedef struct ms_floes {
+    int64_t n;
+    const double *x, *y, *theta, *u, *v, *omega, *r, *h;
+} ms_floes;
+
+/* Forcing, material constants and coupling parameters.
+ *  ocean:  u_o = (uo_x, uo_y) + curl of psi, psi = sum_m A_m sin(2 pi (kx_m X/Lx
+ *          + ky_m Y/Ly) + phi_m); modes = host [n_modes][4] = (A, kx, ky, phi),
+ *          kx, ky integers, n_modes <= MS_MAX_MODES.  Drag Eq. (2.1c-d):
+ *          Cd rho_o pi r^2 (u_o - v)|u_o - v| and Cd rho_o pi r^4 (curl/2 - w)|.|.
+ *  wind:   (wind_x, wind_y) rotated by 2 pi t / wind_period (0: constant);
+ *          drag Ca rho_a pi r^2 (u_a - v)|u_a - v|, no wind torque.
+ *  ice:    mass rho_ice pi r^2 h; inertia m r^2 (inertia_half = 1: m r^2 / 2).
+ *  contact (Eq. 2.2): normal c (h_min/h_ref) (E delta + eta v_n), never
+ *          attractive; tangential c (h_min/h_ref) G v_t capped at mu |normal|.
+ *  coupling (Algorithm 1): couple = 1 runs the coarse Lax-Friedrichs step every
+ *          N0 fine steps and n_t-step gradual updates; 0 runs the cells'
+ *          DEMs alone.  N0 % n_t == 0.
+ *  precision: MS_FP32 (floe state and forces in FP32, positions as 32-bit
+ *          fixed point of the periodic cell; moments and coarse solve in FP64)
+ *          or MS_FP64 (everything in FP64). */
+typedef struct ms_forcing {
+    double uo_x, uo_y;
+    int32_t n_modes;
+    const double *modes;
+    double rho_o, Cd, rho_a, Ca;
+    double wind_x, wind_y, wind_period;
+    double rho_ice, E, G, eta, mu, h_ref;
+    int32_t inertia_half;
+    int32_t couple, N0, n_t;
+    int32_t precision;
+} ms_forcing;
+
+typedef struct ms_model ms_model;
+
+/* Create a model on the current CUDA device: validates the inputs, assigns
+ * floes to cells, builds the per-cell floe layout on the device (floes of a
+ * cell contiguous), uploads the state and a second copy for the truth DEM.
+ * Rejects (MS_ERR_ARG): nx, ny < 1; non-positive or non-finite sizes; n < 0;
+ * non-finite floe values; r <= 0 or h <= 0; 2 r_max >= half the smaller cell
+ * side (the periodic minimum image would be ambiguous); a cell with more than
+ * 4096 floes (FP32) or 2048 (FP64); non-integer wave numbers.
+ * *out receives the handle (NULL on failure). */
+int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes,
+            const ms_forcing *forcing);
+
+/* Advance the msDEM model by nsteps fine steps of dt (forward Euler,
+ * Sec. 3.1), running the coarse step and the gradual updates of Algorithm 1
+ * when couple = 1.  The first call fixes dt; a later call with another dt
+ * returns MS_ERR_ARG.  nsteps = 0 is a no-op.  Full coarse intervals replay a
+ * captured CUDA graph.  MS_ERR_UNSTABLE if the state became non-finite or an
+ * overlap deeper than half the smaller radius appeared. */
+int ms_step(ms_model *m, double dt, int64_t nsteps);
+
+/* As ms_step, but only enqueues the work on the model's stream and returns;
+ * errors raised by the kernels surface at the next synchronous call (ms_sync,
+ * ms_moments, ...).  For callers that time or overlap the step themselves. */
+int ms_step_async(ms_model *m, double dt, int64_t nsteps);
+
+/* Wait for the model's stream and report errors raised by its kernels. */
+int ms_sync(ms_model *m);
+
+/* Moments of the current msDEM state per cell, host out[ncell][MS_NMOM]
+ * (FP64): 0 n, 1 sum m, 2 sum m u, 3 sum m v, 4 sum I, 5 sum I omega,
+ * 6 sum pi r^2, 7 sum m u^2, 8 sum m v^2, 9 sum Fdrag_x, 10 sum Fdrag_y,
+ * 11 sum Tdrag (drag of the last step; zero before the first).
+ * Mass density rho = col1 / A_c, concentration = col6 / A_c (Sec. 2.3, 4.1). */
+int ms_moments(ms_model *m, double *out);
+
+/* Floe state of the msDEM model, host out[8][n] in the caller's original
+ * floe order, domain coordinates: x, y, theta, u, v, omega, r, h. */
+int ms_get_floes(ms_model *m, double *out);
+
+/* Replace the msDEM floe state (same n, every floe in the cell it started
+ * in; MS_ERR_ARG otherwise) from host arrays.  The coupling state is kept. */
+int ms_set_floes(ms_model *m, const ms_floes *floes);
+
+/* Coupling state, host arrays (any may be NULL): q[4][ncell] coarse solution
+ * (rho, rho u, rho v, P_omega per unit area), targets[4][ncell] of the
+ * gradual update (radius scale, du, dv, domega), window[MS_NWIN][ncell]
+ * sums over the current coarse step of (mean u, mean v, sum Fdrag_x,
+ * sum Fdrag_y, sum Tdrag), flags[3] = (coarse state set, targets set, steps). */
+int ms_coupling(ms_model *m, double *q, double *targets, double *window,
+                int64_t *flags);
+
+/* The un-localised truth DEM (Sec. 4): the same floes on the whole periodic
+ * domain, advanced on the library's own copy (rebinned every step by a GPU
+ * counting sort).  Same dt rule as ms_step. */
+int ms_truth_step(ms_model *m, double dt, int64_t nsteps);
+
+/* Truth floes binned by the coarse cell holding their centre; same columns
+ * as ms_moments. */
+int ms_truth_moments(ms_model *m, double *out);
+
+/* Truth floe state, host out[8][n], original order, domain coordinates. */
+int ms_truth_get_floes(ms_model *m, double *out);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*) for all later work;
+ * NULL selects the library's own stream.  The caller keeps the stream alive
+ * while the model uses it. */
+int ms_set_stream(ms_model *m, void *stream);
+
+/* Autotune the msDEM cell kernel on the model's current state: times each
+ * launch variant (pair search, threads per block, bin width) for `reps`
+ * launches out of place (the state is not changed) and keeps the fastest.
+ * best_ms (host, may be NULL) receives its mean launch time. */
+int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
+
+/* Choose the cell-kernel launch by hand: variant 0 = brute-force pairs within
+ * the cell, 1 = binned pair search (FP32 only); threads per block 64, 128 or
+ * 256; persistent = 1 runs a grid of resident blocks that take cells from a
+ * work queue (largest cells first); bin_beta = bin side in units of the cell's
+ * mean floe spacing (variant 1).  MS_ERR_ARG for an unsupported choice. */
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
+
+/* Mean device time (ms, CUDA events on the model's stream) of `reps`
+ * out-of-place launches of the msDEM cell-step kernel (which = 0) or of the
+ * truth step kernel (which = 1) on the current state; the state is not
+ * changed. */
+int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *mean_ms);
+
+/* Model facts, host out[16] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
+ * 4 kernel variant, 5 threads per block, 6 bin width (per mille of the mean
+ * floe spacing), 7 kernels launched per fine step (msDEM, no coarse step),
+ * 8 kernels per coarse step, 9 kernels per truth step, 10 steps done,
+ * 11 truth steps done, 12 graph replays so far, 13-15 reserved. */
+int ms_info(ms_model *m, int64_t *out);
+
+/* Release the model's device memory, graphs, events and stream. */
+void ms_free(ms_model *m);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *ms_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1004 @@
+// api.cu -- host side of libmsdem: validation, device layout, the
+// Algorithm 1 schedule (fine steps, coarse steps, gradual updates) captured
+// in CUDA graphs, the truth DEM driver, and the C-ABI of include/msdem.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "../../include/msdem.h"
+
+using namespace msd;
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(MS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+static const double PI_D = 3.14159265358979323846;
+
+struct ms_model {
+    int precision = 0;
+    ms_grid grid{};
+    ms_forcing fc{};
+    std::vector<double> modes;
+    long long n = 0;
+    int ncell = 0, max_n = 0;
+    Geom g{};
+    Phys<float> P32{};
+    Phys<double> P64{};
+    // layout: stored floe k of cell c at off[c] + ...; orig[k] = caller's index
+    std::vector<int> h_off, h_order, h_cell_of_orig;
+    std::vector<long long> h_orig;
+    int *d_off = nullptr, *d_order = nullptr;
+    // msDEM state and its scratch copy for out-of-place timing
+    DevState32 s32{}, x32{};
+    DevState64 s64{}, x64{};
+    double *d_mom = nullptr, *d_win = nullptr, *d_q0 = nullptr, *d_q1 = nullptr, *d_V = nullptr,
+           *d_S = nullptr, *d_tgt = nullptr, *d_xmom = nullptr, *d_xwin = nullptr;
+    Ctrl *d_ctrl = nullptr;
+    // truth
+    DevState32 t32[2]{};
+    DevState64 t64[2]{};
+    int tcur = 0;
+    void *d_fd = nullptr;
+    TruthBins tb{}, cb{};
+    double *d_tmom = nullptr;
+    // schedule
+    long long steps = 0, truth_steps = 0;
+    double dt = 0.0, truth_dt = 0.0;
+    int interval = 100;   // steps per coarse interval (graph length)
+    cudaStream_t stream = nullptr, own_stream = nullptr;
+    CellLaunch cl{};
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_failed = false;
+    long long replays = 0;
+    int sm_count = 0;
+    // host staging (pinned)
+    void *h_stage = nullptr;
+    size_t h_stage_bytes = 0;
+    std::vector<void *> allocs;
+};
+
+// ---------------------------------------------------------------- helpers
+template <class T>
+static cudaError_t dalloc(ms_model *m, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count > 0 ? count : 1));
+    if (e != cudaSuccess) return e;
+    m->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return cudaSuccess;
+}
+
+static cudaError_t alloc32(ms_model *m, DevState32 &s, size_t n)
+{
+    cudaError_t e;
+    if ((e = dalloc(m, &s.xq, n)) || (e = dalloc(m, &s.yq, n)) || (e = dalloc(m, &s.th, n)) ||
+        (e = dalloc(m, &s.u, n)) || (e = dalloc(m, &s.v, n)) || (e = dalloc(m, &s.w, n)) ||
+        (e = dalloc(m, &s.r, n)) || (e = dalloc(m, &s.h, n)))
+        return e;
+    return cudaSuccess;
+}
+
+static cudaError_t alloc64(ms_model *m, DevState64 &s, size_t n)
+{
+    cudaError_t e;
+    if ((e = dalloc(m, &s.x, n)) || (e = dalloc(m, &s.y, n)) || (e = dalloc(m, &s.th, n)) ||
+        (e = dalloc(m, &s.u, n)) || (e = dalloc(m, &s.v, n)) || (e = dalloc(m, &s.w, n)) ||
+        (e = dalloc(m, &s.r, n)) || (e = dalloc(m, &s.h, n)))
+        return e;
+    return cudaSuccess;
+}
+
+// Pinned host staging buffer.  Copies from and to it are asynchronous, so
+// every use first waits for the model's stream: a previous upload may still
+// be reading it.
+static void *stage(ms_model *m, size_t bytes)
+{
+    if (m->stream && cudaStreamSynchronize(m->stream) != cudaSuccess) return nullptr;
+    if (bytes > m->h_stage_bytes) {
+        if (m->h_stage) cudaFreeHost(m->h_stage);
+        m->h_stage = nullptr;
+        m->h_stage_bytes = 0;
+        if (cudaMallocHost(&m->h_stage, bytes) != cudaSuccess) return nullptr;
+        m->h_stage_bytes = bytes;
+    }
+    return m->h_stage;
+}
+
+static bool isfin(double x) { return std::isfinite(x); }
+
+static int cell_index(double X, double L, double d, int n)
+{
+    double Xw = X - L * std::floor(X / L);
+    int i = (int)std::floor(Xw / d);
+    if (i < 0) i = 0;
+    if (i > n - 1) i = n - 1;
+    return i;
+}
+
+static uint32_t to_fix(double frac)
+{
+    // fraction of the periodic box -> 32-bit fixed point (2^32 == 1, wraps)
+    double v = std::nearbyint(frac * 4294967296.0);
+    long long iv = (long long)v;
+    return (uint32_t)(iv & 0xffffffffLL);
+}
+
+static double from_fix(uint32_t q) { return (double)q * (1.0 / 4294967296.0); }
+
+static int validate_floes(const ms_floes *f, long long expect_n)
+{
+    if (!f) return fail(MS_ERR_ARG, "floes is NULL");
+    if (f->n < 0) return fail(MS_ERR_ARG, "floes->n = %lld < 0", (long long)f->n);
+    if (expect_n >= 0 && f->n != expect_n)
+        return fail(MS_ERR_ARG, "floes->n = %lld, model has %lld floes", (long long)f->n, expect_n);
+    if (f->n > 0 && (!f->x || !f->y || !f->theta || !f->u || !f->v || !f->omega || !f->r || !f->h))
+        return fail(MS_ERR_ARG, "a floe array is NULL");
+    if (f->n > (long long)0x7fffffff) return fail(MS_ERR_ARG, "more than 2^31-1 floes");
+    for (long long l = 0; l < f->n; l++) {
+        if (!(isfin(f->x[l]) && isfin(f->y[l]) && isfin(f->theta[l]) && isfin(f->u[l]) &&
+              isfin(f->v[l]) && isfin(f->omega[l]) && isfin(f->r[l]) && isfin(f->h[l])))
+            return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
+        if (!(f->r[l] > 0.0) || !(f->h[l] > 0.0))
+            return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
+    }
+    return MS_OK;
+}
+
+// upload floes (already validated and assigned) into the msDEM layout
+static int upload_model_state(ms_model *m, const ms_floes *f)
+{
+    const long long n = m->n;
+    const int nx = m->g.nx;
+    if (n == 0) return MS_OK;
+    if (m->precision == MS_FP64) {
+        double *st = (double *)stage(m, sizeof(double) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(64 * n));
+        for (long long k = 0; k < n; k++) {
+            const long long l = m->h_orig[k];
+            const int c = m->h_cell_of_orig[l];
+            const int ix = c % nx, iy = c / nx;
+            const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+            const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+            st[k] = Xw - ix * m->g.Lcx;
+            st[n + k] = Yw - iy * m->g.Lcy;
+            st[2 * n + k] = f->theta[l];
+            st[3 * n + k] = f->u[l];
+            st[4 * n + k] = f->v[l];
+            st[5 * n + k] = f->omega[l];
+            st[6 * n + k] = f->r[l];
+            st[7 * n + k] = f->h[l];
+        }
+        double *dst[8] = {m->s64.x, m->s64.y, m->s64.th, m->s64.u, m->s64.v, m->s64.w, m->s64.r, m->s64.h};
+        for (int a = 0; a < 8; a++)
+            CK(cudaMemcpyAsync(dst[a], st + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
+    } else {
+        unsigned char *st = (unsigned char *)stage(m, sizeof(float) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(32 * n));
+        uint32_t *qx = (uint32_t *)st, *qy = qx + n;
+        float *fl = (float *)(qy + n);
+        for (long long k = 0; k < n; k++) {
+            const long long l = m->h_orig[k];
+            const int c = m->h_cell_of_orig[l];
+            const int ix = c % nx, iy = c / nx;
+            const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+            const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+            qx[k] = to_fix((Xw - ix * m->g.Lcx) / m->g.Lcx);
+            qy[k] = to_fix((Yw - iy * m->g.Lcy) / m->g.Lcy);
+            fl[k] = (float)f->theta[l];
+            fl[n + k] = (float)f->u[l];
+            fl[2 * n + k] = (float)f->v[l];
+            fl[3 * n + k] = (float)f->omega[l];
+            fl[4 * n + k] = (float)f->r[l];
+            fl[5 * n + k] = (float)f->h[l];
+        }
+        CK(cudaMemcpyAsync(m->s32.xq, qx, 4 * n, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->s32.yq, qy, 4 * n, cudaMemcpyHostToDevice, m->stream));
+        float *dst[6] = {m->s32.th, m->s32.u, m->s32.v, m->s32.w, m->s32.r, m->s32.h};
+        for (int a = 0; a < 6; a++)
+            CK(cudaMemcpyAsync(dst[a], fl + a * n, 4 * n, cudaMemcpyHostToDevice, m->stream));
+    }
+    return MS_OK;
+}
+
+static int upload_truth_state(ms_model *m, const ms_floes *f)
+{
+    const long long n = m->n;
+    if (n == 0) return MS_OK;
+    if (m->precision == MS_FP64) {
+        double *st = (double *)stage(m, sizeof(double) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+        for (long long l = 0; l < n; l++) {
+            st[l] = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+            st[n + l] = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+            st[2 * n + l] = f->theta[l];
+            st[3 * n + l] = f->u[l];
+            st[4 * n + l] = f->v[l];
+            st[5 * n + l] = f->omega[l];
+            st[6 * n + l] = f->r[l];
+            st[7 * n + l] = f->h[l];
+        }
+        DevState64 &s = m->t64[m->tcur];
+        double *dst[8] = {s.x, s.y, s.th, s.u, s.v, s.w, s.r, s.h};
+        for (int a = 0; a < 8; a++)
+            CK(cudaMemcpyAsync(dst[a], st + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
+    } else {
+        unsigned char *st = (unsigned char *)stage(m, sizeof(float) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+        uint32_t *qx = (uint32_t *)st, *qy = qx + n;
+        float *fl = (float *)(qy + n);
+        for (long long l = 0; l < n; l++) {
+            const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+            const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+            qx[l] = to_fix(Xw / m->g.Lx);
+            qy[l] = to_fix(Yw / m->g.Ly);
+            fl[l] = (float)f->theta[l];
+            fl[n + l] = (float)f->u[l];
+            fl[2 * n + l] = (float)f->v[l];
+            fl[3 * n + l] = (float)f->omega[l];
+            fl[4 * n + l] = (float)f->r[l];
+            fl[5 * n + l] = (float)f->h[l];
+        }
+        DevState32 &s = m->t32[m->tcur];
+        CK(cudaMemcpyAsync(s.xq, qx, 4 * n, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(s.yq, qy, 4 * n, cudaMemcpyHostToDevice, m->stream));
+        float *dst[6] = {s.th, s.u, s.v, s.w, s.r, s.h};
+        for (int a = 0; a < 6; a++)
+            CK(cudaMemcpyAsync(dst[a], fl + a * n, 4 * n, cudaMemcpyHostToDevice, m->stream));
+    }
+    CK(cudaMemsetAsync(m->d_fd, 0, (m->precision == MS_FP64 ? 8 : 4) * 3 * n, m->stream));
+    return MS_OK;
+}
+
+static StepCommon step_common(ms_model *m, long long i_local, double *mom, double *win)
+{
+    StepCommon sc;
+    sc.off = m->d_off;
+    sc.order = m->d_order;
+    sc.ncell = m->ncell;
+    sc.max_n = m->max_n;
+    sc.mom = mom;
+    sc.win = win;
+    sc.tgt = m->d_tgt;
+    sc.ctrl = m->d_ctrl;
+    sc.g = m->g;
+    sc.dt = m->dt;
+    sc.N0 = m->fc.N0;
+    sc.n_t = m->fc.n_t;
+    sc.couple = m->fc.couple;
+    sc.i_local = i_local;
+    return sc;
+}
+
+static CoarseArgs coarse_args(ms_model *m)
+{
+    CoarseArgs a;
+    a.nx = m->g.nx;
+    a.ny = m->g.ny;
+    a.dx = m->g.Lcx;
+    a.dy = m->g.Lcy;
+    a.Ac = m->g.Lcx * m->g.Lcy;
+    a.dT = (double)m->fc.N0 * m->dt;
+    a.N0 = m->fc.N0;
+    a.mom = m->d_mom;
+    a.win = m->d_win;
+    a.q0 = m->d_q0;
+    a.q1 = m->d_q1;
+    a.V = m->d_V;
+    a.S = m->d_S;
+    a.tgt = m->d_tgt;
+    a.ctrl = m->d_ctrl;
+    return a;
+}
+
+static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
+{
+    StepCommon sc = step_common(m, i_local, scratch_out ? m->d_xmom : m->d_mom,
+                                scratch_out ? m->d_xwin : m->d_win);
+    if (m->precision == MS_FP64)
+        return launch_cell_step64(m->s64, scratch_out ? m->x64 : m->s64, m->P64, sc, m->cl, m->stream);
+    return launch_cell_step32(m->s32, scratch_out ? m->x32 : m->s32, m->P32, sc, m->cl, m->stream);
+}
+
+// the work that closes a coarse interval: coarse step (coupled) or base += N0
+static cudaError_t launch_interval_end(ms_model *m)
+{
+    if (m->fc.couple) return launch_coarse_step(coarse_args(m), m->stream);
+    return launch_advance(m->d_ctrl, m->interval, m->stream);
+}
+
+static void drop_graph(ms_model *m)
+{
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    m->gexec = nullptr;
+}
+
+static cudaError_t build_graph(ms_model *m)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
+    if (le == cudaSuccess) le = launch_interval_end(m);
+    e = cudaStreamEndCapture(m->stream, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+static int read_errors(ms_model *m)
+{
+    Ctrl c;
+    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (c.err & ERR_TIMEOUT) return fail(MS_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (c.err & ERR_NONFINITE) return fail(MS_ERR_UNSTABLE, "floe state became non-finite");
+    if (c.err & ERR_CFL)
+        return fail(MS_ERR_UNSTABLE, "coarse step needs N1 = %d > %d Lax-Friedrichs substeps", c.N1, NSUB_MAX);
+    return MS_OK;
+}
+
+static void fill_phys(ms_model *m)
+{
+    const ms_forcing &f = m->fc;
+    Phys<double> &P = m->P64;
+    Phys<float> &Q = m->P32;
+    std::memset(&P, 0, sizeof(P));
+    std::memset(&Q, 0, sizeof(Q));
+    P.uo_x = f.uo_x; P.uo_y = f.uo_y;
+    P.n_modes = Q.n_modes = f.n_modes;
+    for (int k = 0; k < f.n_modes; k++) {
+        const double *md = &m->modes[4 * k];
+        const double kx = 2.0 * PI_D * md[1] / m->grid.Lx, ky = 2.0 * PI_D * md[2] / m->grid.Ly;
+        P.mA[k] = md[0]; P.mKx[k] = kx; P.mKy[k] = ky; P.mPh[k] = md[3];
+        Q.mkx[k] = (int)md[1]; Q.mky[k] = (int)md[2];
+        double cyc = md[3] / (2.0 * PI_D);
+        cyc -= std::floor(cyc);
+        Q.mCyc[k] = (float)cyc;
+        Q.mAu[k] = (float)(md[0] * ky);
+        Q.mAv[k] = (float)(md[0] * kx);
+        Q.mAz[k] = (float)(md[0] * (kx * kx + ky * ky));
+        Q.mA[k] = (float)md[0];
+    }
+    P.drag_o = f.Cd * f.rho_o * PI_D;
+    P.drag_a = f.Ca * f.rho_a * PI_D;
+    P.wind_x = f.wind_x; P.wind_y = f.wind_y;
+    P.wind_w = f.wind_period > 0.0 ? 2.0 * PI_D / f.wind_period : 0.0;
+    P.mass_c = f.rho_ice * PI_D;
+    P.inertia_f = f.inertia_half ? 0.5 : 1.0;
+    P.E = f.E; P.G = f.G; P.eta = f.eta; P.mu = f.mu; P.inv_h_ref = 1.0 / f.h_ref;
+    Q.uo_x = (float)P.uo_x; Q.uo_y = (float)P.uo_y;
+    Q.drag_o = (float)P.drag_o; Q.drag_a = (float)P.drag_a;
+    Q.wind_x = (float)P.wind_x; Q.wind_y = (float)P.wind_y; Q.wind_w = (float)P.wind_w;
+    Q.mass_c = (float)P.mass_c; Q.inertia_f = (float)P.inertia_f;
+    Q.E = (float)P.E; Q.G = (float)P.G; Q.eta = (float)P.eta; Q.mu = (float)P.mu;
+    Q.inv_h_ref = (float)P.inv_h_ref;
+}
+
+// Binned variant: split the cells (largest first) into size classes, each
+// launched with a block size and shared memory that fit its largest cell.
+static void make_segments(ms_model *m, CellLaunch &c)
+{
+    const int bounds[MAXSEG] = {1 << 30, 512, 256, 64};
+    const int threads[MAXSEG] = {256, 256, 128, 64};
+    c.nseg = 0;
+    c.nbmax = 32;
+    int item = 0;
+    const int nc = m->ncell;
+    auto ncount = [&](int it) { const int cc = m->h_order[it]; return m->h_off[cc + 1] - m->h_off[cc]; };
+    for (int s = 0; s < MAXSEG && item < nc; s++) {
+        const int lo = (s + 1 < MAXSEG) ? bounds[s + 1] : -1;
+        int e = item;
+        while (e < nc && ncount(e) > lo) e++;
+        if (e == item) continue;
+        c.seg_begin[c.nseg] = item;
+        c.seg_end[c.nseg] = e;
+        c.seg_maxn[c.nseg] = std::max(1, ncount(item));
+        c.seg_threads[c.nseg] = threads[s];
+        c.nseg++;
+        item = e;
+    }
+}
+
+static int configure_launch(ms_model *m, const CellLaunch &cl_in)
+{
+    CellLaunch cl = cl_in;
+    if (cl.variant == 1) make_segments(m, cl);
+    const size_t smem = cell_step_smem(m->precision, cl, m->max_n, m->g.nx, m->g.ny);
+    if (smem > 227 * 1024) return fail(MS_ERR_ARG, "cell of %d floes needs %zu B of shared memory", m->max_n, smem);
+    CK(cell_step_prepare(m->precision, cl, smem));
+    m->cl = cl;
+    drop_graph(m);
+    return MS_OK;
+}
+
+static int setup_truth_bins(ms_model *m, double rmax)
+{
+    // bins of side >= 2 r_max; fewer than 3 along an axis -> one bin on that axis
+    int nbx = (int)std::floor(m->g.Lx / (2.0 * rmax));
+    int nby = (int)std::floor(m->g.Ly / (2.0 * rmax));
+    if (nbx < 3) nbx = 1;
+    if (nby < 3) nby = 1;
+    while ((long long)nbx * nby > (1LL << 20)) {
+        if (nbx >= nby) nbx = std::max(3, nbx / 2); else nby = std::max(3, nby / 2);
+    }
+    TruthBins *bs[2] = {&m->tb, &m->cb};
+    int dims[2][2] = {{nbx, nby}, {m->g.nx, m->g.ny}};
+    for (int k = 0; k < 2; k++) {
+        TruthBins &b = *bs[k];
+        b.nbx = dims[k][0];
+        b.nby = dims[k][1];
+        const int nbins = b.nbx * b.nby;
+        b.nscan_blocks = (nbins + 1023) / 1024;
+        if (b.nscan_blocks > 1024) return fail(MS_ERR_ARG, "too many bins (%d)", nbins);
+        CK(dalloc(m, &b.count, nbins));
+        CK(dalloc(m, &b.start, nbins + 1));
+        CK(dalloc(m, &b.cursor, nbins));
+        CK(dalloc(m, &b.sorted, m->n));
+        CK(dalloc(m, &b.bin, m->n));
+        CK(dalloc(m, &b.scan_tmp, b.nscan_blocks));
+        const int nn = (int)m->n;
+        CK(cudaMemcpyAsync(b.start + nbins, &nn, sizeof(int), cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
+    return MS_OK;
+}
+
+// ================================================================== C-ABI
+extern "C" {
+
+const char *ms_last_error(void) { return g_err.c_str(); }
+
+void ms_free(ms_model *m)
+{
+    if (!m) return;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    drop_graph(m);
+    for (void *p : m->allocs) cudaFree(p);
+    if (m->h_stage) cudaFreeHost(m->h_stage);
+    if (m->own_stream) cudaStreamDestroy(m->own_stream);
+    delete m;
+}
+
+int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms_forcing *forcing)
+{
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!grid || !forcing) return fail(MS_ERR_ARG, "grid or forcing is NULL");
+    if (grid->nx < 1 || grid->ny < 1) return fail(MS_ERR_ARG, "grid needs nx, ny >= 1");
+    if ((long long)grid->nx * grid->ny > (1LL << 24)) return fail(MS_ERR_ARG, "more than 2^24 cells");
+    if (!(grid->Lx > 0.0) || !(grid->Ly > 0.0) || !isfin(grid->Lx) || !isfin(grid->Ly))
+        return fail(MS_ERR_ARG, "domain sides must be positive and finite");
+    const ms_forcing &f = *forcing;
+    if (f.precision != MS_FP32 && f.precision != MS_FP64) return fail(MS_ERR_ARG, "precision must be MS_FP32 or MS_FP64");
+    if (f.n_modes < 0 || f.n_modes > MS_MAX_MODES) return fail(MS_ERR_ARG, "n_modes must be in [0, %d]", MS_MAX_MODES);
+    if (f.n_modes > 0 && !f.modes) return fail(MS_ERR_ARG, "modes is NULL");
+    for (int k = 0; k < f.n_modes; k++) {
+        for (int a = 0; a < 4; a++)
+            if (!isfin(f.modes[4 * k + a])) return fail(MS_ERR_ARG, "mode %d is not finite", k);
+        if (f.modes[4 * k + 1] != std::floor(f.modes[4 * k + 1]) || f.modes[4 * k + 2] != std::floor(f.modes[4 * k + 2]) ||
+            std::fabs(f.modes[4 * k + 1]) > 1024 || std::fabs(f.modes[4 * k + 2]) > 1024)
+            return fail(MS_ERR_ARG, "mode %d: wave numbers must be integers of magnitude <= 1024", k);
+    }
+    const double vals[] = {f.uo_x, f.uo_y, f.rho_o, f.Cd, f.rho_a, f.Ca, f.wind_x, f.wind_y, f.wind_period,
+                           f.rho_ice, f.E, f.G, f.eta, f.mu, f.h_ref};
+    for (double v : vals)
+        if (!isfin(v)) return fail(MS_ERR_ARG, "a forcing constant is not finite");
+    if (!(f.rho_ice > 0.0) || !(f.h_ref > 0.0)) return fail(MS_ERR_ARG, "rho_ice and h_ref must be positive");
+    if (f.E < 0 || f.G < 0 || f.eta < 0 || f.mu < 0 || f.Cd < 0 || f.Ca < 0 || f.rho_o < 0 || f.rho_a < 0 ||
+        f.wind_period < 0)
+        return fail(MS_ERR_ARG, "material and drag constants must be non-negative");
+    if (f.couple && (f.N0 <= 0 || f.n_t <= 0 || f.N0 % f.n_t != 0))
+        return fail(MS_ERR_ARG, "coupling needs N0 > 0, n_t > 0 and N0 %% n_t == 0");
+    int rc = validate_floes(floes, -1);
+    if (rc) return rc;
+
+    ms_model *m = new ms_model();
+    m->precision = f.precision;
+    m->grid = *grid;
+    m->fc = f;
+    m->modes.assign(f.modes ? f.modes : nullptr, f.modes ? f.modes + 4 * f.n_modes : nullptr);
+    m->fc.modes = m->modes.data();
+    m->n = floes->n;
+    m->ncell = grid->nx * grid->ny;
+    m->g.nx = grid->nx;
+    m->g.ny = grid->ny;
+    m->g.Lx = grid->Lx;
+    m->g.Ly = grid->Ly;
+    m->g.Lcx = grid->Lx / grid->nx;
+    m->g.Lcy = grid->Ly / grid->ny;
+    m->interval = f.couple ? f.N0 : 100;
+    fill_phys(m);
+
+    // stable assignment of floes to cells; reject ambiguous minimum images
+    const long long n = m->n;
+    double rmax = 0.0;
+    m->h_cell_of_orig.resize(n);
+    m->h_off.assign(m->ncell + 1, 0);
+    for (long long l = 0; l < n; l++) {
+        const int c = cell_index(floes->y[l], grid->Ly, m->g.Lcy, grid->ny) * grid->nx +
+                      cell_index(floes->x[l], grid->Lx, m->g.Lcx, grid->nx);
+        m->h_cell_of_orig[l] = c;
+        m->h_off[c + 1]++;
+        rmax = std::max(rmax, floes->r[l]);
+    }
+    if (n > 0 && !(2.0 * rmax < 0.5 * std::min(m->g.Lcx, m->g.Lcy))) {
+        ms_free(m);
+        return fail(MS_ERR_ARG, "2 r_max = %g m must be below half the cell side (%g m)", 2.0 * rmax,
+                    0.5 * std::min(m->g.Lcx, m->g.Lcy));
+    }
+    for (int c = 0; c < m->ncell; c++) {
+        m->max_n = std::max(m->max_n, m->h_off[c + 1]);
+        m->h_off[c + 1] += m->h_off[c];
+    }
+    const int cap = m->precision == MS_FP64 ? 2048 : 4096;
+    if (m->max_n > cap) {
+        int mx = m->max_n;
+        ms_free(m);
+        return fail(MS_ERR_ARG, "a cell holds %d floes; at most %d are supported", mx, cap);
+    }
+    m->h_orig.resize(n);
+    {
+        std::vector<int> fill(m->h_off.begin(), m->h_off.end() - 1);
+        for (long long l = 0; l < n; l++) m->h_orig[fill[m->h_cell_of_orig[l]]++] = l;
+    }
+    m->h_order.resize(m->ncell);
+    for (int c = 0; c < m->ncell; c++) m->h_order[c] = c;
+    std::stable_sort(m->h_order.begin(), m->h_order.end(), [&](int a, int b) {
+        return (m->h_off[a + 1] - m->h_off[a]) > (m->h_off[b + 1] - m->h_off[b]);
+    });
+
+    int dev = 0;
+    cudaError_t e;
+#define CKM(call)                                                                                 \
+    do {                                                                                          \
+        if ((e = (call)) != cudaSuccess) {                                                        \
+            ms_free(m);                                                                           \
+            return fail(MS_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e));              \
+        }                                                                                         \
+    } while (0)
+    CKM(cudaGetDevice(&dev));
+    CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
+    m->stream = m->own_stream;
+    const int nc = m->ncell;
+    CKM(dalloc(m, &m->d_off, nc + 1));
+    CKM(dalloc(m, &m->d_order, nc));
+    CKM(dalloc(m, &m->d_mom, (size_t)nc * NMOM));
+    CKM(dalloc(m, &m->d_win, (size_t)nc * NWIN));
+    CKM(dalloc(m, &m->d_xmom, (size_t)nc * NMOM));
+    CKM(dalloc(m, &m->d_xwin, (size_t)nc * NWIN));
+    CKM(dalloc(m, &m->d_q0, (size_t)nc * 4));
+    CKM(dalloc(m, &m->d_q1, (size_t)nc * 4));
+    CKM(dalloc(m, &m->d_V, (size_t)nc * 2));
+    CKM(dalloc(m, &m->d_S, (size_t)nc * 4));
+    CKM(dalloc(m, &m->d_tgt, (size_t)nc * 4));
+    CKM(dalloc(m, &m->d_tmom, (size_t)nc * NMOM));
+    CKM(dalloc(m, &m->d_ctrl, 1));
+    if (m->precision == MS_FP64) {
+        CKM(alloc64(m, m->s64, n));
+        CKM(alloc64(m, m->t64[0], n));
+        CKM(alloc64(m, m->t64[1], n));
+        CKM(dalloc(m, (double **)&m->d_fd, 3 * (size_t)n));
+    } else {
+        CKM(alloc32(m, m->s32, n));
+        CKM(alloc32(m, m->t32[0], n));
+        CKM(alloc32(m, m->t32[1], n));
+        CKM(dalloc(m, (float **)&m->d_fd, 3 * (size_t)n));
+    }
+    CKM(cudaMemsetAsync(m->d_ctrl, 0, sizeof(Ctrl), m->stream));
+    CKM(cudaMemsetAsync(m->d_win, 0, sizeof(double) * nc * NWIN, m->stream));
+    CKM(cudaMemsetAsync(m->d_q0, 0, sizeof(double) * nc * 4, m->stream));
+    CKM(cudaMemsetAsync(m->d_tgt, 0, sizeof(double) * nc * 4, m->stream));
+    CKM(cudaMemcpyAsync(m->d_off, m->h_off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, m->stream));
+    CKM(cudaMemcpyAsync(m->d_order, m->h_order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
+    CKM(cudaStreamSynchronize(m->stream));
+#undef CKM
+    if ((rc = upload_model_state(m, floes)) || (rc = upload_truth_state(m, floes)) ||
+        (rc = setup_truth_bins(m, rmax > 0 ? rmax : 1.0))) {
+        ms_free(m);
+        return rc;
+    }
+    CellLaunch cl{};
+    cl.variant = m->precision == MS_FP32 ? 1 : 0;
+    cl.threads = 128;
+    cl.bin_beta = 1.0f;
+    cl.persistent = 0;
+    cl.grid = m->sm_count * 4;
+    if (cl.variant == 1 && configure_launch(m, cl) != MS_OK) cl.variant = 0;   // cells too large to bin in shared memory
+    if ((rc = configure_launch(m, cl))) {
+        ms_free(m);
+        return rc;
+    }
+    StepCommon sc = step_common(m, 0, m->d_mom, m->d_win);
+    e = m->precision == MS_FP64 ? launch_cell_moments64(m->s64, m->P64, sc, m->stream)
+                                : launch_cell_moments32(m->s32, m->P32, sc, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        ms_free(m);
+        return fail(MS_ERR_CUDA, "initial moments failed: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return MS_OK;
+}
+
+int ms_set_stream(ms_model *m, void *stream)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    CK(cudaStreamSynchronize(m->stream));
+    m->stream = stream ? (cudaStream_t)stream : m->own_stream;
+    return MS_OK;
+}
+
+static int step_enqueue(ms_model *m, double dt, int64_t nsteps);
+
+int ms_step(ms_model *m, double dt, int64_t nsteps)
+{
+    int rc = step_enqueue(m, dt, nsteps);
+    if (rc) return rc;
+    return read_errors(m);
+}
+
+int ms_step_async(ms_model *m, double dt, int64_t nsteps) { return step_enqueue(m, dt, nsteps); }
+
+int ms_sync(ms_model *m)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    return read_errors(m);
+}
+
+static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (!(dt > 0.0) || !isfin(dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
+    if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
+    if (m->dt == 0.0) m->dt = dt;
+    else if (dt != m->dt) return fail(MS_ERR_ARG, "dt = %g differs from the model's dt = %g", dt, m->dt);
+    const int N = m->interval;
+    while (nsteps > 0) {
+        const long long i_local = m->steps % N;
+        if (i_local == 0 && nsteps >= N && !m->graph_failed) {
+            if (!m->gexec) {
+                cudaError_t e = build_graph(m);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    m->graph_failed = true;
+                    drop_graph(m);
+                    continue;
+                }
+            }
+            CK(cudaGraphLaunch(m->gexec, m->stream));
+            m->replays++;
+            m->steps += N;
+            nsteps -= N;
+            continue;
+        }
+        CK(launch_step(m, i_local, false));
+        m->steps++;
+        nsteps--;
+        if (m->steps % N == 0) CK(launch_interval_end(m));
+    }
+    return MS_OK;
+}
+
+int ms_moments(ms_model *m, double *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    double *st = (double *)stage(m, sizeof(double) * m->ncell * NMOM);
+    if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+    CK(cudaMemcpyAsync(st, m->d_mom, sizeof(double) * m->ncell * NMOM, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    std::memcpy(out, st, sizeof(double) * m->ncell * NMOM);
+    return MS_OK;
+}
+
+int ms_coupling(ms_model *m, double *q, double *targets, double *window, int64_t *flags)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    const size_t nc = m->ncell;
+    if (q) CK(cudaMemcpyAsync(q, m->d_q0, sizeof(double) * 4 * nc, cudaMemcpyDeviceToHost, m->stream));
+    if (targets) CK(cudaMemcpyAsync(targets, m->d_tgt, sizeof(double) * 4 * nc, cudaMemcpyDeviceToHost, m->stream));
+    if (window) CK(cudaMemcpyAsync(window, m->d_win, sizeof(double) * NWIN * nc, cudaMemcpyDeviceToHost, m->stream));
+    Ctrl c;
+    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    if (flags) {
+        flags[0] = c.have_q;
+        flags[1] = c.have_tgt;
+        flags[2] = m->steps;
+    }
+    return MS_OK;
+}
+
+static int download(ms_model *m, bool truth, double *out)
+{
+    const long long n = m->n;
+    if (n == 0) return MS_OK;
+    const int nx = m->g.nx;
+    if (m->precision == MS_FP64) {
+        double *st = (double *)stage(m, sizeof(double) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+        const DevState64 &s = truth ? m->t64[m->tcur] : m->s64;
+        const double *src[8] = {s.x, s.y, s.th, s.u, s.v, s.w, s.r, s.h};
+        for (int a = 0; a < 8; a++)
+            CK(cudaMemcpyAsync(st + a * n, src[a], sizeof(double) * n, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        for (long long k = 0; k < n; k++) {
+            const long long l = truth ? k : m->h_orig[k];
+            const int c = truth ? 0 : m->h_cell_of_orig[l];
+            const double X0 = truth ? 0.0 : (c % nx) * m->g.Lcx, Y0 = truth ? 0.0 : (c / nx) * m->g.Lcy;
+            out[l] = X0 + st[k];
+            out[n + l] = Y0 + st[n + k];
+            for (int a = 2; a < 8; a++) out[a * n + l] = st[a * n + k];
+        }
+    } else {
+        unsigned char *st = (unsigned char *)stage(m, sizeof(float) * 8 * n);
+        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+        uint32_t *qx = (uint32_t *)st, *qy = qx + n;
+        float *fl = (float *)(qy + n);
+        const DevState32 &s = truth ? m->t32[m->tcur] : m->s32;
+        CK(cudaMemcpyAsync(qx, s.xq, 4 * n, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaMemcpyAsync(qy, s.yq, 4 * n, cudaMemcpyDeviceToHost, m->stream));
+        const float *src[6] = {s.th, s.u, s.v, s.w, s.r, s.h};
+        for (int a = 0; a < 6; a++)
+            CK(cudaMemcpyAsync(fl + a * n, src[a], 4 * n, cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        for (long long k = 0; k < n; k++) {
+            const long long l = truth ? k : m->h_orig[k];
+            if (truth) {
+                out[l] = from_fix(qx[k]) * m->g.Lx;
+                out[n + l] = from_fix(qy[k]) * m->g.Ly;
+            } else {
+                const int c = m->h_cell_of_orig[l];
+                out[l] = ((c % nx) + from_fix(qx[k])) * m->g.Lcx;
+                out[n + l] = ((c / nx) + from_fix(qy[k])) * m->g.Lcy;
+            }
+            for (int a = 0; a < 6; a++) out[(a + 2) * n + l] = fl[a * n + k];
+        }
+    }
+    return MS_OK;
+}
+
+int ms_get_floes(ms_model *m, double *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    return download(m, false, out);
+}
+
+int ms_truth_get_floes(ms_model *m, double *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    return download(m, true, out);
+}
+
+int ms_set_floes(ms_model *m, const ms_floes *floes)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    int rc = validate_floes(floes, m->n);
+    if (rc) return rc;
+    for (long long l = 0; l < m->n; l++) {
+        const int c = cell_index(floes->y[l], m->g.Ly, m->g.Lcy, m->g.ny) * m->g.nx +
+                      cell_index(floes->x[l], m->g.Lx, m->g.Lcx, m->g.nx);
+        if (c != m->h_cell_of_orig[l]) return fail(MS_ERR_ARG, "floe %lld left its cell", l);
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    if ((rc = upload_model_state(m, floes))) return rc;
+    StepCommon sc = step_common(m, 0, m->d_mom, m->d_win);
+    CK(m->precision == MS_FP64 ? launch_cell_moments64(m->s64, m->P64, sc, m->stream)
+                               : launch_cell_moments32(m->s32, m->P32, sc, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return MS_OK;
+}
+
+static cudaError_t truth_one(ms_model *m, int cur, int nxt, long long step)
+{
+    TruthArgs a;
+    a.n = m->n;
+    a.g = m->g;
+    a.dt = m->truth_dt;
+    a.step = step;
+    a.ctrl = m->d_ctrl;
+    a.fd = m->d_fd;
+    if (m->precision == MS_FP64) return launch_truth_step64(m->t64[cur], m->t64[nxt], m->P64, a, m->tb, m->stream);
+    return launch_truth_step32(m->t32[cur], m->t32[nxt], m->P32, a, m->tb, m->stream);
+}
+
+int ms_truth_step(ms_model *m, double dt, int64_t nsteps)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (!(dt > 0.0) || !isfin(dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
+    if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
+    if (m->truth_dt == 0.0) m->truth_dt = dt;
+    else if (dt != m->truth_dt) return fail(MS_ERR_ARG, "dt differs from the truth model's dt");
+    for (long long k = 0; k < nsteps; k++) {
+        CK(truth_one(m, m->tcur, 1 - m->tcur, m->truth_steps));
+        m->tcur = 1 - m->tcur;
+        m->truth_steps++;
+    }
+    return read_errors(m);
+}
+
+int ms_truth_moments(ms_model *m, double *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    TruthArgs a;
+    a.n = m->n;
+    a.g = m->g;
+    a.dt = m->truth_dt;
+    a.step = m->truth_steps;
+    a.ctrl = m->d_ctrl;
+    a.fd = m->d_fd;
+    if (m->precision == MS_FP64) CK(launch_truth_moments64(m->t64[m->tcur], m->P64, a, m->cb, m->d_tmom, m->stream));
+    else CK(launch_truth_moments32(m->t32[m->tcur], m->P32, a, m->cb, m->d_tmom, m->stream));
+    double *st = (double *)stage(m, sizeof(double) * m->ncell * NMOM);
+    if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
+    CK(cudaMemcpyAsync(st, m->d_tmom, sizeof(double) * m->ncell * NMOM, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    std::memcpy(out, st, sizeof(double) * m->ncell * NMOM);
+    return MS_OK;
+}
+
+static int ensure_scratch(ms_model *m)
+{
+    if (m->precision == MS_FP64) {
+        if (!m->x64.x) CK(alloc64(m, m->x64, m->n));
+        // radius is read-only except on update steps; keep the scratch copy valid
+        CK(cudaMemcpyAsync(m->x64.r, m->s64.r, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->x64.h, m->s64.h, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+    } else {
+        if (!m->x32.xq) CK(alloc32(m, m->x32, m->n));
+        CK(cudaMemcpyAsync(m->x32.r, m->s32.r, sizeof(float) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->x32.h, m->s32.h, sizeof(float) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+    }
+    CK(cudaMemcpyAsync(m->d_xwin, m->d_win, sizeof(double) * m->ncell * NWIN, cudaMemcpyDeviceToDevice, m->stream));
+    return MS_OK;
+}
+
+int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *mean_ms)
+{
+    if (!m || !mean_ms) return fail(MS_ERR_ARG, "NULL argument");
+    if (reps < 1) return fail(MS_ERR_ARG, "reps < 1");
+    if (!(dt > 0.0)) return fail(MS_ERR_ARG, "dt must be positive");
+    const double saved = m->dt, tsaved = m->truth_dt;
+    int rc = ensure_scratch(m);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    m->dt = dt;
+    m->truth_dt = dt;
+    cudaError_t le = cudaSuccess;
+    const long long i_local = m->steps % m->interval;
+    // one warm-up launch, then the timed ones
+    for (int k = 0; k <= reps && le == cudaSuccess; k++) {
+        if (k == 1) le = cudaEventRecord(e0, m->stream);
+        if (le != cudaSuccess) break;
+        if (which == 0) le = launch_step(m, i_local, true);
+        else le = truth_one(m, m->tcur, 1 - m->tcur, m->truth_steps);
+    }
+    if (le == cudaSuccess) le = cudaEventRecord(e1, m->stream);
+    if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->dt = saved;
+    m->truth_dt = tsaved;
+    if (le != cudaSuccess) return fail(MS_ERR_CUDA, "kernel timing failed: %s", cudaGetErrorString(le));
+    *mean_ms = (double)ms / reps;
+    return read_errors(m);
+}
+
+int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (reps < 1) return fail(MS_ERR_ARG, "reps < 1");
+    std::vector<CellLaunch> cand;
+    const int threads[3] = {64, 128, 256};
+    for (int p = 0; p < 2; p++)
+        for (int t : threads) {
+            CellLaunch c = m->cl;
+            c.variant = 0;
+            c.threads = t;
+            c.persistent = p;
+            int per_sm = 2048 / t;
+            c.grid = m->sm_count * std::min(per_sm, 8);
+            cand.push_back(c);
+        }
+    if (m->precision == MS_FP32) {
+        const float betas[5] = {0.6f, 0.8f, 1.0f, 1.3f, 1.7f};
+        for (float b : betas) {
+            CellLaunch c = m->cl;
+            c.variant = 1;
+            c.bin_beta = b;
+            cand.push_back(c);
+        }
+    }
+    const CellLaunch keep = m->cl;
+    double best = 1e30;
+    CellLaunch bestc = keep;
+    for (const CellLaunch &c : cand) {
+        if (configure_launch(m, c)) continue;
+        double t = 0.0;
+        if (ms_time_kernel(m, 0, dt, reps, &t)) continue;
+        if (t < best) {
+            best = t;
+            bestc = c;
+        }
+    }
+    int rc = configure_launch(m, best < 1e30 ? bestc : keep);
+    if (rc) return rc;
+    if (best_ms) *best_ms = best;
+    return MS_OK;
+}
+
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (variant != 0 && !(variant == 1 && m->precision == MS_FP32)) return fail(MS_ERR_ARG, "unsupported variant %d", variant);
+    if (threads != 64 && threads != 128 && threads != 256) return fail(MS_ERR_ARG, "threads must be 64, 128 or 256");
+    if (!(bin_beta > 0.1 && bin_beta < 10.0)) return fail(MS_ERR_ARG, "bin_beta must be in (0.1, 10)");
+    CellLaunch c = m->cl;
+    c.variant = variant;
+    c.threads = threads;
+    c.persistent = persistent ? 1 : 0;
+    c.bin_beta = (float)bin_beta;
+    c.grid = m->sm_count * std::min(2048 / threads, 8);
+    CK(cudaStreamSynchronize(m->stream));
+    return configure_launch(m, c);
+}
+
+int ms_info(ms_model *m, int64_t *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    Ctrl c;
+    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    out[0] = m->n;
+    out[1] = m->ncell;
+    out[2] = m->max_n;
+    out[3] = m->precision;
+    out[4] = m->cl.variant;
+    out[5] = m->cl.threads;
+    out[6] = (int64_t)std::lround(m->cl.bin_beta * 1000.0f);
+    out[7] = 1;
+    out[8] = m->fc.couple ? coarse_launches() : 1;
+    out[9] = truth_launches(m->tb);
+    out[10] = m->steps;
+    out[11] = m->truth_steps;
+    out[12] = m->replays;
+    out[13] = (int64_t)c.deep;
+    out[14] = m->cl.persistent;
+    out[15] = c.N1;
+    return MS_OK;
+}
+
+}  // extern "C"

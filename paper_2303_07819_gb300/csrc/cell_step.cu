@@ -1,0 +1,806 @@
+// cell_step.cu -- one fine step of every cell's doubly periodic DEM, fused
+// with the per-cell moment reduction and the gradual coarse-to-fine update.
+//
+// Per cell (superparameterisation, Sec. 3.1): stage the cell's floes in shared
+// memory, find all contacts within the cell under the cell-periodic minimum
+// image, add the contact forces of Eq. (2.2) and the drag of Eq. (2.1c-d),
+// advance by forward Euler, apply the gradual update of Sec. 3.3 on update
+// steps, and reduce the post-step state to the cell's moments (Sec. 2.3) in
+// FP64, accumulating the coarse-step window of Algorithm 1.
+//
+// One block owns one cell at a time, so the update is in place: the block
+// reads its whole cell into shared memory before any thread writes.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace msd {
+
+namespace {
+
+constexpr float TWO32F = 4294967296.0f;
+constexpr float INV2_32F = 2.3283064365386963e-10f;
+
+__device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Step facts shared by all blocks of a launch.
+struct StepInfo {
+    long long s;      // 1-based index of this step
+    double t;         // time at the start of the step
+    bool ramp;        // gradual-update step
+    int ev;           // update index within the coarse step (1..N0/n_t)
+};
+
+__device__ __forceinline__ StepInfo step_info(const StepCommon &sc)
+{
+    StepInfo si;
+    const Ctrl *ctrl = sc.ctrl;
+    si.s = ctrl->base + sc.i_local + 1;
+    si.t = (double)(si.s - 1) * sc.dt;
+    const long long k = sc.i_local + 1;           // step within the coarse interval
+    si.ramp = sc.couple && ctrl->have_tgt && (k % sc.n_t == 0);
+    si.ev = (int)(k / sc.n_t);
+    return si;
+}
+
+// Gradual update of one cell (Sec. 3.3, Eqs. 3.5-3.7).  reading: each update
+// adds n_t/N0 of (target - snapshot at the coarse step); radii follow
+// r = r0 (1 + (s - 1) ev n_t/N0), applied as the per-step ratio g.
+struct RampCell {
+    double g, du, dv, dw;
+};
+
+__device__ __forceinline__ RampCell ramp_cell(const StepCommon &sc, int c, int ev)
+{
+    const int nc = sc.ncell;
+    const double f = (double)sc.n_t / (double)sc.N0;
+    const double s = sc.tgt[c];
+    RampCell rc;
+    rc.g = (1.0 + (s - 1.0) * ev * f) / (1.0 + (s - 1.0) * (ev - 1) * f);
+    rc.du = sc.tgt[nc + c] * f;
+    rc.dv = sc.tgt[2 * nc + c] * f;
+    rc.dw = sc.tgt[3 * nc + c] * f;
+    return rc;
+}
+
+// Work item of this block: a fixed item per block, or a ticket from the
+// model's queue (persistent form).  The last block to leave resets the queue.
+__device__ __forceinline__ int next_item(const StepCommon &sc, int persistent, int *sh_item, bool first)
+{
+    if (!persistent) return first ? (int)blockIdx.x : sc.ncell;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int it = (int)atomicAdd(&sc.ctrl->queue[0], 1u);
+        if (it >= sc.ncell) {
+            __threadfence();
+            unsigned done = atomicAdd(&sc.ctrl->queue[1], 1u);
+            if (done == gridDim.x - 1) {
+                sc.ctrl->queue[0] = 0u;
+                sc.ctrl->queue[1] = 0u;
+                __threadfence();
+            }
+        }
+        *sh_item = it;
+    }
+    __syncthreads();
+    return *sh_item;
+}
+
+// Block reduction of the per-thread moment partials; thread 0 writes the cell
+// moments and adds the window sums (Algorithm 1: mass-weighted mean velocity
+// and total drag of each fine step).
+template <class R, int T>
+__device__ __forceinline__ void reduce_write(R (&acc)[NMOM], double *red, const StepCommon &sc,
+                                             int c, int n)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 1; k < NMOM; k++) {
+        R v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * NMOM + k] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m[NMOM];
+        m[0] = (double)n;
+        for (int k = 1; k < NMOM; k++) {
+            double s = 0.0;
+            for (int w = 0; w < T / 32; w++) s += red[w * NMOM + k];
+            m[k] = s;
+        }
+        double *mo = sc.mom + (size_t)c * NMOM;
+        for (int k = 0; k < NMOM; k++) mo[k] = m[k];
+        if (sc.couple) {
+            const int nc = sc.ncell;
+            if (m[1] > 0.0) {
+                sc.win[c] += m[2] / m[1];
+                sc.win[nc + c] += m[3] / m[1];
+            }
+            sc.win[2 * nc + c] += m[9];
+            sc.win[3 * nc + c] += m[10];
+            sc.win[4 * nc + c] += m[11];
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void add_moments(R (&acc)[NMOM], const R mass_c, const R inertia_f,
+                                            R u, R v, R w, R r, R h, R Fx, R Fy, R T)
+{
+    const R m = mass_c * r * r * h;
+    const R I = inertia_f * m * r * r;
+    acc[1] += m;
+    acc[2] += m * u;
+    acc[3] += m * v;
+    acc[4] += I;
+    acc[5] += I * w;
+    acc[6] += R(3.14159265358979323846) * r * r;
+    acc[7] += m * u * u;
+    acc[8] += m * v * v;
+    acc[9] += Fx;
+    acc[10] += Fy;
+    acc[11] += T;
+}
+
+// ===================================================================== FP32
+// Positions are 32-bit fixed point of the periodic cell (2^32 = cell side), so
+// the periodic wrap after the step and the minimum image of a pair are plain
+// 32-bit integer wrap-around.
+
+template <int T>
+__global__ void __launch_bounds__(T)
+k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, int persistent)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int maxn = sc.max_n;
+    float4 *A = reinterpret_cast<float4 *>(smem);                  // r, h, u, v
+    uint2 *Qp = reinterpret_cast<uint2 *>(smem + align16(sizeof(float4) * maxn));
+    float *W = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(Qp) + align16(sizeof(uint2) * maxn));
+    double *red = reinterpret_cast<double *>(reinterpret_cast<unsigned char *>(W) + align16(sizeof(float) * maxn));
+    float *base = reinterpret_cast<float *>(red + (T / 32) * NMOM);
+    int *sh_item = reinterpret_cast<int *>(base + MAXM);
+
+    const StepInfo si = step_info(sc);
+    float ua, va;
+    wind_at(P, si.t, ua, va);
+    const float dt = (float)sc.dt;
+    const float sx = (float)(sc.g.Lcx / 4294967296.0), sy = (float)(sc.g.Lcy / 4294967296.0);
+    const float isx = (float)(4294967296.0 / sc.g.Lcx), isy = (float)(4294967296.0 / sc.g.Lcy);
+    const float inx = 1.0f / (float)sc.g.nx, iny = 1.0f / (float)sc.g.ny;
+    unsigned deep = 0;
+    bool bad = false;
+
+    for (int item = next_item(sc, persistent, sh_item, true); item < sc.ncell;
+         item = next_item(sc, persistent, sh_item, false)) {
+        const int c = sc.order[item];
+        const int o = sc.off[c], n = sc.off[c + 1] - o;
+        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        if (threadIdx.x < P.n_modes) {
+            const int m = threadIdx.x;
+            int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
+            int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
+            float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
+            base[threadIdx.x] = b - floorf(b);
+        }
+        for (int k = threadIdx.x; k < n; k += T) {
+            A[k] = make_float4(in.r[o + k], in.h[o + k], in.u[o + k], in.v[o + k]);
+            Qp[k] = make_uint2(in.xq[o + k], in.yq[o + k]);
+            W[k] = in.w[o + k];
+        }
+        RampCell rc = {1.0, 0.0, 0.0, 0.0};
+        if (si.ramp) rc = ramp_cell(sc, c, si.ev);
+        __syncthreads();
+
+        float acc[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; k++) acc[k] = 0.0f;
+
+        for (int l = threadIdx.x; l < n; l += T) {
+            const float4 al = A[l];
+            const uint2 ql = Qp[l];
+            const float wl = W[l];
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            for (int j = 0; j < n; j++) {
+                if (j == l) continue;
+                const uint2 qj = Qp[j];
+                const float dx = (float)(int)(qj.x - ql.x) * sx;
+                const float dy = (float)(int)(qj.y - ql.y) * sy;
+                const float d2 = dx * dx + dy * dy;
+                const float4 aj = A[j];
+                const float S = al.x + aj.x;
+                if (d2 < S * S) {
+                    contact_add(dx, dy, d2, al.x, aj.x, al.y, aj.y, aj.z - al.z, aj.w - al.w, wl,
+                                W[j], P, fx, fy, tq, deep);
+                }
+            }
+            // forcing at the floe's global position (reading: cell origin + local)
+            const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
+            float uo, vo, zeta;
+            ocean_f32(P, base, inx, iny, xf, yf, uo, vo, zeta);
+            float Fdx, Fdy, Td;
+            drag_force(P, uo, vo, zeta, ua, va, al.z, al.w, wl, al.x, Fdx, Fdy, Td);
+            fx += Fdx; fy += Fdy; tq += Td;
+            // forward Euler with every right-hand side at t_n
+            const float r = al.x, h = al.y;
+            const float m = P.mass_c * r * r * h;
+            const float I = P.inertia_f * m * r * r;
+            const uint32_t xn = ql.x + (uint32_t)__float2int_rn(dt * al.z * isx);
+            const uint32_t yn = ql.y + (uint32_t)__float2int_rn(dt * al.w * isy);
+            float th = in.th[o + l] + dt * wl;
+            float un = al.z + dt * (fx / m);
+            float vn = al.w + dt * (fy / m);
+            float wn = wl + dt * (tq / I);
+            float rn = r;
+            if (si.ramp) {
+                rn = (float)((double)r * rc.g);
+                un += (float)rc.du;
+                vn += (float)rc.dv;
+                wn += (float)rc.dw;
+            }
+            bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+            out.xq[o + l] = xn;
+            out.yq[o + l] = yn;
+            out.th[o + l] = th;
+            out.u[o + l] = un;
+            out.v[o + l] = vn;
+            out.w[o + l] = wn;
+            if (si.ramp || out.r != in.r) out.r[o + l] = rn;
+            add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+        }
+        reduce_write<float, T>(acc, red, sc, c, n);
+        __syncthreads();
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
+}
+
+// ============================================================= FP32 binned
+// Pair search with a per-cell bin grid in shared memory.  With nb bins per
+// side (nb ~ sqrt(n) / beta, 3 <= nb <= nbmax) of side B, a floe is "small"
+// when r <= B/2: two small floes in contact have centres less than B apart,
+// so a small floe finds its small partners in the 3 x 3 bins around its own.
+// Each neighbouring bin is visited with the periodic shift of the cell that
+// brings it next to the floe, so the pair test needs no minimum image.  The
+// few large floes form one list that every floe scans with a float minimum
+// image; a large floe finds its small partners in the bins within its reach.
+// Every floe sums its own contacts (each pair is evaluated from both sides),
+// so no atomics touch forces and results do not depend on thread timing.
+// The bin test runs on float cell-local positions; the force of a contact
+// uses the exact 32-bit fixed-point separation.  Bin contents are sorted by
+// floe index, so the summation order is fixed.
+
+template <int T>
+__device__ __forceinline__ int block_scan_excl(const int *in, int *out, int count, int *tmp)
+{
+    const int per = (count + T - 1) / T;
+    const int b = threadIdx.x * per;
+    const int e = min(b + per, count);
+    int s = 0;
+    for (int i = b; i < e; i++) s += in[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int w = 0; w < T / 32; w++) {
+            const int t = tmp[w];
+            tmp[w] = acc;
+            acc += t;
+        }
+        tmp[T / 32] = acc;
+    }
+    __syncthreads();
+    int run = tmp[warp] + x - s;
+    for (int i = b; i < e; i++) {
+        const int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    const int total = tmp[T / 32];
+    __syncthreads();
+    return total;
+}
+
+// float minimum image for a separation in (-L, L): subtract L * rint(d / L),
+// rint by the 1.5 * 2^23 rounding constant (round to nearest, FMA pipe only)
+__device__ __forceinline__ float min_image(float d, float L, float iL)
+{
+    const float k = __fsub_rn(__fadd_rn(d * iL, 12582912.0f), 12582912.0f);
+    return fmaf(-k, L, d);
+}
+
+struct Bin32 {
+    float4 *P4;     // x, y (m, cell-local float), r, h          [index order]
+    float4 *V4;     // u, v, w                                   [index order]
+    float4 *S4;     // P4 in search order: small floes by bin, then large floes
+    float4 *F4;     // force x, y, torque                        [index order]
+    uint2 *Q;       // exact fixed-point position                [index order]
+    int *cnt;       // [nb^2 + 1] bin counts, then cursors
+    int *bst;       // [nb^2 + 1] bin starts
+    short *sidx;    // search position -> floe index
+    short *bin;     // floe index -> bin (-1: large)
+    int *tmp;       // scan scratch
+    double *red;
+    float *base;
+    int *misc;
+};
+
+template <int T>
+__device__ __forceinline__ Bin32 carve32(unsigned char *smem, int maxn, int nbmax)
+{
+    Bin32 b;
+    const int nbins = nbmax * nbmax + 1;
+    size_t o = 0;
+    b.P4 = reinterpret_cast<float4 *>(smem + o); o += align16(sizeof(float4) * maxn);
+    b.V4 = reinterpret_cast<float4 *>(smem + o); o += align16(sizeof(float4) * maxn);
+    b.S4 = reinterpret_cast<float4 *>(smem + o); o += align16(sizeof(float4) * maxn);
+    b.F4 = reinterpret_cast<float4 *>(smem + o); o += align16(sizeof(float4) * maxn);
+    b.Q = reinterpret_cast<uint2 *>(smem + o); o += align16(sizeof(uint2) * maxn);
+    b.red = reinterpret_cast<double *>(smem + o); o += align16(sizeof(double) * (T / 32) * NMOM);
+    b.cnt = reinterpret_cast<int *>(smem + o); o += align16(sizeof(int) * nbins);
+    b.bst = reinterpret_cast<int *>(smem + o); o += align16(sizeof(int) * nbins);
+    b.tmp = reinterpret_cast<int *>(smem + o); o += align16(sizeof(int) * (T / 32 + 1));
+    b.base = reinterpret_cast<float *>(smem + o); o += align16(sizeof(float) * MAXM);
+    b.misc = reinterpret_cast<int *>(smem + o); o += align16(sizeof(int) * 8);
+    b.sidx = reinterpret_cast<short *>(smem + o); o += align16(sizeof(short) * maxn);
+    b.bin = reinterpret_cast<short *>(smem + o); o += align16(sizeof(short) * maxn);
+    return b;
+}
+
+__host__ __device__ inline size_t smem32_binned(int T, int maxn, int nbmax)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const int nbins = nbmax * nbmax + 1;
+    return 4 * a16(sizeof(float4) * maxn) + a16(sizeof(uint2) * maxn) + a16(sizeof(double) * (T / 32) * NMOM) +
+           2 * a16(sizeof(int) * nbins) + a16(sizeof(int) * (T / 32 + 1)) + a16(sizeof(float) * MAXM) +
+           a16(sizeof(int) * 8) + 2 * a16(sizeof(short) * maxn);
+}
+
+template <int T>
+__global__ void __launch_bounds__(T)
+k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
+                     int item1, int maxn, int nbmax)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Bin32 sm = carve32<T>(smem, maxn, nbmax);
+
+    const StepInfo si = step_info(sc);
+    float ua, va;
+    wind_at(P, si.t, ua, va);
+    const float dt = (float)sc.dt;
+    const float Lx = (float)sc.g.Lcx, Ly = (float)sc.g.Lcy;
+    const float iLx = 1.0f / Lx, iLy = 1.0f / Ly;
+    const float sx = (float)(sc.g.Lcx / 4294967296.0), sy = (float)(sc.g.Lcy / 4294967296.0);
+    const float isx = (float)(4294967296.0 / sc.g.Lcx), isy = (float)(4294967296.0 / sc.g.Lcy);
+    const float inx = 1.0f / (float)sc.g.nx, iny = 1.0f / (float)sc.g.ny;
+    unsigned deep = 0;
+    bool bad = false;
+
+    for (int item = item0 + blockIdx.x; item < item1; item += gridDim.x) {
+        const int c = sc.order[item];
+        const int o = sc.off[c], n = sc.off[c + 1] - o;
+        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        int nb = (int)(sqrtf((float)n) / beta);
+        nb = nb > nbmax ? nbmax : nb;
+        if (nb < 3) nb = 0;                       // few floes: every floe in the list
+        const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
+        const float Rs = nb ? 0.5f * fminf(Bx, By) : -1.0f;
+        const int nbins = nb * nb;
+        if (threadIdx.x < P.n_modes) {
+            const int m = threadIdx.x;
+            int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
+            int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
+            const float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
+            sm.base[m] = b - floorf(b);
+        }
+        for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
+        __syncthreads();
+        // ---- stage the cell and count small floes per bin
+        for (int k = threadIdx.x; k < n; k += T) {
+            const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
+            const float r = in.r[o + k];
+            sm.P4[k] = make_float4((float)xq * sx, (float)yq * sy, r, in.h[o + k]);
+            sm.V4[k] = make_float4(in.u[o + k], in.v[o + k], in.w[o + k], 0.0f);
+            sm.Q[k] = make_uint2(xq, yq);
+            short b = -1;
+            if (r <= Rs) {
+                b = (short)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb));
+                atomicAdd(&sm.cnt[b], 1);
+            }
+            sm.bin[k] = b;
+        }
+        __syncthreads();
+        const int nsmall = block_scan_excl<T>(sm.cnt, sm.bst, nbins + 1, sm.tmp);
+        for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
+        __syncthreads();
+        // ---- small floes to their bins; large floes, in index order, after them
+        int run = nsmall;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int k0 = 0; k0 < n; k0 += T) {
+            const int k = k0 + threadIdx.x;
+            const bool valid = k < n;
+            const short b = valid ? sm.bin[k] : (short)0;
+            if (valid && b >= 0) sm.sidx[sm.bst[b] + atomicAdd(&sm.cnt[b], 1)] = (short)k;
+            const bool large = valid && b < 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, large);
+            if (lane == 0) sm.tmp[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < T / 32; w++) {
+                const int t = sm.tmp[w];
+                before += (w < warp) ? t : 0;
+                total += t;
+            }
+            if (large) sm.sidx[run + before + __popc(bal & ((1u << lane) - 1u))] = (short)k;
+            run += total;
+            __syncthreads();
+        }
+        // ---- fixed order inside each bin: ascending floe index
+        for (int b = threadIdx.x; b < nbins; b += T) {
+            const int s0 = sm.bst[b], e0 = sm.bst[b + 1];
+            for (int i = s0 + 1; i < e0; i++) {
+                const short key = sm.sidx[i];
+                int j = i - 1;
+                while (j >= s0 && sm.sidx[j] > key) {
+                    sm.sidx[j + 1] = sm.sidx[j];
+                    j--;
+                }
+                sm.sidx[j + 1] = key;
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < n; p += T) sm.S4[p] = sm.P4[sm.sidx[p]];
+        __syncthreads();
+
+        // ---- contacts
+        for (int p = threadIdx.x; p < n; p += T) {
+            const int l = sm.sidx[p];
+            const float4 pl = sm.P4[l];
+            const float4 vl = sm.V4[l];
+            const uint2 ql = sm.Q[l];
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            auto touch = [&](int k) {
+                const int j = sm.sidx[k];
+                const uint2 qj = sm.Q[j];
+                const float dx = (float)(int)(qj.x - ql.x) * sx;
+                const float dy = (float)(int)(qj.y - ql.y) * sy;
+                const float4 pj = sm.P4[j];
+                const float4 vj = sm.V4[j];
+                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
+                            vj.z, P, fx, fy, tq, deep);
+            };
+            // small partners through the bins
+            int bx0, bx1, by0, by1;
+            if (p < nsmall) {
+                const int b = sm.bin[l];
+                const int bx = b % nb, by = b / nb;
+                bx0 = bx - 1; bx1 = bx + 1; by0 = by - 1; by1 = by + 1;
+            } else if (nb) {
+                const float reach = 1.001f * (pl.z + Rs);
+                bx0 = (int)floorf((pl.x - reach) / Bx); bx1 = (int)floorf((pl.x + reach) / Bx);
+                by0 = (int)floorf((pl.y - reach) / By); by1 = (int)floorf((pl.y + reach) / By);
+                if (bx1 - bx0 + 1 >= nb) { bx0 = 0; bx1 = nb - 1; }
+                if (by1 - by0 + 1 >= nb) { by0 = 0; by1 = nb - 1; }
+            } else {
+                bx0 = 0; bx1 = -1; by0 = 0; by1 = -1;
+            }
+            const bool wrapx = (bx0 == 0 && bx1 == nb - 1 && p >= nsmall);
+            const bool wrapy = (by0 == 0 && by1 == nb - 1 && p >= nsmall);
+            for (int by = by0; by <= by1; by++) {
+                const int wy = by < 0 ? by + nb : (by >= nb ? by - nb : by);
+                const float ys = wrapy ? pl.y : (by < 0 ? pl.y + Ly : (by >= nb ? pl.y - Ly : pl.y));
+                for (int bx = bx0; bx <= bx1; bx++) {
+                    const int wx = bx < 0 ? bx + nb : (bx >= nb ? bx - nb : bx);
+                    const float xs = wrapx ? pl.x : (bx < 0 ? pl.x + Lx : (bx >= nb ? pl.x - Lx : pl.x));
+                    const int wb = wy * nb + wx;
+                    const int e0 = sm.bst[wb + 1];
+                    for (int k = sm.bst[wb]; k < e0; k++) {
+                        const float4 q = sm.S4[k];
+                        float dx = q.x - xs, dy = q.y - ys;
+                        if (wrapx) dx = min_image(dx, Lx, iLx);
+                        if (wrapy) dy = min_image(dy, Ly, iLy);
+                        const float S = pl.z + q.z;
+                        if (k != p && dx * dx + dy * dy < S * S) touch(k);
+                    }
+                }
+            }
+            // large partners through the list
+            for (int k = nsmall; k < n; k++) {
+                const float4 q = sm.S4[k];
+                const float dx = min_image(q.x - pl.x, Lx, iLx);
+                const float dy = min_image(q.y - pl.y, Ly, iLy);
+                const float S = pl.z + q.z;
+                if (k != p && dx * dx + dy * dy < S * S) touch(k);
+            }
+            sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
+        }
+        RampCell rc = {1.0, 0.0, 0.0, 0.0};
+        if (si.ramp) rc = ramp_cell(sc, c, si.ev);
+        __syncthreads();
+
+        // ---- drag, forward Euler, gradual update, moments (index order: coalesced I/O)
+        float acc[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; k++) acc[k] = 0.0f;
+        for (int l = threadIdx.x; l < n; l += T) {
+            const float4 pl = sm.P4[l];
+            const float4 vl = sm.V4[l];
+            const uint2 ql = sm.Q[l];
+            const float4 f4 = sm.F4[l];
+            float fx = f4.x, fy = f4.y, tq = f4.z;
+            const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
+            float uo, vo, zeta;
+            ocean_f32(P, sm.base, inx, iny, xf, yf, uo, vo, zeta);
+            float Fdx, Fdy, Td;
+            drag_force(P, uo, vo, zeta, ua, va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+            fx += Fdx; fy += Fdy; tq += Td;
+            const float r = pl.z, h = pl.w;
+            const float m = P.mass_c * r * r * h;
+            const float I = P.inertia_f * m * r * r;
+            const uint32_t xn = ql.x + (uint32_t)__float2int_rn(dt * vl.x * isx);
+            const uint32_t yn = ql.y + (uint32_t)__float2int_rn(dt * vl.y * isy);
+            const float th = in.th[o + l] + dt * vl.z;
+            float un = vl.x + dt * (fx / m);
+            float vn = vl.y + dt * (fy / m);
+            float wn = vl.z + dt * (tq / I);
+            float rn = r;
+            if (si.ramp) {
+                rn = (float)((double)r * rc.g);
+                un += (float)rc.du;
+                vn += (float)rc.dv;
+                wn += (float)rc.dw;
+            }
+            bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+            out.xq[o + l] = xn;
+            out.yq[o + l] = yn;
+            out.th[o + l] = th;
+            out.u[o + l] = un;
+            out.v[o + l] = vn;
+            out.w[o + l] = wn;
+            if (si.ramp || out.r != in.r) out.r[o + l] = rn;
+            add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+        }
+        reduce_write<float, T>(acc, sm.red, sc, c, n);
+        __syncthreads();
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
+}
+
+// ===================================================================== FP64
+// Positions are FP64 offsets from the cell origin; minimum image and wrap as
+// x - L rint(x / L) and x - L floor(x / L).  Pairs are visited in ascending
+// partner index, so each floe sums its contacts in the order the pairs (l < j)
+// of the cell are listed.
+
+template <int T>
+__global__ void __launch_bounds__(T)
+k_cell_step64_brute(DevState64 in, DevState64 out, Phys<double> P, StepCommon sc, int persistent)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int maxn = sc.max_n;
+    double *X = reinterpret_cast<double *>(smem);
+    double *Y = X + maxn, *U = Y + maxn, *V = U + maxn, *Wv = V + maxn, *Rr = Wv + maxn, *H = Rr + maxn;
+    double *red = H + maxn;
+    int *sh_item = reinterpret_cast<int *>(red + (T / 32) * NMOM);
+
+    const StepInfo si = step_info(sc);
+    double ua, va;
+    wind_at(P, si.t, ua, va);
+    const double dt = sc.dt;
+    const double Lx = sc.g.Lcx, Ly = sc.g.Lcy;
+    unsigned deep = 0;
+    bool bad = false;
+
+    for (int item = next_item(sc, persistent, sh_item, true); item < sc.ncell;
+         item = next_item(sc, persistent, sh_item, false)) {
+        const int c = sc.order[item];
+        const int o = sc.off[c], n = sc.off[c + 1] - o;
+        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        const double X0 = ix * Lx, Y0 = iy * Ly;
+        for (int k = threadIdx.x; k < n; k += T) {
+            X[k] = in.x[o + k]; Y[k] = in.y[o + k]; U[k] = in.u[o + k]; V[k] = in.v[o + k];
+            Wv[k] = in.w[o + k]; Rr[k] = in.r[o + k]; H[k] = in.h[o + k];
+        }
+        RampCell rc = {1.0, 0.0, 0.0, 0.0};
+        if (si.ramp) rc = ramp_cell(sc, c, si.ev);
+        __syncthreads();
+
+        double acc[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; k++) acc[k] = 0.0;
+
+        for (int l = threadIdx.x; l < n; l += T) {
+            const double xl = X[l], yl = Y[l], ul = U[l], vl = V[l], wl = Wv[l], rl = Rr[l], hl = H[l];
+            double fx = 0.0, fy = 0.0, tq = 0.0;
+            for (int j = 0; j < n; j++) {
+                if (j == l) continue;
+                double dx = X[j] - xl, dy = Y[j] - yl;
+                dx -= Lx * rint(dx / Lx);
+                dy -= Ly * rint(dy / Ly);
+                const double d2 = dx * dx + dy * dy;
+                contact_add(dx, dy, d2, rl, Rr[j], hl, H[j], U[j] - ul, V[j] - vl, wl, Wv[j], P,
+                            fx, fy, tq, deep);
+            }
+            double uo, vo, zeta;
+            ocean_f64(P, X0 + xl, Y0 + yl, uo, vo, zeta);
+            double Fdx, Fdy, Td;
+            drag_force(P, uo, vo, zeta, ua, va, ul, vl, wl, rl, Fdx, Fdy, Td);
+            fx += Fdx; fy += Fdy; tq += Td;
+            const double m = P.mass_c * rl * rl * hl;
+            const double I = P.inertia_f * m * rl * rl;
+            double xn = xl + dt * ul;
+            double yn = yl + dt * vl;
+            const double th = in.th[o + l] + dt * wl;
+            double un = ul + dt * (fx / m);
+            double vn = vl + dt * (fy / m);
+            double wn = wl + dt * (tq / I);
+            xn -= Lx * floor(xn / Lx);
+            yn -= Ly * floor(yn / Ly);
+            double rn = rl;
+            if (si.ramp) {
+                rn = rl * rc.g;
+                un += rc.du;
+                vn += rc.dv;
+                wn += rc.dw;
+            }
+            bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+            out.x[o + l] = xn;
+            out.y[o + l] = yn;
+            out.th[o + l] = th;
+            out.u[o + l] = un;
+            out.v[o + l] = vn;
+            out.w[o + l] = wn;
+            if (si.ramp || out.r != in.r) out.r[o + l] = rn;
+            add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, hl, Fdx, Fdy, Td);
+        }
+        reduce_write<double, T>(acc, red, sc, c, n);
+        __syncthreads();
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
+}
+
+// ============================================================ moments only
+// Moments of the current state with zero drag columns (before any step, or
+// after the state was replaced).
+template <class R, int T>
+__global__ void __launch_bounds__(T)
+k_cell_moments(const R *u, const R *v, const R *w, const R *r, const R *h, R mass_c, R inertia_f,
+               StepCommon sc)
+{
+    __shared__ double red[(T / 32) * NMOM];
+    const int c = blockIdx.x;
+    const int o = sc.off[c], n = sc.off[c + 1] - o;
+    R acc[NMOM];
+#pragma unroll
+    for (int k = 0; k < NMOM; k++) acc[k] = R(0);
+    for (int l = threadIdx.x; l < n; l += T)
+        add_moments(acc, mass_c, inertia_f, u[o + l], v[o + l], w[o + l], r[o + l], h[o + l], R(0),
+                    R(0), R(0));
+    StepCommon s2 = sc;
+    s2.couple = 0;
+    reduce_write<R, T>(acc, red, s2, c, n);
+}
+
+}  // namespace
+
+// bins per side that a segment can need: nb = sqrt(n) / beta, capped
+int seg_nbmax(const CellLaunch &cl, int s)
+{
+    int nb = (int)(std::sqrt((float)cl.seg_maxn[s]) / cl.bin_beta);
+    nb = nb > cl.nbmax ? cl.nbmax : nb;
+    return nb < 3 ? 3 : nb;
+}
+
+size_t cell_step_smem(int precision, const CellLaunch &cl, int max_n, int, int)
+{
+    const int T = cl.threads;
+    if (precision == 0 && cl.variant == 1) {
+        size_t mx = 0;
+        for (int s = 0; s < cl.nseg; s++) {
+            const size_t sm = smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
+            mx = sm > mx ? sm : mx;
+        }
+        return mx;
+    }
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    if (precision == 1) {
+        return sizeof(double) * 7 * (size_t)max_n + sizeof(double) * (T / 32) * NMOM + 16;
+    }
+    return a16(sizeof(float4) * max_n) + a16(sizeof(uint2) * max_n) + a16(sizeof(float) * max_n) +
+           sizeof(double) * (T / 32) * NMOM + sizeof(float) * MAXM + 16;
+}
+
+#define MS_T_SWITCH(T, ...)                                       \
+    switch (T) {                                                  \
+    case 64: { constexpr int TT = 64; __VA_ARGS__; } break;       \
+    case 128: { constexpr int TT = 128; __VA_ARGS__; } break;     \
+    case 256: { constexpr int TT = 256; __VA_ARGS__; } break;     \
+    default: return cudaErrorInvalidValue;                        \
+    }
+
+// The shared-memory limit is an attribute of each kernel instance, shared by
+// every model in the process: set it once to the device's opt-in maximum
+// (a limit, not a reservation) instead of to one launch's need.
+cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
+{
+    static int done = 0;
+    static int optin = 0;
+    if (!done) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        const void *kern[] = {
+            (const void *)k_cell_step32_brute<64>, (const void *)k_cell_step32_brute<128>,
+            (const void *)k_cell_step32_brute<256>, (const void *)k_cell_step64_brute<64>,
+            (const void *)k_cell_step64_brute<128>, (const void *)k_cell_step64_brute<256>,
+            (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
+            (const void *)k_cell_step32_binned<256>};
+        for (const void *k : kern) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            if (e != cudaSuccess) return e;
+        }
+        done = 1;
+    }
+    return smem <= (size_t)optin ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                               const StepCommon &sc, const CellLaunch &cl, cudaStream_t st)
+{
+    if (cl.variant == 1) {
+        for (int s = 0; s < cl.nseg; s++) {
+            const int items = cl.seg_end[s] - cl.seg_begin[s];
+            if (items <= 0) continue;
+            const int nbm = seg_nbmax(cl, s);
+            const size_t sm = smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], nbm);
+            MS_T_SWITCH(cl.seg_threads[s],
+                        k_cell_step32_binned<TT><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
+                                                                        cl.seg_end[s], cl.seg_maxn[s], nbm));
+        }
+        return cudaGetLastError();
+    }
+    const size_t smem = cell_step_smem(0, cl, sc.max_n, sc.g.nx, sc.g.ny);
+    const int grid = cl.persistent ? cl.grid : sc.ncell;
+    if (grid <= 0) return cudaSuccess;
+    MS_T_SWITCH(cl.threads, k_cell_step32_brute<TT><<<grid, TT, smem, st>>>(in, out, P, sc, cl.persistent));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_step64(const DevState64 &in, const DevState64 &out, const Phys<double> &P,
+                               const StepCommon &sc, const CellLaunch &cl, cudaStream_t st)
+{
+    const size_t smem = cell_step_smem(1, cl, sc.max_n, sc.g.nx, sc.g.ny);
+    const int grid = cl.persistent ? cl.grid : sc.ncell;
+    if (grid <= 0) return cudaSuccess;
+    MS_T_SWITCH(cl.threads, k_cell_step64_brute<TT><<<grid, TT, smem, st>>>(in, out, P, sc, cl.persistent));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_moments32(const DevState32 &s, const Phys<float> &P, const StepCommon &sc,
+                                  cudaStream_t st)
+{
+    if (sc.ncell <= 0) return cudaSuccess;
+    k_cell_moments<float, 128><<<sc.ncell, 128, 0, st>>>(s.u, s.v, s.w, s.r, s.h, P.mass_c, P.inertia_f, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cell_moments64(const DevState64 &s, const Phys<double> &P, const StepCommon &sc,
+                                  cudaStream_t st)
+{
+    if (sc.ncell <= 0) return cudaSuccess;
+    k_cell_moments<double, 128><<<sc.ncell, 128, 0, st>>>(s.u, s.v, s.w, s.r, s.h, P.mass_c, P.inertia_f, sc);
+    return cudaGetLastError();
+}
+
+}  // namespace msd

@@ -1,0 +1,154 @@
+// coarse.cu -- the coarse step of Algorithm 1 in FP64: process the window of
+// DEM data, solve the moment equations by Lax-Friedrichs with N1 substeps, and
+// set the targets of the gradual update.
+//
+// Moment equations, Eq. (2.26a-c): rho and P_omega in conservative form; rho v
+// in the Oseen form <v> . grad(rho v) of Eq. (3.3).  reading: 2-D LF with the
+// four-neighbour average on the periodic grid, <v> = window mean of the cell's
+// mass-weighted velocity, drag sources = window mean of the cell's total drag
+// per unit area; N1 = max(1, ceil(dT max|V|/dX / 0.5)) (Sec. 3.2).
+//
+// N1 is chosen on the device (it depends on the window data), so the step is
+// a fixed sequence of launches (prepare, NSUB_MAX substeps that return at once
+// past N1, targets, finish) and can be captured in a CUDA graph.
+#include "common.cuh"
+
+namespace msd {
+
+namespace {
+
+__device__ __forceinline__ int n_sub(const CoarseArgs &a)
+{
+    const double cmax = __longlong_as_double((long long)a.ctrl->cmax_bits);
+    int N1 = (int)ceil(a.dT * cmax / 0.5);
+    return N1 < 1 ? 1 : N1;
+}
+
+__global__ void k_coarse_prepare(CoarseArgs a)
+{
+    const int nc = a.nx * a.ny;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double *mo = a.mom + (size_t)c * NMOM;
+    if (!a.ctrl->have_q) {
+        // initialise the coarse model from the DEM data (Sec. 3.2)
+        a.q0[c] = mo[1] / a.Ac;
+        a.q0[nc + c] = mo[2] / a.Ac;
+        a.q0[2 * nc + c] = mo[3] / a.Ac;
+        a.q0[3 * nc + c] = mo[5] / a.Ac;
+    }
+    const double N0 = (double)a.N0;
+    const double Vx = a.win[c] / N0, Vy = a.win[nc + c] / N0;
+    a.V[c] = Vx;
+    a.V[nc + c] = Vy;
+    a.S[c] = 0.0;
+    a.S[nc + c] = a.win[2 * nc + c] / N0 / a.Ac;
+    a.S[2 * nc + c] = a.win[3 * nc + c] / N0 / a.Ac;
+    a.S[3 * nc + c] = a.win[4 * nc + c] / N0 / a.Ac;
+    for (int k = 0; k < NWIN; k++) a.win[k * nc + c] = 0.0;
+    const double cx = fabs(Vx) / a.dx, cy = fabs(Vy) / a.dy;
+    const double cc = cx > cy ? cx : cy;
+    atomicMax(&a.ctrl->cmax_bits, (unsigned long long)__double_as_longlong(cc));
+}
+
+__global__ void k_coarse_lf(CoarseArgs a, int k)
+{
+    const int N1 = n_sub(a);
+    if (k >= N1) return;
+    const int nx = a.nx, ny = a.ny, nc = nx * ny;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double *q = (k & 1) ? a.q1 : a.q0;
+    double *qn = (k & 1) ? a.q0 : a.q1;
+    const double dtau = a.dT / N1;
+    const int i = c % nx, j = c / nx;
+    const int cE = j * nx + (i + 1) % nx, cW = j * nx + (i + nx - 1) % nx;
+    const int cN = ((j + 1) % ny) * nx + i, cS = ((j + ny - 1) % ny) * nx + i;
+    const double *Vx = a.V, *Vy = a.V + nc;
+#pragma unroll
+    for (int f = 0; f < 4; f++) {
+        const double *g = q + (size_t)f * nc;
+        const double avg = 0.25 * ((g[cE] + g[cW]) + (g[cN] + g[cS]));
+        double val;
+        if (f == 0 || f == 3) {
+            val = avg - dtau / (2.0 * a.dx) * (Vx[cE] * g[cE] - Vx[cW] * g[cW])
+                      - dtau / (2.0 * a.dy) * (Vy[cN] * g[cN] - Vy[cS] * g[cS]);
+        } else {
+            val = avg - dtau * Vx[c] / (2.0 * a.dx) * (g[cE] - g[cW])
+                      - dtau * Vy[c] / (2.0 * a.dy) * (g[cN] - g[cS]);
+        }
+        qn[(size_t)f * nc + c] = val + dtau * a.S[(size_t)f * nc + c];
+    }
+}
+
+// Targets of the gradual update (Sec. 3.3).  reading: the radius scale s
+// makes the cell mass equal rho* A_c; the uniform velocity and spin increments
+// make the scaled cell's momentum and angular momentum equal the coarse ones.
+__global__ void k_coarse_targets(CoarseArgs a)
+{
+    const int nc = a.nx * a.ny;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int N1 = n_sub(a);
+    const double *q = ((N1 < NSUB_MAX ? N1 : NSUB_MAX) & 1) ? a.q1 : a.q0;
+    double qc[4];
+    for (int f = 0; f < 4; f++) {
+        qc[f] = q[(size_t)f * nc + c];
+        if (q != a.q0) a.q0[(size_t)f * nc + c] = qc[f];
+    }
+    const double *mo = a.mom + (size_t)c * NMOM;
+    const double M = mo[1];
+    double s = 1.0, dvx = 0.0, dvy = 0.0, dw = 0.0;
+    if (M > 0.0) {
+        const double rho_dem = M / a.Ac;
+        const double qr = qc[0] > 0.0 ? qc[0] : 0.0;
+        s = sqrt(qr / rho_dem);
+        const double s2 = s * s, s4 = s2 * s2;
+        if (s2 * M > 0.0) {
+            dvx = (qc[1] * a.Ac - s2 * mo[2]) / (s2 * M);
+            dvy = (qc[2] * a.Ac - s2 * mo[3]) / (s2 * M);
+        }
+        if (s4 * mo[4] > 0.0) dw = (qc[3] * a.Ac - s4 * mo[5]) / (s4 * mo[4]);
+    }
+    a.tgt[c] = s;
+    a.tgt[nc + c] = dvx;
+    a.tgt[2 * nc + c] = dvy;
+    a.tgt[3 * nc + c] = dw;
+}
+
+__global__ void k_coarse_finish(CoarseArgs a)
+{
+    const int N1 = n_sub(a);
+    Ctrl *ctrl = a.ctrl;
+    ctrl->N1 = N1;
+    if (N1 > NSUB_MAX) ctrl->err |= ERR_CFL;
+    ctrl->have_q = 1;
+    ctrl->have_tgt = 1;
+    ctrl->base += a.N0;
+    ctrl->cmax_bits = 0ull;
+}
+
+__global__ void k_advance(Ctrl *ctrl, int N0) { ctrl->base += N0; }
+
+}  // namespace
+
+int coarse_launches() { return NSUB_MAX + 3; }
+
+cudaError_t launch_coarse_step(const CoarseArgs &a, cudaStream_t st)
+{
+    const int nc = a.nx * a.ny;
+    const int T = 256, B = (nc + T - 1) / T;
+    k_coarse_prepare<<<B, T, 0, st>>>(a);
+    for (int k = 0; k < NSUB_MAX; k++) k_coarse_lf<<<B, T, 0, st>>>(a, k);
+    k_coarse_targets<<<B, T, 0, st>>>(a);
+    k_coarse_finish<<<1, 1, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(Ctrl *ctrl, int N0, cudaStream_t st)
+{
+    k_advance<<<1, 1, 0, st>>>(ctrl, N0);
+    return cudaGetLastError();
+}
+
+}  // namespace msd

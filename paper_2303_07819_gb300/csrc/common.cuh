@@ -1,0 +1,279 @@
+// common.cuh -- types and device physics shared by the kernels of libmsdem.
+//
+// Physics follows Deng, Stechmann & Chen (arXiv 2303.07819):
+//   DEM of disk floes, Sec. 2.1, Eq. (2.1a-d); contact law Eq. (2.2) with the
+//   Coulomb limit; ocean (and wind) drag of Eq. (2.1c-d); forward Euler,
+//   Sec. 3.1.  Readings of the places the paper leaves open are stated where
+//   they are used.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace msd {
+
+constexpr int NMOM = 12;      // moment columns (see msdem.h)
+constexpr int NWIN = 5;       // window columns
+constexpr int MAXM = 16;      // stream-function modes
+constexpr int NSUB_MAX = 8;   // Lax-Friedrichs substeps per coarse step (device-chosen N1)
+
+// error bits raised by kernels, read by the host after a call
+constexpr int ERR_NONFINITE = 1;
+constexpr int ERR_TIMEOUT = 2;
+constexpr int ERR_CFL = 4;
+
+// Device-resident control block of one model.
+struct Ctrl {
+    long long base;               // fine steps done before the current coarse interval (multiple of N0)
+    int have_q;                   // coarse state initialised
+    int have_tgt;                 // targets of the gradual update set
+    int err;                      // ERR_* bits
+    int N1;                       // LF substeps of the last coarse step
+    unsigned long long cmax_bits; // max over cells of |V|/dx (non-negative double, as bits)
+    unsigned int queue[2];        // work-queue tickets, one per step parity
+    unsigned long long deep;      // contacts with overlap deeper than r_min / 2 (diagnostic)
+    unsigned long long pad[3];
+};
+
+// Physical constants in the kernel's arithmetic type.  FP64 kernels use the
+// radian wave numbers (mKx, mKy, mPh); FP32 kernels use integer wave numbers
+// and phases in cycles so that the global phase can be reduced exactly with
+// the integer cell index.
+template <class R>
+struct Phys {
+    R uo_x, uo_y;
+    int n_modes;
+    R mA[MAXM], mKx[MAXM], mKy[MAXM], mPh[MAXM];   // FP64: A, 2 pi kx/Lx, 2 pi ky/Ly, phi
+    int mkx[MAXM], mky[MAXM];                      // FP32: integer wave numbers
+    R mCyc[MAXM];                                  // FP32: phi / 2 pi
+    R mAu[MAXM], mAv[MAXM], mAz[MAXM];             // FP32: A ky', A kx', A |k'|^2
+    int kmax_x, kmax_y;                            // FP32: largest |kx|, |ky| (harmonic tables)
+    R drag_o;      // Cd rho_o pi
+    R drag_a;      // Ca rho_a pi
+    R wind_x, wind_y, wind_w;   // wind at t = 0 and its turning rate 2 pi / period
+    R mass_c;      // rho_ice pi
+    R inertia_f;   // 1 (paper) or 1/2
+    R E, G, eta, mu, inv_h_ref;
+};
+
+struct Geom {
+    int nx, ny;
+    double Lx, Ly, Lcx, Lcy;
+};
+
+// ---------------------------------------------------------------- helpers
+template <class R> __device__ __forceinline__ R dmin(R a, R b) { return a < b ? a : b; }
+template <class R> __device__ __forceinline__ R dmax(R a, R b) { return a > b ? a : b; }
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+
+// Contact of floe l with floe j given the minimum-image separation
+// (dx, dy) = x_j - x_l.  Eq. (2.2): n from l to j, delta = d - (r_l + r_j) < 0
+// in overlap; normal force c h (E delta + eta v_n) n, never attractive
+// (reading: optional dashpot eta; thickness factor h = min(h_l, h_j)/h_ref);
+// tangential c h G v_t t with |f_t| <= mu |f_n|; torque r_l f_t on l.
+// The chord c of the overlap lens is written symmetrically in (l, j):
+// c^2 d^2 = (S - d)(S + d)(d - D)(d + D), S = r_l + r_j, D = r_l - r_j
+// (Heron's formula for the triangle (d, r_l, r_j)); a floe inside the other
+// (d <= |D|) gives the smaller diameter.
+// Returns true on contact and adds the force on l to (fx, fy, tq).
+template <class R>
+__device__ __forceinline__ bool contact_add(R dx, R dy, R d2, R rl, R rj, R hl, R hj,
+                                            R dux, R duy, R wl, R wj, const Phys<R> &P,
+                                            R &fx, R &fy, R &tq, unsigned &deep)
+{
+    const R S = rl + rj;
+    if (!(d2 > R(0) && d2 < S * S)) return false;
+    const R d = sqrt(d2);
+    const R nx = dx / d, ny = dy / d;
+    const R delta = d - S;
+    const R D = rl - rj;
+    const R Q = (d - D) * (d + D);
+    const R c = (Q <= R(0)) ? R(2) * dmin(rl, rj) : sqrt((-delta) * (S + d) * Q) / d;
+    const R hc = dmin(hl, hj) * P.inv_h_ref;
+    const R vn = dux * nx + duy * ny;
+    R Fn = c * hc * (P.E * delta + P.eta * vn);
+    Fn = dmin(Fn, R(0));
+    const R vt = dux * (-ny) + duy * nx - wj * rj - wl * rl;
+    R ft = c * hc * P.G * vt;
+    const R cap = P.mu * (-Fn);
+    ft = dmax(dmin(ft, cap), -cap);
+    fx += Fn * nx - ft * ny;
+    fy += Fn * ny + ft * nx;
+    tq += rl * ft;
+    deep |= (delta < R(-0.5) * dmin(rl, rj)) ? 1u : 0u;
+    return true;
+}
+
+// Ocean drag at the floe plus wind drag, Eq. (2.1c-d): translation
+// alpha (u - v)|u - v| with alpha = Cd rho_o pi r^2 (wind: Ca rho_a pi r^2),
+// rotation beta (zeta/2 - w)|zeta/2 - w| with beta = Cd rho_o pi r^4.
+template <class R>
+__device__ __forceinline__ void drag_force(const Phys<R> &P, R uo, R vo, R zeta, R ua, R va,
+                                           R u, R v, R w, R r, R &Fx, R &Fy, R &T)
+{
+    const R ao = P.drag_o * r * r;
+    const R aa = P.drag_a * r * r;
+    const R bo = P.drag_o * r * r * r * r;
+    const R du = uo - u, dv = vo - v;
+    const R so = sqrt(du * du + dv * dv);
+    const R au = ua - u, av = va - v;
+    const R sa = sqrt(au * au + av * av);
+    const R dw = R(0.5) * zeta - w;
+    Fx = ao * du * so + aa * au * sa;
+    Fy = ao * dv * so + aa * av * sa;
+    T = bo * dw * fabs(dw);
+}
+
+// Ocean current and its curl at a global position, FP64:
+// u = uo_x - sum A ky cos(th), v = uo_y + sum A kx cos(th), curl = -sum A |k|^2 sin(th),
+// th = kx X + ky Y + phi (psi = sum A sin(th)).
+__device__ __forceinline__ void ocean_f64(const Phys<double> &P, double X, double Y,
+                                          double &uo, double &vo, double &zeta)
+{
+    uo = P.uo_x; vo = P.uo_y; zeta = 0.0;
+    for (int m = 0; m < P.n_modes; m++) {
+        const double th = P.mKx[m] * X + P.mKy[m] * Y + P.mPh[m];
+        double s, c;
+        sincos(th, &s, &c);
+        const double A = P.mA[m];
+        uo -= A * P.mKy[m] * c;
+        vo += A * P.mKx[m] * c;
+        zeta -= A * (P.mKx[m] * P.mKx[m] + P.mKy[m] * P.mKy[m]) * s;
+    }
+}
+
+// FP32 ocean at cell (ix, iy) + fraction (xf, yf) of the cell.  The phase in
+// cycles is ((kx ix) mod nx + kx xf)/nx + ((ky iy) mod ny + ky yf)/ny + phi/2pi,
+// with the integer part reduced exactly.  base[m] holds the cell's
+// ((kx ix) mod nx)/nx + ((ky iy) mod ny)/ny + phi/2pi.
+__device__ __forceinline__ void ocean_f32(const Phys<float> &P, const float *base, float inx,
+                                          float iny, float xf, float yf, float &uo, float &vo,
+                                          float &zeta)
+{
+    uo = P.uo_x; vo = P.uo_y; zeta = 0.0f;
+    for (int m = 0; m < P.n_modes; m++) {
+        const float cyc = base[m] + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+        float s, c;
+        sincospif(2.0f * cyc, &s, &c);
+        uo -= P.mAu[m] * c;
+        vo += P.mAv[m] * c;
+        zeta -= P.mAz[m] * s;
+    }
+}
+
+// Wind vector at time t: the t = 0 vector turned by wind_w * t.
+template <class R>
+__device__ __forceinline__ void wind_at(const Phys<R> &P, double t, R &ua, R &va)
+{
+    if (P.wind_w != R(0)) {
+        double s, c;
+        sincos((double)P.wind_w * t, &s, &c);
+        ua = (R)((double)P.wind_x * c - (double)P.wind_y * s);
+        va = (R)((double)P.wind_x * s + (double)P.wind_y * c);
+    } else {
+        ua = P.wind_x;
+        va = P.wind_y;
+    }
+}
+
+// ------------------------------------------------------ launch interfaces
+struct DevState32 {
+    uint32_t *xq, *yq;
+    float *th, *u, *v, *w, *r, *h;
+};
+struct DevState64 {
+    double *x, *y, *th, *u, *v, *w, *r, *h;
+};
+
+constexpr int MAXSEG = 4;   // size classes of cells launched separately (binned variant)
+
+struct CellLaunch {
+    int variant;       // 0 brute force, 1 binned (FP32 only)
+    int threads;       // threads per block (brute force)
+    float bin_beta;    // bin side in units of the mean floe spacing (binned variant)
+    int persistent;    // 1: grid of resident blocks + work queue (brute force)
+    int grid;          // blocks for the persistent form
+    // binned variant: cells in processing order split into size classes, each
+    // launched with its own block size and shared memory
+    int nseg;
+    int seg_begin[MAXSEG], seg_end[MAXSEG], seg_maxn[MAXSEG], seg_threads[MAXSEG];
+    int nbmax;         // bins per side at most
+};
+
+struct StepCommon {
+    const int *off;     // [ncell + 1]
+    const int *order;   // [ncell] processing order (largest cells first)
+    int ncell;
+    int max_n;          // largest cell
+    double *mom;        // [ncell][NMOM]
+    double *win;        // [NWIN][ncell]
+    const double *tgt;  // [4][ncell]
+    Ctrl *ctrl;
+    Geom g;
+    double dt;
+    int N0, n_t, couple;
+    long long i_local;  // step within the current coarse interval (0-based)
+};
+
+// cell_step.cu
+cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                               const StepCommon &sc, const CellLaunch &cl, cudaStream_t st);
+cudaError_t launch_cell_step64(const DevState64 &in, const DevState64 &out, const Phys<double> &P,
+                               const StepCommon &sc, const CellLaunch &cl, cudaStream_t st);
+cudaError_t launch_cell_moments32(const DevState32 &s, const Phys<float> &P, const StepCommon &sc,
+                                  cudaStream_t st);
+cudaError_t launch_cell_moments64(const DevState64 &s, const Phys<double> &P, const StepCommon &sc,
+                                  cudaStream_t st);
+size_t cell_step_smem(int precision, const CellLaunch &cl, int max_n, int nx, int ny);
+int seg_nbmax(const CellLaunch &cl, int s);
+cudaError_t cell_step_prepare(int precision, const CellLaunch &cl, size_t smem);
+
+// coarse.cu
+struct CoarseArgs {
+    int nx, ny;
+    double dx, dy, Ac, dT;
+    int N0;
+    const double *mom;  // [ncell][NMOM]
+    double *win;        // [NWIN][ncell]
+    double *q0, *q1;    // [4][ncell] ping-pong
+    double *V;          // [2][ncell]
+    double *S;          // [4][ncell]
+    double *tgt;        // [4][ncell]
+    Ctrl *ctrl;
+};
+cudaError_t launch_coarse_step(const CoarseArgs &a, cudaStream_t st);   // NSUB_MAX + 3 launches
+cudaError_t launch_advance(Ctrl *ctrl, int N0, cudaStream_t st);       // base += N0
+int coarse_launches();
+
+// truth.cu
+struct TruthBins {
+    int nbx, nby;          // bins per side (1 x 1: brute force)
+    int *count;            // [nbins]
+    int *start;            // [nbins + 1]
+    int *cursor;           // [nbins]
+    int *sorted;           // [n] floe indices grouped by bin
+    int *bin;              // [n]
+    int *scan_tmp;         // block sums
+    int nscan_blocks;
+};
+struct TruthArgs {
+    long long n;
+    Geom g;
+    double dt;
+    long long step;        // steps done before this one
+    Ctrl *ctrl;            // error bits and deep-overlap counter
+    void *fd;              // [3][n] drag of the last step (R)
+};
+cudaError_t launch_truth_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                                const TruthArgs &a, TruthBins &b, cudaStream_t st);
+cudaError_t launch_truth_step64(const DevState64 &in, const DevState64 &out, const Phys<double> &P,
+                                const TruthArgs &a, TruthBins &b, cudaStream_t st);
+cudaError_t launch_truth_moments32(const DevState32 &s, const Phys<float> &P, const TruthArgs &a,
+                                   TruthBins &cells, double *mom, cudaStream_t st);
+cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, const TruthArgs &a,
+                                   TruthBins &cells, double *mom, cudaStream_t st);
+int truth_launches(const TruthBins &b);
+cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
+
+}  // namespace msd

@@ -1,0 +1,390 @@
+// truth.cu -- the un-localised DEM over the whole periodic domain (the
+// "truth" the paper compares the multiscale model against, Sec. 4), and the
+// binning of its floes by coarse cell for the moments.
+//
+// Every step the floes are re-binned by a GPU counting sort (count -> scan ->
+// scatter -> per-bin sort by floe index, so the bin contents and thus the
+// force summation order are deterministic) into square-ish bins of side at
+// least 2 r_max; each floe then visits the 3 x 3 neighbouring bins.  The state
+// is double-buffered: the step reads one copy and writes the other.
+#include "common.cuh"
+
+namespace msd {
+
+namespace {
+
+constexpr int SCAN_T = 1024;
+
+__global__ void k_scan_blocks(const int *in, int *out, int *bsum, int n)
+{
+    __shared__ int ws[32];
+    const int i = blockIdx.x * SCAN_T + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = i < n ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? ws[warp - 1] : 0);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == SCAN_T - 1) bsum[blockIdx.x] = incl;
+}
+
+// exclusive scan of the block sums, in place (nb <= SCAN_T)
+__global__ void k_scan_top(int *bsum, int nb)
+{
+    __shared__ int ws[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = threadIdx.x < nb ? bsum[threadIdx.x] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? ws[warp - 1] : 0);
+    if (threadIdx.x < nb) bsum[threadIdx.x] = incl - v;
+}
+
+__global__ void k_scan_add(int *out, const int *bsum, int n)
+{
+    const int i = blockIdx.x * SCAN_T + threadIdx.x;
+    if (i < n) out[i] += bsum[blockIdx.x];
+}
+
+__global__ void k_scatter(const int *bin, const int *start, int *cursor, int *sorted, long long n)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int b = bin[l];
+    sorted[start[b] + atomicAdd(&cursor[b], 1)] = (int)l;
+}
+
+// insertion sort of each bin's floe indices (bins hold a handful of floes)
+__global__ void k_bin_sort(const int *start, int *sorted, int nbins)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int s = start[b], e = start[b + 1];
+    for (int i = s + 1; i < e; i++) {
+        const int key = sorted[i];
+        int j = i - 1;
+        while (j >= s && sorted[j] > key) {
+            sorted[j + 1] = sorted[j];
+            j--;
+        }
+        sorted[j + 1] = key;
+    }
+}
+
+// bin of a fixed-point coordinate: floor(frac * nb) exactly
+__device__ __forceinline__ int fbin(uint32_t q, int nb) { return (int)(((unsigned long long)q * (unsigned)nb) >> 32); }
+
+__device__ __forceinline__ int dbin(double x, double L, int nb)
+{
+    int b = (int)floor(x / (L / nb));
+    return b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
+}
+
+__global__ void k_bin32(const uint32_t *xq, const uint32_t *yq, int nbx, int nby, int *bin, int *count,
+                        long long n)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int b = fbin(yq[l], nby) * nbx + fbin(xq[l], nbx);
+    bin[l] = b;
+    atomicAdd(&count[b], 1);
+}
+
+__global__ void k_bin64(const double *x, const double *y, double Lx, double Ly, int nbx, int nby, int *bin,
+                        int *count, long long n)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int b = dbin(y[l], Ly, nby) * nbx + dbin(x[l], Lx, nbx);
+    bin[l] = b;
+    atomicAdd(&count[b], 1);
+}
+
+// ------------------------------------------------------------ truth steps
+// Neighbour bins of (bx, by): 3 x 3 with periodic wrap, or the bin alone
+// along an axis that has fewer than 3 bins (then it holds the whole axis).
+struct NbRange {
+    int x0, x1, y0, y1;
+};
+__device__ __forceinline__ NbRange nb_range(int nbx, int nby)
+{
+    NbRange r;
+    r.x0 = nbx >= 3 ? -1 : 0; r.x1 = nbx >= 3 ? 1 : 0;
+    r.y0 = nby >= 3 ? -1 : 0; r.y1 = nby >= 3 ? 1 : 0;
+    return r;
+}
+
+__global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArgs a, const int *bin,
+                          const int *start, const int *sorted, int nbx, int nby)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n) return;
+    const float sx = (float)(a.g.Lx / 4294967296.0), sy = (float)(a.g.Ly / 4294967296.0);
+    const float isx = (float)(4294967296.0 / a.g.Lx), isy = (float)(4294967296.0 / a.g.Ly);
+    const uint32_t xl = in.xq[l], yl = in.yq[l];
+    const float ul = in.u[l], vl = in.v[l], wl = in.w[l], rl = in.r[l], hl = in.h[l];
+    const int b = bin[l];
+    const int bx = b % nbx, by = b / nbx;
+    const NbRange nr = nb_range(nbx, nby);
+    float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+    unsigned deep = 0;
+    for (int oy = nr.y0; oy <= nr.y1; oy++) {
+        const int cy = (by + oy + nby) % nby;
+        for (int ox = nr.x0; ox <= nr.x1; ox++) {
+            const int cb = cy * nbx + (bx + ox + nbx) % nbx;
+            for (int k = start[cb]; k < start[cb + 1]; k++) {
+                const int j = sorted[k];
+                if (j == l) continue;
+                const float dx = (float)(int)(in.xq[j] - xl) * sx;
+                const float dy = (float)(int)(in.yq[j] - yl) * sy;
+                const float d2 = dx * dx + dy * dy;
+                const float rj = in.r[j];
+                const float S = rl + rj;
+                if (d2 < S * S)
+                    contact_add(dx, dy, d2, rl, rj, hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
+                                fx, fy, tq, deep);
+            }
+        }
+    }
+    // ocean at the domain fraction; wave numbers are integer over the domain
+    const float xf = (float)xl * 2.3283064365386963e-10f, yf = (float)yl * 2.3283064365386963e-10f;
+    float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
+    for (int m = 0; m < P.n_modes; m++) {
+        float cyc = (float)P.mkx[m] * xf + (float)P.mky[m] * yf + P.mCyc[m];
+        cyc -= floorf(cyc);
+        float s, c;
+        sincospif(2.0f * cyc, &s, &c);
+        uo -= P.mAu[m] * c;
+        vo += P.mAv[m] * c;
+        zeta -= P.mAz[m] * s;
+    }
+    float ua, va;
+    wind_at(P, (double)a.step * a.dt, ua, va);
+    float Fdx, Fdy, Td;
+    drag_force(P, uo, vo, zeta, ua, va, ul, vl, wl, rl, Fdx, Fdy, Td);
+    fx += Fdx; fy += Fdy; tq += Td;
+    const float dt = (float)a.dt;
+    const float m = P.mass_c * rl * rl * hl;
+    const float I = P.inertia_f * m * rl * rl;
+    out.xq[l] = xl + (uint32_t)__float2int_rn(dt * ul * isx);
+    out.yq[l] = yl + (uint32_t)__float2int_rn(dt * vl * isy);
+    out.th[l] = in.th[l] + dt * wl;
+    const float un = ul + dt * (fx / m), vn = vl + dt * (fy / m), wn = wl + dt * (tq / I);
+    out.u[l] = un;
+    out.v[l] = vn;
+    out.w[l] = wn;
+    out.r[l] = rl;
+    out.h[l] = hl;
+    float *fd = reinterpret_cast<float *>(a.fd);
+    fd[l] = Fdx; fd[a.n + l] = Fdy; fd[2 * a.n + l] = Td;
+    if (!(isfinite(un) && isfinite(vn) && isfinite(wn))) atomicOr(&a.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&a.ctrl->deep, 1ull);
+}
+
+__global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthArgs a, const int *bin,
+                          const int *start, const int *sorted, int nbx, int nby)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n) return;
+    const double Lx = a.g.Lx, Ly = a.g.Ly;
+    const double xl = in.x[l], yl = in.y[l], ul = in.u[l], vl = in.v[l], wl = in.w[l], rl = in.r[l],
+                 hl = in.h[l];
+    const int b = bin[l];
+    const int bx = b % nbx, by = b / nbx;
+    const NbRange nr = nb_range(nbx, nby);
+    double fx = 0.0, fy = 0.0, tq = 0.0;
+    unsigned deep = 0;
+    for (int oy = nr.y0; oy <= nr.y1; oy++) {
+        const int cy = (by + oy + nby) % nby;
+        for (int ox = nr.x0; ox <= nr.x1; ox++) {
+            const int cb = cy * nbx + (bx + ox + nbx) % nbx;
+            for (int k = start[cb]; k < start[cb + 1]; k++) {
+                const int j = sorted[k];
+                if (j == l) continue;
+                double dx = in.x[j] - xl, dy = in.y[j] - yl;
+                dx -= Lx * rint(dx / Lx);
+                dy -= Ly * rint(dy / Ly);
+                const double d2 = dx * dx + dy * dy;
+                contact_add(dx, dy, d2, rl, in.r[j], hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
+                            fx, fy, tq, deep);
+            }
+        }
+    }
+    double uo, vo, zeta;
+    ocean_f64(P, xl, yl, uo, vo, zeta);
+    double ua, va;
+    wind_at(P, (double)a.step * a.dt, ua, va);
+    double Fdx, Fdy, Td;
+    drag_force(P, uo, vo, zeta, ua, va, ul, vl, wl, rl, Fdx, Fdy, Td);
+    fx += Fdx; fy += Fdy; tq += Td;
+    const double dt = a.dt;
+    const double m = P.mass_c * rl * rl * hl;
+    const double I = P.inertia_f * m * rl * rl;
+    double xn = xl + dt * ul, yn = yl + dt * vl;
+    xn -= Lx * floor(xn / Lx);
+    yn -= Ly * floor(yn / Ly);
+    out.x[l] = xn;
+    out.y[l] = yn;
+    out.th[l] = in.th[l] + dt * wl;
+    const double un = ul + dt * (fx / m), vn = vl + dt * (fy / m), wn = wl + dt * (tq / I);
+    out.u[l] = un;
+    out.v[l] = vn;
+    out.w[l] = wn;
+    out.r[l] = rl;
+    out.h[l] = hl;
+    double *fd = reinterpret_cast<double *>(a.fd);
+    fd[l] = Fdx; fd[a.n + l] = Fdy; fd[2 * a.n + l] = Td;
+    if (!(isfinite(un) && isfinite(vn) && isfinite(wn))) atomicOr(&a.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&a.ctrl->deep, 1ull);
+}
+
+// --------------------------------------------------------- truth moments
+// One thread per coarse cell sums its floes in ascending floe index, in FP64.
+template <class R>
+__global__ void k_truth_cell_moments(const R *u, const R *v, const R *w, const R *r, const R *h, const R *fd,
+                                     long long n, double mass_c, double inertia_f, const int *start,
+                                     const int *sorted, int ncell, double *mom)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    double mo[NMOM];
+    for (int k = 0; k < NMOM; k++) mo[k] = 0.0;
+    for (int k = start[c]; k < start[c + 1]; k++) {
+        const int l = sorted[k];
+        const double rl = r[l], hl = h[l], ul = u[l], vl = v[l], wl = w[l];
+        const double m = mass_c * rl * rl * hl;
+        const double I = inertia_f * m * rl * rl;
+        mo[0] += 1.0;
+        mo[1] += m;
+        mo[2] += m * ul;
+        mo[3] += m * vl;
+        mo[4] += I;
+        mo[5] += I * wl;
+        mo[6] += 3.14159265358979323846 * rl * rl;
+        mo[7] += m * ul * ul;
+        mo[8] += m * vl * vl;
+        mo[9] += fd[l];
+        mo[10] += fd[n + l];
+        mo[11] += fd[2 * n + l];
+    }
+    for (int k = 0; k < NMOM; k++) mom[(size_t)c * NMOM + k] = mo[k];
+}
+
+template <class BinF>
+cudaError_t counting_sort(TruthBins &b, long long n, BinF binf, cudaStream_t st)
+{
+    const int nbins = b.nbx * b.nby;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.count, 0, sizeof(int) * nbins, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.cursor, 0, sizeof(int) * nbins, st)) != cudaSuccess) return e;
+    if (n > 0) binf();
+    if ((e = bins_scan(b, nbins, st)) != cudaSuccess) return e;
+    const int T = 256;
+    if (n > 0) k_scatter<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.bin, b.start, b.cursor, b.sorted, n);
+    k_bin_sort<<<(nbins + T - 1) / T, T, 0, st>>>(b.start, b.sorted, nbins);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st)
+{
+    const int nb = (nbins + SCAN_T - 1) / SCAN_T;
+    if (nb > SCAN_T) return cudaErrorInvalidValue;
+    k_scan_blocks<<<nb, SCAN_T, 0, st>>>(b.count, b.start, b.scan_tmp, nbins);
+    k_scan_top<<<1, SCAN_T, 0, st>>>(b.scan_tmp, nb);
+    k_scan_add<<<nb, SCAN_T, 0, st>>>(b.start, b.scan_tmp, nbins);
+    return cudaGetLastError();
+}
+
+int truth_launches(const TruthBins &) { return 2 /*memsets*/ + 1 + 3 + 1 + 1 + 1; }
+
+cudaError_t launch_truth_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                                const TruthArgs &a, TruthBins &b, cudaStream_t st)
+{
+    const int T = 256;
+    const unsigned G = (unsigned)((a.n + T - 1) / T);
+    cudaError_t e = counting_sort(b, a.n, [&] {
+        k_bin32<<<G, T, 0, st>>>(in.xq, in.yq, b.nbx, b.nby, b.bin, b.count, a.n);
+    }, st);
+    if (e != cudaSuccess) return e;
+    if (a.n > 0) k_truth32<<<G, T, 0, st>>>(in, out, P, a, b.bin, b.start, b.sorted, b.nbx, b.nby);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_truth_step64(const DevState64 &in, const DevState64 &out, const Phys<double> &P,
+                                const TruthArgs &a, TruthBins &b, cudaStream_t st)
+{
+    const int T = 256;
+    const unsigned G = (unsigned)((a.n + T - 1) / T);
+    cudaError_t e = counting_sort(b, a.n, [&] {
+        k_bin64<<<G, T, 0, st>>>(in.x, in.y, a.g.Lx, a.g.Ly, b.nbx, b.nby, b.bin, b.count, a.n);
+    }, st);
+    if (e != cudaSuccess) return e;
+    if (a.n > 0) k_truth64<<<G, T, 0, st>>>(in, out, P, a, b.bin, b.start, b.sorted, b.nbx, b.nby);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_truth_moments32(const DevState32 &s, const Phys<float> &P, const TruthArgs &a,
+                                   TruthBins &cells, double *mom, cudaStream_t st)
+{
+    const int T = 256;
+    const unsigned G = (unsigned)((a.n + T - 1) / T);
+    cudaError_t e = counting_sort(cells, a.n, [&] {
+        k_bin32<<<G, T, 0, st>>>(s.xq, s.yq, cells.nbx, cells.nby, cells.bin, cells.count, a.n);
+    }, st);
+    if (e != cudaSuccess) return e;
+    const int nc = cells.nbx * cells.nby;
+    k_truth_cell_moments<float><<<(nc + 127) / 128, 128, 0, st>>>(
+        s.u, s.v, s.w, s.r, s.h, reinterpret_cast<const float *>(a.fd), a.n, (double)P.mass_c,
+        (double)P.inertia_f, cells.start, cells.sorted, nc, mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, const TruthArgs &a,
+                                   TruthBins &cells, double *mom, cudaStream_t st)
+{
+    const int T = 256;
+    const unsigned G = (unsigned)((a.n + T - 1) / T);
+    cudaError_t e = counting_sort(cells, a.n, [&] {
+        k_bin64<<<G, T, 0, st>>>(s.x, s.y, a.g.Lx, a.g.Ly, cells.nbx, cells.nby, cells.bin, cells.count, a.n);
+    }, st);
+    if (e != cudaSuccess) return e;
+    const int nc = cells.nbx * cells.nby;
+    k_truth_cell_moments<double><<<(nc + 127) / 128, 128, 0, st>>>(
+        s.u, s.v, s.w, s.r, s.h, reinterpret_cast<const double *>(a.fd), a.n, P.mass_c, P.inertia_f,
+        cells.start, cells.sorted, nc, mom);
+    return cudaGetLastError();
+}
+
+}  // namespace msd

@@ -1,0 +1,236 @@
+"""Thin ctypes binding of libmsdem.so (the C-ABI of include/msdem.h).
+
+Argument marshalling only: every step of the model runs in the library's CUDA
+kernels.  Importing this module loads the library and raises if it is missing
+or no CUDA device is usable; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NMOM = 12
+NWIN = 5
+MAX_MODES = 16
+MS_FP32, MS_FP64 = 0, 1
+ERRORS = {0: "MS_OK", -1: "MS_ERR_ARG", -2: "MS_ERR_CUDA", -3: "MS_ERR_UNSTABLE", -4: "MS_ERR_TIMEOUT",
+          -5: "MS_ERR_STATE"}
+MOMENT_NAMES = ["n", "M", "Mu", "Mv", "I", "Iw", "area", "Muu", "Mvv", "Fdx", "Fdy", "Td"]
+FLOE_KEYS = ("x", "y", "theta", "u", "v", "omega", "r", "h")
+
+_dp = C.POINTER(C.c_double)
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double)]
+
+
+class Floes(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(k, _dp) for k in FLOE_KEYS]
+
+
+class Forcing(C.Structure):
+    _fields_ = [
+        ("uo_x", C.c_double), ("uo_y", C.c_double), ("n_modes", C.c_int32), ("modes", _dp),
+        ("rho_o", C.c_double), ("Cd", C.c_double), ("rho_a", C.c_double), ("Ca", C.c_double),
+        ("wind_x", C.c_double), ("wind_y", C.c_double), ("wind_period", C.c_double),
+        ("rho_ice", C.c_double), ("E", C.c_double), ("G", C.c_double), ("eta", C.c_double),
+        ("mu", C.c_double), ("h_ref", C.c_double), ("inertia_half", C.c_int32),
+        ("couple", C.c_int32), ("N0", C.c_int32), ("n_t", C.c_int32), ("precision", C.c_int32),
+    ]
+
+
+class MsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_get_floes", "ms_set_floes", "ms_coupling",
+           "ms_truth_step", "ms_truth_moments", "ms_truth_get_floes", "ms_set_stream", "ms_autotune",
+           "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libmsdem.so (building it if the sources are newer).  Raises when
+    the library cannot be built or loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if path is None and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libmsdem.so not found at {p}; run __graft_entry__.build()")
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    L.ms_init.argtypes = [C.POINTER(vp), C.POINTER(Grid), C.POINTER(Floes), C.POINTER(Forcing)]
+    L.ms_step.argtypes = [vp, C.c_double, C.c_int64]
+    L.ms_step_async.argtypes = [vp, C.c_double, C.c_int64]
+    L.ms_sync.argtypes = [vp]
+    L.ms_moments.argtypes = [vp, _dp]
+    L.ms_get_floes.argtypes = [vp, _dp]
+    L.ms_set_floes.argtypes = [vp, C.POINTER(Floes)]
+    L.ms_coupling.argtypes = [vp, _dp, _dp, _dp, C.POINTER(C.c_int64)]
+    L.ms_truth_step.argtypes = [vp, C.c_double, C.c_int64]
+    L.ms_truth_moments.argtypes = [vp, _dp]
+    L.ms_truth_get_floes.argtypes = [vp, _dp]
+    L.ms_set_stream.argtypes = [vp, vp]
+    L.ms_autotune.argtypes = [vp, C.c_double, C.c_int32, _dp]
+    L.ms_time_kernel.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, _dp]
+    L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double]
+    L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.ms_free.argtypes = [vp]
+    L.ms_free.restype = None
+    L.ms_last_error.restype = C.c_char_p
+    for name in SYMBOLS:
+        if name not in ("ms_free", "ms_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MsError(rc, load().ms_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def make_floes(floes: dict):
+    arrs = [np.ascontiguousarray(floes[k], dtype=np.float64) for k in FLOE_KEYS]
+    s = Floes()
+    s.n = arrs[0].shape[0]
+    for k, a in zip(FLOE_KEYS, arrs):
+        setattr(s, k, _ptr(a))
+    return s, arrs
+
+
+def make_forcing(p: dict, precision: int):
+    modes = np.ascontiguousarray(np.asarray(p.get("modes", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4))
+    f = Forcing()
+    f.uo_x, f.uo_y = float(p.get("uo_x", 0.0)), float(p.get("uo_y", 0.0))
+    f.n_modes = modes.shape[0]
+    f.modes = _ptr(modes) if modes.shape[0] else _dp()
+    for k in ("rho_o", "Cd", "rho_a", "Ca", "wind_x", "wind_y", "wind_period", "rho_ice", "E", "G", "eta",
+              "mu", "h_ref"):
+        setattr(f, k, float(p.get(k, 0.0)))
+    f.inertia_half = int(p.get("inertia_half", 0))
+    f.couple, f.N0, f.n_t = int(p.get("couple", 0)), int(p.get("N0", 100)), int(p.get("n_t", 10))
+    f.precision = int(precision)
+    return f, modes
+
+
+class Model:
+    """One msDEM model (plus its truth DEM) on the current CUDA device."""
+
+    def __init__(self, params: dict, floes: dict, precision: int = MS_FP32):
+        L = load()
+        self.params = dict(params)
+        self.precision = precision
+        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]))
+        fl, keep1 = make_floes(floes)
+        fc, keep2 = make_forcing(params, precision)
+        h = C.c_void_p()
+        _check(L.ms_init(C.byref(h), C.byref(g), C.byref(fl), C.byref(fc)))
+        self._h = h
+        self.n = int(fl.n)
+        self.ncell = g.nx * g.ny
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().ms_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, dt: float, nsteps: int) -> None:
+        _check(load().ms_step(self._h, float(dt), int(nsteps)))
+
+    def step_async(self, dt: float, nsteps: int) -> None:
+        _check(load().ms_step_async(self._h, float(dt), int(nsteps)))
+
+    def sync(self) -> None:
+        _check(load().ms_sync(self._h))
+
+    def moments(self) -> np.ndarray:
+        out = np.zeros((self.ncell, NMOM))
+        _check(load().ms_moments(self._h, _ptr(out)))
+        return out
+
+    def floes(self) -> dict:
+        out = np.zeros((8, self.n))
+        _check(load().ms_get_floes(self._h, _ptr(out)))
+        return {k: out[i] for i, k in enumerate(FLOE_KEYS)}
+
+    def set_floes(self, floes: dict) -> None:
+        fl, keep = make_floes(floes)
+        _check(load().ms_set_floes(self._h, C.byref(fl)))
+
+    def coupling(self) -> dict:
+        nc = self.ncell
+        q = np.zeros((4, nc)); tg = np.zeros((4, nc)); win = np.zeros((NWIN, nc))
+        fl = np.zeros(3, dtype=np.int64)
+        _check(load().ms_coupling(self._h, _ptr(q), _ptr(tg), _ptr(win),
+                                  fl.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {"q": q, "targets": tg, "window": win, "have_q": int(fl[0]), "have_targets": int(fl[1]),
+                "steps": int(fl[2])}
+
+    def truth_step(self, dt: float, nsteps: int) -> None:
+        _check(load().ms_truth_step(self._h, float(dt), int(nsteps)))
+
+    def truth_moments(self) -> np.ndarray:
+        out = np.zeros((self.ncell, NMOM))
+        _check(load().ms_truth_moments(self._h, _ptr(out)))
+        return out
+
+    def truth_floes(self) -> dict:
+        out = np.zeros((8, self.n))
+        _check(load().ms_truth_get_floes(self._h, _ptr(out)))
+        return {k: out[i] for i, k in enumerate(FLOE_KEYS)}
+
+    def set_stream(self, stream_handle: int | None) -> None:
+        _check(load().ms_set_stream(self._h, C.c_void_p(stream_handle or 0)))
+
+    def autotune(self, dt: float, reps: int = 5) -> float:
+        best = C.c_double(0.0)
+        _check(load().ms_autotune(self._h, float(dt), int(reps), C.byref(best)))
+        return best.value
+
+    def time_kernel(self, which: int, dt: float, reps: int = 10) -> float:
+        out = C.c_double(0.0)
+        _check(load().ms_time_kernel(self._h, int(which), float(dt), int(reps), C.byref(out)))
+        return out.value
+
+    def set_launch(self, variant: int = 0, threads: int = 128, persistent: int = 0,
+                   bin_beta: float = 1.0) -> None:
+        _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta)))
+
+    def info(self) -> dict:
+        out = np.zeros(16, dtype=np.int64)
+        _check(load().ms_info(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        keys = ["n", "ncell", "max_n", "precision", "variant", "threads", "bin_beta_milli",
+                "launches_per_step", "launches_per_coarse", "launches_per_truth_step", "steps",
+                "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1"]
+        return {k: int(v) for k, v in zip(keys, out)}

@@ -1,0 +1,270 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances (relative, per moment field, 2-norm over cells):
+  FP64 path  <= 1e-10 over 100 steps (and through the first coarse steps);
+  FP32 path  <= 1e-4  over 100 steps.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_07819_gb300 import inputs as I
+from tests.parity import rel_errors, report
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ms():
+    from paper_2303_07819_gb300 import msdem
+    msdem.load()
+    return msdem
+
+
+def run_pair(orc, ms, scen, precision, nsteps, params=None):
+    p = dict(scen["params"], **(params or {}))
+    o = orc.Model(p, scen["floes"])
+    g = ms.Model(p, scen["floes"], precision)
+    o.step(scen["dt"], nsteps)
+    g.step(scen["dt"], nsteps)
+    return o, g, p
+
+
+@pytest.mark.parametrize("nsteps", [1, 100, 250])
+def test_fp64_msdem_config0(orc, ms, nsteps):
+    s = I.config0()
+    o, g, p = run_pair(orc, ms, s, ms.MS_FP64, nsteps)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-12)
+    assert e.max() <= TOL64, report(e)
+    if nsteps >= 100:
+        co, cg = o.coupling(), g.coupling()
+        assert cg["have_q"] == co["have_q"] and cg["have_targets"] == co["have_targets"]
+        for key in ("q", "targets"):
+            a, b = cg[key], co[key]
+            assert np.linalg.norm(a - b) <= TOL64 * max(np.linalg.norm(b), 1e-300), key
+
+
+def test_fp64_msdem_floes_config0(orc, ms):
+    s = I.config0()
+    o, g, p = run_pair(orc, ms, s, ms.MS_FP64, 100)
+    fo, fg = o.floes(), g.floes()
+    assert np.max(np.abs(fo["x"] - fg["x"])) < 1e-6 and np.max(np.abs(fo["y"] - fg["y"])) < 1e-6
+    for k in ("u", "v", "omega", "r"):
+        assert np.linalg.norm(fo[k] - fg[k]) <= TOL64 * np.linalg.norm(fo[k]) + 1e-20, k
+
+
+def test_fp32_msdem_config0(orc, ms):
+    s = I.config0()
+    o, g, p = run_pair(orc, ms, s, ms.MS_FP32, 100)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_msdem_config1_small(orc, ms, precision):
+    """config1's laws (power-law radii, lognormal thickness, 8 Fourier modes,
+    wind) on 4 x 4 cells of 12.5 km, ~1000 floes, cells up to ~90 floes."""
+    s = I.config1(nx=4)
+    o, g, p = run_pair(orc, ms, s, precision, 100)
+    tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
+    e = rel_errors(g.moments(), o.moments(), p, eps)
+    assert e.max() <= tol, report(e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_truth_config0(orc, ms, precision):
+    s = I.config0()
+    p = s["params"]
+    o = orc.Truth(p, s["floes"])
+    g = ms.Model(p, s["floes"], precision)
+    o.step(s["dt"], 100)
+    g.truth_step(s["dt"], 100)
+    tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
+    e = rel_errors(g.truth_moments(), o.moments(), p, eps)
+    assert e.max() <= tol, report(e)
+
+
+def test_truth_config1_small_fp64(orc, ms):
+    s = I.config1(nx=4)
+    p = s["params"]
+    o = orc.Truth(p, s["floes"])
+    g = ms.Model(p, s["floes"], ms.MS_FP64)
+    o.step(s["dt"], 50)
+    g.truth_step(s["dt"], 50)
+    e = rel_errors(g.truth_moments(), o.moments(), p, 1e-12)
+    assert e.max() <= TOL64, report(e)
+
+
+def ragged_scenario(counts, L_c=12.5e3, seed=5):
+    """Cells with the given floe counts (0 allowed) on a small periodic grid,
+    power-law radii rescaled to 45% cover, config1 forcing."""
+    rng = np.random.default_rng(seed)
+    nx = ny = int(np.ceil(np.sqrt(len(counts))))
+    counts = list(counts) + [0] * (nx * ny - len(counts))
+    L = L_c * nx
+    radii = [I.power_law_radii(rng, int(c), 100.0, 1500.0) for c in counts]
+    radii, _ = I._rescale_cells(radii, L_c * L_c, 0.45)
+    x, y, r, cell = I.place_floes(rng, nx, ny, L, L, radii, domain_check=False)
+    h = I.lognormal_mean_sd(rng, x.shape[0], 1.5, 0.5)
+    p = I._phys(dt=5.0)
+    p.update({"nx": nx, "ny": ny, "Lx": L, "Ly": L, "modes": I.random_modes(rng, 8, L, L, 0.1),
+              "Ca": 1.2e-3, "wind_x": 10.0, "wind_y": 0.0})
+    fl = I._floes(x, y, r, h)
+    fl["u"] = rng.normal(0, 0.1, x.shape[0])
+    fl["v"] = rng.normal(0, 0.1, x.shape[0])
+    return {"params": p, "floes": fl, "dt": 5.0}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_and_empty_cells(orc, ms, precision):
+    """Cells of 0, 1, 2, 31, 33, 64, 127, 129, 300 floes: empty cells, a lone
+    floe, and counts on both sides of the warp and block tiles."""
+    s = ragged_scenario([0, 1, 2, 31, 33, 64, 127, 129, 300])
+    o, g, p = run_pair(orc, ms, s, precision, 30)
+    tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
+    mo, mg = o.moments(), g.moments()
+    assert np.array_equal(mo[:, 0], mg[:, 0])
+    e = rel_errors(mg, mo, p, eps)
+    assert e.max() <= tol, report(e)
+
+
+def test_no_floes(ms):
+    p = dict(I.config0()["params"])
+    fl = {k: np.zeros(0) for k in ("x", "y", "theta", "u", "v", "omega", "r", "h")}
+    g = ms.Model(p, fl, ms.MS_FP32)
+    g.step(10.0, 150)
+    assert np.all(g.moments() == 0.0)
+    g.truth_step(10.0, 3)
+    assert np.all(g.truth_moments() == 0.0)
+
+
+def test_largest_cell_fp32(orc, ms):
+    """A cell at the 4096-floe limit (several shared-memory tiles), one step."""
+    s = ragged_scenario([4096], L_c=100e3, seed=9)
+    p = dict(s["params"], couple=0)
+    o, g, _ = run_pair(orc, ms, s, ms.MS_FP32, 1, params=p)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= 1e-5, report(e)
+
+
+def test_full_size_config2_sampled_cells(orc, ms):
+    """configs[2] at full size (~2.0M floes, 16,384 cells) on the GPU, one
+    step; the oracle recomputes a sample of 48 cells (the largest and random
+    ones) from those cells' floes alone, since the cells' DEMs are independent
+    within a step."""
+    s = I.config2()
+    p = s["params"]
+    g = ms.Model(p, s["floes"], ms.MS_FP32)
+    g.step(s["dt"], 1)
+    mg = g.moments()
+    cell = s["meta"]["cell"]
+    counts = np.bincount(cell, minlength=p["nx"] * p["ny"])
+    rng = np.random.default_rng(0)
+    pick = np.unique(np.concatenate([np.argsort(-counts)[:8], rng.choice(len(counts), 40, replace=False)]))
+    sel = np.isin(cell, pick)
+    sub = {k: v[sel] for k, v in s["floes"].items()}
+    o = orc.Model(p, sub)
+    o.step(s["dt"], 1)
+    mo = o.moments()[pick]
+    e = rel_errors(mg[pick], mo, p, 1e-6)
+    assert e.max() <= 1e-5, report(e)
+    # totals that hold at any size: floe counts per cell and total mass
+    assert np.array_equal(mg[:, 0], counts.astype(np.float64))
+    g.close()
+
+
+def test_graph_replay_equals_single_steps(ms):
+    s = I.config0()
+    a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    a.step(s["dt"], 230)
+    for _ in range(230):
+        b.step(s["dt"], 1)
+    assert a.info()["graph_replays"] >= 2 and b.info()["graph_replays"] == 0
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_launch_variants_agree(ms):
+    """Threads per block and the persistent work queue change only the order
+    of the moment reduction, never a floe's arithmetic: floes agree bitwise
+    until the first coarse step, which feeds the reduced moments back."""
+    s = I.config1(nx=4)
+    ref = refm = None
+    for threads in (64, 128, 256):
+        for persistent in (0, 1):
+            g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+            g.set_launch(0, threads, persistent)
+            g.step(s["dt"], 99)
+            f = g.floes()
+            g.step(s["dt"], 31)
+            mo = g.moments()
+            if ref is None:
+                ref, refm = f, mo
+            for k in f:
+                assert np.array_equal(f[k], ref[k]), (threads, persistent, k)
+            e = rel_errors(mo, refm, s["params"], 1e-6)
+            assert e.max() < 1e-5, report(e)
+
+
+def test_autotune_keeps_results(ms):
+    s = I.config1(nx=8)
+    a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    best = b.autotune(s["dt"], reps=3)
+    assert best > 0
+    a.step(s["dt"], 120)
+    b.step(s["dt"], 120)
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    ea = rel_errors(b.moments(), a.moments(), s["params"], 1e-6)
+    assert ea.max() < 1e-6, report(ea)
+
+
+def test_time_kernel_leaves_state(ms):
+    s = I.config0()
+    a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    a.step(s["dt"], 5)
+    before = a.floes()
+    t0 = a.time_kernel(0, s["dt"], 5)
+    t1 = a.time_kernel(1, s["dt"], 5)
+    assert t0 > 0 and t1 > 0
+    after = a.floes()
+    for k in before:
+        assert np.array_equal(before[k], after[k])
+
+
+def test_argument_errors(ms):
+    s = I.config0()
+    g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    g.step(10.0, 1)
+    with pytest.raises(ms.MsError) as e:
+        g.step(5.0, 1)
+    assert e.value.code == -1
+    bad = {k: v.copy() for k, v in s["floes"].items()}
+    bad["u"][3] = np.nan
+    with pytest.raises(ms.MsError):
+        ms.Model(s["params"], bad, ms.MS_FP32)
+    big = {k: v.copy() for k, v in s["floes"].items()}
+    big["r"][0] = 7000.0           # 2 r >= L_c / 2 = 12.5 km
+    with pytest.raises(ms.MsError):
+        ms.Model(s["params"], big, ms.MS_FP32)
+    moved = g.floes()
+    moved["x"][0] += 30e3          # into another cell
+    with pytest.raises(ms.MsError):
+        g.set_floes(moved)
+
+
+def test_set_floes_roundtrip(ms):
+    s = I.config0()
+    g = ms.Model(s["params"], s["floes"], ms.MS_FP64)
+    g.step(10.0, 7)
+    f = g.floes()
+    g.set_floes(f)
+    f2 = g.floes()
+    for k in f:
+        assert np.array_equal(f[k], f2[k]), k
