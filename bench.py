@@ -190,6 +190,8 @@ def main():
     ap.add_argument("--config", type=int, default=2)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and autotune")
     ap.add_argument("--variant", type=int, default=-1, help="force the cell-kernel variant (profiling)")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="no timing: build the model, run N fine steps and exit (for ncu captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -215,6 +217,13 @@ def main():
     model = msdem.Model(p, s["floes"], msdem.MS_FP32)
     model.set_stream(stream.cuda_stream)
     n_floes, ncell = model.n, model.ncell
+    if args.profile:
+        if args.variant >= 0:
+            model.set_launch(args.variant, 128, 0)
+        model.step(dt, args.profile)
+        print(json.dumps({"profile_steps": args.profile, "info": model.info()}), flush=True)
+        model.close()
+        return
     if args.variant >= 0:
         model.set_launch(args.variant, 128, 0)
     elif not args.no_extras:
@@ -273,7 +282,7 @@ def main():
                      "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
                      "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso},
         "clocks": clk,
-        "gpu_launches": args.steps * (N0 + (info["launches_per_coarse"])),
+        "gpu_launches": args.steps * (N0 * info["launches_per_step"] + info["launches_per_coarse"]),
         "launch": {"variant": info["variant"], "threads": info["threads"], "persistent": info["persistent"]},
         "wall_s": t_wall,
     }

@@ -172,8 +172,13 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
  * the cell, 1 = binned pair search (FP32 only); threads per block 64, 128 or
  * 256; persistent = 1 runs a grid of resident blocks that take cells from a
  * work queue (largest cells first); bin_beta = bin side in units of the cell's
- * mean floe spacing (variant 1).  MS_ERR_ARG for an unsupported choice. */
-int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
+ * mean floe spacing (variants 1, 2); variant 2 = binned, one warp per cell of
+ * up to 256 floes and a block per larger cell, the two on concurrent streams;
+ * reg_min = in variant 2, register large floes in the bins they reach when
+ * (large floes x small floes) of a cell is at least this (0: keep current).
+ * MS_ERR_ARG for an unsupported choice. */
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta,
+                  int32_t reg_min);
 
 /* Mean device time (ms, CUDA events on the model's stream) of `reps`
  * out-of-place launches of the msDEM cell-step kernel (which = 0) or of the
@@ -185,7 +190,9 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
  * 4 kernel variant, 5 threads per block, 6 bin width (per mille of the mean
  * floe spacing), 7 kernels launched per fine step (msDEM, no coarse step),
  * 8 kernels per coarse step, 9 kernels per truth step, 10 steps done,
- * 11 truth steps done, 12 graph replays so far, 13-15 reserved. */
+ * 11 truth steps done, 12 graph replays so far, 13 contacts seen deeper than
+ * half the smaller radius, 14 persistent launch, 15 LF substeps of the last
+ * coarse step. */
 int ms_info(ms_model *m, int64_t *out);
 
 /* Release the model's device memory, graphs, events and stream. */

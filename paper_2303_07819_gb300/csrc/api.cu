@@ -67,7 +67,8 @@ struct ms_model {
     long long steps = 0, truth_steps = 0;
     double dt = 0.0, truth_dt = 0.0;
     int interval = 100;   // steps per coarse interval (graph length)
-    cudaStream_t stream = nullptr, own_stream = nullptr;
+    cudaStream_t stream = nullptr, own_stream = nullptr, side_stream[MAXSEG] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[MAXSEG] = {};
     CellLaunch cl{};
     cudaGraphExec_t gexec = nullptr;
     bool graph_failed = false;
@@ -272,9 +273,27 @@ static int upload_truth_state(ms_model *m, const ms_floes *f)
     return MS_OK;
 }
 
+static Geo32 geo32(double Lx, double Ly, int nx, int ny, double dt)
+{
+    Geo32 k;
+    k.sx = (float)(Lx / 4294967296.0);
+    k.sy = (float)(Ly / 4294967296.0);
+    k.isx = (float)(4294967296.0 / Lx);
+    k.isy = (float)(4294967296.0 / Ly);
+    k.inx = (float)(1.0 / nx);
+    k.iny = (float)(1.0 / ny);
+    k.Lx = (float)Lx;
+    k.Ly = (float)Ly;
+    k.iLx = (float)(1.0 / Lx);
+    k.iLy = (float)(1.0 / Ly);
+    k.dt = (float)dt;
+    return k;
+}
+
 static StepCommon step_common(ms_model *m, long long i_local, double *mom, double *win)
 {
     StepCommon sc;
+    sc.k = geo32(m->g.Lcx, m->g.Lcy, m->g.nx, m->g.ny, m->dt);
     sc.off = m->d_off;
     sc.order = m->d_order;
     sc.ncell = m->ncell;
@@ -387,6 +406,15 @@ static void fill_phys(ms_model *m)
         Q.mAv[k] = (float)(md[0] * kx);
         Q.mAz[k] = (float)(md[0] * (kx * kx + ky * ky));
         Q.mA[k] = (float)md[0];
+        Q.ta[k] = (float)(2.0 * PI_D * md[1] / m->grid.nx);
+        Q.tb[k] = (float)(2.0 * PI_D * md[2] / m->grid.ny);
+    }
+    // small-angle form of the per-floe phase: valid when no mode turns by more
+    // than 1/16 cycle across one cell
+    Q.taylor = 1;
+    for (int k = 0; k < f.n_modes; k++) {
+        const double *md = &m->modes[4 * k];
+        if (std::fabs(md[1]) / m->grid.nx + std::fabs(md[2]) / m->grid.ny > 1.0 / 16.0) Q.taylor = 0;
     }
     P.drag_o = f.Cd * f.rho_o * PI_D;
     P.drag_a = f.Ca * f.rho_a * PI_D;
@@ -407,31 +435,44 @@ static void fill_phys(ms_model *m)
 // launched with a block size and shared memory that fit its largest cell.
 static void make_segments(ms_model *m, CellLaunch &c)
 {
-    const int bounds[MAXSEG] = {1 << 30, 512, 256, 64};
-    const int threads[MAXSEG] = {256, 256, 128, 64};
+    // classes by floe count, largest first: (upper bound, threads, kind);
+    // variant 1 runs every class as block-per-cell, variant 2 runs cells of
+    // up to 256 floes warp-per-cell with the class bound as the warp capacity
+    struct Cls { int hi, threads, kind; };
+    const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
+    const Cls v2[5] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 1}, {128, 128, 1}, {64, 128, 1}};
+    const Cls *cls = c.variant == 2 ? v2 : v1;
+    const int ncls = c.variant == 2 ? 5 : 4;
     c.nseg = 0;
     c.nbmax = 32;
     int item = 0;
     const int nc = m->ncell;
     auto ncount = [&](int it) { const int cc = m->h_order[it]; return m->h_off[cc + 1] - m->h_off[cc]; };
-    for (int s = 0; s < MAXSEG && item < nc; s++) {
-        const int lo = (s + 1 < MAXSEG) ? bounds[s + 1] : -1;
+    for (int s = 0; s < ncls && item < nc; s++) {
+        const int lo = (s + 1 < ncls) ? cls[s + 1].hi : -1;
         int e = item;
         while (e < nc && ncount(e) > lo) e++;
         if (e == item) continue;
         c.seg_begin[c.nseg] = item;
         c.seg_end[c.nseg] = e;
-        c.seg_maxn[c.nseg] = std::max(1, ncount(item));
-        c.seg_threads[c.nseg] = threads[s];
+        c.seg_kind[c.nseg] = cls[s].kind;
+        c.seg_maxn[c.nseg] = cls[s].kind == 1 ? cls[s].hi : std::max(1, ncount(item));
+        c.seg_threads[c.nseg] = cls[s].threads;
         c.nseg++;
         item = e;
     }
+    for (int k = 0; k < MAXSEG; k++) {
+        c.side[k] = m->side_stream[k];
+        c.ev_join[k] = m->ev_join[k];
+    }
+    c.ev_fork = m->ev_fork;
 }
 
 static int configure_launch(ms_model *m, const CellLaunch &cl_in)
 {
     CellLaunch cl = cl_in;
-    if (cl.variant == 1) make_segments(m, cl);
+    if (cl.variant >= 1) make_segments(m, cl);
+    else cl.nseg = 0;
     const size_t smem = cell_step_smem(m->precision, cl, m->max_n, m->g.nx, m->g.ny);
     if (smem > 227 * 1024) return fail(MS_ERR_ARG, "cell of %d floes needs %zu B of shared memory", m->max_n, smem);
     CK(cell_step_prepare(m->precision, cl, smem));
@@ -485,6 +526,11 @@ void ms_free(ms_model *m)
     for (void *p : m->allocs) cudaFree(p);
     if (m->h_stage) cudaFreeHost(m->h_stage);
     if (m->own_stream) cudaStreamDestroy(m->own_stream);
+    for (int k = 0; k < MAXSEG; k++) {
+        if (m->side_stream[k]) cudaStreamDestroy(m->side_stream[k]);
+        if (m->ev_join[k]) cudaEventDestroy(m->ev_join[k]);
+    }
+    if (m->ev_fork) cudaEventDestroy(m->ev_fork);
     delete m;
 }
 
@@ -588,6 +634,11 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < MAXSEG; k++) {
+        CKM(cudaStreamCreateWithFlags(&m->side_stream[k], cudaStreamNonBlocking));
+        CKM(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
+    }
+    CKM(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
     m->stream = m->own_stream;
     const int nc = m->ncell;
     CKM(dalloc(m, &m->d_off, nc + 1));
@@ -628,12 +679,13 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
         return rc;
     }
     CellLaunch cl{};
-    cl.variant = m->precision == MS_FP32 ? 1 : 0;
+    cl.variant = m->precision == MS_FP32 ? 2 : 0;
     cl.threads = 128;
-    cl.bin_beta = 1.0f;
+    cl.bin_beta = 1.3f;
+    cl.reg_min = 1 << 30;
     cl.persistent = 0;
     cl.grid = m->sm_count * 4;
-    if (cl.variant == 1 && configure_launch(m, cl) != MS_OK) cl.variant = 0;   // cells too large to bin in shared memory
+    if (cl.variant >= 1 && configure_launch(m, cl) != MS_OK) cl.variant = 0;   // cells too large to bin in shared memory
     if ((rc = configure_launch(m, cl))) {
         ms_free(m);
         return rc;
@@ -823,6 +875,7 @@ static cudaError_t truth_one(ms_model *m, int cur, int nxt, long long step)
     TruthArgs a;
     a.n = m->n;
     a.g = m->g;
+    a.k = geo32(m->g.Lx, m->g.Ly, 1, 1, m->truth_dt);
     a.dt = m->truth_dt;
     a.step = step;
     a.ctrl = m->d_ctrl;
@@ -852,6 +905,7 @@ int ms_truth_moments(ms_model *m, double *out)
     TruthArgs a;
     a.n = m->n;
     a.g = m->g;
+    a.k = geo32(m->g.Lx, m->g.Ly, 1, 1, m->truth_dt > 0 ? m->truth_dt : 1.0);
     a.dt = m->truth_dt;
     a.step = m->truth_steps;
     a.ctrl = m->d_ctrl;
@@ -941,6 +995,15 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
             c.bin_beta = b;
             cand.push_back(c);
         }
+        const int regs[3] = {256, 1024, 1 << 30};
+        for (float b : betas)
+            for (int rm : regs) {
+                CellLaunch c = m->cl;
+                c.variant = 2;
+                c.bin_beta = b;
+                c.reg_min = rm;
+                cand.push_back(c);
+            }
     }
     const CellLaunch keep = m->cl;
     double best = 1e30;
@@ -960,10 +1023,12 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
     return MS_OK;
 }
 
-int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta)
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta,
+                  int32_t reg_min)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
-    if (variant != 0 && !(variant == 1 && m->precision == MS_FP32)) return fail(MS_ERR_ARG, "unsupported variant %d", variant);
+    if (variant != 0 && !((variant == 1 || variant == 2) && m->precision == MS_FP32))
+        return fail(MS_ERR_ARG, "unsupported variant %d", variant);
     if (threads != 64 && threads != 128 && threads != 256) return fail(MS_ERR_ARG, "threads must be 64, 128 or 256");
     if (!(bin_beta > 0.1 && bin_beta < 10.0)) return fail(MS_ERR_ARG, "bin_beta must be in (0.1, 10)");
     CellLaunch c = m->cl;
@@ -971,6 +1036,7 @@ int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persist
     c.threads = threads;
     c.persistent = persistent ? 1 : 0;
     c.bin_beta = (float)bin_beta;
+    if (reg_min > 0) c.reg_min = reg_min;
     c.grid = m->sm_count * std::min(2048 / threads, 8);
     CK(cudaStreamSynchronize(m->stream));
     return configure_launch(m, c);
@@ -989,7 +1055,7 @@ int ms_info(ms_model *m, int64_t *out)
     out[4] = m->cl.variant;
     out[5] = m->cl.threads;
     out[6] = (int64_t)std::lround(m->cl.bin_beta * 1000.0f);
-    out[7] = 1;
+    out[7] = (m->cl.variant >= 1) ? m->cl.nseg : 1;
     out[8] = m->fc.couple ? coarse_launches() : 1;
     out[9] = truth_launches(m->tb);
     out[10] = m->steps;

@@ -63,6 +63,41 @@ __device__ __forceinline__ RampCell ramp_cell(const StepCommon &sc, int c, int e
     return rc;
 }
 
+// Per-block copy of the step facts and the current cell's update, set by
+// thread 0 (its FP64 arithmetic runs once per block, not once per thread).
+struct BlockStep {
+    float ua, va;          // wind at the start of the step
+    int ramp, ev;
+    float g, du, dv, dw;   // current cell's gradual update
+};
+
+__device__ __forceinline__ void block_step_init(BlockStep &bs, const StepCommon &sc, const Phys<float> &P)
+{
+    if (threadIdx.x == 0) {
+        const StepInfo si = step_info(sc);
+        float ua, va;
+        wind_at(P, si.t, ua, va);
+        bs.ua = ua;
+        bs.va = va;
+        bs.ramp = si.ramp;
+        bs.ev = si.ev;
+        bs.g = 1.0f;
+        bs.du = bs.dv = bs.dw = 0.0f;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void block_cell_ramp(BlockStep &bs, const StepCommon &sc, int c)
+{
+    if (threadIdx.x == 0 && bs.ramp) {
+        const RampCell rc = ramp_cell(sc, c, bs.ev);
+        bs.g = (float)rc.g;
+        bs.du = (float)rc.du;
+        bs.dv = (float)rc.dv;
+        bs.dw = (float)rc.dw;
+    }
+}
+
 // Work item of this block: a fixed item per block, or a ticket from the
 // model's queue (persistent form).  The last block to leave resets the queue.
 __device__ __forceinline__ int next_item(const StepCommon &sc, int persistent, int *sh_item, bool first)
@@ -162,13 +197,10 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     float *base = reinterpret_cast<float *>(red + (T / 32) * NMOM);
     int *sh_item = reinterpret_cast<int *>(base + MAXM);
 
-    const StepInfo si = step_info(sc);
-    float ua, va;
-    wind_at(P, si.t, ua, va);
-    const float dt = (float)sc.dt;
-    const float sx = (float)(sc.g.Lcx / 4294967296.0), sy = (float)(sc.g.Lcy / 4294967296.0);
-    const float isx = (float)(4294967296.0 / sc.g.Lcx), isy = (float)(4294967296.0 / sc.g.Lcy);
-    const float inx = 1.0f / (float)sc.g.nx, iny = 1.0f / (float)sc.g.ny;
+    __shared__ BlockStep bs;
+    block_step_init(bs, sc, P);
+    const float dt = sc.k.dt;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
     unsigned deep = 0;
     bool bad = false;
 
@@ -189,8 +221,7 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             Qp[k] = make_uint2(in.xq[o + k], in.yq[o + k]);
             W[k] = in.w[o + k];
         }
-        RampCell rc = {1.0, 0.0, 0.0, 0.0};
-        if (si.ramp) rc = ramp_cell(sc, c, si.ev);
+        block_cell_ramp(bs, sc, c);
         __syncthreads();
 
         float acc[NMOM];
@@ -220,7 +251,7 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             float uo, vo, zeta;
             ocean_f32(P, base, inx, iny, xf, yf, uo, vo, zeta);
             float Fdx, Fdy, Td;
-            drag_force(P, uo, vo, zeta, ua, va, al.z, al.w, wl, al.x, Fdx, Fdy, Td);
+            drag_force(P, uo, vo, zeta, bs.ua, bs.va, al.z, al.w, wl, al.x, Fdx, Fdy, Td);
             fx += Fdx; fy += Fdy; tq += Td;
             // forward Euler with every right-hand side at t_n
             const float r = al.x, h = al.y;
@@ -233,11 +264,11 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             float vn = al.w + dt * (fy / m);
             float wn = wl + dt * (tq / I);
             float rn = r;
-            if (si.ramp) {
-                rn = (float)((double)r * rc.g);
-                un += (float)rc.du;
-                vn += (float)rc.dv;
-                wn += (float)rc.dw;
+            if (bs.ramp) {
+                rn = r * bs.g;
+                un += bs.du;
+                vn += bs.dv;
+                wn += bs.dw;
             }
             bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
             out.xq[o + l] = xn;
@@ -246,7 +277,7 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             out.u[o + l] = un;
             out.v[o + l] = vn;
             out.w[o + l] = wn;
-            if (si.ramp || out.r != in.r) out.r[o + l] = rn;
+            if (bs.ramp || out.r != in.r) out.r[o + l] = rn;
             add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
         }
         reduce_write<float, T>(acc, red, sc, c, n);
@@ -317,6 +348,8 @@ __device__ __forceinline__ float min_image(float d, float L, float iL)
     return fmaf(-k, L, d);
 }
 
+constexpr int MAXC_B = 16;   // contacts a thread collects before computing their forces
+
 struct Bin32 {
     float4 *P4;     // x, y (m, cell-local float), r, h          [index order]
     float4 *V4;     // u, v, w                                   [index order]
@@ -327,6 +360,7 @@ struct Bin32 {
     int *bst;       // [nb^2 + 1] bin starts
     short *sidx;    // search position -> floe index
     short *bin;     // floe index -> bin (-1: large)
+    short *clist;   // [MAXC_B][T] contact candidates per thread
     int *tmp;       // scan scratch
     double *red;
     float *base;
@@ -352,6 +386,7 @@ __device__ __forceinline__ Bin32 carve32(unsigned char *smem, int maxn, int nbma
     b.misc = reinterpret_cast<int *>(smem + o); o += align16(sizeof(int) * 8);
     b.sidx = reinterpret_cast<short *>(smem + o); o += align16(sizeof(short) * maxn);
     b.bin = reinterpret_cast<short *>(smem + o); o += align16(sizeof(short) * maxn);
+    b.clist = reinterpret_cast<short *>(smem + o); o += align16(sizeof(short) * MAXC_B * T);
     return b;
 }
 
@@ -361,7 +396,7 @@ __host__ __device__ inline size_t smem32_binned(int T, int maxn, int nbmax)
     const int nbins = nbmax * nbmax + 1;
     return 4 * a16(sizeof(float4) * maxn) + a16(sizeof(uint2) * maxn) + a16(sizeof(double) * (T / 32) * NMOM) +
            2 * a16(sizeof(int) * nbins) + a16(sizeof(int) * (T / 32 + 1)) + a16(sizeof(float) * MAXM) +
-           a16(sizeof(int) * 8) + 2 * a16(sizeof(short) * maxn);
+           a16(sizeof(int) * 8) + 2 * a16(sizeof(short) * maxn) + a16(sizeof(short) * MAXC_B * T);
 }
 
 template <int T>
@@ -372,15 +407,11 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
     extern __shared__ __align__(16) unsigned char smem[];
     const Bin32 sm = carve32<T>(smem, maxn, nbmax);
 
-    const StepInfo si = step_info(sc);
-    float ua, va;
-    wind_at(P, si.t, ua, va);
-    const float dt = (float)sc.dt;
-    const float Lx = (float)sc.g.Lcx, Ly = (float)sc.g.Lcy;
-    const float iLx = 1.0f / Lx, iLy = 1.0f / Ly;
-    const float sx = (float)(sc.g.Lcx / 4294967296.0), sy = (float)(sc.g.Lcy / 4294967296.0);
-    const float isx = (float)(4294967296.0 / sc.g.Lcx), isy = (float)(4294967296.0 / sc.g.Lcy);
-    const float inx = 1.0f / (float)sc.g.nx, iny = 1.0f / (float)sc.g.ny;
+    __shared__ BlockStep bs;
+    block_step_init(bs, sc, P);
+    const float dt = sc.k.dt;
+    const float Lx = sc.k.Lx, Ly = sc.k.Ly, iLx = sc.k.iLx, iLy = sc.k.iLy;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
     unsigned deep = 0;
     bool bad = false;
 
@@ -477,6 +508,18 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                             vj.z, P, fx, fy, tq, deep);
             };
+            // collect candidates, then compute their forces with the threads in step
+            int ncand = 0;
+            short *cl = sm.clist + threadIdx.x;
+            auto flush = [&]() {
+                for (int i = 0; i < ncand; i++) touch(cl[T * i]);
+                ncand = 0;
+            };
+            auto hit = [&](int k) {
+                if (ncand == MAXC_B) flush();
+                cl[T * ncand] = (short)k;
+                ncand++;
+            };
             // small partners through the bins
             int bx0, bx1, by0, by1;
             if (p < nsmall) {
@@ -508,7 +551,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                         if (wrapx) dx = min_image(dx, Lx, iLx);
                         if (wrapy) dy = min_image(dy, Ly, iLy);
                         const float S = pl.z + q.z;
-                        if (k != p && dx * dx + dy * dy < S * S) touch(k);
+                        if (k != p && dx * dx + dy * dy < S * S) hit(k);
                     }
                 }
             }
@@ -518,12 +561,12 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 const float dx = min_image(q.x - pl.x, Lx, iLx);
                 const float dy = min_image(q.y - pl.y, Ly, iLy);
                 const float S = pl.z + q.z;
-                if (k != p && dx * dx + dy * dy < S * S) touch(k);
+                if (k != p && dx * dx + dy * dy < S * S) hit(k);
             }
+            flush();
             sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
         }
-        RampCell rc = {1.0, 0.0, 0.0, 0.0};
-        if (si.ramp) rc = ramp_cell(sc, c, si.ev);
+        block_cell_ramp(bs, sc, c);
         __syncthreads();
 
         // ---- drag, forward Euler, gradual update, moments (index order: coalesced I/O)
@@ -540,7 +583,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             float uo, vo, zeta;
             ocean_f32(P, sm.base, inx, iny, xf, yf, uo, vo, zeta);
             float Fdx, Fdy, Td;
-            drag_force(P, uo, vo, zeta, ua, va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+            drag_force(P, uo, vo, zeta, bs.ua, bs.va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
             fx += Fdx; fy += Fdy; tq += Td;
             const float r = pl.z, h = pl.w;
             const float m = P.mass_c * r * r * h;
@@ -552,11 +595,11 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             float vn = vl.y + dt * (fy / m);
             float wn = vl.z + dt * (tq / I);
             float rn = r;
-            if (si.ramp) {
-                rn = (float)((double)r * rc.g);
-                un += (float)rc.du;
-                vn += (float)rc.dv;
-                wn += (float)rc.dw;
+            if (bs.ramp) {
+                rn = r * bs.g;
+                un += bs.du;
+                vn += bs.dv;
+                wn += bs.dw;
             }
             bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
             out.xq[o + l] = xn;
@@ -565,13 +608,380 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             out.u[o + l] = un;
             out.v[o + l] = vn;
             out.w[o + l] = wn;
-            if (si.ramp || out.r != in.r) out.r[o + l] = rn;
+            if (bs.ramp || out.r != in.r) out.r[o + l] = rn;
             add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
         }
         reduce_write<float, T>(acc, sm.red, sc, c, n);
         __syncthreads();
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
+}
+
+// =============================================================== FP32 warp
+// One warp owns one cell (cells of up to 256 floes): no block barriers, a
+// lane per floe.  The cell is stored in shared memory in search order (small
+// floes by bin, ascending floe index within a bin; then large floes in index
+// order).  The rank of a floe inside its bin comes from __match_any_sync, so
+// placement needs neither atomics nor a sort and the order is deterministic.
+// The same lane finds a floe's contacts and advances it, so the force stays
+// in registers; the floe is written back to its own global slot.
+
+constexpr int MAXC = 24;   // contacts a lane collects before computing their forces
+
+__host__ __device__ inline size_t warp_region_bytes(int cap, int nbmax)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    return 2 * a16(sizeof(float4) * cap) + a16(sizeof(uint2) * cap) + a16(sizeof(short) * cap) +
+           a16(sizeof(short) * MAXC * 32) + 2 * a16(sizeof(int) * (nbmax * nbmax + 1)) + a16(sizeof(float2) * MAXM);
+}
+
+struct WarpSm {
+    float4 *S4;    // x, y (m, float), r, h
+    float4 *SV;    // u, v, w, theta
+    uint2 *SQ;     // exact fixed-point position
+    short *orig;   // floe index within the cell
+    int *cnt, *bst;
+    short *clist;       // [MAXC][32] contact candidates per lane
+    float2 *Cm;    // per mode: (cos, sin) of the cell's phase, or (phase, -) without the small-angle form
+};
+
+__device__ __forceinline__ WarpSm carve_warp(unsigned char *p, int cap, int nbmax)
+{
+    WarpSm w;
+    size_t o = 0;
+    w.S4 = reinterpret_cast<float4 *>(p + o); o += align16(sizeof(float4) * cap);
+    w.SV = reinterpret_cast<float4 *>(p + o); o += align16(sizeof(float4) * cap);
+    w.SQ = reinterpret_cast<uint2 *>(p + o); o += align16(sizeof(uint2) * cap);
+    w.orig = reinterpret_cast<short *>(p + o); o += align16(sizeof(short) * cap);
+    w.clist = reinterpret_cast<short *>(p + o); o += align16(sizeof(short) * MAXC * 32);
+    w.cnt = reinterpret_cast<int *>(p + o); o += align16(sizeof(int) * (nbmax * nbmax + 1));
+    w.bst = reinterpret_cast<int *>(p + o); o += align16(sizeof(int) * (nbmax * nbmax + 1));
+    w.Cm = reinterpret_cast<float2 *>(p + o);
+    return w;
+}
+
+// e^{i th} for |th| <= 0.4 by its Taylor series to th^9 (error < 1e-10)
+__device__ __forceinline__ void rot_small(float th, float &c, float &s)
+{
+    const float t = th * th;
+    c = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+    s = th * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+}
+
+// exclusive scan of in[0..count) into out by one warp; returns the total
+__device__ __forceinline__ int warp_scan_excl(const int *in, int *out, int count, int lane)
+{
+    const int per = (count + 31) >> 5;
+    const int b = lane * per, e = min(b + per, count);
+    int s = 0;
+    for (int i = b; i < e; i++) s += in[i];
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    int run = x - s;
+    for (int i = b; i < e; i++) {
+        const int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    __syncwarp();
+    return total;
+}
+
+// Warp sum of 16 values by halving exchanges (16 shuffles in all): lanes 2k
+// and 2k+1 end with the total of value k.
+__device__ __forceinline__ float warp_sum16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int half = 8 >> r;          // values kept after this round
+        const int off = 16 >> r;          // lane distance
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 8)
+k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
+                   int item1, int cap, int nbmax)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockStep bs;
+    block_step_init(bs, sc, P);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = item0 + blockIdx.x * WARPS + warp;
+    if (item >= item1) return;
+    const WarpSm sm = carve_warp(smem + warp * warp_region_bytes(cap, nbmax), cap, nbmax);
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+
+    const float dt = sc.k.dt;
+    const float Lx = sc.k.Lx, Ly = sc.k.Ly, iLx = sc.k.iLx, iLy = sc.k.iLy;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
+    const int c = sc.order[item];
+    const int o = sc.off[c], n = sc.off[c + 1] - o;
+    const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+
+    float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
+    if (bs.ramp) {
+        if (lane == 0) {
+            const RampCell rc = ramp_cell(sc, c, bs.ev);
+            rg = (float)rc.g; rdu = (float)rc.du; rdv = (float)rc.dv; rdw = (float)rc.dw;
+        }
+        rg = __shfl_sync(FULL, rg, 0); rdu = __shfl_sync(FULL, rdu, 0);
+        rdv = __shfl_sync(FULL, rdv, 0); rdw = __shfl_sync(FULL, rdw, 0);
+    }
+    if (lane < P.n_modes) {
+        const int m = lane;
+        int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
+        int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
+        float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
+        b -= floorf(b);
+        float sn, cs;
+        if (P.taylor) {
+            sincospif(2.0f * b, &sn, &cs);
+            sm.Cm[m] = make_float2(cs, sn);
+        } else {
+            sm.Cm[m] = make_float2(b, 0.0f);
+        }
+    }
+
+    int nb = (int)(sqrtf((float)n) / beta);
+    nb = nb > nbmax ? nbmax : nb;
+    if (nb < 3) nb = 0;
+    const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
+    const float Rs = nb ? 0.5f * fminf(Bx, By) : -1.0f;
+    const int nbins = nb * nb;
+    for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+    __syncwarp();
+
+    // ---- count small floes per bin
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < n;
+        const uint32_t xq = valid ? in.xq[o + k] : 0u, yq = valid ? in.yq[o + k] : 0u;
+        const float r = valid ? in.r[o + k] : 0.0f;
+        const bool small = valid && r <= Rs;
+        const int b = small ? (int)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb)) : -1 - lane;
+        const unsigned m = __match_any_sync(FULL, b);
+        if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+        __syncwarp();
+    }
+    const int nsmall = warp_scan_excl(sm.cnt, sm.bst, nbins + 1, lane);
+    for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+    __syncwarp();
+    // ---- place every floe at its search position
+    int lrun = nsmall;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < n;
+        uint32_t xq = 0u, yq = 0u;
+        float r = 0.0f, h = 0.0f, u = 0.0f, v = 0.0f, w = 0.0f, th = 0.0f;
+        if (valid) {
+            xq = in.xq[o + k]; yq = in.yq[o + k];
+            r = in.r[o + k]; h = in.h[o + k];
+            u = in.u[o + k]; v = in.v[o + k]; w = in.w[o + k]; th = in.th[o + k];
+        }
+        const bool small = valid && r <= Rs;
+        const bool large = valid && !small;
+        const int b = small ? (int)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb)) : -1 - lane;
+        const unsigned m = __match_any_sync(FULL, b);
+        const unsigned bl = __ballot_sync(FULL, large);
+        int pos = 0;
+        if (small) pos = sm.bst[b] + sm.cnt[b] + __popc(m & lt);
+        else if (large) pos = lrun + __popc(bl & lt);
+        if (valid) {
+            sm.S4[pos] = make_float4((float)xq * sx, (float)yq * sy, r, h);
+            sm.SV[pos] = make_float4(u, v, w, 0.0f);
+            sm.SQ[pos] = make_uint2(xq, yq);
+            sm.orig[pos] = (short)k;
+            // forward Euler for position and angle needs only this floe's old
+            // state: write them now (the cell's old positions live in SQ)
+            out.xq[o + k] = xq + (uint32_t)__float2int_rn(dt * u * isx);
+            out.yq[o + k] = yq + (uint32_t)__float2int_rn(dt * v * isy);
+            out.th[o + k] = th + dt * w;
+        }
+        __syncwarp();
+        if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+        lrun += __popc(bl);
+        __syncwarp();
+    }
+
+    float acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = 0.0f;
+    unsigned deep = 0;
+    bool bad = false;
+    for (int p = lane; p < n; p += 32) {
+        const float4 pl = sm.S4[p];
+        const float4 vl = sm.SV[p];
+        const uint2 ql = sm.SQ[p];
+        float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+        auto touch = [&](int k) {
+            const uint2 qj = sm.SQ[k];
+            const float dx = (float)(int)(qj.x - ql.x) * sx;
+            const float dy = (float)(int)(qj.y - ql.y) * sy;
+            const float4 pj = sm.S4[k];
+            const float4 vj = sm.SV[k];
+            contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z, vj.z,
+                        P, fx, fy, tq, deep);
+        };
+        // the search only collects candidates; their forces are computed
+        // afterwards, so the lanes of the warp do the costly part in step
+        int nc = 0;
+        short *cl = sm.clist + lane;
+        auto flush = [&]() {
+            for (int i = 0; i < nc; i++) touch(cl[32 * i]);
+            nc = 0;
+        };
+        auto hit = [&](int k) {
+            if (nc == MAXC) flush();
+            cl[32 * nc] = (short)k;
+            nc++;
+        };
+        auto scan = [&](int k0, int k1, float xs, float ys, bool mix, bool miy) {
+            for (int k = k0; k < k1; k++) {
+                const float4 q = sm.S4[k];
+                float dx = q.x - xs, dy = q.y - ys;
+                if (mix) dx = min_image(dx, Lx, iLx);
+                if (miy) dy = min_image(dy, Ly, iLy);
+                const float S = pl.z + q.z;
+                if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+            }
+        };
+        const bool small = p < nsmall;
+        if (small) {
+            // 3 x 3 bins: per row at most two contiguous runs of bins (one
+            // with the periodic shift), walked as one loop
+            const int bx = (int)__umulhi(ql.x, (unsigned)nb), by = (int)__umulhi(ql.y, (unsigned)nb);
+            int a0 = bx - 1, a1 = bx + 1, c0 = 1, c1 = 0;
+            float xc = pl.x;
+            if (bx == 0) { a0 = 0; a1 = 1; c0 = nb - 1; c1 = nb - 1; xc = pl.x + Lx; }
+            else if (bx == nb - 1) { a0 = nb - 2; a1 = nb - 1; c0 = 0; c1 = 0; xc = pl.x - Lx; }
+#pragma unroll
+            for (int dyb = -1; dyb <= 1; dyb++) {
+                int wy = by + dyb;
+                float ys = pl.y;
+                if (wy < 0) { wy += nb; ys += Ly; } else if (wy >= nb) { wy -= nb; ys -= Ly; }
+                const int row = wy * nb;
+                const int kA = sm.bst[row + a0], nA = sm.bst[row + a1 + 1] - kA;
+                const int kC = sm.bst[row + c0], nC = c1 >= c0 ? sm.bst[row + c1 + 1] - kC : 0;
+                for (int i = 0; i < nA + nC; i++) {
+                    const bool inA = i < nA;
+                    const int k = inA ? kA + i : kC + (i - nA);
+                    const float4 q = sm.S4[k];
+                    const float dx = q.x - (inA ? pl.x : xc), dy = q.y - ys;
+                    const float S = pl.z + q.z;
+                    if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+                }
+            }
+        } else if (nb) {
+            // a large floe: the small floes' bins within its reach
+            const float reach = 1.001f * (pl.z + Rs);
+            int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
+            int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+            const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
+            if (allx) { bx0 = 0; bx1 = nb - 1; }
+            if (ally) { by0 = 0; by1 = nb - 1; }
+            for (int by = by0; by <= by1; by++) {
+                const int wy = by < 0 ? by + nb : (by >= nb ? by - nb : by);
+                const float ys = ally ? pl.y : (by < 0 ? pl.y + Ly : (by >= nb ? pl.y - Ly : pl.y));
+                const int row = wy * nb;
+                if (allx) {
+                    scan(sm.bst[row], sm.bst[row + nb], pl.x, ys, true, ally);
+                } else {
+                    if (bx0 < 0) scan(sm.bst[row + bx0 + nb], sm.bst[row + nb], pl.x + Lx, ys, false, ally);
+                    const int a0 = bx0 < 0 ? 0 : bx0, a1 = bx1 > nb - 1 ? nb - 1 : bx1;
+                    scan(sm.bst[row + a0], sm.bst[row + a1 + 1], pl.x, ys, false, ally);
+                    if (bx1 >= nb) scan(sm.bst[row], sm.bst[row + bx1 - nb + 1], pl.x - Lx, ys, false, ally);
+                }
+            }
+        }
+        scan(nsmall, n, pl.x, pl.y, true, true);
+        flush();
+
+        // ---- drag, forward Euler, gradual update, moments
+        const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
+        float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
+        if (P.taylor) {
+            for (int m = 0; m < P.n_modes; m++) {
+                float c0, s0;
+                rot_small(fmaf(P.ta[m], xf, P.tb[m] * yf), c0, s0);
+                const float2 C = sm.Cm[m];
+                const float cs = C.x * c0 - C.y * s0, sn = C.y * c0 + C.x * s0;
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        } else {
+            for (int m = 0; m < P.n_modes; m++) {
+                const float cyc = sm.Cm[m].x + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+                float sn, cs;
+                sincospif(2.0f * cyc, &sn, &cs);
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        }
+        float Fdx, Fdy, Td;
+        drag_force(P, uo, vo, zeta, bs.ua, bs.va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+        fx += Fdx; fy += Fdy; tq += Td;
+        const float r = pl.z, h = pl.w;
+        const float mass = P.mass_c * r * r * h;
+        const float I = P.inertia_f * mass * r * r;
+        float un = vl.x + dt * (fx / mass);
+        float vn = vl.y + dt * (fy / mass);
+        float wn = vl.z + dt * (tq / I);
+        float rn = r;
+        if (bs.ramp) {
+            rn = r * rg;
+            un += rdu;
+            vn += rdv;
+            wn += rdw;
+        }
+        bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+        const int gi = o + sm.orig[p];
+        out.u[gi] = un;
+        out.v[gi] = vn;
+        out.w[gi] = wn;
+        if (bs.ramp || out.r != in.r) out.r[gi] = rn;
+        float a12[NMOM];
+#pragma unroll
+        for (int k = 0; k < NMOM; k++) a12[k] = 0.0f;
+        add_moments(a12, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+#pragma unroll
+        for (int k = 1; k < NMOM; k++) acc[k] += a12[k];
+    }
+    // ---- moments: lane 2k holds the warp total of column k
+    const float tot = warp_sum16(acc, lane);
+    const double dtot = (double)tot;
+    const double M = __shfl_sync(FULL, dtot, 2), Mu = __shfl_sync(FULL, dtot, 4), Mv = __shfl_sync(FULL, dtot, 6);
+    const double Fx = __shfl_sync(FULL, dtot, 18), Fy = __shfl_sync(FULL, dtot, 20), Tz = __shfl_sync(FULL, dtot, 22);
+    double *mo = sc.mom + (size_t)c * NMOM;
+    if ((lane & 1) == 0 && lane < 2 * NMOM) mo[lane >> 1] = lane == 0 ? (double)n : dtot;
+    if (lane == 0 && sc.couple) {
+        const int nc = sc.ncell;
+        if (M > 0.0) {
+            sc.win[c] += Mu / M;
+            sc.win[nc + c] += Mv / M;
+        }
+        sc.win[2 * nc + c] += Fx;
+        sc.win[3 * nc + c] += Fy;
+        sc.win[4 * nc + c] += Tz;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
     if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
 }
 
@@ -693,21 +1103,57 @@ k_cell_moments(const R *u, const R *v, const R *w, const R *r, const R *h, R mas
 
 }  // namespace
 
+#define MS_T_SWITCH(T, ...)                                       \
+    switch (T) {                                                  \
+    case 64: { constexpr int TT = 64; __VA_ARGS__; } break;       \
+    case 128: { constexpr int TT = 128; __VA_ARGS__; } break;     \
+    case 256: { constexpr int TT = 256; __VA_ARGS__; } break;     \
+    default: return cudaErrorInvalidValue;                        \
+    }
+
+// The shared-memory limit is an attribute of each kernel instance, shared by
+// every model in the process: set it once to the device's opt-in maximum
+// (a limit, not a reservation) instead of to one launch's need.
 // bins per side that a segment can need: nb = sqrt(n) / beta, capped
 int seg_nbmax(const CellLaunch &cl, int s)
 {
     int nb = (int)(std::sqrt((float)cl.seg_maxn[s]) / cl.bin_beta);
-    nb = nb > cl.nbmax ? cl.nbmax : nb;
+    const int cap = cl.seg_kind[s] == 1 ? 16 : cl.nbmax;
+    nb = nb > cap ? cap : nb;
     return nb < 3 ? 3 : nb;
+}
+
+static size_t seg_smem(const CellLaunch &cl, int s)
+{
+    if (cl.seg_kind[s] == 1) return 4 * warp_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
+    return smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
+}
+
+static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                                const StepCommon &sc, const CellLaunch &cl, int s, cudaStream_t st)
+{
+    const int items = cl.seg_end[s] - cl.seg_begin[s];
+    if (items <= 0) return cudaSuccess;
+    const int nbm = seg_nbmax(cl, s);
+    const size_t sm = seg_smem(cl, s);
+    if (cl.seg_kind[s] == 1) {
+        k_cell_step32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
+                                                                cl.seg_end[s], cl.seg_maxn[s], nbm);
+        return cudaGetLastError();
+    }
+    MS_T_SWITCH(cl.seg_threads[s],
+                k_cell_step32_binned<TT><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
+                                                                cl.seg_end[s], cl.seg_maxn[s], nbm));
+    return cudaGetLastError();
 }
 
 size_t cell_step_smem(int precision, const CellLaunch &cl, int max_n, int, int)
 {
     const int T = cl.threads;
-    if (precision == 0 && cl.variant == 1) {
+    if (precision == 0 && cl.variant >= 1) {
         size_t mx = 0;
         for (int s = 0; s < cl.nseg; s++) {
-            const size_t sm = smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
+            const size_t sm = seg_smem(cl, s);
             mx = sm > mx ? sm : mx;
         }
         return mx;
@@ -720,21 +1166,11 @@ size_t cell_step_smem(int precision, const CellLaunch &cl, int max_n, int, int)
            sizeof(double) * (T / 32) * NMOM + sizeof(float) * MAXM + 16;
 }
 
-#define MS_T_SWITCH(T, ...)                                       \
-    switch (T) {                                                  \
-    case 64: { constexpr int TT = 64; __VA_ARGS__; } break;       \
-    case 128: { constexpr int TT = 128; __VA_ARGS__; } break;     \
-    case 256: { constexpr int TT = 256; __VA_ARGS__; } break;     \
-    default: return cudaErrorInvalidValue;                        \
-    }
-
-// The shared-memory limit is an attribute of each kernel instance, shared by
-// every model in the process: set it once to the device's opt-in maximum
-// (a limit, not a reservation) instead of to one launch's need.
 cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
 {
     static int done = 0;
     static int optin = 0;
+    static int limit = 0;
     if (!done) {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -745,14 +1181,20 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step32_brute<256>, (const void *)k_cell_step64_brute<64>,
             (const void *)k_cell_step64_brute<128>, (const void *)k_cell_step64_brute<256>,
             (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
-            (const void *)k_cell_step32_binned<256>};
+            (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>};
+        limit = optin;
         for (const void *k : kern) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncAttributes fa;
+            e = cudaFuncGetAttributes(&fa, k);
             if (e != cudaSuccess) return e;
+            const int dyn = optin - (int)fa.sharedSizeBytes;
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+            if (e != cudaSuccess) return e;
+            limit = dyn < limit ? dyn : limit;
         }
         done = 1;
     }
-    return smem <= (size_t)optin ? cudaSuccess : cudaErrorInvalidValue;
+    return smem <= (size_t)limit ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
@@ -760,15 +1202,22 @@ cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, cons
 {
     if (cl.variant == 1) {
         for (int s = 0; s < cl.nseg; s++) {
-            const int items = cl.seg_end[s] - cl.seg_begin[s];
-            if (items <= 0) continue;
-            const int nbm = seg_nbmax(cl, s);
-            const size_t sm = smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], nbm);
-            MS_T_SWITCH(cl.seg_threads[s],
-                        k_cell_step32_binned<TT><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
-                                                                        cl.seg_end[s], cl.seg_maxn[s], nbm));
+            cudaError_t e = launch_seg32(in, out, P, sc, cl, s, st);
+            if (e != cudaSuccess) return e;
         }
-        return cudaGetLastError();
+        return cudaSuccess;
+    }
+    if (cl.variant == 2) {
+        // every size class on its own stream: the classes hold disjoint cells,
+        // so their kernels overlap and their tails hide each other
+        cudaError_t e = cudaEventRecord(cl.ev_fork, st);
+        for (int s = 0; s < cl.nseg && e == cudaSuccess; s++) {
+            if ((e = cudaStreamWaitEvent(cl.side[s], cl.ev_fork, 0)) != cudaSuccess) break;
+            if ((e = launch_seg32(in, out, P, sc, cl, s, cl.side[s])) != cudaSuccess) break;
+            if ((e = cudaEventRecord(cl.ev_join[s], cl.side[s])) != cudaSuccess) break;
+            e = cudaStreamWaitEvent(st, cl.ev_join[s], 0);
+        }
+        return e;
     }
     const size_t smem = cell_step_smem(0, cl, sc.max_n, sc.g.nx, sc.g.ny);
     const int grid = cl.persistent ? cl.grid : sc.ncell;

@@ -47,7 +47,8 @@ struct Phys {
     int mkx[MAXM], mky[MAXM];                      // FP32: integer wave numbers
     R mCyc[MAXM];                                  // FP32: phi / 2 pi
     R mAu[MAXM], mAv[MAXM], mAz[MAXM];             // FP32: A ky', A kx', A |k'|^2
-    int kmax_x, kmax_y;                            // FP32: largest |kx|, |ky| (harmonic tables)
+    int taylor;                                    // FP32: 1 if every mode turns by <= 1/16 cycle across a cell
+    R ta[MAXM], tb[MAXM];                          // FP32: 2 pi kx / nx, 2 pi ky / ny (radians per cell)
     R drag_o;      // Cd rho_o pi
     R drag_a;      // Ca rho_a pi
     R wind_x, wind_y, wind_w;   // wind at t = 0 and its turning rate 2 pi / period
@@ -65,7 +66,10 @@ struct Geom {
 template <class R> __device__ __forceinline__ R dmin(R a, R b) { return a < b ? a : b; }
 template <class R> __device__ __forceinline__ R dmax(R a, R b) { return a > b ? a : b; }
 
-__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+// 1/sqrt(x): the hardware reciprocal square root in FP32, the IEEE
+// operations in FP64 (the parity path)
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
 
 // Contact of floe l with floe j given the minimum-image separation
 // (dx, dy) = x_j - x_l.  Eq. (2.2): n from l to j, delta = d - (r_l + r_j) < 0
@@ -84,12 +88,13 @@ __device__ __forceinline__ bool contact_add(R dx, R dy, R d2, R rl, R rj, R hl, 
 {
     const R S = rl + rj;
     if (!(d2 > R(0) && d2 < S * S)) return false;
-    const R d = sqrt(d2);
-    const R nx = dx / d, ny = dy / d;
+    const R id = inv_sqrt(d2);
+    const R d = d2 * id;
+    const R nx = dx * id, ny = dy * id;
     const R delta = d - S;
     const R D = rl - rj;
     const R Q = (d - D) * (d + D);
-    const R c = (Q <= R(0)) ? R(2) * dmin(rl, rj) : sqrt((-delta) * (S + d) * Q) / d;
+    const R c = (Q <= R(0)) ? R(2) * dmin(rl, rj) : sqrt((-delta) * (S + d) * Q) * id;
     const R hc = dmin(hl, hj) * P.inv_h_ref;
     const R vn = dux * nx + duy * ny;
     R Fn = c * hc * (P.E * delta + P.eta * vn);
@@ -186,10 +191,10 @@ struct DevState64 {
     double *x, *y, *th, *u, *v, *w, *r, *h;
 };
 
-constexpr int MAXSEG = 4;   // size classes of cells launched separately (binned variant)
+constexpr int MAXSEG = 6;   // size classes of cells launched separately (binned variants)
 
 struct CellLaunch {
-    int variant;       // 0 brute force, 1 binned (FP32 only)
+    int variant;       // 0 brute force, 1 binned block per cell, 2 binned warp per cell (FP32 only)
     int threads;       // threads per block (brute force)
     float bin_beta;    // bin side in units of the mean floe spacing (binned variant)
     int persistent;    // 1: grid of resident blocks + work queue (brute force)
@@ -198,10 +203,28 @@ struct CellLaunch {
     // launched with its own block size and shared memory
     int nseg;
     int seg_begin[MAXSEG], seg_end[MAXSEG], seg_maxn[MAXSEG], seg_threads[MAXSEG];
+    int seg_kind[MAXSEG];   // 0: block per cell, 1: warp per cell (seg_maxn = the warp's capacity)
     int nbmax;         // bins per side at most
+    int reg_min;       // register large floes in bins when (large x small floes) >= this
+    // segments of variant 2 run on their own streams, forked from and joined
+    // back into the launching stream (concurrent branches in a graph)
+    cudaStream_t side[MAXSEG];
+    cudaEvent_t ev_fork, ev_join[MAXSEG];
+};
+
+// FP32 constants of a launch, computed once on the host (FP64 arithmetic on
+// the device runs at a small fraction of the FP32 rate).
+struct Geo32 {
+    float sx, sy;       // cell side / 2^32 (fixed point -> m)
+    float isx, isy;     // 2^32 / cell side
+    float inx, iny;     // 1 / nx, 1 / ny
+    float Lx, Ly;       // cell sides (m)
+    float iLx, iLy;
+    float dt;
 };
 
 struct StepCommon {
+    Geo32 k;
     const int *off;     // [ncell + 1]
     const int *order;   // [ncell] processing order (largest cells first)
     int ncell;
@@ -260,6 +283,7 @@ struct TruthBins {
 struct TruthArgs {
     long long n;
     Geom g;
+    Geo32 k;               // domain-sized constants (fixed point of the domain)
     double dt;
     long long step;        // steps done before this one
     Ctrl *ctrl;            // error bits and deep-overlap counter

@@ -147,10 +147,17 @@ __device__ __forceinline__ NbRange nb_range(int nbx, int nby)
 __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArgs a, const int *bin,
                           const int *start, const int *sorted, int nbx, int nby)
 {
+    __shared__ float wind[2];
+    if (threadIdx.x == 0) {
+        float ua, va;
+        wind_at(P, (double)a.step * a.dt, ua, va);
+        wind[0] = ua;
+        wind[1] = va;
+    }
+    __syncthreads();
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= a.n) return;
-    const float sx = (float)(a.g.Lx / 4294967296.0), sy = (float)(a.g.Ly / 4294967296.0);
-    const float isx = (float)(4294967296.0 / a.g.Lx), isy = (float)(4294967296.0 / a.g.Ly);
+    const float sx = a.k.sx, sy = a.k.sy, isx = a.k.isx, isy = a.k.isy;
     const uint32_t xl = in.xq[l], yl = in.yq[l];
     const float ul = in.u[l], vl = in.v[l], wl = in.w[l], rl = in.r[l], hl = in.h[l];
     const int b = bin[l];
@@ -188,12 +195,10 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
         vo += P.mAv[m] * c;
         zeta -= P.mAz[m] * s;
     }
-    float ua, va;
-    wind_at(P, (double)a.step * a.dt, ua, va);
     float Fdx, Fdy, Td;
-    drag_force(P, uo, vo, zeta, ua, va, ul, vl, wl, rl, Fdx, Fdy, Td);
+    drag_force(P, uo, vo, zeta, wind[0], wind[1], ul, vl, wl, rl, Fdx, Fdy, Td);
     fx += Fdx; fy += Fdy; tq += Td;
-    const float dt = (float)a.dt;
+    const float dt = a.k.dt;
     const float m = P.mass_c * rl * rl * hl;
     const float I = P.inertia_f * m * rl * rl;
     out.xq[l] = xl + (uint32_t)__float2int_rn(dt * ul * isx);

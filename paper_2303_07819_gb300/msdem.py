@@ -87,7 +87,7 @@ def load(path: str | None = None):
     L.ms_set_stream.argtypes = [vp, vp]
     L.ms_autotune.argtypes = [vp, C.c_double, C.c_int32, _dp]
     L.ms_time_kernel.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, _dp]
-    L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double]
+    L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32]
     L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
@@ -224,8 +224,9 @@ class Model:
         return out.value
 
     def set_launch(self, variant: int = 0, threads: int = 128, persistent: int = 0,
-                   bin_beta: float = 1.0) -> None:
-        _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta)))
+                   bin_beta: float = 1.0, reg_min: int = 0) -> None:
+        _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta),
+                                    int(reg_min)))
 
     def info(self) -> dict:
         out = np.zeros(16, dtype=np.int64)

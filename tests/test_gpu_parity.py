@@ -216,6 +216,8 @@ def test_autotune_keeps_results(ms):
     b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     best = b.autotune(s["dt"], reps=3)
     assert best > 0
+    ib = b.info()
+    a.set_launch(ib["variant"], ib["threads"], ib["persistent"], ib["bin_beta_milli"] / 1000.0)
     a.step(s["dt"], 120)
     b.step(s["dt"], 120)
     fa, fb = a.floes(), b.floes()
@@ -268,3 +270,34 @@ def test_set_floes_roundtrip(ms):
     f2 = g.floes()
     for k in f:
         assert np.array_equal(f[k], f2[k]), k
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_fp32_variants_match_oracle(orc, ms, variant):
+    """Brute-force, block-binned and warp-binned pair search: each within the
+    FP32 tolerance of the oracle over 100 steps on a ragged mix of cells
+    (0 to 300 floes, so every size class and both launch kinds run)."""
+    s = ragged_scenario([0, 1, 5, 17, 31, 33, 64, 65, 100, 127, 129, 200, 256, 257, 300], seed=21)
+    p = s["params"]
+    o = orc.Model(p, s["floes"])
+    g = ms.Model(p, s["floes"], ms.MS_FP32)
+    g.set_launch(variant, 128, 0, 1.0)
+    o.step(s["dt"], 100)
+    g.step(s["dt"], 100)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+
+
+def test_fp32_variants_agree_one_step(ms):
+    """One step of configs[1]'s laws on 16 x 16 cells: the three pair searches
+    find the same contacts, so moments agree to FP32 summation order."""
+    s = I.config1(nx=16)
+    res = []
+    for variant in (0, 1, 2):
+        g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+        g.set_launch(variant, 128, 0, 1.0)
+        g.step(s["dt"], 1)
+        res.append(g.moments())
+    for r in res[1:]:
+        e = rel_errors(r, res[0], s["params"], 1e-6)
+        assert e.max() < 1e-6, report(e)
