@@ -195,6 +195,32 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
  * coarse step. */
 int ms_info(ms_model *m, int64_t *out);
 
+/* Per-cell moments of a floe set held in the caller's device memory, computed
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc while they run, such as
+ * a host code that reserves all its device memory up front and forbids
+ * allocation inside its time loop, or a framework whose allocator already owns
+ * the device memory.  It bins the floes by the coarse cell holding their
+ * centre (half-open cells of `grid`) and writes out[ncell][MS_NMOM] with the
+ * columns of ms_moments, in ascending floe order within each cell.
+ * Inputs (device, FP64, n each, caller-owned): x, y in domain coordinates,
+ * u, v, omega, r, h, and fd = [3][n] per-floe drag (Fx, Fy, torque; zeros if
+ * there is none); mass rho_ice pi r^2 h, inertia m r^2 (inertia_half = 1:
+ * m r^2 / 2).  out is device memory for ncell * MS_NMOM doubles.
+ * Working memory is one fixed device array compiled into the library (about
+ * 2.2 MB on every device that loads it, held until exit): at most 262144
+ * floes and 16384 cells; larger inputs return MS_ERR_ARG.  The first call on
+ * each device looks the array's device address up, so make it before any
+ * stream capture.  All calls on a device share that array and each call
+ * clears what must start at zero, so calls whose work overlaps on the GPU
+ * (from different host threads or streams) corrupt each other's results.
+ * The work runs on `stream` (NULL: the legacy default stream) and the call
+ * waits for it before returning. */
+int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia_half, int64_t n,
+                            const double *x, const double *y, const double *u, const double *v,
+                            const double *omega, const double *r, const double *h, const double *fd,
+                            double *out, void *stream);
+
 /* Release the model's device memory, graphs, events and stream. */
 void ms_free(ms_model *m);
 

@@ -1067,4 +1067,35 @@ int ms_info(ms_model *m, int64_t *out)
     return MS_OK;
 }
 
+int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia_half, int64_t n,
+                            const double *x, const double *y, const double *u, const double *v,
+                            const double *omega, const double *r, const double *h, const double *fd,
+                            double *out, void *stream)
+{
+    if (!grid) return fail(MS_ERR_ARG, "grid is NULL");
+    if (grid->nx < 1 || grid->ny < 1 || !(grid->Lx > 0.0) || !(grid->Ly > 0.0) || !isfin(grid->Lx) ||
+        !isfin(grid->Ly))
+        return fail(MS_ERR_ARG, "grid needs nx, ny >= 1 and positive finite sides");
+    if ((long long)grid->nx * grid->ny > noalloc_max_cells())
+        return fail(MS_ERR_ARG, "ms_cell_moments_noalloc handles at most %d cells, got %lld", noalloc_max_cells(),
+                    (long long)grid->nx * grid->ny);
+    if (n < 0 || n > noalloc_max_floes())
+        return fail(MS_ERR_ARG, "ms_cell_moments_noalloc handles 0 to %lld floes, got %lld", noalloc_max_floes(),
+                    (long long)n);
+    if (!(rho_ice > 0.0) || !isfin(rho_ice)) return fail(MS_ERR_ARG, "rho_ice must be positive");
+    if (!out) return fail(MS_ERR_ARG, "out is NULL");
+    if (n > 0 && (!x || !y || !u || !v || !omega || !r || !h || !fd)) return fail(MS_ERR_ARG, "a floe array is NULL");
+    Geom g;
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.Lx = grid->Lx;
+    g.Ly = grid->Ly;
+    g.Lcx = grid->Lx / grid->nx;
+    g.Lcy = grid->Ly / grid->ny;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(noalloc_cell_moments(g, rho_ice * PI_D, inertia_half ? 0.5 : 1.0, n, x, y, u, v, omega, r, h, fd, out, st));
+    CK(cudaStreamSynchronize(st));
+    return MS_OK;
+}
+
 }  // extern "C"

@@ -298,6 +298,13 @@ cudaError_t launch_truth_moments32(const DevState32 &s, const Phys<float> &P, co
 cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, const TruthArgs &a,
                                    TruthBins &cells, double *mom, cudaStream_t st);
 int truth_launches(const TruthBins &b);
+// per-cell moments with scratch from a static device array (no allocation)
+long long noalloc_max_floes();
+int noalloc_max_cells();
+cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f, long long n, const double *x,
+                                 const double *y, const double *u, const double *v, const double *w,
+                                 const double *r, const double *h, const double *fd, double *mom,
+                                 cudaStream_t st);
 cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
 
 }  // namespace msd

@@ -7,6 +7,8 @@
 // force summation order are deterministic) into square-ish bins of side at
 // least 2 r_max; each floe then visits the 3 x 3 neighbouring bins.  The state
 // is double-buffered: the step reads one copy and writes the other.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace msd {
@@ -389,6 +391,89 @@ cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, c
     k_truth_cell_moments<double><<<(nc + 127) / 128, 128, 0, st>>>(
         s.u, s.v, s.w, s.r, s.h, reinterpret_cast<const double *>(a.fd), a.n, P.mass_c, P.inertia_f,
         cells.start, cells.sorted, nc, mom);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------- moments without allocating
+// A variant of the per-cell moment binning above whose working memory (the
+// counting sort's counts, starts, cursors and the sorted floe list) lives in
+// one file-scope device array instead of buffers from cudaMalloc, for callers
+// that must not allocate device memory while they run (see msdem.h).  Every
+// call on a device reuses the same array: the counts and cursors are cleared
+// at the start of each call, and two calls that run on the GPU at the same
+// time corrupt each other.
+
+namespace {
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
+
+}  // namespace
+
+}  // namespace msd
+
+// Scratch of ms_cell_moments_noalloc: 3 * NA_CELLS + 1 + NA_SCAN ints for the
+// cell counts, starts and cursors plus the scan's block sums, then 2 * NA_FLOES
+// ints for each floe's cell and the floes sorted by cell (about 2.2 MB).
+#define MS_NA_FLOES (1 << 18)
+#define MS_NA_CELLS (1 << 14)
+#define MS_NA_SCAN ((MS_NA_CELLS + 1 + 1023) / 1024)
+static __device__ __align__(256) int ms_noalloc_scratch[3 * MS_NA_CELLS + 1 + MS_NA_SCAN + 2 * MS_NA_FLOES];
+
+namespace msd {
+
+long long noalloc_max_floes() { return MS_NA_FLOES; }
+int noalloc_max_cells() { return MS_NA_CELLS; }
+
+// Device address of the scratch array on the current device.  The address a
+// host program sees for the symbol is only a host-side placeholder; the device
+// address is looked up once per device, with that device current.
+static cudaError_t noalloc_scratch(int **out)
+{
+    static std::mutex mu;
+    static int *addr[128] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, ms_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = reinterpret_cast<int *>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f, long long n, const double *x,
+                                 const double *y, const double *u, const double *v, const double *w,
+                                 const double *r, const double *h, const double *fd, double *mom,
+                                 cudaStream_t st)
+{
+    int *base = nullptr;
+    cudaError_t e = noalloc_scratch(&base);
+    if (e != cudaSuccess) return e;
+    TruthBins b{};
+    b.nbx = g.nx;
+    b.nby = g.ny;
+    const int nbins = g.nx * g.ny;
+    b.count = base;
+    b.start = b.count + MS_NA_CELLS;
+    b.cursor = b.start + MS_NA_CELLS + 1;
+    b.scan_tmp = b.cursor + MS_NA_CELLS;
+    b.bin = b.scan_tmp + MS_NA_SCAN;
+    b.sorted = b.bin + MS_NA_FLOES;
+    b.nscan_blocks = (nbins + 1023) / 1024;
+    k_set_int<<<1, 1, 0, st>>>(b.start + nbins, (int)n);
+    const int T = 256;
+    const unsigned G = (unsigned)((n + T - 1) / T);
+    e = counting_sort(b, n, [&] {
+        k_bin64<<<G, T, 0, st>>>(x, y, g.Lx, g.Ly, b.nbx, b.nby, b.bin, b.count, n);
+    }, st);
+    if (e != cudaSuccess) return e;
+    k_truth_cell_moments<double><<<(nbins + 127) / 128, 128, 0, st>>>(u, v, w, r, h, fd, n, mass_c, inertia_f,
+                                                                     b.start, b.sorted, nbins, mom);
     return cudaGetLastError();
 }
 

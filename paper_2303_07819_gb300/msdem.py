@@ -53,7 +53,7 @@ class MsError(RuntimeError):
 _lib = None
 SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_get_floes", "ms_set_floes", "ms_coupling",
            "ms_truth_step", "ms_truth_moments", "ms_truth_get_floes", "ms_set_stream", "ms_autotune",
-           "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error"]
+           "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc"]
 
 
 def lib_path() -> str:
@@ -89,6 +89,7 @@ def load(path: str | None = None):
     L.ms_time_kernel.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, _dp]
     L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32]
     L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.ms_cell_moments_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int32, C.c_int64] + [vp] * 10
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
@@ -235,3 +236,16 @@ class Model:
                 "launches_per_step", "launches_per_coarse", "launches_per_truth_step", "steps",
                 "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1"]
         return {k: int(v) for k, v in zip(keys, out)}
+
+
+def cell_moments_noalloc(params: dict, n: int, x: int, y: int, u: int, v: int, omega: int, r: int, h: int,
+                         fd: int, out: int, stream: int | None = None) -> None:
+    """Per-cell moments of floes in device memory (addresses as ints, FP64),
+    computed without any device allocation (see ms_cell_moments_noalloc in
+    include/msdem.h): for callers that must not allocate while they run.
+    `out` receives ncell x 12 doubles; fd is [3][n] per-floe drag."""
+    L = load()
+    g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]))
+    ptrs = [C.c_void_p(a) for a in (x, y, u, v, omega, r, h, fd, out)]
+    _check(L.ms_cell_moments_noalloc(C.byref(g), float(params["rho_ice"]), int(params.get("inertia_half", 0)),
+                                     int(n), *ptrs, C.c_void_p(stream or 0)))
