@@ -221,6 +221,48 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
                             const double *omega, const double *r, const double *h, const double *fd,
                             double *out, void *stream);
 
+/* ---- learned closure (not in the paper: a learned model of the bulk feedback)
+ * A 12 -> 128 -> 128 -> 128 -> 4 MLP, tanh hidden units:
+ *   xh = (x - mu_x)/sd_x, h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2),
+ *   h3 = tanh(W3 h2 + b3), yh = W4 h3 + b4, y = mu_y + sd_y yh,
+ * trained on the mean-squared error of yh against (y_target - mu_y)/sd_y with
+ * Adam (beta 0.9, 0.999, eps 1e-8).  Products run on BF16 tensor cores with
+ * FP32 accumulation; master weights, biases and Adam state are FP32.
+ * Packed parameter layout (35,204 floats): W1[128][12], b1[128], W2[128][128],
+ * b2[128], W3[128][128], b3[128], W4[4][128], b4[4] (W[out][in]).
+ * Features x (12 per sample) and targets y (4) are FP32, sample-major. */
+typedef struct ms_mlp ms_mlp;
+
+/* Create a network from host params (packed) and norm = host
+ * [mu_x(12), sd_x(12), mu_y(4), sd_y(4)] (sd > 0); max_batch = largest batch
+ * of any later call (1 .. 2^22). */
+int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t max_batch);
+
+/* Forward pass: host X[n][12] -> host Y[n][4] in physical units. */
+int ms_mlp_predict(ms_mlp *m, const float *X, int64_t n, float *Y);
+
+/* Gradient of the loss of one batch (n <= max_batch) without updating:
+ * host grads in the packed layout, *loss (host, may be NULL). */
+int ms_mlp_grad(ms_mlp *m, const float *X, const float *Y, int64_t n, float *grads, double *loss);
+
+/* One Adam step of learning rate lr on one batch (n <= max_batch). */
+int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr);
+
+/* Train for `epochs` passes over host data (n samples) in batches of
+ * `batch` (8 .. max_batch), reshuffled every epoch from `seed`;
+ * loss_per_epoch (host [epochs], may be NULL) gets each epoch's mean loss. */
+int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                 uint64_t seed, double *loss_per_epoch);
+
+/* Current FP32 parameters, host, packed layout. */
+int ms_mlp_get_params(ms_mlp *m, float *params);
+
+/* Forward pass on device buffers X[n][12] -> Y[n][4] on `stream`, without
+ * waiting. */
+int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream);
+
+void ms_mlp_free(ms_mlp *m);
+
 /* Release the model's device memory, graphs, events and stream. */
 void ms_free(ms_model *m);
 

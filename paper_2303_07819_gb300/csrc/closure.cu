@@ -1,0 +1,642 @@
+// closure.cu -- the learned closure: a 12 -> 128 -> 128 -> 128 -> 4 tanh MLP
+// that maps a cell's moments and forcing to its bulk drag tendencies, trained
+// and evaluated with BF16 tensor-core products accumulated in FP32 (FP32
+// master weights, Adam).
+//
+// Every product of the forward and backward pass is one call of a single
+// tiled GEMM, C[m][n] = sum_k A[m][k] B[n][k], both operands BF16 with k
+// contiguous, so the backward pass keeps each activation and each gradient in
+// two layouts ([sample][unit] and [unit][sample]) written by the producing
+// epilogue.  The weight gradients (sum over the batch) split the batch across
+// blocks and add their partial products atomically.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "../../include/msdem.h"
+
+namespace msd {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int NIN = 12, NH = 128, NOUT = 4;
+constexpr int KIN = 16;          // input features padded to a multiple of 16
+constexpr int NOP = 8;           // outputs padded to one n-tile
+constexpr int BM = 64, BN = 64, BK = 32, SPAD = 8;
+
+enum Epi { EPI_TANH = 0, EPI_LIN = 1, EPI_DZ = 2, EPI_F32 = 3 };
+
+struct EpiArgs {
+    const float *bias;     // EPI_TANH, EPI_LIN
+    bf16 *out, *outT;      // EPI_TANH, EPI_DZ: [m][n] (ld ldo) and [n][m] (ld ldt)
+    int ldo, ldt;
+    const bf16 *h;         // EPI_DZ: the activation whose tanh' scales the product, [m][n] ld ldo
+    float *bgrad;          // EPI_DZ: column sums (bias gradient), atomically
+    float *f32;            // EPI_LIN, EPI_F32: FP32 result [m][n] ld ldf
+    int ldf;
+    int atomic;            // EPI_F32: add instead of store (split over k)
+    int n_real;            // columns that exist (outputs beyond are padding)
+};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C = A B^T over a BM x BN tile per block (4 warps, 32 x 32 each), k-slice
+// [kz * kchunk, (kz + 1) * kchunk) for blockIdx.z = kz.  lda, ldb and K are
+// multiples of 8 (16-byte rows of BF16); out-of-range rows and k read as 0.
+template <int EPI>
+__global__ void __launch_bounds__(128)
+k_gemm(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
+       EpiArgs ea)
+{
+    __shared__ __align__(16) bf16 As[BM][BK + SPAD];
+    __shared__ __align__(16) bf16 Bs[BN][BK + SPAD];
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.0f;
+
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        // 64 rows x 4 chunks of 8 BF16 for each operand: 2 chunks per thread
+        for (int c = threadIdx.x; c < BM * (BK / 8); c += 128) {
+            const int r = c >> 2, kc = (c & 3) * 8;
+            const int gk = k0 + kc;
+            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+            if (m0 + r < M && gk < kend) va = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + gk);
+            if (n0 + r < N && gk < kend) vb = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + gk);
+            *reinterpret_cast<uint4 *>(&As[r][kc]) = va;
+            *reinterpret_cast<uint4 *>(&Bs[r][kc]) = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = wm + 16 * i + g;
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 2 * t]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 2 * t]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[r][kk + 8 + 2 * t]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int c = wn + 8 * j + g;
+                bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 2 * t]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][kk + 8 + 2 * t]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+
+    // epilogue: element (m, n) of fragment value q: m = row + (q >= 2) * 8, n = col + (q & 1)
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            float csum[2] = {0.0f, 0.0f};
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int m = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0);
+                const int n = n0 + wn + 8 * j + 2 * t + (q & 1);
+                float v = acc[i][j][q];
+                const bool ok = m < M && n < N;
+                if (EPI == EPI_TANH) {
+                    if (ok) {
+                        const float h = tanhf(v + ea.bias[n]);
+                        const bf16 hb = __float2bfloat16_rn(h);
+                        ea.out[(size_t)m * ea.ldo + n] = hb;
+                        ea.outT[(size_t)n * ea.ldt + m] = hb;
+                    }
+                } else if (EPI == EPI_LIN) {
+                    if (ok) ea.f32[(size_t)m * ea.ldf + n] = v + (n < ea.n_real ? ea.bias[n] : 0.0f);
+                } else if (EPI == EPI_DZ) {
+                    if (ok) {
+                        const float h = __bfloat162float(ea.h[(size_t)m * ea.ldo + n]);
+                        const float dz = v * (1.0f - h * h);
+                        const bf16 db = __float2bfloat16_rn(dz);
+                        ea.out[(size_t)m * ea.ldo + n] = db;
+                        ea.outT[(size_t)n * ea.ldt + m] = db;
+                        csum[q & 1] += dz;
+                    }
+                } else {
+                    if (ok) {
+                        float *p = ea.f32 + (size_t)m * ea.ldf + n;
+                        if (ea.atomic) atomicAdd(p, v);
+                        else *p = v;
+                    }
+                }
+            }
+            if (EPI == EPI_DZ) {
+                // bias gradient: sum the column over the 8 row groups of the warp
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    float x = csum[s];
+                    x += __shfl_xor_sync(0xffffffffu, x, 4);
+                    x += __shfl_xor_sync(0xffffffffu, x, 8);
+                    x += __shfl_xor_sync(0xffffffffu, x, 16);
+                    const int n = n0 + wn + 8 * j + 2 * t + s;
+                    if (g == 0 && n < N) atomicAdd(&ea.bgrad[n], x);
+                }
+            }
+        }
+}
+
+// raw features -> z-scored BF16, [B][KIN] and [KIN][B] (padding columns 0)
+__global__ void k_prep_input(const float *X, int B, int Bp, const float *mu, const float *sd, bf16 *xh, bf16 *xht)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= Bp) return;
+    for (int f = 0; f < KIN; f++) {
+        float v = 0.0f;
+        if (s < B && f < NIN) v = (X[(size_t)s * NIN + f] - mu[f]) / sd[f];
+        const bf16 b = __float2bfloat16_rn(v);
+        xh[(size_t)s * KIN + f] = b;
+        xht[(size_t)f * Bp + s] = b;
+    }
+}
+
+// z-scored residual of the outputs: loss sum, dL/dy in both layouts, output
+// bias gradient
+__global__ void k_loss_grad(const float *yp, const float *Y, int B, int Bp, const float *mu, const float *sd,
+                            bf16 *dy, bf16 *dyt, float *b4grad, double *loss)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (s < Bp) {
+        for (int o = 0; o < NOP; o++) {
+            float g = 0.0f;
+            if (s < B && o < NOUT) {
+                const float r = yp[(size_t)s * NOP + o] - (Y[(size_t)s * NOUT + o] - mu[o]) / sd[o];
+                l += (double)r * r;
+                g = 2.0f * r / (4.0f * (float)B);
+                atomicAdd(&b4grad[o], g);
+            }
+            const bf16 b = __float2bfloat16_rn(g);
+            dy[(size_t)s * NOP + o] = b;
+            dyt[(size_t)o * Bp + s] = b;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l / (4.0 * B));
+}
+
+// z-scored outputs -> physical units
+__global__ void k_denorm(const float *yp, int B, const float *mu, const float *sd, float *Y)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B) return;
+    for (int o = 0; o < NOUT; o++) Y[(size_t)s * NOUT + o] = mu[o] + sd[o] * yp[(size_t)s * NOP + o];
+}
+
+struct LayerDev {
+    int nin, nout, kin, nop;   // logical and padded sizes
+    float *W, *b;              // FP32 master [nout][nin], [nout]
+    float *mW, *vW, *mb, *vb;  // Adam moments
+    float *gW, *gb;            // gradients [nop][kin] (padded), [nout]
+    bf16 *Wb, *Wt;             // BF16 copies [nop][kin] and [kin][nop]
+};
+
+// Adam on one layer, then refresh its BF16 copies (both layouts)
+__global__ void k_adam(LayerDev L, float lr, float c1, float c2, float beta1, float beta2, float eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = L.nout * L.nin;
+    if (i < nw) {
+        const int o = i / L.nin, k = i % L.nin;
+        const float g = L.gW[o * L.kin + k];
+        const float m = beta1 * L.mW[i] + (1.0f - beta1) * g;
+        const float v = beta2 * L.vW[i] + (1.0f - beta2) * g * g;
+        L.mW[i] = m;
+        L.vW[i] = v;
+        const float w = L.W[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+        L.W[i] = w;
+        const bf16 wb = __float2bfloat16_rn(w);
+        L.Wb[o * L.kin + k] = wb;
+        L.Wt[k * L.nop + o] = wb;
+    } else if (i < nw + L.nout) {
+        const int o = i - nw;
+        const float g = L.gb[o];
+        const float m = beta1 * L.mb[o] + (1.0f - beta1) * g;
+        const float v = beta2 * L.vb[o] + (1.0f - beta2) * g * g;
+        L.mb[o] = m;
+        L.vb[o] = v;
+        L.b[o] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+__global__ void k_cast_layer(LayerDev L)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.nop * L.kin) return;
+    const int o = i / L.kin, k = i % L.kin;
+    const float w = (o < L.nout && k < L.nin) ? L.W[o * L.nin + k] : 0.0f;
+    const bf16 wb = __float2bfloat16_rn(w);
+    L.Wb[i] = wb;
+    L.Wt[k * L.nop + o] = wb;
+}
+
+}  // namespace
+
+}  // namespace msd
+
+using namespace msd;
+
+struct ms_mlp {
+    int max_batch = 0, bp = 0;
+    LayerDev L[4];
+    float *mu_x = nullptr, *sd_x = nullptr, *mu_y = nullptr, *sd_y = nullptr;
+    float *X = nullptr, *Y = nullptr, *yp = nullptr, *yout = nullptr;
+    bf16 *xh = nullptr, *xht = nullptr, *H[3] = {}, *Ht[3] = {}, *dZ[3] = {}, *dZt[3] = {}, *dy = nullptr,
+         *dyt = nullptr;
+    double *loss = nullptr;
+    long long t = 0;           // Adam steps
+    cudaStream_t st = nullptr;
+    std::vector<void *> allocs;
+    std::vector<float> hnorm;
+};
+
+namespace msd {
+
+static const int LIN[4] = {NIN, NH, NH, NH}, LOUT[4] = {NH, NH, NH, NOUT};
+static const int LKIN[4] = {KIN, NH, NH, NH}, LNOP[4] = {NH, NH, NH, NOP};
+
+template <class T>
+static cudaError_t mal(ms_mlp *m, T **p, size_t n)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) return e;
+    m->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return cudaMemsetAsync(q, 0, sizeof(T) * (n ? n : 1), m->st);
+}
+
+static cudaError_t gemm(int epi, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, const EpiArgs &ea,
+                        cudaStream_t st, int ksplit = 1)
+{
+    const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
+    dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, (K + kchunk - 1) / kchunk);
+    switch (epi) {
+    case EPI_TANH: k_gemm<EPI_TANH><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea); break;
+    case EPI_LIN: k_gemm<EPI_LIN><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea); break;
+    case EPI_DZ: k_gemm<EPI_DZ><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea); break;
+    default: k_gemm<EPI_F32><<<grid, 128, 0, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea); break;
+    }
+    return cudaGetLastError();
+}
+
+// forward pass of a batch already z-scored in m->xh (Bp rows): m->yp = z-scored outputs
+static cudaError_t forward(ms_mlp *m, int Bp)
+{
+    cudaError_t e;
+    const bf16 *in = m->xh;
+    int ldin = KIN;
+    for (int l = 0; l < 3; l++) {
+        EpiArgs ea{};
+        ea.bias = m->L[l].b;
+        ea.out = m->H[l];
+        ea.outT = m->Ht[l];
+        ea.ldo = NH;
+        ea.ldt = Bp;
+        if ((e = gemm(EPI_TANH, Bp, NH, LKIN[l], in, ldin, m->L[l].Wb, LKIN[l], ea, m->st)) != cudaSuccess) return e;
+        in = m->H[l];
+        ldin = NH;
+    }
+    EpiArgs ea{};
+    ea.bias = m->L[3].b;
+    ea.f32 = m->yp;
+    ea.ldf = NOP;
+    ea.n_real = NOUT;
+    return gemm(EPI_LIN, Bp, NOP, NH, in, NH, m->L[3].Wb, NH, ea, m->st);
+}
+
+// gradients of the batch loss (z-scored units) into the layers' gW, gb
+static cudaError_t backward(ms_mlp *m, int B, int Bp)
+{
+    cudaError_t e;
+    for (int l = 0; l < 4; l++) {
+        if ((e = cudaMemsetAsync(m->L[l].gW, 0, sizeof(float) * LNOP[l] * LKIN[l], m->st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(m->L[l].gb, 0, sizeof(float) * LOUT[l], m->st)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemsetAsync(m->loss, 0, sizeof(double), m->st)) != cudaSuccess) return e;
+    k_loss_grad<<<(Bp + 255) / 256, 256, 0, m->st>>>(m->yp, m->Y, B, Bp, m->mu_y, m->sd_y, m->dy, m->dyt, m->L[3].gb,
+                                                     m->loss);
+    const int ks = Bp >= 4096 ? 32 : (Bp >= 512 ? 8 : 1);
+    // output layer: gW4 = dy^T H3, then the gradient through it
+    const bf16 *dz = m->dy, *dzt = m->dyt;
+    int ldz = NOP;
+    for (int l = 3; l >= 0; l--) {
+        const bf16 *xt = l > 0 ? m->Ht[l - 1] : m->xht;
+        EpiArgs eg{};
+        eg.f32 = m->L[l].gW;
+        eg.ldf = LKIN[l];
+        eg.atomic = ks > 1;
+        if ((e = gemm(EPI_F32, LOUT[l], LKIN[l], Bp, dzt, Bp, xt, Bp, eg, m->st, ks)) != cudaSuccess) return e;
+        if (l == 0) break;
+        // dH_{l} = dz W_l -> dZ_{l-1} = dH (1 - h^2), plus its bias gradient
+        EpiArgs ed{};
+        ed.h = m->H[l - 1];
+        ed.out = m->dZ[l - 1];
+        ed.outT = m->dZt[l - 1];
+        ed.ldo = NH;
+        ed.ldt = Bp;
+        ed.bgrad = m->L[l - 1].gb;
+        if ((e = gemm(EPI_DZ, Bp, NH, LNOP[l], dz, ldz, m->L[l].Wt, LNOP[l], ed, m->st)) != cudaSuccess) return e;
+        dz = m->dZ[l - 1];
+        dzt = m->dZt[l - 1];
+        ldz = NH;
+    }
+    return cudaGetLastError();
+}
+
+static int pad8(long long n) { return (int)((n + 7) / 8 * 8); }
+
+}  // namespace msd
+
+// ----------------------------------------------------------------- C-ABI
+static int ms_closure_fail(int code, const char *msg) { return msd::set_error(code, msg); }
+
+extern "C" {
+
+static int ck(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return MS_OK;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s failed: %s", what, cudaGetErrorString(e));
+    return ms_closure_fail(MS_ERR_CUDA, buf);
+}
+#define CKC(x) do { int rc_ = ck((x), #x); if (rc_) return rc_; } while (0)
+
+int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t max_batch)
+{
+    if (!out || !params || !norm) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (max_batch < 1 || max_batch > (1 << 22)) return ms_closure_fail(MS_ERR_ARG, "max_batch must be in [1, 2^22]");
+    for (int i = 0; i < 2 * NIN + 2 * NOUT; i++)
+        if (!std::isfinite(norm[i]) || (((i >= NIN && i < 2 * NIN) || i >= 2 * NIN + NOUT) && !(norm[i] > 0.0f)))
+            return ms_closure_fail(MS_ERR_ARG, "normalisation needs finite means and positive spreads");
+    ms_mlp *m = new ms_mlp();
+    m->max_batch = max_batch;
+    m->bp = pad8(max_batch);
+    m->hnorm.assign(norm, norm + 2 * NIN + 2 * NOUT);
+    int rc = MS_OK;
+    auto fail_free = [&](int r) { ms_mlp_free(m); return r; };
+    if ((rc = ck(cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking), "stream"))) return fail_free(rc);
+    const int Bp = m->bp;
+    size_t off = 0;
+    for (int l = 0; l < 4; l++) {
+        LayerDev &L = m->L[l];
+        L.nin = LIN[l]; L.nout = LOUT[l]; L.kin = LKIN[l]; L.nop = LNOP[l];
+        const size_t nw = (size_t)L.nout * L.nin;
+        cudaError_t e;
+        if ((e = mal(m, &L.W, nw)) || (e = mal(m, &L.b, L.nout)) || (e = mal(m, &L.mW, nw)) ||
+            (e = mal(m, &L.vW, nw)) || (e = mal(m, &L.mb, L.nout)) || (e = mal(m, &L.vb, L.nout)) ||
+            (e = mal(m, &L.gW, (size_t)L.nop * L.kin)) || (e = mal(m, &L.gb, L.nout)) ||
+            (e = mal(m, &L.Wb, (size_t)L.nop * L.kin)) || (e = mal(m, &L.Wt, (size_t)L.nop * L.kin)))
+            return fail_free(ck(e, "cudaMalloc"));
+        if ((rc = ck(cudaMemcpyAsync(L.W, params + off, sizeof(float) * nw, cudaMemcpyHostToDevice, m->st), "copy")))
+            return fail_free(rc);
+        off += nw;
+        if ((rc = ck(cudaMemcpyAsync(L.b, params + off, sizeof(float) * L.nout, cudaMemcpyHostToDevice, m->st), "copy")))
+            return fail_free(rc);
+        off += L.nout;
+        k_cast_layer<<<(L.nop * L.kin + 255) / 256, 256, 0, m->st>>>(L);
+    }
+    cudaError_t e;
+    if ((e = mal(m, &m->mu_x, NIN)) || (e = mal(m, &m->sd_x, NIN)) || (e = mal(m, &m->mu_y, NOUT)) ||
+        (e = mal(m, &m->sd_y, NOUT)) || (e = mal(m, &m->X, (size_t)Bp * NIN)) || (e = mal(m, &m->Y, (size_t)Bp * NOUT)) ||
+        (e = mal(m, &m->yp, (size_t)Bp * NOP)) || (e = mal(m, &m->yout, (size_t)Bp * NOUT)) ||
+        (e = mal(m, &m->xh, (size_t)Bp * KIN)) || (e = mal(m, &m->xht, (size_t)Bp * KIN)) ||
+        (e = mal(m, &m->dy, (size_t)Bp * NOP)) || (e = mal(m, &m->dyt, (size_t)Bp * NOP)) || (e = mal(m, &m->loss, 1)))
+        return fail_free(ck(e, "cudaMalloc"));
+    for (int l = 0; l < 3; l++)
+        if ((e = mal(m, &m->H[l], (size_t)Bp * NH)) || (e = mal(m, &m->Ht[l], (size_t)Bp * NH)) ||
+            (e = mal(m, &m->dZ[l], (size_t)Bp * NH)) || (e = mal(m, &m->dZt[l], (size_t)Bp * NH)))
+            return fail_free(ck(e, "cudaMalloc"));
+    const float *nz = m->hnorm.data();
+    if ((rc = ck(cudaMemcpyAsync(m->mu_x, nz, 4 * NIN, cudaMemcpyHostToDevice, m->st), "copy")) ||
+        (rc = ck(cudaMemcpyAsync(m->sd_x, nz + NIN, 4 * NIN, cudaMemcpyHostToDevice, m->st), "copy")) ||
+        (rc = ck(cudaMemcpyAsync(m->mu_y, nz + 2 * NIN, 4 * NOUT, cudaMemcpyHostToDevice, m->st), "copy")) ||
+        (rc = ck(cudaMemcpyAsync(m->sd_y, nz + 2 * NIN + NOUT, 4 * NOUT, cudaMemcpyHostToDevice, m->st), "copy")) ||
+        (rc = ck(cudaStreamSynchronize(m->st), "sync")))
+        return fail_free(rc);
+    *out = m;
+    return MS_OK;
+}
+
+void ms_mlp_free(ms_mlp *m)
+{
+    if (!m) return;
+    if (m->st) cudaStreamSynchronize(m->st);
+    for (void *p : m->allocs) cudaFree(p);
+    if (m->st) cudaStreamDestroy(m->st);
+    delete m;
+}
+
+// device-pointer forward used by the model's hybrid step: X [n][12] raw -> Y [n][4]
+int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream)
+{
+    if (!m || (n > 0 && (!X || !Y))) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    cudaStream_t keep = m->st;
+    if (stream) m->st = (cudaStream_t)stream;
+    int rc = MS_OK;
+    for (int64_t s0 = 0; s0 < n && rc == MS_OK; s0 += m->max_batch) {
+        const int B = (int)std::min<int64_t>(m->max_batch, n - s0), Bp = pad8(B);
+        k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(X + s0 * NIN, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
+        rc = ck(forward(m, Bp), "forward");
+        if (rc == MS_OK) k_denorm<<<(B + 255) / 256, 256, 0, m->st>>>(m->yp, B, m->mu_y, m->sd_y, Y + s0 * NOUT);
+        if (rc == MS_OK) rc = ck(cudaGetLastError(), "denorm");
+    }
+    m->st = keep;
+    return rc;
+}
+
+int ms_mlp_predict(ms_mlp *m, const float *X, int64_t n, float *Y)
+{
+    if (!m || n < 0 || (n > 0 && (!X || !Y))) return ms_closure_fail(MS_ERR_ARG, "bad argument");
+    for (int64_t s0 = 0; s0 < n; s0 += m->max_batch) {
+        const int B = (int)std::min<int64_t>(m->max_batch, n - s0);
+        CKC(cudaMemcpyAsync(m->X, X + s0 * NIN, sizeof(float) * B * NIN, cudaMemcpyHostToDevice, m->st));
+        int rc = ms_mlp_forward_device(m, m->X, B, m->yout, nullptr);
+        if (rc) return rc;
+        CKC(cudaMemcpyAsync(Y + s0 * NOUT, m->yout, sizeof(float) * B * NOUT, cudaMemcpyDeviceToHost, m->st));
+        CKC(cudaStreamSynchronize(m->st));
+    }
+    return MS_OK;
+}
+
+static int gather_grads(ms_mlp *m, float *grads)
+{
+    size_t off = 0;
+    std::vector<float> tmp;
+    for (int l = 0; l < 4; l++) {
+        const LayerDev &L = m->L[l];
+        tmp.resize((size_t)L.nop * L.kin);
+        CKC(cudaMemcpyAsync(tmp.data(), L.gW, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, m->st));
+        CKC(cudaMemcpyAsync(grads + off + (size_t)L.nout * L.nin, L.gb, sizeof(float) * L.nout, cudaMemcpyDeviceToHost,
+                            m->st));
+        CKC(cudaStreamSynchronize(m->st));
+        for (int o = 0; o < L.nout; o++)
+            for (int k = 0; k < L.nin; k++) grads[off + (size_t)o * L.nin + k] = tmp[(size_t)o * L.kin + k];
+        off += (size_t)L.nout * L.nin + L.nout;
+    }
+    return MS_OK;
+}
+
+int ms_mlp_grad(ms_mlp *m, const float *X, const float *Y, int64_t n, float *grads, double *loss)
+{
+    if (!m || !X || !Y || !grads) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (n < 1 || n > m->max_batch) return ms_closure_fail(MS_ERR_ARG, "n must be in [1, max_batch]");
+    const int B = (int)n, Bp = pad8(B);
+    CKC(cudaMemcpyAsync(m->X, X, sizeof(float) * B * NIN, cudaMemcpyHostToDevice, m->st));
+    CKC(cudaMemcpyAsync(m->Y, Y, sizeof(float) * B * NOUT, cudaMemcpyHostToDevice, m->st));
+    k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(m->X, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
+    CKC(forward(m, Bp));
+    CKC(backward(m, B, Bp));
+    if (loss) CKC(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
+    CKC(cudaStreamSynchronize(m->st));
+    return gather_grads(m, grads);
+}
+
+int ms_mlp_get_params(ms_mlp *m, float *params)
+{
+    if (!m || !params) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    size_t off = 0;
+    for (int l = 0; l < 4; l++) {
+        const LayerDev &L = m->L[l];
+        const size_t nw = (size_t)L.nout * L.nin;
+        CKC(cudaMemcpyAsync(params + off, L.W, sizeof(float) * nw, cudaMemcpyDeviceToHost, m->st));
+        off += nw;
+        CKC(cudaMemcpyAsync(params + off, L.b, sizeof(float) * L.nout, cudaMemcpyDeviceToHost, m->st));
+        off += L.nout;
+    }
+    CKC(cudaStreamSynchronize(m->st));
+    return MS_OK;
+}
+
+// one Adam step on the gradients of the batch (X, Y) already on the device
+static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float lr)
+{
+    const int Bp = pad8(B);
+    k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(Xd, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
+    const float *keepY = m->Y;
+    m->Y = const_cast<float *>(Yd);
+    cudaError_t e = forward(m, Bp);
+    if (e == cudaSuccess) e = backward(m, B, Bp);
+    m->Y = const_cast<float *>(keepY);
+    CKC(e);
+    m->t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - std::pow(b1, (float)m->t), c2 = 1.0f - std::pow(b2, (float)m->t);
+    for (int l = 0; l < 4; l++) {
+        const int tot = m->L[l].nout * m->L[l].nin + m->L[l].nout;
+        k_adam<<<(tot + 255) / 256, 256, 0, m->st>>>(m->L[l], lr, c1, c2, b1, b2, 1e-8f);
+    }
+    return ck(cudaGetLastError(), "adam");
+}
+
+int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr)
+{
+    if (!m || !X || !Y) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (n < 1 || n > m->max_batch) return ms_closure_fail(MS_ERR_ARG, "n must be in [1, max_batch]");
+    CKC(cudaMemcpyAsync(m->X, X, sizeof(float) * n * NIN, cudaMemcpyHostToDevice, m->st));
+    CKC(cudaMemcpyAsync(m->Y, Y, sizeof(float) * n * NOUT, cudaMemcpyHostToDevice, m->st));
+    int rc = train_step(m, m->X, m->Y, (int)n, lr);
+    if (rc) return rc;
+    CKC(cudaStreamSynchronize(m->st));
+    return MS_OK;
+}
+
+int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                 uint64_t seed, double *loss_per_epoch)
+{
+    if (!m || !X || !Y) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (n < 1 || epochs < 0 || batch < 8 || batch > m->max_batch || !(lr > 0.0f))
+        return ms_closure_fail(MS_ERR_ARG, "need n >= 1, epochs >= 0, 8 <= batch <= max_batch, lr > 0");
+    // the whole training set on the device, shuffled per epoch on the host
+    float *Xd = nullptr, *Yd = nullptr, *Xs = nullptr, *Ys = nullptr;
+    std::vector<void *> loc;
+    auto dm = [&](float **p, size_t cnt) {
+        cudaError_t e = cudaMalloc(p, sizeof(float) * cnt);
+        if (e == cudaSuccess) loc.push_back(*p);
+        return e;
+    };
+    auto cleanup = [&]() { for (void *p : loc) cudaFree(p); };
+    cudaError_t e;
+    if ((e = dm(&Xd, (size_t)n * NIN)) || (e = dm(&Yd, (size_t)n * NOUT)) || (e = dm(&Xs, (size_t)n * NIN)) ||
+        (e = dm(&Ys, (size_t)n * NOUT))) {
+        cleanup();
+        return ck(e, "cudaMalloc");
+    }
+    std::vector<float> hx(X, X + n * NIN), hy(Y, Y + n * NOUT), sx((size_t)n * NIN), sy((size_t)n * NOUT);
+    std::vector<int64_t> perm(n);
+    for (int64_t i = 0; i < n; i++) perm[i] = i;
+    uint64_t st = seed ? seed : 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {   // SplitMix64
+        st += 0x9E3779B97F4A7C15ull;
+        uint64_t z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    int rc = MS_OK;
+    for (int ep = 0; ep < epochs && rc == MS_OK; ep++) {
+        for (int64_t i = n - 1; i > 0; i--) std::swap(perm[i], perm[(int64_t)(next() % (uint64_t)(i + 1))]);
+        for (int64_t i = 0; i < n; i++) {
+            std::memcpy(&sx[(size_t)i * NIN], &hx[(size_t)perm[i] * NIN], sizeof(float) * NIN);
+            std::memcpy(&sy[(size_t)i * NOUT], &hy[(size_t)perm[i] * NOUT], sizeof(float) * NOUT);
+        }
+        if ((rc = ck(cudaMemcpyAsync(Xs, sx.data(), sizeof(float) * sx.size(), cudaMemcpyHostToDevice, m->st), "copy")))
+            break;
+        if ((rc = ck(cudaMemcpyAsync(Ys, sy.data(), sizeof(float) * sy.size(), cudaMemcpyHostToDevice, m->st), "copy")))
+            break;
+        double lsum = 0.0;
+        int64_t nb = 0;
+        for (int64_t s0 = 0; s0 < n && rc == MS_OK; s0 += batch) {
+            const int B = (int)std::min<int64_t>(batch, n - s0);
+            if (B < 8) break;   // a ragged last batch below one tile row group is dropped this epoch
+            rc = train_step(m, Xs + s0 * NIN, Ys + s0 * NOUT, B, lr);
+            if (rc == MS_OK && loss_per_epoch) {
+                double l = 0.0;
+                rc = ck(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st), "copy");
+                if (rc == MS_OK) rc = ck(cudaStreamSynchronize(m->st), "sync");
+                lsum += l * B;
+                nb += B;
+            }
+        }
+        if (loss_per_epoch && nb) loss_per_epoch[ep] = lsum / nb;
+    }
+    if (rc == MS_OK) rc = ck(cudaStreamSynchronize(m->st), "sync");
+    cleanup();
+    return rc;
+}
+
+}  // extern "C"

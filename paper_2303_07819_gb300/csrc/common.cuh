@@ -307,4 +307,7 @@ cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f,
                                  cudaStream_t st);
 cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
 
+// api.cu: record the calling thread's error message and return code
+int set_error(int code, const char *msg);
+
 }  // namespace msd

@@ -269,3 +269,16 @@ def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, r
 
 
 CONFIGS = {0: config0, 1: config1, 2: config2}
+
+
+def mlp_init(seed: int = BASE_SEED + 3, layers=((12, 128), (128, 128), (128, 128), (128, 4))) -> dict:
+    """Initial closure weights (uniform Glorot: U(-a, a), a = sqrt(6/(fan_in +
+    fan_out)); zero biases), drawn here so both sides start from the same
+    network.  W[out][in]."""
+    rng = np.random.default_rng(seed)
+    p = {}
+    for i, (fi, fo) in enumerate(layers, start=1):
+        a = math.sqrt(6.0 / (fi + fo))
+        p[f"W{i}"] = rng.uniform(-a, a, size=(fo, fi))
+        p[f"b{i}"] = np.zeros(fo)
+    return p

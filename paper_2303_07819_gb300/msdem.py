@@ -53,7 +53,9 @@ class MsError(RuntimeError):
 _lib = None
 SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_get_floes", "ms_set_floes", "ms_coupling",
            "ms_truth_step", "ms_truth_moments", "ms_truth_get_floes", "ms_set_stream", "ms_autotune",
-           "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc"]
+           "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
+           "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
+           "ms_mlp_forward_device", "ms_mlp_free"]
 
 
 def lib_path() -> str:
@@ -94,7 +96,7 @@ def load(path: str | None = None):
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
     for name in SYMBOLS:
-        if name not in ("ms_free", "ms_last_error"):
+        if name not in ("ms_free", "ms_last_error", "ms_mlp_free"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -249,3 +251,104 @@ def cell_moments_noalloc(params: dict, n: int, x: int, y: int, u: int, v: int, o
     ptrs = [C.c_void_p(a) for a in (x, y, u, v, omega, r, h, fd, out)]
     _check(L.ms_cell_moments_noalloc(C.byref(g), float(params["rho_ice"]), int(params.get("inertia_half", 0)),
                                      int(n), *ptrs, C.c_void_p(stream or 0)))
+
+
+MLP_SHAPES = [("W1", (128, 12)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+              ("W3", (128, 128)), ("b3", (128,)), ("W4", (4, 128)), ("b4", (4,))]
+_fp = C.POINTER(C.c_float)
+
+
+def pack_params(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1) for k, _ in MLP_SHAPES])
+
+
+def unpack_params(flat: np.ndarray) -> dict:
+    out, off = {}, 0
+    for k, shp in MLP_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = flat[off:off + n].reshape(shp)
+        off += n
+    return out
+
+
+def _load_mlp():
+    L = load()
+    if getattr(L, "_mlp_ready", False):
+        return L
+    vp = C.c_void_p
+    L.ms_mlp_create.argtypes = [C.POINTER(vp), _fp, _fp, C.c_int32]
+    L.ms_mlp_predict.argtypes = [vp, _fp, C.c_int64, _fp]
+    L.ms_mlp_grad.argtypes = [vp, _fp, _fp, C.c_int64, _fp, C.POINTER(C.c_double)]
+    L.ms_mlp_step.argtypes = [vp, _fp, _fp, C.c_int64, C.c_float]
+    L.ms_mlp_train.argtypes = [vp, _fp, _fp, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
+                               C.POINTER(C.c_double)]
+    L.ms_mlp_get_params.argtypes = [vp, _fp]
+    L.ms_mlp_forward_device.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.ms_mlp_free.argtypes = [vp]
+    L.ms_mlp_free.restype = None
+    for n in ("ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train",
+              "ms_mlp_get_params", "ms_mlp_forward_device"):
+        getattr(L, n).restype = C.c_int
+    L._mlp_ready = True
+    return L
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class MLP:
+    """The closure network on the current CUDA device (see include/msdem.h)."""
+
+    def __init__(self, params: dict, norm: dict, max_batch: int = 8192):
+        L = _load_mlp()
+        self._keep = [pack_params(params),
+                      _f32(np.concatenate([norm["mu_x"], norm["sd_x"], norm["mu_y"], norm["sd_y"]]))]
+        h = C.c_void_p()
+        _check(L.ms_mlp_create(C.byref(h), self._keep[0].ctypes.data_as(_fp), self._keep[1].ctypes.data_as(_fp),
+                               int(max_batch)))
+        self._h = h
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load_mlp().ms_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        Y = np.zeros((X.shape[0], 4), dtype=np.float32)
+        _check(_load_mlp().ms_mlp_predict(self._h, X.ctypes.data_as(_fp), X.shape[0], Y.ctypes.data_as(_fp)))
+        return Y
+
+    def grad(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        g = np.zeros(35204, dtype=np.float32)
+        loss = C.c_double(0.0)
+        _check(_load_mlp().ms_mlp_grad(self._h, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0],
+                                       g.ctypes.data_as(_fp), C.byref(loss)))
+        return loss.value, unpack_params(g)
+
+    def step(self, X, Y, lr: float) -> None:
+        X, Y = _f32(X), _f32(Y)
+        _check(_load_mlp().ms_mlp_step(self._h, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0],
+                                       float(lr)))
+
+    def train(self, X, Y, epochs: int, batch: int, lr: float, seed: int = 1) -> np.ndarray:
+        X, Y = _f32(X), _f32(Y)
+        losses = np.zeros(epochs)
+        _check(_load_mlp().ms_mlp_train(self._h, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0],
+                                        int(epochs), int(batch), float(lr), int(seed),
+                                        losses.ctypes.data_as(C.POINTER(C.c_double))))
+        return losses
+
+    def params(self) -> dict:
+        flat = np.zeros(35204, dtype=np.float32)
+        _check(_load_mlp().ms_mlp_get_params(self._h, flat.ctypes.data_as(_fp)))
+        return {k: v.astype(np.float64) for k, v in unpack_params(flat).items()}

@@ -1,0 +1,87 @@
+"""The closure network's BF16 tensor-core forward, backward and Adam kernels
+against the FP64 oracle (oracle/closure_oracle.py)."""
+import numpy as np
+import pytest
+
+from oracle import closure_oracle as CO
+from paper_2303_07819_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    from paper_2303_07819_gb300 import msdem
+    msdem.load()
+    return msdem
+
+
+def _data(seed, B):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(B, 12)) * np.linspace(0.5, 3.0, 12) + np.arange(12)
+    Y = np.stack([np.sin(X[:, 0]), X[:, 1] * 0.1, np.tanh(X[:, 3] - 3), 0.01 * X[:, 4] ** 2], 1)
+    Y = Y * np.array([1e-3, 2e-3, 1e-6, 5e-5])
+    return X, Y
+
+
+def _params(seed=5):
+    rng = np.random.default_rng(seed)
+    p = I.mlp_init(seed=seed)
+    for k in ("b1", "b2", "b3", "b4"):
+        p[k] = rng.normal(scale=0.1, size=p[k].shape)
+    return p
+
+
+def test_forward_matches_oracle(ms):
+    X, Y = _data(0, 301)
+    norm = CO.normalisation(X, Y)
+    p = _params()
+    net = ms.MLP(p, norm, max_batch=128)          # 3 batches, the last ragged
+    got = net.predict(X)
+    ref = CO.predict(p, X, norm)
+    err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref - ref.mean(0), axis=0)
+    assert err.max() < 2e-2, err
+
+
+@pytest.mark.parametrize("B", [64, 1000, 5000])
+def test_gradients_match_oracle(ms, B):
+    """BF16 products with FP32 accumulation: each parameter's gradient within
+    2e-2 of the FP64 gradient (normwise)."""
+    X, Y = _data(1, B)
+    norm = CO.normalisation(X, Y)
+    p = _params()
+    net = ms.MLP(p, norm, max_batch=8192)
+    loss, g = net.grad(X, Y)
+    lref, gref = CO.loss_and_grads(p, X, Y, norm)
+    assert abs(loss - lref) <= 2e-2 * lref
+    for k in CO.NAMES:
+        e = np.linalg.norm(g[k] - gref[k]) / np.linalg.norm(gref[k])
+        assert e < 2e-2, (k, e)
+
+
+def test_adam_first_step(ms):
+    """The first Adam step moves each parameter by lr * g / (|g| + eps): the
+    same as the oracle's wherever the two gradients agree in sign."""
+    X, Y = _data(2, 512)
+    norm = CO.normalisation(X, Y)
+    p = _params()
+    net = ms.MLP(p, norm)
+    _, gref = CO.loss_and_grads(p, X, Y, norm)
+    net.step(X, Y, 1e-3)
+    q = net.params()
+    pr = {k: v.copy() for k, v in p.items()}
+    CO.adam_step(pr, gref, {}, lr=1e-3)
+    for k in CO.NAMES:
+        big = np.abs(gref[k]) > 1e-2 * np.abs(gref[k]).max()
+        d = np.abs(q[k] - pr[k])[big]
+        assert np.mean(d < 1e-6) > 0.97, (k, np.mean(d < 1e-6))
+
+
+def test_training_on_gpu_reduces_loss(ms):
+    X, Y = _data(3, 20000)
+    norm = CO.normalisation(X, Y)
+    net = ms.MLP(I.mlp_init(), norm, max_batch=4096)
+    losses = net.train(X, Y, epochs=25, batch=1024, lr=2e-3, seed=7)
+    assert losses[-1] < 0.1 * losses[0], losses
+    ref = CO.loss_and_grads(net.params(), X, Y, norm)[0]
+    assert abs(ref - losses[-1]) < 0.5 * losses[-1] + 1e-3
