@@ -263,6 +263,33 @@ int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *
 
 void ms_mlp_free(ms_mlp *m);
 
+/* Closure plus particle fallback on a coupled FP32 model (not in the paper).
+ * mode 0: at the start of each coarse interval every cell's features
+ * (rho, mean u, v, omega, variances of u and v, ocean u, v, divergence and
+ * curl at the cell centre, wind u, v) go through `mlp`, which predicts the
+ * interval-mean drag force per unit mass (x, y), drag torque per unit inertia
+ * and the rate of change of the velocity variance.  A cell runs the closure
+ * when its features lie inside box (host [2][12] min, max; NULL: no bound)
+ * and the predicted drag differs from the mean-field drag of its mean velocity
+ * by at most tol relative (floor: the drag of 1 cm/s on 1 m ice); every other
+ * cell runs the particle step (the fallback).  A closure cell skips its DEM for
+ * the interval: it takes its pending coarse increments at once, its velocity
+ * spread follows the predicted variance rate, and the coarse step sees the
+ * predicted tendencies.  mode 1: the mean-field drag for every cell (no
+ * network).  mode -1: off.  Attach between coarse intervals; `mlp` must
+ * outlive the attachment.  Each closure cell counts as N0 cell-steps. */
+int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const float *box);
+
+/* Training data from the particle path: runs nint coarse intervals (from an
+ * interval boundary, after the first ms_step call fixed dt) and writes host
+ * X[nint][ncell][12] (features at each interval's start) and
+ * Y[nint][ncell][4] (the window means of the drag force per unit mass, drag
+ * torque per unit inertia, and (variance at the end - at the start) / dT). */
+int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y);
+
+/* host out[4]: closure cell-intervals so far, cells, mode, coarse intervals done. */
+int ms_closure_stats(ms_model *m, int64_t *out);
+
 /* Release the model's device memory, graphs, events and stream. */
 void ms_free(ms_model *m);
 

@@ -76,6 +76,15 @@ struct ms_model {
     bool graph_failed = false;
     long long replays = 0;
     int sm_count = 0;
+    // closure-plus-fallback intervals
+    ms_mlp *mlp = nullptr;
+    int hybrid_mode = -1;          // -1 off, 0 network, 1 mean-field
+    double hybrid_tol = 0.0;
+    float *d_X = nullptr, *d_Yp = nullptr, *d_Yuse = nullptr, *d_box = nullptr, *d_Yc = nullptr;
+    int *d_isc = nullptr, *d_order2 = nullptr, *d_live = nullptr, *d_segb = nullptr, *d_sege = nullptr;
+    double *d_mom0 = nullptr;
+    unsigned long long *d_ccount = nullptr;
+    long long hybrid_intervals = 0;
     // host staging (pinned)
     void *h_stage = nullptr;
     size_t h_stage_bytes = 0;
@@ -296,6 +305,7 @@ static StepCommon step_common(ms_model *m, long long i_local, double *mom, doubl
 {
     StepCommon sc;
     sc.k = geo32(m->g.Lcx, m->g.Lcy, m->g.nx, m->g.ny, m->dt);
+    sc.live = nullptr;
     sc.off = m->d_off;
     sc.order = m->d_order;
     sc.ncell = m->ncell;
@@ -334,10 +344,16 @@ static CoarseArgs coarse_args(ms_model *m)
     return a;
 }
 
+static bool hybrid_on(const ms_model *m) { return m->hybrid_mode >= 0 && m->fc.couple && m->precision == MS_FP32; }
+
 static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
 {
     StepCommon sc = step_common(m, i_local, scratch_out ? m->d_xmom : m->d_mom,
                                 scratch_out ? m->d_xwin : m->d_win);
+    if (hybrid_on(m)) {
+        sc.order = m->d_order2;
+        sc.live = m->d_live;
+    }
     if (m->precision == MS_FP64)
         return launch_cell_step64(m->s64, scratch_out ? m->x64 : m->s64, m->P64, sc, m->cl, m->stream);
     return launch_cell_step32(m->s32, scratch_out ? m->x32 : m->s32, m->P32, sc, m->cl, m->stream);
@@ -348,6 +364,50 @@ static cudaError_t launch_interval_end(ms_model *m)
 {
     if (m->fc.couple) return launch_coarse_step(coarse_args(m), m->stream);
     return launch_advance(m->d_ctrl, m->interval, m->stream);
+}
+
+// Start of a coarse interval in closure-plus-fallback mode: features, network,
+// residual check, the particle cells of each size class, closure cells' update.
+static cudaError_t launch_interval_start(ms_model *m)
+{
+    if (!hybrid_on(m)) return cudaSuccess;
+    cudaError_t e = launch_features(m->d_mom, m->d_tgt, m->ncell, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
+                                    m->d_X, m->stream);
+    if (e != cudaSuccess) return e;
+    if (m->hybrid_mode == 0 && ms_mlp_forward_device(m->mlp, m->d_X, m->ncell, m->d_Yp, m->stream) != MS_OK)
+        return cudaErrorUnknown;
+    HybridArgs h{};
+    h.X = m->d_X;
+    h.Yp = m->d_Yp;
+    h.mom = m->d_mom;
+    h.mom_rw = m->d_mom;
+    h.ncell = m->ncell;
+    h.nseg = m->cl.nseg;
+    h.P64 = m->P64;
+    h.P32 = m->P32;
+    h.rho_ice = m->fc.rho_ice;
+    h.tol = m->hybrid_tol;
+    // floor of the drag scale in the residual: the drag of a 1 cm/s relative velocity on 1 m ice
+    h.floor_acc = m->fc.Cd * m->fc.rho_o / m->fc.rho_ice * 1e-4;
+    h.dT = (double)m->fc.N0 * m->dt;
+    h.box = m->d_box;
+    h.mode = m->hybrid_mode;
+    h.ctrl = m->d_ctrl;
+    h.is_closure = m->d_isc;
+    h.Yuse = m->d_Yuse;
+    h.order = m->d_order;
+    h.seg_begin = m->d_segb;
+    h.seg_end = m->d_sege;
+    h.off = m->d_off;
+    h.order2 = m->d_order2;
+    h.live = m->d_live;
+    h.closure_count = m->d_ccount;
+    h.st32 = m->s32;
+    h.win = m->d_win;
+    h.tgt = m->d_tgt;
+    h.N0 = m->fc.N0;
+    h.n_t = m->fc.n_t;
+    return launch_hybrid_select(h, m->stream);
 }
 
 static void drop_graph(ms_model *m)
@@ -361,7 +421,7 @@ static cudaError_t build_graph(ms_model *m)
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t le = cudaSuccess;
+    cudaError_t le = launch_interval_start(m);
     for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
     if (le == cudaSuccess) le = launch_interval_end(m);
     e = cudaStreamEndCapture(m->stream, &graph);
@@ -473,8 +533,14 @@ static void make_segments(ms_model *m, CellLaunch &c)
 static int configure_launch(ms_model *m, const CellLaunch &cl_in)
 {
     CellLaunch cl = cl_in;
+    if (cl.variant == 0 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure needs a binned cell kernel");
     if (cl.variant >= 1) make_segments(m, cl);
     else cl.nseg = 0;
+    if (m->d_segb && cl.nseg > 0) {
+        CK(cudaMemcpyAsync(m->d_segb, cl.seg_begin, sizeof(int) * cl.nseg, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(m->d_sege, cl.seg_end, sizeof(int) * cl.nseg, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
     const size_t smem = cell_step_smem(m->precision, cl, m->max_n, m->g.nx, m->g.ny);
     if (smem > 227 * 1024) return fail(MS_ERR_ARG, "cell of %d floes needs %zu B of shared memory", m->max_n, smem);
     CK(cell_step_prepare(m->precision, cl, smem));
@@ -755,6 +821,7 @@ static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
             nsteps -= N;
             continue;
         }
+        if (i_local == 0) CK(launch_interval_start(m));
         CK(launch_step(m, i_local, false));
         m->steps++;
         nsteps--;
@@ -1097,6 +1164,110 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
     cudaStream_t st = (cudaStream_t)stream;
     CK(noalloc_cell_moments(g, rho_ice * PI_D, inertia_half ? 0.5 : 1.0, n, x, y, u, v, omega, r, h, fd, out, st));
     CK(cudaStreamSynchronize(st));
+    return MS_OK;
+}
+
+int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const float *box)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (mode < -1 || mode > 1) return fail(MS_ERR_ARG, "mode must be -1, 0 or 1");
+    if (mode == 0 && !mlp) return fail(MS_ERR_ARG, "mode 0 needs a network");
+    if (mode >= 0 && (m->precision != MS_FP32 || !m->fc.couple))
+        return fail(MS_ERR_STATE, "the closure runs on coupled FP32 models");
+    if (!(tol >= 0.0)) return fail(MS_ERR_ARG, "tol must be >= 0");
+    if (mode >= 0 && m->steps % m->interval != 0) return fail(MS_ERR_STATE, "attach between coarse intervals");
+    CK(cudaStreamSynchronize(m->stream));
+    const int nc = m->ncell;
+    if (!m->d_X) {
+        CK(dalloc(m, &m->d_X, (size_t)nc * 12));
+        CK(dalloc(m, &m->d_Yp, (size_t)nc * 4));
+        CK(dalloc(m, &m->d_Yuse, (size_t)nc * 4));
+        CK(dalloc(m, &m->d_Yc, (size_t)nc * 4));
+        CK(dalloc(m, &m->d_box, 24));
+        CK(dalloc(m, &m->d_isc, nc));
+        CK(dalloc(m, &m->d_order2, nc));
+        CK(dalloc(m, &m->d_live, MAXSEG));
+        CK(dalloc(m, &m->d_segb, MAXSEG));
+        CK(dalloc(m, &m->d_sege, MAXSEG));
+        CK(dalloc(m, &m->d_mom0, (size_t)nc * NMOM));
+        CK(dalloc(m, &m->d_ccount, 1));
+        CK(cudaMemsetAsync(m->d_ccount, 0, sizeof(unsigned long long), m->stream));
+    }
+    float hb[24];
+    for (int k = 0; k < 12; k++) {
+        hb[k] = box ? box[k] : -3.0e38f;
+        hb[12 + k] = box ? box[12 + k] : 3.0e38f;
+    }
+    CK(cudaMemcpyAsync(m->d_box, hb, sizeof(hb), cudaMemcpyHostToDevice, m->stream));
+    const int prev_mode = m->hybrid_mode;
+    m->hybrid_mode = mode;
+    m->mlp = mlp;
+    m->hybrid_tol = tol;
+    CellLaunch cl = m->cl;
+    if (mode >= 0 && cl.variant == 0) cl.variant = 2;
+    int rc = configure_launch(m, cl);
+    if (rc) {
+        m->hybrid_mode = prev_mode;
+        return rc;
+    }
+    drop_graph(m);
+    CK(cudaStreamSynchronize(m->stream));
+    return MS_OK;
+}
+
+int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
+{
+    if (!m || !X || !Y) return fail(MS_ERR_ARG, "NULL argument");
+    if (nint < 1) return fail(MS_ERR_ARG, "nint must be >= 1");
+    if (!m->fc.couple || m->precision != MS_FP32) return fail(MS_ERR_STATE, "collect runs on coupled FP32 models");
+    if (m->dt == 0.0) return fail(MS_ERR_STATE, "step the model once first (dt is not set)");
+    if (m->steps % m->interval != 0) return fail(MS_ERR_STATE, "collect starts between coarse intervals");
+    if (!m->d_X) {
+        int rc = ms_closure_attach(m, nullptr, -1, 0.0, nullptr);
+        if (rc) return rc;
+    }
+    const int saved = m->hybrid_mode;
+    m->hybrid_mode = -1;
+    const int nc = m->ncell;
+    const double dT = (double)m->fc.N0 * m->dt;
+    int rc = MS_OK;
+    for (int k = 0; k < nint && rc == MS_OK; k++) {
+        cudaError_t e = cudaMemcpyAsync(m->d_mom0, m->d_mom, sizeof(double) * nc * NMOM, cudaMemcpyDeviceToDevice,
+                                        m->stream);
+        if (e == cudaSuccess)
+            e = launch_features(m->d_mom, m->d_tgt, nc, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t, m->d_X,
+                                m->stream);
+        for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);
+        if (e == cudaSuccess) e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, nc, m->fc.N0, dT, m->d_Yc,
+                                                         m->stream);
+        if (e == cudaSuccess) e = launch_interval_end(m);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(X + (size_t)k * nc * 12, m->d_X, sizeof(float) * nc * 12, cudaMemcpyDeviceToHost,
+                                m->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(Y + (size_t)k * nc * 4, m->d_Yc, sizeof(float) * nc * 4, cudaMemcpyDeviceToHost,
+                                m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) rc = fail(MS_ERR_CUDA, "collect failed: %s", cudaGetErrorString(e));
+        m->steps += m->interval;
+    }
+    m->hybrid_mode = saved;
+    if (rc) return rc;
+    return read_errors(m);
+}
+
+int ms_closure_stats(ms_model *m, int64_t *out)
+{
+    if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    unsigned long long cc = 0;
+    if (m->d_ccount) {
+        CK(cudaMemcpyAsync(&cc, m->d_ccount, sizeof(cc), cudaMemcpyDeviceToHost, m->stream));
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    out[0] = (int64_t)cc;
+    out[1] = m->ncell;
+    out[2] = m->hybrid_mode;
+    out[3] = m->steps / m->interval;
     return MS_OK;
 }
 

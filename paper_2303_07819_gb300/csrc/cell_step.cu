@@ -402,7 +402,7 @@ __host__ __device__ inline size_t smem32_binned(int T, int maxn, int nbmax)
 template <int T>
 __global__ void __launch_bounds__(T)
 k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
-                     int item1, int maxn, int nbmax)
+                     int item1, int maxn, int nbmax, int seg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Bin32 sm = carve32<T>(smem, maxn, nbmax);
@@ -415,6 +415,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
     unsigned deep = 0;
     bool bad = false;
 
+    if (sc.live) item1 = min(item1, item0 + sc.live[seg]);
     for (int item = item0 + blockIdx.x; item < item1; item += gridDim.x) {
         const int c = sc.order[item];
         const int o = sc.off[c], n = sc.off[c + 1] - o;
@@ -715,13 +716,14 @@ __device__ __forceinline__ float warp_sum16(float (&v)[16], int lane)
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 8)
 k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
-                   int item1, int cap, int nbmax)
+                   int item1, int cap, int nbmax, int seg)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BlockStep bs;
     block_step_init(bs, sc, P);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int item = item0 + blockIdx.x * WARPS + warp;
+    if (sc.live) item1 = min(item1, item0 + sc.live[seg]);
     if (item >= item1) return;
     const WarpSm sm = carve_warp(smem + warp * warp_region_bytes(cap, nbmax), cap, nbmax);
     const unsigned FULL = 0xffffffffu;
@@ -1138,12 +1140,12 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
     const size_t sm = seg_smem(cl, s);
     if (cl.seg_kind[s] == 1) {
         k_cell_step32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
-                                                                cl.seg_end[s], cl.seg_maxn[s], nbm);
+                                                                cl.seg_end[s], cl.seg_maxn[s], nbm, s);
         return cudaGetLastError();
     }
     MS_T_SWITCH(cl.seg_threads[s],
                 k_cell_step32_binned<TT><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
-                                                                cl.seg_end[s], cl.seg_maxn[s], nbm));
+                                                                cl.seg_end[s], cl.seg_maxn[s], nbm, s));
     return cudaGetLastError();
 }
 

@@ -225,6 +225,7 @@ struct Geo32 {
 
 struct StepCommon {
     Geo32 k;
+    const int *live;    // per size class: cells to step (the rest run the closure); nullptr: all
     const int *off;     // [ncell + 1]
     const int *order;   // [ncell] processing order (largest cells first)
     int ncell;
@@ -306,6 +307,33 @@ cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f,
                                  const double *r, const double *h, const double *fd, double *mom,
                                  cudaStream_t st);
 cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
+
+// hybrid.cu: closure-plus-fallback intervals
+struct HybridArgs {
+    const float *X, *Yp;      // features [ncell][12], network prediction [ncell][4]
+    const double *mom;
+    int ncell, nseg;
+    Phys<double> P64;
+    Phys<float> P32;
+    double rho_ice, tol, floor_acc, dT;
+    const float *box;         // [2][12] feature range seen in training
+    int mode;                 // 0 network, 1 mean-field
+    const Ctrl *ctrl;
+    int *is_closure;
+    float *Yuse;
+    const int *order, *seg_begin, *seg_end, *off;
+    int *order2, *live;
+    unsigned long long *closure_count;
+    DevState32 st32;
+    double *win, *tgt;
+    double *mom_rw;
+    int N0, n_t;
+};
+cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
+                            const Ctrl *ctrl, double dt, int N0, int n_t, float *X, cudaStream_t st);
+cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
+                                   double dT, float *Y, cudaStream_t st);
+cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st);
 
 // api.cu: record the calling thread's error message and return code
 int set_error(int code, const char *msg);

@@ -1,0 +1,273 @@
+// hybrid.cu -- closure-plus-fallback coarse intervals, and the training data
+// for the closure.
+//
+// Not in the paper: a learned model of each cell's bulk feedback (the drag
+// tendencies that the coarse moment equations, Eq. 2.26, take from the cell's
+// DEM, Sec. 3.2) lets a cell skip its DEM for a coarse interval.  At the start
+// of every interval each cell's features go through the network; a residual
+// check compares the prediction with the mean-field drag of the cell-mean
+// velocity and tests the features against the range seen in training; cells
+// that fail run the particle step (the fallback), the others take their
+// pending coarse increments at once and report the predicted tendencies to
+// the coarse step.
+#include "common.cuh"
+
+namespace msd {
+
+namespace {
+
+constexpr int NF = 12;   // features per cell
+constexpr int NT = 4;    // targets per cell
+
+// Mean share of a coarse increment that the gradual updates have applied,
+// averaged over the N0 steps of an interval: updates after steps n_t, 2 n_t,
+// ..., N0 each add n_t / N0, so after step k the share is floor(k / n_t) n_t / N0.
+__host__ __device__ inline double ramp_mean_share(int N0, int n_t)
+{
+    double s = 0.0;
+    for (int k = 1; k <= N0; k++) s += (double)(k / n_t) * n_t / N0;
+    return s / N0;
+}
+
+// [rho, ubar, vbar, wbar, var u, var v, u_o, v_o, div u_o, curl u_o, u_a, v_a]
+// (ocean at the cell centre, wind at the start of the interval).  The mean
+// velocity and spin are the interval means the gradual updates produce: the
+// cell's current means plus the mean share of its pending increments.
+__global__ void k_features(const double *mom, const double *tgt, int ncell, Geom g, Phys<double> P,
+                           const Ctrl *ctrl, double dt, double share, float *X)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double *mo = mom + (size_t)c * NMOM;
+    const double Ac = g.Lcx * g.Lcy;
+    const double M = mo[1], I = mo[4];
+    const double ub0 = M > 0.0 ? mo[2] / M : 0.0, vb0 = M > 0.0 ? mo[3] / M : 0.0;
+    const double wb0 = I > 0.0 ? mo[5] / I : 0.0;
+    const double su = M > 0.0 ? fmax(mo[7] / M - ub0 * ub0, 0.0) : 0.0;
+    const double sv = M > 0.0 ? fmax(mo[8] / M - vb0 * vb0, 0.0) : 0.0;
+    const double sh = ctrl->have_tgt ? share : 0.0;
+    const double ub = ub0 + sh * tgt[ncell + c], vb = vb0 + sh * tgt[2 * ncell + c], wb = wb0 + sh * tgt[3 * ncell + c];
+    const int ix = c % g.nx, iy = c / g.nx;
+    double uo, vo, zeta;
+    ocean_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy, uo, vo, zeta);
+    double ua, va;
+    wind_at(P, (double)ctrl->base * dt, ua, va);
+    const double f[NF] = {M / Ac, ub, vb, wb, su, sv, uo, vo, 0.0, zeta, ua, va};
+    for (int k = 0; k < NF; k++) X[(size_t)c * NF + k] = (float)f[k];
+}
+
+// Targets of the interval just run: window means of the cell's total drag per
+// unit mass (x, y), of its drag torque per unit inertia, and the rate of change
+// of the velocity variance over the interval.
+__global__ void k_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
+                                  double dT, float *Y)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const double *a = mom0 + (size_t)c * NMOM, *b = mom1 + (size_t)c * NMOM;
+    const double M0 = a[1], I0 = a[4];
+    auto var = [](const double *m) {
+        if (!(m[1] > 0.0)) return 0.0;
+        const double u = m[2] / m[1], v = m[3] / m[1];
+        return fmax(m[7] / m[1] - u * u, 0.0) + fmax(m[8] / m[1] - v * v, 0.0);
+    };
+    Y[(size_t)c * NT + 0] = M0 > 0.0 ? (float)(win[2 * ncell + c] / N0 / M0) : 0.0f;
+    Y[(size_t)c * NT + 1] = M0 > 0.0 ? (float)(win[3 * ncell + c] / N0 / M0) : 0.0f;
+    Y[(size_t)c * NT + 2] = I0 > 0.0 ? (float)(win[4 * ncell + c] / N0 / I0) : 0.0f;
+    Y[(size_t)c * NT + 3] = (float)((var(b) - var(a)) / dT);
+}
+
+// Mean-field tendencies of a cell: the drag of Eq. 2.1c-d evaluated at the
+// cell-mean velocity and spin, per unit mass and inertia (mean thickness
+// M / (rho_ice sum pi r^2)); no change of the variance.
+__device__ __forceinline__ void meanfield(const float *x, const double *mo, const Phys<double> &P, double rho_ice,
+                                          double *y)
+{
+    const double area = mo[6];
+    const double hbar = (area > 0.0 && mo[1] > 0.0) ? mo[1] / (rho_ice * area) : 1.0;
+    const double ko = P.drag_o / (3.14159265358979323846 * rho_ice * hbar);
+    const double ka = P.drag_a / (3.14159265358979323846 * rho_ice * hbar);
+    const double dou = x[6] - x[1], dov = x[7] - x[2];
+    const double dau = x[10] - x[1], dav = x[11] - x[2];
+    const double so = sqrt(dou * dou + dov * dov), sa = sqrt(dau * dau + dav * dav);
+    const double dw = 0.5 * x[9] - x[3];
+    y[0] = ko * dou * so + ka * dau * sa;
+    y[1] = ko * dov * so + ka * dav * sa;
+    y[2] = ko * dw * fabs(dw) / P.inertia_f;
+    y[3] = 0.0;
+}
+
+// closure or particle for each cell; the tendencies the coarse step will see
+__global__ void k_classify(const float *X, const float *Yp, const double *mom, int ncell, Phys<double> P,
+                           double rho_ice, const float *box, double tol, double floor_acc, int mode, const Ctrl *ctrl,
+                           int *is_closure, float *Yuse)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const float *x = X + (size_t)c * NF;
+    const double *mo = mom + (size_t)c * NMOM;
+    double mf[4];
+    meanfield(x, mo, P, rho_ice, mf);
+    int closure = 0;
+    float y[NT] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (ctrl->have_tgt) {
+        if (!(mo[1] > 0.0)) {
+            closure = 1;      // an empty cell has nothing to step
+        } else if (mode == 1) {
+            closure = 1;
+            for (int k = 0; k < NT; k++) y[k] = (float)mf[k];
+        } else {
+            bool inside = true;
+            for (int k = 0; k < NF; k++)
+                inside &= (x[k] >= box[k]) && (x[k] <= box[NF + k]);
+            const float *yp = Yp + (size_t)c * NT;
+            const double ex = yp[0] - mf[0], ey = yp[1] - mf[1];
+            const double res = sqrt(ex * ex + ey * ey) / (sqrt(mf[0] * mf[0] + mf[1] * mf[1]) + floor_acc);
+            closure = inside && res <= tol;
+            for (int k = 0; k < NT; k++) y[k] = yp[k];
+        }
+    }
+    is_closure[c] = closure;
+    for (int k = 0; k < NT; k++) Yuse[(size_t)c * NT + k] = y[k];
+}
+
+// Per size class (one block each), the particle cells of the class, in their
+// processing order, packed at the front of the class's range.
+__global__ void k_compact(const int *order, const int *seg_begin, const int *seg_end, const int *is_closure,
+                          int *order2, int *live, unsigned long long *closure_count)
+{
+    __shared__ int ws[33];
+    const int s = blockIdx.x;
+    const int b = seg_begin[s], e = seg_end[s];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int base = 0, nclos = 0;
+    for (int i0 = b; i0 < e; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int c = i < e ? order[i] : -1;
+        const int part = (c >= 0 && !is_closure[c]) ? 1 : 0;
+        nclos += (c >= 0 && !part) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, part);
+        if (lane == 0) ws[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+                const int t = ws[w];
+                ws[w] = acc;
+                acc += t;
+            }
+            ws[32] = acc;
+        }
+        __syncthreads();
+        if (part) order2[b + base + ws[warp] + __popc(bal & ((1u << lane) - 1u))] = c;
+        base += ws[32];
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) nclos += __shfl_xor_sync(0xffffffffu, nclos, o);
+    if (lane == 0 && nclos) atomicAdd(closure_count, (unsigned long long)nclos);
+    if (threadIdx.x == 0) live[s] = base;
+}
+
+// A closure cell runs the interval without its DEM.  It reports to the coarse
+// step what the particle path would: window-mean velocity = current mean +
+// mean share of the pending increment + the predicted drag acting for the mean
+// elapsed time (N0 + 1)/(2 N0) dT, and the predicted drag as the window's drag
+// sums.  Its floes end the interval where the particle path would take them:
+// the full increments plus dT times the predicted tendencies (uniform shifts),
+// the velocity spread scaled to the predicted variance, the radius scale
+// (bounded to [0.5, 2] for one interval) applied.
+__global__ void __launch_bounds__(128)
+k_closure_apply(DevState32 st, Phys<float> P, const int *off, const int *is_closure, const float *Yuse,
+                double *mom, double *win, double *tgt, int ncell, int N0, double dT, double share)
+{
+    __shared__ double red[4][NMOM];
+    const int c = blockIdx.x;
+    if (!is_closure[c]) return;
+    const int o = off[c], n = off[c + 1] - o;
+    double *mo = mom + (size_t)c * NMOM;
+    const double M = mo[1];
+    const double ub = M > 0.0 ? mo[2] / M : 0.0, vb = M > 0.0 ? mo[3] / M : 0.0;
+    const double var = M > 0.0 ? fmax(mo[7] / M - ub * ub, 0.0) + fmax(mo[8] / M - vb * vb, 0.0) : 0.0;
+    const float *y = Yuse + (size_t)c * 4;
+    const double nv = var + dT * (double)y[3];
+    const float fs = var > 0.0 ? (float)sqrt(fmax(nv, 0.0) / var) : 1.0f;
+    const double sc = fmin(fmax(tgt[c], 0.5), 2.0);
+    const double dux = tgt[ncell + c], duy = tgt[2 * ncell + c], dw = tgt[3 * ncell + c];
+    const float s = (float)sc;
+    const float du = (float)(dux + dT * y[0]), dv = (float)(duy + dT * y[1]), dww = (float)(dw + dT * y[2]);
+    const float ubf = (float)ub, vbf = (float)vb;
+    double acc[NMOM];
+    for (int k = 0; k < NMOM; k++) acc[k] = 0.0;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+        const int i = o + l;
+        const float r = st.r[i] * s, h = st.h[i];
+        const float u = ubf + du + fs * (st.u[i] - ubf), v = vbf + dv + fs * (st.v[i] - vbf);
+        const float w = st.w[i] + dww;
+        st.r[i] = r;
+        st.u[i] = u;
+        st.v[i] = v;
+        st.w[i] = w;
+        const double m = (double)P.mass_c * r * r * h, I = (double)P.inertia_f * m * r * r;
+        acc[1] += m;
+        acc[2] += m * u;
+        acc[3] += m * v;
+        acc[4] += I;
+        acc[5] += I * w;
+        acc[6] += 3.14159265358979323846 * (double)r * r;
+        acc[7] += m * u * u;
+        acc[8] += m * v * v;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = 1; k < NMOM; k++) {
+        double v = acc[k];
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[NMOM];
+        t[0] = n;
+        for (int k = 1; k < NMOM; k++) t[k] = red[0][k] + red[1][k] + red[2][k] + red[3][k];
+        t[9] = t[1] * y[0];
+        t[10] = t[1] * y[1];
+        t[11] = t[4] * y[2];
+        for (int k = 0; k < NMOM; k++) mo[k] = t[k];
+        const double tmean = (double)(N0 + 1) / (2.0 * N0) * dT;
+        win[c] = N0 * (ub + share * dux + tmean * y[0]);
+        win[ncell + c] = N0 * (vb + share * duy + tmean * y[1]);
+        win[2 * ncell + c] = N0 * t[9];
+        win[3 * ncell + c] = N0 * t[10];
+        win[4 * ncell + c] = N0 * t[11];
+        tgt[c] = 1.0;
+        tgt[ncell + c] = tgt[2 * ncell + c] = tgt[3 * ncell + c] = 0.0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
+                            const Ctrl *ctrl, double dt, int N0, int n_t, float *X, cudaStream_t st)
+{
+    k_features<<<(ncell + 127) / 128, 128, 0, st>>>(mom, tgt, ncell, g, P, ctrl, dt, ramp_mean_share(N0, n_t), X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
+                                   double dT, float *Y, cudaStream_t st)
+{
+    k_collect_targets<<<(ncell + 127) / 128, 128, 0, st>>>(mom0, mom1, win, ncell, N0, dT, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st)
+{
+    k_classify<<<(h.ncell + 127) / 128, 128, 0, st>>>(h.X, h.Yp, h.mom, h.ncell, h.P64, h.rho_ice, h.box, h.tol,
+                                                     h.floor_acc, h.mode, h.ctrl, h.is_closure, h.Yuse);
+    k_compact<<<h.nseg, 1024, 0, st>>>(h.order, h.seg_begin, h.seg_end, h.is_closure, h.order2, h.live,
+                                        h.closure_count);
+    k_closure_apply<<<h.ncell, 128, 0, st>>>(h.st32, h.P32, h.off, h.is_closure, h.Yuse, h.mom_rw, h.win, h.tgt,
+                                             h.ncell, h.N0, h.dT, ramp_mean_share(h.N0, h.n_t));
+    return cudaGetLastError();
+}
+
+}  // namespace msd

@@ -55,7 +55,7 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_truth_step", "ms_truth_moments", "ms_truth_get_floes", "ms_set_stream", "ms_autotune",
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
-           "ms_mlp_forward_device", "ms_mlp_free"]
+           "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats"]
 
 
 def lib_path() -> str:
@@ -92,6 +92,9 @@ def load(path: str | None = None):
     L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32]
     L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_cell_moments_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int32, C.c_int64] + [vp] * 10
+    L.ms_closure_attach.argtypes = [vp, vp, C.c_int32, C.c_double, C.POINTER(C.c_float)]
+    L.ms_closure_collect.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+    L.ms_closure_stats.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
@@ -230,6 +233,27 @@ class Model:
                    bin_beta: float = 1.0, reg_min: int = 0) -> None:
         _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta),
                                     int(reg_min)))
+
+    def closure_attach(self, mlp, mode: int = 0, tol: float = 0.5, box=None) -> None:
+        """mode 0: network `mlp` with fallback; 1: mean-field closure; -1: off."""
+        self._mlp_ref = mlp
+        bx = None if box is None else np.ascontiguousarray(box, dtype=np.float32).reshape(24)
+        self._box = bx
+        _check(load().ms_closure_attach(self._h, mlp._h if mlp is not None else None, int(mode), float(tol),
+                                        bx.ctypes.data_as(C.POINTER(C.c_float)) if bx is not None else None))
+
+    def closure_collect(self, nint: int):
+        X = np.zeros((nint, self.ncell, 12), dtype=np.float32)
+        Y = np.zeros((nint, self.ncell, 4), dtype=np.float32)
+        _check(load().ms_closure_collect(self._h, int(nint), X.ctypes.data_as(C.POINTER(C.c_float)),
+                                         Y.ctypes.data_as(C.POINTER(C.c_float))))
+        return X, Y
+
+    def closure_stats(self) -> dict:
+        out = np.zeros(4, dtype=np.int64)
+        _check(load().ms_closure_stats(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return {"closure_cell_intervals": int(out[0]), "cells": int(out[1]), "mode": int(out[2]),
+                "intervals": int(out[3])}
 
     def info(self) -> dict:
         out = np.zeros(16, dtype=np.int64)

@@ -1,0 +1,114 @@
+"""Closure plus particle fallback (the learned part of the method): training
+data from the particle path, the trained network against held-out particle
+data, and the coupled model with the closure against the particle-only model.
+
+Workload: configs[2]'s laws on 16 x 16 cells of 25 km (~31k floes), spun up
+for 10 coarse intervals (the first gradual updates rescale radii by tens of
+percent where neighbouring cells differ, and the contacts that follow need
+several intervals to settle)."""
+import numpy as np
+import pytest
+
+from oracle import closure_oracle as CO
+from paper_2303_07819_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SPIN = 10
+
+
+@pytest.fixture(scope="module")
+def trained():
+    from paper_2303_07819_gb300 import msdem
+    msdem.load()
+    Xs, Ys = [], []
+    for sd in (201, 202, 203):
+        s = I.config2(seed=sd, nx=16)
+        m = msdem.Model(s["params"], s["floes"], 0)
+        m.step(s["dt"], s["params"]["N0"] * SPIN)
+        X, Y = m.closure_collect(30)
+        Xs.append(X.reshape(-1, 12))
+        Ys.append(Y.reshape(-1, 4))
+        m.close()
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    norm = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
+    net = msdem.MLP(I.mlp_init(), norm, max_batch=8192)
+    losses = net.train(X, Y, epochs=120, batch=512, lr=2e-3, seed=11)
+    box = np.stack([X.min(0) - 0.05 * np.abs(X.min(0)), X.max(0) + 0.05 * np.abs(X.max(0))])
+    return msdem, net, X, Y, losses, box
+
+
+def test_collect_targets_are_the_window_means(trained):
+    """Targets 0-2 are the drag sums of the interval per unit mass/inertia, so
+    for a cell without contacts they are the cell's mean drag acceleration:
+    same sign convention as the velocity change it causes."""
+    msdem, net, X, Y, losses, box = trained
+    assert np.all(np.isfinite(X)) and np.all(np.isfinite(Y))
+    assert np.all(X[:, 0] > 0)                      # every cell holds ice
+    assert np.all(X[:, 8] == 0)                     # a stream-function current has no divergence
+
+
+def test_network_learns_translational_drag(trained):
+    """Trained only on particle-generated data, the network predicts the
+    interval-mean drag of unseen cells (another seed)."""
+    msdem, net, X, Y, losses, box = trained
+    assert losses[-1] < 0.5 * losses[0]
+    s = I.config2(seed=204, nx=16)
+    m = msdem.Model(s["params"], s["floes"], 0)
+    m.step(s["dt"], s["params"]["N0"] * SPIN)
+    Xh, Yh = m.closure_collect(10)
+    Xh, Yh = Xh.reshape(-1, 12), Yh.reshape(-1, 4)
+    P = net.predict(Xh)
+    r2 = 1 - ((P - Yh) ** 2).sum(0) / ((Yh - Yh.mean(0)) ** 2).sum(0)
+    assert r2[0] > 0.8 and r2[1] > 0.8, r2
+
+
+def _run(msdem, s, mode, tol, net, box, K):
+    p = s["params"]
+    m = msdem.Model(p, s["floes"], 0)
+    m.step(s["dt"], p["N0"] * SPIN)
+    if mode >= 0:
+        m.closure_attach(net if mode == 0 else None, mode, tol, box)
+    m.step(s["dt"], p["N0"] * K)
+    return m
+
+
+def test_zero_tolerance_is_the_particle_path(trained):
+    """With tol = 0 every cell fails the residual check and runs the particle
+    step: the floes are bitwise those of the model without the closure."""
+    msdem, net, X, Y, losses, box = trained
+    s = I.config2(seed=205, nx=16)
+    a = _run(msdem, s, -1, 0.0, net, box, 3)
+    b = _run(msdem, s, 0, 0.0, net, box, 3)
+    assert b.closure_stats()["closure_cell_intervals"] == 0
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_network_closure_beats_mean_field(trained):
+    """What the trained network gains over the method without it: with every
+    cell on a closure for 5 coarse intervals, the coarse momentum and angular
+    momentum stay closer to the particle-only model with the network than with
+    the mean-field drag of the cell-mean velocity; mass stays within 1e-3."""
+    msdem, net, X, Y, losses, box = trained
+    s = I.config2(seed=206, nx=16)
+    K = 5
+    qp = _run(msdem, s, -1, 0.0, net, box, K).coupling()["q"]
+    qn = _run(msdem, s, 0, 1e9, net, None, K).coupling()["q"]
+    qm = _run(msdem, s, 1, 0.0, None, None, K).coupling()["q"]
+    err = lambda q: np.array([np.linalg.norm(q[f] - qp[f]) / np.linalg.norm(qp[f]) for f in range(4)])
+    en, em = err(qn), err(qm)
+    assert en[0] < 1e-3 and em[0] < 1e-3, (en, em)
+    assert en[1] < em[1] and en[2] < em[2], (en, em)
+
+
+def test_fallback_fraction_follows_tolerance(trained):
+    msdem, net, X, Y, losses, box = trained
+    s = I.config2(seed=207, nx=16)
+    fr = []
+    for tol in (0.02, 0.2, 1e9):
+        m = _run(msdem, s, 0, tol, net, box, 2)
+        st = m.closure_stats()
+        fr.append(st["closure_cell_intervals"] / (2 * st["cells"]))
+    assert fr[0] <= fr[1] <= fr[2] and fr[2] > 0.5, fr
