@@ -628,7 +628,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
 // The same lane finds a floe's contacts and advances it, so the force stays
 // in registers; the floe is written back to its own global slot.
 
-constexpr int MAXC = 24;   // contacts a lane collects before computing their forces
+constexpr int MAXC = 12;   // contacts a lane collects before computing their forces
 
 __host__ __device__ inline size_t warp_region_bytes(int cap, int nbmax)
 {
