@@ -44,6 +44,91 @@ def peaks():
     return HBM_FALLBACK_GBS, "fallback", {}
 
 
+def profile_traffic():
+    """DRAM bytes per fine step of the cell-step kernels from the committed
+    ncu summary, if the kernel sources have not changed since (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "cell_step32_config2.txt")
+    if not os.path.exists(path):
+        return None, None
+    rec = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in ("cell_step.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2303_07819_gb300", "csrc", f), "rb").read())
+    if h.hexdigest()[:16] != rec.get("sources_sha256_16"):
+        return None, rec
+    return float(rec["dram_bytes_read_per_fine_step"]) + float(rec["dram_bytes_write_per_fine_step"]), rec
+
+
+def closure_eval(msdem, seeds=(101, 102, 103, 105), nx=32, spin=15, nint=25, K=10):
+    """The learned closure on a 32 x 32-cell version of the workload: training
+    data from the particle path (after spin-up), GPU training, then K coarse
+    intervals of the particle-only model against the closure-plus-fallback
+    model (network) and the mean-field closure, from the same state."""
+    from oracle import closure_oracle as CO
+    from paper_2303_07819_gb300 import inputs as I
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    for sd in seeds:
+        ss = I.config2(seed=sd, nx=nx)
+        m = msdem.Model(ss["params"], ss["floes"], msdem.MS_FP32)
+        m.step(ss["dt"], ss["params"]["N0"] * spin)
+        X, Y = m.closure_collect(nint)
+        Xs.append(X.reshape(-1, 12)); Ys.append(Y.reshape(-1, 4))
+        m.close()
+    X, Y = np.concatenate(Xs), np.concatenate(Ys)
+    norm = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
+    net = msdem.MLP(I.mlp_init(), norm, max_batch=8192)
+    tt = time.perf_counter()
+    losses = net.train(X, Y, epochs=150, batch=1024, lr=2e-3, seed=3)
+    t_train = time.perf_counter() - tt
+    s = I.config2(seed=100, nx=nx)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    m = msdem.Model(p, s["floes"], msdem.MS_FP32)
+    m.step(dt, N0 * spin)
+    Xh, Yh = m.closure_collect(10)
+    Xh, Yh = Xh.reshape(-1, 12), Yh.reshape(-1, 4)
+    P = net.predict(Xh)
+    r2 = 1 - ((P - Yh) ** 2).sum(0) / ((Yh - Yh.mean(0)) ** 2).sum(0)
+    m.close()
+    box = np.stack([X.min(0) - 0.05 * np.abs(X.min(0)), X.max(0) + 0.05 * np.abs(X.max(0))])
+
+    def run(mode, tol):
+        mm = msdem.Model(p, s["floes"], msdem.MS_FP32)
+        mm.step(dt, N0 * spin)
+        if mode >= 0:
+            mm.closure_attach(net if mode == 0 else None, mode, tol, box if mode == 0 else None)
+        mm.step(dt, N0)                       # builds the interval graph
+        c0 = mm.closure_stats()["closure_cell_intervals"]
+        ta = time.perf_counter()
+        mm.step(dt, N0 * K)
+        el = time.perf_counter() - ta
+        st = mm.closure_stats()
+        q = mm.coupling()["q"]
+        mm.close()
+        return q, el, (st["closure_cell_intervals"] - c0) / (st["cells"] * K)
+
+    qp, tp, _ = run(-1, 0.0)
+    cells = p["nx"] * p["ny"]
+    out = {"workload": f"{nx}x{nx} cells of 25 km, config2 laws, spun up {spin} coarse intervals, {K} intervals timed",
+           "train_samples": int(X.shape[0]), "train_seconds": t_train, "loss_first_last": [losses[0], losses[-1]],
+           "heldout_r2": [float(v) for v in r2],
+           "particle": {"cell_steps_per_s": cells * N0 * K / tp}}
+    names = ["rho", "rho_u", "rho_v", "P_omega"]
+    for label, mode, tol in (("network_tol_0.05", 0, 0.05), ("network_all", 0, 1e9), ("mean_field_all", 1, 0.0)):
+        q, t, frac = run(mode, tol)
+        err = {n: float(np.linalg.norm(q[f] - qp[f]) / np.linalg.norm(qp[f])) for f, n in enumerate(names)}
+        out[label] = {"closure_fraction": frac, "cell_steps_per_s": cells * N0 * K / t, "speedup": tp / t,
+                      "coarse_state_rel_err": err}
+    out["seconds"] = time.perf_counter() - t0
+    net.close()
+    return out
+
+
 def load_scenario(cfg: int):
     from paper_2303_07819_gb300 import inputs as I
     cache = os.path.join(tempfile.gettempdir(), f"msdem_inputs_cfg{cfg}_{I.BASE_SEED}.npz")
@@ -266,6 +351,7 @@ def main():
     cell_rate = world * ncell * fine_steps / (tot_ms / 1e3)
 
     hbm, peak_kind, _ = peaks()
+    traffic, prof = profile_traffic()
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
     kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
     achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
@@ -277,7 +363,7 @@ def main():
         "data": "synthetic", "cell_steps_per_s": cell_rate,
         "config": workload_config(s, "flushed before every timed step (512 MB write); state 64 MB"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
+                     "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "msd::k_cell_step32", "peak_source": peak_kind,
                      "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
                      "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso},
@@ -307,6 +393,7 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{ncells} random cells ({n} floes) x {steps} fine steps, "
                                           f"{tdt:.1f} s wall, FP64, OpenMP over cells"}
+        line["closure"] = closure_eval(msdem)
     model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
