@@ -163,32 +163,37 @@ int ms_truth_get_floes(ms_model *m, double *out);
 int ms_set_stream(ms_model *m, void *stream);
 
 /* Autotune the msDEM cell kernel on the model's current state: times each
- * launch variant (pair search, threads per block, bin width) for `reps`
- * launches out of place (the state is not changed) and keeps the fastest.
- * best_ms (host, may be NULL) receives its mean launch time. */
+ * launch variant (pair search, threads per block, bin width) out of place
+ * (the state is not changed) and keeps the fastest.  FP32 candidates are
+ * timed over `reps` whole coarse intervals (ms_time_kernel which = 2), FP64
+ * ones over `reps` single steps.  best_ms (host, may be NULL) receives the
+ * fastest mean time per fine step. */
 int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
 
 /* Choose the cell-kernel launch by hand: variant 0 = brute-force pairs within
  * the cell, 1 = binned pair search (FP32 only); threads per block 64, 128 or
  * 256; persistent = 1 runs a grid of resident blocks that take cells from a
  * work queue (largest cells first); bin_beta = bin side in units of the cell's
- * mean floe spacing (variants 1, 2); variant 2 = binned, one warp per cell of
- * up to 256 floes and a block per larger cell, the two on concurrent streams;
- * reg_min = in variant 2, register large floes in the bins they reach when
- * (large floes x small floes) of a cell is at least this (0: keep current).
+ * mean floe spacing (variants 1-3); variant 2 = binned, one warp per cell of
+ * up to 256 floes and a block per larger cell, the size classes on concurrent
+ * streams; variant 3 = variant 2 with each warp keeping its cell in shared
+ * memory for a whole coarse interval (one launch per interval instead of one
+ * per fine step; the per-step arithmetic of variant 2, and the same results
+ * whether an interval runs in one launch or step by step).
  * MS_ERR_ARG for an unsupported choice. */
-int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta,
-                  int32_t reg_min);
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
 
 /* Mean device time (ms, CUDA events on the model's stream) of `reps`
- * out-of-place launches of the msDEM cell-step kernel (which = 0) or of the
- * truth step kernel (which = 1) on the current state; the state is not
- * changed. */
+ * out-of-place runs on the current state, which the runs do not change:
+ * which = 0, one fine step of the msDEM cell kernels; 1, one truth step;
+ * 2, the cell kernels of one whole coarse interval (N0 fine steps from the
+ * interval's first step, no coarse step). */
 int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *mean_ms);
 
 /* Model facts, host out[16] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
  * 4 kernel variant, 5 threads per block, 6 bin width (per mille of the mean
- * floe spacing), 7 kernels launched per fine step (msDEM, no coarse step),
+ * floe spacing), 7 cell-kernel launches per coarse interval (msDEM, whole
+ * intervals, no coarse step),
  * 8 kernels per coarse step, 9 kernels per truth step, 10 steps done,
  * 11 truth steps done, 12 graph replays so far, 13 contacts seen deeper than
  * half the smaller radius, 14 persistent launch, 15 LF substeps of the last

@@ -346,7 +346,9 @@ static CoarseArgs coarse_args(ms_model *m)
 
 static bool hybrid_on(const ms_model *m) { return m->hybrid_mode >= 0 && m->fc.couple && m->precision == MS_FP32; }
 
-static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
+// step facts of fine step i_local of the interval, for the model's state or
+// (scratch_out) for the out-of-place timing copies
+static StepCommon cell_common(ms_model *m, long long i_local, bool scratch_out)
 {
     StepCommon sc = step_common(m, i_local, scratch_out ? m->d_xmom : m->d_mom,
                                 scratch_out ? m->d_xwin : m->d_win);
@@ -354,6 +356,35 @@ static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
         sc.order = m->d_order2;
         sc.live = m->d_live;
     }
+    return sc;
+}
+
+// the cell kernels of a whole coarse interval (FP32 variants 2 and 3): every
+// size class's N0 steps on its own stream, forked once
+static cudaError_t launch_interval_cells(ms_model *m, bool scratch_out)
+{
+    const StepCommon sc = cell_common(m, 0, scratch_out);
+    cudaError_t e = cell_fork(m->cl, m->stream);
+    if (e == cudaSuccess) e = launch_cell_run32(m->s32, scratch_out ? m->x32 : m->s32, m->P32, sc, m->cl, m->interval);
+    if (e == cudaSuccess) e = cell_join(m->cl, m->stream);
+    return e;
+}
+
+static bool interval_cells(const ms_model *m) { return m->precision == MS_FP32 && m->cl.variant >= 2; }
+
+// cell-kernel launches of one coarse interval on the graph path
+static int64_t interval_launches(const ms_model *m)
+{
+    if (m->cl.variant == 0 || m->precision == MS_FP64) return m->interval;
+    int64_t k = 0;
+    for (int s = 0; s < m->cl.nseg; s++)
+        k += (m->cl.variant == 3 && m->cl.seg_kind[s] == 1) ? 1 : m->interval;
+    return k;
+}
+
+static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
+{
+    StepCommon sc = cell_common(m, i_local, scratch_out);
     if (m->precision == MS_FP64)
         return launch_cell_step64(m->s64, scratch_out ? m->x64 : m->s64, m->P64, sc, m->cl, m->stream);
     return launch_cell_step32(m->s32, scratch_out ? m->x32 : m->s32, m->P32, sc, m->cl, m->stream);
@@ -422,7 +453,11 @@ static cudaError_t build_graph(ms_model *m)
     cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     cudaError_t le = launch_interval_start(m);
-    for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
+    // FP32 size classes: one fork per interval, so that a class's next step
+    // does not wait for the other classes' current one
+    if (le == cudaSuccess && interval_cells(m)) le = launch_interval_cells(m, false);
+    else
+        for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
     if (le == cudaSuccess) le = launch_interval_end(m);
     e = cudaStreamEndCapture(m->stream, &graph);
     if (le != cudaSuccess) {
@@ -503,8 +538,8 @@ static void make_segments(ms_model *m, CellLaunch &c)
     struct Cls { int hi, threads, kind; };
     const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
     const Cls v2[6] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 1}, {192, 128, 1}, {128, 128, 1}, {64, 128, 1}};
-    const Cls *cls = c.variant == 2 ? v2 : v1;
-    const int ncls = c.variant == 2 ? 6 : 4;
+    const Cls *cls = c.variant >= 2 ? v2 : v1;
+    const int ncls = c.variant >= 2 ? 6 : 4;
     c.nseg = 0;
     c.nbmax = 32;
     int item = 0;
@@ -750,7 +785,6 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     cl.variant = m->precision == MS_FP32 ? 2 : 0;
     cl.threads = 128;
     cl.bin_beta = 1.3f;
-    cl.reg_min = 1 << 30;
     cl.persistent = 0;
     cl.grid = m->sm_count * 4;
     if (cl.variant >= 1 && configure_launch(m, cl) != MS_OK) cl.variant = 0;   // cells too large to bin in shared memory
@@ -1025,6 +1059,9 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
         if (k == 1) le = cudaEventRecord(e0, m->stream);
         if (le != cudaSuccess) break;
         if (which == 0) le = launch_step(m, i_local, true);
+        else if (which == 2 && interval_cells(m)) le = launch_interval_cells(m, true);
+        else if (which == 2)
+            for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, true);
         else le = truth_one(m, m->tcur, 1 - m->tcur, m->truth_steps);
     }
     if (le == cudaSuccess) le = cudaEventRecord(e1, m->stream);
@@ -1064,23 +1101,26 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
             c.bin_beta = b;
             cand.push_back(c);
         }
-        const int regs[3] = {256, 1024, 1 << 30};
-        for (float b : betas)
-            for (int rm : regs) {
+        for (int v = 2; v <= 3; v++)
+            for (float b : betas) {
                 CellLaunch c = m->cl;
-                c.variant = 2;
+                c.variant = v;
                 c.bin_beta = b;
-                c.reg_min = rm;
                 cand.push_back(c);
             }
     }
+    // FP32: whole coarse intervals, so that variants that keep a cell
+    // resident across steps are timed by what they save
+    const int which = m->precision == MS_FP32 ? 2 : 0;
+    const double per = which == 2 ? (double)m->interval : 1.0;
     const CellLaunch keep = m->cl;
     double best = 1e30;
     CellLaunch bestc = keep;
     for (const CellLaunch &c : cand) {
         if (configure_launch(m, c)) continue;
         double t = 0.0;
-        if (ms_time_kernel(m, 0, dt, reps, &t)) continue;
+        if (ms_time_kernel(m, which, dt, reps, &t)) continue;
+        t /= per;
         if (t < best) {
             best = t;
             bestc = c;
@@ -1092,11 +1132,10 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
     return MS_OK;
 }
 
-int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta,
-                  int32_t reg_min)
+int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
-    if (variant != 0 && !((variant == 1 || variant == 2) && m->precision == MS_FP32))
+    if (variant != 0 && !((variant >= 1 && variant <= 3) && m->precision == MS_FP32))
         return fail(MS_ERR_ARG, "unsupported variant %d", variant);
     if (threads != 64 && threads != 128 && threads != 256) return fail(MS_ERR_ARG, "threads must be 64, 128 or 256");
     if (!(bin_beta > 0.1 && bin_beta < 10.0)) return fail(MS_ERR_ARG, "bin_beta must be in (0.1, 10)");
@@ -1105,7 +1144,6 @@ int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persist
     c.threads = threads;
     c.persistent = persistent ? 1 : 0;
     c.bin_beta = (float)bin_beta;
-    if (reg_min > 0) c.reg_min = reg_min;
     c.grid = m->sm_count * std::min(2048 / threads, 8);
     CK(cudaStreamSynchronize(m->stream));
     return configure_launch(m, c);
@@ -1124,7 +1162,7 @@ int ms_info(ms_model *m, int64_t *out)
     out[4] = m->cl.variant;
     out[5] = m->cl.threads;
     out[6] = (int64_t)std::lround(m->cl.bin_beta * 1000.0f);
-    out[7] = (m->cl.variant >= 1) ? m->cl.nseg : 1;
+    out[7] = interval_launches(m);
     out[8] = m->fc.couple ? coarse_launches() : 1;
     out[9] = truth_launches(m->tb);
     out[10] = m->steps;

@@ -987,6 +987,358 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
     if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
 }
 
+// ======================================================= FP32 warp, resident
+// The warp kernel's step, repeated for a run of fine steps with the cell kept
+// in shared memory.  Between coarse steps a cell depends on nothing but
+// itself (its gradual-update increments are fixed at the coarse step), so a
+// warp can take its cell through a whole coarse interval and touch global
+// memory only at the two ends.  Every step is written as the step of
+// k_cell_step32_warp (same search order, same sums; the compiler may still
+// fuse a multiply-add differently in the two kernels), and a run of steps
+// gives the floes, moments and window of the same number of one-step
+// launches of this kernel, bit for bit.
+//
+// Shared memory per warp: the cell in floe order (home: position, velocity,
+// spin, radius, angle, thickness), updated in place at the end of each step,
+// and the search-order copy of the step's start state that the contact
+// search reads.
+
+__host__ __device__ inline size_t run_region_bytes(int cap, int nbmax)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    return a16(sizeof(uint2) * cap) + a16(sizeof(float4) * cap) + a16(sizeof(float2) * cap) +
+           warp_region_bytes(cap, nbmax) + a16(sizeof(double) * NWIN);
+}
+
+struct RunSm {
+    uint2 *HQ;     // home: fixed-point position
+    float4 *HU;    // home: u, v, w, r
+    float2 *HT;    // home: theta, h
+    double *win;   // the cell's window sums over the run
+    WarpSm w;      // search-order copy and bins, as in the single-step kernel
+};
+
+__device__ __forceinline__ RunSm carve_run(unsigned char *p, int cap, int nbmax)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    RunSm r;
+    size_t o = 0;
+    r.HQ = reinterpret_cast<uint2 *>(p + o); o += a16(sizeof(uint2) * cap);
+    r.HU = reinterpret_cast<float4 *>(p + o); o += a16(sizeof(float4) * cap);
+    r.HT = reinterpret_cast<float2 *>(p + o); o += a16(sizeof(float2) * cap);
+    r.win = reinterpret_cast<double *>(p + o); o += a16(sizeof(double) * NWIN);
+    r.w = carve_warp(p + o, cap, nbmax);
+    return r;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 5)
+k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, int nsteps, float beta, int item0,
+                  int item1, int cap, int nbmax, int seg)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = item0 + blockIdx.x * WARPS + warp;
+    if (sc.live) item1 = min(item1, item0 + sc.live[seg]);
+    if (item >= item1) return;
+    const RunSm R = carve_run(smem + warp * run_region_bytes(cap, nbmax), cap, nbmax);
+    const WarpSm &sm = R.w;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+
+    const float dt = sc.k.dt;
+    const float Lx = sc.k.Lx, Ly = sc.k.Ly, iLx = sc.k.iLx, iLy = sc.k.iLy;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
+    const int c = sc.order[item];
+    const int o = sc.off[c], n = sc.off[c + 1] - o;
+    const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+    const long long base = sc.ctrl->base;
+    const bool have_tgt = sc.couple && sc.ctrl->have_tgt;
+    const int nc = sc.ncell;
+
+    // ---- the cell into shared memory; window sums so far
+    for (int k = lane; k < n; k += 32) {
+        R.HQ[k] = make_uint2(in.xq[o + k], in.yq[o + k]);
+        R.HU[k] = make_float4(in.u[o + k], in.v[o + k], in.w[o + k], in.r[o + k]);
+        R.HT[k] = make_float2(in.th[o + k], in.h[o + k]);
+    }
+    if (sc.couple && lane < NWIN) R.win[lane] = sc.win[(size_t)lane * nc + c];
+    if (lane < P.n_modes) {
+        const int m = lane;
+        int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
+        int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
+        float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
+        b -= floorf(b);
+        float sn, cs;
+        if (P.taylor) {
+            sincospif(2.0f * b, &sn, &cs);
+            sm.Cm[m] = make_float2(cs, sn);
+        } else {
+            sm.Cm[m] = make_float2(b, 0.0f);
+        }
+    }
+    int nb = (int)(sqrtf((float)n) / beta);
+    nb = nb > nbmax ? nbmax : nb;
+    if (nb < 3) nb = 0;
+    const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
+    const float Rs = nb ? 0.5f * fminf(Bx, By) : -1.0f;
+    const int nbins = nb * nb;
+    __syncwarp();
+
+    unsigned deep_steps = 0;
+    bool bad = false;
+    float wua = 0.0f, wva = 0.0f;     // lane i: wind of step j0 + 32 q + i
+    const int j0 = (int)sc.i_local;
+    for (int js = 0; js < nsteps; js++) {
+        const int j = j0 + js;
+        // wind at the start of each step, 32 steps at a time (one FP64
+        // evaluation per lane)
+        if ((js & 31) == 0) {
+            const long long sj = base + j + lane + 1;
+            wind_at(P, (double)(sj - 1) * sc.dt, wua, wva);
+        }
+        const float ua = __shfl_sync(FULL, wua, js & 31), va = __shfl_sync(FULL, wva, js & 31);
+        const long long kk = (long long)j + 1;
+        const bool ramp = have_tgt && (kk % sc.n_t == 0);
+        float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
+        if (ramp) {
+            if (lane == 0) {
+                const RampCell rc = ramp_cell(sc, c, (int)(kk / sc.n_t));
+                rg = (float)rc.g; rdu = (float)rc.du; rdv = (float)rc.dv; rdw = (float)rc.dw;
+            }
+            rg = __shfl_sync(FULL, rg, 0); rdu = __shfl_sync(FULL, rdu, 0);
+            rdv = __shfl_sync(FULL, rdv, 0); rdw = __shfl_sync(FULL, rdw, 0);
+        }
+
+        for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+        __syncwarp();
+        // ---- count small floes per bin
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n;
+            const uint2 q = valid ? R.HQ[k] : make_uint2(0u, 0u);
+            const float r = valid ? R.HU[k].w : 0.0f;
+            const bool small = valid && r <= Rs;
+            const int b = small ? (int)(__umulhi(q.y, (unsigned)nb) * nb + __umulhi(q.x, (unsigned)nb)) : -1 - lane;
+            const unsigned m = __match_any_sync(FULL, b);
+            if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+            __syncwarp();
+        }
+        const int nsmall = warp_scan_excl(sm.cnt, sm.bst, nbins + 1, lane);
+        for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+        __syncwarp();
+        // ---- place every floe at its search position; position and angle
+        // advance at once (they need only the floe's own start state)
+        int lrun = nsmall;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n;
+            uint2 q = make_uint2(0u, 0u);
+            float4 U = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float2 T = make_float2(0.0f, 0.0f);
+            if (valid) {
+                q = R.HQ[k];
+                U = R.HU[k];
+                T = R.HT[k];
+            }
+            const float r = U.w;
+            const bool small = valid && r <= Rs;
+            const bool large = valid && !small;
+            const int b = small ? (int)(__umulhi(q.y, (unsigned)nb) * nb + __umulhi(q.x, (unsigned)nb)) : -1 - lane;
+            const unsigned m = __match_any_sync(FULL, b);
+            const unsigned bl = __ballot_sync(FULL, large);
+            int pos = 0;
+            if (small) pos = sm.bst[b] + sm.cnt[b] + __popc(m & lt);
+            else if (large) pos = lrun + __popc(bl & lt);
+            if (valid) {
+                sm.S4[pos] = make_float4((float)q.x * sx, (float)q.y * sy, r, T.y);
+                sm.SV[pos] = make_float4(U.x, U.y, U.z, 0.0f);
+                sm.SQ[pos] = q;
+                sm.orig[pos] = (short)k;
+                R.HQ[k] = make_uint2(q.x + (uint32_t)__float2int_rn(dt * U.x * isx),
+                                     q.y + (uint32_t)__float2int_rn(dt * U.y * isy));
+                R.HT[k].x = T.x + dt * U.z;
+            }
+            __syncwarp();
+            if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+            lrun += __popc(bl);
+            __syncwarp();
+        }
+
+        float acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; k++) acc[k] = 0.0f;
+        unsigned deep = 0;
+        for (int p = lane; p < n; p += 32) {
+            const float4 pl = sm.S4[p];
+            const float4 vl = sm.SV[p];
+            const uint2 ql = sm.SQ[p];
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            auto touch = [&](int k) {
+                const uint2 qj = sm.SQ[k];
+                const float dx = (float)(int)(qj.x - ql.x) * sx;
+                const float dy = (float)(int)(qj.y - ql.y) * sy;
+                const float4 pj = sm.S4[k];
+                const float4 vj = sm.SV[k];
+                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
+                            vj.z, P, fx, fy, tq, deep);
+            };
+            int ncand = 0;
+            short *cl = sm.clist + lane;
+            auto flush = [&]() {
+                for (int i = 0; i < ncand; i++) touch(cl[32 * i]);
+                ncand = 0;
+            };
+            auto hit = [&](int k) {
+                if (ncand == MAXC) flush();
+                cl[32 * ncand] = (short)k;
+                ncand++;
+            };
+            auto scan = [&](int k0, int k1, float xs, float ys, bool mix, bool miy) {
+                for (int k = k0; k < k1; k++) {
+                    const float4 q = sm.S4[k];
+                    float dx = q.x - xs, dy = q.y - ys;
+                    if (mix) dx = min_image(dx, Lx, iLx);
+                    if (miy) dy = min_image(dy, Ly, iLy);
+                    const float S = pl.z + q.z;
+                    if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+                }
+            };
+            const bool small = p < nsmall;
+            if (small) {
+                const int bx = (int)__umulhi(ql.x, (unsigned)nb), by = (int)__umulhi(ql.y, (unsigned)nb);
+                int a0 = bx - 1, a1 = bx + 1, c0 = 1, c1 = 0;
+                float xc = pl.x;
+                if (bx == 0) { a0 = 0; a1 = 1; c0 = nb - 1; c1 = nb - 1; xc = pl.x + Lx; }
+                else if (bx == nb - 1) { a0 = nb - 2; a1 = nb - 1; c0 = 0; c1 = 0; xc = pl.x - Lx; }
+#pragma unroll
+                for (int dyb = -1; dyb <= 1; dyb++) {
+                    int wy = by + dyb;
+                    float ys = pl.y;
+                    if (wy < 0) { wy += nb; ys += Ly; } else if (wy >= nb) { wy -= nb; ys -= Ly; }
+                    const int row = wy * nb;
+                    const int kA = sm.bst[row + a0], nA = sm.bst[row + a1 + 1] - kA;
+                    const int kC = sm.bst[row + c0], nC = c1 >= c0 ? sm.bst[row + c1 + 1] - kC : 0;
+                    for (int i = 0; i < nA + nC; i++) {
+                        const bool inA = i < nA;
+                        const int k = inA ? kA + i : kC + (i - nA);
+                        const float4 q = sm.S4[k];
+                        const float dx = q.x - (inA ? pl.x : xc), dy = q.y - ys;
+                        const float S = pl.z + q.z;
+                        if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+                    }
+                }
+            } else if (nb) {
+                const float reach = 1.001f * (pl.z + Rs);
+                int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
+                int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+                const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
+                if (allx) { bx0 = 0; bx1 = nb - 1; }
+                if (ally) { by0 = 0; by1 = nb - 1; }
+                for (int by = by0; by <= by1; by++) {
+                    const int wy = by < 0 ? by + nb : (by >= nb ? by - nb : by);
+                    const float ys = ally ? pl.y : (by < 0 ? pl.y + Ly : (by >= nb ? pl.y - Ly : pl.y));
+                    const int row = wy * nb;
+                    if (allx) {
+                        scan(sm.bst[row], sm.bst[row + nb], pl.x, ys, true, ally);
+                    } else {
+                        if (bx0 < 0) scan(sm.bst[row + bx0 + nb], sm.bst[row + nb], pl.x + Lx, ys, false, ally);
+                        const int a0 = bx0 < 0 ? 0 : bx0, a1 = bx1 > nb - 1 ? nb - 1 : bx1;
+                        scan(sm.bst[row + a0], sm.bst[row + a1 + 1], pl.x, ys, false, ally);
+                        if (bx1 >= nb) scan(sm.bst[row], sm.bst[row + bx1 - nb + 1], pl.x - Lx, ys, false, ally);
+                    }
+                }
+            }
+            scan(nsmall, n, pl.x, pl.y, true, true);
+            flush();
+
+            // ---- drag, forward Euler, gradual update, moments
+            const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
+            float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
+            if (P.taylor) {
+                for (int m = 0; m < P.n_modes; m++) {
+                    float c0, s0;
+                    rot_small(fmaf(P.ta[m], xf, P.tb[m] * yf), c0, s0);
+                    const float2 C = sm.Cm[m];
+                    const float cs = C.x * c0 - C.y * s0, sn = C.y * c0 + C.x * s0;
+                    uo -= P.mAu[m] * cs;
+                    vo += P.mAv[m] * cs;
+                    zeta -= P.mAz[m] * sn;
+                }
+            } else {
+                for (int m = 0; m < P.n_modes; m++) {
+                    const float cyc = sm.Cm[m].x + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+                    float sn, cs;
+                    sincospif(2.0f * cyc, &sn, &cs);
+                    uo -= P.mAu[m] * cs;
+                    vo += P.mAv[m] * cs;
+                    zeta -= P.mAz[m] * sn;
+                }
+            }
+            float Fdx, Fdy, Td;
+            drag_force(P, uo, vo, zeta, ua, va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+            fx += Fdx; fy += Fdy; tq += Td;
+            const float r = pl.z, h = pl.w;
+            const float mass = P.mass_c * r * r * h;
+            const float I = P.inertia_f * mass * r * r;
+            float un = vl.x + dt * (fx / mass);
+            float vn = vl.y + dt * (fy / mass);
+            float wn = vl.z + dt * (tq / I);
+            float rn = r;
+            if (ramp) {
+                rn = r * rg;
+                un += rdu;
+                vn += rdv;
+                wn += rdw;
+            }
+            bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+            R.HU[sm.orig[p]] = make_float4(un, vn, wn, rn);
+            float a12[NMOM];
+#pragma unroll
+            for (int k = 0; k < NMOM; k++) a12[k] = 0.0f;
+            add_moments(a12, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+#pragma unroll
+            for (int k = 1; k < NMOM; k++) acc[k] += a12[k];
+        }
+        deep_steps += deep ? 1u : 0u;
+        // ---- moments of the step: lane 2k holds the warp total of column k
+        const float tot = warp_sum16(acc, lane);
+        const double dtot = (double)tot;
+        const double M = __shfl_sync(FULL, dtot, 2), Mu = __shfl_sync(FULL, dtot, 4), Mv = __shfl_sync(FULL, dtot, 6);
+        const double Fx = __shfl_sync(FULL, dtot, 18), Fy = __shfl_sync(FULL, dtot, 20), Tz = __shfl_sync(FULL, dtot, 22);
+        if (js == nsteps - 1) {
+            double *mo = sc.mom + (size_t)c * NMOM;
+            if ((lane & 1) == 0 && lane < 2 * NMOM) mo[lane >> 1] = lane == 0 ? (double)n : dtot;
+        }
+        if (lane == 0 && sc.couple) {
+            if (M > 0.0) {
+                R.win[0] += Mu / M;
+                R.win[1] += Mv / M;
+            }
+            R.win[2] += Fx;
+            R.win[3] += Fy;
+            R.win[4] += Tz;
+        }
+        __syncwarp();
+    }
+
+    // ---- the cell back to global memory
+    for (int k = lane; k < n; k += 32) {
+        const uint2 q = R.HQ[k];
+        const float4 U = R.HU[k];
+        out.xq[o + k] = q.x;
+        out.yq[o + k] = q.y;
+        out.th[o + k] = R.HT[k].x;
+        out.u[o + k] = U.x;
+        out.v[o + k] = U.y;
+        out.w[o + k] = U.z;
+        out.r[o + k] = U.w;
+    }
+    if (sc.couple && lane < NWIN) sc.win[(size_t)lane * nc + c] = R.win[lane];
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep_steps) atomicAdd(&sc.ctrl->deep, (unsigned long long)deep_steps);
+}
+
 // ===================================================================== FP64
 // Positions are FP64 offsets from the cell origin; minimum image and wrap as
 // x - L rint(x / L) and x - L floor(x / L).  Pairs are visited in ascending
@@ -1127,17 +1479,35 @@ int seg_nbmax(const CellLaunch &cl, int s)
 
 static size_t seg_smem(const CellLaunch &cl, int s)
 {
+    if (cl.seg_kind[s] == 1 && cl.variant == 3) return 4 * run_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     if (cl.seg_kind[s] == 1) return 4 * warp_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     return smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
 }
 
+// nsteps fine steps of size class s from step sc.i_local of the interval:
+// one launch of the resident warp kernel (variant 3), else one launch per step
 static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
-                                const StepCommon &sc, const CellLaunch &cl, int s, cudaStream_t st)
+                                const StepCommon &sc0, const CellLaunch &cl, int s, cudaStream_t st, int nsteps = 1)
 {
     const int items = cl.seg_end[s] - cl.seg_begin[s];
     if (items <= 0) return cudaSuccess;
     const int nbm = seg_nbmax(cl, s);
     const size_t sm = seg_smem(cl, s);
+    if (cl.seg_kind[s] == 1 && cl.variant == 3) {
+        k_cell_run32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc0, nsteps, cl.bin_beta, cl.seg_begin[s],
+                                                               cl.seg_end[s], cl.seg_maxn[s], nbm, s);
+        return cudaGetLastError();
+    }
+    if (nsteps > 1) {
+        StepCommon sc = sc0;
+        for (int i = 0; i < nsteps; i++) {
+            sc.i_local = sc0.i_local + i;
+            cudaError_t e = launch_seg32(i == 0 ? in : out, out, P, sc, cl, s, st, 1);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const StepCommon &sc = sc0;
     if (cl.seg_kind[s] == 1) {
         k_cell_step32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
                                                                 cl.seg_end[s], cl.seg_maxn[s], nbm, s);
@@ -1183,7 +1553,8 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step32_brute<256>, (const void *)k_cell_step64_brute<64>,
             (const void *)k_cell_step64_brute<128>, (const void *)k_cell_step64_brute<256>,
             (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
-            (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>};
+            (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>,
+            (const void *)k_cell_run32_warp<4>};
         limit = optin;
         for (const void *k : kern) {
             cudaFuncAttributes fa;
@@ -1199,6 +1570,33 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
     return smem <= (size_t)limit ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+cudaError_t cell_fork(const CellLaunch &cl, cudaStream_t st)
+{
+    cudaError_t e = cudaEventRecord(cl.ev_fork, st);
+    for (int s = 0; s < cl.nseg && e == cudaSuccess; s++) e = cudaStreamWaitEvent(cl.side[s], cl.ev_fork, 0);
+    return e;
+}
+
+cudaError_t cell_join(const CellLaunch &cl, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int s = 0; s < cl.nseg && e == cudaSuccess; s++) {
+        if ((e = cudaEventRecord(cl.ev_join[s], cl.side[s])) != cudaSuccess) break;
+        e = cudaStreamWaitEvent(st, cl.ev_join[s], 0);
+    }
+    return e;
+}
+
+cudaError_t launch_cell_run32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                              const StepCommon &sc, const CellLaunch &cl, int nsteps)
+{
+    for (int s = 0; s < cl.nseg; s++) {
+        cudaError_t e = launch_seg32(in, out, P, sc, cl, s, cl.side[s], nsteps);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                                const StepCommon &sc, const CellLaunch &cl, cudaStream_t st)
 {
@@ -1209,7 +1607,7 @@ cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, cons
         }
         return cudaSuccess;
     }
-    if (cl.variant == 2) {
+    if (cl.variant == 2 || cl.variant == 3) {
         // every size class on its own stream: the classes hold disjoint cells,
         // so their kernels overlap and their tails hide each other
         cudaError_t e = cudaEventRecord(cl.ev_fork, st);

@@ -194,7 +194,8 @@ struct DevState64 {
 constexpr int MAXSEG = 6;   // size classes of cells launched separately (binned variants)
 
 struct CellLaunch {
-    int variant;       // 0 brute force, 1 binned block per cell, 2 binned warp per cell (FP32 only)
+    int variant;       // 0 brute force, 1 binned block per cell, 2 binned warp per cell, 3 as 2 with
+                       // the warp classes resident for a run of steps (FP32 only)
     int threads;       // threads per block (brute force)
     float bin_beta;    // bin side in units of the mean floe spacing (binned variant)
     int persistent;    // 1: grid of resident blocks + work queue (brute force)
@@ -205,7 +206,6 @@ struct CellLaunch {
     int seg_begin[MAXSEG], seg_end[MAXSEG], seg_maxn[MAXSEG], seg_threads[MAXSEG];
     int seg_kind[MAXSEG];   // 0: block per cell, 1: warp per cell (seg_maxn = the warp's capacity)
     int nbmax;         // bins per side at most
-    int reg_min;       // register large floes in bins when (large x small floes) >= this
     // segments of variant 2 run on their own streams, forked from and joined
     // back into the launching stream (concurrent branches in a graph)
     cudaStream_t side[MAXSEG];
@@ -243,6 +243,14 @@ struct StepCommon {
 // cell_step.cu
 cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                                const StepCommon &sc, const CellLaunch &cl, cudaStream_t st);
+// nsteps fine steps of every size class from step sc.i_local of the interval,
+// each class on its own stream (variants 2 and 3; the streams forked by
+// cell_fork); variant 3 runs each warp class's steps in one resident launch
+cudaError_t launch_cell_run32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                              const StepCommon &sc, const CellLaunch &cl, int nsteps);
+// fork the size-class streams off st / join them back (variants 2 and 3)
+cudaError_t cell_fork(const CellLaunch &cl, cudaStream_t st);
+cudaError_t cell_join(const CellLaunch &cl, cudaStream_t st);
 cudaError_t launch_cell_step64(const DevState64 &in, const DevState64 &out, const Phys<double> &P,
                                const StepCommon &sc, const CellLaunch &cl, cudaStream_t st);
 cudaError_t launch_cell_moments32(const DevState32 &s, const Phys<float> &P, const StepCommon &sc,

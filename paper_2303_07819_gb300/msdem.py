@@ -89,7 +89,7 @@ def load(path: str | None = None):
     L.ms_set_stream.argtypes = [vp, vp]
     L.ms_autotune.argtypes = [vp, C.c_double, C.c_int32, _dp]
     L.ms_time_kernel.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, _dp]
-    L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_int32]
+    L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double]
     L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_cell_moments_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int32, C.c_int64] + [vp] * 10
     L.ms_closure_attach.argtypes = [vp, vp, C.c_int32, C.c_double, C.POINTER(C.c_float)]
@@ -230,9 +230,8 @@ class Model:
         return out.value
 
     def set_launch(self, variant: int = 0, threads: int = 128, persistent: int = 0,
-                   bin_beta: float = 1.0, reg_min: int = 0) -> None:
-        _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta),
-                                    int(reg_min)))
+                   bin_beta: float = 1.0) -> None:
+        _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta)))
 
     def closure_attach(self, mlp, mode: int = 0, tol: float = 0.5, box=None) -> None:
         """mode 0: network `mlp` with fallback; 1: mean-field closure; -1: off."""
@@ -259,7 +258,7 @@ class Model:
         out = np.zeros(16, dtype=np.int64)
         _check(load().ms_info(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "ncell", "max_n", "precision", "variant", "threads", "bin_beta_milli",
-                "launches_per_step", "launches_per_coarse", "launches_per_truth_step", "steps",
+                "launches_per_interval", "launches_per_coarse", "launches_per_truth_step", "steps",
                 "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1"]
         return {k: int(v) for k, v in zip(keys, out)}
 

@@ -188,6 +188,30 @@ def test_graph_replay_equals_single_steps(ms):
         assert np.array_equal(fa[k], fb[k]), k
 
 
+def test_resident_run_equals_single_steps(ms):
+    """Variant 3 keeps each warp cell in shared memory for a whole coarse
+    interval (one launch per interval on the graph path) and runs one step
+    per launch otherwise: the two give the same floes and moments bitwise,
+    across coarse steps and gradual updates."""
+    s = I.config2(seed=7, nx=16)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    a = ms.Model(p, s["floes"], ms.MS_FP32)
+    b = ms.Model(p, s["floes"], ms.MS_FP32)
+    a.set_launch(3, 128, 0, 1.3)
+    b.set_launch(3, 128, 0, 1.3)
+    a.step(dt, 2 * N0 + 17)
+    for _ in range(2 * N0 + 17):
+        b.step(dt, 1)
+    assert a.info()["graph_replays"] == 2 and b.info()["graph_replays"] == 0
+    li = a.info()["launches_per_interval"]
+    assert 1 <= li % N0 <= 4           # one launch per warp size class, N0 per block class
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(a.moments(), b.moments())
+    assert np.array_equal(a.coupling()["q"], b.coupling()["q"])
+
+
 def test_launch_variants_agree(ms):
     """Threads per block and the persistent work queue change only the order
     of the moment reduction, never a floe's arithmetic: floes agree bitwise
@@ -234,7 +258,8 @@ def test_time_kernel_leaves_state(ms):
     before = a.floes()
     t0 = a.time_kernel(0, s["dt"], 5)
     t1 = a.time_kernel(1, s["dt"], 5)
-    assert t0 > 0 and t1 > 0
+    t2 = a.time_kernel(2, s["dt"], 2)
+    assert t0 > 0 and t1 > 0 and t2 > t0
     after = a.floes()
     for k in before:
         assert np.array_equal(before[k], after[k])
@@ -272,11 +297,12 @@ def test_set_floes_roundtrip(ms):
         assert np.array_equal(f[k], f2[k]), k
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_fp32_variants_match_oracle(orc, ms, variant):
-    """Brute-force, block-binned and warp-binned pair search: each within the
-    FP32 tolerance of the oracle over 100 steps on a ragged mix of cells
-    (0 to 300 floes, so every size class and both launch kinds run)."""
+    """Brute-force, block-binned, warp-binned and resident warp-binned pair
+    search: each within the FP32 tolerance of the oracle over 100 steps on a
+    ragged mix of cells (0 to 300 floes, so every size class and both launch
+    kinds run)."""
     s = ragged_scenario([0, 1, 5, 17, 31, 33, 64, 65, 100, 127, 129, 200, 256, 257, 300], seed=21)
     p = s["params"]
     o = orc.Model(p, s["floes"])
@@ -293,7 +319,7 @@ def test_fp32_variants_agree_one_step(ms):
     find the same contacts, so moments agree to FP32 summation order."""
     s = I.config1(nx=16)
     res = []
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
         g.set_launch(variant, 128, 0, 1.0)
         g.step(s["dt"], 1)
