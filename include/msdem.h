@@ -68,7 +68,12 @@ typedef struct ms_floes {
 /* Forcing, material constants and coupling parameters.
  *  ocean:  u_o = (uo_x, uo_y) + curl of psi, psi = sum_m A_m sin(2 pi (kx_m X/Lx
  *          + ky_m Y/Ly) + phi_m); modes = host [n_modes][4] = (A, kx, ky, phi),
- *          kx, ky integers, n_modes <= MS_MAX_MODES.  Drag Eq. (2.1c-d):
+ *          kx, ky integers; plus velocity modes for compressible currents
+ *          (the currents of Secs. 4.2-4.3): u_o += sum_m (Au_m, Av_m)
+ *          cos(kx_m X + ky_m Y + phi_m), vmodes = host [n_vmodes][5] = (Au,
+ *          Av, kx, ky, phi), kx, ky real (rad per unit length; the current need
+ *          not be periodic), curl -(Av kx - Au ky) sin(.) per mode;
+ *          n_modes + n_vmodes <= MS_MAX_MODES.  Drag Eq. (2.1c-d):
  *          Cd rho_o pi r^2 (u_o - v)|u_o - v| and Cd rho_o pi r^4 (curl/2 - w)|.|.
  *  wind:   (wind_x, wind_y) rotated by 2 pi t / wind_period (0: constant);
  *          drag Ca rho_a pi r^2 (u_a - v)|u_a - v|, no wind torque.
@@ -91,6 +96,8 @@ typedef struct ms_forcing {
     int32_t inertia_half;
     int32_t couple, N0, n_t;
     int32_t precision;
+    int32_t n_vmodes;
+    const double *vmodes;
 } ms_forcing;
 
 typedef struct ms_model ms_model;

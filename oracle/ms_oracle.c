@@ -63,6 +63,16 @@ void orc_forcing(const orc_params *p, double X, double Y, double t, double *out)
         vo += A * kx * c;
         zeta -= A * (kx * kx + ky * ky) * s;
     }
+    /* velocity modes: u += Au cos(th), v += Av cos(th), so the curl
+     * dv/dx - du/dy adds -(Av kx - Au ky) sin(th) */
+    for (int32_t m = 0; m < p->n_vmodes; m++) {
+        const double *md = p->vmodes + 5 * m;
+        double th = md[2] * X + md[3] * Y + md[4];
+        double c = cos(th), s = sin(th);
+        uo += md[0] * c;
+        vo += md[1] * c;
+        zeta -= (md[1] * md[2] - md[0] * md[3]) * s;
+    }
     double ua, va;
     wind_at(p, t, &ua, &va);
     out[0] = uo; out[1] = vo; out[2] = zeta; out[3] = ua; out[4] = va;
@@ -236,15 +246,21 @@ struct orc_model {
     double dt;
 };
 
+/* copy of the parameters with both mode tables in one owned buffer */
 static void copy_params(orc_params *dst, double **modes, const orc_params *src)
 {
     *dst = *src;
     *modes = NULL;
-    if (src->n_modes > 0) {
-        *modes = (double *)malloc(sizeof(double) * 4 * src->n_modes);
-        memcpy(*modes, src->modes, sizeof(double) * 4 * src->n_modes);
+    const int32_t ns = src->n_modes > 0 ? src->n_modes : 0, nv = src->n_vmodes > 0 ? src->n_vmodes : 0;
+    if (ns + nv > 0) {
+        *modes = (double *)malloc(sizeof(double) * (4 * ns + 5 * nv));
+        if (ns) memcpy(*modes, src->modes, sizeof(double) * 4 * ns);
+        if (nv) memcpy(*modes + 4 * ns, src->vmodes, sizeof(double) * 5 * nv);
     }
-    dst->modes = *modes;
+    dst->n_modes = ns;
+    dst->n_vmodes = nv;
+    dst->modes = ns ? *modes : NULL;
+    dst->vmodes = nv ? *modes + 4 * ns : NULL;
 }
 
 static int32_t cell_index(double X, double L, double d, int32_t n)
@@ -565,7 +581,97 @@ struct orc_truth {
     double *fx, *fy, *tq, *fdx, *fdy, *tdq;
     int64_t steps;
     double dt;
+    int brute;                     /* 1: the plain loop over all pairs only */
 };
+
+void orc_truth_set_brute(orc_truth *t, int32_t brute) { t->brute = brute ? 1 : 0; }
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Contact forces of the truth DEM with a bin search.  Same result, bit for
+ * bit, as the loop over all pairs (l < j) in index order: floe l's sums take
+ * the pairs (i, l), i < l, in increasing i, then (l, j), j > l, in increasing
+ * j, which is the order in which that loop reaches floe l; each pair's force
+ * comes from the same orc_pair(lower index, higher index) call, and pairs
+ * not in contact add nothing.  Bins of side >= 2 r_max hold every contact
+ * partner of a floe within its 3 x 3 neighbourhood.  Returns 0 when the
+ * domain is too small for 3 bins per side (the caller uses the plain loop). */
+static int truth_forces_binned(orc_truth *t)
+{
+    const orc_params *p = &t->p;
+    const int64_t n = t->n;
+    double rmax = 0.0;
+    for (int64_t l = 0; l < n; l++) rmax = t->r[l] > rmax ? t->r[l] : rmax;
+    if (!(rmax > 0.0)) return 0;
+    int64_t nbx = (int64_t)floor(p->Lx / (2.0 * rmax)), nby = (int64_t)floor(p->Ly / (2.0 * rmax));
+    if (nbx < 3 || nby < 3) return 0;
+    if (nbx > 4096) nbx = 4096;
+    if (nby > 4096) nby = 4096;
+    const double bx = p->Lx / (double)nbx, by = p->Ly / (double)nby;
+    int64_t *start = (int64_t *)calloc((size_t)(nbx * nby + 1), sizeof(int64_t));
+    int64_t *bin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t l = 0; l < n; l++) {
+        int64_t ix = (int64_t)floor(t->x[l] / bx), iy = (int64_t)floor(t->y[l] / by);
+        ix = ix < 0 ? 0 : (ix >= nbx ? nbx - 1 : ix);
+        iy = iy < 0 ? 0 : (iy >= nby ? nby - 1 : iy);
+        bin[l] = iy * nbx + ix;
+        start[bin[l] + 1]++;
+    }
+    for (int64_t b = 0; b < nbx * nby; b++) start[b + 1] += start[b];
+    {
+        int64_t *cur = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nbx * nby));
+        memcpy(cur, start, sizeof(int64_t) * (size_t)(nbx * nby));
+        for (int64_t l = 0; l < n; l++) list[cur[bin[l]]++] = l;   /* ascending within each bin */
+        free(cur);
+    }
+    int64_t l;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) num_threads(g_threads)
+#endif
+    for (l = 0; l < n; l++) {
+        int64_t cand[4096];
+        int64_t nc = 0;
+        const int64_t ix = bin[l] % nbx, iy = bin[l] / nbx;
+        int overflow = 0;
+        for (int64_t dy = -1; dy <= 1; dy++)
+            for (int64_t dx = -1; dx <= 1; dx++) {
+                const int64_t jx = (ix + dx + nbx) % nbx, jy = (iy + dy + nby) % nby;
+                const int64_t b = jy * nbx + jx;
+                for (int64_t k = start[b]; k < start[b + 1]; k++) {
+                    if (list[k] == l) continue;
+                    if (nc < 4096) cand[nc++] = list[k];
+                    else overflow = 1;
+                }
+            }
+        (void)overflow;   /* 4096 partners within 3 x 3 bins cannot occur for disks that do not pile up */
+        qsort(cand, (size_t)nc, sizeof(int64_t), cmp_i64);
+        double fx = 0.0, fy = 0.0, tq = 0.0, o[16];
+        for (int64_t k = 0; k < nc; k++) {
+            const int64_t j = cand[k];
+            if (j < l) {
+                if (orc_pair(p, p->Lx, p->Ly,
+                             t->x[j], t->y[j], t->u[j], t->v[j], t->w[j], t->r[j], t->h[j],
+                             t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l], o)) {
+                    fx -= o[0]; fy -= o[1]; tq += o[3];
+                }
+            } else if (orc_pair(p, p->Lx, p->Ly,
+                                t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l],
+                                t->x[j], t->y[j], t->u[j], t->v[j], t->w[j], t->r[j], t->h[j], o)) {
+                fx += o[0]; fy += o[1]; tq += o[2];
+            }
+        }
+        t->fx[l] = fx; t->fy[l] = fy; t->tq[l] = tq;
+    }
+    free(start);
+    free(bin);
+    free(list);
+    return 1;
+}
 
 orc_truth *orc_truth_create(const orc_params *p, int64_t n,
                             const double *x, const double *y, const double *theta,
@@ -610,7 +716,8 @@ int orc_truth_step(orc_truth *t, double dt, int64_t nsteps)
     for (int64_t k = 0; k < nsteps; k++) {
         double time = (double)t->steps * dt;
         for (int64_t l = 0; l < n; l++) { t->fx[l] = 0.0; t->fy[l] = 0.0; t->tq[l] = 0.0; }
-        for (int64_t l = 0; l < n; l++)
+        const int64_t npl = (!t->brute && truth_forces_binned(t)) ? 0 : n;   /* 0: forces done */
+        for (int64_t l = 0; l < npl; l++)
             for (int64_t j = l + 1; j < n; j++) {
                 if (orc_pair(p, p->Lx, p->Ly,
                              t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l],

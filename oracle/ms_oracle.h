@@ -37,6 +37,11 @@ typedef struct orc_params {
     int32_t inertia_half;          /* 0: I = m r^2 (paper), 1: I = m r^2 / 2 */
     /* coupling (Algorithm 1) */
     int32_t couple, N0, n_t;
+    /* ocean, second part: velocity Fourier modes (compressible currents such
+     * as those of Secs. 4.2-4.3), u_o += sum_m (Au_m, Av_m) cos(kx_m X +
+     * ky_m Y + phi_m) with real wave numbers (rad per unit length) */
+    int32_t n_vmodes;
+    const double *vmodes;          /* [n_vmodes][5] = Au, Av, kx, ky, phi */
 } orc_params;
 
 /* ---- unit-level functions (used by the pins) ---- */
@@ -96,6 +101,10 @@ orc_truth *orc_truth_create(const orc_params *p, int64_t n,
                             const double *r, const double *h);
 void orc_truth_free(orc_truth *t);
 int  orc_truth_step(orc_truth *t, double dt, int64_t nsteps);
+/* brute = 1: contact forces by the plain loop over all pairs (l < j); 0 (the
+ * default): the same pairs found through bins of side >= 2 r_max, summed in
+ * the same order, so the result is identical bit for bit. */
+void orc_truth_set_brute(orc_truth *t, int32_t brute);
 void orc_truth_moments(const orc_truth *t, double *out);
 void orc_truth_floes(const orc_truth *t, double *out);
 

@@ -37,6 +37,7 @@ class Params(C.Structure):
         ("rho_ice", C.c_double), ("E", C.c_double), ("G", C.c_double), ("eta", C.c_double),
         ("mu", C.c_double), ("h_ref", C.c_double), ("inertia_half", C.c_int32),
         ("couple", C.c_int32), ("N0", C.c_int32), ("n_t", C.c_int32),
+        ("n_vmodes", C.c_int32), ("vmodes", C.POINTER(C.c_double)),
     ]
 
 
@@ -87,6 +88,7 @@ def lib():
         L.orc_truth_step.restype = C.c_int
         L.orc_truth_moments.argtypes = [C.c_void_p, dp]
         L.orc_truth_floes.argtypes = [C.c_void_p, dp]
+        L.orc_truth_set_brute.argtypes = [C.c_void_p, C.c_int32]
         L.orc_l2_diff.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, dp, dp]
         L.orc_l2_diff.restype = C.c_double
         L.orc_set_threads.argtypes = [C.c_int32]
@@ -105,8 +107,9 @@ def _ip(a: np.ndarray):
 
 def make_params(p: dict):
     """Build the C parameter struct from a scenario parameter dict.  Returns
-    (struct, keep-alive array of modes)."""
+    (struct, keep-alive arrays of the stream and velocity modes)."""
     modes = np.ascontiguousarray(np.asarray(p.get("modes", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4))
+    vmodes = np.ascontiguousarray(np.asarray(p.get("vmodes", np.zeros((0, 5))), dtype=np.float64).reshape(-1, 5))
     s = Params()
     s.nx, s.ny = int(p["nx"]), int(p["ny"])
     s.Lx, s.Ly = float(p["Lx"]), float(p["Ly"])
@@ -118,7 +121,9 @@ def make_params(p: dict):
         setattr(s, k, float(p.get(k, 0.0)))
     s.inertia_half = int(p.get("inertia_half", 0))
     s.couple, s.N0, s.n_t = int(p.get("couple", 0)), int(p.get("N0", 100)), int(p.get("n_t", 10))
-    return s, modes
+    s.n_vmodes = vmodes.shape[0]
+    s.vmodes = _dp(vmodes) if vmodes.shape[0] else C.POINTER(C.c_double)()
+    return s, (modes, vmodes)
 
 
 def set_threads(n: int) -> None:
@@ -234,6 +239,11 @@ class Truth(_Base):
     """The un-localised DEM over the whole periodic domain."""
     _create, _free, _step = "orc_truth_create", "orc_truth_free", "orc_truth_step"
     _moments, _floes = "orc_truth_moments", "orc_truth_floes"
+
+    def set_brute(self, brute: bool) -> None:
+        """True: contact forces by the plain all-pairs loop (the definition);
+        False (default): the binned search, identical bit for bit."""
+        lib().orc_truth_set_brute(self._h, int(bool(brute)))
 
 
 if __name__ == "__main__":

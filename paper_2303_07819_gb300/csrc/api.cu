@@ -42,7 +42,7 @@ struct ms_model {
     int precision = 0;
     ms_grid grid{};
     ms_forcing fc{};
-    std::vector<double> modes;
+    std::vector<double> modes, vmodes;
     long long n = 0;
     int ncell = 0, max_n = 0;
     Geom g{};
@@ -490,28 +490,58 @@ static void fill_phys(ms_model *m)
     std::memset(&P, 0, sizeof(P));
     std::memset(&Q, 0, sizeof(Q));
     P.uo_x = f.uo_x; P.uo_y = f.uo_y;
-    P.n_modes = Q.n_modes = f.n_modes;
-    for (int k = 0; k < f.n_modes; k++) {
-        const double *md = &m->modes[4 * k];
-        const double kx = 2.0 * PI_D * md[1] / m->grid.Lx, ky = 2.0 * PI_D * md[2] / m->grid.Ly;
-        P.mA[k] = md[0]; P.mKx[k] = kx; P.mKy[k] = ky; P.mPh[k] = md[3];
-        Q.mkx[k] = (int)md[1]; Q.mky[k] = (int)md[2];
-        double cyc = md[3] / (2.0 * PI_D);
+    P.n_modes = Q.n_modes = f.n_modes + f.n_vmodes;
+    const double Lcx = m->grid.Lx / m->grid.nx, Lcy = m->grid.Ly / m->grid.ny;
+    Q.taylor = 1;
+    for (int k = 0; k < P.n_modes; k++) {
+        const bool sf = k < f.n_modes;          // stream-function mode (integer wave numbers)
+        const double *md = sf ? &m->modes[4 * k] : &m->vmodes[5 * (k - f.n_modes)];
+        double kx, ky, ph, Au, Av, Az, Ad;
+        if (sf) {
+            kx = 2.0 * PI_D * md[1] / m->grid.Lx;
+            ky = 2.0 * PI_D * md[2] / m->grid.Ly;
+            ph = md[3];
+            Au = md[0] * ky;
+            Av = md[0] * kx;
+            Az = md[0] * (kx * kx + ky * ky);
+            Ad = 0.0;
+            P.mA[k] = md[0];
+            Q.mkx[k] = (int)md[1];
+            Q.mky[k] = (int)md[2];
+            Q.kdx[k] = (float)md[1];
+            Q.kdy[k] = (float)md[2];
+        } else {
+            kx = md[2];
+            ky = md[3];
+            ph = md[4];
+            Au = -md[0];
+            Av = md[1];
+            Az = md[1] * kx - md[0] * ky;
+            Ad = md[0] * kx + md[1] * ky;
+            Q.kdx[k] = (float)(kx * m->grid.Lx / (2.0 * PI_D));
+            Q.kdy[k] = (float)(ky * m->grid.Ly / (2.0 * PI_D));
+        }
+        P.mKx[k] = kx; P.mKy[k] = ky; P.mPh[k] = ph;
+        P.mAu[k] = Au; P.mAv[k] = Av; P.mAz[k] = Az; P.mAd[k] = Ad;
+        Q.isint[k] = P.isint[k] = sf ? 1 : 0;
+        double cyc = ph / (2.0 * PI_D);
         cyc -= std::floor(cyc);
         Q.mCyc[k] = (float)cyc;
-        Q.mAu[k] = (float)(md[0] * ky);
-        Q.mAv[k] = (float)(md[0] * kx);
-        Q.mAz[k] = (float)(md[0] * (kx * kx + ky * ky));
-        Q.mA[k] = (float)md[0];
-        Q.ta[k] = (float)(2.0 * PI_D * md[1] / m->grid.nx);
-        Q.tb[k] = (float)(2.0 * PI_D * md[2] / m->grid.ny);
-    }
-    // small-angle form of the per-floe phase: valid when no mode turns by more
-    // than 1/16 cycle across one cell
-    Q.taylor = 1;
-    for (int k = 0; k < f.n_modes; k++) {
-        const double *md = &m->modes[4 * k];
-        if (std::fabs(md[1]) / m->grid.nx + std::fabs(md[2]) / m->grid.ny > 1.0 / 16.0) Q.taylor = 0;
+        Q.bx[k] = kx * Lcx / (2.0 * PI_D);
+        Q.by[k] = ky * Lcy / (2.0 * PI_D);
+        Q.bph[k] = cyc;
+        Q.kcx[k] = (float)Q.bx[k];
+        Q.kcy[k] = (float)Q.by[k];
+        Q.mAu[k] = (float)Au;
+        Q.mAv[k] = (float)Av;
+        Q.mAz[k] = (float)Az;
+        Q.mAd[k] = (float)Ad;
+        Q.mA[k] = (float)P.mA[k];
+        Q.ta[k] = (float)(kx * Lcx);
+        Q.tb[k] = (float)(ky * Lcy);
+        // small-angle form of the per-floe phase: valid when no mode turns
+        // by more than 1/16 cycle across one cell
+        if ((std::fabs(kx) * Lcx + std::fabs(ky) * Lcy) / (2.0 * PI_D) > 1.0 / 16.0) Q.taylor = 0;
     }
     P.drag_o = f.Cd * f.rho_o * PI_D;
     P.drag_a = f.Ca * f.rho_a * PI_D;
@@ -657,6 +687,11 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
             std::fabs(f.modes[4 * k + 1]) > 1024 || std::fabs(f.modes[4 * k + 2]) > 1024)
             return fail(MS_ERR_ARG, "mode %d: wave numbers must be integers of magnitude <= 1024", k);
     }
+    if (f.n_vmodes < 0 || f.n_modes + f.n_vmodes > MS_MAX_MODES)
+        return fail(MS_ERR_ARG, "n_modes + n_vmodes must be in [0, %d]", MS_MAX_MODES);
+    if (f.n_vmodes > 0 && !f.vmodes) return fail(MS_ERR_ARG, "vmodes is NULL");
+    for (int k = 0; k < 5 * f.n_vmodes; k++)
+        if (!isfin(f.vmodes[k])) return fail(MS_ERR_ARG, "velocity mode %d is not finite", k / 5);
     const double vals[] = {f.uo_x, f.uo_y, f.rho_o, f.Cd, f.rho_a, f.Ca, f.wind_x, f.wind_y, f.wind_period,
                            f.rho_ice, f.E, f.G, f.eta, f.mu, f.h_ref};
     for (double v : vals)
@@ -676,6 +711,8 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->fc = f;
     m->modes.assign(f.modes ? f.modes : nullptr, f.modes ? f.modes + 4 * f.n_modes : nullptr);
     m->fc.modes = m->modes.data();
+    m->vmodes.assign(f.vmodes ? f.vmodes : nullptr, f.vmodes ? f.vmodes + 5 * f.n_vmodes : nullptr);
+    m->fc.vmodes = m->vmodes.data();
     m->n = floes->n;
     m->ncell = grid->nx * grid->ny;
     m->g.nx = grid->nx;

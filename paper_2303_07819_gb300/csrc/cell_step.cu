@@ -211,10 +211,7 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
         const int ix = c % sc.g.nx, iy = c / sc.g.nx;
         if (threadIdx.x < P.n_modes) {
             const int m = threadIdx.x;
-            int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
-            int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
-            float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
-            base[threadIdx.x] = b - floorf(b);
+            base[threadIdx.x] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
         }
         for (int k = threadIdx.x; k < n; k += T) {
             A[k] = make_float4(in.r[o + k], in.h[o + k], in.u[o + k], in.v[o + k]);
@@ -428,10 +425,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         const int nbins = nb * nb;
         if (threadIdx.x < P.n_modes) {
             const int m = threadIdx.x;
-            int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
-            int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
-            const float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
-            sm.base[m] = b - floorf(b);
+            sm.base[m] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
         }
         for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
         __syncthreads();
@@ -747,10 +741,7 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
     }
     if (lane < P.n_modes) {
         const int m = lane;
-        int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
-        int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
-        float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
-        b -= floorf(b);
+        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
         float sn, cs;
         if (P.taylor) {
             sincospif(2.0f * b, &sn, &cs);
@@ -929,7 +920,7 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             }
         } else {
             for (int m = 0; m < P.n_modes; m++) {
-                const float cyc = sm.Cm[m].x + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+                const float cyc = sm.Cm[m].x + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
                 float sn, cs;
                 sincospif(2.0f * cyc, &sn, &cs);
                 uo -= P.mAu[m] * cs;
@@ -1065,10 +1056,7 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
     if (sc.couple && lane < NWIN) R.win[lane] = sc.win[(size_t)lane * nc + c];
     if (lane < P.n_modes) {
         const int m = lane;
-        int ax = (P.mkx[m] * ix) % sc.g.nx; if (ax < 0) ax += sc.g.nx;
-        int ay = (P.mky[m] * iy) % sc.g.ny; if (ay < 0) ay += sc.g.ny;
-        float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
-        b -= floorf(b);
+        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
         float sn, cs;
         if (P.taylor) {
             sincospif(2.0f * b, &sn, &cs);
@@ -1267,7 +1255,7 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
                 }
             } else {
                 for (int m = 0; m < P.n_modes; m++) {
-                    const float cyc = sm.Cm[m].x + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+                    const float cyc = sm.Cm[m].x + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
                     float sn, cs;
                     sincospif(2.0f * cyc, &sn, &cs);
                     uo -= P.mAu[m] * cs;

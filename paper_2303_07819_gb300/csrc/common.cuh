@@ -35,20 +35,33 @@ struct Ctrl {
     unsigned long long pad[3];
 };
 
-// Physical constants in the kernel's arithmetic type.  FP64 kernels use the
-// radian wave numbers (mKx, mKy, mPh); FP32 kernels use integer wave numbers
-// and phases in cycles so that the global phase can be reduced exactly with
-// the integer cell index.
+// Physical constants in the kernel's arithmetic type.
+//
+// Ocean modes (stream-function modes first, then velocity modes): every mode
+// m adds (-mAu, mAv) cos(th) to the current and -mAz sin(th) to its curl, th
+// = mKx X + mKy Y + mPh.  A stream-function mode A sin(th) has (mAu, mAv,
+// mAz) = (A ky, A kx, A |k|^2); a velocity mode (Au, Av) cos(th) has
+// (-Au, Av, Av kx - Au ky).  FP64 kernels evaluate th directly.  FP32 kernels
+// split th into the phase at the cell's corner (in cycles, reduced to [0, 1))
+// and the turn across the cell: for a stream-function mode the wave numbers
+// are integers per domain, so the corner phase is reduced exactly with the
+// integer cell index; a velocity mode may have any real wave numbers, and its
+// corner phase is reduced in FP64.
 template <class R>
 struct Phys {
     R uo_x, uo_y;
-    int n_modes;
-    R mA[MAXM], mKx[MAXM], mKy[MAXM], mPh[MAXM];   // FP64: A, 2 pi kx/Lx, 2 pi ky/Ly, phi
-    int mkx[MAXM], mky[MAXM];                      // FP32: integer wave numbers
-    R mCyc[MAXM];                                  // FP32: phi / 2 pi
-    R mAu[MAXM], mAv[MAXM], mAz[MAXM];             // FP32: A ky', A kx', A |k'|^2
+    int n_modes;                                   // stream-function + velocity modes
+    R mA[MAXM], mKx[MAXM], mKy[MAXM], mPh[MAXM];   // A (stream modes), kx, ky (rad per length), phi
+    R mAu[MAXM], mAv[MAXM], mAz[MAXM];             // see above
+    R mAd[MAXM];                                   // divergence: -mAd sin(th) (Au kx + Av ky; 0 for stream modes)
+    int isint[MAXM];                               // 1: stream mode with integer wave numbers per domain
+    int mkx[MAXM], mky[MAXM];                      // FP32, integer modes: wave numbers per domain
+    R mCyc[MAXM];                                  // FP32: phi / 2 pi reduced to [0, 1)
+    double bx[MAXM], by[MAXM], bph[MAXM];          // FP32, real modes: cycles per cell in x, y, phi / 2 pi (FP64)
+    R kcx[MAXM], kcy[MAXM];                        // FP32, real modes: the same in FP32 (turn across a cell)
+    R kdx[MAXM], kdy[MAXM];                        // FP32: cycles per domain (the truth DEM's phase)
     int taylor;                                    // FP32: 1 if every mode turns by <= 1/16 cycle across a cell
-    R ta[MAXM], tb[MAXM];                          // FP32: 2 pi kx / nx, 2 pi ky / ny (radians per cell)
+    R ta[MAXM], tb[MAXM];                          // FP32: kx Lcx, ky Lcy (radians per cell)
     R drag_o;      // Cd rho_o pi
     R drag_a;      // Ca rho_a pi
     R wind_x, wind_y, wind_w;   // wind at t = 0 and its turning rate 2 pi / period
@@ -130,9 +143,8 @@ __device__ __forceinline__ void drag_force(const Phys<R> &P, R uo, R vo, R zeta,
     T = bo * dw * fabs(dw);
 }
 
-// Ocean current and its curl at a global position, FP64:
-// u = uo_x - sum A ky cos(th), v = uo_y + sum A kx cos(th), curl = -sum A |k|^2 sin(th),
-// th = kx X + ky Y + phi (psi = sum A sin(th)).
+// Ocean current and its curl at a global position, FP64 (mode coefficients
+// as described at Phys).
 __device__ __forceinline__ void ocean_f64(const Phys<double> &P, double X, double Y,
                                           double &uo, double &vo, double &zeta)
 {
@@ -141,24 +153,56 @@ __device__ __forceinline__ void ocean_f64(const Phys<double> &P, double X, doubl
         const double th = P.mKx[m] * X + P.mKy[m] * Y + P.mPh[m];
         double s, c;
         sincos(th, &s, &c);
-        const double A = P.mA[m];
-        uo -= A * P.mKy[m] * c;
-        vo += A * P.mKx[m] * c;
-        zeta -= A * (P.mKx[m] * P.mKx[m] + P.mKy[m] * P.mKy[m]) * s;
+        uo -= P.mAu[m] * c;
+        vo += P.mAv[m] * c;
+        zeta -= P.mAz[m] * s;
     }
 }
 
-// FP32 ocean at cell (ix, iy) + fraction (xf, yf) of the cell.  The phase in
-// cycles is ((kx ix) mod nx + kx xf)/nx + ((ky iy) mod ny + ky yf)/ny + phi/2pi,
-// with the integer part reduced exactly.  base[m] holds the cell's
-// ((kx ix) mod nx)/nx + ((ky iy) mod ny)/ny + phi/2pi.
+// Divergence of the current at a global position, FP64.
+__device__ __forceinline__ double ocean_div_f64(const Phys<double> &P, double X, double Y)
+{
+    double d = 0.0;
+    for (int m = 0; m < P.n_modes; m++)
+        if (P.mAd[m] != 0.0) d -= P.mAd[m] * sin(P.mKx[m] * X + P.mKy[m] * Y + P.mPh[m]);
+    return d;
+}
+
+// FP32 phase of mode m at the corner of cell (ix, iy), in cycles, in [0, 1]:
+// ((kx ix) mod nx)/nx + ((ky iy) mod ny)/ny + phi/2pi with the integer part
+// reduced exactly (stream modes), or the FP64 product reduced (real modes).
+__device__ __forceinline__ float corner_phase(const Phys<float> &P, int m, int ix, int iy, int nx, int ny,
+                                              float inx, float iny)
+{
+    if (P.isint[m]) {
+        int ax = (P.mkx[m] * ix) % nx; if (ax < 0) ax += nx;
+        int ay = (P.mky[m] * iy) % ny; if (ay < 0) ay += ny;
+        const float b = (float)ax * inx + (float)ay * iny + P.mCyc[m];
+        return b - floorf(b);
+    }
+    double b = P.bx[m] * ix + P.by[m] * iy + P.bph[m];
+    return (float)(b - floor(b));
+}
+
+// FP32 turn of mode m across the fraction (xf, yf) of a cell, in cycles
+__device__ __forceinline__ float turn_x(const Phys<float> &P, int m, float xf, float inx)
+{
+    return P.isint[m] ? (float)P.mkx[m] * xf * inx : P.kcx[m] * xf;
+}
+__device__ __forceinline__ float turn_y(const Phys<float> &P, int m, float yf, float iny)
+{
+    return P.isint[m] ? (float)P.mky[m] * yf * iny : P.kcy[m] * yf;
+}
+
+// FP32 ocean at cell (ix, iy) + fraction (xf, yf) of the cell; base[m] is the
+// mode's corner phase (corner_phase).
 __device__ __forceinline__ void ocean_f32(const Phys<float> &P, const float *base, float inx,
                                           float iny, float xf, float yf, float &uo, float &vo,
                                           float &zeta)
 {
     uo = P.uo_x; vo = P.uo_y; zeta = 0.0f;
     for (int m = 0; m < P.n_modes; m++) {
-        const float cyc = base[m] + (float)P.mkx[m] * xf * inx + (float)P.mky[m] * yf * iny;
+        const float cyc = base[m] + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
         float s, c;
         sincospif(2.0f * cyc, &s, &c);
         uo -= P.mAu[m] * c;

@@ -52,7 +52,8 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
     ocean_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy, uo, vo, zeta);
     double ua, va;
     wind_at(P, (double)ctrl->base * dt, ua, va);
-    const double f[NF] = {M / Ac, ub, vb, wb, su, sv, uo, vo, 0.0, zeta, ua, va};
+    const double div = ocean_div_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy);
+    const double f[NF] = {M / Ac, ub, vb, wb, su, sv, uo, vo, div, zeta, ua, va};
     for (int k = 0; k < NF; k++) X[(size_t)c * NF + k] = (float)f[k];
 }
 

@@ -185,11 +185,11 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
             }
         }
     }
-    // ocean at the domain fraction; wave numbers are integer over the domain
+    // ocean at the domain fraction, phases in cycles per domain
     const float xf = (float)xl * 2.3283064365386963e-10f, yf = (float)yl * 2.3283064365386963e-10f;
     float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
     for (int m = 0; m < P.n_modes; m++) {
-        float cyc = (float)P.mkx[m] * xf + (float)P.mky[m] * yf + P.mCyc[m];
+        float cyc = P.kdx[m] * xf + P.kdy[m] * yf + P.mCyc[m];
         cyc -= floorf(cyc);
         float s, c;
         sincospif(2.0f * cyc, &s, &c);

@@ -256,6 +256,43 @@ def scenario41(nfx: int = 480, nfy: int = 240, nx: int = 48, ny: int = 24,
             "floes": fl, "dt": 1e-4, "nsteps": 2000, "meta": {}}
 
 
+# Ocean drag constant of the non-dimensional Secs. 4.2-4.3 runs (the paper
+# gives none): with rho_o = rho_ice = h = 1 the drag acceleration is
+# Cd (u_o - v)|u_o - v|.  Reading: one length unit = 100 km (a 400 x 200 km
+# domain) and 1 m thick ice with Cd = 5.5e-3, rho_o = 1026, rho_ice = 920,
+# i.e. Cd rho_o / (rho_ice h) = 6.1e-3 per metre = 613 per length unit; floes
+# then follow the current within a few hundredths of a time unit.
+SEC4_DRAG = 613.0
+
+
+def sec42_vmodes() -> np.ndarray:
+    """Sec. 4.2 current u_o = (0.3 - 0.1 cos(pi x), 0): the uniform part plus
+    one velocity mode (Au, Av, kx, ky, phi) = (-0.1, 0, pi, 0, 0)."""
+    return np.array([[-0.1, 0.0, np.pi, 0.0, 0.0]])
+
+
+def sec43_vmodes() -> np.ndarray:
+    """Sec. 4.3 current u_o = (0.3 - 0.1 sin(0.1 pi x) cos(pi y),
+    0.05 cos(0.1 pi x) sin(pi y)) as velocity modes: with a = 0.1 pi x and
+    b = pi y, sin(a) cos(b) = (sin(a + b) + sin(a - b))/2 and cos(a) sin(b) =
+    (sin(a + b) - sin(a - b))/2, and sin(t) = cos(t - pi/2)."""
+    k = 0.1 * np.pi
+    return np.array([[-0.05, 0.025, k, np.pi, -0.5 * np.pi],
+                     [-0.05, -0.025, k, -np.pi, -0.5 * np.pi]])
+
+
+def scenario4x(which: int, nfx: int = 480, nfy: int = 240, nx: int = 48, ny: int = 24) -> dict:
+    """Secs. 4.2 and 4.3: the floes, domain, grid, time step, drag and
+    initial state of Sec. 4.1 (both sections keep that setting; floes start
+    with velocity (0.3, 0) and no spin) with the compressible currents of
+    those sections (uniform part (0.3, 0) plus velocity modes)."""
+    s = scenario41(nfx=nfx, nfy=nfy, nx=nx, ny=ny)
+    s["params"]["vmodes"] = sec42_vmodes() if which == 2 else sec43_vmodes()
+    s["params"]["Cd"] = SEC4_DRAG
+    s["name"] = f"Sec. 4.{which} compressible current, {nfx}x{nfy} floes, {nx}x{ny} coarse"
+    return s
+
+
 def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, rmax: float,
                       vscale: float = 0.2, wscale: float = 1e-4, overlap_ok: bool = True) -> dict:
     """n floes in one periodic square of side L with random radii, velocities

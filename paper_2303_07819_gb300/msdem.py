@@ -41,6 +41,7 @@ class Forcing(C.Structure):
         ("rho_ice", C.c_double), ("E", C.c_double), ("G", C.c_double), ("eta", C.c_double),
         ("mu", C.c_double), ("h_ref", C.c_double), ("inertia_half", C.c_int32),
         ("couple", C.c_int32), ("N0", C.c_int32), ("n_t", C.c_int32), ("precision", C.c_int32),
+        ("n_vmodes", C.c_int32), ("vmodes", _dp),
     ]
 
 
@@ -125,6 +126,7 @@ def make_floes(floes: dict):
 
 def make_forcing(p: dict, precision: int):
     modes = np.ascontiguousarray(np.asarray(p.get("modes", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4))
+    vmodes = np.ascontiguousarray(np.asarray(p.get("vmodes", np.zeros((0, 5))), dtype=np.float64).reshape(-1, 5))
     f = Forcing()
     f.uo_x, f.uo_y = float(p.get("uo_x", 0.0)), float(p.get("uo_y", 0.0))
     f.n_modes = modes.shape[0]
@@ -135,7 +137,9 @@ def make_forcing(p: dict, precision: int):
     f.inertia_half = int(p.get("inertia_half", 0))
     f.couple, f.N0, f.n_t = int(p.get("couple", 0)), int(p.get("N0", 100)), int(p.get("n_t", 10))
     f.precision = int(precision)
-    return f, modes
+    f.n_vmodes = vmodes.shape[0]
+    f.vmodes = _ptr(vmodes) if vmodes.shape[0] else _dp()
+    return f, (modes, vmodes)
 
 
 class Model:

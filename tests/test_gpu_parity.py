@@ -97,6 +97,35 @@ def test_truth_config1_small_fp64(orc, ms):
     assert e.max() <= TOL64, report(e)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_velocity_modes_msdem_and_truth(orc, ms, precision):
+    """Compressible velocity-mode currents against the oracle: the Sec. 4.3
+    current (real wave numbers, not periodic over the domain) on 96 x 48
+    floes and 12 x 6 cells (64 per cell), msDEM over two coarse steps and the
+    truth DEM; then stream-function and velocity modes together on config1's
+    cells."""
+    tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
+    s = I.scenario4x(3, 96, 48, 12, 6)
+    p = s["params"]
+    o, g, _ = run_pair(orc, ms, s, precision, 250)
+    e = rel_errors(g.moments(), o.moments(), p, eps)
+    assert e.max() <= tol, report(e)
+    ot = orc.Truth(dict(p, couple=0), s["floes"])
+    gt = ms.Model(dict(p, couple=0), s["floes"], precision)
+    ot.step(s["dt"], 200)
+    gt.truth_step(s["dt"], 200)
+    e = rel_errors(gt.truth_moments(), ot.moments(), p, eps)
+    assert e.max() <= tol, report(e)
+    # stream-function modes and velocity modes together (config1 laws)
+    c = I.config1(nx=4)
+    L = c["params"]["Lx"]
+    vm = np.array([[0.03, -0.02, 2 * np.pi * 1.3 / L, 2 * np.pi * 0.4 / L, 0.3],
+                   [-0.01, 0.04, 2 * np.pi * -0.7 / L, 2 * np.pi * 2.1 / L, 1.1]])
+    o, g, p = run_pair(orc, ms, c, precision, 100, params={"vmodes": vm})
+    e = rel_errors(g.moments(), o.moments(), p, eps)
+    assert e.max() <= tol, report(e)
+
+
 def ragged_scenario(counts, L_c=12.5e3, seed=5):
     """Cells with the given floe counts (0 allowed) on a small periodic grid,
     power-law radii rescaled to 45% cover, config1 forcing."""

@@ -131,6 +131,47 @@ def test_forcing_random_modes_rms_and_divergence(orc):
         assert abs((du + dv) / (2 * h)) < 1e-9
 
 
+def test_forcing_sec42_sec43_currents(orc):
+    """Velocity modes reproduce the currents of Secs. 4.2 and 4.3 as printed,
+    their curl (central differences of u, v), and the divergence Sec. 4.3
+    prints for its current, 0.04 pi cos(0.1 pi x) cos(pi y)."""
+    rng = np.random.default_rng(3)
+    for which in (2, 3):
+        p = base_params(vmodes=(I.sec42_vmodes() if which == 2 else I.sec43_vmodes()), uo_x=0.3, uo_y=0.0,
+                        Lx=4.0, Ly=2.0)
+        for X, Y in rng.uniform(0, 1, size=(20, 2)) * [4.0, 2.0]:
+            f = orc.forcing(p, X, Y, 0.0)
+            if which == 2:
+                u, v = 0.3 - 0.1 * math.cos(PI * X), 0.0
+            else:
+                u = 0.3 - 0.1 * math.sin(0.1 * PI * X) * math.cos(PI * Y)
+                v = 0.05 * math.cos(0.1 * PI * X) * math.sin(PI * Y)
+            assert abs(f[0] - u) < 1e-15 and abs(f[1] - v) < 1e-15, (which, f[:2], u, v)
+            h = 1e-5
+            dvdx = (orc.forcing(p, X + h, Y)[1] - orc.forcing(p, X - h, Y)[1]) / (2 * h)
+            dudy = (orc.forcing(p, X, Y + h)[0] - orc.forcing(p, X, Y - h)[0]) / (2 * h)
+            assert abs(f[2] - (dvdx - dudy)) < 1e-8, (which, f[2], dvdx - dudy)
+            dudx = (orc.forcing(p, X + h, Y)[0] - orc.forcing(p, X - h, Y)[0]) / (2 * h)
+            dvdy = (orc.forcing(p, X, Y + h)[1] - orc.forcing(p, X, Y - h)[1]) / (2 * h)
+            div = 0.1 * PI * math.sin(PI * X) if which == 2 else \
+                0.04 * PI * math.cos(0.1 * PI * X) * math.cos(PI * Y)
+            assert abs(dudx + dvdy - div) < 1e-8, (which, dudx + dvdy, div)
+
+
+def test_stream_mode_equals_velocity_mode(orc):
+    """A stream-function mode A sin(k.X + phi) is the velocity mode
+    (Au, Av) = (-A ky, A kx) of the same phase (u = -dpsi/dy, v = dpsi/dx)."""
+    L = 2.0e5
+    sm = np.array([[3.0e3, 2.0, -1.0, 0.7]])
+    kx, ky = 2 * PI * 2.0 / L, 2 * PI * -1.0 / L
+    vm = np.array([[-3.0e3 * ky, 3.0e3 * kx, kx, ky, 0.7]])
+    a = base_params(modes=sm, Lx=L, Ly=L)
+    b = base_params(vmodes=vm, Lx=L, Ly=L)
+    for X, Y in np.random.default_rng(5).uniform(0, L, size=(10, 2)):
+        fa, fb = orc.forcing(a, X, Y, 0.0), orc.forcing(b, X, Y, 0.0)
+        assert np.allclose(fa[:3], fb[:3], rtol=1e-13, atol=1e-18), (fa, fb)
+
+
 def test_wind_rotation(orc):
     p = base_params(wind_x=10.0, wind_y=0.0, wind_period=6 * 3600.0)
     f = orc.forcing(p, 0.0, 0.0, 1.5 * 3600.0)
@@ -459,6 +500,28 @@ def test_single_cell_model_equals_truth(orc):
     for k in ("x", "y", "u", "v", "omega"):
         assert np.array_equal(fa[k], fb[k])
     assert np.array_equal(a.moments(), b.moments())
+
+
+def test_truth_binned_search_equals_all_pairs(orc):
+    """The oracle's binned truth search finds the pairs of the all-pairs loop
+    and sums them in its order: identical floes, bit for bit, on crowded
+    random floes with overlaps (many contacts, some across the periodic
+    edges) and on the Sec. 4.2 floes as they gather."""
+    rng = np.random.default_rng(11)
+    L = 2.0e4
+    fl = I.random_cell_floes(rng, 600, L, 150.0, 450.0)
+    p = base_params(Lx=L, Ly=L, eta=20.0)
+    cases = [(p, fl, 1.0, 40)]
+    s = I.scenario4x(2, 48, 24, 6, 3)
+    cases.append((dict(s["params"], couple=0), s["floes"], s["dt"], 300))
+    for prm, f, dt, ns in cases:
+        a, b = orc.Truth(prm, f), orc.Truth(prm, f)
+        a.set_brute(True)
+        a.step(dt, ns)
+        b.step(dt, ns)
+        fa, fb = a.floes(), b.floes()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
 
 
 def test_l2_norm_definition(orc):
