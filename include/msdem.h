@@ -50,10 +50,19 @@ enum { MS_FP32 = 0, MS_FP64 = 1 };
 
 /* Coarse grid over the doubly periodic domain [0, Lx) x [0, Ly): nx x ny
  * cells of side (Lx/nx, Ly/ny); cell c = iy * nx + ix.  Each cell carries its
- * own periodic DEM (Sec. 3.1). */
+ * own periodic DEM (Sec. 3.1).
+ * nens > 1: an ensemble of nens independent realizations of that domain
+ * (same forcing, own floes), batched in one model.  Realization e occupies
+ * y in [e Ly, (e + 1) Ly) (floe y coordinates, ms_get_floes and cell indices
+ * c = (e ny + iy) nx + ix follow this stacking); each realization is periodic
+ * on its own, in the coarse step as in the ocean forcing, and takes its own
+ * number of Lax-Friedrichs substeps, so the result is that of nens separate
+ * models.  An ensemble has no truth DEM (ms_truth_* return MS_ERR_STATE).
+ * 0 or 1: one realization. */
 typedef struct ms_grid {
     int32_t nx, ny;
     double Lx, Ly;
+    int32_t nens;
 } ms_grid;
 
 /* Floe state (Sec. 2.1): centre (x, y) in domain coordinates, angle theta,

@@ -58,6 +58,7 @@ struct ms_model {
     double *d_mom = nullptr, *d_win = nullptr, *d_q0 = nullptr, *d_q1 = nullptr, *d_V = nullptr,
            *d_S = nullptr, *d_tgt = nullptr, *d_xmom = nullptr, *d_xwin = nullptr;
     Ctrl *d_ctrl = nullptr;
+    unsigned long long *d_cmax = nullptr;   // [nens] coarse-step CFL maxima
     // truth
     DevState32 t32[2]{};
     DevState64 t64[2]{};
@@ -304,7 +305,7 @@ static Geo32 geo32(double Lx, double Ly, int nx, int ny, double dt)
 static StepCommon step_common(ms_model *m, long long i_local, double *mom, double *win)
 {
     StepCommon sc;
-    sc.k = geo32(m->g.Lcx, m->g.Lcy, m->g.nx, m->g.ny, m->dt);
+    sc.k = geo32(m->g.Lcx, m->g.Lcy, m->g.nx, m->g.nyr, m->dt);
     sc.live = nullptr;
     sc.off = m->d_off;
     sc.order = m->d_order;
@@ -328,6 +329,9 @@ static CoarseArgs coarse_args(ms_model *m)
     CoarseArgs a;
     a.nx = m->g.nx;
     a.ny = m->g.ny;
+    a.nyr = m->g.nyr;
+    a.nens = m->g.nens;
+    a.cmax = m->d_cmax;
     a.dx = m->g.Lcx;
     a.dy = m->g.Lcy;
     a.Ac = m->g.Lcx * m->g.Lcy;
@@ -673,7 +677,9 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     *out = nullptr;
     if (!grid || !forcing) return fail(MS_ERR_ARG, "grid or forcing is NULL");
     if (grid->nx < 1 || grid->ny < 1) return fail(MS_ERR_ARG, "grid needs nx, ny >= 1");
-    if ((long long)grid->nx * grid->ny > (1LL << 24)) return fail(MS_ERR_ARG, "more than 2^24 cells");
+    if (grid->nens < 0 || grid->nens > 65536) return fail(MS_ERR_ARG, "nens must be in [0, 65536]");
+    const int nens = grid->nens > 1 ? grid->nens : 1;
+    if ((long long)grid->nx * grid->ny * nens > (1LL << 24)) return fail(MS_ERR_ARG, "more than 2^24 cells");
     if (!(grid->Lx > 0.0) || !(grid->Ly > 0.0) || !isfin(grid->Lx) || !isfin(grid->Ly))
         return fail(MS_ERR_ARG, "domain sides must be positive and finite");
     const ms_forcing &f = *forcing;
@@ -714,11 +720,13 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->vmodes.assign(f.vmodes ? f.vmodes : nullptr, f.vmodes ? f.vmodes + 5 * f.n_vmodes : nullptr);
     m->fc.vmodes = m->vmodes.data();
     m->n = floes->n;
-    m->ncell = grid->nx * grid->ny;
+    m->ncell = grid->nx * grid->ny * nens;
     m->g.nx = grid->nx;
-    m->g.ny = grid->ny;
+    m->g.ny = grid->ny * nens;
+    m->g.nyr = grid->ny;
+    m->g.nens = nens;
     m->g.Lx = grid->Lx;
-    m->g.Ly = grid->Ly;
+    m->g.Ly = grid->Ly * nens;
     m->g.Lcx = grid->Lx / grid->nx;
     m->g.Lcy = grid->Ly / grid->ny;
     m->interval = f.couple ? f.N0 : 100;
@@ -730,8 +738,8 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->h_cell_of_orig.resize(n);
     m->h_off.assign(m->ncell + 1, 0);
     for (long long l = 0; l < n; l++) {
-        const int c = cell_index(floes->y[l], grid->Ly, m->g.Lcy, grid->ny) * grid->nx +
-                      cell_index(floes->x[l], grid->Lx, m->g.Lcx, grid->nx);
+        const int c = cell_index(floes->y[l], m->g.Ly, m->g.Lcy, m->g.ny) * m->g.nx +
+                      cell_index(floes->x[l], m->g.Lx, m->g.Lcx, m->g.nx);
         m->h_cell_of_orig[l] = c;
         m->h_off[c + 1]++;
         rmax = std::max(rmax, floes->r[l]);
@@ -794,15 +802,21 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(dalloc(m, &m->d_tgt, (size_t)nc * 4));
     CKM(dalloc(m, &m->d_tmom, (size_t)nc * NMOM));
     CKM(dalloc(m, &m->d_ctrl, 1));
+    CKM(dalloc(m, &m->d_cmax, nens));
+    CKM(cudaMemsetAsync(m->d_cmax, 0, sizeof(unsigned long long) * nens, m->stream));
     if (m->precision == MS_FP64) {
         CKM(alloc64(m, m->s64, n));
-        CKM(alloc64(m, m->t64[0], n));
-        CKM(alloc64(m, m->t64[1], n));
+        if (nens == 1) {
+            CKM(alloc64(m, m->t64[0], n));
+            CKM(alloc64(m, m->t64[1], n));
+        }
         CKM(dalloc(m, (double **)&m->d_fd, 3 * (size_t)n));
     } else {
         CKM(alloc32(m, m->s32, n));
-        CKM(alloc32(m, m->t32[0], n));
-        CKM(alloc32(m, m->t32[1], n));
+        if (nens == 1) {
+            CKM(alloc32(m, m->t32[0], n));
+            CKM(alloc32(m, m->t32[1], n));
+        }
         CKM(dalloc(m, (float **)&m->d_fd, 3 * (size_t)n));
     }
     CKM(cudaMemsetAsync(m->d_ctrl, 0, sizeof(Ctrl), m->stream));
@@ -813,8 +827,9 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaMemcpyAsync(m->d_order, m->h_order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
     CKM(cudaStreamSynchronize(m->stream));
 #undef CKM
-    if ((rc = upload_model_state(m, floes)) || (rc = upload_truth_state(m, floes)) ||
-        (rc = setup_truth_bins(m, rmax > 0 ? rmax : 1.0))) {
+    // an ensemble has no truth DEM (each realization's truth is a model of its own)
+    if ((rc = upload_model_state(m, floes)) ||
+        (nens == 1 && ((rc = upload_truth_state(m, floes)) || (rc = setup_truth_bins(m, rmax > 0 ? rmax : 1.0))))) {
         ms_free(m);
         return rc;
     }
@@ -985,9 +1000,15 @@ int ms_get_floes(ms_model *m, double *out)
     return download(m, false, out);
 }
 
+static int no_truth(const ms_model *m)
+{
+    return m->g.nens > 1 ? fail(MS_ERR_STATE, "an ensemble model has no truth DEM") : MS_OK;
+}
+
 int ms_truth_get_floes(ms_model *m, double *out)
 {
     if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    if (no_truth(m)) return MS_ERR_STATE;
     return download(m, true, out);
 }
 
@@ -1027,6 +1048,7 @@ static cudaError_t truth_one(ms_model *m, int cur, int nxt, long long step)
 int ms_truth_step(ms_model *m, double dt, int64_t nsteps)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (no_truth(m)) return MS_ERR_STATE;
     if (!(dt > 0.0) || !isfin(dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
     if (m->truth_dt == 0.0) m->truth_dt = dt;
@@ -1042,6 +1064,7 @@ int ms_truth_step(ms_model *m, double dt, int64_t nsteps)
 int ms_truth_moments(ms_model *m, double *out)
 {
     if (!m || !out) return fail(MS_ERR_ARG, "NULL argument");
+    if (no_truth(m)) return MS_ERR_STATE;
     TruthArgs a;
     a.n = m->n;
     a.g = m->g;
@@ -1081,6 +1104,8 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
     if (!m || !mean_ms) return fail(MS_ERR_ARG, "NULL argument");
     if (reps < 1) return fail(MS_ERR_ARG, "reps < 1");
     if (!(dt > 0.0)) return fail(MS_ERR_ARG, "dt must be positive");
+    if (which == 1 && no_truth(m)) return MS_ERR_STATE;
+    if (which < 0 || which > 2) return fail(MS_ERR_ARG, "which must be 0, 1 or 2");
     const double saved = m->dt, tsaved = m->truth_dt;
     int rc = ensure_scratch(m);
     if (rc) return rc;
@@ -1220,9 +1245,11 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
     if (grid->nx < 1 || grid->ny < 1 || !(grid->Lx > 0.0) || !(grid->Ly > 0.0) || !isfin(grid->Lx) ||
         !isfin(grid->Ly))
         return fail(MS_ERR_ARG, "grid needs nx, ny >= 1 and positive finite sides");
-    if ((long long)grid->nx * grid->ny > noalloc_max_cells())
+    if (grid->nens < 0) return fail(MS_ERR_ARG, "nens must be >= 0");
+    const int nens = grid->nens > 1 ? grid->nens : 1;
+    if ((long long)grid->nx * grid->ny * nens > noalloc_max_cells())
         return fail(MS_ERR_ARG, "ms_cell_moments_noalloc handles at most %d cells, got %lld", noalloc_max_cells(),
-                    (long long)grid->nx * grid->ny);
+                    (long long)grid->nx * grid->ny * nens);
     if (n < 0 || n > noalloc_max_floes())
         return fail(MS_ERR_ARG, "ms_cell_moments_noalloc handles 0 to %lld floes, got %lld", noalloc_max_floes(),
                     (long long)n);
@@ -1231,9 +1258,11 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
     if (n > 0 && (!x || !y || !u || !v || !omega || !r || !h || !fd)) return fail(MS_ERR_ARG, "a floe array is NULL");
     Geom g;
     g.nx = grid->nx;
-    g.ny = grid->ny;
+    g.ny = grid->ny * nens;
+    g.nyr = grid->ny;
+    g.nens = nens;
     g.Lx = grid->Lx;
-    g.Ly = grid->Ly;
+    g.Ly = grid->Ly * nens;
     g.Lcx = grid->Lx / grid->nx;
     g.Lcy = grid->Ly / grid->ny;
     cudaStream_t st = (cudaStream_t)stream;

@@ -208,10 +208,10 @@ k_cell_step32_brute(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
          item = next_item(sc, persistent, sh_item, false)) {
         const int c = sc.order[item];
         const int o = sc.off[c], n = sc.off[c + 1] - o;
-        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
         if (threadIdx.x < P.n_modes) {
             const int m = threadIdx.x;
-            base[threadIdx.x] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
+            base[threadIdx.x] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
         }
         for (int k = threadIdx.x; k < n; k += T) {
             A[k] = make_float4(in.r[o + k], in.h[o + k], in.u[o + k], in.v[o + k]);
@@ -416,7 +416,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
     for (int item = item0 + blockIdx.x; item < item1; item += gridDim.x) {
         const int c = sc.order[item];
         const int o = sc.off[c], n = sc.off[c + 1] - o;
-        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
         int nb = (int)(sqrtf((float)n) / beta);
         nb = nb > nbmax ? nbmax : nb;
         if (nb < 3) nb = 0;                       // few floes: every floe in the list
@@ -425,7 +425,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         const int nbins = nb * nb;
         if (threadIdx.x < P.n_modes) {
             const int m = threadIdx.x;
-            sm.base[m] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
+            sm.base[m] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
         }
         for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
         __syncthreads();
@@ -728,7 +728,7 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
     const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
     const int c = sc.order[item];
     const int o = sc.off[c], n = sc.off[c + 1] - o;
-    const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+    const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
 
     float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
     if (bs.ramp) {
@@ -741,7 +741,7 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
     }
     if (lane < P.n_modes) {
         const int m = lane;
-        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
+        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
         float sn, cs;
         if (P.taylor) {
             sincospif(2.0f * b, &sn, &cs);
@@ -1042,7 +1042,7 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
     const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
     const int c = sc.order[item];
     const int o = sc.off[c], n = sc.off[c + 1] - o;
-    const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+    const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
     const long long base = sc.ctrl->base;
     const bool have_tgt = sc.couple && sc.ctrl->have_tgt;
     const int nc = sc.ncell;
@@ -1056,7 +1056,7 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
     if (sc.couple && lane < NWIN) R.win[lane] = sc.win[(size_t)lane * nc + c];
     if (lane < P.n_modes) {
         const int m = lane;
-        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.ny, inx, iny);
+        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
         float sn, cs;
         if (P.taylor) {
             sincospif(2.0f * b, &sn, &cs);
@@ -1356,7 +1356,7 @@ k_cell_step64_brute(DevState64 in, DevState64 out, Phys<double> P, StepCommon sc
          item = next_item(sc, persistent, sh_item, false)) {
         const int c = sc.order[item];
         const int o = sc.off[c], n = sc.off[c + 1] - o;
-        const int ix = c % sc.g.nx, iy = c / sc.g.nx;
+        const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
         const double X0 = ix * Lx, Y0 = iy * Ly;
         for (int k = threadIdx.x; k < n; k += T) {
             X[k] = in.x[o + k]; Y[k] = in.y[o + k]; U[k] = in.u[o + k]; V[k] = in.v[o + k];

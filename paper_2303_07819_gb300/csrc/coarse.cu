@@ -17,9 +17,11 @@ namespace msd {
 
 namespace {
 
-__device__ __forceinline__ int n_sub(const CoarseArgs &a)
+// substeps of realization e (each realization of an ensemble is its own
+// coarse problem, so each takes its own N1)
+__device__ __forceinline__ int n_sub(const CoarseArgs &a, int e)
 {
-    const double cmax = __longlong_as_double((long long)a.ctrl->cmax_bits);
+    const double cmax = __longlong_as_double((long long)a.cmax[e]);
     int N1 = (int)ceil(a.dT * cmax / 0.5);
     return N1 < 1 ? 1 : N1;
 }
@@ -48,22 +50,23 @@ __global__ void k_coarse_prepare(CoarseArgs a)
     for (int k = 0; k < NWIN; k++) a.win[k * nc + c] = 0.0;
     const double cx = fabs(Vx) / a.dx, cy = fabs(Vy) / a.dy;
     const double cc = cx > cy ? cx : cy;
-    atomicMax(&a.ctrl->cmax_bits, (unsigned long long)__double_as_longlong(cc));
+    atomicMax(&a.cmax[c / (a.nx * a.nyr)], (unsigned long long)__double_as_longlong(cc));
 }
 
 __global__ void k_coarse_lf(CoarseArgs a, int k)
 {
-    const int N1 = n_sub(a);
-    if (k >= N1) return;
-    const int nx = a.nx, ny = a.ny, nc = nx * ny;
+    const int nx = a.nx, ny = a.nyr, nc = nx * a.ny;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
+    const int e = c / (nx * ny);
+    const int N1 = n_sub(a, e);
+    if (k >= N1) return;
     const double *q = (k & 1) ? a.q1 : a.q0;
     double *qn = (k & 1) ? a.q0 : a.q1;
     const double dtau = a.dT / N1;
-    const int i = c % nx, j = c / nx;
-    const int cE = j * nx + (i + 1) % nx, cW = j * nx + (i + nx - 1) % nx;
-    const int cN = ((j + 1) % ny) * nx + i, cS = ((j + ny - 1) % ny) * nx + i;
+    const int i = c % nx, j = (c / nx) % ny, b = e * nx * ny;   // b: the realization's first cell
+    const int cE = b + j * nx + (i + 1) % nx, cW = b + j * nx + (i + nx - 1) % nx;
+    const int cN = b + ((j + 1) % ny) * nx + i, cS = b + ((j + ny - 1) % ny) * nx + i;
     const double *Vx = a.V, *Vy = a.V + nc;
 #pragma unroll
     for (int f = 0; f < 4; f++) {
@@ -89,7 +92,7 @@ __global__ void k_coarse_targets(CoarseArgs a)
     const int nc = a.nx * a.ny;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nc) return;
-    const int N1 = n_sub(a);
+    const int N1 = n_sub(a, c / (a.nx * a.nyr));
     const double *q = ((N1 < NSUB_MAX ? N1 : NSUB_MAX) & 1) ? a.q1 : a.q0;
     double qc[4];
     for (int f = 0; f < 4; f++) {
@@ -118,14 +121,18 @@ __global__ void k_coarse_targets(CoarseArgs a)
 
 __global__ void k_coarse_finish(CoarseArgs a)
 {
-    const int N1 = n_sub(a);
+    int N1 = 1;
+    for (int e = 0; e < a.nens; e++) {
+        const int n1 = n_sub(a, e);
+        N1 = n1 > N1 ? n1 : N1;
+        a.cmax[e] = 0ull;
+    }
     Ctrl *ctrl = a.ctrl;
-    ctrl->N1 = N1;
+    ctrl->N1 = N1;      // the largest over the realizations
     if (N1 > NSUB_MAX) ctrl->err |= ERR_CFL;
     ctrl->have_q = 1;
     ctrl->have_tgt = 1;
     ctrl->base += a.N0;
-    ctrl->cmax_bits = 0ull;
 }
 
 __global__ void k_advance(Ctrl *ctrl, int N0) { ctrl->base += N0; }

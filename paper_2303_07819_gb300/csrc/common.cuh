@@ -29,7 +29,6 @@ struct Ctrl {
     int have_tgt;                 // targets of the gradual update set
     int err;                      // ERR_* bits
     int N1;                       // LF substeps of the last coarse step
-    unsigned long long cmax_bits; // max over cells of |V|/dx (non-negative double, as bits)
     unsigned int queue[2];        // work-queue tickets, one per step parity
     unsigned long long deep;      // contacts with overlap deeper than r_min / 2 (diagnostic)
     unsigned long long pad[3];
@@ -70,9 +69,13 @@ struct Phys {
     R E, G, eta, mu, inv_h_ref;
 };
 
+// Coarse grid.  An ensemble of nens independent realizations is stored as
+// nens copies of the nx x nyr grid stacked in y (ny = nens nyr rows, Ly =
+// nens times one realization's side); each realization is periodic on its own.
 struct Geom {
     int nx, ny;
     double Lx, Ly, Lcx, Lcy;
+    int nyr, nens;      // rows per realization, realizations
 };
 
 // ---------------------------------------------------------------- helpers
@@ -307,7 +310,9 @@ cudaError_t cell_step_prepare(int precision, const CellLaunch &cl, size_t smem);
 
 // coarse.cu
 struct CoarseArgs {
-    int nx, ny;
+    int nx, ny;         // ny: rows of all realizations
+    int nyr, nens;      // rows per realization, realizations
+    unsigned long long *cmax;   // [nens] max over the realization's cells of |V|/dx (non-negative double bits)
     double dx, dy, Ac, dT;
     int N0;
     const double *mom;  // [ncell][NMOM]

@@ -47,7 +47,7 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
     const double sv = M > 0.0 ? fmax(mo[8] / M - vb0 * vb0, 0.0) : 0.0;
     const double sh = ctrl->have_tgt ? share : 0.0;
     const double ub = ub0 + sh * tgt[ncell + c], vb = vb0 + sh * tgt[2 * ncell + c], wb = wb0 + sh * tgt[3 * ncell + c];
-    const int ix = c % g.nx, iy = c / g.nx;
+    const int ix = c % g.nx, iy = (c / g.nx) % g.nyr;
     double uo, vo, zeta;
     ocean_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy, uo, vo, zeta);
     double ua, va;

@@ -233,6 +233,38 @@ def config2(seed: int | None = None, nx: int = 128) -> dict:
                             f"periodic {L/1e3:.0f} km, {nx}x{nx} cells, lognormal(96, 0.69) floes/cell")
 
 
+def stack_ensemble(scens: list) -> dict:
+    """An ensemble of realizations of one grid and forcing (different floes)
+    as one model input: realization e's floes move to y + e Ly (the stacking
+    of ms_grid.nens); params from the first realization with nens set."""
+    p = dict(scens[0]["params"], nens=len(scens))
+    Ly = p["Ly"]
+    fl = {k: np.concatenate([sc["floes"][k] + (e * Ly if k == "y" else 0.0) for e, sc in enumerate(scens)])
+          for k in scens[0]["floes"]}
+    return {"name": f"{len(scens)} realizations of {scens[0]['name']}", "params": p, "floes": fl,
+            "dt": scens[0]["dt"], "nsteps": scens[0]["nsteps"], "meta": {}}
+
+
+def config4(nreal: int = 16, nx: int = 256, seed: int | None = None) -> dict:
+    """Ensemble batch: nreal seeded realizations of an nx x nx grid of 25 km
+    cells with few floes per cell, lognormal(median 6, sigma 0.69) clipped to
+    [1, 64] (about 7.6 on average; 16 x 256^2 cells hold about 8M floes),
+    radius/thickness laws of config1, one ocean (8 modes) and one wind (10 m/s
+    turning with a 6 h period) for all realizations, dt = 5 s."""
+    base = (BASE_SEED + 4) if seed is None else seed
+    L = 25e3 * nx
+    forcing = random_modes(np.random.default_rng(base), 8, L, L, 0.1)
+    scens = []
+    for e in range(nreal):
+        rng = np.random.default_rng(base + 1 + e)
+        counts = lognormal_counts(rng, nx * nx, 6.0, 0.69, 1, 64)
+        sc = _powerlaw_config(rng, nx, nx, L, counts, 5.0, 10000, (10.0, 0.0), 6 * 3600.0, False,
+                              f"periodic {L/1e3:.0f} km, {nx}x{nx} cells, lognormal(6, 0.69) floes/cell")
+        sc["params"]["modes"] = forcing
+        scens.append(sc)
+    return stack_ensemble(scens)
+
+
 def scenario41(nfx: int = 480, nfy: int = 240, nx: int = 48, ny: int = 24,
                uo: tuple = (0.3, 0.0)) -> dict:
     """Sec. 4.1 of the paper (non-dimensional): domain [0,4] x [0,2], one floe at
@@ -305,7 +337,7 @@ def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, r
             "h": rng.uniform(0.5, 2.0, n)}
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2}
+CONFIGS = {0: config0, 1: config1, 2: config2, 4: config4}
 
 
 def mlp_init(seed: int = BASE_SEED + 3, layers=((12, 128), (128, 128), (128, 128), (128, 4))) -> dict:

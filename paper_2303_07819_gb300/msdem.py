@@ -26,7 +26,8 @@ _dp = C.POINTER(C.c_double)
 
 
 class Grid(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double)]
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("nens", C.c_int32)]
 
 
 class Floes(C.Structure):
@@ -149,14 +150,15 @@ class Model:
         L = load()
         self.params = dict(params)
         self.precision = precision
-        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]))
+        nens = max(1, int(params.get("nens", 1)))
+        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]), nens)
         fl, keep1 = make_floes(floes)
         fc, keep2 = make_forcing(params, precision)
         h = C.c_void_p()
         _check(L.ms_init(C.byref(h), C.byref(g), C.byref(fl), C.byref(fc)))
         self._h = h
         self.n = int(fl.n)
-        self.ncell = g.nx * g.ny
+        self.ncell = g.nx * g.ny * nens
 
     def close(self):
         if getattr(self, "_h", None):
@@ -274,7 +276,8 @@ def cell_moments_noalloc(params: dict, n: int, x: int, y: int, u: int, v: int, o
     include/msdem.h): for callers that must not allocate while they run.
     `out` receives ncell x 12 doubles; fd is [3][n] per-floe drag."""
     L = load()
-    g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]))
+    g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]),
+             max(1, int(params.get("nens", 1))))
     ptrs = [C.c_void_p(a) for a in (x, y, u, v, omega, r, h, fd, out)]
     _check(L.ms_cell_moments_noalloc(C.byref(g), float(params["rho_ice"]), int(params.get("inertia_half", 0)),
                                      int(n), *ptrs, C.c_void_p(stream or 0)))
