@@ -191,11 +191,13 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
  * 256; persistent = 1 runs a grid of resident blocks that take cells from a
  * work queue (largest cells first); bin_beta = bin side in units of the cell's
  * mean floe spacing (variants 1-3); variant 2 = binned, one warp per cell of
- * up to 256 floes and a block per larger cell, the size classes on concurrent
- * streams; variant 3 = variant 2 with each warp keeping its cell in shared
- * memory for a whole coarse interval (one launch per interval instead of one
- * per fine step; the per-step arithmetic of variant 2, and the same results
- * whether an interval runs in one launch or step by step).
+ * 33 to 256 floes, a block per larger cell, and cells of at most 32 floes
+ * packed several to a warp (a lane per floe, the floe kept in registers for a
+ * whole coarse interval), the size classes on concurrent streams; variant 3 =
+ * variant 2 with each warp cell also kept in shared memory for a whole
+ * coarse interval (one launch per interval instead of one per fine step; the
+ * per-step arithmetic of variant 2).  Variants 2 and 3 give the same results
+ * whether an interval runs in one launch or step by step.
  * MS_ERR_ARG for an unsupported choice. */
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
 

@@ -59,6 +59,7 @@ struct ms_model {
            *d_S = nullptr, *d_tgt = nullptr, *d_xmom = nullptr, *d_xwin = nullptr;
     Ctrl *d_ctrl = nullptr;
     unsigned long long *d_cmax = nullptr;   // [nens] coarse-step CFL maxima
+    int2 *d_pack = nullptr;                  // [ncell] packed-warp table (at most one warp per cell)
     // truth
     DevState32 t32[2]{};
     DevState64 t64[2]{};
@@ -309,6 +310,8 @@ static StepCommon step_common(ms_model *m, long long i_local, double *mom, doubl
     sc.live = nullptr;
     sc.off = m->d_off;
     sc.order = m->d_order;
+    sc.order0 = m->d_order;
+    sc.skip = nullptr;
     sc.ncell = m->ncell;
     sc.max_n = m->max_n;
     sc.mom = mom;
@@ -359,6 +362,7 @@ static StepCommon cell_common(ms_model *m, long long i_local, bool scratch_out)
     if (hybrid_on(m)) {
         sc.order = m->d_order2;
         sc.live = m->d_live;
+        sc.skip = m->d_isc;
     }
     return sc;
 }
@@ -382,7 +386,7 @@ static int64_t interval_launches(const ms_model *m)
     if (m->cl.variant == 0 || m->precision == MS_FP64) return m->interval;
     int64_t k = 0;
     for (int s = 0; s < m->cl.nseg; s++)
-        k += (m->cl.variant == 3 && m->cl.seg_kind[s] == 1) ? 1 : m->interval;
+        k += (m->cl.seg_kind[s] == 2 || (m->cl.variant == 3 && m->cl.seg_kind[s] == 1)) ? 1 : m->interval;
     return k;
 }
 
@@ -571,9 +575,10 @@ static void make_segments(ms_model *m, CellLaunch &c)
     // up to 256 floes warp-per-cell with the class bound as the warp capacity
     struct Cls { int hi, threads, kind; };
     const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
-    const Cls v2[6] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 1}, {192, 128, 1}, {128, 128, 1}, {64, 128, 1}};
+    const Cls v2[7] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 1}, {192, 128, 1},
+                       {128, 128, 1}, {64, 128, 1}, {32, 128, 2}};
     const Cls *cls = c.variant >= 2 ? v2 : v1;
-    const int ncls = c.variant >= 2 ? 6 : 4;
+    const int ncls = c.variant >= 2 ? 7 : 4;
     c.nseg = 0;
     c.nbmax = 32;
     int item = 0;
@@ -587,7 +592,7 @@ static void make_segments(ms_model *m, CellLaunch &c)
         c.seg_begin[c.nseg] = item;
         c.seg_end[c.nseg] = e;
         c.seg_kind[c.nseg] = cls[s].kind;
-        c.seg_maxn[c.nseg] = cls[s].kind == 1 ? cls[s].hi : std::max(1, ncount(item));
+        c.seg_maxn[c.nseg] = cls[s].kind >= 1 ? cls[s].hi : std::max(1, ncount(item));
         c.seg_threads[c.nseg] = cls[s].threads;
         c.nseg++;
         item = e;
@@ -605,6 +610,30 @@ static int configure_launch(ms_model *m, const CellLaunch &cl_in)
     if (cl.variant == 0 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure needs a binned cell kernel");
     if (cl.variant >= 1) make_segments(m, cl);
     else cl.nseg = 0;
+    // packed warps: consecutive cells of the class, at most 32 floes and 32
+    // cells per warp
+    cl.pack = m->d_pack;
+    cl.npack = 0;
+    for (int s = 0; s < cl.nseg; s++) {
+        if (cl.seg_kind[s] != 2) continue;
+        std::vector<int2> pk;
+        int first = cl.seg_begin[s], cnt = 0, sum = 0;
+        for (int it = cl.seg_begin[s]; it < cl.seg_end[s]; it++) {
+            const int cc = m->h_order[it], nf = m->h_off[cc + 1] - m->h_off[cc];
+            if (cnt > 0 && (sum + nf > 32 || cnt == 32)) {
+                pk.push_back(make_int2(first, cnt));
+                first = it;
+                cnt = 0;
+                sum = 0;
+            }
+            cnt++;
+            sum += nf;
+        }
+        if (cnt > 0) pk.push_back(make_int2(first, cnt));
+        cl.npack = (int)pk.size();
+        CK(cudaMemcpyAsync(m->d_pack, pk.data(), sizeof(int2) * pk.size(), cudaMemcpyHostToDevice, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
     if (m->d_segb && cl.nseg > 0) {
         CK(cudaMemcpyAsync(m->d_segb, cl.seg_begin, sizeof(int) * cl.nseg, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(m->d_sege, cl.seg_end, sizeof(int) * cl.nseg, cudaMemcpyHostToDevice, m->stream));
@@ -803,6 +832,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(dalloc(m, &m->d_tmom, (size_t)nc * NMOM));
     CKM(dalloc(m, &m->d_ctrl, 1));
     CKM(dalloc(m, &m->d_cmax, nens));
+    CKM(dalloc(m, &m->d_pack, nc));
     CKM(cudaMemsetAsync(m->d_cmax, 0, sizeof(unsigned long long) * nens, m->stream));
     if (m->precision == MS_FP64) {
         CKM(alloc64(m, m->s64, n));

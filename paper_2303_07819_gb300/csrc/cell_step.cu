@@ -1327,6 +1327,263 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
     if (deep_steps) atomicAdd(&sc.ctrl->deep, (unsigned long long)deep_steps);
 }
 
+// ================================================= FP32 packed warps, resident
+// Cells of at most 32 floes (few-floe cells, as in an ensemble of sparse
+// realizations), several to a warp with a lane per floe: the lanes of one
+// cell are contiguous, and a host table lists each warp's cells (consecutive
+// in the processing order, 32 floes at most together).  Each lane keeps its
+// floe in registers for the whole run of steps; shared memory holds only the
+// copy of the step's start state that the other lanes of the cell read.  No
+// bins: a lane tests every other floe of its cell, in floe order.  A cell's
+// moments are a segmented shuffle sum over its lanes (a fixed tree order).
+
+constexpr int PACKW = 32;   // floes (and cells) per packed warp at most
+
+struct PackSm {
+    uint2 *Q;      // [32] fixed-point position
+    float4 *A;     // [32] u, v, w, r
+    float *H;      // [32] thickness
+    int *cstart, *cnum, *ccell, *coff;   // [32] the warp's cells: first lane, floes, cell, first floe
+    unsigned char *slot;                 // [32] lane -> cell of the warp
+    float2 *Cm;    // [32][MAXM] per cell and mode: (cos, sin) of the corner phase, or (phase, -)
+};
+
+__host__ __device__ inline size_t pack_region_bytes()
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    return a16(sizeof(uint2) * PACKW) + a16(sizeof(float4) * PACKW) + a16(sizeof(float) * PACKW) +
+           4 * a16(sizeof(int) * PACKW) + a16(PACKW) + a16(sizeof(float2) * PACKW * MAXM);
+}
+
+__device__ __forceinline__ PackSm carve_pack(unsigned char *p)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    PackSm S;
+    size_t o = 0;
+    S.Q = reinterpret_cast<uint2 *>(p + o); o += a16(sizeof(uint2) * PACKW);
+    S.A = reinterpret_cast<float4 *>(p + o); o += a16(sizeof(float4) * PACKW);
+    S.H = reinterpret_cast<float *>(p + o); o += a16(sizeof(float) * PACKW);
+    S.cstart = reinterpret_cast<int *>(p + o); o += a16(sizeof(int) * PACKW);
+    S.cnum = reinterpret_cast<int *>(p + o); o += a16(sizeof(int) * PACKW);
+    S.ccell = reinterpret_cast<int *>(p + o); o += a16(sizeof(int) * PACKW);
+    S.coff = reinterpret_cast<int *>(p + o); o += a16(sizeof(int) * PACKW);
+    S.slot = p + o; o += a16(PACKW);
+    S.Cm = reinterpret_cast<float2 *>(p + o);
+    return S;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 8)
+k_cell_run32_packed(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, const int2 *pack, int npack,
+                    int nsteps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wi = blockIdx.x * WARPS + warp;
+    if (wi >= npack) return;
+    const PackSm S = carve_pack(smem + warp * pack_region_bytes());
+    const unsigned FULL = 0xffffffffu;
+    const float dt = sc.k.dt;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
+    const long long base = sc.ctrl->base;
+    const bool have_tgt = sc.couple && sc.ctrl->have_tgt;
+    const int nc = sc.ncell;
+
+    // ---- the warp's cells (lane j describes cell j); closure cells take no lanes
+    const int2 pk = pack[wi];
+    int cj = -1, oj = 0, nj = 0;
+    if (lane < pk.y) {
+        cj = sc.order0[pk.x + lane];
+        oj = sc.off[cj];
+        nj = sc.off[cj + 1] - oj;
+        if (sc.skip && sc.skip[cj]) cj = -1;
+        if (cj < 0) nj = 0;
+    }
+    int incl = nj;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (lane < pk.y) {
+        S.cstart[lane] = incl - nj;
+        S.cnum[lane] = nj;
+        S.ccell[lane] = cj;
+        S.coff[lane] = oj;
+        for (int k = incl - nj; k < incl; k++) S.slot[k] = (unsigned char)lane;
+    }
+    __syncwarp();
+    for (int idx = lane; idx < pk.y * P.n_modes; idx += 32) {
+        const int j = idx / P.n_modes, m = idx - j * P.n_modes;
+        const int c = S.ccell[j];
+        if (c < 0) continue;
+        const float b = corner_phase(P, m, c % sc.g.nx, (c / sc.g.nx) % sc.g.nyr, sc.g.nx, sc.g.nyr, inx, iny);
+        float sn, cs;
+        if (P.taylor) {
+            sincospif(2.0f * b, &sn, &cs);
+            S.Cm[j * MAXM + m] = make_float2(cs, sn);
+        } else {
+            S.Cm[j * MAXM + m] = make_float2(b, 0.0f);
+        }
+    }
+
+    // ---- this lane's floe, kept in registers for the run
+    const bool act = lane < total;
+    const int j = act ? S.slot[lane] : 0;
+    const int s0 = act ? S.cstart[j] : lane, n = act ? S.cnum[j] : 1;
+    const int c = act ? S.ccell[j] : -1;
+    const int gi = act ? S.coff[j] + (lane - s0) : 0;
+    const bool head = act && lane == s0;
+    uint32_t xq = 0u, yq = 0u;
+    float th = 0.0f, u = 0.0f, v = 0.0f, w = 0.0f, r = 0.0f, h = 0.0f;
+    if (act) {
+        xq = in.xq[gi]; yq = in.yq[gi]; th = in.th[gi];
+        u = in.u[gi]; v = in.v[gi]; w = in.w[gi]; r = in.r[gi]; h = in.h[gi];
+    }
+    double win[NWIN] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (head && sc.couple)
+        for (int k = 0; k < NWIN; k++) win[k] = sc.win[(size_t)k * nc + c];
+
+    unsigned deep_steps = 0;
+    bool bad = false;
+    float wua = 0.0f, wva = 0.0f;
+    float acc[NMOM];
+    const int j0 = (int)sc.i_local;
+    for (int js = 0; js < nsteps; js++) {
+        const int jstep = j0 + js;
+        if ((js & 31) == 0) {
+            const long long sj = base + jstep + lane + 1;
+            wind_at(P, (double)(sj - 1) * sc.dt, wua, wva);
+        }
+        const float ua = __shfl_sync(FULL, wua, js & 31), va = __shfl_sync(FULL, wva, js & 31);
+        const long long kk = (long long)jstep + 1;
+        const bool ramp = have_tgt && (kk % sc.n_t == 0);
+        float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
+        if (ramp) {
+            if (head) {
+                const RampCell rc = ramp_cell(sc, c, (int)(kk / sc.n_t));
+                rg = (float)rc.g; rdu = (float)rc.du; rdv = (float)rc.dv; rdw = (float)rc.dw;
+            }
+            rg = __shfl_sync(FULL, rg, s0); rdu = __shfl_sync(FULL, rdu, s0);
+            rdv = __shfl_sync(FULL, rdv, s0); rdw = __shfl_sync(FULL, rdw, s0);
+        }
+        // start state for the other lanes of the cell
+        S.Q[lane] = make_uint2(xq, yq);
+        S.A[lane] = make_float4(u, v, w, r);
+        S.H[lane] = h;
+        __syncwarp();
+        // ---- contacts with the other floes of the cell, in floe order
+        float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+        unsigned deep = 0;
+        if (act) {
+            for (int k = s0; k < s0 + n; k++) {
+                if (k == lane) continue;
+                const uint2 qk = S.Q[k];
+                const float dx = (float)(int)(qk.x - xq) * sx;
+                const float dy = (float)(int)(qk.y - yq) * sy;
+                const float4 ak = S.A[k];
+                contact_add(dx, dy, dx * dx + dy * dy, r, ak.w, h, S.H[k], ak.x - u, ak.y - v, w, ak.z, P, fx, fy,
+                            tq, deep);
+            }
+        }
+        // ---- drag, forward Euler, gradual update
+        const float xf = (float)xq * INV2_32F, yf = (float)yq * INV2_32F;
+        float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
+        if (P.taylor) {
+            for (int m = 0; m < P.n_modes; m++) {
+                float c0, s0m;
+                rot_small(fmaf(P.ta[m], xf, P.tb[m] * yf), c0, s0m);
+                const float2 C = S.Cm[j * MAXM + m];
+                const float cs = C.x * c0 - C.y * s0m, sn = C.y * c0 + C.x * s0m;
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        } else {
+            for (int m = 0; m < P.n_modes; m++) {
+                const float cyc = S.Cm[j * MAXM + m].x + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
+                float sn, cs;
+                sincospif(2.0f * cyc, &sn, &cs);
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        }
+        float Fdx, Fdy, Td;
+        drag_force(P, uo, vo, zeta, ua, va, u, v, w, r, Fdx, Fdy, Td);
+        fx += Fdx; fy += Fdy; tq += Td;
+        const float mass = P.mass_c * r * r * h;
+        const float I = P.inertia_f * mass * r * r;
+        const uint32_t xn = xq + (uint32_t)__float2int_rn(dt * u * isx);
+        const uint32_t yn = yq + (uint32_t)__float2int_rn(dt * v * isy);
+        const float thn = th + dt * w;
+        float un = u + dt * (fx / mass);
+        float vn = v + dt * (fy / mass);
+        float wn = w + dt * (tq / I);
+        float rn = r;
+        if (ramp) {
+            rn = r * rg;
+            un += rdu;
+            vn += rdv;
+            wn += rdw;
+        }
+        if (act) {
+            bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+            xq = xn; yq = yn; th = thn; u = un; v = vn; w = wn; r = rn;
+        }
+        deep_steps += deep ? 1u : 0u;
+        // ---- the cell's moments: segmented sums over its lanes
+#pragma unroll
+        for (int k = 0; k < NMOM; k++) acc[k] = 0.0f;
+        if (act) add_moments(acc, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+        const int end = s0 + n;
+#pragma unroll
+        for (int k = 1; k < NMOM; k++) {
+            float x = acc[k];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float y = __shfl_down_sync(FULL, x, d);
+                if (lane + d < end) x += y;
+            }
+            acc[k] = x;
+        }
+        if (head) {
+            if (js == nsteps - 1) {
+                double *mo = sc.mom + (size_t)c * NMOM;
+                mo[0] = (double)n;
+                for (int k = 1; k < NMOM; k++) mo[k] = (double)acc[k];
+            }
+            if (sc.couple) {
+                const double M = (double)acc[1];
+                if (M > 0.0) {
+                    win[0] += (double)acc[2] / M;
+                    win[1] += (double)acc[3] / M;
+                }
+                win[2] += (double)acc[9];
+                win[3] += (double)acc[10];
+                win[4] += (double)acc[11];
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- back to global memory
+    if (act) {
+        out.xq[gi] = xq; out.yq[gi] = yq; out.th[gi] = th;
+        out.u[gi] = u; out.v[gi] = v; out.w[gi] = w; out.r[gi] = r;
+    }
+    if (head && sc.couple)
+        for (int k = 0; k < NWIN; k++) sc.win[(size_t)k * nc + c] = win[k];
+    // an empty cell of the warp: zero moments
+    if (lane < pk.y && cj >= 0 && nj == 0) {
+        double *mo = sc.mom + (size_t)cj * NMOM;
+        for (int k = 0; k < NMOM; k++) mo[k] = 0.0;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep_steps) atomicAdd(&sc.ctrl->deep, (unsigned long long)deep_steps);
+}
+
 // ===================================================================== FP64
 // Positions are FP64 offsets from the cell origin; minimum image and wrap as
 // x - L rint(x / L) and x - L floor(x / L).  Pairs are visited in ascending
@@ -1467,13 +1724,15 @@ int seg_nbmax(const CellLaunch &cl, int s)
 
 static size_t seg_smem(const CellLaunch &cl, int s)
 {
+    if (cl.seg_kind[s] == 2) return 4 * pack_region_bytes();
     if (cl.seg_kind[s] == 1 && cl.variant == 3) return 4 * run_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     if (cl.seg_kind[s] == 1) return 4 * warp_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     return smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
 }
 
 // nsteps fine steps of size class s from step sc.i_local of the interval:
-// one launch of the resident warp kernel (variant 3), else one launch per step
+// one launch of a resident kernel (packed cells; warp cells in variant 3),
+// else one launch per step
 static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                                 const StepCommon &sc0, const CellLaunch &cl, int s, cudaStream_t st, int nsteps = 1)
 {
@@ -1481,6 +1740,11 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
     if (items <= 0) return cudaSuccess;
     const int nbm = seg_nbmax(cl, s);
     const size_t sm = seg_smem(cl, s);
+    if (cl.seg_kind[s] == 2) {   // resident in registers: one launch for the whole run
+        if (cl.npack <= 0) return cudaSuccess;
+        k_cell_run32_packed<4><<<(cl.npack + 3) / 4, 128, sm, st>>>(in, out, P, sc0, cl.pack, cl.npack, nsteps);
+        return cudaGetLastError();
+    }
     if (cl.seg_kind[s] == 1 && cl.variant == 3) {
         k_cell_run32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc0, nsteps, cl.bin_beta, cl.seg_begin[s],
                                                                cl.seg_end[s], cl.seg_maxn[s], nbm, s);
@@ -1542,7 +1806,7 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step64_brute<128>, (const void *)k_cell_step64_brute<256>,
             (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
             (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>,
-            (const void *)k_cell_run32_warp<4>};
+            (const void *)k_cell_run32_warp<4>, (const void *)k_cell_run32_packed<4>};
         limit = optin;
         for (const void *k : kern) {
             cudaFuncAttributes fa;

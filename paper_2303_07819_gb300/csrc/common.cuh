@@ -238,7 +238,7 @@ struct DevState64 {
     double *x, *y, *th, *u, *v, *w, *r, *h;
 };
 
-constexpr int MAXSEG = 6;   // size classes of cells launched separately (binned variants)
+constexpr int MAXSEG = 8;   // size classes of cells launched separately (binned variants)
 
 struct CellLaunch {
     int variant;       // 0 brute force, 1 binned block per cell, 2 binned warp per cell, 3 as 2 with
@@ -251,7 +251,10 @@ struct CellLaunch {
     // launched with its own block size and shared memory
     int nseg;
     int seg_begin[MAXSEG], seg_end[MAXSEG], seg_maxn[MAXSEG], seg_threads[MAXSEG];
-    int seg_kind[MAXSEG];   // 0: block per cell, 1: warp per cell (seg_maxn = the warp's capacity)
+    int seg_kind[MAXSEG];   // 0: block per cell, 1: warp per cell (seg_maxn = the warp's capacity),
+                            // 2: cells of <= 32 floes packed several to a warp
+    const int2 *pack;  // kind 2: per warp (first item, cells), device
+    int npack;
     int nbmax;         // bins per side at most
     // segments of variant 2 run on their own streams, forked from and joined
     // back into the launching stream (concurrent branches in a graph)
@@ -274,7 +277,10 @@ struct StepCommon {
     Geo32 k;
     const int *live;    // per size class: cells to step (the rest run the closure); nullptr: all
     const int *off;     // [ncell + 1]
-    const int *order;   // [ncell] processing order (largest cells first)
+    const int *order;   // [ncell] processing order (largest cells first); in closure mode the
+                        // particle cells of each size class first
+    const int *order0;  // [ncell] processing order (the packed warps' table refers to it)
+    const int *skip;    // [ncell] 1: the cell runs the closure this interval (packed warps); nullptr: none
     int ncell;
     int max_n;          // largest cell
     double *mom;        // [ncell][NMOM]

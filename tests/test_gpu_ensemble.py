@@ -91,13 +91,17 @@ def test_ensemble_has_no_truth(ms):
     assert g.time_kernel(2, ens["dt"], 1) > 0
 
 
-def test_small_cell_ensemble_runs(ms, orc):
-    """Few floes per cell (configs[4]'s law, 1 to 64): 4 realizations of
-    16 x 16 cells through two coarse steps, each realization's moments within
-    the FP32 tolerance of its oracle model."""
+@pytest.mark.parametrize("variant", [2, 3])
+def test_small_cell_ensemble_runs(ms, orc, variant):
+    """Few floes per cell (configs[4]'s law, 1 to 64; cells of up to 32 floes
+    run packed several to a warp): 4 realizations of 16 x 16 cells through
+    two coarse steps, one launch per step (variant 2) or per interval
+    (variant 3), each realization's moments within the FP32 tolerance of its
+    oracle model."""
     ens = I.config4(nreal=4, nx=16)
     p = ens["params"]
     g = ms.Model(p, ens["floes"], ms.MS_FP32)
+    g.set_launch(variant, 128, 0, 1.3)
     g.step(ens["dt"], 200)
     me = g.moments()
     nc = p["nx"] * p["ny"]
