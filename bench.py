@@ -64,10 +64,10 @@ def profile_traffic():
     return float(rec["dram_bytes_read_per_fine_step"]) + float(rec["dram_bytes_write_per_fine_step"]), rec
 
 
-def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=64, spin=15, nint=20, K=10):
+def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     """The learned closure on the timed workload.  Training data come from the
-    particle path of other seeds on 64 x 64 cells (after spin-up); the network
-    trains on the GPU; then K coarse intervals of the particle-only model are
+    particle path of another seed of the same workload (after spin-up); the
+    network trains on the GPU; then K coarse intervals of the particle-only model are
     compared with the closure-plus-fallback model (network, two tolerances),
     the mean-field closure, and, as the noise floor, the particle path with
     another reduction order (the block-per-cell kernel), all from the same
@@ -81,7 +81,7 @@ def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=64, spin=15, nint=20,
         m = msdem.Model(ss["params"], ss["floes"], msdem.MS_FP32)
         m.step(ss["dt"], ss["params"]["N0"] * spin)
         X, Y = m.closure_collect(nint)
-        Xs.append(X.reshape(-1, 12)); Ys.append(Y.reshape(-1, 4))
+        Xs.append(X.reshape(-1, 16)); Ys.append(Y.reshape(-1, 4))
         m.close()
     X, Y = np.concatenate(Xs), np.concatenate(Ys)
     norm = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
@@ -116,7 +116,7 @@ def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=64, spin=15, nint=20,
         return q, el, (st["closure_cell_intervals"] - c0) / (cells * K), Xh, Yh
 
     qp, tp, _, Xh, Yh = run(-1, 0.0)
-    Xh, Yh = Xh.reshape(-1, 12), Yh.reshape(-1, 4)
+    Xh, Yh = Xh.reshape(-1, 16), Yh.reshape(-1, 4)
     P = net.predict(Xh)
     r2 = 1 - ((P - Yh) ** 2).sum(0) / ((Yh - Yh.mean(0)) ** 2).sum(0)
     names = ["rho", "rho_u", "rho_v", "P_omega"]

@@ -245,23 +245,23 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
                             double *out, void *stream);
 
 /* ---- learned closure (not in the paper: a learned model of the bulk feedback)
- * A 12 -> 128 -> 128 -> 128 -> 4 MLP, tanh hidden units:
+ * A 16 -> 128 -> 128 -> 128 -> 4 MLP, tanh hidden units:
  *   xh = (x - mu_x)/sd_x, h1 = tanh(W1 xh + b1), h2 = tanh(W2 h1 + b2),
  *   h3 = tanh(W3 h2 + b3), yh = W4 h3 + b4, y = mu_y + sd_y yh,
  * trained on the mean-squared error of yh against (y_target - mu_y)/sd_y with
  * Adam (beta 0.9, 0.999, eps 1e-8).  Products run on BF16 tensor cores with
  * FP32 accumulation; master weights, biases and Adam state are FP32.
- * Packed parameter layout (35,204 floats): W1[128][12], b1[128], W2[128][128],
+ * Packed parameter layout (35,716 floats): W1[128][16], b1[128], W2[128][128],
  * b2[128], W3[128][128], b3[128], W4[4][128], b4[4] (W[out][in]).
- * Features x (12 per sample) and targets y (4) are FP32, sample-major. */
+ * Features x (16 per sample) and targets y (4) are FP32, sample-major. */
 typedef struct ms_mlp ms_mlp;
 
 /* Create a network from host params (packed) and norm = host
- * [mu_x(12), sd_x(12), mu_y(4), sd_y(4)] (sd > 0); max_batch = largest batch
+ * [mu_x(16), sd_x(16), mu_y(4), sd_y(4)] (sd > 0); max_batch = largest batch
  * of any later call (1 .. 2^22). */
 int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t max_batch);
 
-/* Forward pass: host X[n][12] -> host Y[n][4] in physical units. */
+/* Forward pass: host X[n][16] -> host Y[n][4] in physical units. */
 int ms_mlp_predict(ms_mlp *m, const float *X, int64_t n, float *Y);
 
 /* Gradient of the loss of one batch (n <= max_batch) without updating:
@@ -280,7 +280,7 @@ int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t e
 /* Current FP32 parameters, host, packed layout. */
 int ms_mlp_get_params(ms_mlp *m, float *params);
 
-/* Forward pass on device buffers X[n][12] -> Y[n][4] on `stream`, without
+/* Forward pass on device buffers X[n][16] -> Y[n][4] on `stream`, without
  * waiting. */
 int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream);
 
@@ -289,10 +289,13 @@ void ms_mlp_free(ms_mlp *m);
 /* Closure plus particle fallback on a coupled FP32 model (not in the paper).
  * mode 0: at the start of each coarse interval every cell's features
  * (rho, mean u, v, omega, variances of u and v, ocean u, v, divergence and
- * curl at the cell centre, wind u, v) go through `mlp`, which predicts the
- * interval-mean drag force per unit mass (x, y), drag torque per unit inertia
- * and the rate of change of the velocity variance.  A cell runs the closure
- * when its features lie inside box (host [2][12] min, max; NULL: no bound)
+ * curl at the cell centre, wind u, v, and the cell's four tendencies of the
+ * interval before, measured by its DEM or predicted) go through `mlp`, which
+ * predicts the interval-mean drag force per unit mass (x, y), drag torque per
+ * unit inertia and the rate of change of the velocity variance.  A cell runs
+ * the closure only when the interval before computed tendencies (so the first
+ * interval after attaching runs every cell's DEM), its features lie inside
+ * box (host [2][16] min, max; NULL: no bound)
  * and the predicted drag differs from the mean-field drag of its mean velocity
  * by at most tol relative (floor: the drag of 1 cm/s on 1 m ice); every other
  * cell runs the particle step (the fallback).  A closure cell skips its DEM for
@@ -305,7 +308,9 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
 
 /* Training data from the particle path: runs nint coarse intervals (from an
  * interval boundary, after the first ms_step call fixed dt) and writes host
- * X[nint][ncell][12] (features at each interval's start) and
+ * X[nint][ncell][16] (features at each interval's start; when the interval
+ * before the first computed no tendencies, one unrecorded interval runs
+ * first) and
  * Y[nint][ncell][4] (the window means of the drag force per unit mass, drag
  * torque per unit inertia, and (variance at the end - at the start) / dT). */
 int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y);

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (imported by tests/ and bench.py's CPU legs).  Shares
 no code with the CUDA closure kernels.
 
 Network (the definition both sides implement):
-    xh = (x - mu_x) / sd_x                         12 cell features, z-scored
+    xh = (x - mu_x) / sd_x                         16 cell features, z-scored
     h1 = tanh(W1 xh + b1)                          128
     h2 = tanh(W2 h1 + b2)                          128
     h3 = tanh(W3 h2 + b3)                          128
@@ -20,12 +20,12 @@ from __future__ import annotations
 
 import numpy as np
 
-LAYERS = [(12, 128), (128, 128), (128, 128), (128, 4)]
+LAYERS = [(16, 128), (128, 128), (128, 128), (128, 4)]
 NAMES = ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
 
 
 def forward(p: dict, X: np.ndarray, norm: dict, keep: bool = False):
-    """X: [B, 12] raw features.  Returns yh [B, 4] (z-scored), and the
+    """X: [B, 16] raw features.  Returns yh [B, 4] (z-scored), and the
     activations when keep."""
     xh = (X - norm["mu_x"]) / norm["sd_x"]
     h1 = np.tanh(xh @ p["W1"].T + p["b1"])

@@ -82,7 +82,7 @@ struct ms_model {
     ms_mlp *mlp = nullptr;
     int hybrid_mode = -1;          // -1 off, 0 network, 1 mean-field
     double hybrid_tol = 0.0;
-    float *d_X = nullptr, *d_Yp = nullptr, *d_Yuse = nullptr, *d_box = nullptr, *d_Yc = nullptr;
+    float *d_X = nullptr, *d_Yp = nullptr, *d_Yuse = nullptr, *d_box = nullptr, *d_Yc = nullptr, *d_Ylag = nullptr;
     int *d_isc = nullptr, *d_order2 = nullptr, *d_live = nullptr, *d_segb = nullptr, *d_sege = nullptr;
     double *d_mom0 = nullptr;
     unsigned long long *d_ccount = nullptr;
@@ -401,6 +401,14 @@ static cudaError_t launch_step(ms_model *m, long long i_local, bool scratch_out)
 // the work that closes a coarse interval: coarse step (coupled) or base += N0
 static cudaError_t launch_interval_end(ms_model *m)
 {
+    if (hybrid_on(m)) {
+        // the interval's tendencies (measured or predicted) become the next
+        // interval's lagged features; the window is still unconsumed here
+        cudaError_t e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, m->ncell, m->fc.N0,
+                                               (double)m->fc.N0 * m->dt, m->d_isc, m->d_Yuse, m->d_ctrl, m->d_Ylag,
+                                               nullptr, m->stream);
+        if (e != cudaSuccess) return e;
+    }
     if (m->fc.couple) return launch_coarse_step(coarse_args(m), m->stream);
     return launch_advance(m->d_ctrl, m->interval, m->stream);
 }
@@ -410,8 +418,11 @@ static cudaError_t launch_interval_end(ms_model *m)
 static cudaError_t launch_interval_start(ms_model *m)
 {
     if (!hybrid_on(m)) return cudaSuccess;
-    cudaError_t e = launch_features(m->d_mom, m->d_tgt, m->ncell, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
-                                    m->d_X, m->stream);
+    cudaError_t e = cudaMemcpyAsync(m->d_mom0, m->d_mom, sizeof(double) * m->ncell * NMOM, cudaMemcpyDeviceToDevice,
+                                    m->stream);
+    if (e == cudaSuccess)
+        e = launch_features(m->d_mom, m->d_tgt, m->ncell, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
+                            m->d_Ylag, m->d_X, m->stream);
     if (e != cudaSuccess) return e;
     if (m->hybrid_mode == 0 && ms_mlp_forward_device(m->mlp, m->d_X, m->ncell, m->d_Yp, m->stream) != MS_OK)
         return cudaErrorUnknown;
@@ -1313,11 +1324,12 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
     CK(cudaStreamSynchronize(m->stream));
     const int nc = m->ncell;
     if (!m->d_X) {
-        CK(dalloc(m, &m->d_X, (size_t)nc * 12));
+        CK(dalloc(m, &m->d_X, (size_t)nc * NFEAT));
+        CK(dalloc(m, &m->d_Ylag, (size_t)nc * 4));
         CK(dalloc(m, &m->d_Yp, (size_t)nc * 4));
         CK(dalloc(m, &m->d_Yuse, (size_t)nc * 4));
         CK(dalloc(m, &m->d_Yc, (size_t)nc * 4));
-        CK(dalloc(m, &m->d_box, 24));
+        CK(dalloc(m, &m->d_box, 2 * NFEAT));
         CK(dalloc(m, &m->d_isc, nc));
         CK(dalloc(m, &m->d_order2, nc));
         CK(dalloc(m, &m->d_live, MAXSEG));
@@ -1327,10 +1339,10 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
         CK(dalloc(m, &m->d_ccount, 1));
         CK(cudaMemsetAsync(m->d_ccount, 0, sizeof(unsigned long long), m->stream));
     }
-    float hb[24];
-    for (int k = 0; k < 12; k++) {
+    float hb[2 * NFEAT];
+    for (int k = 0; k < NFEAT; k++) {
         hb[k] = box ? box[k] : -3.0e38f;
-        hb[12 + k] = box ? box[12 + k] : 3.0e38f;
+        hb[NFEAT + k] = box ? box[NFEAT + k] : 3.0e38f;
     }
     CK(cudaMemcpyAsync(m->d_box, hb, sizeof(hb), cudaMemcpyHostToDevice, m->stream));
     const int prev_mode = m->hybrid_mode;
@@ -1365,20 +1377,27 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
     const int nc = m->ncell;
     const double dT = (double)m->fc.N0 * m->dt;
     int rc = MS_OK;
-    for (int k = 0; k < nint && rc == MS_OK; k++) {
+    // the lagged features need the tendencies of the interval before: without
+    // them, run one interval first and return only the ones after it
+    Ctrl c0;
+    CK(cudaMemcpyAsync(&c0, m->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    const int first = (c0.lag_mark == c0.base + 1) ? 0 : -1;
+    for (int k = first; k < nint && rc == MS_OK; k++) {
         cudaError_t e = cudaMemcpyAsync(m->d_mom0, m->d_mom, sizeof(double) * nc * NMOM, cudaMemcpyDeviceToDevice,
                                         m->stream);
         if (e == cudaSuccess)
-            e = launch_features(m->d_mom, m->d_tgt, nc, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t, m->d_X,
-                                m->stream);
+            e = launch_features(m->d_mom, m->d_tgt, nc, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
+                                m->d_Ylag, m->d_X, m->stream);
         for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);
-        if (e == cudaSuccess) e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, nc, m->fc.N0, dT, m->d_Yc,
-                                                         m->stream);
+        if (e == cudaSuccess)
+            e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, nc, m->fc.N0, dT, nullptr, nullptr, m->d_ctrl,
+                                       m->d_Ylag, m->d_Yc, m->stream);
         if (e == cudaSuccess) e = launch_interval_end(m);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(X + (size_t)k * nc * 12, m->d_X, sizeof(float) * nc * 12, cudaMemcpyDeviceToHost,
-                                m->stream);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && k >= 0)
+            e = cudaMemcpyAsync(X + (size_t)k * nc * NFEAT, m->d_X, sizeof(float) * nc * NFEAT,
+                                cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess && k >= 0)
             e = cudaMemcpyAsync(Y + (size_t)k * nc * 4, m->d_Yc, sizeof(float) * nc * 4, cudaMemcpyDeviceToHost,
                                 m->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);

@@ -1,4 +1,4 @@
-// closure.cu -- the learned closure: a 12 -> 128 -> 128 -> 128 -> 4 tanh MLP
+// closure.cu -- the learned closure: a 16 -> 128 -> 128 -> 128 -> 4 tanh MLP
 // that maps a cell's moments and forcing to its bulk drag tendencies, trained
 // and evaluated with BF16 tensor-core products accumulated in FP32 (FP32
 // master weights, Adam).
@@ -27,7 +27,7 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int NIN = 12, NH = 128, NOUT = 4;
+constexpr int NIN = 16, NH = 128, NOUT = 4;
 constexpr int KIN = 16;          // input features padded to a multiple of 16
 constexpr int NOP = 8;           // outputs padded to one n-tile
 constexpr int BM = 64, BN = 64, BK = 32, SPAD = 8;
@@ -461,7 +461,7 @@ void ms_mlp_free(ms_mlp *m)
     delete m;
 }
 
-// device-pointer forward used by the model's hybrid step: X [n][12] raw -> Y [n][4]
+// device-pointer forward used by the model's hybrid step: X [n][16] raw -> Y [n][4]
 int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream)
 {
     if (!m || (n > 0 && (!X || !Y))) return ms_closure_fail(MS_ERR_ARG, "NULL argument");

@@ -31,7 +31,8 @@ struct Ctrl {
     int N1;                       // LF substeps of the last coarse step
     unsigned int queue[2];        // work-queue tickets, one per step parity
     unsigned long long deep;      // contacts with overlap deeper than r_min / 2 (diagnostic)
-    unsigned long long pad[3];
+    long long lag_mark;           // base + 1 at whose start the stored last-interval tendencies are valid
+    unsigned long long pad[2];
 };
 
 // Physical constants in the kernel's arithmetic type.
@@ -392,10 +393,12 @@ struct HybridArgs {
     double *mom_rw;
     int N0, n_t;
 };
+constexpr int NFEAT = 16;   // closure features per cell (12 from the moments and forcing, 4 lagged tendencies)
 cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
-                            const Ctrl *ctrl, double dt, int N0, int n_t, float *X, cudaStream_t st);
+                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, float *X, cudaStream_t st);
 cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
-                                   double dT, float *Y, cudaStream_t st);
+                                   double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
+                                   float *Y, cudaStream_t st);
 cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st);
 
 // api.cu: record the calling thread's error message and return code

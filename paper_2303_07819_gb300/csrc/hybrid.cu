@@ -9,14 +9,18 @@
 // velocity and tests the features against the range seen in training; cells
 // that fail run the particle step (the fallback), the others take their
 // pending coarse increments at once and report the predicted tendencies to
-// the coarse step.
+// the coarse step.  The features include the cell's tendencies of the
+// interval before (measured by its DEM, or predicted if it ran the closure):
+// the drag torque of a cell depends on the spread of its floes' spins, which
+// its moments do not carry but which changes slowly from one interval to the
+// next.
 #include "common.cuh"
 
 namespace msd {
 
 namespace {
 
-constexpr int NF = 12;   // features per cell
+constexpr int NF = NFEAT;   // features per cell
 constexpr int NT = 4;    // targets per cell
 
 // Mean share of a coarse increment that the gradual updates have applied,
@@ -29,12 +33,14 @@ __host__ __device__ inline double ramp_mean_share(int N0, int n_t)
     return s / N0;
 }
 
-// [rho, ubar, vbar, wbar, var u, var v, u_o, v_o, div u_o, curl u_o, u_a, v_a]
-// (ocean at the cell centre, wind at the start of the interval).  The mean
-// velocity and spin are the interval means the gradual updates produce: the
-// cell's current means plus the mean share of its pending increments.
+// [rho, ubar, vbar, wbar, var u, var v, u_o, v_o, div u_o, curl u_o, u_a, v_a,
+//  and the four tendencies of the interval before] (ocean at the cell centre,
+// wind at the start of the interval; the last four are zero when the
+// interval before computed none).  The mean velocity and spin are the
+// interval means the gradual updates produce: the cell's current means plus
+// the mean share of its pending increments.
 __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom g, Phys<double> P,
-                           const Ctrl *ctrl, double dt, double share, float *X)
+                           const Ctrl *ctrl, double dt, double share, const float *Ylag, float *X)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -53,18 +59,32 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
     double ua, va;
     wind_at(P, (double)ctrl->base * dt, ua, va);
     const double div = ocean_div_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy);
-    const double f[NF] = {M / Ac, ub, vb, wb, su, sv, uo, vo, div, zeta, ua, va};
-    for (int k = 0; k < NF; k++) X[(size_t)c * NF + k] = (float)f[k];
+    const bool lag = ctrl->lag_mark == ctrl->base + 1;
+    const double f[12] = {M / Ac, ub, vb, wb, su, sv, uo, vo, div, zeta, ua, va};
+    for (int k = 0; k < 12; k++) X[(size_t)c * NF + k] = (float)f[k];
+    for (int k = 0; k < NT; k++) X[(size_t)c * NF + 12 + k] = lag ? Ylag[(size_t)c * NT + k] : 0.0f;
 }
 
 // Targets of the interval just run: window means of the cell's total drag per
 // unit mass (x, y), of its drag torque per unit inertia, and the rate of change
-// of the velocity variance over the interval.
+// of the velocity variance over the interval.  A closure cell's are its
+// predicted ones (is_closure, Yuse; nullptr: every cell ran its DEM).  They
+// are kept as the next interval's lagged features (Ylag, marked valid for
+// the interval that starts at base + N0) and, if Y is given, returned.
 __global__ void k_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
-                                  double dT, float *Y)
+                                  double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
+                                  float *Y)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) ctrl->lag_mark = ctrl->base + N0 + 1;
     if (c >= ncell) return;
+    if (is_closure && is_closure[c]) {
+        for (int k = 0; k < NT; k++) {
+            Ylag[(size_t)c * NT + k] = Yuse[(size_t)c * NT + k];
+            if (Y) Y[(size_t)c * NT + k] = Yuse[(size_t)c * NT + k];
+        }
+        return;
+    }
     const double *a = mom0 + (size_t)c * NMOM, *b = mom1 + (size_t)c * NMOM;
     const double M0 = a[1], I0 = a[4];
     auto var = [](const double *m) {
@@ -72,10 +92,14 @@ __global__ void k_collect_targets(const double *mom0, const double *mom1, const 
         const double u = m[2] / m[1], v = m[3] / m[1];
         return fmax(m[7] / m[1] - u * u, 0.0) + fmax(m[8] / m[1] - v * v, 0.0);
     };
-    Y[(size_t)c * NT + 0] = M0 > 0.0 ? (float)(win[2 * ncell + c] / N0 / M0) : 0.0f;
-    Y[(size_t)c * NT + 1] = M0 > 0.0 ? (float)(win[3 * ncell + c] / N0 / M0) : 0.0f;
-    Y[(size_t)c * NT + 2] = I0 > 0.0 ? (float)(win[4 * ncell + c] / N0 / I0) : 0.0f;
-    Y[(size_t)c * NT + 3] = (float)((var(b) - var(a)) / dT);
+    const float y[NT] = {M0 > 0.0 ? (float)(win[2 * ncell + c] / N0 / M0) : 0.0f,
+                         M0 > 0.0 ? (float)(win[3 * ncell + c] / N0 / M0) : 0.0f,
+                         I0 > 0.0 ? (float)(win[4 * ncell + c] / N0 / I0) : 0.0f,
+                         (float)((var(b) - var(a)) / dT)};
+    for (int k = 0; k < NT; k++) {
+        Ylag[(size_t)c * NT + k] = y[k];
+        if (Y) Y[(size_t)c * NT + k] = y[k];
+    }
 }
 
 // Mean-field tendencies of a cell: the drag of Eq. 2.1c-d evaluated at the
@@ -117,7 +141,7 @@ __global__ void k_classify(const float *X, const float *Yp, const double *mom, i
         } else if (mode == 1) {
             closure = 1;
             for (int k = 0; k < NT; k++) y[k] = (float)mf[k];
-        } else {
+        } else if (ctrl->lag_mark == ctrl->base + 1) {   // the network needs last interval's tendencies
             bool inside = true;
             for (int k = 0; k < NF; k++)
                 inside &= (x[k] >= box[k]) && (x[k] <= box[NF + k]);
@@ -247,16 +271,19 @@ k_closure_apply(DevState32 st, Phys<float> P, const int *off, const int *is_clos
 }  // namespace
 
 cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
-                            const Ctrl *ctrl, double dt, int N0, int n_t, float *X, cudaStream_t st)
+                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, float *X, cudaStream_t st)
 {
-    k_features<<<(ncell + 127) / 128, 128, 0, st>>>(mom, tgt, ncell, g, P, ctrl, dt, ramp_mean_share(N0, n_t), X);
+    k_features<<<(ncell + 127) / 128, 128, 0, st>>>(mom, tgt, ncell, g, P, ctrl, dt, ramp_mean_share(N0, n_t), Ylag,
+                                                     X);
     return cudaGetLastError();
 }
 
 cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
-                                   double dT, float *Y, cudaStream_t st)
+                                   double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
+                                   float *Y, cudaStream_t st)
 {
-    k_collect_targets<<<(ncell + 127) / 128, 128, 0, st>>>(mom0, mom1, win, ncell, N0, dT, Y);
+    k_collect_targets<<<(ncell + 127) / 128, 128, 0, st>>>(mom0, mom1, win, ncell, N0, dT, is_closure, Yuse, ctrl,
+                                                            Ylag, Y);
     return cudaGetLastError();
 }
 

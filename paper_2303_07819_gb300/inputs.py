@@ -340,7 +340,7 @@ def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, r
 CONFIGS = {0: config0, 1: config1, 2: config2, 4: config4}
 
 
-def mlp_init(seed: int = BASE_SEED + 3, layers=((12, 128), (128, 128), (128, 128), (128, 4))) -> dict:
+def mlp_init(seed: int = BASE_SEED + 3, layers=((16, 128), (128, 128), (128, 128), (128, 4))) -> dict:
     """Initial closure weights (uniform Glorot: U(-a, a), a = sqrt(6/(fan_in +
     fan_out)); zero biases), drawn here so both sides start from the same
     network.  W[out][in]."""

@@ -242,13 +242,13 @@ class Model:
     def closure_attach(self, mlp, mode: int = 0, tol: float = 0.5, box=None) -> None:
         """mode 0: network `mlp` with fallback; 1: mean-field closure; -1: off."""
         self._mlp_ref = mlp
-        bx = None if box is None else np.ascontiguousarray(box, dtype=np.float32).reshape(24)
+        bx = None if box is None else np.ascontiguousarray(box, dtype=np.float32).reshape(2 * NFEAT)
         self._box = bx
         _check(load().ms_closure_attach(self._h, mlp._h if mlp is not None else None, int(mode), float(tol),
                                         bx.ctypes.data_as(C.POINTER(C.c_float)) if bx is not None else None))
 
     def closure_collect(self, nint: int):
-        X = np.zeros((nint, self.ncell, 12), dtype=np.float32)
+        X = np.zeros((nint, self.ncell, NFEAT), dtype=np.float32)
         Y = np.zeros((nint, self.ncell, 4), dtype=np.float32)
         _check(load().ms_closure_collect(self._h, int(nint), X.ctypes.data_as(C.POINTER(C.c_float)),
                                          Y.ctypes.data_as(C.POINTER(C.c_float))))
@@ -283,8 +283,10 @@ def cell_moments_noalloc(params: dict, n: int, x: int, y: int, u: int, v: int, o
                                      int(n), *ptrs, C.c_void_p(stream or 0)))
 
 
-MLP_SHAPES = [("W1", (128, 12)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
+NFEAT = 16       # closure features per cell
+MLP_SHAPES = [("W1", (128, NFEAT)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)),
               ("W3", (128, 128)), ("b3", (128,)), ("W4", (4, 128)), ("b4", (4,))]
+NPARAM = sum(int(np.prod(shp)) for _, shp in MLP_SHAPES)
 _fp = C.POINTER(C.c_float)
 
 
@@ -359,7 +361,7 @@ class MLP:
 
     def grad(self, X, Y):
         X, Y = _f32(X), _f32(Y)
-        g = np.zeros(35204, dtype=np.float32)
+        g = np.zeros(NPARAM, dtype=np.float32)
         loss = C.c_double(0.0)
         _check(_load_mlp().ms_mlp_grad(self._h, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0],
                                        g.ctypes.data_as(_fp), C.byref(loss)))
@@ -379,6 +381,6 @@ class MLP:
         return losses
 
     def params(self) -> dict:
-        flat = np.zeros(35204, dtype=np.float32)
+        flat = np.zeros(NPARAM, dtype=np.float32)
         _check(_load_mlp().ms_mlp_get_params(self._h, flat.ctypes.data_as(_fp)))
         return {k: v.astype(np.float64) for k, v in unpack_params(flat).items()}

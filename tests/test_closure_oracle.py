@@ -9,7 +9,7 @@ from paper_2303_07819_gb300 import inputs as I
 
 
 def _data(rng, B=37):
-    X = rng.normal(size=(B, 12)) * np.linspace(0.5, 3.0, 12) + np.arange(12)
+    X = rng.normal(size=(B, 16)) * np.linspace(0.5, 3.0, 16) + np.arange(16)
     Y = rng.normal(size=(B, 4)) * np.array([1e-3, 2e-3, 1e-6, 5e-5]) + np.array([1e-3, 0, 0, 1e-4])
     return X, Y
 
@@ -65,7 +65,7 @@ def test_adam_first_step_closed_form():
 
 def test_training_reduces_loss():
     rng = np.random.default_rng(3)
-    X = rng.normal(size=(512, 12))
+    X = rng.normal(size=(512, 16))
     Y = np.stack([np.sin(X[:, 0]), X[:, 1] * X[:, 2], np.tanh(X[:, 3]), X[:, 4] ** 2], 1)
     norm = CO.normalisation(X, Y)
     p = I.mlp_init()

@@ -18,7 +18,7 @@ def ms():
 
 def _data(seed, B):
     rng = np.random.default_rng(seed)
-    X = rng.normal(size=(B, 12)) * np.linspace(0.5, 3.0, 12) + np.arange(12)
+    X = rng.normal(size=(B, 16)) * np.linspace(0.5, 3.0, 16) + np.arange(16)
     Y = np.stack([np.sin(X[:, 0]), X[:, 1] * 0.1, np.tanh(X[:, 3] - 3), 0.01 * X[:, 4] ** 2], 1)
     Y = Y * np.array([1e-3, 2e-3, 1e-6, 5e-5])
     return X, Y
