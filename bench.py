@@ -68,7 +68,8 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     """The learned closure on the timed workload.  Training data come from the
     particle path of another seed of the same workload (after spin-up); the
     network trains on the GPU; then K coarse intervals of the particle-only model are
-    compared with the closure-plus-fallback model (network, two tolerances),
+    compared with the closure-plus-fallback model (network: two bounds on its
+    checked error, and none),
     the mean-field closure, and, as the noise floor, the particle path with
     another reduction order (the block-per-cell kernel), all from the same
     spun-up state.  A closure cell's coarse interval counts as N0 cell-steps."""
@@ -134,8 +135,8 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
            "particle": {"cell_steps_per_s": cells * N0 * K / tp}}
     qn, tn, _, _, _ = run(-1, 0.0, variant=1)
     out["noise_floor_other_reduction_order"] = {"coarse_state_rel_err": err(qn)}
-    for label, mode, tol in (("network_tol_0.05", 0, 0.05), ("network_tol_0.2", 0, 0.2),
-                             ("network_all", 0, 1e9), ("mean_field_all", 1, 0.0)):
+    for label, mode, tol in (("network_tol_0.1", 0, 0.1), ("network_tol_0.3", 0, 0.3),
+                             ("network_no_bound", 0, 1e9), ("mean_field_all", 1, 0.0)):
         q, t, frac, _, _ = run(mode, tol)
         out[label] = {"closure_fraction": frac, "cell_steps_per_s": cells * N0 * K / t, "speedup": tp / t,
                       "coarse_state_rel_err": err(q)}

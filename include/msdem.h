@@ -293,12 +293,14 @@ void ms_mlp_free(ms_mlp *m);
  * interval before, measured by its DEM or predicted) go through `mlp`, which
  * predicts the interval-mean drag force per unit mass (x, y), drag torque per
  * unit inertia and the rate of change of the velocity variance.  A cell runs
- * the closure only when the interval before computed tendencies (so the first
- * interval after attaching runs every cell's DEM), its features lie inside
- * box (host [2][16] min, max; NULL: no bound)
- * and the predicted drag differs from the mean-field drag of its mean velocity
- * by at most tol relative (floor: the drag of 1 cm/s on 1 m ice); every other
- * cell runs the particle step (the fallback).  A closure cell skips its DEM for
+ * the closure only when the interval before computed tendencies, its
+ * features lie inside box (host [2][16] min, max; NULL: no bound), and the
+ * particle path has checked the network on it: after each interval a cell
+ * runs its DEM, the network's prediction for that interval is compared with
+ * the measured drag, and the cell may take the closure for at most 3
+ * intervals after a check whose relative error was at most tol (floor: the
+ * drag of 1 cm/s on 1 m ice).  So the first interval after attaching runs
+ * every cell's DEM.  Every other cell runs the particle step (the fallback).  A closure cell skips its DEM for
  * the interval: it takes its pending coarse increments at once, its velocity
  * spread follows the predicted variance rate, and the coarse step sees the
  * predicted tendencies.  mode 1: the mean-field drag for every cell (no

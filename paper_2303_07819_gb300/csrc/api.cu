@@ -82,7 +82,9 @@ struct ms_model {
     ms_mlp *mlp = nullptr;
     int hybrid_mode = -1;          // -1 off, 0 network, 1 mean-field
     double hybrid_tol = 0.0;
-    float *d_X = nullptr, *d_Yp = nullptr, *d_Yuse = nullptr, *d_box = nullptr, *d_Yc = nullptr, *d_Ylag = nullptr;
+    float *d_X = nullptr, *d_Yp = nullptr, *d_Yuse = nullptr, *d_box = nullptr, *d_Yc = nullptr, *d_Ylag = nullptr,
+          *d_nerr = nullptr;
+    int *d_age = nullptr;
     int *d_isc = nullptr, *d_order2 = nullptr, *d_live = nullptr, *d_segb = nullptr, *d_sege = nullptr;
     double *d_mom0 = nullptr;
     unsigned long long *d_ccount = nullptr;
@@ -353,6 +355,10 @@ static CoarseArgs coarse_args(ms_model *m)
 
 static bool hybrid_on(const ms_model *m) { return m->hybrid_mode >= 0 && m->fc.couple && m->precision == MS_FP32; }
 
+// drag floor of the closure's relative error: the drag of a 1 cm/s relative
+// velocity on 1 m of ice
+static double floor_acc(const ms_model *m) { return m->fc.Cd * m->fc.rho_o / m->fc.rho_ice * 1e-4; }
+
 // step facts of fine step i_local of the interval, for the model's state or
 // (scratch_out) for the out-of-place timing copies
 static StepCommon cell_common(ms_model *m, long long i_local, bool scratch_out)
@@ -404,9 +410,11 @@ static cudaError_t launch_interval_end(ms_model *m)
     if (hybrid_on(m)) {
         // the interval's tendencies (measured or predicted) become the next
         // interval's lagged features; the window is still unconsumed here
+        const bool net = m->hybrid_mode == 0;
         cudaError_t e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, m->ncell, m->fc.N0,
                                                (double)m->fc.N0 * m->dt, m->d_isc, m->d_Yuse, m->d_ctrl, m->d_Ylag,
-                                               nullptr, m->stream);
+                                               nullptr, net ? m->d_Yp : nullptr, floor_acc(m),
+                                               net ? m->d_nerr : nullptr, net ? m->d_age : nullptr, m->stream);
         if (e != cudaSuccess) return e;
     }
     if (m->fc.couple) return launch_coarse_step(coarse_args(m), m->stream);
@@ -437,8 +445,9 @@ static cudaError_t launch_interval_start(ms_model *m)
     h.P32 = m->P32;
     h.rho_ice = m->fc.rho_ice;
     h.tol = m->hybrid_tol;
-    // floor of the drag scale in the residual: the drag of a 1 cm/s relative velocity on 1 m ice
-    h.floor_acc = m->fc.Cd * m->fc.rho_o / m->fc.rho_ice * 1e-4;
+    h.floor_acc = floor_acc(m);
+    h.nerr = m->d_nerr;
+    h.age = m->d_age;
     h.dT = (double)m->fc.N0 * m->dt;
     h.box = m->d_box;
     h.mode = m->hybrid_mode;
@@ -1326,6 +1335,8 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
     if (!m->d_X) {
         CK(dalloc(m, &m->d_X, (size_t)nc * NFEAT));
         CK(dalloc(m, &m->d_Ylag, (size_t)nc * 4));
+        CK(dalloc(m, &m->d_nerr, nc));
+        CK(dalloc(m, &m->d_age, nc));
         CK(dalloc(m, &m->d_Yp, (size_t)nc * 4));
         CK(dalloc(m, &m->d_Yuse, (size_t)nc * 4));
         CK(dalloc(m, &m->d_Yc, (size_t)nc * 4));
@@ -1345,6 +1356,13 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
         hb[NFEAT + k] = box ? box[NFEAT + k] : 3.0e38f;
     }
     CK(cudaMemcpyAsync(m->d_box, hb, sizeof(hb), cudaMemcpyHostToDevice, m->stream));
+    // no cell has been checked yet: every cell's first interval runs its DEM
+    {
+        std::vector<float> big(nc, 3.0e38f);
+        CK(cudaMemcpyAsync(m->d_nerr, big.data(), sizeof(float) * nc, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemsetAsync(m->d_age, 0, sizeof(int) * nc, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+    }
     const int prev_mode = m->hybrid_mode;
     m->hybrid_mode = mode;
     m->mlp = mlp;
@@ -1392,7 +1410,7 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
         for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);
         if (e == cudaSuccess)
             e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, nc, m->fc.N0, dT, nullptr, nullptr, m->d_ctrl,
-                                       m->d_Ylag, m->d_Yc, m->stream);
+                                       m->d_Ylag, m->d_Yc, nullptr, 0.0, nullptr, nullptr, m->stream);
         if (e == cudaSuccess) e = launch_interval_end(m);
         if (e == cudaSuccess && k >= 0)
             e = cudaMemcpyAsync(X + (size_t)k * nc * NFEAT, m->d_X, sizeof(float) * nc * NFEAT,

@@ -374,13 +374,15 @@ cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
 
 // hybrid.cu: closure-plus-fallback intervals
 struct HybridArgs {
-    const float *X, *Yp;      // features [ncell][12], network prediction [ncell][4]
+    const float *X, *Yp;      // features [ncell][NFEAT], network prediction [ncell][4]
+    const float *nerr;        // [ncell] the network's drag error on the cell's last DEM interval
+    const int *age;           // [ncell] closure intervals since that DEM interval
     const double *mom;
     int ncell, nseg;
     Phys<double> P64;
     Phys<float> P32;
     double rho_ice, tol, floor_acc, dT;
-    const float *box;         // [2][12] feature range seen in training
+    const float *box;         // [2][NFEAT] feature range seen in training
     int mode;                 // 0 network, 1 mean-field
     const Ctrl *ctrl;
     int *is_closure;
@@ -398,7 +400,10 @@ cudaError_t launch_features(const double *mom, const double *tgt, int ncell, con
                             const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, float *X, cudaStream_t st);
 cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
                                    double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
-                                   float *Y, cudaStream_t st);
+                                   float *Y, const float *Yp, double floor_acc, float *nerr, int *age,
+                                   cudaStream_t st);
+// closure intervals a cell may run between two DEM intervals that check the network on it
+constexpr int CLOSURE_MAX_RUN = 3;
 cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st);
 
 // api.cu: record the calling thread's error message and return code

@@ -9,7 +9,11 @@
 // velocity and tests the features against the range seen in training; cells
 // that fail run the particle step (the fallback), the others take their
 // pending coarse increments at once and report the predicted tendencies to
-// the coarse step.  The features include the cell's tendencies of the
+// the coarse step.  The particle path judges the network: after every DEM
+// interval of a cell the network's prediction for that interval is compared
+// with the cell's measured drag, and only a cell whose last check passed, and
+// that has run at most CLOSURE_MAX_RUN closure intervals since, may take the
+// closure.  The features include the cell's tendencies of the
 // interval before (measured by its DEM, or predicted if it ran the closure):
 // the drag torque of a cell depends on the spread of its floes' spins, which
 // its moments do not carry but which changes slowly from one interval to the
@@ -71,9 +75,13 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
 // predicted ones (is_closure, Yuse; nullptr: every cell ran its DEM).  They
 // are kept as the next interval's lagged features (Ylag, marked valid for
 // the interval that starts at base + N0) and, if Y is given, returned.
+// With the network's prediction for the interval (Yp, nerr, age non-null),
+// a DEM cell also records the network's relative drag error on it (nerr,
+// floor: floor_acc) and resets its closure run (age); a closure cell extends
+// its run.
 __global__ void k_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
                                   double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
-                                  float *Y)
+                                  float *Y, const float *Yp, double floor_acc, float *nerr, int *age)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c == 0) ctrl->lag_mark = ctrl->base + N0 + 1;
@@ -83,6 +91,7 @@ __global__ void k_collect_targets(const double *mom0, const double *mom1, const 
             Ylag[(size_t)c * NT + k] = Yuse[(size_t)c * NT + k];
             if (Y) Y[(size_t)c * NT + k] = Yuse[(size_t)c * NT + k];
         }
+        if (age) age[c] += 1;
         return;
     }
     const double *a = mom0 + (size_t)c * NMOM, *b = mom1 + (size_t)c * NMOM;
@@ -99,6 +108,12 @@ __global__ void k_collect_targets(const double *mom0, const double *mom1, const 
     for (int k = 0; k < NT; k++) {
         Ylag[(size_t)c * NT + k] = y[k];
         if (Y) Y[(size_t)c * NT + k] = y[k];
+    }
+    if (Yp && nerr && age) {
+        const double ex = (double)Yp[(size_t)c * NT] - y[0], ey = (double)Yp[(size_t)c * NT + 1] - y[1];
+        const double ym = sqrt((double)y[0] * y[0] + (double)y[1] * y[1]);
+        nerr[c] = M0 > 0.0 ? (float)(sqrt(ex * ex + ey * ey) / (ym + floor_acc)) : 0.0f;
+        age[c] = 0;
     }
 }
 
@@ -124,8 +139,8 @@ __device__ __forceinline__ void meanfield(const float *x, const double *mo, cons
 
 // closure or particle for each cell; the tendencies the coarse step will see
 __global__ void k_classify(const float *X, const float *Yp, const double *mom, int ncell, Phys<double> P,
-                           double rho_ice, const float *box, double tol, double floor_acc, int mode, const Ctrl *ctrl,
-                           int *is_closure, float *Yuse)
+                           double rho_ice, const float *box, double tol, int mode, const Ctrl *ctrl,
+                           const float *nerr, const int *age, int *is_closure, float *Yuse)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -146,9 +161,9 @@ __global__ void k_classify(const float *X, const float *Yp, const double *mom, i
             for (int k = 0; k < NF; k++)
                 inside &= (x[k] >= box[k]) && (x[k] <= box[NF + k]);
             const float *yp = Yp + (size_t)c * NT;
-            const double ex = yp[0] - mf[0], ey = yp[1] - mf[1];
-            const double res = sqrt(ex * ex + ey * ey) / (sqrt(mf[0] * mf[0] + mf[1] * mf[1]) + floor_acc);
-            closure = inside && res <= tol;
+            // the residual check: the network's drag error on this cell's last
+            // DEM interval, and a bounded run of closure intervals since
+            closure = inside && nerr[c] <= tol && age[c] < CLOSURE_MAX_RUN;
             for (int k = 0; k < NT; k++) y[k] = yp[k];
         }
     }
@@ -280,17 +295,18 @@ cudaError_t launch_features(const double *mom, const double *tgt, int ncell, con
 
 cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
                                    double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
-                                   float *Y, cudaStream_t st)
+                                   float *Y, const float *Yp, double floor_acc, float *nerr, int *age,
+                                   cudaStream_t st)
 {
     k_collect_targets<<<(ncell + 127) / 128, 128, 0, st>>>(mom0, mom1, win, ncell, N0, dT, is_closure, Yuse, ctrl,
-                                                            Ylag, Y);
+                                                            Ylag, Y, Yp, floor_acc, nerr, age);
     return cudaGetLastError();
 }
 
 cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st)
 {
     k_classify<<<(h.ncell + 127) / 128, 128, 0, st>>>(h.X, h.Yp, h.mom, h.ncell, h.P64, h.rho_ice, h.box, h.tol,
-                                                     h.floor_acc, h.mode, h.ctrl, h.is_closure, h.Yuse);
+                                                     h.mode, h.ctrl, h.nerr, h.age, h.is_closure, h.Yuse);
     k_compact<<<h.nseg, 1024, 0, st>>>(h.order, h.seg_begin, h.seg_end, h.is_closure, h.order2, h.live,
                                         h.closure_count);
     k_closure_apply<<<h.ncell, 128, 0, st>>>(h.st32, h.P32, h.off, h.is_closure, h.Yuse, h.mom_rw, h.win, h.tgt,
