@@ -54,6 +54,7 @@ struct ms_model {
     int *d_off = nullptr, *d_order = nullptr;
     // msDEM state and its scratch copy for out-of-place timing
     DevState32 s32{}, x32{};
+    NbLists nl{}, xnl{};          // candidate lists of s32 and of the timing copy x32
     DevState64 s64{}, x64{};
     double *d_mom = nullptr, *d_win = nullptr, *d_q0 = nullptr, *d_q1 = nullptr, *d_V = nullptr,
            *d_S = nullptr, *d_tgt = nullptr, *d_xmom = nullptr, *d_xwin = nullptr;
@@ -115,6 +116,25 @@ static cudaError_t alloc32(ms_model *m, DevState32 &s, size_t n)
         (e = dalloc(m, &s.r, n)) || (e = dalloc(m, &s.h, n)))
         return e;
     return cudaSuccess;
+}
+
+static cudaError_t alloc_lists(ms_model *m, NbLists &l, size_t n, int ncell)
+{
+    cudaError_t e;
+    if ((e = dalloc(m, &l.idx, n * 32)) || (e = dalloc(m, &l.cnt, n)) || (e = dalloc(m, &l.xb, n)) ||
+        (e = dalloc(m, &l.cstep, ncell)) || (e = dalloc(m, &l.skin, ncell)))
+        return e;
+    return cudaMemsetAsync(l.cstep, 0xff, sizeof(long long) * ncell, m->stream);
+}
+
+// forget the candidate lists (the floes changed outside a cell step)
+static cudaError_t invalidate_lists(ms_model *m)
+{
+    cudaError_t e = cudaSuccess;
+    if (m->nl.cstep) e = cudaMemsetAsync(m->nl.cstep, 0xff, sizeof(long long) * m->ncell, m->stream);
+    if (e == cudaSuccess && m->xnl.cstep)
+        e = cudaMemsetAsync(m->xnl.cstep, 0xff, sizeof(long long) * m->ncell, m->stream);
+    return e;
 }
 
 static cudaError_t alloc64(ms_model *m, DevState64 &s, size_t n)
@@ -309,6 +329,7 @@ static StepCommon step_common(ms_model *m, long long i_local, double *mom, doubl
 {
     StepCommon sc;
     sc.k = geo32(m->g.Lcx, m->g.Lcy, m->g.nx, m->g.nyr, m->dt);
+    sc.nl = m->nl;
     sc.live = nullptr;
     sc.off = m->d_off;
     sc.order = m->d_order;
@@ -365,6 +386,7 @@ static StepCommon cell_common(ms_model *m, long long i_local, bool scratch_out)
 {
     StepCommon sc = step_common(m, i_local, scratch_out ? m->d_xmom : m->d_mom,
                                 scratch_out ? m->d_xwin : m->d_win);
+    sc.nl = scratch_out ? m->xnl : m->nl;
     if (hybrid_on(m)) {
         sc.order = m->d_order2;
         sc.live = m->d_live;
@@ -662,6 +684,7 @@ static int configure_launch(ms_model *m, const CellLaunch &cl_in)
     const size_t smem = cell_step_smem(m->precision, cl, m->max_n, m->g.nx, m->g.ny);
     if (smem > 227 * 1024) return fail(MS_ERR_ARG, "cell of %d floes needs %zu B of shared memory", m->max_n, smem);
     CK(cell_step_prepare(m->precision, cl, smem));
+    CK(invalidate_lists(m));
     m->cl = cl;
     drop_graph(m);
     return MS_OK;
@@ -863,6 +886,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
         CKM(dalloc(m, (double **)&m->d_fd, 3 * (size_t)n));
     } else {
         CKM(alloc32(m, m->s32, n));
+        CKM(alloc_lists(m, m->nl, n, nc));
         if (nens == 1) {
             CKM(alloc32(m, m->t32[0], n));
             CKM(alloc32(m, m->t32[1], n));
@@ -884,7 +908,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
         return rc;
     }
     CellLaunch cl{};
-    cl.variant = m->precision == MS_FP32 ? 2 : 0;
+    cl.variant = m->precision == MS_FP32 ? 4 : 0;
     cl.threads = 128;
     cl.bin_beta = 1.3f;
     cl.persistent = 0;
@@ -1074,6 +1098,7 @@ int ms_set_floes(ms_model *m, const ms_floes *floes)
     }
     CK(cudaStreamSynchronize(m->stream));
     if ((rc = upload_model_state(m, floes))) return rc;
+    CK(invalidate_lists(m));
     StepCommon sc = step_common(m, 0, m->d_mom, m->d_win);
     CK(m->precision == MS_FP64 ? launch_cell_moments64(m->s64, m->P64, sc, m->stream)
                                : launch_cell_moments32(m->s32, m->P32, sc, m->stream));
@@ -1141,7 +1166,10 @@ static int ensure_scratch(ms_model *m)
         CK(cudaMemcpyAsync(m->x64.r, m->s64.r, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
         CK(cudaMemcpyAsync(m->x64.h, m->s64.h, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
     } else {
-        if (!m->x32.xq) CK(alloc32(m, m->x32, m->n));
+        if (!m->x32.xq) {
+            CK(alloc32(m, m->x32, m->n));
+            CK(alloc_lists(m, m->xnl, m->n, m->ncell));
+        }
         CK(cudaMemcpyAsync(m->x32.r, m->s32.r, sizeof(float) * m->n, cudaMemcpyDeviceToDevice, m->stream));
         CK(cudaMemcpyAsync(m->x32.h, m->s32.h, sizeof(float) * m->n, cudaMemcpyDeviceToDevice, m->stream));
     }
@@ -1213,7 +1241,7 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
             c.bin_beta = b;
             cand.push_back(c);
         }
-        for (int v = 2; v <= 3; v++)
+        for (int v = 2; v <= 4; v++)
             for (float b : betas) {
                 CellLaunch c = m->cl;
                 c.variant = v;
@@ -1247,7 +1275,7 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
-    if (variant != 0 && !((variant >= 1 && variant <= 3) && m->precision == MS_FP32))
+    if (variant != 0 && !((variant >= 1 && variant <= 4) && m->precision == MS_FP32))
         return fail(MS_ERR_ARG, "unsupported variant %d", variant);
     if (threads != 64 && threads != 128 && threads != 256) return fail(MS_ERR_ARG, "threads must be 64, 128 or 256");
     if (!(bin_beta > 0.1 && bin_beta < 10.0)) return fail(MS_ERR_ARG, "bin_beta must be in (0.1, 10)");

@@ -978,6 +978,359 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
     if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
 }
 
+// ============================================= FP32 warp, neighbour lists
+// The warp kernel with per-floe contact candidate lists kept across steps
+// (variant 4).  A floe moves about |v| dt per step (metres) against radii and
+// bins of kilometres, so the pairs within r_l + r_j + skin found by the bin
+// search stay a superset of the contacts for several steps.  A cell rebuilds
+// its lists (the full binned search of k_cell_step32_warp with the reach
+// widened by the skin) at the first step of every gradual-update period (its
+// radii may just have changed), when any floe has moved more than half the
+// skin since the build, or when a list overflowed; otherwise each floe only
+// tests its list.  The lists of a cell are stored entry-major (entry t of floe
+// k at o NBL + t n + k) so that the lanes' reads coalesce.  Contact forces
+// are summed in list order, which is the search order of the build.
+
+constexpr int NBL = 32;   // list entries per floe
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 8)
+k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
+                    int item1, int cap, int nbmax, int seg)
+{
+    const NbLists &nl = sc.nl;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BlockStep bs;
+    block_step_init(bs, sc, P);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = item0 + blockIdx.x * WARPS + warp;
+    if (sc.live) item1 = min(item1, item0 + sc.live[seg]);
+    if (item >= item1) return;
+    const WarpSm sm = carve_warp(smem + warp * warp_region_bytes(cap, nbmax), cap, nbmax);
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+
+    const float dt = sc.k.dt;
+    const float Lx = sc.k.Lx, Ly = sc.k.Ly, iLx = sc.k.iLx, iLy = sc.k.iLy;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
+    const int c = sc.order[item];
+    const int o = sc.off[c], n = sc.off[c + 1] - o;
+    const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
+    const long long sidx = sc.ctrl->base + sc.i_local + 1;     // this step's index
+    uint16_t *lidx = nl.idx + (size_t)o * NBL;                   // the cell's lists, entry-major
+
+    float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
+    if (bs.ramp) {
+        if (lane == 0) {
+            const RampCell rc = ramp_cell(sc, c, bs.ev);
+            rg = (float)rc.g; rdu = (float)rc.du; rdv = (float)rc.dv; rdw = (float)rc.dw;
+        }
+        rg = __shfl_sync(FULL, rg, 0); rdu = __shfl_sync(FULL, rdu, 0);
+        rdv = __shfl_sync(FULL, rdv, 0); rdw = __shfl_sync(FULL, rdw, 0);
+    }
+    if (lane < P.n_modes) {
+        const int m = lane;
+        const float b = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
+        float sn, cs;
+        if (P.taylor) {
+            sincospif(2.0f * b, &sn, &cs);
+            sm.Cm[m] = make_float2(cs, sn);
+        } else {
+            sm.Cm[m] = make_float2(b, 0.0f);
+        }
+    }
+
+    // ---- keep the lists or rebuild them?
+    const long long built = nl.cstep[c];
+    const float skin0 = nl.skin[c];
+    bool rebuild = (sc.i_local % sc.n_t == 0) || built < 0 || sidx - built >= sc.n_t || sidx < built;
+    if (!rebuild) {
+        const float lim = 0.25f * skin0 * skin0;
+        bool far = false;
+        for (int k = lane; k < n; k += 32) {
+            const uint2 b = nl.xb[o + k];
+            const float dx = (float)(int)(in.xq[o + k] - b.x) * sx, dy = (float)(int)(in.yq[o + k] - b.y) * sy;
+            far |= dx * dx + dy * dy > lim;
+        }
+        rebuild = __any_sync(FULL, far);
+    }
+
+    float acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) acc[k] = 0.0f;
+    unsigned deep = 0;
+    bool bad = false;
+    // drag, forward Euler, gradual update and moments of floe k (stored slot)
+    // given its contact force; shared by both paths
+    auto finish = [&](int k, const float4 &pl, const float4 &vl, const uint2 &ql, float fx, float fy, float tq) {
+        const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
+        float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
+        if (P.taylor) {
+            for (int m = 0; m < P.n_modes; m++) {
+                float c0, s0;
+                rot_small(fmaf(P.ta[m], xf, P.tb[m] * yf), c0, s0);
+                const float2 C = sm.Cm[m];
+                const float cs = C.x * c0 - C.y * s0, sn = C.y * c0 + C.x * s0;
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        } else {
+            for (int m = 0; m < P.n_modes; m++) {
+                const float cyc = sm.Cm[m].x + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
+                float sn, cs;
+                sincospif(2.0f * cyc, &sn, &cs);
+                uo -= P.mAu[m] * cs;
+                vo += P.mAv[m] * cs;
+                zeta -= P.mAz[m] * sn;
+            }
+        }
+        float Fdx, Fdy, Td;
+        drag_force(P, uo, vo, zeta, bs.ua, bs.va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+        fx += Fdx; fy += Fdy; tq += Td;
+        const float r = pl.z, h = pl.w;
+        const float mass = P.mass_c * r * r * h;
+        const float I = P.inertia_f * mass * r * r;
+        float un = vl.x + dt * (fx / mass);
+        float vn = vl.y + dt * (fy / mass);
+        float wn = vl.z + dt * (tq / I);
+        float rn = r;
+        if (bs.ramp) {
+            rn = r * rg;
+            un += rdu;
+            vn += rdv;
+            wn += rdw;
+        }
+        bad |= !(isfinite(un) && isfinite(vn) && isfinite(wn));
+        const int gi = o + k;
+        out.u[gi] = un;
+        out.v[gi] = vn;
+        out.w[gi] = wn;
+        if (bs.ramp || out.r != in.r) out.r[gi] = rn;
+        float a12[NMOM];
+#pragma unroll
+        for (int q = 0; q < NMOM; q++) a12[q] = 0.0f;
+        add_moments(a12, P.mass_c, P.inertia_f, un, vn, wn, rn, h, Fdx, Fdy, Td);
+#pragma unroll
+        for (int q = 1; q < NMOM; q++) acc[q] += a12[q];
+    };
+
+    if (!rebuild) {
+        // ---- the cell in floe order; each floe tests its list
+        for (int k = lane; k < n; k += 32) {
+            const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
+            const float u = in.u[o + k], v = in.v[o + k], w = in.w[o + k];
+            sm.S4[k] = make_float4((float)xq * sx, (float)yq * sy, in.r[o + k], in.h[o + k]);
+            sm.SV[k] = make_float4(u, v, w, 0.0f);
+            sm.SQ[k] = make_uint2(xq, yq);
+            out.xq[o + k] = xq + (uint32_t)__float2int_rn(dt * u * isx);
+            out.yq[o + k] = yq + (uint32_t)__float2int_rn(dt * v * isy);
+            out.th[o + k] = in.th[o + k] + dt * w;
+        }
+        __syncwarp();
+        for (int p = lane; p < n; p += 32) {
+            const float4 pl = sm.S4[p];
+            const float4 vl = sm.SV[p];
+            const uint2 ql = sm.SQ[p];
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            const int cnt = nl.cnt[o + p];
+            for (int t = 0; t < cnt; t++) {
+                const int j = lidx[(size_t)t * n + p];
+                const uint2 qj = sm.SQ[j];
+                const float dx = (float)(int)(qj.x - ql.x) * sx;
+                const float dy = (float)(int)(qj.y - ql.y) * sy;
+                const float4 pj = sm.S4[j];
+                const float4 vj = sm.SV[j];
+                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z, vj.z,
+                            P, fx, fy, tq, deep);
+            }
+            finish(p, pl, vl, ql, fx, fy, tq);
+        }
+    } else {
+        // ---- rebuild: the binned search of k_cell_step32_warp with the reach
+        // widened by the skin, recording every candidate
+        float vmax = 0.0f;
+        for (int k = lane; k < n; k += 32) vmax = fmaxf(vmax, fmaxf(fabsf(in.u[o + k]), fabsf(in.v[o + k])));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(FULL, vmax, d));
+        // over one gradual-update period a floe moving at the cell's largest
+        // speed covers 0.71 of half the skin (sqrt 2 for both axes)
+        const float skin = 4.0f * vmax * dt * (float)sc.n_t + 1.0e-3f;
+        int nb = (int)(sqrtf((float)n) / beta);
+        nb = nb > nbmax ? nbmax : nb;
+        if (nb < 3) nb = 0;
+        const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
+        const float Rs = nb ? 0.5f * fminf(Bx, By) - 0.5f * skin : -1.0f;
+        const int nbins = nb * nb;
+        for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+        __syncwarp();
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n;
+            const uint32_t xq = valid ? in.xq[o + k] : 0u, yq = valid ? in.yq[o + k] : 0u;
+            const float r = valid ? in.r[o + k] : 0.0f;
+            const bool small = valid && r <= Rs;
+            const int b = small ? (int)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb)) : -1 - lane;
+            const unsigned m = __match_any_sync(FULL, b);
+            if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+            __syncwarp();
+        }
+        const int nsmall = warp_scan_excl(sm.cnt, sm.bst, nbins + 1, lane);
+        for (int b = lane; b <= nbins; b += 32) sm.cnt[b] = 0;
+        __syncwarp();
+        int lrun = nsmall;
+        for (int k0 = 0; k0 < n; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < n;
+            uint32_t xq = 0u, yq = 0u;
+            float r = 0.0f, h = 0.0f, u = 0.0f, v = 0.0f, w = 0.0f, th = 0.0f;
+            if (valid) {
+                xq = in.xq[o + k]; yq = in.yq[o + k];
+                r = in.r[o + k]; h = in.h[o + k];
+                u = in.u[o + k]; v = in.v[o + k]; w = in.w[o + k]; th = in.th[o + k];
+            }
+            const bool small = valid && r <= Rs;
+            const bool large = valid && !small;
+            const int b = small ? (int)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb)) : -1 - lane;
+            const unsigned m = __match_any_sync(FULL, b);
+            const unsigned bl = __ballot_sync(FULL, large);
+            int pos = 0;
+            if (small) pos = sm.bst[b] + sm.cnt[b] + __popc(m & lt);
+            else if (large) pos = lrun + __popc(bl & lt);
+            if (valid) {
+                sm.S4[pos] = make_float4((float)xq * sx, (float)yq * sy, r, h);
+                sm.SV[pos] = make_float4(u, v, w, 0.0f);
+                sm.SQ[pos] = make_uint2(xq, yq);
+                sm.orig[pos] = (short)k;
+                out.xq[o + k] = xq + (uint32_t)__float2int_rn(dt * u * isx);
+                out.yq[o + k] = yq + (uint32_t)__float2int_rn(dt * v * isy);
+                out.th[o + k] = th + dt * w;
+                nl.xb[o + k] = make_uint2(xq, yq);
+            }
+            __syncwarp();
+            if (small && lane == __ffs(m) - 1) sm.cnt[b] += __popc(m);
+            lrun += __popc(bl);
+            __syncwarp();
+        }
+        bool overflow = false;
+        for (int p = lane; p < n; p += 32) {
+            const float4 pl = sm.S4[p];
+            const float4 vl = sm.SV[p];
+            const uint2 ql = sm.SQ[p];
+            const int kp = sm.orig[p];
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            int nlst = 0;
+            auto touch = [&](int k) {
+                const uint2 qj = sm.SQ[k];
+                const float dx = (float)(int)(qj.x - ql.x) * sx;
+                const float dy = (float)(int)(qj.y - ql.y) * sy;
+                const float4 pj = sm.S4[k];
+                const float4 vj = sm.SV[k];
+                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
+                            vj.z, P, fx, fy, tq, deep);
+                if (nlst < NBL) lidx[(size_t)nlst * n + kp] = (uint16_t)sm.orig[k];
+                nlst++;
+            };
+            int ncand = 0;
+            short *cl = sm.clist + lane;
+            auto flush = [&]() {
+                for (int i = 0; i < ncand; i++) touch(cl[32 * i]);
+                ncand = 0;
+            };
+            auto hit = [&](int k) {
+                if (ncand == MAXC) flush();
+                cl[32 * ncand] = (short)k;
+                ncand++;
+            };
+            auto scan = [&](int k0, int k1, float xs, float ys, bool mix, bool miy) {
+                for (int k = k0; k < k1; k++) {
+                    const float4 q = sm.S4[k];
+                    float dx = q.x - xs, dy = q.y - ys;
+                    if (mix) dx = min_image(dx, Lx, iLx);
+                    if (miy) dy = min_image(dy, Ly, iLy);
+                    const float S = pl.z + q.z + skin;
+                    if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+                }
+            };
+            const bool small = p < nsmall;
+            if (small) {
+                const int bx = (int)__umulhi(ql.x, (unsigned)nb), by = (int)__umulhi(ql.y, (unsigned)nb);
+                int a0 = bx - 1, a1 = bx + 1, c0 = 1, c1 = 0;
+                float xc = pl.x;
+                if (bx == 0) { a0 = 0; a1 = 1; c0 = nb - 1; c1 = nb - 1; xc = pl.x + Lx; }
+                else if (bx == nb - 1) { a0 = nb - 2; a1 = nb - 1; c0 = 0; c1 = 0; xc = pl.x - Lx; }
+#pragma unroll
+                for (int dyb = -1; dyb <= 1; dyb++) {
+                    int wy = by + dyb;
+                    float ys = pl.y;
+                    if (wy < 0) { wy += nb; ys += Ly; } else if (wy >= nb) { wy -= nb; ys -= Ly; }
+                    const int row = wy * nb;
+                    const int kA = sm.bst[row + a0], nA = sm.bst[row + a1 + 1] - kA;
+                    const int kC = sm.bst[row + c0], nC = c1 >= c0 ? sm.bst[row + c1 + 1] - kC : 0;
+                    for (int i = 0; i < nA + nC; i++) {
+                        const bool inA = i < nA;
+                        const int k = inA ? kA + i : kC + (i - nA);
+                        const float4 q = sm.S4[k];
+                        const float dx = q.x - (inA ? pl.x : xc), dy = q.y - ys;
+                        const float S = pl.z + q.z + skin;
+                        if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+                    }
+                }
+            } else if (nb) {
+                const float reach = 1.001f * (pl.z + Rs + skin);
+                int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
+                int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+                const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
+                if (allx) { bx0 = 0; bx1 = nb - 1; }
+                if (ally) { by0 = 0; by1 = nb - 1; }
+                for (int by = by0; by <= by1; by++) {
+                    const int wy = by < 0 ? by + nb : (by >= nb ? by - nb : by);
+                    const float ys = ally ? pl.y : (by < 0 ? pl.y + Ly : (by >= nb ? pl.y - Ly : pl.y));
+                    const int row = wy * nb;
+                    if (allx) {
+                        scan(sm.bst[row], sm.bst[row + nb], pl.x, ys, true, ally);
+                    } else {
+                        if (bx0 < 0) scan(sm.bst[row + bx0 + nb], sm.bst[row + nb], pl.x + Lx, ys, false, ally);
+                        const int a0 = bx0 < 0 ? 0 : bx0, a1 = bx1 > nb - 1 ? nb - 1 : bx1;
+                        scan(sm.bst[row + a0], sm.bst[row + a1 + 1], pl.x, ys, false, ally);
+                        if (bx1 >= nb) scan(sm.bst[row], sm.bst[row + bx1 - nb + 1], pl.x - Lx, ys, false, ally);
+                    }
+                }
+            }
+            scan(nsmall, n, pl.x, pl.y, true, true);
+            flush();
+            overflow |= nlst > NBL;
+            nl.cnt[o + kp] = (uint8_t)(nlst < NBL ? nlst : NBL);
+            finish(kp, pl, vl, ql, fx, fy, tq);
+        }
+        const bool any_over = __any_sync(FULL, overflow);
+        if (lane == 0) {
+            nl.cstep[c] = any_over ? -1 : sidx;     // an overflowing cell searches again next step
+            nl.skin[c] = skin;
+        }
+    }
+
+    // ---- moments: lane 2k holds the warp total of column k
+    const float tot = warp_sum16(acc, lane);
+    const double dtot = (double)tot;
+    const double M = __shfl_sync(FULL, dtot, 2), Mu = __shfl_sync(FULL, dtot, 4), Mv = __shfl_sync(FULL, dtot, 6);
+    const double Fx = __shfl_sync(FULL, dtot, 18), Fy = __shfl_sync(FULL, dtot, 20), Tz = __shfl_sync(FULL, dtot, 22);
+    double *mo = sc.mom + (size_t)c * NMOM;
+    if ((lane & 1) == 0 && lane < 2 * NMOM) mo[lane >> 1] = lane == 0 ? (double)n : dtot;
+    if (lane == 0 && sc.couple) {
+        const int nc = sc.ncell;
+        if (M > 0.0) {
+            sc.win[c] += Mu / M;
+            sc.win[nc + c] += Mv / M;
+        }
+        sc.win[2 * nc + c] += Fx;
+        sc.win[3 * nc + c] += Fy;
+        sc.win[4 * nc + c] += Tz;
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+    if (deep) atomicAdd(&sc.ctrl->deep, 1ull);
+}
+
 // ======================================================= FP32 warp, resident
 // The warp kernel's step, repeated for a run of fine steps with the cell kept
 // in shared memory.  Between coarse steps a cell depends on nothing but
@@ -1745,6 +2098,11 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
         k_cell_run32_packed<4><<<(cl.npack + 3) / 4, 128, sm, st>>>(in, out, P, sc0, cl.pack, cl.npack, nsteps);
         return cudaGetLastError();
     }
+    if (cl.seg_kind[s] == 1 && cl.variant == 4 && nsteps == 1) {
+        k_cell_step32_wlist<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc0, cl.bin_beta, cl.seg_begin[s],
+                                                                 cl.seg_end[s], cl.seg_maxn[s], nbm, s);
+        return cudaGetLastError();
+    }
     if (cl.seg_kind[s] == 1 && cl.variant == 3) {
         k_cell_run32_warp<4><<<(items + 3) / 4, 128, sm, st>>>(in, out, P, sc0, nsteps, cl.bin_beta, cl.seg_begin[s],
                                                                cl.seg_end[s], cl.seg_maxn[s], nbm, s);
@@ -1806,7 +2164,8 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step64_brute<128>, (const void *)k_cell_step64_brute<256>,
             (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
             (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>,
-            (const void *)k_cell_run32_warp<4>, (const void *)k_cell_run32_packed<4>};
+            (const void *)k_cell_run32_warp<4>, (const void *)k_cell_run32_packed<4>,
+            (const void *)k_cell_step32_wlist<4>};
         limit = optin;
         for (const void *k : kern) {
             cudaFuncAttributes fa;
@@ -1859,7 +2218,7 @@ cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, cons
         }
         return cudaSuccess;
     }
-    if (cl.variant == 2 || cl.variant == 3) {
+    if (cl.variant >= 2) {
         // every size class on its own stream: the classes hold disjoint cells,
         // so their kernels overlap and their tails hide each other
         cudaError_t e = cudaEventRecord(cl.ev_fork, st);

@@ -274,8 +274,20 @@ struct Geo32 {
     float dt;
 };
 
+// Contact candidate lists of the FP32 state (variant 4): per floe up to 32
+// cell-local floe indices, stored entry-major per cell; the positions they
+// were built from; per cell the step of the build (< 0: none) and the skin.
+struct NbLists {
+    uint16_t *idx;      // [n][32]: entry t of floe k of a cell at off NBL + t n_cell + k
+    uint8_t *cnt;       // [n]
+    uint2 *xb;          // [n] fixed-point position at the build
+    long long *cstep;   // [ncell]
+    float *skin;        // [ncell]
+};
+
 struct StepCommon {
     Geo32 k;
+    NbLists nl;         // candidate lists of the state the launch writes
     const int *live;    // per size class: cells to step (the rest run the closure); nullptr: all
     const int *off;     // [ncell + 1]
     const int *order;   // [ncell] processing order (largest cells first); in closure mode the

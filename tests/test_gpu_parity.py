@@ -241,6 +241,41 @@ def test_resident_run_equals_single_steps(ms):
     assert np.array_equal(a.coupling()["q"], b.coupling()["q"])
 
 
+def test_neighbour_lists_graph_equals_single_steps(ms):
+    """Variant 4 keeps candidate lists in device memory across steps; an
+    interval replayed from the graph and the same steps launched one by one
+    give the same floes bitwise, across list rebuilds, coarse steps and
+    gradual updates; after set_floes the lists are rebuilt (a moved floe must
+    not keep stale partners)."""
+    s = I.config2(seed=9, nx=16)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    a = ms.Model(p, s["floes"], ms.MS_FP32)
+    b = ms.Model(p, s["floes"], ms.MS_FP32)
+    a.set_launch(4, 128, 0, 1.3)
+    b.set_launch(4, 128, 0, 1.3)
+    a.step(dt, 2 * N0 + 23)
+    for _ in range(2 * N0 + 23):
+        b.step(dt, 1)
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(a.moments(), b.moments())
+    # squeeze every cell's floes a quarter of the way towards its centre line
+    # through the public API (many new overlaps): variant 4 must search again
+    # and agree with variant 2 given the same floes
+    d = ms.Model(p, s["floes"], ms.MS_FP32)
+    d.set_launch(2, 128, 0, 1.3)
+    d.step(dt, 2 * N0 + 23)
+    f = a.floes()
+    f["x"] = f["x"] + 0.25 * (np.floor(f["x"] / 25e3) * 25e3 + 12.5e3 - f["x"])
+    a.set_floes(f)
+    d.set_floes(f)
+    a.step(dt, 7)
+    d.step(dt, 7)
+    ea = rel_errors(a.moments(), d.moments(), p, 1e-6)
+    assert ea.max() < 1e-4, report(ea)
+
+
 def test_launch_variants_agree(ms):
     """Threads per block and the persistent work queue change only the order
     of the moment reduction, never a floe's arithmetic: floes agree bitwise
@@ -326,12 +361,12 @@ def test_set_floes_roundtrip(ms):
         assert np.array_equal(f[k], f2[k]), k
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_fp32_variants_match_oracle(orc, ms, variant):
-    """Brute-force, block-binned, warp-binned and resident warp-binned pair
-    search: each within the FP32 tolerance of the oracle over 100 steps on a
-    ragged mix of cells (0 to 300 floes, so every size class and both launch
-    kinds run)."""
+    """Brute-force, block-binned, warp-binned, resident warp-binned and
+    neighbour-list pair search: each within the FP32 tolerance of the oracle
+    over 100 steps on a ragged mix of cells (0 to 300 floes, so every size
+    class and every launch kind runs)."""
     s = ragged_scenario([0, 1, 5, 17, 31, 33, 64, 65, 100, 127, 129, 200, 256, 257, 300], seed=21)
     p = s["params"]
     o = orc.Model(p, s["floes"])
@@ -348,7 +383,7 @@ def test_fp32_variants_agree_one_step(ms):
     find the same contacts, so moments agree to FP32 summation order."""
     s = I.config1(nx=16)
     res = []
-    for variant in (0, 1, 2, 3):
+    for variant in (0, 1, 2, 3, 4):
         g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
         g.set_launch(variant, 128, 0, 1.0)
         g.step(s["dt"], 1)
