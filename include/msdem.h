@@ -197,9 +197,10 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
  * variant 2 with each warp cell also kept in shared memory for a whole
  * coarse interval (one launch per interval instead of one per fine step; the
  * per-step arithmetic of variant 2); variant 4 = variant 2 with per-floe
- * contact candidate lists kept across steps (pairs within r_l + r_j + skin,
- * rebuilt by the binned search at the start of every gradual-update period
- * and whenever a floe has moved half the skin).  Variants 2-4 give the same
+ * contact candidate lists kept across steps in the warp and block cells
+ * (pairs within r_l + r_j + skin, rebuilt by the binned search at the start
+ * of every gradual-update period and whenever a floe has moved half the
+ * skin).  Variants 2-4 give the same
  * results whether an interval runs in one launch or step by step.
  * MS_ERR_ARG for an unsupported choice. */
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);

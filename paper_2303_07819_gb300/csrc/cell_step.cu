@@ -396,11 +396,15 @@ __host__ __device__ inline size_t smem32_binned(int T, int maxn, int nbmax)
            a16(sizeof(int) * 8) + 2 * a16(sizeof(short) * maxn) + a16(sizeof(short) * MAXC_B * T);
 }
 
-template <int T>
+// LISTS: variant 4's candidate lists (see k_cell_step32_wlist) kept across
+// steps; a cell rebuilds them with this kernel's binned search, widened by
+// the skin, and otherwise tests only its lists.
+template <int T, bool LISTS = false>
 __global__ void __launch_bounds__(T)
 k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
                      int item1, int maxn, int nbmax, int seg)
 {
+    __shared__ float s_vmax[T / 32];
     extern __shared__ __align__(16) unsigned char smem[];
     const Bin32 sm = carve32<T>(smem, maxn, nbmax);
 
@@ -417,11 +421,39 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         const int c = sc.order[item];
         const int o = sc.off[c], n = sc.off[c + 1] - o;
         const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
+        // ---- candidate lists: keep them or rebuild (block-uniform decision)
+        bool rebuild = true;
+        float skin = 0.0f;
+        const long long sstep = sc.ctrl->base + sc.i_local + 1;
+        uint16_t *lidx = LISTS ? sc.nl.idx + (size_t)o * NBL : nullptr;
+        if (LISTS) {
+            const long long built = sc.nl.cstep[c];
+            const float lim = 0.25f * sc.nl.skin[c] * sc.nl.skin[c];
+            const bool r0 = (sc.i_local % sc.n_t == 0) || built < 0 || sstep - built >= sc.n_t || sstep < built;
+            bool far = false;
+            float vmax = 0.0f;
+            for (int k = threadIdx.x; k < n; k += T) {
+                if (!r0) {
+                    const uint2 b = sc.nl.xb[o + k];
+                    const float dx = (float)(int)(in.xq[o + k] - b.x) * sx;
+                    const float dy = (float)(int)(in.yq[o + k] - b.y) * sy;
+                    far |= dx * dx + dy * dy > lim;
+                }
+                vmax = fmaxf(vmax, fmaxf(fabsf(in.u[o + k]), fabsf(in.v[o + k])));
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
+            if ((threadIdx.x & 31) == 0) s_vmax[threadIdx.x >> 5] = vmax;
+            rebuild = __syncthreads_or(r0 || far) != 0;
+            for (int w = 0; w < T / 32; w++) vmax = fmaxf(vmax, s_vmax[w]);
+            // as in k_cell_step32_wlist
+            if (rebuild) skin = 4.0f * vmax * dt * (float)sc.n_t + 1.0e-3f;
+        }
         int nb = (int)(sqrtf((float)n) / beta);
         nb = nb > nbmax ? nbmax : nb;
         if (nb < 3) nb = 0;                       // few floes: every floe in the list
         const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
-        const float Rs = nb ? 0.5f * fminf(Bx, By) : -1.0f;
+        const float Rs = nb ? 0.5f * fminf(Bx, By) - 0.5f * skin : -1.0f;
         const int nbins = nb * nb;
         if (threadIdx.x < P.n_modes) {
             const int m = threadIdx.x;
@@ -436,14 +468,38 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             sm.P4[k] = make_float4((float)xq * sx, (float)yq * sy, r, in.h[o + k]);
             sm.V4[k] = make_float4(in.u[o + k], in.v[o + k], in.w[o + k], 0.0f);
             sm.Q[k] = make_uint2(xq, yq);
-            short b = -1;
-            if (r <= Rs) {
-                b = (short)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb));
-                atomicAdd(&sm.cnt[b], 1);
+            if (rebuild) {
+                short b = -1;
+                if (r <= Rs) {
+                    b = (short)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb));
+                    atomicAdd(&sm.cnt[b], 1);
+                }
+                sm.bin[k] = b;
+                if (LISTS) sc.nl.xb[o + k] = make_uint2(xq, yq);
             }
-            sm.bin[k] = b;
         }
         __syncthreads();
+        if (LISTS && !rebuild) {
+            // ---- contacts from the lists
+            for (int l = threadIdx.x; l < n; l += T) {
+                const float4 pl = sm.P4[l];
+                const float4 vl = sm.V4[l];
+                const uint2 ql = sm.Q[l];
+                float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+                const int cnt = sc.nl.cnt[o + l];
+                for (int t = 0; t < cnt; t++) {
+                    const int j = lidx[(size_t)t * n + l];
+                    const uint2 qj = sm.Q[j];
+                    const float dx = (float)(int)(qj.x - ql.x) * sx;
+                    const float dy = (float)(int)(qj.y - ql.y) * sy;
+                    const float4 pj = sm.P4[j];
+                    const float4 vj = sm.V4[j];
+                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
+                                vj.z, P, fx, fy, tq, deep);
+                }
+                sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
+            }
+        } else {
         const int nsmall = block_scan_excl<T>(sm.cnt, sm.bst, nbins + 1, sm.tmp);
         for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
         __syncthreads();
@@ -486,13 +542,15 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         for (int p = threadIdx.x; p < n; p += T) sm.S4[p] = sm.P4[sm.sidx[p]];
         __syncthreads();
 
-        // ---- contacts
+        // ---- contacts (and, with lists, every candidate within the skin recorded)
+        bool overflow = false;
         for (int p = threadIdx.x; p < n; p += T) {
             const int l = sm.sidx[p];
             const float4 pl = sm.P4[l];
             const float4 vl = sm.V4[l];
             const uint2 ql = sm.Q[l];
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            int nlst = 0;
             auto touch = [&](int k) {
                 const int j = sm.sidx[k];
                 const uint2 qj = sm.Q[j];
@@ -502,6 +560,10 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 const float4 vj = sm.V4[j];
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                             vj.z, P, fx, fy, tq, deep);
+                if (LISTS) {
+                    if (nlst < NBL) lidx[(size_t)nlst * n + l] = (uint16_t)j;
+                    nlst++;
+                }
             };
             // collect candidates, then compute their forces with the threads in step
             int ncand = 0;
@@ -522,7 +584,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 const int bx = b % nb, by = b / nb;
                 bx0 = bx - 1; bx1 = bx + 1; by0 = by - 1; by1 = by + 1;
             } else if (nb) {
-                const float reach = 1.001f * (pl.z + Rs);
+                const float reach = 1.001f * (pl.z + Rs + skin);
                 bx0 = (int)floorf((pl.x - reach) / Bx); bx1 = (int)floorf((pl.x + reach) / Bx);
                 by0 = (int)floorf((pl.y - reach) / By); by1 = (int)floorf((pl.y + reach) / By);
                 if (bx1 - bx0 + 1 >= nb) { bx0 = 0; bx1 = nb - 1; }
@@ -545,7 +607,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                         float dx = q.x - xs, dy = q.y - ys;
                         if (wrapx) dx = min_image(dx, Lx, iLx);
                         if (wrapy) dy = min_image(dy, Ly, iLy);
-                        const float S = pl.z + q.z;
+                        const float S = pl.z + q.z + skin;
                         if (k != p && dx * dx + dy * dy < S * S) hit(k);
                     }
                 }
@@ -555,11 +617,23 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 const float4 q = sm.S4[k];
                 const float dx = min_image(q.x - pl.x, Lx, iLx);
                 const float dy = min_image(q.y - pl.y, Ly, iLy);
-                const float S = pl.z + q.z;
+                const float S = pl.z + q.z + skin;
                 if (k != p && dx * dx + dy * dy < S * S) hit(k);
             }
             flush();
             sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
+            if (LISTS) {
+                sc.nl.cnt[o + l] = (uint8_t)(nlst < NBL ? nlst : NBL);
+                overflow |= nlst > NBL;
+            }
+        }
+        if (LISTS) {
+            const bool any_over = __syncthreads_or(overflow) != 0;
+            if (threadIdx.x == 0) {
+                sc.nl.cstep[c] = any_over ? -1 : sstep;   // an overflowing cell searches again next step
+                sc.nl.skin[c] = skin;
+            }
+        }
         }
         block_cell_ramp(bs, sc, c);
         __syncthreads();
@@ -990,8 +1064,6 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 // tests its list.  The lists of a cell are stored entry-major (entry t of floe
 // k at o NBL + t n + k) so that the lanes' reads coalesce.  Contact forces
 // are summed in list order, which is the search order of the build.
-
-constexpr int NBL = 32;   // list entries per floe
 
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 8)
@@ -2123,6 +2195,12 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
                                                                 cl.seg_end[s], cl.seg_maxn[s], nbm, s);
         return cudaGetLastError();
     }
+    if (cl.variant == 4) {
+        MS_T_SWITCH(cl.seg_threads[s],
+                    k_cell_step32_binned<TT, true><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
+                                                                          cl.seg_end[s], cl.seg_maxn[s], nbm, s));
+        return cudaGetLastError();
+    }
     MS_T_SWITCH(cl.seg_threads[s],
                 k_cell_step32_binned<TT><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
                                                                 cl.seg_end[s], cl.seg_maxn[s], nbm, s));
@@ -2165,7 +2243,8 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step32_binned<64>, (const void *)k_cell_step32_binned<128>,
             (const void *)k_cell_step32_binned<256>, (const void *)k_cell_step32_warp<4>,
             (const void *)k_cell_run32_warp<4>, (const void *)k_cell_run32_packed<4>,
-            (const void *)k_cell_step32_wlist<4>};
+            (const void *)k_cell_step32_wlist<4>, (const void *)k_cell_step32_binned<64, true>,
+            (const void *)k_cell_step32_binned<128, true>, (const void *)k_cell_step32_binned<256, true>};
         limit = optin;
         for (const void *k : kern) {
             cudaFuncAttributes fa;

@@ -277,6 +277,8 @@ struct Geo32 {
 // Contact candidate lists of the FP32 state (variant 4): per floe up to 32
 // cell-local floe indices, stored entry-major per cell; the positions they
 // were built from; per cell the step of the build (< 0: none) and the skin.
+constexpr int NBL = 32;   // candidate list entries per floe
+
 struct NbLists {
     uint16_t *idx;      // [n][32]: entry t of floe k of a cell at off NBL + t n_cell + k
     uint8_t *cnt;       // [n]
