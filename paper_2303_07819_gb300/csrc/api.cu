@@ -617,7 +617,7 @@ static void make_segments(ms_model *m, CellLaunch &c)
     // up to 256 floes warp-per-cell with the class bound as the warp capacity
     struct Cls { int hi, threads, kind; };
     const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
-    const Cls v2[7] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 1}, {192, 128, 1},
+    const Cls v2[7] = {{1 << 30, 128, 0}, {512, 128, 0}, {256, 128, 1}, {192, 128, 1},
                        {128, 128, 1}, {64, 128, 1}, {32, 128, 2}};
     const Cls *cls = c.variant >= 2 ? v2 : v1;
     const int ncls = c.variant >= 2 ? 7 : 4;

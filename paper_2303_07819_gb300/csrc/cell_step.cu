@@ -426,20 +426,34 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         float skin = 0.0f;
         const long long sstep = sc.ctrl->base + sc.i_local + 1;
         uint16_t *lidx = LISTS ? sc.nl.idx + (size_t)o * NBL : nullptr;
+        int nb = (int)(sqrtf((float)n) / beta);
+        nb = nb > nbmax ? nbmax : nb;
+        if (nb < 3) nb = 0;                       // few floes: every floe in the list
+        const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
+        const int nbins = nb * nb;
+        if (threadIdx.x < P.n_modes) {
+            const int m = threadIdx.x;
+            sm.base[m] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
+        }
+        for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
         if (LISTS) {
+            // ---- stage the cell, and decide whether the lists still hold:
+            // one pass, all of a floe's loads independent
             const long long built = sc.nl.cstep[c];
             const float lim = 0.25f * sc.nl.skin[c] * sc.nl.skin[c];
             const bool r0 = (sc.i_local % sc.n_t == 0) || built < 0 || sstep - built >= sc.n_t || sstep < built;
             bool far = false;
             float vmax = 0.0f;
             for (int k = threadIdx.x; k < n; k += T) {
-                if (!r0) {
-                    const uint2 b = sc.nl.xb[o + k];
-                    const float dx = (float)(int)(in.xq[o + k] - b.x) * sx;
-                    const float dy = (float)(int)(in.yq[o + k] - b.y) * sy;
-                    far |= dx * dx + dy * dy > lim;
-                }
-                vmax = fmaxf(vmax, fmaxf(fabsf(in.u[o + k]), fabsf(in.v[o + k])));
+                const uint2 b = sc.nl.xb[o + k];
+                const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
+                const float r = in.r[o + k], h = in.h[o + k], u = in.u[o + k], v = in.v[o + k], w = in.w[o + k];
+                sm.P4[k] = make_float4((float)xq * sx, (float)yq * sy, r, h);
+                sm.V4[k] = make_float4(u, v, w, 0.0f);
+                sm.Q[k] = make_uint2(xq, yq);
+                const float dx = (float)(int)(xq - b.x) * sx, dy = (float)(int)(yq - b.y) * sy;
+                far |= dx * dx + dy * dy > lim;
+                vmax = fmaxf(vmax, fmaxf(fabsf(u), fabsf(v)));
             }
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, d));
@@ -448,47 +462,55 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             for (int w = 0; w < T / 32; w++) vmax = fmaxf(vmax, s_vmax[w]);
             // as in k_cell_step32_wlist
             if (rebuild) skin = 4.0f * vmax * dt * (float)sc.n_t + 1.0e-3f;
+        } else {
+            __syncthreads();
         }
-        int nb = (int)(sqrtf((float)n) / beta);
-        nb = nb > nbmax ? nbmax : nb;
-        if (nb < 3) nb = 0;                       // few floes: every floe in the list
-        const float Bx = nb ? Lx / nb : Lx, By = nb ? Ly / nb : Ly;
         const float Rs = nb ? 0.5f * fminf(Bx, By) - 0.5f * skin : -1.0f;
-        const int nbins = nb * nb;
-        if (threadIdx.x < P.n_modes) {
-            const int m = threadIdx.x;
-            sm.base[m] = corner_phase(P, m, ix, iy, sc.g.nx, sc.g.nyr, inx, iny);
-        }
-        for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
-        __syncthreads();
-        // ---- stage the cell and count small floes per bin
-        for (int k = threadIdx.x; k < n; k += T) {
-            const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
-            const float r = in.r[o + k];
-            sm.P4[k] = make_float4((float)xq * sx, (float)yq * sy, r, in.h[o + k]);
-            sm.V4[k] = make_float4(in.u[o + k], in.v[o + k], in.w[o + k], 0.0f);
-            sm.Q[k] = make_uint2(xq, yq);
+        if (LISTS) {
+            // ---- bins from the staged cell (only when searching again)
             if (rebuild) {
+                for (int k = threadIdx.x; k < n; k += T) {
+                    const uint2 q = sm.Q[k];
+                    short b = -1;
+                    if (sm.P4[k].z <= Rs) {
+                        b = (short)(__umulhi(q.y, (unsigned)nb) * nb + __umulhi(q.x, (unsigned)nb));
+                        atomicAdd(&sm.cnt[b], 1);
+                    }
+                    sm.bin[k] = b;
+                    sc.nl.xb[o + k] = q;
+                }
+            }
+        } else {
+            // ---- stage the cell and count small floes per bin
+            for (int k = threadIdx.x; k < n; k += T) {
+                const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
+                const float r = in.r[o + k];
+                sm.P4[k] = make_float4((float)xq * sx, (float)yq * sy, r, in.h[o + k]);
+                sm.V4[k] = make_float4(in.u[o + k], in.v[o + k], in.w[o + k], 0.0f);
+                sm.Q[k] = make_uint2(xq, yq);
                 short b = -1;
                 if (r <= Rs) {
                     b = (short)(__umulhi(yq, (unsigned)nb) * nb + __umulhi(xq, (unsigned)nb));
                     atomicAdd(&sm.cnt[b], 1);
                 }
                 sm.bin[k] = b;
-                if (LISTS) sc.nl.xb[o + k] = make_uint2(xq, yq);
             }
         }
         __syncthreads();
         if (LISTS && !rebuild) {
-            // ---- contacts from the lists
+            // ---- contacts from the lists; the first LPF entries are loaded
+            // with the count (in bounds: NBL entries per floe are allocated)
+            constexpr int LPF = 8;
             for (int l = threadIdx.x; l < n; l += T) {
+                const int cnt = sc.nl.cnt[o + l];
+                uint16_t jj[LPF];
+#pragma unroll
+                for (int t = 0; t < LPF; t++) jj[t] = lidx[(size_t)t * n + l];
                 const float4 pl = sm.P4[l];
                 const float4 vl = sm.V4[l];
                 const uint2 ql = sm.Q[l];
                 float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-                const int cnt = sc.nl.cnt[o + l];
-                for (int t = 0; t < cnt; t++) {
-                    const int j = lidx[(size_t)t * n + l];
+                auto pair = [&](int j) {
                     const uint2 qj = sm.Q[j];
                     const float dx = (float)(int)(qj.x - ql.x) * sx;
                     const float dy = (float)(int)(qj.y - ql.y) * sy;
@@ -496,7 +518,11 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                     const float4 vj = sm.V4[j];
                     contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                                 vj.z, P, fx, fy, tq, deep);
-                }
+                };
+#pragma unroll
+                for (int t = 0; t < LPF; t++)
+                    if (t < cnt) pair(jj[t]);
+                for (int t = LPF; t < cnt; t++) pair(lidx[(size_t)t * n + l]);
                 sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
             }
         } else {
@@ -1117,12 +1143,20 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     const float skin0 = nl.skin[c];
     bool rebuild = (sc.i_local % sc.n_t == 0) || built < 0 || sidx - built >= sc.n_t || sidx < built;
     if (!rebuild) {
+        // the cell in floe order (angle in SV.w), and the displacement check,
+        // in one pass: all of a floe's loads are independent
         const float lim = 0.25f * skin0 * skin0;
         bool far = false;
         for (int k = lane; k < n; k += 32) {
             const uint2 b = nl.xb[o + k];
-            const float dx = (float)(int)(in.xq[o + k] - b.x) * sx, dy = (float)(int)(in.yq[o + k] - b.y) * sy;
+            const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
+            const float r = in.r[o + k], h = in.h[o + k], u = in.u[o + k], v = in.v[o + k], w = in.w[o + k];
+            const float th = in.th[o + k];
+            const float dx = (float)(int)(xq - b.x) * sx, dy = (float)(int)(yq - b.y) * sy;
             far |= dx * dx + dy * dy > lim;
+            sm.S4[k] = make_float4((float)xq * sx, (float)yq * sy, r, h);
+            sm.SV[k] = make_float4(u, v, w, th);
+            sm.SQ[k] = make_uint2(xq, yq);
         }
         rebuild = __any_sync(FULL, far);
     }
@@ -1188,26 +1222,24 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     };
 
     if (!rebuild) {
-        // ---- the cell in floe order; each floe tests its list
-        for (int k = lane; k < n; k += 32) {
-            const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
-            const float u = in.u[o + k], v = in.v[o + k], w = in.w[o + k];
-            sm.S4[k] = make_float4((float)xq * sx, (float)yq * sy, in.r[o + k], in.h[o + k]);
-            sm.SV[k] = make_float4(u, v, w, 0.0f);
-            sm.SQ[k] = make_uint2(xq, yq);
-            out.xq[o + k] = xq + (uint32_t)__float2int_rn(dt * u * isx);
-            out.yq[o + k] = yq + (uint32_t)__float2int_rn(dt * v * isy);
-            out.th[o + k] = in.th[o + k] + dt * w;
-        }
+        // ---- each floe tests its list; the first LPF entries are loaded
+        // together with the count (all in bounds: the cell's list block
+        // holds NBL entries per floe), so one memory latency covers them
         __syncwarp();
+        constexpr int LPF = 8;
         for (int p = lane; p < n; p += 32) {
+            const int cnt = nl.cnt[o + p];
+            uint16_t jj[LPF];
+#pragma unroll
+            for (int t = 0; t < LPF; t++) jj[t] = lidx[(size_t)t * n + p];
             const float4 pl = sm.S4[p];
             const float4 vl = sm.SV[p];
             const uint2 ql = sm.SQ[p];
+            out.xq[o + p] = ql.x + (uint32_t)__float2int_rn(dt * vl.x * isx);
+            out.yq[o + p] = ql.y + (uint32_t)__float2int_rn(dt * vl.y * isy);
+            out.th[o + p] = vl.w + dt * vl.z;
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-            const int cnt = nl.cnt[o + p];
-            for (int t = 0; t < cnt; t++) {
-                const int j = lidx[(size_t)t * n + p];
+            auto pair = [&](int j) {
                 const uint2 qj = sm.SQ[j];
                 const float dx = (float)(int)(qj.x - ql.x) * sx;
                 const float dy = (float)(int)(qj.y - ql.y) * sy;
@@ -1215,7 +1247,11 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
                 const float4 vj = sm.SV[j];
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z, vj.z,
                             P, fx, fy, tq, deep);
-            }
+            };
+#pragma unroll
+            for (int t = 0; t < LPF; t++)
+                if (t < cnt) pair(jj[t]);
+            for (int t = LPF; t < cnt; t++) pair(lidx[(size_t)t * n + p]);
             finish(p, pl, vl, ql, fx, fy, tq);
         }
     } else {
