@@ -121,7 +121,7 @@ static cudaError_t alloc32(ms_model *m, DevState32 &s, size_t n)
 static cudaError_t alloc_lists(ms_model *m, NbLists &l, size_t n, int ncell)
 {
     cudaError_t e;
-    if ((e = dalloc(m, &l.idx, n * 32)) || (e = dalloc(m, &l.cnt, n)) || (e = dalloc(m, &l.xb, n)) ||
+    if ((e = dalloc(m, &l.head, n)) || (e = dalloc(m, &l.tail, n * NLT)) || (e = dalloc(m, &l.xb, n)) ||
         (e = dalloc(m, &l.cstep, ncell)) || (e = dalloc(m, &l.skin, ncell)))
         return e;
     return cudaMemsetAsync(l.cstep, 0xff, sizeof(long long) * ncell, m->stream);

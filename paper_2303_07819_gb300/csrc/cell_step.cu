@@ -396,6 +396,63 @@ __host__ __device__ inline size_t smem32_binned(int T, int maxn, int nbmax)
            a16(sizeof(int) * 8) + 2 * a16(sizeof(short) * maxn) + a16(sizeof(short) * MAXC_B * T);
 }
 
+// ---- candidate lists (variant 4): recording and walking a floe's list
+
+// half h (0..7) of a 16-byte list group
+__device__ __forceinline__ int list_half(const uint4 &g, int h)
+{
+    const uint32_t w = h < 2 ? g.x : (h < 4 ? g.y : (h < 6 ? g.z : g.w));
+    return (int)((h & 1) ? (w >> 16) : (w & 0xffffu));
+}
+
+// A floe's list as the search finds its candidates: the head in registers,
+// entries past it straight to the floe's tail groups.
+struct ListRec {
+    uint32_t h0 = 0u, h1 = 0u, h2 = 0u, h3 = 0u;
+    int nlst = 0;
+    __device__ __forceinline__ void add(uint16_t *tail16, int j)
+    {
+        if (nlst < NLH) {
+            const int s = nlst + 1;   // half 0 holds the count
+            const uint32_t v = (uint32_t)j << ((s & 1) * 16);
+            const int wd = s >> 1;
+            h0 |= wd == 0 ? v : 0u;
+            h1 |= wd == 1 ? v : 0u;
+            h2 |= wd == 2 ? v : 0u;
+            h3 |= wd == 3 ? v : 0u;
+        } else if (nlst < NBL) {
+            tail16[nlst - NLH] = (uint16_t)j;
+        }
+        nlst++;
+    }
+    __device__ __forceinline__ uint4 head() const
+    {
+        return make_uint4(h0 | (uint32_t)(nlst < NBL ? nlst : NBL), h1, h2, h3);
+    }
+};
+
+// Calls pair(j) for the entries of a floe's list in order, from one call
+// site (every candidate gets the same compiled arithmetic).  The next tail
+// group is loaded one group ahead of its use.
+template <class PairF>
+__device__ __forceinline__ void list_walk(const uint4 hd, const uint4 *tl, PairF &&pair)
+{
+    const int cnt = (int)(hd.x & 0xffffu);
+    uint4 g = hd, nx = make_uint4(0u, 0u, 0u, 0u);
+    if (cnt > NLH) nx = tl[0];
+    int h = 1, gi = 1;
+    for (int t = 0; t < cnt; t++) {
+        if (h == 8) {
+            g = nx;
+            h = 0;
+            if (NLH + 8 * gi < cnt) nx = tl[gi];
+            gi++;
+        }
+        pair(list_half(g, h));
+        h++;
+    }
+}
+
 // LISTS: variant 4's candidate lists (see k_cell_step32_wlist) kept across
 // steps; a cell rebuilds them with this kernel's binned search, widened by
 // the skin, and otherwise tests only its lists.
@@ -424,8 +481,8 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         // ---- candidate lists: keep them or rebuild (block-uniform decision)
         bool rebuild = true;
         float skin = 0.0f;
+        uint4 hn = make_uint4(0u, 0u, 0u, 0u);     // list head of this thread's next floe
         const long long sstep = sc.ctrl->base + sc.i_local + 1;
-        uint16_t *lidx = LISTS ? sc.nl.idx + (size_t)o * NBL : nullptr;
         int nb = (int)(sqrtf((float)n) / beta);
         nb = nb > nbmax ? nbmax : nb;
         if (nb < 3) nb = 0;                       // few floes: every floe in the list
@@ -442,6 +499,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             const long long built = sc.nl.cstep[c];
             const float lim = 0.25f * sc.nl.skin[c] * sc.nl.skin[c];
             const bool r0 = (sc.i_local % sc.n_t == 0) || built < 0 || sstep - built >= sc.n_t || sstep < built;
+            if (!r0 && (int)threadIdx.x < n) hn = sc.nl.head[o + threadIdx.x];
             bool far = false;
             float vmax = 0.0f;
             for (int k = threadIdx.x; k < n; k += T) {
@@ -498,19 +556,16 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
         }
         __syncthreads();
         if (LISTS && !rebuild) {
-            // ---- contacts from the lists; the first LPF entries are loaded
-            // with the count (in bounds: NBL entries per floe are allocated)
-            constexpr int LPF = 8;
+            // ---- contacts from the lists (the next floe's head is loaded
+            // while this floe's candidates are tested)
             for (int l = threadIdx.x; l < n; l += T) {
-                const int cnt = sc.nl.cnt[o + l];
-                uint16_t jj[LPF];
-#pragma unroll
-                for (int t = 0; t < LPF; t++) jj[t] = lidx[(size_t)t * n + l];
+                const uint4 hd = hn;
+                if (l + T < n) hn = sc.nl.head[o + l + T];
                 const float4 pl = sm.P4[l];
                 const float4 vl = sm.V4[l];
                 const uint2 ql = sm.Q[l];
                 float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-                auto pair = [&](int j) {
+                list_walk(hd, sc.nl.tail + (size_t)(o + l) * NLT, [&](int j) {
                     const uint2 qj = sm.Q[j];
                     const float dx = (float)(int)(qj.x - ql.x) * sx;
                     const float dy = (float)(int)(qj.y - ql.y) * sy;
@@ -518,11 +573,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                     const float4 vj = sm.V4[j];
                     contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                                 vj.z, P, fx, fy, tq, deep);
-                };
-#pragma unroll
-                for (int t = 0; t < LPF; t++)
-                    if (t < cnt) pair(jj[t]);
-                for (int t = LPF; t < cnt; t++) pair(lidx[(size_t)t * n + l]);
+                });
                 sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
             }
         } else {
@@ -576,7 +627,8 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             const float4 vl = sm.V4[l];
             const uint2 ql = sm.Q[l];
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-            int nlst = 0;
+            ListRec rec;
+            uint16_t *tail16 = LISTS ? reinterpret_cast<uint16_t *>(sc.nl.tail + (size_t)(o + l) * NLT) : nullptr;
             auto touch = [&](int k) {
                 const int j = sm.sidx[k];
                 const uint2 qj = sm.Q[j];
@@ -586,10 +638,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 const float4 vj = sm.V4[j];
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                             vj.z, P, fx, fy, tq, deep);
-                if (LISTS) {
-                    if (nlst < NBL) lidx[(size_t)nlst * n + l] = (uint16_t)j;
-                    nlst++;
-                }
+                if (LISTS) rec.add(tail16, j);
             };
             // collect candidates, then compute their forces with the threads in step
             int ncand = 0;
@@ -649,8 +698,8 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             flush();
             sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
             if (LISTS) {
-                sc.nl.cnt[o + l] = (uint8_t)(nlst < NBL ? nlst : NBL);
-                overflow |= nlst > NBL;
+                sc.nl.head[o + l] = rec.head();
+                overflow |= rec.nlst > NBL;
             }
         }
         if (LISTS) {
@@ -1087,9 +1136,10 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 // widened by the skin) at the first step of every gradual-update period (its
 // radii may just have changed), when any floe has moved more than half the
 // skin since the build, or when a list overflowed; otherwise each floe only
-// tests its list.  The lists of a cell are stored entry-major (entry t of floe
-// k at o NBL + t n + k) so that the lanes' reads coalesce.  Contact forces
-// are summed in list order, which is the search order of the build.
+// tests its list.  A floe's count and first NLH entries are one 16-byte head
+// (consecutive floes' heads are adjacent, so the lanes' loads coalesce); the
+// rest follow in 16-byte groups.  Contact forces are summed in list order,
+// which is the search order of the build.
 
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 8)
@@ -1115,7 +1165,6 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     const int o = sc.off[c], n = sc.off[c + 1] - o;
     const int ix = c % sc.g.nx, iy = (c / sc.g.nx) % sc.g.nyr;
     const long long sidx = sc.ctrl->base + sc.i_local + 1;     // this step's index
-    uint16_t *lidx = nl.idx + (size_t)o * NBL;                   // the cell's lists, entry-major
 
     float rg = 1.0f, rdu = 0.0f, rdv = 0.0f, rdw = 0.0f;
     if (bs.ramp) {
@@ -1142,7 +1191,9 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     const long long built = nl.cstep[c];
     const float skin0 = nl.skin[c];
     bool rebuild = (sc.i_local % sc.n_t == 0) || built < 0 || sidx - built >= sc.n_t || sidx < built;
+    uint4 hn = make_uint4(0u, 0u, 0u, 0u);     // list head of this lane's next floe
     if (!rebuild) {
+        if (lane < n) hn = nl.head[o + lane];
         // the cell in floe order (angle in SV.w), and the displacement check,
         // in one pass: all of a floe's loads are independent
         const float lim = 0.25f * skin0 * skin0;
@@ -1222,16 +1273,12 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     };
 
     if (!rebuild) {
-        // ---- each floe tests its list; the first LPF entries are loaded
-        // together with the count (all in bounds: the cell's list block
-        // holds NBL entries per floe), so one memory latency covers them
+        // ---- each floe tests its list (the next floe's head is loaded while
+        // this floe's candidates are tested)
         __syncwarp();
-        constexpr int LPF = 8;
         for (int p = lane; p < n; p += 32) {
-            const int cnt = nl.cnt[o + p];
-            uint16_t jj[LPF];
-#pragma unroll
-            for (int t = 0; t < LPF; t++) jj[t] = lidx[(size_t)t * n + p];
+            const uint4 hd = hn;
+            if (p + 32 < n) hn = nl.head[o + p + 32];
             const float4 pl = sm.S4[p];
             const float4 vl = sm.SV[p];
             const uint2 ql = sm.SQ[p];
@@ -1239,7 +1286,7 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             out.yq[o + p] = ql.y + (uint32_t)__float2int_rn(dt * vl.y * isy);
             out.th[o + p] = vl.w + dt * vl.z;
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-            auto pair = [&](int j) {
+            list_walk(hd, nl.tail + (size_t)(o + p) * NLT, [&](int j) {
                 const uint2 qj = sm.SQ[j];
                 const float dx = (float)(int)(qj.x - ql.x) * sx;
                 const float dy = (float)(int)(qj.y - ql.y) * sy;
@@ -1247,11 +1294,7 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
                 const float4 vj = sm.SV[j];
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z, vj.z,
                             P, fx, fy, tq, deep);
-            };
-#pragma unroll
-            for (int t = 0; t < LPF; t++)
-                if (t < cnt) pair(jj[t]);
-            for (int t = LPF; t < cnt; t++) pair(lidx[(size_t)t * n + p]);
+            });
             finish(p, pl, vl, ql, fx, fy, tq);
         }
     } else {
@@ -1327,7 +1370,8 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             const uint2 ql = sm.SQ[p];
             const int kp = sm.orig[p];
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-            int nlst = 0;
+            ListRec rec;
+            uint16_t *tail16 = reinterpret_cast<uint16_t *>(nl.tail + (size_t)(o + kp) * NLT);
             auto touch = [&](int k) {
                 const uint2 qj = sm.SQ[k];
                 const float dx = (float)(int)(qj.x - ql.x) * sx;
@@ -1336,8 +1380,7 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
                 const float4 vj = sm.SV[k];
                 contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
                             vj.z, P, fx, fy, tq, deep);
-                if (nlst < NBL) lidx[(size_t)nlst * n + kp] = (uint16_t)sm.orig[k];
-                nlst++;
+                rec.add(tail16, sm.orig[k]);
             };
             int ncand = 0;
             short *cl = sm.clist + lane;
@@ -1407,8 +1450,8 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             }
             scan(nsmall, n, pl.x, pl.y, true, true);
             flush();
-            overflow |= nlst > NBL;
-            nl.cnt[o + kp] = (uint8_t)(nlst < NBL ? nlst : NBL);
+            overflow |= rec.nlst > NBL;
+            nl.head[o + kp] = rec.head();
             finish(kp, pl, vl, ql, fx, fy, tq);
         }
         const bool any_over = __any_sync(FULL, overflow);

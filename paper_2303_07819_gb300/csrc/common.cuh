@@ -274,14 +274,19 @@ struct Geo32 {
     float dt;
 };
 
-// Contact candidate lists of the FP32 state (variant 4): per floe up to 32
-// cell-local floe indices, stored entry-major per cell; the positions they
-// were built from; per cell the step of the build (< 0: none) and the skin.
-constexpr int NBL = 32;   // candidate list entries per floe
+// Contact candidate lists of the FP32 state (variant 4): per floe up to NBL
+// cell-local floe indices in search order.  The count and the first NLH
+// entries share one 16-byte head, so a floe's list starts with one load; the
+// rest follow in 16-byte groups of 8 entries, floe-major.  Also the positions
+// the lists were built from, and per cell the step of the build (< 0: none)
+// and the skin.
+constexpr int NLH = 7;               // entries in the head
+constexpr int NLT = 3;               // 8-entry tail groups per floe
+constexpr int NBL = NLH + 8 * NLT;   // candidate list entries per floe
 
 struct NbLists {
-    uint16_t *idx;      // [n][32]: entry t of floe k of a cell at off NBL + t n_cell + k
-    uint8_t *cnt;       // [n]
+    uint4 *head;        // [n]: 16-bit halves: count, then entries 0 .. NLH-1
+    uint4 *tail;        // [n][NLT]: entries NLH .. NBL-1, 8 per group
     uint2 *xb;          // [n] fixed-point position at the build
     long long *cstep;   // [ncell]
     float *skin;        // [ncell]
