@@ -1142,7 +1142,7 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 // which is the search order of the build.
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 8)
+__global__ void __launch_bounds__(WARPS * 32, 6)
 k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
                     int item1, int cap, int nbmax, int seg)
 {
