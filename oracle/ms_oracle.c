@@ -92,9 +92,9 @@ int orc_pair(const orc_params *p, double Px, double Py,
              double *out)
 {
     double dx = xj - xl, dy = yj - yl;
-    /* periodic minimum image */
-    dx -= Px * rint(dx / Px);
-    dy -= Py * rint(dy / Py);
+    /* periodic minimum image (none along an axis with a wall) */
+    if (Px > 0.0) dx -= Px * rint(dx / Px);
+    if (Py > 0.0) dy -= Py * rint(dy / Py);
     double d = sqrt(dx * dx + dy * dy);
     double sum_r = rl + rj;
     for (int k = 0; k < 16; k++) out[k] = 0.0;
@@ -136,6 +136,43 @@ int orc_pair(const orc_params *p, double Px, double Py,
     out[9] = ny;
     out[11] = vt;
     return 1;
+}
+
+/* Floe l against the walls X = 0 and X = Lx (Sec. 4.4), the law of
+ * orc_pair with the wall as partner: at rest, no spin, thickness >= h_l, and
+ * its boundary the straight wall line, so the overlap lens becomes the
+ * circular segment the line cuts off and its chord 2 sqrt(r^2 - d^2). */
+int orc_wall(const orc_params *p, double Lx, double xl, double ul, double vl, double wl,
+             double rl, double hl, double *out)
+{
+    for (int k = 0; k < 16; k++) out[k] = 0.0;
+    int touched = 0;
+    for (int side = 0; side < 2; side++) {
+        /* the normal n points from the floe into the wall */
+        double d = side == 0 ? xl : Lx - xl;
+        double nx = side == 0 ? -1.0 : 1.0, ny = 0.0;
+        if (!(d < rl)) continue;
+        double tx = -ny, ty = nx;
+        double delta = d - rl;
+        double chord = d > -rl ? 2.0 * sqrt(rl * rl - d * d) : 2.0 * rl;
+        double hc = hl / p->h_ref;
+        double dux = -ul, duy = -vl;              /* wall velocity minus floe velocity */
+        double vn = dux * nx + duy * ny;
+        double Fn = chord * hc * (p->E * delta + p->eta * vn);
+        if (Fn > 0.0) Fn = 0.0;
+        double vt = dux * tx + duy * ty - wl * rl;
+        double ft = chord * hc * p->G * vt;
+        double cap = p->mu * fabs(Fn);
+        if (ft > cap) ft = cap;
+        else if (ft < -cap) ft = -cap;
+        out[0] += Fn * nx + ft * tx;
+        out[1] += Fn * ny + ft * ty;
+        out[2] += rl * ft;
+        out[4] = Fn; out[5] = ft; out[6] = delta; out[7] = chord;
+        out[8] = nx; out[9] = ny; out[10] = d; out[11] = vt;
+        touched++;
+    }
+    return touched;
 }
 
 int64_t orc_contacts(const orc_params *p, double Px, double Py, int64_t n,
@@ -190,9 +227,14 @@ static void drag(const orc_params *p, const double *f, double u, double v,
 /* Lax-Friedrichs on the periodic coarse grid (Sec. 3.2).
  * reading: 2-D LF with the four-neighbour average; rho and P_omega in the
  * conservative form of Eq. (2.26a,c); rho v in the Oseen form of Eq. (3.3),
- * <v> . grad(rho v) with <v> taken at the cell itself. */
-void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
-            const double *V, const double *S, double dtau, int32_t nsub)
+ * <v> . grad(rho v) with <v> taken at the cell itself.
+ * Walls (Sec. 4.4): a neighbour beyond x = 0 or x = Lx is a ghost cell.
+ * walls = 1, zero Dirichlet as the paper states it: the ghost's fields, and so
+ * its fluxes, are zero.  walls = 2, impermeable wall: the ghost mirrors the
+ * boundary cell (rho, rho v_y, P_omega equal, rho v_x and <v_x> of opposite
+ * sign), so neither the flux nor the averaging moves mass through the wall. */
+void orc_lf_bc(int32_t nx, int32_t ny, double dx, double dy, double *q,
+               const double *V, const double *S, double dtau, int32_t nsub, int32_t walls)
 {
     int64_t nc = (int64_t)nx * ny;
     double *qn = (double *)malloc(sizeof(double) * 4 * nc);
@@ -205,15 +247,21 @@ void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
                 int64_t cW = (int64_t)j * nx + (i + nx - 1) % nx;
                 int64_t cN = (int64_t)((j + 1) % ny) * nx + i;
                 int64_t cS = (int64_t)((j + ny - 1) % ny) * nx + i;
+                int ghostE = walls && i == nx - 1, ghostW = walls && i == 0;
                 for (int f = 0; f < 4; f++) {
                     const double *g = q + f * nc;
-                    double avg = 0.25 * ((g[cE] + g[cW]) + (g[cN] + g[cS]));
+                    /* ghost value and ghost <v_x> */
+                    double sg = f == 1 ? -1.0 : 1.0;
+                    double gG = walls == 2 ? sg * g[c] : 0.0, VG = walls == 2 ? -Vx[c] : 0.0;
+                    double gE = ghostE ? gG : g[cE], gW = ghostW ? gG : g[cW];
+                    double VE = ghostE ? VG : Vx[cE], VW = ghostW ? VG : Vx[cW];
+                    double avg = 0.25 * ((gE + gW) + (g[cN] + g[cS]));
                     double val;
                     if (f == 0 || f == 3) {
-                        val = avg - dtau / (2.0 * dx) * (Vx[cE] * g[cE] - Vx[cW] * g[cW])
+                        val = avg - dtau / (2.0 * dx) * (VE * gE - VW * gW)
                                   - dtau / (2.0 * dy) * (Vy[cN] * g[cN] - Vy[cS] * g[cS]);
                     } else {
-                        val = avg - dtau * Vx[c] / (2.0 * dx) * (g[cE] - g[cW])
+                        val = avg - dtau * Vx[c] / (2.0 * dx) * (gE - gW)
                                   - dtau * Vy[c] / (2.0 * dy) * (g[cN] - g[cS]);
                     }
                     qn[f * nc + c] = val + dtau * S[f * nc + c];
@@ -222,6 +270,12 @@ void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
         memcpy(q, qn, sizeof(double) * 4 * nc);
     }
     free(qn);
+}
+
+void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
+            const double *V, const double *S, double dtau, int32_t nsub)
+{
+    orc_lf_bc(nx, ny, dx, dy, q, V, S, dtau, nsub, 0);
 }
 
 /* ------------------------------------------------------------ msDEM model */
@@ -477,7 +531,7 @@ static void model_coarse_step(orc_model *m, double dt)
     double dT = N0 * dt;
     int32_t N1 = (int32_t)ceil(dT * cmax / 0.5);
     if (N1 < 1) N1 = 1;
-    orc_lf(p->nx, p->ny, m->dx, m->dy, m->q, V, S, dT / N1, N1);
+    orc_lf_bc(p->nx, p->ny, m->dx, m->dy, m->q, V, S, dT / N1, N1, p->walls);
     /* targets of the gradual update over the next coarse step */
     for (int32_t c = 0; c < nc; c++) {
         const double *mo = m->mom + (size_t)c * ORC_NMOM;
@@ -612,6 +666,7 @@ static int truth_forces_binned(orc_truth *t)
     if (nbx > 4096) nbx = 4096;
     if (nby > 4096) nby = 4096;
     const double bx = p->Lx / (double)nbx, by = p->Ly / (double)nby;
+    const double Px = p->walls ? 0.0 : p->Lx;     /* no periodic image in x between walls */
     int64_t *start = (int64_t *)calloc((size_t)(nbx * nby + 1), sizeof(int64_t));
     int64_t *bin = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t *list = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
@@ -640,6 +695,7 @@ static int truth_forces_binned(orc_truth *t)
         int overflow = 0;
         for (int64_t dy = -1; dy <= 1; dy++)
             for (int64_t dx = -1; dx <= 1; dx++) {
+                if (p->walls && (ix + dx < 0 || ix + dx >= nbx)) continue;   /* no image across a wall */
                 const int64_t jx = (ix + dx + nbx) % nbx, jy = (iy + dy + nby) % nby;
                 const int64_t b = jy * nbx + jx;
                 for (int64_t k = start[b]; k < start[b + 1]; k++) {
@@ -654,12 +710,12 @@ static int truth_forces_binned(orc_truth *t)
         for (int64_t k = 0; k < nc; k++) {
             const int64_t j = cand[k];
             if (j < l) {
-                if (orc_pair(p, p->Lx, p->Ly,
+                if (orc_pair(p, Px, p->Ly,
                              t->x[j], t->y[j], t->u[j], t->v[j], t->w[j], t->r[j], t->h[j],
                              t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l], o)) {
                     fx -= o[0]; fy -= o[1]; tq += o[3];
                 }
-            } else if (orc_pair(p, p->Lx, p->Ly,
+            } else if (orc_pair(p, Px, p->Ly,
                                 t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l],
                                 t->x[j], t->y[j], t->u[j], t->v[j], t->w[j], t->r[j], t->h[j], o)) {
                 fx += o[0]; fy += o[1]; tq += o[2];
@@ -686,7 +742,7 @@ orc_truth *orc_truth_create(const orc_params *p, int64_t n,
     for (size_t k = 0; k < sizeof(arrs) / sizeof(arrs[0]); k++)
         *arrs[k] = (double *)calloc(n > 0 ? n : 1, sizeof(double));
     for (int64_t l = 0; l < n; l++) {
-        t->x[l] = x[l] - p->Lx * floor(x[l] / p->Lx);
+        t->x[l] = p->walls ? x[l] : x[l] - p->Lx * floor(x[l] / p->Lx);
         t->y[l] = y[l] - p->Ly * floor(y[l] / p->Ly);
         t->th[l] = theta[l]; t->u[l] = u[l]; t->v[l] = v[l]; t->w[l] = omega[l];
         t->r[l] = r[l]; t->h[l] = h[l];
@@ -704,7 +760,8 @@ void orc_truth_free(orc_truth *t)
 }
 
 /* The truth: the same DEM (Eq. 2.1) on the whole periodic domain, no
- * localisation and no coupling (Sec. 4). */
+ * localisation and no coupling (Sec. 4); with walls (Sec. 4.4) periodic in y
+ * only, and the walls' contact forces added after the floe pairs. */
 int orc_truth_step(orc_truth *t, double dt, int64_t nsteps)
 {
     const orc_params *p = &t->p;
@@ -717,15 +774,21 @@ int orc_truth_step(orc_truth *t, double dt, int64_t nsteps)
         double time = (double)t->steps * dt;
         for (int64_t l = 0; l < n; l++) { t->fx[l] = 0.0; t->fy[l] = 0.0; t->tq[l] = 0.0; }
         const int64_t npl = (!t->brute && truth_forces_binned(t)) ? 0 : n;   /* 0: forces done */
+        const double Px = p->walls ? 0.0 : p->Lx;
         for (int64_t l = 0; l < npl; l++)
             for (int64_t j = l + 1; j < n; j++) {
-                if (orc_pair(p, p->Lx, p->Ly,
+                if (orc_pair(p, Px, p->Ly,
                              t->x[l], t->y[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l],
                              t->x[j], t->y[j], t->u[j], t->v[j], t->w[j], t->r[j], t->h[j], o)) {
                     t->fx[l] += o[0]; t->fy[l] += o[1]; t->tq[l] += o[2];
                     t->fx[j] -= o[0]; t->fy[j] -= o[1]; t->tq[j] += o[3];
                 }
             }
+        if (p->walls)
+            for (int64_t l = 0; l < n; l++)
+                if (orc_wall(p, p->Lx, t->x[l], t->u[l], t->v[l], t->w[l], t->r[l], t->h[l], o)) {
+                    t->fx[l] += o[0]; t->fy[l] += o[1]; t->tq[l] += o[2];
+                }
         for (int64_t l = 0; l < n; l++) {
             double f[5], Fx, Fy, T;
             orc_forcing(p, t->x[l], t->y[l], time, f);
@@ -742,7 +805,9 @@ int orc_truth_step(orc_truth *t, double dt, int64_t nsteps)
             t->u[l] += dt * (t->fx[l] / ms);
             t->v[l] += dt * (t->fy[l] / ms);
             t->w[l] += dt * (t->tq[l] / I);
-            t->x[l] -= p->Lx * floor(t->x[l] / p->Lx);
+            if (!p->walls) t->x[l] -= p->Lx * floor(t->x[l] / p->Lx);
+            /* reading: a centre that would pass a wall stays on it */
+            else t->x[l] = fmin(fmax(t->x[l], 0.0), p->Lx);
             t->y[l] -= p->Ly * floor(t->y[l] / p->Ly);
         }
         t->steps++;

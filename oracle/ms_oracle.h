@@ -42,6 +42,13 @@ typedef struct orc_params {
      * ky_m Y + phi_m) with real wave numbers (rad per unit length) */
     int32_t n_vmodes;
     const double *vmodes;          /* [n_vmodes][5] = Au, Av, kx, ky, phi */
+    /* boundary in x (Sec. 4.4): 0 periodic; 1 or 2 rigid walls at X = 0 and
+     * X = Lx.  The truth DEM is then not periodic in x, a floe touching a wall
+     * gets the contact law of Eq. (2.2) against it (orc_wall), and a centre
+     * that would pass a wall stays on it; the coarse solve has ghost cells
+     * beyond the walls, zero (1) or mirrored (2) (orc_lf_bc); the per-cell
+     * DEMs of the multiscale model stay doubly periodic (Sec. 3.1). */
+    int32_t walls;
 } orc_params;
 
 /* ---- unit-level functions (used by the pins) ---- */
@@ -50,13 +57,26 @@ typedef struct orc_params {
 void orc_forcing(const orc_params *p, double X, double Y, double t, double *out);
 
 /* Contact of floe l with floe j under periodic minimum image with periods
- * (Px, Py).  Returns 1 if in contact.  out (16 doubles):
+ * (Px, Py); a period <= 0 means no periodic image along that axis.  Returns
+ * 1 if in contact.  out (16 doubles):
  * {Fx_l, Fy_l, T_l, T_j, F_normal, f_t, delta, chord, nx, ny, d, v_t, 0,0,0,0}
  * The force on j is -(Fx_l, Fy_l). */
 int orc_pair(const orc_params *p, double Px, double Py,
              double xl, double yl, double ul, double vl, double wl, double rl, double hl,
              double xj, double yj, double uj, double vj, double wj, double rj, double hj,
              double *out);
+
+/* Contact of floe l with the rigid walls X = 0 and X = Lx (Sec. 4.4).
+ * reading: a wall acts as a floe at rest, without spin, of unbounded radius
+ * and of at least floe l's thickness, whose edge is the wall line: the overlap
+ * is delta = d - r_l with d the distance from the centre to the wall, the
+ * chord of Eq. (2.2) is the chord the wall line cuts from the disk, the
+ * normal points from the floe into the wall.  Returns the number of walls
+ * touched (0, 1, or 2 for a floe wider than the domain).  out (16 doubles):
+ * {Fx_l, Fy_l, T_l, 0, F_normal, f_t, delta, chord, nx, ny, d, v_t, 0,0,0,0},
+ * forces summed over the walls, the other entries those of the last wall. */
+int orc_wall(const orc_params *p, double Lx, double xl, double ul, double vl, double wl,
+             double rl, double hl, double *out);
 
 /* All contacting pairs (l < j) among n floes with periods (Px, Py).
  * Writes up to max_pairs pairs into pairs[2k], pairs[2k+1]; returns count. */
@@ -69,6 +89,13 @@ int64_t orc_contacts(const orc_params *p, double Px, double Py, int64_t n,
  * in place; V = [2][ncell]; S = [4][ncell]. */
 void orc_lf(int32_t nx, int32_t ny, double dx, double dy, double *q,
             const double *V, const double *S, double dtau, int32_t nsub);
+/* The same with walls (Sec. 4.4): periodic in y only; the neighbours beyond
+ * x = 0 and x = Lx are ghost cells, holding zero with walls = 1 (zero
+ * Dirichlet on every field) or mirroring the boundary cell with walls = 2
+ * (rho, rho v_y, P_omega equal, rho v_x and <v_x> reversed: an impermeable
+ * wall).  walls = 0 is orc_lf. */
+void orc_lf_bc(int32_t nx, int32_t ny, double dx, double dy, double *q,
+               const double *V, const double *S, double dtau, int32_t nsub, int32_t walls);
 
 /* ---- multiscale model (msDEM) ---- */
 typedef struct orc_model orc_model;

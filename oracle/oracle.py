@@ -38,6 +38,7 @@ class Params(C.Structure):
         ("mu", C.c_double), ("h_ref", C.c_double), ("inertia_half", C.c_int32),
         ("couple", C.c_int32), ("N0", C.c_int32), ("n_t", C.c_int32),
         ("n_vmodes", C.c_int32), ("vmodes", C.POINTER(C.c_double)),
+        ("walls", C.c_int32),
     ]
 
 
@@ -72,6 +73,10 @@ def lib():
         L.orc_contacts.restype = C.c_int64
         L.orc_lf.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, dp, dp, dp,
                              C.c_double, C.c_int32]
+        L.orc_lf_bc.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, dp, dp, dp,
+                                C.c_double, C.c_int32, C.c_int32]
+        L.orc_wall.argtypes = [P, C.c_double] + [C.c_double] * 6 + [dp]
+        L.orc_wall.restype = C.c_int
         L.orc_model_create.argtypes = [P, C.c_int64] + [dp] * 8
         L.orc_model_create.restype = C.c_void_p
         L.orc_model_free.argtypes = [C.c_void_p]
@@ -123,6 +128,7 @@ def make_params(p: dict):
     s.couple, s.N0, s.n_t = int(p.get("couple", 0)), int(p.get("N0", 100)), int(p.get("n_t", 10))
     s.n_vmodes = vmodes.shape[0]
     s.vmodes = _dp(vmodes) if vmodes.shape[0] else C.POINTER(C.c_double)()
+    s.walls = int(p.get("walls", 0))
     return s, (modes, vmodes)
 
 
@@ -149,6 +155,15 @@ def pair(p: dict, Px: float, Py: float, fl: tuple, fj: tuple):
     return bool(hit), out
 
 
+def wall(p: dict, Lx: float, fl: tuple):
+    """Floe fl = (x, u, v, omega, r, h) against the walls X = 0 and X = Lx.
+    Returns (walls touched, out[16])."""
+    s, keep = make_params(p)
+    out = np.zeros(16)
+    hit = lib().orc_wall(C.byref(s), Lx, *[float(a) for a in fl], _dp(out))
+    return int(hit), out
+
+
 def contacts(p: dict, Px: float, Py: float, x, y, r) -> set:
     s, keep = make_params(p)
     x, y, r = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, r))
@@ -164,6 +179,14 @@ def lf(nx, ny, dx, dy, q, V, S, dtau, nsub) -> np.ndarray:
     V = np.ascontiguousarray(V, dtype=np.float64)
     S = np.ascontiguousarray(S, dtype=np.float64)
     lib().orc_lf(nx, ny, dx, dy, _dp(q), _dp(V), _dp(S), dtau, nsub)
+    return q
+
+
+def lf_bc(nx, ny, dx, dy, q, V, S, dtau, nsub, walls) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64).copy()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    lib().orc_lf_bc(nx, ny, dx, dy, _dp(q), _dp(V), _dp(S), dtau, nsub, int(walls))
     return q
 
 

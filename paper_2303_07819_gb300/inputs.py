@@ -325,6 +325,18 @@ def scenario4x(which: int, nfx: int = 480, nfy: int = 240, nx: int = 48, ny: int
     return s
 
 
+def scenario44(nfx: int = 480, nfy: int = 240, nx: int = 48, ny: int = 24) -> dict:
+    """Sec. 4.4: the floes, domain, grid, time step and initial state of Sec.
+    4.1 driven by the uniform current u_o = (0.3, 0) into rigid walls at x = 0
+    and x = 4 (periodic in y); the drag constant of Secs. 4.2-4.3 (a
+    reading, see SEC4_DRAG)."""
+    s = scenario41(nfx=nfx, nfy=nfy, nx=nx, ny=ny)
+    s["params"]["Cd"] = SEC4_DRAG
+    s["params"]["walls"] = 1
+    s["name"] = f"Sec. 4.4 floes against a wall, {nfx}x{nfy} floes, {nx}x{ny} coarse"
+    return s
+
+
 def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, rmax: float,
                       vscale: float = 0.2, wscale: float = 1e-4, overlap_ok: bool = True) -> dict:
     """n floes in one periodic square of side L with random radii, velocities
