@@ -63,6 +63,20 @@ typedef struct ms_grid {
     int32_t nx, ny;
     double Lx, Ly;
     int32_t nens;
+    /* Boundary in x: 0 periodic (above); 1 or 2 rigid walls at x = 0 and
+     * x = Lx, periodic in y (Sec. 4.4).  With walls the floes must start
+     * inside [0, Lx); the truth DEM is not periodic in x and a floe touching a
+     * wall gets the contact law of Eq. (2.2) against it (the wall taken as a
+     * floe at rest of unbounded radius and at least the floe's thickness:
+     * overlap d - r with d the centre's distance to the wall, chord
+     * 2 sqrt(r^2 - d^2)); a centre that would pass a wall stays on it.  The
+     * coarse Lax-Friedrichs step has ghost cells beyond the walls: walls = 1
+     * holds them at zero (zero Dirichlet on concentration, momentum and
+     * angular momentum, as Sec. 4.4 states it); walls = 2 mirrors the
+     * boundary cell (normal momentum and velocity reversed), an impermeable
+     * wall that keeps the coarse mass.  Each cell's own DEM stays doubly
+     * periodic (Sec. 3.1).  Any other value is MS_ERR_ARG. */
+    int32_t walls;
 } ms_grid;
 
 /* Floe state (Sec. 2.1): centre (x, y) in domain coordinates, angle theta,
@@ -126,8 +140,9 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes,
  * Sec. 3.1), running the coarse step and the gradual updates of Algorithm 1
  * when couple = 1.  The first call fixes dt; a later call with another dt
  * returns MS_ERR_ARG.  nsteps = 0 is a no-op.  Full coarse intervals replay a
- * captured CUDA graph.  MS_ERR_UNSTABLE if the state became non-finite or an
- * overlap deeper than half the smaller radius appeared. */
+ * captured CUDA graph.  MS_ERR_UNSTABLE if the state became non-finite or the
+ * coarse step needed more Lax-Friedrichs substeps than it holds; overlaps
+ * deeper than half the smaller radius are counted (ms_info entry 13). */
 int ms_step(ms_model *m, double dt, int64_t nsteps);
 
 /* As ms_step, but only enqueues the work on the model's stream and returns;

@@ -357,6 +357,7 @@ static CoarseArgs coarse_args(ms_model *m)
     a.ny = m->g.ny;
     a.nyr = m->g.nyr;
     a.nens = m->g.nens;
+    a.walls = m->g.walls;
     a.cmax = m->d_cmax;
     a.dx = m->g.Lcx;
     a.dy = m->g.Lcy;
@@ -750,6 +751,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     if (!grid || !forcing) return fail(MS_ERR_ARG, "grid or forcing is NULL");
     if (grid->nx < 1 || grid->ny < 1) return fail(MS_ERR_ARG, "grid needs nx, ny >= 1");
     if (grid->nens < 0 || grid->nens > 65536) return fail(MS_ERR_ARG, "nens must be in [0, 65536]");
+    if (grid->walls < 0 || grid->walls > 2) return fail(MS_ERR_ARG, "walls must be 0, 1 or 2");
     const int nens = grid->nens > 1 ? grid->nens : 1;
     if ((long long)grid->nx * grid->ny * nens > (1LL << 24)) return fail(MS_ERR_ARG, "more than 2^24 cells");
     if (!(grid->Lx > 0.0) || !(grid->Ly > 0.0) || !isfin(grid->Lx) || !isfin(grid->Ly))
@@ -782,6 +784,10 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
         return fail(MS_ERR_ARG, "coupling needs N0 > 0, n_t > 0 and N0 %% n_t == 0");
     int rc = validate_floes(floes, -1);
     if (rc) return rc;
+    if (grid->walls)
+        for (long long l = 0; l < floes->n; l++)
+            if (!(floes->x[l] >= 0.0 && floes->x[l] < grid->Lx))
+                return fail(MS_ERR_ARG, "floe %lld starts outside [0, Lx) between the walls", l);
 
     ms_model *m = new ms_model();
     m->precision = f.precision;
@@ -801,6 +807,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->g.Ly = grid->Ly * nens;
     m->g.Lcx = grid->Lx / grid->nx;
     m->g.Lcy = grid->Ly / grid->ny;
+    m->g.walls = grid->walls;
     m->interval = f.couple ? f.N0 : 100;
     fill_phys(m);
 

@@ -7,6 +7,11 @@
 // four-neighbour average on the periodic grid, <v> = window mean of the cell's
 // mass-weighted velocity, drag sources = window mean of the cell's total drag
 // per unit area; N1 = max(1, ceil(dT max|V|/dX / 0.5)) (Sec. 3.2).
+// Walls (Sec. 4.4): the neighbours beyond x = 0 and x = Lx are ghost cells;
+// walls = 1, zero Dirichlet as the paper states it: the ghost's fields, and so
+// its fluxes, are zero; walls = 2, impermeable: the ghost mirrors the boundary
+// cell (rho, rho v_y, P_omega equal; rho v_x and <v_x> of opposite sign), so
+// no mass crosses the wall.
 //
 // N1 is chosen on the device (it depends on the window data), so the step is
 // a fixed sequence of launches (prepare, NSUB_MAX substeps that return at once
@@ -68,16 +73,22 @@ __global__ void k_coarse_lf(CoarseArgs a, int k)
     const int cE = b + j * nx + (i + 1) % nx, cW = b + j * nx + (i + nx - 1) % nx;
     const int cN = b + ((j + 1) % ny) * nx + i, cS = b + ((j + ny - 1) % ny) * nx + i;
     const double *Vx = a.V, *Vy = a.V + nc;
+    const bool ghE = a.walls && i == nx - 1, ghW = a.walls && i == 0;
+    const bool mirror = a.walls == 2;
 #pragma unroll
     for (int f = 0; f < 4; f++) {
         const double *g = q + (size_t)f * nc;
-        const double avg = 0.25 * ((g[cE] + g[cW]) + (g[cN] + g[cS]));
+        // the ghost's field and <v_x>
+        const double gG = mirror ? (f == 1 ? -g[c] : g[c]) : 0.0, VG = mirror ? -Vx[c] : 0.0;
+        const double gE = ghE ? gG : g[cE], gW = ghW ? gG : g[cW];
+        const double VE = ghE ? VG : Vx[cE], VW = ghW ? VG : Vx[cW];
+        const double avg = 0.25 * ((gE + gW) + (g[cN] + g[cS]));
         double val;
         if (f == 0 || f == 3) {
-            val = avg - dtau / (2.0 * a.dx) * (Vx[cE] * g[cE] - Vx[cW] * g[cW])
+            val = avg - dtau / (2.0 * a.dx) * (VE * gE - VW * gW)
                       - dtau / (2.0 * a.dy) * (Vy[cN] * g[cN] - Vy[cS] * g[cS]);
         } else {
-            val = avg - dtau * Vx[c] / (2.0 * a.dx) * (g[cE] - g[cW])
+            val = avg - dtau * Vx[c] / (2.0 * a.dx) * (gE - gW)
                       - dtau * Vy[c] / (2.0 * a.dy) * (g[cN] - g[cS]);
         }
         qn[(size_t)f * nc + c] = val + dtau * a.S[(size_t)f * nc + c];

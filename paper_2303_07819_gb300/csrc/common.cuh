@@ -77,6 +77,7 @@ struct Geom {
     int nx, ny;
     double Lx, Ly, Lcx, Lcy;
     int nyr, nens;      // rows per realization, realizations
+    int walls;          // 1, 2: rigid walls at x = 0 and x = Lx (Sec. 4.4); 0: periodic in x
 };
 
 // ---------------------------------------------------------------- helpers
@@ -338,6 +339,7 @@ cudaError_t cell_step_prepare(int precision, const CellLaunch &cl, size_t smem);
 struct CoarseArgs {
     int nx, ny;         // ny: rows of all realizations
     int nyr, nens;      // rows per realization, realizations
+    int walls;          // ghost cells beyond x = 0 and x = Lx (Sec. 4.4): 1 zero, 2 mirrored
     unsigned long long *cmax;   // [nens] max over the realization's cells of |V|/dx (non-negative double bits)
     double dx, dy, Ac, dT;
     int N0;

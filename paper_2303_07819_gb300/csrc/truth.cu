@@ -133,6 +133,39 @@ __global__ void k_bin64(const double *x, const double *y, double Lx, double Ly, 
 }
 
 // ------------------------------------------------------------ truth steps
+// Floe l against the rigid walls x = 0 and x = Lx (Sec. 4.4): the contact law
+// of Eq. (2.2) with the wall as the partner, a floe at rest without spin, of
+// unbounded radius and at least floe l's thickness.  Its edge is the wall
+// line, so the overlap is delta = d - r_l (d: the centre's distance to the
+// wall, dl and dr below), the lens becomes the segment the line cuts off with
+// chord 2 sqrt(r_l^2 - d^2), and the normal n = (-1, 0) or (1, 0) points into
+// the wall; the tangent t = (0, n_x).  Adds the force on l.
+template <class R>
+__device__ __forceinline__ void wall_add(R dl, R dr, R ul, R vl, R wl, R rl, R hl, const Phys<R> &P, R &fx,
+                                         R &fy, R &tq, unsigned &deep)
+{
+#pragma unroll
+    for (int side = 0; side < 2; side++) {
+        const R d = side == 0 ? dl : dr;
+        if (!(d < rl)) continue;
+        const R nx = side == 0 ? R(-1) : R(1);
+        const R delta = d - rl;
+        const R c = d > -rl ? R(2) * sqrt(rl * rl - d * d) : R(2) * rl;
+        const R hc = hl * P.inv_h_ref;
+        const R vn = -ul * nx;                 // (wall - floe) velocity along n
+        R Fn = c * hc * (P.E * delta + P.eta * vn);
+        Fn = dmin(Fn, R(0));
+        const R vt = -vl * nx - wl * rl;       // along t, minus the floe's rim speed
+        R ft = c * hc * P.G * vt;
+        const R cap = P.mu * (-Fn);
+        ft = dmax(dmin(ft, cap), -cap);
+        fx += Fn * nx;
+        fy += ft * nx;
+        tq += rl * ft;
+        deep |= (delta < R(-0.5) * rl) ? 1u : 0u;
+    }
+}
+
 // Neighbour bins of (bx, by): 3 x 3 with periodic wrap, or the bin alone
 // along an axis that has fewer than 3 bins (then it holds the whole axis).
 struct NbRange {
@@ -165,16 +198,22 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
     const int b = bin[l];
     const int bx = b % nbx, by = b / nbx;
     const NbRange nr = nb_range(nbx, nby);
+    const bool walls = a.g.walls != 0;
     float fx = 0.0f, fy = 0.0f, tq = 0.0f;
     unsigned deep = 0;
     for (int oy = nr.y0; oy <= nr.y1; oy++) {
         const int cy = (by + oy + nby) % nby;
         for (int ox = nr.x0; ox <= nr.x1; ox++) {
+            if (walls && (bx + ox < 0 || bx + ox >= nbx)) continue;   // no image across a wall
             const int cb = cy * nbx + (bx + ox + nbx) % nbx;
             for (int k = start[cb]; k < start[cb + 1]; k++) {
                 const int j = sorted[k];
                 if (j == l) continue;
-                const float dx = (float)(int)(in.xq[j] - xl) * sx;
+                // between walls the plain difference (partners up to two bins
+                // away may be more than half the domain apart), else the
+                // periodic minimum image of the 32-bit fixed point
+                const float dx = walls ? (float)((long long)in.xq[j] - (long long)xl) * sx
+                                       : (float)(int)(in.xq[j] - xl) * sx;
                 const float dy = (float)(int)(in.yq[j] - yl) * sy;
                 const float d2 = dx * dx + dy * dy;
                 const float rj = in.r[j];
@@ -197,13 +236,26 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
         vo += P.mAv[m] * c;
         zeta -= P.mAz[m] * s;
     }
+    if (walls) {
+        // distances to the walls from the fixed point: exact integers, one rounding
+        const float dl = (float)xl * sx, dr = (float)(4294967296ll - (long long)xl) * sx;
+        wall_add(dl, dr, ul, vl, wl, rl, hl, P, fx, fy, tq, deep);
+    }
     float Fdx, Fdy, Td;
     drag_force(P, uo, vo, zeta, wind[0], wind[1], ul, vl, wl, rl, Fdx, Fdy, Td);
     fx += Fdx; fy += Fdy; tq += Td;
     const float dt = a.k.dt;
     const float m = P.mass_c * rl * rl * hl;
     const float I = P.inertia_f * m * rl * rl;
-    out.xq[l] = xl + (uint32_t)__float2int_rn(dt * ul * isx);
+    if (walls) {
+        // reading: a centre that would pass a wall stays on it (in a stable run
+        // the wall's contact force stops the floe long before)
+        long long xn = (long long)xl + __float2int_rn(dt * ul * isx);
+        xn = xn < 0 ? 0 : (xn > 4294967295ll ? 4294967295ll : xn);
+        out.xq[l] = (uint32_t)xn;
+    } else {
+        out.xq[l] = xl + (uint32_t)__float2int_rn(dt * ul * isx);
+    }
     out.yq[l] = yl + (uint32_t)__float2int_rn(dt * vl * isy);
     out.th[l] = in.th[l] + dt * wl;
     const float un = ul + dt * (fx / m), vn = vl + dt * (fy / m), wn = wl + dt * (tq / I);
@@ -229,17 +281,19 @@ __global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthAr
     const int b = bin[l];
     const int bx = b % nbx, by = b / nbx;
     const NbRange nr = nb_range(nbx, nby);
+    const bool walls = a.g.walls != 0;
     double fx = 0.0, fy = 0.0, tq = 0.0;
     unsigned deep = 0;
     for (int oy = nr.y0; oy <= nr.y1; oy++) {
         const int cy = (by + oy + nby) % nby;
         for (int ox = nr.x0; ox <= nr.x1; ox++) {
+            if (walls && (bx + ox < 0 || bx + ox >= nbx)) continue;   // no image across a wall
             const int cb = cy * nbx + (bx + ox + nbx) % nbx;
             for (int k = start[cb]; k < start[cb + 1]; k++) {
                 const int j = sorted[k];
                 if (j == l) continue;
                 double dx = in.x[j] - xl, dy = in.y[j] - yl;
-                dx -= Lx * rint(dx / Lx);
+                if (!walls) dx -= Lx * rint(dx / Lx);
                 dy -= Ly * rint(dy / Ly);
                 const double d2 = dx * dx + dy * dy;
                 contact_add(dx, dy, d2, rl, in.r[j], hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
@@ -251,6 +305,7 @@ __global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthAr
     ocean_f64(P, xl, yl, uo, vo, zeta);
     double ua, va;
     wind_at(P, (double)a.step * a.dt, ua, va);
+    if (walls) wall_add(xl, Lx - xl, ul, vl, wl, rl, hl, P, fx, fy, tq, deep);
     double Fdx, Fdy, Td;
     drag_force(P, uo, vo, zeta, ua, va, ul, vl, wl, rl, Fdx, Fdy, Td);
     fx += Fdx; fy += Fdy; tq += Td;
@@ -258,7 +313,8 @@ __global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthAr
     const double m = P.mass_c * rl * rl * hl;
     const double I = P.inertia_f * m * rl * rl;
     double xn = xl + dt * ul, yn = yl + dt * vl;
-    xn -= Lx * floor(xn / Lx);
+    if (!walls) xn -= Lx * floor(xn / Lx);
+    else xn = fmin(fmax(xn, 0.0), Lx);   // reading: a centre that would pass a wall stays on it
     yn -= Ly * floor(yn / Ly);
     out.x[l] = xn;
     out.y[l] = yn;

@@ -27,7 +27,7 @@ _dp = C.POINTER(C.c_double)
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("Lx", C.c_double), ("Ly", C.c_double),
-                ("nens", C.c_int32)]
+                ("nens", C.c_int32), ("walls", C.c_int32)]
 
 
 class Floes(C.Structure):
@@ -151,7 +151,8 @@ class Model:
         self.params = dict(params)
         self.precision = precision
         nens = max(1, int(params.get("nens", 1)))
-        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]), nens)
+        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]), nens,
+                 int(params.get("walls", 0)))
         fl, keep1 = make_floes(floes)
         fc, keep2 = make_forcing(params, precision)
         h = C.c_void_p()
