@@ -500,6 +500,7 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             const float lim = 0.25f * sc.nl.skin[c] * sc.nl.skin[c];
             const bool r0 = (sc.i_local % sc.n_t == 0) || built < 0 || sstep - built >= sc.n_t || sstep < built;
             if (!r0 && (int)threadIdx.x < n) hn = sc.nl.head[o + threadIdx.x];
+            block_cell_ramp(bs, sc, c);      // read after the barrier below
             bool far = false;
             float vmax = 0.0f;
             for (int k = threadIdx.x; k < n; k += T) {
@@ -554,29 +555,8 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 sm.bin[k] = b;
             }
         }
+        if (!(LISTS && !rebuild)) {
         __syncthreads();
-        if (LISTS && !rebuild) {
-            // ---- contacts from the lists (the next floe's head is loaded
-            // while this floe's candidates are tested)
-            for (int l = threadIdx.x; l < n; l += T) {
-                const uint4 hd = hn;
-                if (l + T < n) hn = sc.nl.head[o + l + T];
-                const float4 pl = sm.P4[l];
-                const float4 vl = sm.V4[l];
-                const uint2 ql = sm.Q[l];
-                float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-                list_walk(hd, sc.nl.tail + (size_t)(o + l) * NLT, [&](int j) {
-                    const uint2 qj = sm.Q[j];
-                    const float dx = (float)(int)(qj.x - ql.x) * sx;
-                    const float dy = (float)(int)(qj.y - ql.y) * sy;
-                    const float4 pj = sm.P4[j];
-                    const float4 vj = sm.V4[j];
-                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
-                                vj.z, P, fx, fy, tq, deep);
-                });
-                sm.F4[l] = make_float4(fx, fy, tq, 0.0f);
-            }
-        } else {
         const int nsmall = block_scan_excl<T>(sm.cnt, sm.bst, nbins + 1, sm.tmp);
         for (int b = threadIdx.x; b <= nbins; b += T) sm.cnt[b] = 0;
         __syncthreads();
@@ -710,10 +690,13 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             }
         }
         }
-        block_cell_ramp(bs, sc, c);
-        __syncthreads();
+        if (!LISTS) block_cell_ramp(bs, sc, c);
+        if (!(LISTS && !rebuild)) __syncthreads();   // the search's forces come from other threads
 
-        // ---- drag, forward Euler, gradual update, moments (index order: coalesced I/O)
+        // ---- contact forces from the lists (each thread its own floes: no
+        // barrier; the next floe's head is loaded while this floe's candidates
+        // are tested) or from the search above; then drag, forward Euler,
+        // gradual update, moments (index order: coalesced I/O)
         float acc[NMOM];
 #pragma unroll
         for (int k = 0; k < NMOM; k++) acc[k] = 0.0f;
@@ -721,8 +704,23 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             const float4 pl = sm.P4[l];
             const float4 vl = sm.V4[l];
             const uint2 ql = sm.Q[l];
-            const float4 f4 = sm.F4[l];
-            float fx = f4.x, fy = f4.y, tq = f4.z;
+            float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+            if (LISTS && !rebuild) {
+                const uint4 hd = hn;
+                if (l + T < n) hn = sc.nl.head[o + l + T];
+                list_walk(hd, sc.nl.tail + (size_t)(o + l) * NLT, [&](int j) {
+                    const uint2 qj = sm.Q[j];
+                    const float dx = (float)(int)(qj.x - ql.x) * sx;
+                    const float dy = (float)(int)(qj.y - ql.y) * sy;
+                    const float4 pj = sm.P4[j];
+                    const float4 vj = sm.V4[j];
+                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
+                                vj.z, P, fx, fy, tq, deep);
+                });
+            } else {
+                const float4 f4 = sm.F4[l];
+                fx = f4.x; fy = f4.y; tq = f4.z;
+            }
             const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
             float uo, vo, zeta;
             ocean_f32(P, sm.base, inx, iny, xf, yf, uo, vo, zeta);
