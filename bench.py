@@ -383,6 +383,16 @@ def main():
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
     kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
     achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
+    # the FP32 side of the roofline: the FMA rate this GPU reaches (probe),
+    # the FMA-pipe activity ncu measured on the cell kernels, and the issue
+    # rate the live step implies for ncu's instruction count (of the peak
+    # 4 warp instructions per SM per cycle at the sampled clock)
+    fp32_peak = msdem.probe_fp32(5)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    issue_frac = None
+    if prof is not None and traffic is not None and clk.get("sm_mhz"):
+        wi = float(prof["warp_instructions_per_fine_step"])
+        issue_frac = wi / (kern_ms_live / 1e3) / (nsm * 4 * clk["sm_mhz"] * 1e6)
 
     line = {
         "metric": "floe-steps/s", "value": value, "unit": "floe-steps/s", "n_gpus": world,
@@ -394,7 +404,10 @@ def main():
                      "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "msd::k_cell_step32", "peak_source": peak_kind,
                      "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
-                     "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso},
+                     "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso,
+                     "fp32_peak_tflops_probe": fp32_peak,
+                     "fp32_pipe_frac_ncu": (float(prof["fp32_pipe_frac"]) if traffic is not None else None),
+                     "issue_frac": issue_frac},
         "clocks": clk,
         "gpu_launches": args.steps * (info["launches_per_interval"] + info["launches_per_coarse"]),
         "launch": {"variant": info["variant"], "threads": info["threads"], "persistent": info["persistent"]},

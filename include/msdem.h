@@ -342,6 +342,14 @@ int ms_closure_stats(ms_model *m, int64_t *out);
 /* Release the model's device memory, graphs, events and stream. */
 void ms_free(ms_model *m);
 
+/* FP32 FMA throughput of the current device in TFLOP/s (host *tflops; an FMA
+ * counts as 2 flops): `reps` timed launches (>= 1) of a kernel whose every
+ * thread runs 8 independent FMA chains on all SMs, after one warm-up launch,
+ * on a stream of its own (about 2 ms per launch on a GB300).  The
+ * denominator of the FP32-pipe fraction of the cell step.  MS_ERR_ARG for
+ * reps < 1 or a NULL pointer; MS_ERR_CUDA if a CUDA call fails. */
+int ms_probe_fp32(int32_t reps, double *tflops);
+
 /* Message of the calling thread's last failed call ("" if none). */
 const char *ms_last_error(void);
 

@@ -728,6 +728,14 @@ extern "C" {
 
 const char *ms_last_error(void) { return g_err.c_str(); }
 
+int ms_probe_fp32(int32_t reps, double *tflops)
+{
+    if (reps < 1 || !tflops) return fail(MS_ERR_ARG, "probe needs reps >= 1 and an output");
+    const cudaError_t e = fma_probe(reps, tflops);
+    if (e != cudaSuccess) return fail(MS_ERR_CUDA, "FP32 probe: %s", cudaGetErrorString(e));
+    return MS_OK;
+}
+
 void ms_free(ms_model *m)
 {
     if (!m) return;

@@ -57,7 +57,8 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_truth_step", "ms_truth_moments", "ms_truth_get_floes", "ms_set_stream", "ms_autotune",
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
-           "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats"]
+           "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
+           "ms_probe_fp32"]
 
 
 def lib_path() -> str:
@@ -97,6 +98,7 @@ def load(path: str | None = None):
     L.ms_closure_attach.argtypes = [vp, vp, C.c_int32, C.c_double, C.POINTER(C.c_float)]
     L.ms_closure_collect.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.ms_closure_stats.argtypes = [vp, C.POINTER(C.c_int64)]
+    L.ms_probe_fp32.argtypes = [C.c_int32, _dp]
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
@@ -289,6 +291,13 @@ MLP_SHAPES = [("W1", (128, NFEAT)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (
               ("W3", (128, 128)), ("b3", (128,)), ("W4", (4, 128)), ("b4", (4,))]
 NPARAM = sum(int(np.prod(shp)) for _, shp in MLP_SHAPES)
 _fp = C.POINTER(C.c_float)
+
+
+def probe_fp32(reps: int = 5) -> float:
+    """FP32 FMA throughput of the current GPU in TFLOP/s (ms_probe_fp32)."""
+    out = np.zeros(1)
+    _check(load().ms_probe_fp32(int(reps), _ptr(out)))
+    return float(out[0])
 
 
 def pack_params(p: dict) -> np.ndarray:

@@ -391,3 +391,14 @@ def test_fp32_variants_agree_one_step(ms):
     for r in res[1:]:
         e = rel_errors(r, res[0], s["params"], 1e-6)
         assert e.max() < 1e-6, report(e)
+
+
+def test_fp32_probe(ms):
+    """The FMA probe (the FP32-pipe roofline's denominator) reports a rate
+    between 30 and 100 TFLOP/s on a GB300 (nominal 152 SMs x 128 lanes x 2
+    flops x 2.07 GHz = 80.6); reps < 1 is an argument error."""
+    t = ms.probe_fp32(3)
+    assert 30.0 < t < 100.0, t
+    with pytest.raises(ms.MsError) as e:
+        ms.probe_fp32(0)
+    assert e.value.code == -1
