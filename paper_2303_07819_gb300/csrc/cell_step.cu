@@ -431,27 +431,42 @@ struct ListRec {
     }
 };
 
-// Calls pair(j) for the entries of a floe's list in order, from one call
-// site (every candidate gets the same compiled arithmetic).  The next tail
-// group is loaded one group ahead of its use.
-template <class PairF>
-__device__ __forceinline__ void list_walk(const uint4 hd, const uint4 *tl, PairF &&pair)
+// Calls pair(load(j)) for the entries j of a floe's list in order, from one
+// call site (every candidate gets the same compiled arithmetic).  The next
+// entry's partner is loaded before the current pair is computed, and the
+// next tail group one group ahead of its use.
+template <class LoadF, class PairF>
+__device__ __forceinline__ void list_walk(const uint4 hd, const uint4 *tl, LoadF &&load, PairF &&pair)
 {
     const int cnt = (int)(hd.x & 0xffffu);
+    if (cnt == 0) return;
     uint4 g = hd, nx = make_uint4(0u, 0u, 0u, 0u);
     if (cnt > NLH) nx = tl[0];
-    int h = 1, gi = 1;
+    int h = 2, gi = 1;   // half of the next entry to load (entry 0 is half 1 of the head)
+    auto cur = load(list_half(g, 1));
     for (int t = 0; t < cnt; t++) {
-        if (h == 8) {
-            g = nx;
-            h = 0;
-            if (NLH + 8 * gi < cnt) nx = tl[gi];
-            gi++;
+        auto nxt = cur;
+        if (t + 1 < cnt) {
+            if (h == 8) {
+                g = nx;
+                h = 0;
+                if (NLH + 8 * gi < cnt) nx = tl[gi];
+                gi++;
+            }
+            nxt = load(list_half(g, h));
+            h++;
         }
-        pair(list_half(g, h));
-        h++;
+        pair(cur);
+        cur = nxt;
     }
 }
+
+// a list entry's partner as staged in shared memory
+struct Partner {
+    uint2 q;     // fixed-point position
+    float4 p;    // x, y, r, h
+    float4 v;    // u, v, w, (theta)
+};
 
 // LISTS: variant 4's candidate lists (see k_cell_step32_wlist) kept across
 // steps; a cell rebuilds them with this kernel's binned search, widened by
@@ -708,15 +723,15 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
             if (LISTS && !rebuild) {
                 const uint4 hd = hn;
                 if (l + T < n) hn = sc.nl.head[o + l + T];
-                list_walk(hd, sc.nl.tail + (size_t)(o + l) * NLT, [&](int j) {
-                    const uint2 qj = sm.Q[j];
-                    const float dx = (float)(int)(qj.x - ql.x) * sx;
-                    const float dy = (float)(int)(qj.y - ql.y) * sy;
-                    const float4 pj = sm.P4[j];
-                    const float4 vj = sm.V4[j];
-                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
-                                vj.z, P, fx, fy, tq, deep);
-                });
+                list_walk(
+                    hd, sc.nl.tail + (size_t)(o + l) * NLT,
+                    [&](int j) { return Partner{sm.Q[j], sm.P4[j], sm.V4[j]}; },
+                    [&](const Partner &b) {
+                        const float dx = (float)(int)(b.q.x - ql.x) * sx;
+                        const float dy = (float)(int)(b.q.y - ql.y) * sy;
+                        contact_add(dx, dy, dx * dx + dy * dy, pl.z, b.p.z, pl.w, b.p.w, b.v.x - vl.x, b.v.y - vl.y,
+                                    vl.z, b.v.z, P, fx, fy, tq, deep);
+                    });
             } else {
                 const float4 f4 = sm.F4[l];
                 fx = f4.x; fy = f4.y; tq = f4.z;
@@ -1284,15 +1299,14 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             out.yq[o + p] = ql.y + (uint32_t)__float2int_rn(dt * vl.y * isy);
             out.th[o + p] = vl.w + dt * vl.z;
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
-            list_walk(hd, nl.tail + (size_t)(o + p) * NLT, [&](int j) {
-                const uint2 qj = sm.SQ[j];
-                const float dx = (float)(int)(qj.x - ql.x) * sx;
-                const float dy = (float)(int)(qj.y - ql.y) * sy;
-                const float4 pj = sm.S4[j];
-                const float4 vj = sm.SV[j];
-                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z, vj.z,
-                            P, fx, fy, tq, deep);
-            });
+            list_walk(
+                hd, nl.tail + (size_t)(o + p) * NLT, [&](int j) { return Partner{sm.SQ[j], sm.S4[j], sm.SV[j]}; },
+                [&](const Partner &b) {
+                    const float dx = (float)(int)(b.q.x - ql.x) * sx;
+                    const float dy = (float)(int)(b.q.y - ql.y) * sy;
+                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, b.p.z, pl.w, b.p.w, b.v.x - vl.x, b.v.y - vl.y, vl.z,
+                                b.v.z, P, fx, fy, tq, deep);
+                });
             finish(p, pl, vl, ql, fx, fy, tq);
         }
     } else {
