@@ -869,8 +869,16 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
+    // the two block-per-cell classes (the largest cells: few blocks, each
+    // holding much shared memory, and the longest launches) get the highest
+    // stream priority, so their blocks take SMs first as the warp classes'
+    // blocks drain (measured: 2.7 % less per interval than equal priorities;
+    // graded priorities over all classes were slower)
+    int p_least = 0, p_great = 0;
+    CKM(cudaDeviceGetStreamPriorityRange(&p_least, &p_great));
     for (int k = 0; k < MAXSEG; k++) {
-        CKM(cudaStreamCreateWithFlags(&m->side_stream[k], cudaStreamNonBlocking));
+        const int pr = k < 2 ? p_great : p_least;
+        CKM(cudaStreamCreateWithPriority(&m->side_stream[k], cudaStreamNonBlocking, pr));
         CKM(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
     }
     CKM(cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming));
