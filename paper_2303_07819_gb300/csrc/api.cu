@@ -869,11 +869,12 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
-    // the two block-per-cell classes (the largest cells: few blocks, each
-    // holding much shared memory, and the longest launches) get the highest
-    // stream priority, so their blocks take SMs first as the warp classes'
-    // blocks drain (measured: 2.7 % less per interval than equal priorities;
-    // graded priorities over all classes were slower)
+    // the streams of the first two size classes (the largest cells, a block
+    // per cell when there are cells above 256 floes: few blocks, each holding
+    // much shared memory, and the longest launches) get the highest stream
+    // priority, so their blocks take SMs first as the other classes' blocks
+    // drain (measured on the 128 x 128 batched workload: 2.7 % less per
+    // interval than equal priorities; graded priorities were slower)
     int p_least = 0, p_great = 0;
     CKM(cudaDeviceGetStreamPriorityRange(&p_least, &p_great));
     for (int k = 0; k < MAXSEG; k++) {
