@@ -1154,6 +1154,49 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 // rest follow in 16-byte groups.  Contact forces are summed in list order,
 // which is the search order of the build.
 
+// Shared memory per warp: 30 B per floe (the search and the lists need the
+// fixed-point position for the periodic minimum image, radius, thickness,
+// velocity and spin; the angle goes from global memory to global memory).
+__host__ __device__ inline size_t list_region_bytes(int cap, int nbmax)
+{
+    auto a16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    return a16(sizeof(float4) * cap) + a16(sizeof(uint2) * cap) + a16(sizeof(float) * cap) +
+           a16(sizeof(short) * cap) + a16(sizeof(short) * MAXC * 32) + 2 * a16(sizeof(int) * (nbmax * nbmax + 1)) +
+           a16(sizeof(float2) * MAXM);
+}
+
+struct ListSm {
+    float4 *P4;    // r, h, u, v
+    uint2 *SQ;     // exact fixed-point position
+    float *W;      // spin
+    short *orig;   // floe slot in the cell (search order -> slot)
+    short *clist;  // [MAXC][32] contact candidates per lane
+    int *cnt, *bst;
+    float2 *Cm;    // per mode: (cos, sin) of the cell's phase, or (phase, -)
+};
+
+__device__ __forceinline__ ListSm carve_list(unsigned char *p, int cap, int nbmax)
+{
+    ListSm w;
+    size_t o = 0;
+    w.P4 = reinterpret_cast<float4 *>(p + o); o += align16(sizeof(float4) * cap);
+    w.SQ = reinterpret_cast<uint2 *>(p + o); o += align16(sizeof(uint2) * cap);
+    w.W = reinterpret_cast<float *>(p + o); o += align16(sizeof(float) * cap);
+    w.orig = reinterpret_cast<short *>(p + o); o += align16(sizeof(short) * cap);
+    w.clist = reinterpret_cast<short *>(p + o); o += align16(sizeof(short) * MAXC * 32);
+    w.cnt = reinterpret_cast<int *>(p + o); o += align16(sizeof(int) * (nbmax * nbmax + 1));
+    w.bst = reinterpret_cast<int *>(p + o); o += align16(sizeof(int) * (nbmax * nbmax + 1));
+    w.Cm = reinterpret_cast<float2 *>(p + o);
+    return w;
+}
+
+// a list entry's partner as the warp list kernel stages it
+struct PartnerW {
+    uint2 q;     // fixed-point position
+    float4 p;    // r, h, u, v
+    float w;     // spin
+};
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 6)
 k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, float beta, int item0,
@@ -1167,12 +1210,12 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     const int item = item0 + blockIdx.x * WARPS + warp;
     if (sc.live) item1 = min(item1, item0 + sc.live[seg]);
     if (item >= item1) return;
-    const WarpSm sm = carve_warp(smem + warp * warp_region_bytes(cap, nbmax), cap, nbmax);
+    const ListSm sm = carve_list(smem + warp * list_region_bytes(cap, nbmax), cap, nbmax);
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
 
     const float dt = sc.k.dt;
-    const float Lx = sc.k.Lx, Ly = sc.k.Ly, iLx = sc.k.iLx, iLy = sc.k.iLy;
+    const float Lx = sc.k.Lx, Ly = sc.k.Ly;
     const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy, inx = sc.k.inx, iny = sc.k.iny;
     const int c = sc.order[item];
     const int o = sc.off[c], n = sc.off[c + 1] - o;
@@ -1207,19 +1250,18 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     uint4 hn = make_uint4(0u, 0u, 0u, 0u);     // list head of this lane's next floe
     if (!rebuild) {
         if (lane < n) hn = nl.head[o + lane];
-        // the cell in floe order (angle in SV.w), and the displacement check,
-        // in one pass: all of a floe's loads are independent
+        // the cell in floe order, and the displacement check, in one pass:
+        // all of a floe's loads are independent
         const float lim = 0.25f * skin0 * skin0;
         bool far = false;
         for (int k = lane; k < n; k += 32) {
             const uint2 b = nl.xb[o + k];
             const uint32_t xq = in.xq[o + k], yq = in.yq[o + k];
             const float r = in.r[o + k], h = in.h[o + k], u = in.u[o + k], v = in.v[o + k], w = in.w[o + k];
-            const float th = in.th[o + k];
             const float dx = (float)(int)(xq - b.x) * sx, dy = (float)(int)(yq - b.y) * sy;
             far |= dx * dx + dy * dy > lim;
-            sm.S4[k] = make_float4((float)xq * sx, (float)yq * sy, r, h);
-            sm.SV[k] = make_float4(u, v, w, th);
+            sm.P4[k] = make_float4(r, h, u, v);
+            sm.W[k] = w;
             sm.SQ[k] = make_uint2(xq, yq);
         }
         rebuild = __any_sync(FULL, far);
@@ -1232,7 +1274,7 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
     bool bad = false;
     // drag, forward Euler, gradual update and moments of floe k (stored slot)
     // given its contact force; shared by both paths
-    auto finish = [&](int k, const float4 &pl, const float4 &vl, const uint2 &ql, float fx, float fy, float tq) {
+    auto finish = [&](int k, const uint2 &ql, const float4 &pl, float wl, float fx, float fy, float tq) {
         const float xf = (float)ql.x * INV2_32F, yf = (float)ql.y * INV2_32F;
         float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
         if (P.taylor) {
@@ -1256,14 +1298,14 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             }
         }
         float Fdx, Fdy, Td;
-        drag_force(P, uo, vo, zeta, bs.ua, bs.va, vl.x, vl.y, vl.z, pl.z, Fdx, Fdy, Td);
+        drag_force(P, uo, vo, zeta, bs.ua, bs.va, pl.z, pl.w, wl, pl.x, Fdx, Fdy, Td);
         fx += Fdx; fy += Fdy; tq += Td;
-        const float r = pl.z, h = pl.w;
+        const float r = pl.x, h = pl.y;
         const float mass = P.mass_c * r * r * h;
         const float I = P.inertia_f * mass * r * r;
-        float un = vl.x + dt * (fx / mass);
-        float vn = vl.y + dt * (fy / mass);
-        float wn = vl.z + dt * (tq / I);
+        float un = pl.z + dt * (fx / mass);
+        float vn = pl.w + dt * (fy / mass);
+        float wn = wl + dt * (tq / I);
         float rn = r;
         if (bs.ramp) {
             rn = r * rg;
@@ -1292,22 +1334,22 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
         for (int p = lane; p < n; p += 32) {
             const uint4 hd = hn;
             if (p + 32 < n) hn = nl.head[o + p + 32];
-            const float4 pl = sm.S4[p];
-            const float4 vl = sm.SV[p];
+            const float4 pl = sm.P4[p];
+            const float wl = sm.W[p];
             const uint2 ql = sm.SQ[p];
-            out.xq[o + p] = ql.x + (uint32_t)__float2int_rn(dt * vl.x * isx);
-            out.yq[o + p] = ql.y + (uint32_t)__float2int_rn(dt * vl.y * isy);
-            out.th[o + p] = vl.w + dt * vl.z;
+            out.xq[o + p] = ql.x + (uint32_t)__float2int_rn(dt * pl.z * isx);
+            out.yq[o + p] = ql.y + (uint32_t)__float2int_rn(dt * pl.w * isy);
+            out.th[o + p] = in.th[o + p] + dt * wl;
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
             list_walk(
-                hd, nl.tail + (size_t)(o + p) * NLT, [&](int j) { return Partner{sm.SQ[j], sm.S4[j], sm.SV[j]}; },
-                [&](const Partner &b) {
+                hd, nl.tail + (size_t)(o + p) * NLT, [&](int j) { return PartnerW{sm.SQ[j], sm.P4[j], sm.W[j]}; },
+                [&](const PartnerW &b) {
                     const float dx = (float)(int)(b.q.x - ql.x) * sx;
                     const float dy = (float)(int)(b.q.y - ql.y) * sy;
-                    contact_add(dx, dy, dx * dx + dy * dy, pl.z, b.p.z, pl.w, b.p.w, b.v.x - vl.x, b.v.y - vl.y, vl.z,
-                                b.v.z, P, fx, fy, tq, deep);
+                    contact_add(dx, dy, dx * dx + dy * dy, pl.x, b.p.x, pl.y, b.p.y, b.p.z - pl.z, b.p.w - pl.w, wl,
+                                b.w, P, fx, fy, tq, deep);
                 });
-            finish(p, pl, vl, ql, fx, fy, tq);
+            finish(p, ql, pl, wl, fx, fy, tq);
         }
     } else {
         // ---- rebuild: the binned search of k_cell_step32_warp with the reach
@@ -1361,8 +1403,8 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             if (small) pos = sm.bst[b] + sm.cnt[b] + __popc(m & lt);
             else if (large) pos = lrun + __popc(bl & lt);
             if (valid) {
-                sm.S4[pos] = make_float4((float)xq * sx, (float)yq * sy, r, h);
-                sm.SV[pos] = make_float4(u, v, w, 0.0f);
+                sm.P4[pos] = make_float4(r, h, u, v);
+                sm.W[pos] = w;
                 sm.SQ[pos] = make_uint2(xq, yq);
                 sm.orig[pos] = (short)k;
                 out.xq[o + k] = xq + (uint32_t)__float2int_rn(dt * u * isx);
@@ -1377,8 +1419,8 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
         }
         bool overflow = false;
         for (int p = lane; p < n; p += 32) {
-            const float4 pl = sm.S4[p];
-            const float4 vl = sm.SV[p];
+            const float4 pl = sm.P4[p];
+            const float wl = sm.W[p];
             const uint2 ql = sm.SQ[p];
             const int kp = sm.orig[p];
             float fx = 0.0f, fy = 0.0f, tq = 0.0f;
@@ -1388,10 +1430,9 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
                 const uint2 qj = sm.SQ[k];
                 const float dx = (float)(int)(qj.x - ql.x) * sx;
                 const float dy = (float)(int)(qj.y - ql.y) * sy;
-                const float4 pj = sm.S4[k];
-                const float4 vj = sm.SV[k];
-                contact_add(dx, dy, dx * dx + dy * dy, pl.z, pj.z, pl.w, pj.w, vj.x - vl.x, vj.y - vl.y, vl.z,
-                            vj.z, P, fx, fy, tq, deep);
+                const float4 pj = sm.P4[k];
+                contact_add(dx, dy, dx * dx + dy * dy, pl.x, pj.x, pl.y, pj.y, pj.z - pl.z, pj.w - pl.w, wl,
+                            sm.W[k], P, fx, fy, tq, deep);
                 rec.add(tail16, sm.orig[k]);
             };
             int ncand = 0;
@@ -1405,66 +1446,58 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
                 cl[32 * ncand] = (short)k;
                 ncand++;
             };
-            auto scan = [&](int k0, int k1, float xs, float ys, bool mix, bool miy) {
-                for (int k = k0; k < k1; k++) {
-                    const float4 q = sm.S4[k];
-                    float dx = q.x - xs, dy = q.y - ys;
-                    if (mix) dx = min_image(dx, Lx, iLx);
-                    if (miy) dy = min_image(dy, Ly, iLy);
-                    const float S = pl.z + q.z + skin;
-                    if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
-                }
+            // candidate test: the 32-bit fixed-point difference is the
+            // periodic minimum image in the cell, whichever bin k came from
+            auto test = [&](int k) {
+                const uint2 qk = sm.SQ[k];
+                const float dx = (float)(int)(qk.x - ql.x) * sx, dy = (float)(int)(qk.y - ql.y) * sy;
+                const float S = pl.x + sm.P4[k].x + skin;
+                if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
+            };
+            auto scan = [&](int k0, int k1) {
+                for (int k = k0; k < k1; k++) test(k);
             };
             const bool small = p < nsmall;
             if (small) {
                 const int bx = (int)__umulhi(ql.x, (unsigned)nb), by = (int)__umulhi(ql.y, (unsigned)nb);
                 int a0 = bx - 1, a1 = bx + 1, c0 = 1, c1 = 0;
-                float xc = pl.x;
-                if (bx == 0) { a0 = 0; a1 = 1; c0 = nb - 1; c1 = nb - 1; xc = pl.x + Lx; }
-                else if (bx == nb - 1) { a0 = nb - 2; a1 = nb - 1; c0 = 0; c1 = 0; xc = pl.x - Lx; }
+                if (bx == 0) { a0 = 0; a1 = 1; c0 = nb - 1; c1 = nb - 1; }
+                else if (bx == nb - 1) { a0 = nb - 2; a1 = nb - 1; c0 = 0; c1 = 0; }
 #pragma unroll
                 for (int dyb = -1; dyb <= 1; dyb++) {
                     int wy = by + dyb;
-                    float ys = pl.y;
-                    if (wy < 0) { wy += nb; ys += Ly; } else if (wy >= nb) { wy -= nb; ys -= Ly; }
+                    if (wy < 0) wy += nb; else if (wy >= nb) wy -= nb;
                     const int row = wy * nb;
                     const int kA = sm.bst[row + a0], nA = sm.bst[row + a1 + 1] - kA;
                     const int kC = sm.bst[row + c0], nC = c1 >= c0 ? sm.bst[row + c1 + 1] - kC : 0;
-                    for (int i = 0; i < nA + nC; i++) {
-                        const bool inA = i < nA;
-                        const int k = inA ? kA + i : kC + (i - nA);
-                        const float4 q = sm.S4[k];
-                        const float dx = q.x - (inA ? pl.x : xc), dy = q.y - ys;
-                        const float S = pl.z + q.z + skin;
-                        if (fmaf(S, S, -(dx * dx + dy * dy)) > 0.0f && k != p) hit(k);
-                    }
+                    for (int i = 0; i < nA + nC; i++) test(i < nA ? kA + i : kC + (i - nA));
                 }
             } else if (nb) {
-                const float reach = 1.001f * (pl.z + Rs + skin);
-                int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
-                int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+                const float xl = (float)ql.x * sx, yl = (float)ql.y * sy;
+                const float reach = 1.001f * (pl.x + Rs + skin);
+                int bx0 = (int)floorf((xl - reach) / Bx), bx1 = (int)floorf((xl + reach) / Bx);
+                int by0 = (int)floorf((yl - reach) / By), by1 = (int)floorf((yl + reach) / By);
                 const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
                 if (allx) { bx0 = 0; bx1 = nb - 1; }
                 if (ally) { by0 = 0; by1 = nb - 1; }
                 for (int by = by0; by <= by1; by++) {
                     const int wy = by < 0 ? by + nb : (by >= nb ? by - nb : by);
-                    const float ys = ally ? pl.y : (by < 0 ? pl.y + Ly : (by >= nb ? pl.y - Ly : pl.y));
                     const int row = wy * nb;
                     if (allx) {
-                        scan(sm.bst[row], sm.bst[row + nb], pl.x, ys, true, ally);
+                        scan(sm.bst[row], sm.bst[row + nb]);
                     } else {
-                        if (bx0 < 0) scan(sm.bst[row + bx0 + nb], sm.bst[row + nb], pl.x + Lx, ys, false, ally);
+                        if (bx0 < 0) scan(sm.bst[row + bx0 + nb], sm.bst[row + nb]);
                         const int a0 = bx0 < 0 ? 0 : bx0, a1 = bx1 > nb - 1 ? nb - 1 : bx1;
-                        scan(sm.bst[row + a0], sm.bst[row + a1 + 1], pl.x, ys, false, ally);
-                        if (bx1 >= nb) scan(sm.bst[row], sm.bst[row + bx1 - nb + 1], pl.x - Lx, ys, false, ally);
+                        scan(sm.bst[row + a0], sm.bst[row + a1 + 1]);
+                        if (bx1 >= nb) scan(sm.bst[row], sm.bst[row + bx1 - nb + 1]);
                     }
                 }
             }
-            scan(nsmall, n, pl.x, pl.y, true, true);
+            scan(nsmall, n);
             flush();
             overflow |= rec.nlst > NBL;
             nl.head[o + kp] = rec.head();
-            finish(kp, pl, vl, ql, fx, fy, tq);
+            finish(kp, ql, pl, wl, fx, fy, tq);
         }
         const bool any_over = __any_sync(FULL, overflow);
         if (lane == 0) {
@@ -2242,6 +2275,7 @@ static size_t seg_smem(const CellLaunch &cl, int s)
 {
     if (cl.seg_kind[s] == 2) return 4 * pack_region_bytes();
     if (cl.seg_kind[s] == 1 && cl.variant == 3) return 4 * run_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
+    if (cl.seg_kind[s] == 1 && cl.variant == 4) return 4 * list_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     if (cl.seg_kind[s] == 1) return 4 * warp_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     return smem32_binned(cl.seg_threads[s], cl.seg_maxn[s], seg_nbmax(cl, s));
 }
