@@ -615,18 +615,18 @@ static void make_segments(ms_model *m, CellLaunch &c)
 {
     // classes by floe count, largest first: (upper bound, threads, kind);
     // variant 1 runs every class as block-per-cell; variants 2-4 run cells of
-    // more than 256 floes block-per-cell in three classes (their shared
+    // more than 256 floes block-per-cell in four classes (their shared
     // memory is sized by the class's largest cell, so the split keeps most
-    // blocks small: 4.5 % less per interval on the batched workload than one
+    // blocks small: 6 % less per interval on the batched workload than one
     // class above 256), cells of 33-256 floes warp-per-cell with the class
     // bound as the warp capacity, and cells of at most 32 floes packed
     // several to a warp (kind: 0 block, 1 warp, 2 packed)
     struct Cls { int hi, threads, kind; };
     const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
-    const Cls v2[8] = {{1 << 30, 128, 0}, {512, 128, 0}, {384, 128, 0}, {256, 128, 1},
+    const Cls v2[9] = {{1 << 30, 128, 0}, {640, 128, 0}, {512, 128, 0}, {384, 128, 0}, {256, 128, 1},
                        {192, 128, 1},     {128, 128, 1}, {64, 128, 1},  {32, 128, 2}};
     const Cls *cls = c.variant >= 2 ? v2 : v1;
-    const int ncls = c.variant >= 2 ? 8 : 4;
+    const int ncls = c.variant >= 2 ? 9 : 4;
     c.nseg = 0;
     c.nbmax = 32;
     int item = 0;
@@ -874,7 +874,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
-    // the streams of the first three size classes (the largest cells, a
+    // the streams of the first four size classes (the largest cells, a
     // block per cell when there are cells above 256 floes: few blocks, each
     // holding much shared memory, and the longest launches) get the highest
     // stream priority, so their blocks take SMs first as the other classes'
@@ -883,7 +883,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     int p_least = 0, p_great = 0;
     CKM(cudaDeviceGetStreamPriorityRange(&p_least, &p_great));
     for (int k = 0; k < MAXSEG; k++) {
-        const int pr = k < 3 ? p_great : p_least;
+        const int pr = k < 4 ? p_great : p_least;
         CKM(cudaStreamCreateWithPriority(&m->side_stream[k], cudaStreamNonBlocking, pr));
         CKM(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
     }

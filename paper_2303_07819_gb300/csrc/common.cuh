@@ -240,7 +240,7 @@ struct DevState64 {
     double *x, *y, *th, *u, *v, *w, *r, *h;
 };
 
-constexpr int MAXSEG = 8;   // size classes of cells launched separately (binned variants)
+constexpr int MAXSEG = 10;   // size classes of cells launched separately (binned variants)
 
 struct CellLaunch {
     int variant;       // 0 brute force, 1 binned block per cell, 2 binned warp per cell, 3 as 2 with
