@@ -378,6 +378,56 @@ def test_fp32_variants_match_oracle(orc, ms, variant):
     assert e.max() <= TOL32, report(e)
 
 
+def test_neighbour_lists_every_class_match_oracle(orc, ms):
+    """Variant 4 over 100 steps (ten list rebuilds, list steps between them,
+    a coarse step) on cells in every size class: the four block classes (300,
+    400, 520 and 700 floes), the warp classes and the packed one; within the
+    FP32 tolerance of the oracle."""
+    s = ragged_scenario([0, 1, 20, 35, 70, 130, 200, 300, 400, 520, 700], seed=23)
+    p = s["params"]
+    o = orc.Model(p, s["floes"])
+    g = ms.Model(p, s["floes"], ms.MS_FP32)
+    g.set_launch(4, 128, 0, 1.3)
+    o.step(s["dt"], 100)
+    g.step(s["dt"], 100)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+
+
+def test_neighbour_list_overflow(orc, ms):
+    """A 3 km floe ringed by 60 floes of 150 m that touch it: its candidate
+    list (at most 31 entries) overflows, so its cell searches again every
+    step; the result stays within the FP32 tolerance of the oracle and of
+    the warp-binned kernel (variant 2) over 30 steps."""
+    rng = np.random.default_rng(31)
+    L_c, nx = 25e3, 2
+    ang = 2 * np.pi * (np.arange(60) + 0.5) / 60
+    x = np.concatenate([[12.5e3], 12.5e3 + 3140.0 * np.cos(ang)])
+    y = np.concatenate([[12.5e3], 12.5e3 + 3140.0 * np.sin(ang)])
+    r = np.concatenate([[3000.0], np.full(60, 150.0)])
+    # a few loose floes in the other cells
+    for cx, cy in ((1, 0), (0, 1), (1, 1)):
+        x = np.concatenate([x, cx * L_c + rng.uniform(2e3, 23e3, 5)])
+        y = np.concatenate([y, cy * L_c + rng.uniform(2e3, 23e3, 5)])
+        r = np.concatenate([r, np.full(5, 400.0)])
+    n = x.shape[0]
+    p = I._phys(dt=5.0)
+    p.update({"nx": nx, "ny": nx, "Lx": nx * L_c, "Ly": nx * L_c,
+              "modes": I.random_modes(rng, 4, nx * L_c, nx * L_c, 0.1)})
+    fl = I._floes(x, y, r, np.ones(n), u=rng.normal(0, 0.05, n), v=rng.normal(0, 0.05, n))
+    o = orc.Model(p, fl)
+    g = ms.Model(p, fl, ms.MS_FP32)
+    d = ms.Model(p, fl, ms.MS_FP32)
+    g.set_launch(4, 128, 0, 1.3)
+    d.set_launch(2, 128, 0, 1.3)
+    for m in (o, g, d):
+        m.step(5.0, 30)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+    e = rel_errors(g.moments(), d.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+
+
 def test_fp32_variants_agree_one_step(ms):
     """One step of configs[1]'s laws on 16 x 16 cells: the three pair searches
     find the same contacts, so moments agree to FP32 summation order."""
