@@ -613,19 +613,23 @@ static void fill_phys(ms_model *m)
 // launched with a block size and shared memory that fit its largest cell.
 static void make_segments(ms_model *m, CellLaunch &c)
 {
-    // classes by floe count, largest first: (upper bound, threads, kind);
-    // variant 1 runs every class as block-per-cell; variants 2-4 run cells of
-    // more than 256 floes block-per-cell in four classes (their shared
-    // memory is sized by the class's largest cell, so the split keeps most
-    // blocks small: 6 % less per interval on the batched workload than one
-    // class above 256), cells of 33-256 floes warp-per-cell with the class
-    // bound as the warp capacity, and cells of at most 32 floes packed
-    // several to a warp (kind: 0 block, 1 warp, 2 packed)
+    // classes by floe count, largest first: (upper bound, threads, kind:
+    // 0 block per cell, 1 warp per cell with the class bound as the warp
+    // capacity, 2 several cells packed to a warp).  Variant 1 runs every
+    // class block-per-cell.  Variants 2-3 run cells above 256 floes
+    // block-per-cell in four classes (each class's shared memory is sized by
+    // its largest cell, so the split keeps most blocks small).  Variant 4's
+    // warp list kernel beats its block kernel up to 640 floes (measured on the
+    // 128 x 128 batched workload: 9.5 ms per interval against 10.6 ms with
+    // block cells above 256 floes), so only larger cells run block-per-cell.
+    // Cells of at most 32 floes are packed.
     struct Cls { int hi, threads, kind; };
     const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
     const Cls v2[9] = {{1 << 30, 128, 0}, {640, 128, 0}, {512, 128, 0}, {384, 128, 0}, {256, 128, 1},
                        {192, 128, 1},     {128, 128, 1}, {64, 128, 1},  {32, 128, 2}};
-    const Cls *cls = c.variant >= 2 ? v2 : v1;
+    const Cls v4[9] = {{1 << 30, 128, 0}, {640, 128, 1}, {512, 128, 1}, {384, 128, 1}, {256, 128, 1},
+                       {192, 128, 1},     {128, 128, 1}, {64, 128, 1},  {32, 128, 2}};
+    const Cls *cls = c.variant == 4 ? v4 : (c.variant >= 2 ? v2 : v1);
     const int ncls = c.variant >= 2 ? 9 : 4;
     c.nseg = 0;
     c.nbmax = 32;
@@ -874,12 +878,12 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
-    // the streams of the first four size classes (the largest cells, a
-    // block per cell when there are cells above 256 floes: few blocks, each
-    // holding much shared memory, and the longest launches) get the highest
-    // stream priority, so their blocks take SMs first as the other classes'
-    // blocks drain (measured on the 128 x 128 batched workload: 2-3 % less per
-    // interval than equal priorities; graded priorities were slower)
+    // the streams of the first four size classes (the largest cells: few
+    // blocks, each holding much shared memory, and the longest launches) get
+    // the highest stream priority, so their blocks take SMs first as the
+    // other classes' blocks drain (measured on the 128 x 128 batched
+    // workload: 2-6 % less per interval than equal priorities or than
+    // priority for fewer classes; graded priorities were slower)
     int p_least = 0, p_great = 0;
     CKM(cudaDeviceGetStreamPriorityRange(&p_least, &p_great));
     for (int k = 0; k < MAXSEG; k++) {
