@@ -203,19 +203,21 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
 
 /* Choose the cell-kernel launch by hand: variant 0 = brute-force pairs within
  * the cell, 1 = binned pair search (FP32 only); threads per block 64, 128 or
- * 256; persistent = 1 runs a grid of resident blocks that take cells from a
- * work queue (largest cells first); bin_beta = bin side in units of the cell's
- * mean floe spacing (variants 1-3); variant 2 = binned, one warp per cell of
+ * 256 (variants 0-1; the size classes of variants 2-4 set their own);
+ * persistent = 1 runs a grid of resident blocks that take cells from a work
+ * queue (largest cells first); bin_beta = bin side in units of the cell's
+ * mean floe spacing (variants 1-4); variant 2 = binned, one warp per cell of
  * 33 to 256 floes, a block per larger cell, and cells of at most 32 floes
  * packed several to a warp (a lane per floe, the floe kept in registers for a
  * whole coarse interval), the size classes on concurrent streams; variant 3 =
  * variant 2 with each warp cell also kept in shared memory for a whole
  * coarse interval (one launch per interval instead of one per fine step; the
- * per-step arithmetic of variant 2); variant 4 = variant 2 with per-floe
- * contact candidate lists kept across steps in the warp and block cells
- * (pairs within r_l + r_j + skin, rebuilt by the binned search at the start
- * of every gradual-update period and whenever a floe has moved half the
- * skin).  Variants 2-4 give the same
+ * per-step arithmetic of variant 2); variant 4 (the default) = variant 2
+ * with per-floe contact candidate lists kept across steps (pairs within
+ * r_l + r_j + skin, rebuilt by the binned search at the start of every
+ * gradual-update period, whenever a floe has moved half the skin, and
+ * after a list overflowed), cells of up to 640 floes warp-per-cell and
+ * larger ones block-per-cell.  Variants 2-4 give the same
  * results whether an interval runs in one launch or step by step.
  * MS_ERR_ARG for an unsupported choice. */
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
