@@ -203,7 +203,7 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
 
 /* Choose the cell-kernel launch by hand: variant 0 = brute-force pairs within
  * the cell, 1 = binned pair search (FP32 only); threads per block 64, 128 or
- * 256 (variants 0-1; the size classes of variants 2-4 set their own);
+ * 256 (variant 0 and FP64; the size classes of variants 1-4 set their own);
  * persistent = 1 runs a grid of resident blocks that take cells from a work
  * queue (largest cells first); bin_beta = bin side in units of the cell's
  * mean floe spacing (variants 1-4); variant 2 = binned, one warp per cell of
