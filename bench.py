@@ -57,7 +57,7 @@ def profile_traffic():
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
     h = hashlib.sha256()
-    for f in ("cell_step.cu", "common.cuh", "api.cu"):   # kernels, and the launch's size classes
+    for f in ("cell_step.cu", "common.cuh", "classes.cuh"):   # kernels and the launch's size classes
         h.update(open(os.path.join(ROOT, "paper_2303_07819_gb300", "csrc", f), "rb").read())
     if h.hexdigest()[:16] != rec.get("sources_sha256_16"):
         return None, rec

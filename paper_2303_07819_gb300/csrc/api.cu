@@ -2,13 +2,17 @@
 // Algorithm 1 schedule (fine steps, coarse steps, gradual updates) captured
 // in CUDA graphs, the truth DEM driver, and the C-ABI of include/msdem.h.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
+#include "classes.cuh"
 #include "common.cuh"
 #include "../../include/msdem.h"
 
@@ -184,6 +188,46 @@ static uint32_t to_fix(double frac)
 
 static double from_fix(uint32_t q) { return (double)q * (1.0 / 4294967296.0); }
 
+// f(begin, end) over [0, n) in contiguous chunks on the host's cores (the
+// per-floe loops of uploads, downloads and their checks; each index is
+// handled by exactly one chunk, so the results do not depend on the split)
+template <class F>
+static void host_parallel(long long n, F &&f)
+{
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt == 0 ? 1u : (nt > 32u ? 32u : nt);
+    if (n < 65536 || nt == 1) {
+        f(0LL, n);
+        return;
+    }
+    const long long chunk = (n + nt - 1) / nt;
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; t++) {
+        const long long b = t * chunk, e = std::min(n, b + chunk);
+        if (b < e) th.emplace_back([&f, b, e] { f(b, e); });
+    }
+    f(0LL, std::min(n, chunk));
+    for (auto &x : th) x.join();
+}
+
+// smallest index in [0, n) for which bad(l) holds, or n
+template <class B>
+static long long host_first(long long n, B &&bad)
+{
+    std::atomic<long long> first{LLONG_MAX};
+    host_parallel(n, [&](long long b, long long e) {
+        for (long long l = b; l < e; l++)
+            if (bad(l)) {
+                long long cur = first.load();
+                while (l < cur && !first.compare_exchange_weak(cur, l)) {
+                }
+                break;
+            }
+    });
+    const long long f = first.load();
+    return f < n ? f : n;
+}
+
 static int validate_floes(const ms_floes *f, long long expect_n)
 {
     if (!f) return fail(MS_ERR_ARG, "floes is NULL");
@@ -193,12 +237,14 @@ static int validate_floes(const ms_floes *f, long long expect_n)
     if (f->n > 0 && (!f->x || !f->y || !f->theta || !f->u || !f->v || !f->omega || !f->r || !f->h))
         return fail(MS_ERR_ARG, "a floe array is NULL");
     if (f->n > (long long)0x7fffffff) return fail(MS_ERR_ARG, "more than 2^31-1 floes");
-    for (long long l = 0; l < f->n; l++) {
-        if (!(isfin(f->x[l]) && isfin(f->y[l]) && isfin(f->theta[l]) && isfin(f->u[l]) &&
-              isfin(f->v[l]) && isfin(f->omega[l]) && isfin(f->r[l]) && isfin(f->h[l])))
-            return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
-        if (!(f->r[l] > 0.0) || !(f->h[l] > 0.0))
-            return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
+    auto finite = [f](long long l) {
+        return isfin(f->x[l]) && isfin(f->y[l]) && isfin(f->theta[l]) && isfin(f->u[l]) && isfin(f->v[l]) &&
+               isfin(f->omega[l]) && isfin(f->r[l]) && isfin(f->h[l]);
+    };
+    const long long l = host_first(f->n, [&](long long k) { return !finite(k) || !(f->r[k] > 0.0) || !(f->h[k] > 0.0); });
+    if (l < f->n) {
+        if (!finite(l)) return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
+        return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
     }
     return MS_OK;
 }
@@ -212,21 +258,23 @@ static int upload_model_state(ms_model *m, const ms_floes *f)
     if (m->precision == MS_FP64) {
         double *st = (double *)stage(m, sizeof(double) * 8 * n);
         if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(64 * n));
-        for (long long k = 0; k < n; k++) {
-            const long long l = m->h_orig[k];
-            const int c = m->h_cell_of_orig[l];
-            const int ix = c % nx, iy = c / nx;
-            const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
-            const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
-            st[k] = Xw - ix * m->g.Lcx;
-            st[n + k] = Yw - iy * m->g.Lcy;
-            st[2 * n + k] = f->theta[l];
-            st[3 * n + k] = f->u[l];
-            st[4 * n + k] = f->v[l];
-            st[5 * n + k] = f->omega[l];
-            st[6 * n + k] = f->r[l];
-            st[7 * n + k] = f->h[l];
-        }
+        host_parallel(n, [&](long long k0, long long k1) {
+            for (long long k = k0; k < k1; k++) {
+                const long long l = m->h_orig[k];
+                const int c = m->h_cell_of_orig[l];
+                const int ix = c % nx, iy = c / nx;
+                const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+                const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+                st[k] = Xw - ix * m->g.Lcx;
+                st[n + k] = Yw - iy * m->g.Lcy;
+                st[2 * n + k] = f->theta[l];
+                st[3 * n + k] = f->u[l];
+                st[4 * n + k] = f->v[l];
+                st[5 * n + k] = f->omega[l];
+                st[6 * n + k] = f->r[l];
+                st[7 * n + k] = f->h[l];
+            }
+        });
         double *dst[8] = {m->s64.x, m->s64.y, m->s64.th, m->s64.u, m->s64.v, m->s64.w, m->s64.r, m->s64.h};
         for (int a = 0; a < 8; a++)
             CK(cudaMemcpyAsync(dst[a], st + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
@@ -235,21 +283,23 @@ static int upload_model_state(ms_model *m, const ms_floes *f)
         if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(32 * n));
         uint32_t *qx = (uint32_t *)st, *qy = qx + n;
         float *fl = (float *)(qy + n);
-        for (long long k = 0; k < n; k++) {
-            const long long l = m->h_orig[k];
-            const int c = m->h_cell_of_orig[l];
-            const int ix = c % nx, iy = c / nx;
-            const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
-            const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
-            qx[k] = to_fix((Xw - ix * m->g.Lcx) / m->g.Lcx);
-            qy[k] = to_fix((Yw - iy * m->g.Lcy) / m->g.Lcy);
-            fl[k] = (float)f->theta[l];
-            fl[n + k] = (float)f->u[l];
-            fl[2 * n + k] = (float)f->v[l];
-            fl[3 * n + k] = (float)f->omega[l];
-            fl[4 * n + k] = (float)f->r[l];
-            fl[5 * n + k] = (float)f->h[l];
-        }
+        host_parallel(n, [&](long long k0, long long k1) {
+            for (long long k = k0; k < k1; k++) {
+                const long long l = m->h_orig[k];
+                const int c = m->h_cell_of_orig[l];
+                const int ix = c % nx, iy = c / nx;
+                const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
+                const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
+                qx[k] = to_fix((Xw - ix * m->g.Lcx) / m->g.Lcx);
+                qy[k] = to_fix((Yw - iy * m->g.Lcy) / m->g.Lcy);
+                fl[k] = (float)f->theta[l];
+                fl[n + k] = (float)f->u[l];
+                fl[2 * n + k] = (float)f->v[l];
+                fl[3 * n + k] = (float)f->omega[l];
+                fl[4 * n + k] = (float)f->r[l];
+                fl[5 * n + k] = (float)f->h[l];
+            }
+        });
         CK(cudaMemcpyAsync(m->s32.xq, qx, 4 * n, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(m->s32.yq, qy, 4 * n, cudaMemcpyHostToDevice, m->stream));
         float *dst[6] = {m->s32.th, m->s32.u, m->s32.v, m->s32.w, m->s32.r, m->s32.h};
@@ -613,24 +663,10 @@ static void fill_phys(ms_model *m)
 // launched with a block size and shared memory that fit its largest cell.
 static void make_segments(ms_model *m, CellLaunch &c)
 {
-    // classes by floe count, largest first: (upper bound, threads, kind:
-    // 0 block per cell, 1 warp per cell with the class bound as the warp
-    // capacity, 2 several cells packed to a warp).  Variant 1 runs every
-    // class block-per-cell.  Variants 2-3 run cells above 256 floes
-    // block-per-cell in four classes (each class's shared memory is sized by
-    // its largest cell, so the split keeps most blocks small).  Variant 4's
-    // warp list kernel beats its block kernel up to 640 floes (measured on the
-    // 128 x 128 batched workload: 9.5 ms per interval against 10.6 ms with
-    // block cells above 256 floes), so only larger cells run block-per-cell.
-    // Cells of at most 32 floes are packed.
-    struct Cls { int hi, threads, kind; };
-    const Cls v1[4] = {{1 << 30, 256, 0}, {512, 256, 0}, {256, 128, 0}, {64, 64, 0}};
-    const Cls v2[9] = {{1 << 30, 128, 0}, {640, 128, 0}, {512, 128, 0}, {384, 128, 0}, {256, 128, 1},
-                       {192, 128, 1},     {128, 128, 1}, {64, 128, 1},  {32, 128, 2}};
-    const Cls v4[9] = {{1 << 30, 128, 0}, {640, 128, 1}, {512, 128, 1}, {384, 128, 1}, {256, 128, 1},
-                       {192, 128, 1},     {128, 128, 1}, {64, 128, 1},  {32, 128, 2}};
-    const Cls *cls = c.variant == 4 ? v4 : (c.variant >= 2 ? v2 : v1);
-    const int ncls = c.variant >= 2 ? 9 : 4;
+    const SizeClass *cls = c.variant == 4 ? kClassesV4 : (c.variant >= 2 ? kClassesV2 : kClassesV1);
+    const int ncls = c.variant == 4 ? (int)(sizeof(kClassesV4) / sizeof(SizeClass))
+                     : c.variant >= 2 ? (int)(sizeof(kClassesV2) / sizeof(SizeClass))
+                                      : (int)(sizeof(kClassesV1) / sizeof(SizeClass));
     c.nseg = 0;
     c.nbmax = 32;
     int item = 0;
@@ -878,16 +914,10 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaGetDevice(&dev));
     CKM(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKM(cudaStreamCreateWithFlags(&m->own_stream, cudaStreamNonBlocking));
-    // the streams of the first four size classes (the largest cells: few
-    // blocks, each holding much shared memory, and the longest launches) get
-    // the highest stream priority, so their blocks take SMs first as the
-    // other classes' blocks drain (measured on the 128 x 128 batched
-    // workload: 2-6 % less per interval than equal priorities or than
-    // priority for fewer classes; graded priorities were slower)
     int p_least = 0, p_great = 0;
     CKM(cudaDeviceGetStreamPriorityRange(&p_least, &p_great));
     for (int k = 0; k < MAXSEG; k++) {
-        const int pr = k < 4 ? p_great : p_least;
+        const int pr = k < kHighPriorityClasses ? p_great : p_least;
         CKM(cudaStreamCreateWithPriority(&m->side_stream[k], cudaStreamNonBlocking, pr));
         CKM(cudaEventCreateWithFlags(&m->ev_join[k], cudaEventDisableTiming));
     }
@@ -1065,14 +1095,16 @@ static int download(ms_model *m, bool truth, double *out)
         for (int a = 0; a < 8; a++)
             CK(cudaMemcpyAsync(st + a * n, src[a], sizeof(double) * n, cudaMemcpyDeviceToHost, m->stream));
         CK(cudaStreamSynchronize(m->stream));
-        for (long long k = 0; k < n; k++) {
-            const long long l = truth ? k : m->h_orig[k];
-            const int c = truth ? 0 : m->h_cell_of_orig[l];
-            const double X0 = truth ? 0.0 : (c % nx) * m->g.Lcx, Y0 = truth ? 0.0 : (c / nx) * m->g.Lcy;
-            out[l] = X0 + st[k];
-            out[n + l] = Y0 + st[n + k];
-            for (int a = 2; a < 8; a++) out[a * n + l] = st[a * n + k];
-        }
+        host_parallel(n, [&](long long k0, long long k1) {
+            for (long long k = k0; k < k1; k++) {
+                const long long l = truth ? k : m->h_orig[k];
+                const int c = truth ? 0 : m->h_cell_of_orig[l];
+                const double X0 = truth ? 0.0 : (c % nx) * m->g.Lcx, Y0 = truth ? 0.0 : (c / nx) * m->g.Lcy;
+                out[l] = X0 + st[k];
+                out[n + l] = Y0 + st[n + k];
+                for (int a = 2; a < 8; a++) out[a * n + l] = st[a * n + k];
+            }
+        });
     } else {
         unsigned char *st = (unsigned char *)stage(m, sizeof(float) * 8 * n);
         if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost failed");
@@ -1085,18 +1117,20 @@ static int download(ms_model *m, bool truth, double *out)
         for (int a = 0; a < 6; a++)
             CK(cudaMemcpyAsync(fl + a * n, src[a], 4 * n, cudaMemcpyDeviceToHost, m->stream));
         CK(cudaStreamSynchronize(m->stream));
-        for (long long k = 0; k < n; k++) {
-            const long long l = truth ? k : m->h_orig[k];
-            if (truth) {
-                out[l] = from_fix(qx[k]) * m->g.Lx;
-                out[n + l] = from_fix(qy[k]) * m->g.Ly;
-            } else {
-                const int c = m->h_cell_of_orig[l];
-                out[l] = ((c % nx) + from_fix(qx[k])) * m->g.Lcx;
-                out[n + l] = ((c / nx) + from_fix(qy[k])) * m->g.Lcy;
+        host_parallel(n, [&](long long k0, long long k1) {
+            for (long long k = k0; k < k1; k++) {
+                const long long l = truth ? k : m->h_orig[k];
+                if (truth) {
+                    out[l] = from_fix(qx[k]) * m->g.Lx;
+                    out[n + l] = from_fix(qy[k]) * m->g.Ly;
+                } else {
+                    const int c = m->h_cell_of_orig[l];
+                    out[l] = ((c % nx) + from_fix(qx[k])) * m->g.Lcx;
+                    out[n + l] = ((c / nx) + from_fix(qy[k])) * m->g.Lcy;
+                }
+                for (int a = 0; a < 6; a++) out[(a + 2) * n + l] = fl[a * n + k];
             }
-            for (int a = 0; a < 6; a++) out[(a + 2) * n + l] = fl[a * n + k];
-        }
+        });
     }
     return MS_OK;
 }
@@ -1124,11 +1158,12 @@ int ms_set_floes(ms_model *m, const ms_floes *floes)
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
     int rc = validate_floes(floes, m->n);
     if (rc) return rc;
-    for (long long l = 0; l < m->n; l++) {
+    const long long left = host_first(m->n, [&](long long l) {
         const int c = cell_index(floes->y[l], m->g.Ly, m->g.Lcy, m->g.ny) * m->g.nx +
                       cell_index(floes->x[l], m->g.Lx, m->g.Lcx, m->g.nx);
-        if (c != m->h_cell_of_orig[l]) return fail(MS_ERR_ARG, "floe %lld left its cell", l);
-    }
+        return c != m->h_cell_of_orig[l];
+    });
+    if (left < m->n) return fail(MS_ERR_ARG, "floe %lld left its cell", left);
     CK(cudaStreamSynchronize(m->stream));
     if ((rc = upload_model_state(m, floes))) return rc;
     CK(invalidate_lists(m));
