@@ -380,6 +380,8 @@ def main():
 
     hbm, peak_kind, _ = peaks()
     traffic, prof = profile_traffic()
+    if args.config != 2:     # the committed capture is of the 128 x 128 batched workload only
+        traffic, prof = None, None
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
     kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
     achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9

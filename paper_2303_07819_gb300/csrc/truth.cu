@@ -7,6 +7,7 @@
 // force summation order are deterministic) into square-ish bins of side at
 // least 2 r_max; each floe then visits the 3 x 3 neighbouring bins.  The state
 // is double-buffered: the step reads one copy and writes the other.
+#include <climits>
 #include <mutex>
 
 #include "common.cuh"
@@ -86,21 +87,61 @@ __global__ void k_scatter(const int *bin, const int *start, int *cursor, int *so
     sorted[start[b] + atomicAdd(&cursor[b], 1)] = (int)l;
 }
 
-// insertion sort of each bin's floe indices (bins hold a handful of floes)
-__global__ void k_bin_sort(const int *start, int *sorted, int nbins)
+// Each bin's floe indices into ascending order, a warp per bin: every
+// index's final place is its rank, the number of smaller indices in the bin
+// (indices are distinct), so a lane ranks its entries against the bin's
+// entries and all lanes write after all have read.  Bins of up to 32 floes
+// rank from registers by shuffles; larger ones read the bin again per entry.
+constexpr int SORT_WARPS = 8;
+
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_bin_sort(const int *start, int *sorted, int nbins)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * SORT_WARPS + (threadIdx.x >> 5);
     if (b >= nbins) return;
-    const int s = start[b], e = start[b + 1];
-    for (int i = s + 1; i < e; i++) {
-        const int key = sorted[i];
-        int j = i - 1;
-        while (j >= s && sorted[j] > key) {
-            sorted[j + 1] = sorted[j];
-            j--;
-        }
-        sorted[j + 1] = key;
+    const int s = start[b], m = start[b + 1] - s;
+    if (m <= 1) return;
+    int *bin = sorted + s;
+    if (m <= 32) {
+        const int key = lane < m ? bin[lane] : INT_MAX;
+        int rank = 0;
+        for (int i = 0; i < m; i++) rank += __shfl_sync(0xffffffffu, key, i) < key ? 1 : 0;
+        __syncwarp();
+        if (lane < m) bin[rank] = key;
+        return;
     }
+    // larger bins: at most 8 entries per lane held in registers until all
+    // lanes have ranked theirs (bins above 256 floes fall back to a serial
+    // insertion sort by lane 0)
+    if (m > 256) {
+        if (lane == 0)
+            for (int i = 1; i < m; i++) {
+                const int key = bin[i];
+                int j = i - 1;
+                while (j >= 0 && bin[j] > key) {
+                    bin[j + 1] = bin[j];
+                    j--;
+                }
+                bin[j + 1] = key;
+            }
+        return;
+    }
+    int keys[8], ranks[8];
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        const int i = lane + 32 * t;
+        keys[t] = i < m ? bin[i] : INT_MAX;
+        ranks[t] = 0;
+    }
+    for (int i = 0; i < m; i++) {
+        const int other = bin[i];
+#pragma unroll
+        for (int t = 0; t < 8; t++) ranks[t] += other < keys[t] ? 1 : 0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < 8; t++)
+        if (lane + 32 * t < m) bin[ranks[t]] = keys[t];
 }
 
 // bin of a fixed-point coordinate: floor(frac * nb) exactly
@@ -374,7 +415,7 @@ cudaError_t counting_sort(TruthBins &b, long long n, BinF binf, cudaStream_t st)
     if ((e = bins_scan(b, nbins, st)) != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) k_scatter<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.bin, b.start, b.cursor, b.sorted, n);
-    k_bin_sort<<<(nbins + T - 1) / T, T, 0, st>>>(b.start, b.sorted, nbins);
+    k_bin_sort<<<(nbins + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(b.start, b.sorted, nbins);
     return cudaGetLastError();
 }
 
