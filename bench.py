@@ -247,6 +247,19 @@ def calibrated_oracle(s, target_s: float, ncells: int = 4096):
     return ncells, steps
 
 
+def job_rate(units_per_rank, ms_local, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` ranks that each processed
+    `units_per_rank` units (replicas of one workload, one per GPU): all ranks'
+    units over the slowest rank's timed milliseconds.  Returns (rate, max ms)."""
+    import torch
+    tot_ms = float(ms_local)
+    if dist is not None:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    return world * units_per_rank / (tot_ms / 1e3), tot_ms
+
+
 def run_reference(args, s, rank):
     if rank != 0:
         return
@@ -369,13 +382,8 @@ def main():
     clk = clocks.stop()
     model.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
     fine_steps = args.steps * N0
-    value = world * n_floes * fine_steps / (tot_ms / 1e3)
+    value, tot_ms = job_rate(n_floes * fine_steps, float(sum(step_ms)), world, dist, "cuda")
     cell_rate = world * ncell * fine_steps / (tot_ms / 1e3)
 
     hbm, peak_kind, _ = peaks()
