@@ -736,23 +736,67 @@ static int configure_launch(ms_model *m, const CellLaunch &cl_in)
     return MS_OK;
 }
 
-static int setup_truth_bins(ms_model *m, double rmax)
+// Grid of bins of side > 2 rad on the domain (fewer than 3 bins along an
+// axis: one bin on that axis), at most 2^20 bins.
+static void truth_grid(const ms_model *m, double rad, int &nbx, int &nby)
 {
-    // bins of side >= 2 r_max; fewer than 3 along an axis -> one bin on that axis
-    int nbx = (int)std::floor(m->g.Lx / (2.0 * rmax));
-    int nby = (int)std::floor(m->g.Ly / (2.0 * rmax));
+    nbx = (int)std::floor(m->g.Lx / (2.0002 * rad));
+    nby = (int)std::floor(m->g.Ly / (2.0002 * rad));
     if (nbx < 3) nbx = 1;
     if (nby < 3) nby = 1;
     while ((long long)nbx * nby > (1LL << 20)) {
         if (nbx >= nby) nbx = std::max(3, nbx / 2); else nby = std::max(3, nby / 2);
     }
+}
+
+// Bins of the truth DEM.  One grid of bins wider than 2 r_max holds every
+// contact partner of a floe in its 3 x 3 neighbourhood; with a wide radius
+// distribution most floes are small and such bins hold many candidates, so
+// floes of radius <= r_split go to a finer grid and only the larger ones to
+// the 2 r_max grid.  r_split is the fraction of r_max (1, 1/2, ..., 1/8) that
+// minimises the expected work of a floe's search: candidates tested (bins
+// visited times the mean floes per bin, from the actual radii) and bins
+// visited.
+static int setup_truth_bins(ms_model *m, const double *r, double rmax)
+{
+    const long long n = m->n;
+    int nbx, nby, nbx2, nby2;
+    truth_grid(m, rmax, nbx2, nby2);
+    double best = -1.0, best_q = 1.0;
+    for (double q : {1.0, 0.5, 1.0 / 3.0, 0.25, 1.0 / 6.0, 0.125}) {
+        const double rs = q * rmax;
+        truth_grid(m, rs, nbx, nby);
+        long long nS = 0;
+        for (long long l = 0; l < n; l++) nS += r[l] <= rs ? 1 : 0;
+        const long long nL = n - nS;
+        const double dS = (double)nS / ((double)nbx * nby), dL = nL ? (double)nL / ((double)nbx2 * nby2) : 0.0;
+        const double Bx = m->g.Lx / nbx, By = m->g.Ly / nby;
+        const double large_bins = std::min(3, nbx2) * (double)std::min(3, nby2);
+        // a visited bin costs about half a candidate test (its bounds, the loop)
+        double cost = 0.0;
+        for (long long l = 0; l < n; l++) {
+            const int kx = (int)std::ceil((r[l] + rs) / Bx), ky = (int)std::ceil((r[l] + rs) / By);
+            const double bins = std::min(2 * kx + 1, nbx) * (double)std::min(2 * ky + 1, nby);
+            cost += bins * (dS + 0.5) + (nL ? large_bins * (dL + 0.5) : 0.0);
+        }
+        if (best < 0.0 || cost < 0.9 * best) {   // a finer grid only for a clear gain
+            best = cost;
+            best_q = q;
+        }
+    }
+    truth_grid(m, best_q * rmax, nbx, nby);
+    long long nL = 0;
+    for (long long l = 0; l < n; l++) nL += r[l] <= best_q * rmax ? 0 : 1;
     TruthBins *bs[2] = {&m->tb, &m->cb};
-    int dims[2][2] = {{nbx, nby}, {m->g.nx, m->g.ny}};
+    const int dims[2][4] = {{nbx, nby, nL ? nbx2 : 0, nL ? nby2 : 0}, {m->g.nx, m->g.ny, 0, 0}};
     for (int k = 0; k < 2; k++) {
         TruthBins &b = *bs[k];
         b.nbx = dims[k][0];
         b.nby = dims[k][1];
-        const int nbins = b.nbx * b.nby;
+        b.nbx2 = dims[k][2];
+        b.nby2 = dims[k][3];
+        b.r_split = k == 0 ? (float)(best_q * rmax) : 0.0f;
+        const int nbins = b.nbins();
         b.nscan_blocks = (nbins + 1023) / 1024;
         if (b.nscan_blocks > 1024) return fail(MS_ERR_ARG, "too many bins (%d)", nbins);
         CK(dalloc(m, &b.count, nbins));
@@ -966,7 +1010,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
 #undef CKM
     // an ensemble has no truth DEM (each realization's truth is a model of its own)
     if ((rc = upload_model_state(m, floes)) ||
-        (nens == 1 && ((rc = upload_truth_state(m, floes)) || (rc = setup_truth_bins(m, rmax > 0 ? rmax : 1.0))))) {
+        (nens == 1 && ((rc = upload_truth_state(m, floes)) || (rc = setup_truth_bins(m, floes->r, rmax > 0 ? rmax : 1.0))))) {
         ms_free(m);
         return rc;
     }

@@ -357,8 +357,15 @@ cudaError_t launch_advance(Ctrl *ctrl, int N0, cudaStream_t st);       // base +
 int coarse_launches();
 
 // truth.cu
+// Bins of the truth DEM (and of the per-cell moment binning): floes of radius
+// <= r_split in a grid of nbx x nby bins, the others in a second grid of
+// nbx2 x nby2 bins (0 x 0: none), one bin index space (the second grid's bins
+// after the first's).
 struct TruthBins {
     int nbx, nby;          // bins per side (1 x 1: brute force)
+    int nbx2, nby2;        // the large floes' grid
+    float r_split;
+    __host__ __device__ int nbins() const { return nbx * nby + nbx2 * nby2; }
     int *count;            // [nbins]
     int *start;            // [nbins + 1]
     int *cursor;           // [nbins]

@@ -4,9 +4,12 @@
 //
 // Every step the floes are re-binned by a GPU counting sort (count -> scan ->
 // scatter -> per-bin sort by floe index, so the bin contents and thus the
-// force summation order are deterministic) into square-ish bins of side at
-// least 2 r_max; each floe then visits the 3 x 3 neighbouring bins.  The state
-// is double-buffered: the step reads one copy and writes the other.
+// force summation order are deterministic).  Floes of radius <= r_split go to
+// a grid of bins wider than 2 r_split, larger ones to a grid of bins wider
+// than 2 r_max (with a narrow radius distribution r_split = r_max and the
+// second grid is empty); a floe visits the bins of the first grid within
+// r_l + r_split of its own and the 3 x 3 neighbourhood in the second.  The
+// state is double-buffered: the step reads one copy and writes the other.
 #include <climits>
 #include <mutex>
 
@@ -87,6 +90,46 @@ __global__ void k_scatter(const int *bin, const int *start, int *cursor, int *so
     sorted[start[b] + atomicAdd(&cursor[b], 1)] = (int)l;
 }
 
+// Each bin's floe indices into ascending order, a thread per bin (grids with
+// few floes per bin): up to 16 indices sorted in registers, larger bins in
+// place in global memory.
+__global__ void k_bin_sort_sparse(const int *start, int *sorted, int nbins)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int s = start[b], m = start[b + 1] - s;
+    if (m <= 1) return;
+    int *bin = sorted + s;
+    if (m <= 16) {
+        int v[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] = i < m ? bin[i] : INT_MAX;
+        // insertion sort on registers (the unrolled indices keep v in registers)
+#pragma unroll
+        for (int i = 1; i < 16; i++) {
+#pragma unroll
+            for (int j = i; j > 0; j--) {
+                const int lo = min(v[j - 1], v[j]), hi = max(v[j - 1], v[j]);
+                v[j - 1] = lo;
+                v[j] = hi;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+            if (i < m) bin[i] = v[i];
+        return;
+    }
+    for (int i = 1; i < m; i++) {
+        const int key = bin[i];
+        int j = i - 1;
+        while (j >= 0 && bin[j] > key) {
+            bin[j + 1] = bin[j];
+            j--;
+        }
+        bin[j + 1] = key;
+    }
+}
+
 // Each bin's floe indices into ascending order, a warp per bin: every
 // index's final place is its rank, the number of smaller indices in the bin
 // (indices are distinct), so a lane ranks its entries against the bin's
@@ -153,24 +196,29 @@ __device__ __forceinline__ int dbin(double x, double L, int nb)
     return b < 0 ? 0 : (b > nb - 1 ? nb - 1 : b);
 }
 
-__global__ void k_bin32(const uint32_t *xq, const uint32_t *yq, int nbx, int nby, int *bin, int *count,
+// bin of floe l: the first grid for radii <= r_split (or r == nullptr), the
+// second grid's bins after the first's
+__global__ void k_bin32(const uint32_t *xq, const uint32_t *yq, const float *r, TruthBins tb, long long n)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    int b;
+    if (!r || r[l] <= tb.r_split) b = fbin(yq[l], tb.nby) * tb.nbx + fbin(xq[l], tb.nbx);
+    else b = tb.nbx * tb.nby + fbin(yq[l], tb.nby2) * tb.nbx2 + fbin(xq[l], tb.nbx2);
+    tb.bin[l] = b;
+    atomicAdd(&tb.count[b], 1);
+}
+
+__global__ void k_bin64(const double *x, const double *y, const double *r, double Lx, double Ly, TruthBins tb,
                         long long n)
 {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
-    const int b = fbin(yq[l], nby) * nbx + fbin(xq[l], nbx);
-    bin[l] = b;
-    atomicAdd(&count[b], 1);
-}
-
-__global__ void k_bin64(const double *x, const double *y, double Lx, double Ly, int nbx, int nby, int *bin,
-                        int *count, long long n)
-{
-    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n) return;
-    const int b = dbin(y[l], Ly, nby) * nbx + dbin(x[l], Lx, nbx);
-    bin[l] = b;
-    atomicAdd(&count[b], 1);
+    int b;
+    if (!r || r[l] <= (double)tb.r_split) b = dbin(y[l], Ly, tb.nby) * tb.nbx + dbin(x[l], Lx, tb.nbx);
+    else b = tb.nbx * tb.nby + dbin(y[l], Ly, tb.nby2) * tb.nbx2 + dbin(x[l], Lx, tb.nbx2);
+    tb.bin[l] = b;
+    atomicAdd(&tb.count[b], 1);
 }
 
 // ------------------------------------------------------------ truth steps
@@ -207,21 +255,49 @@ __device__ __forceinline__ void wall_add(R dl, R dr, R ul, R vl, R wl, R rl, R h
     }
 }
 
-// Neighbour bins of (bx, by): 3 x 3 with periodic wrap, or the bin alone
-// along an axis that has fewer than 3 bins (then it holds the whole axis).
-struct NbRange {
-    int x0, x1, y0, y1;
+// The bins along one axis whose floes can touch a floe at coordinate bin b
+// reaching `reach` beyond its own bin's edge (k = ceil(reach / bin side)
+// bins to either side): offsets o0..o1 from b, or every bin of the axis
+// (offsets 0..nb-1 from bin 0, `all`) when that many would wrap onto
+// themselves.
+struct AxisRange {
+    int b0, o0, o1;
+    bool all;
 };
-__device__ __forceinline__ NbRange nb_range(int nbx, int nby)
+__device__ __forceinline__ AxisRange axis_range(int b, int nb, float reach_bins)
 {
-    NbRange r;
-    r.x0 = nbx >= 3 ? -1 : 0; r.x1 = nbx >= 3 ? 1 : 0;
-    r.y0 = nby >= 3 ? -1 : 0; r.y1 = nby >= 3 ? 1 : 0;
-    return r;
+    AxisRange a;
+    const int k = (int)ceilf(reach_bins * 1.0001f);   // margin against rounding; bins are wider than 2.0002 r
+    if (2 * k + 1 >= nb) {
+        a.all = true; a.b0 = 0; a.o0 = 0; a.o1 = nb - 1;
+    } else {
+        a.all = false; a.b0 = b; a.o0 = -k; a.o1 = k;
+    }
+    return a;
 }
 
-__global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArgs a, const int *bin,
-                          const int *start, const int *sorted, int nbx, int nby)
+// Visits the bins of one grid (nbx x nby bins from bin index `base`) that
+// can hold a partner of a floe at coordinate bins (bx, by) reaching
+// (rx, ry) bin sides beyond its own bin, in a fixed order (y, then x), with
+// periodic wrap in y and, without walls, in x.
+template <class F>
+__device__ __forceinline__ void visit_bins(int base, int nbx, int nby, int bx, int by, float rx, float ry, bool walls,
+                                           F &&scan_bin)
+{
+    const AxisRange ax = axis_range(bx, nbx, rx), ay = axis_range(by, nby, ry);
+    for (int oy = ay.o0; oy <= ay.o1; oy++) {
+        int cy = ay.b0 + oy;
+        cy = cy < 0 ? cy + nby : (cy >= nby ? cy - nby : cy);
+        for (int ox = ax.o0; ox <= ax.o1; ox++) {
+            int cx = ax.b0 + ox;
+            if (walls && (cx < 0 || cx >= nbx)) continue;   // no image across a wall
+            cx = cx < 0 ? cx + nbx : (cx >= nbx ? cx - nbx : cx);
+            scan_bin(base + cy * nbx + cx);
+        }
+    }
+}
+
+__global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArgs a, TruthBins tb)
 {
     __shared__ float wind[2];
     if (threadIdx.x == 0) {
@@ -236,35 +312,35 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
     const float sx = a.k.sx, sy = a.k.sy, isx = a.k.isx, isy = a.k.isy;
     const uint32_t xl = in.xq[l], yl = in.yq[l];
     const float ul = in.u[l], vl = in.v[l], wl = in.w[l], rl = in.r[l], hl = in.h[l];
-    const int b = bin[l];
-    const int bx = b % nbx, by = b / nbx;
-    const NbRange nr = nb_range(nbx, nby);
     const bool walls = a.g.walls != 0;
     float fx = 0.0f, fy = 0.0f, tq = 0.0f;
     unsigned deep = 0;
-    for (int oy = nr.y0; oy <= nr.y1; oy++) {
-        const int cy = (by + oy + nby) % nby;
-        for (int ox = nr.x0; ox <= nr.x1; ox++) {
-            if (walls && (bx + ox < 0 || bx + ox >= nbx)) continue;   // no image across a wall
-            const int cb = cy * nbx + (bx + ox + nbx) % nbx;
-            for (int k = start[cb]; k < start[cb + 1]; k++) {
-                const int j = sorted[k];
-                if (j == l) continue;
-                // between walls the plain difference (partners up to two bins
-                // away may be more than half the domain apart), else the
-                // periodic minimum image of the 32-bit fixed point
-                const float dx = walls ? (float)((long long)in.xq[j] - (long long)xl) * sx
-                                       : (float)(int)(in.xq[j] - xl) * sx;
-                const float dy = (float)(int)(in.yq[j] - yl) * sy;
-                const float d2 = dx * dx + dy * dy;
-                const float rj = in.r[j];
-                const float S = rl + rj;
-                if (d2 < S * S)
-                    contact_add(dx, dy, d2, rl, rj, hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
-                                fx, fy, tq, deep);
-            }
+    auto scan_bin = [&](int cb) {
+        for (int k = tb.start[cb]; k < tb.start[cb + 1]; k++) {
+            const int j = tb.sorted[k];
+            if (j == l) continue;
+            // between walls the plain difference (partners up to two bins
+            // away may be more than half the domain apart), else the
+            // periodic minimum image of the 32-bit fixed point
+            const float dx = walls ? (float)((long long)in.xq[j] - (long long)xl) * sx
+                                   : (float)(int)(in.xq[j] - xl) * sx;
+            const float dy = (float)(int)(in.yq[j] - yl) * sy;
+            const float d2 = dx * dx + dy * dy;
+            const float rj = in.r[j];
+            const float S = rl + rj;
+            if (d2 < S * S)
+                contact_add(dx, dy, d2, rl, rj, hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
+                            fx, fy, tq, deep);
         }
-    }
+    };
+    // partners of radius <= r_split in the first grid, within r_l + r_split;
+    // larger partners in the second grid (bins wider than 2 r_max: 3 x 3)
+    const float Lx = (float)a.g.Lx, Ly = (float)a.g.Ly, reach = rl + tb.r_split;
+    visit_bins(0, tb.nbx, tb.nby, fbin(xl, tb.nbx), fbin(yl, tb.nby), reach * tb.nbx / Lx, reach * tb.nby / Ly,
+               walls, scan_bin);
+    if (tb.nbx2 > 0)
+        visit_bins(tb.nbx * tb.nby, tb.nbx2, tb.nby2, fbin(xl, tb.nbx2), fbin(yl, tb.nby2), 0.99f, 0.99f, walls,
+                   scan_bin);   // bins wider than 2 r_max: every partner within one bin
     // ocean at the domain fraction, phases in cycles per domain
     const float xf = (float)xl * 2.3283064365386963e-10f, yf = (float)yl * 2.3283064365386963e-10f;
     float uo = P.uo_x, vo = P.uo_y, zeta = 0.0f;
@@ -311,37 +387,34 @@ __global__ void k_truth32(DevState32 in, DevState32 out, Phys<float> P, TruthArg
     if (deep) atomicAdd(&a.ctrl->deep, 1ull);
 }
 
-__global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthArgs a, const int *bin,
-                          const int *start, const int *sorted, int nbx, int nby)
+__global__ void k_truth64(DevState64 in, DevState64 out, Phys<double> P, TruthArgs a, TruthBins tb)
 {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= a.n) return;
     const double Lx = a.g.Lx, Ly = a.g.Ly;
     const double xl = in.x[l], yl = in.y[l], ul = in.u[l], vl = in.v[l], wl = in.w[l], rl = in.r[l],
                  hl = in.h[l];
-    const int b = bin[l];
-    const int bx = b % nbx, by = b / nbx;
-    const NbRange nr = nb_range(nbx, nby);
     const bool walls = a.g.walls != 0;
     double fx = 0.0, fy = 0.0, tq = 0.0;
     unsigned deep = 0;
-    for (int oy = nr.y0; oy <= nr.y1; oy++) {
-        const int cy = (by + oy + nby) % nby;
-        for (int ox = nr.x0; ox <= nr.x1; ox++) {
-            if (walls && (bx + ox < 0 || bx + ox >= nbx)) continue;   // no image across a wall
-            const int cb = cy * nbx + (bx + ox + nbx) % nbx;
-            for (int k = start[cb]; k < start[cb + 1]; k++) {
-                const int j = sorted[k];
-                if (j == l) continue;
-                double dx = in.x[j] - xl, dy = in.y[j] - yl;
-                if (!walls) dx -= Lx * rint(dx / Lx);
-                dy -= Ly * rint(dy / Ly);
-                const double d2 = dx * dx + dy * dy;
-                contact_add(dx, dy, d2, rl, in.r[j], hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
-                            fx, fy, tq, deep);
-            }
+    auto scan_bin = [&](int cb) {
+        for (int k = tb.start[cb]; k < tb.start[cb + 1]; k++) {
+            const int j = tb.sorted[k];
+            if (j == l) continue;
+            double dx = in.x[j] - xl, dy = in.y[j] - yl;
+            if (!walls) dx -= Lx * rint(dx / Lx);
+            dy -= Ly * rint(dy / Ly);
+            const double d2 = dx * dx + dy * dy;
+            contact_add(dx, dy, d2, rl, in.r[j], hl, in.h[j], in.u[j] - ul, in.v[j] - vl, wl, in.w[j], P,
+                        fx, fy, tq, deep);
         }
-    }
+    };
+    const double reach = rl + (double)tb.r_split;
+    visit_bins(0, tb.nbx, tb.nby, dbin(xl, Lx, tb.nbx), dbin(yl, Ly, tb.nby), (float)(reach * tb.nbx / Lx),
+               (float)(reach * tb.nby / Ly), walls, scan_bin);
+    if (tb.nbx2 > 0)
+        visit_bins(tb.nbx * tb.nby, tb.nbx2, tb.nby2, dbin(xl, Lx, tb.nbx2), dbin(yl, Ly, tb.nby2), 0.99f, 0.99f,
+                   walls, scan_bin);   // bins wider than 2 r_max: every partner within one bin
     double uo, vo, zeta;
     ocean_f64(P, xl, yl, uo, vo, zeta);
     double ua, va;
@@ -407,7 +480,7 @@ __global__ void k_truth_cell_moments(const R *u, const R *v, const R *w, const R
 template <class BinF>
 cudaError_t counting_sort(TruthBins &b, long long n, BinF binf, cudaStream_t st)
 {
-    const int nbins = b.nbx * b.nby;
+    const int nbins = b.nbins();
     cudaError_t e;
     if ((e = cudaMemsetAsync(b.count, 0, sizeof(int) * nbins, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b.cursor, 0, sizeof(int) * nbins, st)) != cudaSuccess) return e;
@@ -415,7 +488,10 @@ cudaError_t counting_sort(TruthBins &b, long long n, BinF binf, cudaStream_t st)
     if ((e = bins_scan(b, nbins, st)) != cudaSuccess) return e;
     const int T = 256;
     if (n > 0) k_scatter<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.bin, b.start, b.cursor, b.sorted, n);
-    k_bin_sort<<<(nbins + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(b.start, b.sorted, nbins);
+    if (n < 4LL * nbins)   // few floes per bin on average: a thread per bin
+        k_bin_sort_sparse<<<(nbins + T - 1) / T, T, 0, st>>>(b.start, b.sorted, nbins);
+    else
+        k_bin_sort<<<(nbins + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, st>>>(b.start, b.sorted, nbins);
     return cudaGetLastError();
 }
 
@@ -439,10 +515,10 @@ cudaError_t launch_truth_step32(const DevState32 &in, const DevState32 &out, con
     const int T = 256;
     const unsigned G = (unsigned)((a.n + T - 1) / T);
     cudaError_t e = counting_sort(b, a.n, [&] {
-        k_bin32<<<G, T, 0, st>>>(in.xq, in.yq, b.nbx, b.nby, b.bin, b.count, a.n);
+        k_bin32<<<G, T, 0, st>>>(in.xq, in.yq, in.r, b, a.n);
     }, st);
     if (e != cudaSuccess) return e;
-    if (a.n > 0) k_truth32<<<G, T, 0, st>>>(in, out, P, a, b.bin, b.start, b.sorted, b.nbx, b.nby);
+    if (a.n > 0) k_truth32<<<G, T, 0, st>>>(in, out, P, a, b);
     return cudaGetLastError();
 }
 
@@ -452,10 +528,10 @@ cudaError_t launch_truth_step64(const DevState64 &in, const DevState64 &out, con
     const int T = 256;
     const unsigned G = (unsigned)((a.n + T - 1) / T);
     cudaError_t e = counting_sort(b, a.n, [&] {
-        k_bin64<<<G, T, 0, st>>>(in.x, in.y, a.g.Lx, a.g.Ly, b.nbx, b.nby, b.bin, b.count, a.n);
+        k_bin64<<<G, T, 0, st>>>(in.x, in.y, in.r, a.g.Lx, a.g.Ly, b, a.n);
     }, st);
     if (e != cudaSuccess) return e;
-    if (a.n > 0) k_truth64<<<G, T, 0, st>>>(in, out, P, a, b.bin, b.start, b.sorted, b.nbx, b.nby);
+    if (a.n > 0) k_truth64<<<G, T, 0, st>>>(in, out, P, a, b);
     return cudaGetLastError();
 }
 
@@ -465,7 +541,7 @@ cudaError_t launch_truth_moments32(const DevState32 &s, const Phys<float> &P, co
     const int T = 256;
     const unsigned G = (unsigned)((a.n + T - 1) / T);
     cudaError_t e = counting_sort(cells, a.n, [&] {
-        k_bin32<<<G, T, 0, st>>>(s.xq, s.yq, cells.nbx, cells.nby, cells.bin, cells.count, a.n);
+        k_bin32<<<G, T, 0, st>>>(s.xq, s.yq, nullptr, cells, a.n);
     }, st);
     if (e != cudaSuccess) return e;
     const int nc = cells.nbx * cells.nby;
@@ -481,7 +557,7 @@ cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, c
     const int T = 256;
     const unsigned G = (unsigned)((a.n + T - 1) / T);
     cudaError_t e = counting_sort(cells, a.n, [&] {
-        k_bin64<<<G, T, 0, st>>>(s.x, s.y, a.g.Lx, a.g.Ly, cells.nbx, cells.nby, cells.bin, cells.count, a.n);
+        k_bin64<<<G, T, 0, st>>>(s.x, s.y, nullptr, a.g.Lx, a.g.Ly, cells, a.n);
     }, st);
     if (e != cudaSuccess) return e;
     const int nc = cells.nbx * cells.nby;
@@ -566,7 +642,7 @@ cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f,
     const int T = 256;
     const unsigned G = (unsigned)((n + T - 1) / T);
     e = counting_sort(b, n, [&] {
-        k_bin64<<<G, T, 0, st>>>(x, y, g.Lx, g.Ly, b.nbx, b.nby, b.bin, b.count, n);
+        k_bin64<<<G, T, 0, st>>>(x, y, nullptr, g.Lx, g.Ly, b, n);
     }, st);
     if (e != cudaSuccess) return e;
     k_truth_cell_moments<double><<<(nbins + 127) / 128, 128, 0, st>>>(u, v, w, r, h, fd, n, mass_c, inertia_f,
