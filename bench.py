@@ -318,6 +318,10 @@ def main():
     ap.add_argument("--variant", type=int, default=-1, help="force the cell-kernel variant (profiling)")
     ap.add_argument("--profile", type=int, default=0,
                     help="no timing: build the model, run N fine steps and exit (for ncu captures)")
+    ap.add_argument("--truth", type=int, default=0,
+                    help="the truth DEM of --config alone: run N steps and exit (for ncu captures), "
+                         "or with --truth-time time it")
+    ap.add_argument("--truth-time", action="store_true", help="print the truth DEM's time per step")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -336,6 +340,19 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     msdem.load()
+    if args.truth:
+        tp = dict(s["params"], couple=0)
+        tm = msdem.Model(tp, s["floes"], msdem.MS_FP32)
+        tm.truth_step(s["dt"], args.truth)
+        out = {"truth_steps": args.truth}
+        if args.truth_time:
+            ms = min(tm.time_kernel(1, s["dt"], 50) for _ in range(3))
+            n = int(s["floes"]["x"].shape[0])
+            out.update({"floes": n, "ms_per_truth_step": ms, "floe_steps_per_s": n / (ms * 1e-3)})
+        tm.sync()
+        print(json.dumps(out), flush=True)
+        tm.close()
+        return
     p = s["params"]
     dt = s["dt"]
     N0 = int(p["N0"])
