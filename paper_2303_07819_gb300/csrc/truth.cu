@@ -512,7 +512,7 @@ int truth_launches(const TruthBins &) { return 2 /*memsets*/ + 1 + 3 + 1 + 1 + 1
 cudaError_t launch_truth_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                                 const TruthArgs &a, TruthBins &b, cudaStream_t st)
 {
-    const int T = 256;
+    const int T = 128;
     const unsigned G = (unsigned)((a.n + T - 1) / T);
     cudaError_t e = counting_sort(b, a.n, [&] {
         k_bin32<<<G, T, 0, st>>>(in.xq, in.yq, in.r, b, a.n);
