@@ -48,7 +48,7 @@ def profile_traffic():
     """DRAM bytes per fine step of the cell-step kernels from the committed
     ncu summary, if the kernel sources have not changed since (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "cell_step32_config2.txt")
+    path = os.path.join(ROOT, "profiles", "cell_step32_batched128x128.txt")
     if not os.path.exists(path):
         return None, None
     rec = {}
@@ -78,7 +78,7 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     t0 = time.perf_counter()
     Xs, Ys = [], []
     for sd in seeds:
-        ss = I.config2(seed=sd, nx=nx_train)
+        ss = I.batched_128x128(seed=sd, nx=nx_train)
         m = msdem.Model(ss["params"], ss["floes"], msdem.MS_FP32)
         m.step(ss["dt"], ss["params"]["N0"] * spin)
         X, Y = m.closure_collect(nint)
@@ -145,14 +145,14 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     return out
 
 
-def load_scenario(cfg: int):
+def load_scenario(name: str):
     from paper_2303_07819_gb300 import inputs as I
-    cache = os.path.join(tempfile.gettempdir(), f"msdem_inputs_cfg{cfg}_{I.BASE_SEED}.npz")
+    cache = os.path.join(tempfile.gettempdir(), f"msdem_inputs_{name}_{I.BASE_SEED}.npz")
     if os.path.exists(cache):
         z = np.load(cache, allow_pickle=True)
         s = z["s"].item()
         return s
-    s = I.CONFIGS[cfg]()
+    s = I.WORKLOADS[name]()
     try:
         np.savez(cache, s=np.array(s, dtype=object))
     except OSError:
@@ -313,13 +313,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--workload", default="batched_128x128",
+                    choices=["square_4x4", "powerlaw_32x32", "batched_128x128", "ensemble_16x256x256"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, cpu baseline and autotune")
     ap.add_argument("--variant", type=int, default=-1, help="force the cell-kernel variant (profiling)")
     ap.add_argument("--profile", type=int, default=0,
                     help="no timing: build the model, run N fine steps and exit (for ncu captures)")
     ap.add_argument("--truth", type=int, default=0,
-                    help="the truth DEM of --config alone: run N steps and exit (for ncu captures), "
+                    help="the truth DEM of --workload alone: run N steps and exit (for ncu captures), "
                          "or with --truth-time time it")
     ap.add_argument("--truth-time", action="store_true", help="print the truth DEM's time per step")
     args = ap.parse_args()
@@ -327,7 +328,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    s = load_scenario(args.config)
+    s = load_scenario(args.workload)
     if args.impl == "reference":
         run_reference(args, s, rank)
         return
@@ -405,7 +406,7 @@ def main():
 
     hbm, peak_kind, _ = peaks()
     traffic, prof = profile_traffic()
-    if args.config != 2:     # the committed capture is of the 128 x 128 batched workload only
+    if args.workload != "batched_128x128":     # the committed capture is of this workload only
         traffic, prof = None, None
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
     kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
@@ -461,7 +462,7 @@ def main():
         line["cpu_baseline"] = {"value": rate, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{ncells} random cells ({n} floes) x {steps} fine steps, "
                                           f"{tdt:.1f} s wall, FP64, OpenMP over cells"}
-        if args.config == 2:
+        if args.workload == "batched_128x128":
             line["closure"] = closure_eval(msdem, s)
     model.close()
     if rank == 0:

@@ -170,7 +170,7 @@ def _rescale_cells(radii: list, Ac: float, target: float) -> tuple:
     return out, np.array(scales)
 
 
-def config0(seed: int | None = None) -> dict:
+def square_4x4(seed: int | None = None) -> dict:
     """Plain msDEM, FP64: periodic 100 km square, 4 x 4 cells, 16 floes per cell,
     r ~ U[1, 2.5] km, h = 1 m; psi = U L sin sin with U = 0.1 m/s; no wind;
     dt = 10 s, 1000 steps; the truth DEM runs on the same floes."""
@@ -202,7 +202,7 @@ def _powerlaw_config(rng, nx, ny, L, counts, dt, nsteps, wind, wind_period, doma
             "meta": {"cell": cell, "radius_scale": scales}}
 
 
-def config1(seed: int | None = None, nx: int = 32) -> dict:
+def powerlaw_32x32(seed: int | None = None, nx: int = 32) -> dict:
     """32 x 32 cells over a periodic 400 km square (L_c = 12.5 km), floes per cell
     ~ Poisson(64), power-law radii 0.2-3 km, lognormal thickness (1.5, 0.5) m,
     8-mode ocean with 0.1 m/s RMS, uniform 10 m/s wind with Ca = 1.2e-3,
@@ -220,10 +220,10 @@ def lognormal_counts(rng, ncell: int, median: float, sigma: float, lo: int, hi: 
     return np.clip(n, lo, hi).astype(np.int64)
 
 
-def config2(seed: int | None = None, nx: int = 128) -> dict:
+def batched_128x128(seed: int | None = None, nx: int = 128) -> dict:
     """128 x 128 cells of 25 km (3200 km periodic square), floes per cell
     lognormal(median 96, sigma 0.69) clipped to [8, 1024] (~2.0M floes),
-    radius/thickness/ocean laws of config1, wind of 10 m/s rotating with a
+    radius/thickness/ocean laws of powerlaw_32x32, wind of 10 m/s rotating with a
     6 h period, dt = 5 s, 5000 steps.  No truth run, so only the cell metric
     is kept overlap-free."""
     rng = np.random.default_rng((BASE_SEED + 2) if seed is None else seed)
@@ -245,11 +245,11 @@ def stack_ensemble(scens: list) -> dict:
             "dt": scens[0]["dt"], "nsteps": scens[0]["nsteps"], "meta": {}}
 
 
-def config4(nreal: int = 16, nx: int = 256, seed: int | None = None) -> dict:
+def ensemble_16x256x256(nreal: int = 16, nx: int = 256, seed: int | None = None) -> dict:
     """Ensemble batch: nreal seeded realizations of an nx x nx grid of 25 km
     cells with few floes per cell, lognormal(median 6, sigma 0.69) clipped to
     [1, 64] (about 7.6 on average; 16 x 256^2 cells hold about 8M floes),
-    radius/thickness laws of config1, one ocean (8 modes) and one wind (10 m/s
+    radius/thickness laws of powerlaw_32x32, one ocean (8 modes) and one wind (10 m/s
     turning with a 6 h period) for all realizations, dt = 5 s."""
     base = (BASE_SEED + 4) if seed is None else seed
     L = 25e3 * nx
@@ -349,7 +349,7 @@ def random_cell_floes(rng: np.random.Generator, n: int, L: float, rmin: float, r
             "h": rng.uniform(0.5, 2.0, n)}
 
 
-CONFIGS = {0: config0, 1: config1, 2: config2, 4: config4}
+WORKLOADS = {f.__name__: f for f in (square_4x4, powerlaw_32x32, batched_128x128, ensemble_16x256x256)}
 
 
 def mlp_init(seed: int = BASE_SEED + 3, layers=((16, 128), (128, 128), (128, 128), (128, 4))) -> dict:

@@ -18,9 +18,9 @@ def ms():
 
 
 def realizations(R=3, nx=4):
-    """config1's laws on nx x nx cells, one seed per realization, the first
+    """The power-law workload's laws on nx x nx cells, one seed per realization, the first
     realization's ocean for all."""
-    scens = [I.config1(seed=100 + e, nx=nx) for e in range(R)]
+    scens = [I.powerlaw_32x32(seed=100 + e, nx=nx) for e in range(R)]
     for sc in scens[1:]:
         sc["params"]["modes"] = scens[0]["params"]["modes"]
     return scens
@@ -93,12 +93,12 @@ def test_ensemble_has_no_truth(ms):
 
 @pytest.mark.parametrize("variant", [2, 3])
 def test_small_cell_ensemble_runs(ms, orc, variant):
-    """Few floes per cell (configs[4]'s law, 1 to 64; cells of up to 32 floes
+    """Few floes per cell (the ensemble workload's law, 1 to 64; cells of up to 32 floes
     run packed several to a warp): 4 realizations of 16 x 16 cells through
     two coarse steps, one launch per step (variant 2) or per interval
     (variant 3), each realization's moments within the FP32 tolerance of its
     oracle model."""
-    ens = I.config4(nreal=4, nx=16)
+    ens = I.ensemble_16x256x256(nreal=4, nx=16)
     p = ens["params"]
     g = ms.Model(p, ens["floes"], ms.MS_FP32)
     g.set_launch(variant, 128, 0, 1.3)

@@ -2,7 +2,7 @@
 data from the particle path, the trained network against held-out particle
 data, and the coupled model with the closure against the particle-only model.
 
-Workload: configs[2]'s laws on 16 x 16 cells of 25 km (~31k floes), spun up
+Workload: the batched workload's laws on 16 x 16 cells of 25 km (~31k floes), spun up
 for 10 coarse intervals (the first gradual updates rescale radii by tens of
 percent where neighbouring cells differ, and the contacts that follow need
 several intervals to settle)."""
@@ -23,7 +23,7 @@ def trained():
     msdem.load()
     Xs, Ys = [], []
     for sd in (201, 202, 203):
-        s = I.config2(seed=sd, nx=16)
+        s = I.batched_128x128(seed=sd, nx=16)
         m = msdem.Model(s["params"], s["floes"], 0)
         m.step(s["dt"], s["params"]["N0"] * SPIN)
         X, Y = m.closure_collect(30)
@@ -53,7 +53,7 @@ def test_network_learns_translational_drag(trained):
     interval-mean drag of unseen cells (another seed)."""
     msdem, net, X, Y, losses, box = trained
     assert losses[-1] < 0.5 * losses[0]
-    s = I.config2(seed=204, nx=16)
+    s = I.batched_128x128(seed=204, nx=16)
     m = msdem.Model(s["params"], s["floes"], 0)
     m.step(s["dt"], s["params"]["N0"] * SPIN)
     Xh, Yh = m.closure_collect(10)
@@ -77,7 +77,7 @@ def test_zero_tolerance_is_the_particle_path(trained):
     """With tol = 0 every cell fails the residual check and runs the particle
     step: the floes are bitwise those of the model without the closure."""
     msdem, net, X, Y, losses, box = trained
-    s = I.config2(seed=205, nx=16)
+    s = I.batched_128x128(seed=205, nx=16)
     a = _run(msdem, s, -1, 0.0, net, box, 3)
     b = _run(msdem, s, 0, 0.0, net, box, 3)
     assert b.closure_stats()["closure_cell_intervals"] == 0
@@ -94,7 +94,7 @@ def test_network_closure_beats_mean_field(trained):
     mean-field drag of the cell-mean velocity and spin; mass stays within
     1e-3."""
     msdem, net, X, Y, losses, box = trained
-    s = I.config2(seed=206, nx=16)
+    s = I.batched_128x128(seed=206, nx=16)
     K = 5
     qp = _run(msdem, s, -1, 0.0, net, box, K).coupling()["q"]
     qn = _run(msdem, s, 0, 1e9, net, None, K).coupling()["q"]
@@ -107,7 +107,7 @@ def test_network_closure_beats_mean_field(trained):
 
 def test_fallback_fraction_follows_tolerance(trained):
     msdem, net, X, Y, losses, box = trained
-    s = I.config2(seed=207, nx=16)
+    s = I.batched_128x128(seed=207, nx=16)
     fr = []
     for tol in (0.02, 0.2, 1e9):
         # the first interval after attaching runs every DEM (the network needs

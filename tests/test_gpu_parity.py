@@ -33,8 +33,8 @@ def run_pair(orc, ms, scen, precision, nsteps, params=None):
 
 
 @pytest.mark.parametrize("nsteps", [1, 100, 250])
-def test_fp64_msdem_config0(orc, ms, nsteps):
-    s = I.config0()
+def test_fp64_msdem_square(orc, ms, nsteps):
+    s = I.square_4x4()
     o, g, p = run_pair(orc, ms, s, ms.MS_FP64, nsteps)
     e = rel_errors(g.moments(), o.moments(), p, 1e-12)
     assert e.max() <= TOL64, report(e)
@@ -46,8 +46,8 @@ def test_fp64_msdem_config0(orc, ms, nsteps):
             assert np.linalg.norm(a - b) <= TOL64 * max(np.linalg.norm(b), 1e-300), key
 
 
-def test_fp64_msdem_floes_config0(orc, ms):
-    s = I.config0()
+def test_fp64_msdem_floes_square(orc, ms):
+    s = I.square_4x4()
     o, g, p = run_pair(orc, ms, s, ms.MS_FP64, 100)
     fo, fg = o.floes(), g.floes()
     assert np.max(np.abs(fo["x"] - fg["x"])) < 1e-6 and np.max(np.abs(fo["y"] - fg["y"])) < 1e-6
@@ -55,18 +55,18 @@ def test_fp64_msdem_floes_config0(orc, ms):
         assert np.linalg.norm(fo[k] - fg[k]) <= TOL64 * np.linalg.norm(fo[k]) + 1e-20, k
 
 
-def test_fp32_msdem_config0(orc, ms):
-    s = I.config0()
+def test_fp32_msdem_square(orc, ms):
+    s = I.square_4x4()
     o, g, p = run_pair(orc, ms, s, ms.MS_FP32, 100)
     e = rel_errors(g.moments(), o.moments(), p, 1e-6)
     assert e.max() <= TOL32, report(e)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_msdem_config1_small(orc, ms, precision):
-    """config1's laws (power-law radii, lognormal thickness, 8 Fourier modes,
+def test_msdem_powerlaw_small(orc, ms, precision):
+    """The power-law workload's laws (power-law radii, lognormal thickness, 8 Fourier modes,
     wind) on 4 x 4 cells of 12.5 km, ~1000 floes, cells up to ~90 floes."""
-    s = I.config1(nx=4)
+    s = I.powerlaw_32x32(nx=4)
     o, g, p = run_pair(orc, ms, s, precision, 100)
     tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
     e = rel_errors(g.moments(), o.moments(), p, eps)
@@ -74,8 +74,8 @@ def test_msdem_config1_small(orc, ms, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_truth_config0(orc, ms, precision):
-    s = I.config0()
+def test_truth_square(orc, ms, precision):
+    s = I.square_4x4()
     p = s["params"]
     o = orc.Truth(p, s["floes"])
     g = ms.Model(p, s["floes"], precision)
@@ -86,8 +86,8 @@ def test_truth_config0(orc, ms, precision):
     assert e.max() <= tol, report(e)
 
 
-def test_truth_config1_small_fp64(orc, ms):
-    s = I.config1(nx=4)
+def test_truth_powerlaw_small_fp64(orc, ms):
+    s = I.powerlaw_32x32(nx=4)
     p = s["params"]
     o = orc.Truth(p, s["floes"])
     g = ms.Model(p, s["floes"], ms.MS_FP64)
@@ -102,7 +102,7 @@ def test_velocity_modes_msdem_and_truth(orc, ms, precision):
     """Compressible velocity-mode currents against the oracle: the Sec. 4.3
     current (real wave numbers, not periodic over the domain) on 96 x 48
     floes and 12 x 6 cells (64 per cell), msDEM over two coarse steps and the
-    truth DEM; then stream-function and velocity modes together on config1's
+    truth DEM; then stream-function and velocity modes together on the power-law workload's
     cells."""
     tol, eps = (TOL64, 1e-12) if precision == 1 else (TOL32, 1e-6)
     s = I.scenario4x(3, 96, 48, 12, 6)
@@ -116,8 +116,8 @@ def test_velocity_modes_msdem_and_truth(orc, ms, precision):
     gt.truth_step(s["dt"], 200)
     e = rel_errors(gt.truth_moments(), ot.moments(), p, eps)
     assert e.max() <= tol, report(e)
-    # stream-function modes and velocity modes together (config1 laws)
-    c = I.config1(nx=4)
+    # stream-function modes and velocity modes together (the power-law workload's laws)
+    c = I.powerlaw_32x32(nx=4)
     L = c["params"]["Lx"]
     vm = np.array([[0.03, -0.02, 2 * np.pi * 1.3 / L, 2 * np.pi * 0.4 / L, 0.3],
                    [-0.01, 0.04, 2 * np.pi * -0.7 / L, 2 * np.pi * 2.1 / L, 1.1]])
@@ -128,7 +128,7 @@ def test_velocity_modes_msdem_and_truth(orc, ms, precision):
 
 def ragged_scenario(counts, L_c=12.5e3, seed=5):
     """Cells with the given floe counts (0 allowed) on a small periodic grid,
-    power-law radii rescaled to 45% cover, config1 forcing."""
+    power-law radii rescaled to 45% cover, the power-law workload's forcing."""
     rng = np.random.default_rng(seed)
     nx = ny = int(np.ceil(np.sqrt(len(counts))))
     counts = list(counts) + [0] * (nx * ny - len(counts))
@@ -160,7 +160,7 @@ def test_ragged_and_empty_cells(orc, ms, precision):
 
 
 def test_no_floes(ms):
-    p = dict(I.config0()["params"])
+    p = dict(I.square_4x4()["params"])
     fl = {k: np.zeros(0) for k in ("x", "y", "theta", "u", "v", "omega", "r", "h")}
     g = ms.Model(p, fl, ms.MS_FP32)
     g.step(10.0, 150)
@@ -178,12 +178,12 @@ def test_largest_cell_fp32(orc, ms):
     assert e.max() <= 1e-5, report(e)
 
 
-def test_full_size_config2_sampled_cells(orc, ms):
-    """configs[2] at full size (~2.0M floes, 16,384 cells) on the GPU, one
+def test_full_size_batched_sampled_cells(orc, ms):
+    """The 128 x 128 batched workload at full size (~2.0M floes, 16,384 cells) on the GPU, one
     step; the oracle recomputes a sample of 48 cells (the largest and random
     ones) from those cells' floes alone, since the cells' DEMs are independent
     within a step."""
-    s = I.config2()
+    s = I.batched_128x128()
     p = s["params"]
     g = ms.Model(p, s["floes"], ms.MS_FP32)
     g.step(s["dt"], 1)
@@ -205,7 +205,7 @@ def test_full_size_config2_sampled_cells(orc, ms):
 
 
 def test_graph_replay_equals_single_steps(ms):
-    s = I.config0()
+    s = I.square_4x4()
     a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     a.step(s["dt"], 230)
@@ -222,7 +222,7 @@ def test_resident_run_equals_single_steps(ms):
     interval (one launch per interval on the graph path) and runs one step
     per launch otherwise: the two give the same floes and moments bitwise,
     across coarse steps and gradual updates."""
-    s = I.config2(seed=7, nx=16)
+    s = I.batched_128x128(seed=7, nx=16)
     p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
     a = ms.Model(p, s["floes"], ms.MS_FP32)
     b = ms.Model(p, s["floes"], ms.MS_FP32)
@@ -247,7 +247,7 @@ def test_neighbour_lists_graph_equals_single_steps(ms):
     give the same floes bitwise, across list rebuilds, coarse steps and
     gradual updates; after set_floes the lists are rebuilt (a moved floe must
     not keep stale partners)."""
-    s = I.config2(seed=9, nx=16)
+    s = I.batched_128x128(seed=9, nx=16)
     p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
     a = ms.Model(p, s["floes"], ms.MS_FP32)
     b = ms.Model(p, s["floes"], ms.MS_FP32)
@@ -280,7 +280,7 @@ def test_launch_variants_agree(ms):
     """Threads per block and the persistent work queue change only the order
     of the moment reduction, never a floe's arithmetic: floes agree bitwise
     until the first coarse step, which feeds the reduced moments back."""
-    s = I.config1(nx=4)
+    s = I.powerlaw_32x32(nx=4)
     ref = refm = None
     for threads in (64, 128, 256):
         for persistent in (0, 1):
@@ -299,7 +299,7 @@ def test_launch_variants_agree(ms):
 
 
 def test_autotune_keeps_results(ms):
-    s = I.config1(nx=8)
+    s = I.powerlaw_32x32(nx=8)
     a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     best = b.autotune(s["dt"], reps=3)
@@ -316,7 +316,7 @@ def test_autotune_keeps_results(ms):
 
 
 def test_time_kernel_leaves_state(ms):
-    s = I.config0()
+    s = I.square_4x4()
     a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     a.step(s["dt"], 5)
     before = a.floes()
@@ -330,7 +330,7 @@ def test_time_kernel_leaves_state(ms):
 
 
 def test_argument_errors(ms):
-    s = I.config0()
+    s = I.square_4x4()
     g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     g.step(10.0, 1)
     with pytest.raises(ms.MsError) as e:
@@ -351,7 +351,7 @@ def test_argument_errors(ms):
 
 
 def test_set_floes_roundtrip(ms):
-    s = I.config0()
+    s = I.square_4x4()
     g = ms.Model(s["params"], s["floes"], ms.MS_FP64)
     g.step(10.0, 7)
     f = g.floes()
@@ -429,9 +429,9 @@ def test_neighbour_list_overflow(orc, ms):
 
 
 def test_fp32_variants_agree_one_step(ms):
-    """One step of configs[1]'s laws on 16 x 16 cells: the three pair searches
+    """One step of the power-law workload's laws on 16 x 16 cells: the pair searches
     find the same contacts, so moments agree to FP32 summation order."""
-    s = I.config1(nx=16)
+    s = I.powerlaw_32x32(nx=16)
     res = []
     for variant in (0, 1, 2, 3, 4):
         g = ms.Model(s["params"], s["floes"], ms.MS_FP32)

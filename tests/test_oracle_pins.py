@@ -466,7 +466,7 @@ def test_p8_coarse_initialisation_and_window(orc):
 
 # ------------------------------------------------------------ P9 moments
 def test_p9_moments_match_numpy_reduction(orc):
-    s = I.config0()
+    s = I.square_4x4()
     m = orc.Model(s["params"], s["floes"])
     m.step(s["dt"], 30)
     mo = m.moments()
@@ -490,7 +490,7 @@ def test_p9_moments_match_numpy_reduction(orc):
 
 def test_single_cell_model_equals_truth(orc):
     """With one coarse cell and no coupling the localised DEM is the truth DEM."""
-    s = I.config0()
+    s = I.square_4x4()
     p = dict(s["params"], nx=1, ny=1, couple=0)
     a = orc.Model(p, s["floes"])
     b = orc.Truth(p, s["floes"])

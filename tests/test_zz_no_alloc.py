@@ -39,7 +39,7 @@ def test_noalloc_moments_match_existing_entry_points():
     torch = pytest.importorskip("torch")
     from paper_2303_07819_gb300 import msdem as ms
     ms.load()
-    s = I.config0()
+    s = I.square_4x4()
     p = s["params"]
     m = ms.Model(p, s["floes"], ms.MS_FP64)
 
