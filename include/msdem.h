@@ -341,6 +341,27 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y);
 /* host out[4]: closure cell-intervals so far, cells, mode, coarse intervals done. */
 int ms_closure_stats(ms_model *m, int64_t *out);
 
+/* Checkpoint ("save data", Algorithm 1): write the model's whole state to
+ * the file at host path `path`: the floes in the model's cell layout, the
+ * per-cell moments, window sums, coarse state and gradual-update targets, the
+ * device control block (step counters, flags), dt, the launch choice, the
+ * FP32 candidate lists, and the truth DEM's state and last drag.  The file
+ * holds device-order raw values of this library and is read back only by
+ * ms_load.  MS_ERR_STATE while a closure is attached; MS_ERR_ARG if the file
+ * cannot be written; MS_ERR_CUDA if reading the device state fails. */
+int ms_save(ms_model *m, const char *path);
+
+/* Resume from a checkpoint written by ms_save, into a model made by ms_init
+ * with the same grid, boundary, precision, number of floes and floes per
+ * cell (and, for an exact resume, the same floes, forcing and laws as the
+ * saved model): it then continues as the saved model would have, bit for
+ * bit, and restores the saved launch choice.  MS_ERR_ARG for a file that is
+ * not such a checkpoint, is truncated, or belongs to another model (after a
+ * failure in the middle of the state the model's state is undefined: load
+ * again or call ms_set_floes); MS_ERR_STATE while a closure is attached;
+ * MS_ERR_CUDA if writing the device state fails. */
+int ms_load(ms_model *m, const char *path);
+
 /* Release the model's device memory, graphs, events and stream. */
 void ms_free(ms_model *m);
 

@@ -817,6 +817,183 @@ extern "C" {
 
 const char *ms_last_error(void) { return g_err.c_str(); }
 
+// ---------------------------------------------------------------- checkpoint
+// File layout: an 8-byte tag, then (for every item below, in this order) an
+// int64 byte count followed by the bytes.  Items: the header (precision,
+// sizes, schedule counters, dt, launch choice), the cell offsets (the layout
+// the state is stored in), the msDEM state in cell order, the per-cell
+// moments, window sums, coarse state and gradual-update targets, the device
+// control block, the candidate lists (FP32), and the truth DEM's current
+// state with its last drag.
+namespace {
+constexpr char CK_TAG[8] = {'M', 'S', 'D', 'E', 'M', 'C', 'K', '1'};
+
+struct CkHeader {
+    int32_t precision, nens, walls, variant, threads, persistent;
+    int64_t n, ncell, steps, truth_steps;
+    double dt, truth_dt, bin_beta;
+};
+
+struct CkItem {
+    void *dev;      // device pointer, or nullptr for a host item
+    void *host;
+    size_t bytes;
+};
+}  // namespace
+
+// the device arrays of a model's state, in file order
+static std::vector<CkItem> ck_items(ms_model *m)
+{
+    std::vector<CkItem> it;
+    const size_t n = (size_t)m->n, nc = (size_t)m->ncell;
+    auto dev = [&](void *p, size_t bytes) { it.push_back({p, nullptr, bytes}); };
+    if (m->precision == MS_FP64) {
+        double *a[8] = {m->s64.x, m->s64.y, m->s64.th, m->s64.u, m->s64.v, m->s64.w, m->s64.r, m->s64.h};
+        for (double *p : a) dev(p, 8 * n);
+    } else {
+        dev(m->s32.xq, 4 * n);
+        dev(m->s32.yq, 4 * n);
+        float *a[6] = {m->s32.th, m->s32.u, m->s32.v, m->s32.w, m->s32.r, m->s32.h};
+        for (float *p : a) dev(p, 4 * n);
+    }
+    dev(m->d_mom, sizeof(double) * NMOM * nc);
+    dev(m->d_win, sizeof(double) * NWIN * nc);
+    dev(m->d_q0, sizeof(double) * 4 * nc);
+    dev(m->d_tgt, sizeof(double) * 4 * nc);
+    dev(m->d_ctrl, sizeof(Ctrl));
+    if (m->precision == MS_FP32 && m->nl.head) {
+        dev(m->nl.head, sizeof(uint4) * n);
+        dev(m->nl.tail, sizeof(uint4) * NLT * n);
+        dev(m->nl.xb, sizeof(uint2) * n);
+        dev(m->nl.cstep, sizeof(long long) * nc);
+        dev(m->nl.skin, sizeof(float) * nc);
+    }
+    if (m->g.nens == 1 && m->n > 0) {
+        const size_t es = m->precision == MS_FP64 ? 8 : 4;
+        if (m->precision == MS_FP64) {
+            const DevState64 &t = m->t64[m->tcur];
+            double *a[8] = {t.x, t.y, t.th, t.u, t.v, t.w, t.r, t.h};
+            for (double *p : a) dev(p, 8 * n);
+        } else {
+            const DevState32 &t = m->t32[m->tcur];
+            dev(t.xq, 4 * n);
+            dev(t.yq, 4 * n);
+            float *a[6] = {t.th, t.u, t.v, t.w, t.r, t.h};
+            for (float *p : a) dev(p, 4 * n);
+        }
+        dev(m->d_fd, es * 3 * n);
+    }
+    return it;
+}
+
+int ms_save(ms_model *m, const char *path)
+{
+    if (!m || !path) return fail(MS_ERR_ARG, "NULL argument");
+    if (hybrid_on(m)) return fail(MS_ERR_STATE, "detach the closure before a checkpoint");
+    CK(cudaStreamSynchronize(m->stream));
+    CkHeader h{};
+    h.precision = m->precision;
+    h.nens = m->g.nens;
+    h.walls = m->g.walls;
+    h.variant = m->cl.variant;
+    h.threads = m->cl.threads;
+    h.persistent = m->cl.persistent;
+    h.n = m->n;
+    h.ncell = m->ncell;
+    h.steps = m->steps;
+    h.truth_steps = m->truth_steps;
+    h.dt = m->dt;
+    h.truth_dt = m->truth_dt;
+    h.bin_beta = m->cl.bin_beta;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(MS_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = std::fwrite(CK_TAG, 1, 8, f) == 8;
+    auto put = [&](const void *p, size_t bytes) {
+        const int64_t b = (int64_t)bytes;
+        ok = ok && std::fwrite(&b, sizeof(b), 1, f) == 1 && (bytes == 0 || std::fwrite(p, 1, bytes, f) == bytes);
+    };
+    put(&h, sizeof(h));
+    put(m->h_off.data(), sizeof(int) * m->h_off.size());
+    std::vector<unsigned char> buf;
+    for (const CkItem &it : ck_items(m)) {
+        buf.resize(it.bytes);
+        if (it.bytes && cudaMemcpy(buf.data(), it.dev, it.bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            std::fclose(f);
+            return fail(MS_ERR_CUDA, "reading the state for the checkpoint failed");
+        }
+        put(buf.data(), it.bytes);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? MS_OK : fail(MS_ERR_ARG, "writing %s failed", path);
+}
+
+int ms_load(ms_model *m, const char *path)
+{
+    if (!m || !path) return fail(MS_ERR_ARG, "NULL argument");
+    if (hybrid_on(m)) return fail(MS_ERR_STATE, "detach the closure before loading a checkpoint");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(MS_ERR_ARG, "cannot open %s", path);
+    char tag[8];
+    bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, CK_TAG, 8) == 0;
+    auto get = [&](void *p, size_t bytes) {
+        int64_t b = -1;
+        ok = ok && std::fread(&b, sizeof(b), 1, f) == 1 && b == (int64_t)bytes &&
+             (bytes == 0 || std::fread(p, 1, bytes, f) == bytes);
+    };
+    CkHeader h{};
+    get(&h, sizeof(h));
+    if (!ok) {
+        std::fclose(f);
+        return fail(MS_ERR_ARG, "%s is not a checkpoint of this library", path);
+    }
+    if (h.precision != m->precision || h.nens != m->g.nens || h.walls != m->g.walls || h.n != m->n ||
+        h.ncell != m->ncell) {
+        std::fclose(f);
+        return fail(MS_ERR_ARG, "checkpoint of another model (precision, floes, cells or boundary differ)");
+    }
+    std::vector<int> off(m->h_off.size());
+    get(off.data(), sizeof(int) * off.size());
+    if (!ok || off != m->h_off) {
+        std::fclose(f);
+        return fail(MS_ERR_ARG, "checkpoint of another floe layout (the floes per cell differ)");
+    }
+    // the saved launch first (configuring a launch forgets the candidate
+    // lists; the checkpoint's lists are restored below)
+    CellLaunch c = m->cl;
+    c.variant = h.variant;
+    c.threads = h.threads;
+    c.persistent = h.persistent;
+    c.bin_beta = (float)h.bin_beta;
+    int rc = configure_launch(m, c);
+    if (rc) {
+        std::fclose(f);
+        return rc;
+    }
+    CK(cudaStreamSynchronize(m->stream));
+    m->tcur = 0;   // the truth state goes into the first copy
+    std::vector<unsigned char> buf;
+    for (const CkItem &it : ck_items(m)) {
+        buf.resize(it.bytes);
+        get(buf.data(), it.bytes);
+        if (!ok) break;
+        if (it.bytes && cudaMemcpy(it.dev, buf.data(), it.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            std::fclose(f);
+            return fail(MS_ERR_CUDA, "writing the checkpoint's state to the device failed");
+        }
+    }
+    std::fclose(f);
+    if (!ok) {
+        CK(invalidate_lists(m));
+        return fail(MS_ERR_ARG, "%s is truncated or of another model", path);
+    }
+    m->steps = h.steps;
+    m->truth_steps = h.truth_steps;
+    m->dt = h.dt;
+    m->truth_dt = h.truth_dt;
+    drop_graph(m);
+    return MS_OK;
+}
+
 int ms_probe_fp32(int32_t reps, double *tflops)
 {
     if (reps < 1 || !tflops) return fail(MS_ERR_ARG, "probe needs reps >= 1 and an output");

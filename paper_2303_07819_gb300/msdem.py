@@ -58,7 +58,7 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
-           "ms_probe_fp32"]
+           "ms_probe_fp32", "ms_save", "ms_load"]
 
 
 def lib_path() -> str:
@@ -99,6 +99,8 @@ def load(path: str | None = None):
     L.ms_closure_collect.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float)]
     L.ms_closure_stats.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_probe_fp32.argtypes = [C.c_int32, _dp]
+    L.ms_save.argtypes = [vp, C.c_char_p]
+    L.ms_load.argtypes = [vp, C.c_char_p]
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
@@ -237,6 +239,14 @@ class Model:
         out = C.c_double(0.0)
         _check(load().ms_time_kernel(self._h, int(which), float(dt), int(reps), C.byref(out)))
         return out.value
+
+    def save(self, path: str) -> None:
+        """Checkpoint the model's whole state to `path` (ms_save)."""
+        _check(load().ms_save(self._h, os.fsencode(path)))
+
+    def load_checkpoint(self, path: str) -> None:
+        """Resume from a checkpoint written by save() (ms_load)."""
+        _check(load().ms_load(self._h, os.fsencode(path)))
 
     def set_launch(self, variant: int = 0, threads: int = 128, persistent: int = 0,
                    bin_beta: float = 1.0) -> None:
