@@ -12,6 +12,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "classes.cuh"
 #include "common.cuh"
 #include "../../include/msdem.h"
@@ -41,6 +43,16 @@ int msd::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
     } while (0)
 
 static const double PI_D = 3.14159265358979323846;
+
+// NVTX range over a host-side phase (API call, graph replay, coarse step):
+// profilers attribute the kernels launched inside it to the phase; without a
+// profiler attached the calls cost next to nothing.
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
 
 struct ms_model {
     int precision = 0;
@@ -889,6 +901,7 @@ static std::vector<CkItem> ck_items(ms_model *m)
 int ms_save(ms_model *m, const char *path)
 {
     if (!m || !path) return fail(MS_ERR_ARG, "NULL argument");
+    Trace tr("msdem.save");
     if (hybrid_on(m)) return fail(MS_ERR_STATE, "detach the closure before a checkpoint");
     CK(cudaStreamSynchronize(m->stream));
     CkHeader h{};
@@ -930,6 +943,7 @@ int ms_save(ms_model *m, const char *path)
 int ms_load(ms_model *m, const char *path)
 {
     if (!m || !path) return fail(MS_ERR_ARG, "NULL argument");
+    Trace tr("msdem.load");
     if (hybrid_on(m)) return fail(MS_ERR_STATE, "detach the closure before loading a checkpoint");
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(MS_ERR_ARG, "cannot open %s", path);
@@ -1242,6 +1256,7 @@ int ms_sync(ms_model *m)
 static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    Trace tr("msdem.step");
     if (!(dt > 0.0) || !isfin(dt)) return fail(MS_ERR_ARG, "dt must be positive and finite");
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
     if (m->dt == 0.0) m->dt = dt;
@@ -1259,17 +1274,29 @@ static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
                     continue;
                 }
             }
-            CK(cudaGraphLaunch(m->gexec, m->stream));
+            {
+                Trace ti("msdem.interval (graph)");
+                CK(cudaGraphLaunch(m->gexec, m->stream));
+            }
             m->replays++;
             m->steps += N;
             nsteps -= N;
             continue;
         }
-        if (i_local == 0) CK(launch_interval_start(m));
-        CK(launch_step(m, i_local, false));
+        if (i_local == 0) {
+            Trace ts("msdem.interval start");
+            CK(launch_interval_start(m));
+        }
+        {
+            Trace tf("msdem.fine step");
+            CK(launch_step(m, i_local, false));
+        }
         m->steps++;
         nsteps--;
-        if (m->steps % N == 0) CK(launch_interval_end(m));
+        if (m->steps % N == 0) {
+            Trace te("msdem.interval end (coarse step)");
+            CK(launch_interval_end(m));
+        }
     }
     return MS_OK;
 }
@@ -1305,6 +1332,7 @@ int ms_coupling(ms_model *m, double *q, double *targets, double *window, int64_t
 
 static int download(ms_model *m, bool truth, double *out)
 {
+    Trace tr("msdem.get_floes");
     const long long n = m->n;
     if (n == 0) return MS_OK;
     const int nx = m->g.nx;
@@ -1377,6 +1405,7 @@ int ms_truth_get_floes(ms_model *m, double *out)
 int ms_set_floes(ms_model *m, const ms_floes *floes)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    Trace tr("msdem.set_floes");
     int rc = validate_floes(floes, m->n);
     if (rc) return rc;
     const long long left = host_first(m->n, [&](long long l) {
@@ -1417,6 +1446,7 @@ int ms_truth_step(ms_model *m, double dt, int64_t nsteps)
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
     if (m->truth_dt == 0.0) m->truth_dt = dt;
     else if (dt != m->truth_dt) return fail(MS_ERR_ARG, "dt differs from the truth model's dt");
+    Trace tr("msdem.truth steps");
     for (long long k = 0; k < nsteps; k++) {
         CK(truth_one(m, m->tcur, 1 - m->tcur, m->truth_steps));
         m->tcur = 1 - m->tcur;
