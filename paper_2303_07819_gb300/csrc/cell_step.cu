@@ -1303,8 +1303,9 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
         const float r = pl.x, h = pl.y;
         const float mass = P.mass_c * r * r * h;
         const float I = P.inertia_f * mass * r * r;
-        float un = pl.z + dt * (fx / mass);
-        float vn = pl.w + dt * (fy / mass);
+        const float dtm = dt / mass;
+        float un = pl.z + dtm * fx;
+        float vn = pl.w + dtm * fy;
         float wn = wl + dt * (tq / I);
         float rn = r;
         if (bs.ramp) {
