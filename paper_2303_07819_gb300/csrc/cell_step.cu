@@ -19,6 +19,13 @@ namespace msd {
 namespace {
 
 constexpr float TWO32F = 4294967296.0f;
+
+// A large floe's search reach, capped at the cell side of its axis; NaN (a
+// diverged state) takes the whole side.  Positions lie in [0, L), so the bin
+// bounds derived from a capped reach stay within [-nb - 1, 2 nb + 1]: the
+// integer width of the range cannot overflow, and a range narrower than the
+// cell wraps into the bin table at most once on either side.
+__device__ __forceinline__ float reach_cap(float reach, float L) { return reach < L ? reach : L; }
 constexpr float INV2_32F = 2.3283064365386963e-10f;
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -655,8 +662,9 @@ k_cell_step32_binned(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc
                 bx0 = bx - 1; bx1 = bx + 1; by0 = by - 1; by1 = by + 1;
             } else if (nb) {
                 const float reach = 1.001f * (pl.z + Rs + skin);
-                bx0 = (int)floorf((pl.x - reach) / Bx); bx1 = (int)floorf((pl.x + reach) / Bx);
-                by0 = (int)floorf((pl.y - reach) / By); by1 = (int)floorf((pl.y + reach) / By);
+                const float rx = reach_cap(reach, Lx), ry = reach_cap(reach, Ly);
+                bx0 = (int)floorf((pl.x - rx) / Bx); bx1 = (int)floorf((pl.x + rx) / Bx);
+                by0 = (int)floorf((pl.y - ry) / By); by1 = (int)floorf((pl.y + ry) / By);
                 if (bx1 - bx0 + 1 >= nb) { bx0 = 0; bx1 = nb - 1; }
                 if (by1 - by0 + 1 >= nb) { by0 = 0; by1 = nb - 1; }
             } else {
@@ -1045,8 +1053,9 @@ k_cell_step32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
         } else if (nb) {
             // a large floe: the small floes' bins within its reach
             const float reach = 1.001f * (pl.z + Rs);
-            int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
-            int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+            const float rx = reach_cap(reach, Lx), ry = reach_cap(reach, Ly);
+            int bx0 = (int)floorf((pl.x - rx) / Bx), bx1 = (int)floorf((pl.x + rx) / Bx);
+            int by0 = (int)floorf((pl.y - ry) / By), by1 = (int)floorf((pl.y + ry) / By);
             const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
             if (allx) { bx0 = 0; bx1 = nb - 1; }
             if (ally) { by0 = 0; by1 = nb - 1; }
@@ -1476,8 +1485,9 @@ k_cell_step32_wlist(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc,
             } else if (nb) {
                 const float xl = (float)ql.x * sx, yl = (float)ql.y * sy;
                 const float reach = 1.001f * (pl.x + Rs + skin);
-                int bx0 = (int)floorf((xl - reach) / Bx), bx1 = (int)floorf((xl + reach) / Bx);
-                int by0 = (int)floorf((yl - reach) / By), by1 = (int)floorf((yl + reach) / By);
+                const float rx = reach_cap(reach, Lx), ry = reach_cap(reach, Ly);
+                int bx0 = (int)floorf((xl - rx) / Bx), bx1 = (int)floorf((xl + rx) / Bx);
+                int by0 = (int)floorf((yl - ry) / By), by1 = (int)floorf((yl + ry) / By);
                 const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
                 if (allx) { bx0 = 0; bx1 = nb - 1; }
                 if (ally) { by0 = 0; by1 = nb - 1; }
@@ -1768,8 +1778,9 @@ k_cell_run32_warp(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, i
                 }
             } else if (nb) {
                 const float reach = 1.001f * (pl.z + Rs);
-                int bx0 = (int)floorf((pl.x - reach) / Bx), bx1 = (int)floorf((pl.x + reach) / Bx);
-                int by0 = (int)floorf((pl.y - reach) / By), by1 = (int)floorf((pl.y + reach) / By);
+                const float rx = reach_cap(reach, Lx), ry = reach_cap(reach, Ly);
+                int bx0 = (int)floorf((pl.x - rx) / Bx), bx1 = (int)floorf((pl.x + rx) / Bx);
+                int by0 = (int)floorf((pl.y - ry) / By), by1 = (int)floorf((pl.y + ry) / By);
                 const bool allx = bx1 - bx0 + 1 >= nb, ally = by1 - by0 + 1 >= nb;
                 if (allx) { bx0 = 0; bx1 = nb - 1; }
                 if (ally) { by0 = 0; by1 = nb - 1; }

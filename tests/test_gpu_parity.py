@@ -169,6 +169,27 @@ def test_no_floes(ms):
     assert np.all(g.truth_moments() == 0.0)
 
 
+def test_diverged_state_is_reported(ms):
+    """Every floe given 1e12 m/s (finite, so the upload accepts it): drag and
+    forward Euler drive the state through huge finite values to inf and NaN
+    within a few steps.  The list rebuilds meanwhile see a skin of 4 |v|max
+    dt n_t far beyond the cell; the large-floe bin search caps its reach at
+    the cell side, so packed, warp-list and block-list cells all finish their
+    steps, the step reports MS_ERR_UNSTABLE, and the context stays usable."""
+    s = ragged_scenario([0, 20, 100, 300, 700], seed=31)
+    g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    g.set_launch(4, 128, 0, 1.3)
+    g.step(s["dt"], 3)
+    f = g.floes()
+    f["u"][:] = 1.0e12
+    g.set_floes(f)
+    with pytest.raises(ms.MsError) as e:
+        g.step(s["dt"], 30)
+    assert e.value.code == -3, str(e.value)
+    assert g.moments().shape[0] == 9
+    assert np.all(np.isfinite(ms.Model(s["params"], s["floes"], ms.MS_FP32).moments()))
+
+
 def test_largest_cell_fp32(orc, ms):
     """A cell at the 4096-floe limit (several shared-memory tiles), one step."""
     s = ragged_scenario([4096], L_c=100e3, seed=9)
