@@ -16,6 +16,7 @@
 
 #include "classes.cuh"
 #include "common.cuh"
+#include "upload.cuh"
 #include "../../include/msdem.h"
 
 using namespace msd;
@@ -68,6 +69,11 @@ struct ms_model {
     std::vector<int> h_off, h_order, h_cell_of_orig;
     std::vector<long long> h_orig;
     int *d_off = nullptr, *d_order = nullptr;
+    // uploads: the caller's arrays as sent ([8][n] FP64), orig and cell of
+    // the caller's floes on the device, the checks' first failing indices
+    double *d_raw = nullptr;
+    int *d_orig = nullptr, *d_cell_of = nullptr;
+    unsigned long long *d_first = nullptr;
     // msDEM state and its scratch copy for out-of-place timing
     DevState32 s32{}, x32{};
     NbLists nl{}, xnl{};          // candidate lists of s32 and of the timing copy x32
@@ -240,7 +246,8 @@ static long long host_first(long long n, B &&bad)
     return f < n ? f : n;
 }
 
-static int validate_floes(const ms_floes *f, long long expect_n)
+// the checks that need no per-floe pass: pointers and counts
+static int check_floe_args(const ms_floes *f, long long expect_n)
 {
     if (!f) return fail(MS_ERR_ARG, "floes is NULL");
     if (f->n < 0) return fail(MS_ERR_ARG, "floes->n = %lld < 0", (long long)f->n);
@@ -249,76 +256,76 @@ static int validate_floes(const ms_floes *f, long long expect_n)
     if (f->n > 0 && (!f->x || !f->y || !f->theta || !f->u || !f->v || !f->omega || !f->r || !f->h))
         return fail(MS_ERR_ARG, "a floe array is NULL");
     if (f->n > (long long)0x7fffffff) return fail(MS_ERR_ARG, "more than 2^31-1 floes");
-    auto finite = [f](long long l) {
-        return isfin(f->x[l]) && isfin(f->y[l]) && isfin(f->theta[l]) && isfin(f->u[l]) && isfin(f->v[l]) &&
-               isfin(f->omega[l]) && isfin(f->r[l]) && isfin(f->h[l]);
-    };
-    const long long l = host_first(f->n, [&](long long k) { return !finite(k) || !(f->r[k] > 0.0) || !(f->h[k] > 0.0); });
+    return MS_OK;
+}
+
+static bool floe_finite(const ms_floes *f, long long l)
+{
+    return isfin(f->x[l]) && isfin(f->y[l]) && isfin(f->theta[l]) && isfin(f->u[l]) && isfin(f->v[l]) &&
+           isfin(f->omega[l]) && isfin(f->r[l]) && isfin(f->h[l]);
+}
+
+static int validate_floes(const ms_floes *f, long long expect_n)
+{
+    const int rc = check_floe_args(f, expect_n);
+    if (rc) return rc;
+    const long long l = host_first(f->n, [&](long long k) {
+        return !floe_finite(f, k) || !(f->r[k] > 0.0) || !(f->h[k] > 0.0);
+    });
     if (l < f->n) {
-        if (!finite(l)) return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
+        if (!floe_finite(f, l)) return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
         return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
     }
+    return MS_OK;
+}
+
+static UpGeom up_geom(const ms_model *m)
+{
+    UpGeom g;
+    g.n = m->n;
+    g.nx = m->g.nx;
+    g.ny = m->g.ny;
+    g.Lx = m->g.Lx;
+    g.Ly = m->g.Ly;
+    g.Lcx = m->g.Lcx;
+    g.Lcy = m->g.Lcy;
+    return g;
+}
+
+// the caller's eight arrays into the pinned stage (all host cores), then to
+// the device's raw copy in one transfer (queued on the model's stream)
+static int send_raw(ms_model *m, const ms_floes *f)
+{
+    const long long n = m->n;
+    double *st = (double *)stage(m, sizeof(double) * 8 * n);
+    if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(64 * n));
+    const double *src[8] = {f->x, f->y, f->theta, f->u, f->v, f->omega, f->r, f->h};
+    host_parallel(n, [&](long long k0, long long k1) {
+        for (int a = 0; a < 8; a++) std::memcpy(st + a * n + k0, src[a] + k0, sizeof(double) * (k1 - k0));
+    });
+    CK(cudaMemcpyAsync(m->d_raw, st, sizeof(double) * 8 * n, cudaMemcpyHostToDevice, m->stream));
+    return MS_OK;
+}
+
+// the raw copy (already checked and assigned to cells) into the msDEM layout
+static int raw_to_state(ms_model *m)
+{
+    if (m->n == 0) return MS_OK;
+    const UpGeom g = up_geom(m);
+    if (m->precision == MS_FP64)
+        CK(launch_floes_to_cells64(m->d_raw, m->d_orig, m->d_cell_of, g, m->s64, m->stream));
+    else
+        CK(launch_floes_to_cells32(m->d_raw, m->d_orig, m->d_cell_of, g, m->s32, m->stream));
     return MS_OK;
 }
 
 // upload floes (already validated and assigned) into the msDEM layout
 static int upload_model_state(ms_model *m, const ms_floes *f)
 {
-    const long long n = m->n;
-    const int nx = m->g.nx;
-    if (n == 0) return MS_OK;
-    if (m->precision == MS_FP64) {
-        double *st = (double *)stage(m, sizeof(double) * 8 * n);
-        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(64 * n));
-        host_parallel(n, [&](long long k0, long long k1) {
-            for (long long k = k0; k < k1; k++) {
-                const long long l = m->h_orig[k];
-                const int c = m->h_cell_of_orig[l];
-                const int ix = c % nx, iy = c / nx;
-                const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
-                const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
-                st[k] = Xw - ix * m->g.Lcx;
-                st[n + k] = Yw - iy * m->g.Lcy;
-                st[2 * n + k] = f->theta[l];
-                st[3 * n + k] = f->u[l];
-                st[4 * n + k] = f->v[l];
-                st[5 * n + k] = f->omega[l];
-                st[6 * n + k] = f->r[l];
-                st[7 * n + k] = f->h[l];
-            }
-        });
-        double *dst[8] = {m->s64.x, m->s64.y, m->s64.th, m->s64.u, m->s64.v, m->s64.w, m->s64.r, m->s64.h};
-        for (int a = 0; a < 8; a++)
-            CK(cudaMemcpyAsync(dst[a], st + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
-    } else {
-        unsigned char *st = (unsigned char *)stage(m, sizeof(float) * 8 * n);
-        if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(32 * n));
-        uint32_t *qx = (uint32_t *)st, *qy = qx + n;
-        float *fl = (float *)(qy + n);
-        host_parallel(n, [&](long long k0, long long k1) {
-            for (long long k = k0; k < k1; k++) {
-                const long long l = m->h_orig[k];
-                const int c = m->h_cell_of_orig[l];
-                const int ix = c % nx, iy = c / nx;
-                const double Xw = f->x[l] - m->g.Lx * std::floor(f->x[l] / m->g.Lx);
-                const double Yw = f->y[l] - m->g.Ly * std::floor(f->y[l] / m->g.Ly);
-                qx[k] = to_fix((Xw - ix * m->g.Lcx) / m->g.Lcx);
-                qy[k] = to_fix((Yw - iy * m->g.Lcy) / m->g.Lcy);
-                fl[k] = (float)f->theta[l];
-                fl[n + k] = (float)f->u[l];
-                fl[2 * n + k] = (float)f->v[l];
-                fl[3 * n + k] = (float)f->omega[l];
-                fl[4 * n + k] = (float)f->r[l];
-                fl[5 * n + k] = (float)f->h[l];
-            }
-        });
-        CK(cudaMemcpyAsync(m->s32.xq, qx, 4 * n, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(m->s32.yq, qy, 4 * n, cudaMemcpyHostToDevice, m->stream));
-        float *dst[6] = {m->s32.th, m->s32.u, m->s32.v, m->s32.w, m->s32.r, m->s32.h};
-        for (int a = 0; a < 6; a++)
-            CK(cudaMemcpyAsync(dst[a], fl + a * n, 4 * n, cudaMemcpyHostToDevice, m->stream));
-    }
-    return MS_OK;
+    if (m->n == 0) return MS_OK;
+    Trace tr("msdem.upload");
+    const int rc = send_raw(m, f);
+    return rc ? rc : raw_to_state(m);
 }
 
 static int upload_truth_state(ms_model *m, const ms_floes *f)
@@ -1174,6 +1181,10 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(dalloc(m, &m->d_ctrl, 1));
     CKM(dalloc(m, &m->d_cmax, nens));
     CKM(dalloc(m, &m->d_pack, nc));
+    CKM(dalloc(m, &m->d_raw, 8 * (size_t)n));
+    CKM(dalloc(m, &m->d_orig, (size_t)n));
+    CKM(dalloc(m, &m->d_cell_of, (size_t)n));
+    CKM(dalloc(m, &m->d_first, 2));
     CKM(cudaMemsetAsync(m->d_cmax, 0, sizeof(unsigned long long) * nens, m->stream));
     if (m->precision == MS_FP64) {
         CKM(alloc64(m, m->s64, n));
@@ -1197,7 +1208,13 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaMemsetAsync(m->d_tgt, 0, sizeof(double) * nc * 4, m->stream));
     CKM(cudaMemcpyAsync(m->d_off, m->h_off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, m->stream));
     CKM(cudaMemcpyAsync(m->d_order, m->h_order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
-    CKM(cudaStreamSynchronize(m->stream));
+    {
+        const std::vector<int> orig32(m->h_orig.begin(), m->h_orig.end());
+        CKM(cudaMemcpyAsync(m->d_orig, orig32.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream));
+        CKM(cudaMemcpyAsync(m->d_cell_of, m->h_cell_of_orig.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                            m->stream));
+        CKM(cudaStreamSynchronize(m->stream));
+    }
 #undef CKM
     // an ensemble has no truth DEM (each realization's truth is a model of its own)
     if ((rc = upload_model_state(m, floes)) ||
@@ -1406,16 +1423,25 @@ int ms_set_floes(ms_model *m, const ms_floes *floes)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
     Trace tr("msdem.set_floes");
-    int rc = validate_floes(floes, m->n);
+    int rc = check_floe_args(floes, m->n);
     if (rc) return rc;
-    const long long left = host_first(m->n, [&](long long l) {
-        const int c = cell_index(floes->y[l], m->g.Ly, m->g.Lcy, m->g.ny) * m->g.nx +
-                      cell_index(floes->x[l], m->g.Lx, m->g.Lcx, m->g.nx);
-        return c != m->h_cell_of_orig[l];
-    });
-    if (left < m->n) return fail(MS_ERR_ARG, "floe %lld left its cell", left);
-    CK(cudaStreamSynchronize(m->stream));
-    if ((rc = upload_model_state(m, floes))) return rc;
+    if (m->n > 0) {
+        // checks on the device over the raw copy; the state changes only
+        // after both pass
+        if ((rc = send_raw(m, floes))) return rc;
+        unsigned long long first[2];
+        CK(cudaMemsetAsync(m->d_first, 0xff, sizeof(first), m->stream));
+        CK(launch_check_floes(m->d_raw, m->d_cell_of, up_geom(m), m->d_first, m->stream));
+        CK(cudaMemcpyAsync(first, m->d_first, sizeof(first), cudaMemcpyDeviceToHost, m->stream));
+        CK(cudaStreamSynchronize(m->stream));
+        if (first[0] < (unsigned long long)m->n) {
+            const long long l = (long long)first[0];
+            if (!floe_finite(floes, l)) return fail(MS_ERR_ARG, "floe %lld has a non-finite value", l);
+            return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
+        }
+        if (first[1] < (unsigned long long)m->n) return fail(MS_ERR_ARG, "floe %lld left its cell", (long long)first[1]);
+        if ((rc = raw_to_state(m))) return rc;
+    }
     CK(invalidate_lists(m));
     StepCommon sc = step_common(m, 0, m->d_mom, m->d_win);
     CK(m->precision == MS_FP64 ? launch_cell_moments64(m->s64, m->P64, sc, m->stream)

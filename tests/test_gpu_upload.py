@@ -1,0 +1,106 @@
+"""Uploads: the caller's FP64 floes are checked and converted into the cell
+layout on the device (ms_init and ms_set_floes).  The stored state must be
+what the plain IEEE arithmetic of the assignment gives: cell = floor of the
+wrapped position over the cell side, FP32 positions the offset in the cell
+as 32-bit fixed point rounded to nearest even, the other FP32 fields the
+FP64 values rounded once; FP64 positions the offset itself.  numpy computes
+the same operations here, so the comparison is bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2303_07819_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    from paper_2303_07819_gb300 import msdem
+    msdem.load()
+    return msdem
+
+
+def expected(p, f, precision):
+    """floes() of a model holding f, from the assignment's arithmetic"""
+    nens = int(p.get("nens", 1))
+    nx, ny = int(p["nx"]), int(p["ny"]) * nens
+    Lx, Ly = float(p["Lx"]), float(p["Ly"]) * nens
+    Lcx, Lcy = float(p["Lx"]) / p["nx"], float(p["Ly"]) / p["ny"]
+    Xw = f["x"] - Lx * np.floor(f["x"] / Lx)
+    Yw = f["y"] - Ly * np.floor(f["y"] / Ly)
+    ix = np.clip(np.floor(Xw / Lcx), 0, nx - 1)
+    iy = np.clip(np.floor(Yw / Lcy), 0, ny - 1)
+    out = {}
+    if precision == 0:
+        fix = lambda fr: (np.rint(fr * 4294967296.0).astype(np.int64) & 0xFFFFFFFF).astype(np.float64)
+        out["x"] = (ix + fix((Xw - ix * Lcx) / Lcx) / 4294967296.0) * Lcx
+        out["y"] = (iy + fix((Yw - iy * Lcy) / Lcy) / 4294967296.0) * Lcy
+        for k in ("theta", "u", "v", "omega", "r", "h"):
+            out[k] = f[k].astype(np.float32).astype(np.float64)
+    else:
+        out["x"] = ix * Lcx + (Xw - ix * Lcx)
+        out["y"] = iy * Lcy + (Yw - iy * Lcy)
+        for k in ("theta", "u", "v", "omega", "r", "h"):
+            out[k] = f[k].copy()
+    return out
+
+
+def scenarios():
+    ens = I.stack_ensemble([I.powerlaw_32x32(seed=200 + e, nx=4) for e in range(3)])
+    # non-dimensional domain, cell sides 4/48 and 2/24 not representable
+    return [I.batched_128x128(seed=5, nx=16), I.scenario41(96, 48, 48, 24), ens]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_init_and_set_floes_round_as_the_host(ms, precision):
+    for s in scenarios():
+        p, f = s["params"], s["floes"]
+        g = ms.Model(p, f, precision)
+        got, want = g.floes(), expected(p, f, precision)
+        for k in want:
+            assert np.array_equal(got[k], want[k]), k
+        # moved within their cells (and a wrapped copy of the x positions:
+        # one period further, the same floe) through ms_set_floes
+        rng = np.random.default_rng(7)
+        m = {k: v.copy() for k, v in got.items()}
+        Lcx = float(p["Lx"]) / p["nx"]
+        cx = (np.floor(m["x"] / Lcx) + 0.5) * Lcx
+        m["x"] = m["x"] + rng.uniform(0.1, 0.5, m["x"].shape) * (cx - m["x"]) + float(p["Lx"])
+        m["u"] = m["u"] + rng.normal(0.0, 0.01, m["u"].shape)
+        m["r"] = m["r"] * 0.99
+        g.set_floes(m)
+        got, want = g.floes(), expected(p, m, precision)
+        for k in want:
+            assert np.array_equal(got[k], want[k]), k
+        g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_floes_rejects_and_keeps_state(ms, precision):
+    """A non-finite value, r <= 0, h <= 0 or a floe outside its cell is
+    reported with the smallest offending index, and the model keeps its
+    floes and moments."""
+    s = I.powerlaw_32x32(nx=4)
+    g = ms.Model(s["params"], s["floes"], precision)
+    g.step(s["dt"], 3)
+    f0, m0 = g.floes(), g.moments()
+    n = f0["x"].shape[0]
+    cases = [("omega", n - 1, np.inf, "non-finite"), ("y", 5, np.nan, "non-finite"), ("r", 17, 0.0, "r <= 0"),
+             ("h", 3, -1.0, "r <= 0"), ("x", 9, None, "left its cell")]
+    for key, idx, val, msg in cases:
+        bad = {k: v.copy() for k, v in f0.items()}
+        if val is None:
+            bad["x"][idx] += float(s["params"]["Lx"]) / s["params"]["nx"]
+            bad["x"][idx + 40] += float(s["params"]["Lx"]) / s["params"]["nx"]
+        else:
+            bad[key][idx] = val
+            if idx + 50 < n:
+                bad["r"][idx + 50] = -1.0      # a later index: the smaller one is reported
+        with pytest.raises(ms.MsError) as e:
+            g.set_floes(bad)
+        assert e.value.code == -1 and msg in str(e.value) and f"floe {idx} " in str(e.value), str(e.value)
+        f1 = g.floes()
+        for k in f0:
+            assert np.array_equal(f0[k], f1[k]), (key, k)
+        assert np.array_equal(m0, g.moments())
+    g.close()
