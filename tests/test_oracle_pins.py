@@ -488,6 +488,45 @@ def test_p9_moments_match_numpy_reduction(orc):
     del cell
 
 
+def test_p9_moment_columns_follow_the_dynamics(orc):
+    """Eq. (2.1a-b) with forward Euler (Sec. 3.1) and Newton's third law of
+    Eq. (2.2): contact forces cancel in pairs, so from one step to the next a
+    cell's momentum columns change by exactly dt times its drag columns (the
+    drag of that step, columns 9 and 10); without coupling nothing changes n,
+    sum m, sum I or sum pi r^2.  Crowded cells (many contacts, some across the
+    periodic edges), an ocean of modes and wind."""
+    rng = np.random.default_rng(4)
+    L = 2.0e4
+    fl = I.random_cell_floes(rng, 300, L, 150.0, 450.0)
+    fl["u"] = rng.normal(0.0, 0.3, 300)
+    fl["v"] = rng.normal(0.0, 0.3, 300)
+    p = base_params(nx=2, ny=2, Lx=2 * L, Ly=2 * L, eta=20.0, Ca=1.2e-3, wind_x=10.0, wind_y=-4.0,
+                    modes=I.random_modes(rng, 4, 2 * L, 2 * L, 0.2))
+    # the four cells hold shifted copies of the crowded set
+    four = {k: np.concatenate([v + (L * (c % 2) if k == "x" else L * (c // 2) if k == "y" else 0.0)
+                               for c in range(4)]) for k, v in fl.items()}
+    m = orc.Model(p, four)
+    dt = 2.0
+    m.step(dt, 1)
+    prev = m.moments().copy()
+    touched = 0
+    for _ in range(40):
+        m.step(dt, 1)
+        mo = m.moments()
+        for col in (0, 1, 4, 6):
+            assert np.array_equal(mo[:, col], prev[:, col]), col
+        for cm, cf in ((2, 9), (3, 10)):
+            scale = np.abs(mo[:, cm]).max() + dt * np.abs(mo[:, cf]).max()
+            assert np.allclose(mo[:, cm] - prev[:, cm], dt * mo[:, cf], rtol=0, atol=1e-12 * scale), (cm, cf)
+        touched += int(np.any(mo[:, 9] != 0.0))
+        prev = mo.copy()
+    assert touched == 40
+    f = m.floes()
+    d = np.hypot(*(np.subtract.outer(f[k][:300], f[k][:300]) for k in ("x", "y")))
+    r = f["r"][:300]
+    assert np.any((d < np.add.outer(r, r)) & ~np.eye(300, dtype=bool))   # contacts present
+
+
 def test_single_cell_model_equals_truth(orc):
     """With one coarse cell and no coupling the localised DEM is the truth DEM."""
     s = I.square_4x4()
