@@ -527,6 +527,39 @@ def test_p9_moment_columns_follow_the_dynamics(orc):
     assert np.any((d < np.add.outer(r, r)) & ~np.eye(300, dtype=bool))   # contacts present
 
 
+def test_p9_spin_column_follows_the_drag_torque(orc):
+    """Eq. (2.1d) with forward Euler: while no floes touch, a cell's angular
+    momentum column sum I omega changes each step by exactly dt times its
+    drag-torque column (11), and its momentum columns by dt times the drag
+    columns.  The 4 x 4 square workload without coupling, 20 steps of 1 s:
+    floes start at rest and apart, and the smallest gap (about 19 m) exceeds
+    twice the distance any floe can travel in 20 s (0.5 a t^2 < 2 m even at
+    a drag acceleration of 0.01 m/s^2, several times the largest the
+    workload's current gives), so no contact occurs."""
+    s = I.square_4x4()
+    p = dict(s["params"], couple=0)
+    m = orc.Model(p, s["floes"])
+    f = m.floes()
+    n = f["x"].shape[0]
+    assert np.all(f["u"] == 0.0) and np.all(f["v"] == 0.0)
+    d = np.hypot(*(np.subtract.outer(f[k], f[k]) for k in ("x", "y")))
+    gap = (d - np.add.outer(f["r"], f["r"]))[~np.eye(n, dtype=bool)].min()
+    dt, steps = 1.0, 20
+    assert gap > 2 * 0.5 * 0.01 * (dt * steps) ** 2
+    m.step(dt, 1)
+    prev = m.moments().copy()
+    for _ in range(steps - 1):
+        m.step(dt, 1)
+        mo = m.moments()
+        for cm, cf in ((2, 9), (3, 10), (5, 11)):
+            scale = np.abs(mo[:, cm]).max() + dt * np.abs(mo[:, cf]).max()
+            assert np.allclose(mo[:, cm] - prev[:, cm], dt * mo[:, cf], rtol=0, atol=1e-12 * scale), (cm, cf)
+        assert np.any(mo[:, 11] != 0.0)
+        prev = mo.copy()
+    u = m.floes()
+    assert np.hypot(u["u"], u["v"]).max() < 0.01 * dt * steps
+
+
 def test_single_cell_model_equals_truth(orc):
     """With one coarse cell and no coupling the localised DEM is the truth DEM."""
     s = I.square_4x4()
