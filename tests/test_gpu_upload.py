@@ -104,3 +104,41 @@ def test_set_floes_rejects_and_keeps_state(ms, precision):
             assert np.array_equal(f0[k], f1[k]), (key, k)
         assert np.array_equal(m0, g.moments())
     g.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uploading_the_held_state_continues_the_run(ms, precision):
+    """Uploading, at an interval boundary, the floes the model holds (what the
+    bench's end-to-end loop does every step) changes nothing in FP32: the
+    fixed-point round trip is exact, the moments pass of ms_set_floes leaves
+    the coupling window alone, and an interval's first step searches again
+    either way, so the run goes on bit for bit as the uninterrupted one,
+    coupling included.  FP64 keeps positions as offsets from the cell origin
+    while the API speaks global coordinates, so there the round trip can move
+    a floe by an ulp of its global coordinate (get, set, get is still exact)
+    and the run goes on within 1e-10."""
+    from tests.parity import rel_errors, report
+    s = I.batched_128x128(seed=12, nx=8)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    a = ms.Model(p, s["floes"], precision)
+    b = ms.Model(p, s["floes"], precision)
+    a.step(dt, 3 * N0)
+    b.step(dt, N0)
+    for _ in range(2):
+        b.set_floes(b.floes())
+        b.step(dt, N0)
+    fa, fb = a.floes(), b.floes()
+    qa, qb = a.coupling()["q"], b.coupling()["q"]
+    if precision == 0:
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+        assert np.array_equal(a.moments(), b.moments())
+        assert np.array_equal(qa, qb)
+    else:
+        for k in fa:
+            assert np.allclose(fa[k], fb[k], rtol=1e-10, atol=1e-6 if k in "xy" else 1e-12), k
+        err = rel_errors(b.moments(), a.moments(), p, 1e-12)
+        assert err.max() <= 1e-10, report(err)
+        assert np.linalg.norm(qa - qb) <= 1e-10 * np.linalg.norm(qa)
+    a.close()
+    b.close()
