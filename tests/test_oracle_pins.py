@@ -445,6 +445,35 @@ def test_p8_gradual_update_reaches_targets(orc):
     assert np.allclose(mo[:, 5], qstar[3] * Ac, rtol=1e-12, atol=1e-9 * np.abs(qstar[3] * Ac).max())
 
 
+def test_c14_substep_count(orc):
+    """Sec. 3.2 (Eq. 3.1), reading c14: the coarse step takes N1 = max(1,
+    ceil(dT max(|Vx|/dx, |Vy|/dy) / 0.5)) Lax-Friedrichs substeps of dT / N1,
+    from the DEM's moments per unit area with the window's mean velocity.
+    Cells drifting with no forces at speeds that need three substeps: the
+    first coarse state is the (separately pinned) LF step taken N1 times, and
+    N1 - 1 or N1 + 1 substeps give a visibly different state."""
+    p, fl = _drift_cells()
+    N0, nx, ny = p["N0"], p["nx"], p["ny"]
+    dx = p["Lx"] / nx
+    cmax = max(np.abs(fl["u"]).max(), np.abs(fl["v"]).max()) / dx
+    dt = 2.5 * 0.5 / (cmax * N0)           # dT cmax / 0.5 = 2.5: three substeps
+    m = orc.Model(p, fl)
+    m.step(dt, N0)
+    mo = m.moments()
+    q0 = mo[:, [1, 2, 3, 5]].T / (dx * dx)
+    V = np.stack([mo[:, 2] / mo[:, 1], mo[:, 3] / mo[:, 1]])
+    dT = N0 * dt
+    N1 = max(1, math.ceil(dT * np.max(np.abs(V) / dx) / 0.5))
+    assert N1 == 3
+    S = np.zeros((4, nx * ny))
+    want = orc.lf(nx, ny, dx, dx, q0, V, S, dT / N1, N1)
+    got = m.coupling()["q"]
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+    for k in (N1 - 1, N1 + 1):
+        other = orc.lf(nx, ny, dx, dx, q0, V, S, dT / k, k)
+        assert not np.allclose(got, other, rtol=1e-6, atol=0), k
+
+
 def test_p8_coarse_initialisation_and_window(orc):
     """Algorithm 1: after the first N0 steps the coarse state is the DEM's
     (mass, momentum, angular momentum) per unit area, and the velocity that
