@@ -172,6 +172,36 @@ def test_stream_mode_equals_velocity_mode(orc):
         assert np.allclose(fa[:3], fb[:3], rtol=1e-13, atol=1e-18), (fa, fb)
 
 
+def test_c9_ocean_at_the_global_position(orc):
+    """Sec. 2.1 with Sec. 3.1, reading c9: a cell's DEM samples the ocean at
+    the floe's global position (cell origin plus position in the cell).  A
+    floe at rest in cell (2, 1) of a 4 x 4 grid under the sin-sin current:
+    its first Euler step changes u, v by dt Cd rho_o |u_o| u_o / (rho_ice h)
+    and omega by dt Cd rho_o pi r^4 |zeta/2| zeta/2 / I (Eq. 2.1c-d, I = m
+    r^2) with the current at the global position; the current at the
+    position within the cell is a different one."""
+    L = 1.0e5
+    Lc = L / 4
+    p = base_params(nx=4, ny=4, Lx=L, Ly=L, modes=I.psi_sin_sin_modes(0.1, L))
+    X, Y = 2 * Lc + 3.7e3, 1 * Lc + 17.9e3
+    r, h, dt = 800.0, 1.3, 5.0
+    m = orc.Model(p, one_floe(X, Y, r=r, h=h))
+    m.step(dt, 1)
+    f = m.floes()
+    uo, vo, zeta, _, _ = orc.forcing(p, X, Y)
+    k = p["Cd"] * p["rho_o"] / (p["rho_ice"] * h)
+    sp = math.hypot(uo, vo)
+    assert sp > 0.02 and abs(zeta) > 1e-7
+    assert math.isclose(f["u"][0], dt * k * sp * uo, rel_tol=1e-12)
+    assert math.isclose(f["v"][0], dt * k * sp * vo, rel_tol=1e-12)
+    mass = p["rho_ice"] * PI * r * r * h
+    wz = 0.5 * zeta
+    assert math.isclose(f["omega"][0], dt * p["Cd"] * p["rho_o"] * PI * r ** 4 * abs(wz) * wz / (mass * r * r),
+                        rel_tol=1e-12)
+    ul, vl, zl, _, _ = orc.forcing(p, X - 2 * Lc, Y - Lc)
+    assert abs(ul - uo) > 0.01 and abs(vl - vo) > 0.01 and abs(zl - zeta) > 1e-7
+
+
 def test_wind_rotation(orc):
     p = base_params(wind_x=10.0, wind_y=0.0, wind_period=6 * 3600.0)
     f = orc.forcing(p, 0.0, 0.0, 1.5 * 3600.0)
