@@ -288,6 +288,23 @@ def test_p5_coulomb_cap(orc):
     assert o[5] > 0          # j slides in +t = +y: friction drags l along +y
 
 
+def test_c3_thickness_factor(orc):
+    """Eq. (2.2), reading c3: the contact law scales with the thinner floe's
+    thickness over h_ref, min(h_l, h_j) / h_ref, in the normal and in the
+    tangential force, and seen from j the pair gives the opposite force."""
+    geo_l, geo_j = (0.0, 0.0, 0.0, 0.0, 0.0, 1000.0), (1990.0, 0.0, 0.0, 0.02, 0.0, 1000.0)
+    ok, unit = orc.pair(base_params(eta=0.0, h_ref=1.0), 1e6, 1e6, geo_l + (1.0,), geo_j + (1.0,))
+    p = base_params(eta=0.0, h_ref=1.3)
+    hit, o = orc.pair(p, 1e6, 1e6, geo_l + (2.0,), geo_j + (0.5,))
+    assert ok and hit and unit[4] < 0 and unit[5] != 0.0
+    assert abs(unit[5]) < p["mu"] * abs(unit[4])              # below the Coulomb cap: viscous law
+    f = 0.5 / 1.3
+    for i in (0, 1, 4, 5):                                      # Fx, Fy, normal, tangential
+        assert math.isclose(o[i], f * unit[i], rel_tol=1e-13), i
+    hit2, o2 = orc.pair(p, 1e6, 1e6, geo_j + (0.5,), geo_l + (2.0,))
+    assert hit2 and math.isclose(o2[0], -o[0], rel_tol=1e-13) and math.isclose(o2[1], -o[1], rel_tol=1e-13)
+
+
 def test_contact_normal_is_repulsive_hooke(orc):
     """f_n = c E delta n with n from l to j and delta < 0 in overlap: repulsive,
     linear in the overlap at fixed chord."""
