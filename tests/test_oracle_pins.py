@@ -521,6 +521,26 @@ def test_c14_substep_count(orc):
         assert not np.allclose(got, other, rtol=1e-6, atol=0), k
 
 
+def test_c20_empty_cell(orc):
+    """Reading c20: an empty cell contributes no window velocity, takes the
+    targets s = 1 with zero increments even when the Lax-Friedrichs step
+    carries coarse mass into it from drifting neighbours, and nothing in
+    the coupled steps becomes non-finite."""
+    p, fl = _drift_cells()
+    Lc = p["Lx"] / p["nx"]
+    keep = ~((fl["x"] < Lc) & (fl["y"] < Lc))                   # cell 0 emptied
+    fl = {k: v[keep] for k, v in fl.items()}
+    m = orc.Model(p, fl)
+    m.step(50.0, 3 * p["N0"])
+    cp = m.coupling()
+    assert cp["have_q"] and cp["have_targets"]
+    assert cp["q"][0, 0] > 0.0                                  # coarse mass arrived
+    assert np.array_equal(cp["targets"][:, 0], [1.0, 0.0, 0.0, 0.0])
+    assert m.moments()[0, 0] == 0 and np.all(m.moments()[0] == 0.0)
+    assert np.all(np.isfinite(cp["q"])) and np.all(np.isfinite(cp["targets"]))
+    assert np.all(np.isfinite(m.moments()))
+
+
 def test_p8_coarse_initialisation_and_window(orc):
     """Algorithm 1: after the first N0 steps the coarse state is the DEM's
     (mass, momentum, angular momentum) per unit area, and the velocity that
