@@ -656,6 +656,26 @@ def test_p9_spin_column_follows_the_drag_torque(orc):
     assert np.hypot(u["u"], u["v"]).max() < 0.01 * dt * steps
 
 
+def test_c23_half_open_cells(orc):
+    """Reading c23: cells are half-open, [i dX, (i + 1) dX), with positions
+    wrapped by floor into the periodic domain: a floe on a cell's left edge
+    belongs to that cell, one at X = Lx (or -dX) to the column it wraps to."""
+    L = 4.0e4
+    dX = L / 4
+    xs = [dX, 2 * dX, L, -dX, 0.5 * dX]
+    ys = [0.5 * dX, dX, 3 * dX, 0.5 * dX, -0.5 * dX]
+    want = [1, 4 + 2, 12 + 0, 3, 12 + 0]          # cell = iy nx + ix
+    n = len(xs)
+    fl = {"x": np.array(xs), "y": np.array(ys), "theta": np.zeros(n), "u": np.zeros(n), "v": np.zeros(n),
+          "omega": np.zeros(n), "r": np.full(n, 100.0), "h": np.ones(n)}
+    m = orc.Model(base_params(nx=4, ny=4, Lx=L, Ly=L), fl)
+    off, orig = m.layout()
+    cell = np.empty(n, dtype=np.int64)
+    for c in range(16):
+        cell[orig[off[c]:off[c + 1]]] = c
+    assert cell.tolist() == want
+
+
 def test_single_cell_model_equals_truth(orc):
     """With one coarse cell and no coupling the localised DEM is the truth DEM."""
     s = I.square_4x4()
