@@ -142,3 +142,27 @@ def test_uploading_the_held_state_continues_the_run(ms, precision):
         assert np.linalg.norm(qa - qb) <= 1e-10 * np.linalg.norm(qa)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_half_open_cells_match_the_oracle(ms, orc, precision):
+    """Floes on a cell's left edge, at X = Lx and at negative coordinates
+    are assigned as the oracle assigns them (half-open cells, floor wrap):
+    by ms_init on the host, and by the device-side check of ms_set_floes,
+    which accepts the same floes again."""
+    L = 4.0e4
+    dX = L / 4
+    xs = [dX, 2 * dX, L, -dX, 0.5 * dX]
+    ys = [0.5 * dX, dX, 3 * dX, 0.5 * dX, -0.5 * dX]
+    n = len(xs)
+    fl = {"x": np.array(xs), "y": np.array(ys), "theta": np.zeros(n), "u": np.zeros(n), "v": np.zeros(n),
+          "omega": np.zeros(n), "r": np.full(n, 100.0), "h": np.ones(n)}
+    p = I._phys(dt=5.0)
+    p.update({"nx": 4, "ny": 4, "Lx": L, "Ly": L, "modes": np.zeros((0, 4))})
+    g = ms.Model(p, fl, precision)
+    o = orc.Model(p, fl)
+    assert np.array_equal(g.moments()[:, 0], o.moments()[:, 0])
+    assert g.moments()[:, 0].tolist() == [0, 1, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 2, 0, 0, 0]
+    g.set_floes(fl)
+    assert np.array_equal(g.moments()[:, 0], o.moments()[:, 0])
+    g.close()
