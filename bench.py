@@ -73,7 +73,6 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     the mean-field closure, and, as the noise floor, the particle path with
     another reduction order (the block-per-cell kernel), all from the same
     spun-up state.  A closure cell's coarse interval counts as N0 cell-steps."""
-    from oracle import closure_oracle as CO
     from paper_2303_07819_gb300 import inputs as I
     t0 = time.perf_counter()
     Xs, Ys = [], []
@@ -85,7 +84,7 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
         Xs.append(X.reshape(-1, 16)); Ys.append(Y.reshape(-1, 4))
         m.close()
     X, Y = np.concatenate(Xs), np.concatenate(Ys)
-    norm = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
+    norm = msdem.fit_norm(X, Y)
     net = msdem.MLP(I.mlp_init(), norm, max_batch=8192)
     tt = time.perf_counter()
     losses = net.train(X, Y, epochs=100, batch=1024, lr=2e-3, seed=3)

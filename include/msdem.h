@@ -288,6 +288,16 @@ typedef struct ms_mlp ms_mlp;
  * of any later call (1 .. 2^22). */
 int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t max_batch);
 
+/* Input and output normalisation of a training set, computed on the
+ * device: host X[n][16] and Y[n][4] (FP32, sample-major, only read) ->
+ * host norm[40] = [mu_x(16), sd_x(16), mu_y(4), sd_y(4)], the per-column
+ * mean and population standard deviation (sums in FP64, fixed order, so the
+ * same inputs give the same result), each sd at least 1e-12: the z-scoring
+ * of the loss above, in the layout ms_mlp_create takes.  MS_ERR_ARG for a
+ * NULL pointer or n outside [1, 2^31]; MS_ERR_CUDA if a CUDA call fails (the
+ * call allocates 80 n bytes of device memory for its duration). */
+int ms_mlp_fit_norm(const float *X, const float *Y, int64_t n, float *norm);
+
 /* Forward pass: host X[n][16] -> host Y[n][4] in physical units. */
 int ms_mlp_predict(ms_mlp *m, const float *X, int64_t n, float *Y);
 

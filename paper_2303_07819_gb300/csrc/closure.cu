@@ -216,6 +216,41 @@ __global__ void k_denorm(const float *yp, int B, const float *mu, const float *s
     for (int o = 0; o < NOUT; o++) Y[(size_t)s * NOUT + o] = mu[o] + sd[o] * yp[(size_t)s * NOP + o];
 }
 
+// Per-column mean and spread of a sample-major FP32 array [n][ncol], FP64
+// sums: block b takes column b, each thread a strided share of the samples,
+// then a fixed-order tree over the block (the same result on every run).
+// out[b] = mean, out[ncol + b] = max(population sd, floor).
+__global__ void __launch_bounds__(256) k_col_stats(const float *A, long long n, int ncol, double floor_sd,
+                                                   double *out)
+{
+    __shared__ double red[256];
+    const int col = blockIdx.x, t = threadIdx.x;
+    auto block_sum = [&](double v) {
+        red[t] = v;
+        __syncthreads();
+        for (int s = 128; s > 0; s >>= 1) {
+            if (t < s) red[t] += red[t + s];
+            __syncthreads();
+        }
+        const double r = red[0];
+        __syncthreads();
+        return r;
+    };
+    double s = 0.0;
+    for (long long i = t; i < n; i += 256) s += (double)A[i * ncol + col];
+    const double mean = block_sum(s) / (double)n;
+    double q = 0.0;
+    for (long long i = t; i < n; i += 256) {
+        const double d = (double)A[i * ncol + col] - mean;
+        q += d * d;
+    }
+    const double var = block_sum(q) / (double)n;
+    if (t == 0) {
+        out[col] = mean;
+        out[ncol + col] = fmax(sqrt(var), floor_sd);
+    }
+}
+
 struct LayerDev {
     int nin, nout, kin, nop;   // logical and padded sizes
     float *W, *b;              // FP32 master [nout][nin], [nout]
@@ -449,6 +484,41 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         (rc = ck(cudaStreamSynchronize(m->st), "sync")))
         return fail_free(rc);
     *out = m;
+    return MS_OK;
+}
+
+int ms_mlp_fit_norm(const float *X, const float *Y, int64_t n, float *norm)
+{
+    if (!X || !Y || !norm) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (n < 1 || n > (int64_t(1) << 31)) return ms_closure_fail(MS_ERR_ARG, "n must be in [1, 2^31]");
+    cudaStream_t st = nullptr;
+    float *Xd = nullptr, *Yd = nullptr;
+    double *sd = nullptr;
+    int rc = ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
+    if (rc == MS_OK) rc = ck(cudaMalloc(&Xd, sizeof(float) * (size_t)n * NIN), "cudaMalloc");
+    if (rc == MS_OK) rc = ck(cudaMalloc(&Yd, sizeof(float) * (size_t)n * NOUT), "cudaMalloc");
+    if (rc == MS_OK) rc = ck(cudaMalloc(&sd, sizeof(double) * 2 * (NIN + NOUT)), "cudaMalloc");
+    if (rc == MS_OK)
+        rc = ck(cudaMemcpyAsync(Xd, X, sizeof(float) * (size_t)n * NIN, cudaMemcpyHostToDevice, st), "copy");
+    if (rc == MS_OK)
+        rc = ck(cudaMemcpyAsync(Yd, Y, sizeof(float) * (size_t)n * NOUT, cudaMemcpyHostToDevice, st), "copy");
+    double h[2 * (NIN + NOUT)];
+    if (rc == MS_OK) {
+        k_col_stats<<<NIN, 256, 0, st>>>(Xd, n, NIN, 1e-12, sd);
+        k_col_stats<<<NOUT, 256, 0, st>>>(Yd, n, NOUT, 1e-12, sd + 2 * NIN);
+        rc = ck(cudaGetLastError(), "k_col_stats");
+    }
+    if (rc == MS_OK) rc = ck(cudaMemcpyAsync(h, sd, sizeof(h), cudaMemcpyDeviceToHost, st), "copy");
+    if (rc == MS_OK) rc = ck(cudaStreamSynchronize(st), "sync");
+    if (st) cudaStreamSynchronize(st);
+    cudaFree(Xd);
+    cudaFree(Yd);
+    cudaFree(sd);
+    if (st) cudaStreamDestroy(st);
+    if (rc != MS_OK) return rc;
+    // packed as ms_mlp_create reads it: mu_x, sd_x, mu_y, sd_y
+    for (int i = 0; i < 2 * NIN; i++) norm[i] = (float)h[i];
+    for (int i = 0; i < 2 * NOUT; i++) norm[2 * NIN + i] = (float)h[2 * NIN + i];
     return MS_OK;
 }
 

@@ -58,7 +58,7 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
-           "ms_probe_fp32", "ms_save", "ms_load"]
+           "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm"]
 
 
 def lib_path() -> str:
@@ -336,10 +336,11 @@ def _load_mlp():
                                C.POINTER(C.c_double)]
     L.ms_mlp_get_params.argtypes = [vp, _fp]
     L.ms_mlp_forward_device.argtypes = [vp, vp, C.c_int64, vp, vp]
+    L.ms_mlp_fit_norm.argtypes = [_fp, _fp, C.c_int64, _fp]
     L.ms_mlp_free.argtypes = [vp]
     L.ms_mlp_free.restype = None
     for n in ("ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train",
-              "ms_mlp_get_params", "ms_mlp_forward_device"):
+              "ms_mlp_get_params", "ms_mlp_forward_device", "ms_mlp_fit_norm"):
         getattr(L, n).restype = C.c_int
     L._mlp_ready = True
     return L
@@ -347,6 +348,20 @@ def _load_mlp():
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def fit_norm(X, Y) -> dict:
+    """Per-column mean and population sd of a training set (features X[n][16],
+    targets Y[n][4]), computed by the library on the device: the z-scoring the
+    network's loss uses, as the dict MLP() takes."""
+    X, Y = _f32(X), _f32(Y)
+    if X.ndim != 2 or X.shape[1] != 16 or Y.shape != (X.shape[0], 4):
+        raise ValueError("X must be [n][16] and Y [n][4]")
+    out = np.zeros(40, dtype=np.float32)
+    _check(_load_mlp().ms_mlp_fit_norm(X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0],
+                                       out.ctypes.data_as(_fp)))
+    return {"mu_x": out[:16].astype(np.float64), "sd_x": out[16:32].astype(np.float64),
+            "mu_y": out[32:36].astype(np.float64), "sd_y": out[36:40].astype(np.float64)}
 
 
 class MLP:

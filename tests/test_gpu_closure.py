@@ -32,6 +32,24 @@ def _params(seed=5):
     return p
 
 
+def test_fit_norm_matches_oracle(ms):
+    """The library's own normalisation (device FP64 sums over FP32 inputs)
+    against the oracle's NumPy mean and population sd of the same FP32
+    values: equal to FP32 rounding; a constant column takes the floor."""
+    X, Y = _data(4, 100003)
+    X = X.astype(np.float32)
+    Y = Y.astype(np.float32)
+    X[:, 8] = 0.0                                   # a column without spread
+    got = ms.fit_norm(X, Y)
+    ref = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
+    for k in ("mu_x", "mu_y"):
+        sd = ref["sd_x" if k == "mu_x" else "sd_y"]
+        assert np.all(np.abs(got[k] - ref[k]) <= 1e-6 * (np.abs(ref[k]) + sd)), k
+    for k in ("sd_x", "sd_y"):
+        assert np.all(np.abs(got[k] - ref[k]) <= 1e-6 * ref[k]), k
+    assert got["sd_x"][8] == np.float32(1e-12)
+
+
 def test_forward_matches_oracle(ms):
     X, Y = _data(0, 301)
     norm = CO.normalisation(X, Y)
@@ -41,6 +59,11 @@ def test_forward_matches_oracle(ms):
     ref = CO.predict(p, X, norm)
     err = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref - ref.mean(0), axis=0)
     assert err.max() < 2e-2, err
+    # sample by sample, in the network's own (z-scored) output units: BF16
+    # operands carry 8 significant bits through four layers
+    ez = np.abs(got - ref) / norm["sd_y"]
+    assert ez.max() < 0.1, ez.max(0)
+    assert np.quantile(ez, 0.99) < 0.04, np.quantile(ez, 0.99, axis=0)
 
 
 @pytest.mark.parametrize("B", [64, 1000, 5000])

@@ -9,7 +9,6 @@ several intervals to settle)."""
 import numpy as np
 import pytest
 
-from oracle import closure_oracle as CO
 from paper_2303_07819_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -31,7 +30,7 @@ def trained():
         Ys.append(Y.reshape(-1, 4))
         m.close()
     X, Y = np.concatenate(Xs), np.concatenate(Ys)
-    norm = CO.normalisation(X.astype(np.float64), Y.astype(np.float64))
+    norm = msdem.fit_norm(X, Y)
     net = msdem.MLP(I.mlp_init(), norm, max_batch=8192)
     losses = net.train(X, Y, epochs=120, batch=512, lr=2e-3, seed=11)
     box = np.stack([X.min(0) - 0.05 * np.abs(X.min(0)), X.max(0) + 0.05 * np.abs(X.max(0))])
