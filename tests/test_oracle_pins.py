@@ -288,6 +288,138 @@ def test_p5_coulomb_cap(orc):
     assert o[5] > 0          # j slides in +t = +y: friction drags l along +y
 
 
+# ------------------------------------------------- wind drag (Eq. 2.1c)
+@pytest.mark.parametrize("r,h", [(700.0, 1.0), (2500.0, 2.0)])
+def test_wind_drag_closed_form(orc, r, h):
+    """Sec. 2.1 adds wind drag with the ocean drag's form: m dv/dt =
+    Ca rho_a pi r^2 (u_a - v)|u_a - v|.  With no ocean drag (Cd = 0) and a
+    steady wind, w = u_a - v obeys dw/dt = -k_a w|w|, k_a = Ca rho_a/(rho_ice h),
+    so w(t) = w0 / (1 + k_a |w0| t), independent of r; forward Euler converges
+    to it at first order.  No wind torque: the spin stays zero.  Ocean
+    constants in place of Ca rho_a (a rate 3600 times larger), an extra r^2,
+    or the wrong sign all fail."""
+    ua = np.array([8.0, -6.0])
+    p = base_params(Cd=0.0, Ca=1.2e-3, rho_a=1.3, wind_x=ua[0], wind_y=ua[1])
+    ka = p["Ca"] * p["rho_a"] / (p["rho_ice"] * h)
+    v0 = np.array([0.1, 0.2])
+    w0 = ua - v0
+    T = 120000.0
+    exact = w0 / (1.0 + ka * np.linalg.norm(w0) * T)
+    assert np.linalg.norm(exact) < 0.55 * np.linalg.norm(w0)     # a real relaxation over T
+    errs = []
+    for dt in (400.0, 200.0, 100.0):
+        m = orc.Model(p, one_floe(5e5, 5e5, u=v0[0], v=v0[1], r=r, h=h))
+        m.step(dt, int(T / dt))
+        f = m.floes()
+        assert f["omega"][0] == 0.0
+        errs.append(np.linalg.norm((ua - np.array([f["u"][0], f["v"][0]])) - exact))
+    assert errs[-1] < 3e-3 * np.linalg.norm(w0)
+    for a, b in zip(errs, errs[1:]):
+        assert 1.8 < a / b < 2.2
+
+
+def test_wind_and_ocean_free_drift(orc):
+    """Ocean and wind drag add (Eq. 2.1c with the wind term of Sec. 2.1).
+    With a steady current u_o and a steady wind u_a along the same line, the
+    floe drifts at the speed where the two balance:
+    Cd rho_o (v - u_o)^2 = Ca rho_a (u_a - v)^2, i.e.
+    v = (sqrt(Cd rho_o) u_o + sqrt(Ca rho_a) u_a) / (sqrt(Cd rho_o) + sqrt(Ca rho_a)).
+    Swapping the two constants, or dropping either term, moves it."""
+    p = base_params(uo_x=0.1, Ca=1.2e-3, rho_a=1.3, wind_x=15.0)
+    a, b = math.sqrt(p["Cd"] * p["rho_o"]), math.sqrt(p["Ca"] * p["rho_a"])
+    vstar = (a * p["uo_x"] + b * p["wind_x"]) / (a + b)
+    m = orc.Model(p, one_floe(5e5, 5e5, u=0.0, v=0.0, r=1200.0, h=1.0))
+    m.step(10.0, 20000)
+    f = m.floes()
+    assert abs(f["u"][0] - vstar) < 1e-9 * vstar and abs(f["v"][0]) < 1e-15
+    assert vstar > 2 * p["uo_x"]          # the wind matters: 0.1 m/s current, 0.31 m/s drift
+
+
+# ----------------------------------- tangential law with spin (Eq. 2.2)
+def _chord_heron(d, rl, rj):
+    """Chord of the lens of two overlapping disks: twice the height of the
+    triangle (d, r_l, r_j) over the side d, from Heron's formula."""
+    s = 0.5 * (d + rl + rj)
+    K = math.sqrt(s * (s - d) * (s - rl) * (s - rj))
+    return 4.0 * K / d
+
+
+@pytest.mark.parametrize("wl,wj", [(3e-4, -5e-4), (2e-4, 2e-4), (-1e-4, 4e-4)])
+def test_tangential_law_with_spin(orc, wl, wj):
+    """Eq. (2.2): f_t = c h G v_t t below the Coulomb cap, with v_t the
+    relative velocity of the contact points along t = z x n.  For floes at
+    rest with spins w_l, w_j, the contact point of l (arm r_l n) moves at
+    w_l r_l t and that of j (arm -r_j n, towards l) at -w_j r_j t, so
+    v_t = -w_j r_j - w_l r_l.  Written out here from the geometry (chord by
+    Heron's formula), with r_l != r_j and h_l != h_j so a swapped radius,
+    spin or thickness, or a sign, shows.  Force on l: F n + f_t t; torques
+    r_l f_t on l and r_j f_t on j."""
+    rl, rj, hl, hj, d = 1000.0, 1500.0, 1.2, 0.9, 2400.0
+    p = base_params(E=4e3, G=5e3, eta=0.0, mu=0.5, h_ref=1.0)
+    th = 0.7                                         # line of centres at 0.7 rad
+    n = np.array([math.cos(th), math.sin(th)])
+    t = np.array([-n[1], n[0]])
+    xl = np.array([3e5, 4e5])
+    xj = xl + d * n
+    hit, o = orc.pair(p, 1e6, 1e6, (xl[0], xl[1], 0, 0, wl, rl, hl), (xj[0], xj[1], 0, 0, wj, rj, hj))
+    c = _chord_heron(d, rl, rj)
+    hc = min(hl, hj) / p["h_ref"]
+    Fn = c * hc * p["E"] * (d - rl - rj)
+    vt = -wj * rj - wl * rl
+    ft = c * hc * p["G"] * vt
+    assert hit and abs(ft) < p["mu"] * abs(Fn)       # viscous, below the cap
+    F = Fn * n + ft * t
+    assert abs(o[0] - F[0]) <= 1e-12 * abs(Fn) and abs(o[1] - F[1]) <= 1e-12 * abs(Fn)
+    assert abs(o[2] - rl * ft) <= 1e-12 * abs(rl * ft)
+    assert abs(o[3] - rj * ft) <= 1e-12 * abs(rj * ft)
+    assert abs(o[11] - vt) <= 1e-12 * abs(vt)
+
+
+def test_tangential_friction_removes_spin_energy(orc):
+    """Friction dissipates: for two overlapping floes that only spin, the
+    torques do work sum(tau w) = f_t (r_l w_l + r_j w_j) = -c h G v_t^2 < 0,
+    so one forward-Euler step lowers the rotational kinetic energy, by that
+    rate times dt to first order (a sign error on a spin term, on f_t or on a
+    torque raises it).  Drag off."""
+    p = base_params(Cd=0.0, E=4e3, G=5e3, eta=0.0, mu=0.5)
+    rl, rj, d = 1000.0, 1500.0, 2400.0
+    fl = {"x": np.array([3e5, 3e5 + d]), "y": np.array([4e5, 4e5]), "theta": np.zeros(2),
+          "u": np.zeros(2), "v": np.zeros(2), "omega": np.array([3e-4, -5e-4]),
+          "r": np.array([rl, rj]), "h": np.array([1.0, 1.0])}
+    m = orc.Model(p, fl)
+    mass = p["rho_ice"] * PI * fl["r"] ** 2 * fl["h"]
+    I = mass * fl["r"] ** 2
+    ke0 = 0.5 * np.sum(I * fl["omega"] ** 2)
+    dt = 0.5
+    m.step(dt, 1)
+    f = m.floes()
+    ke1 = 0.5 * np.sum(I * f["omega"] ** 2)
+    c = _chord_heron(d, rl, rj)
+    vt = -fl["omega"][1] * rj - fl["omega"][0] * rl
+    rate = -c * p["G"] * vt * vt
+    assert ke1 < ke0
+    assert abs((ke1 - ke0) / dt - rate) < 1e-3 * abs(rate)
+
+
+def test_normal_dashpot(orc):
+    """Normal law with the dashpot (reading c5): F = c h (E delta + eta v_n),
+    v_n = (v_j - v_l) . n, never attractive.  Approaching floes (v_n < 0)
+    push apart harder than the spring alone, by exactly c h eta |v_n|;
+    separating ones less; separating fast enough, not at all (F = 0, and
+    then no friction either)."""
+    rl, rj, hl, hj, d = 1200.0, 800.0, 1.0, 1.5, 1950.0
+    p = base_params(E=4e3, G=5e3, eta=1e5, mu=0.3)
+    c = _chord_heron(d, rl, rj)
+    hc = min(hl, hj)
+    spring = c * hc * p["E"] * (d - rl - rj)
+    for vn in (-0.05, 0.0, 0.8, 3.0):
+        hit, o = orc.pair(p, 1e6, 1e6, (1e5, 1e5, 0, 0, 0, rl, hl), (1e5 + d, 1e5, vn, 0.0, 0, rj, hj))
+        want = min(0.0, spring + c * hc * p["eta"] * vn)
+        assert hit and abs(o[4] - want) <= 1e-12 * abs(spring)
+        assert abs(o[0] - want) <= 1e-12 * abs(spring) and o[1] == 0.0
+    assert spring + c * hc * p["eta"] * 3.0 > 0 > spring + c * hc * p["eta"] * 0.8   # only the last is clamped
+
+
 def test_c3_thickness_factor(orc):
     """Eq. (2.2), reading c3: the contact law scales with the thinner floe's
     thickness over h_ref, min(h_l, h_j) / h_ref, in the normal and in the
