@@ -251,19 +251,25 @@ int ms_info(ms_model *m, int64_t *out);
  * a host code that reserves all its device memory up front and forbids
  * allocation inside its time loop, or a framework whose allocator already owns
  * the device memory.  It bins the floes by the coarse cell holding their
- * centre (half-open cells of `grid`) and writes out[ncell][MS_NMOM] with the
- * columns of ms_moments, in ascending floe order within each cell.
+ * centre and writes out[ncell][MS_NMOM] with the columns of ms_moments, in
+ * ascending floe order within each cell.  Cells are assigned as ms_init
+ * assigns them: each coordinate is first wrapped into the periodic domain
+ * (X - Lx floor(X / Lx); y over the nens stacked realizations), then falls in
+ * the half-open cell [i dX, (i + 1) dX); so x = Lx lands in cell 0 and
+ * x = -dX in the last column.
  * Inputs (device, FP64, n each, caller-owned): x, y in domain coordinates,
  * u, v, omega, r, h, and fd = [3][n] per-floe drag (Fx, Fy, torque; zeros if
  * there is none); mass rho_ice pi r^2 h, inertia m r^2 (inertia_half = 1:
  * m r^2 / 2).  out is device memory for ncell * MS_NMOM doubles.
  * Working memory is one fixed device array compiled into the library (about
  * 2.2 MB on every device that loads it, held until exit): at most 262144
- * floes and 16384 cells; larger inputs return MS_ERR_ARG.  The first call on
- * each device looks the array's device address up, so make it before any
- * stream capture.  All calls on a device share that array and each call
- * clears what must start at zero, so calls whose work overlaps on the GPU
- * (from different host threads or streams) corrupt each other's results.
+ * floes and 16384 cells; larger inputs return MS_ERR_ARG.  Every call looks
+ * the array's device address up on the current device
+ * (cudaGetSymbolAddress), so the call works on whichever device is current
+ * and after a context was torn down and created again.  All calls on a device
+ * share that array and each call clears what must start at zero, so calls
+ * whose work overlaps on the GPU (from different host threads or streams)
+ * corrupt each other's results.
  * The work runs on `stream` (NULL: the legacy default stream) and the call
  * waits for it before returning. */
 int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia_half, int64_t n,

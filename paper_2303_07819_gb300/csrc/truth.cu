@@ -11,7 +11,6 @@
 // r_l + r_split of its own and the 3 x 3 neighbourhood in the second.  The
 // state is double-buffered: the step reads one copy and writes the other.
 #include <climits>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -580,6 +579,25 @@ namespace {
 
 __global__ void k_set_int(int *p, int v) { *p = v; }
 
+// cell of a caller's floe: each coordinate wrapped into [0, L) by
+// X - L floor(X / L), then the half-open cell floor(X / (L / n)), clamped
+// (rounding can put a wrapped X on L itself) -- the assignment ms_init makes
+__device__ __forceinline__ int wrap_cell(double X, double L, int n)
+{
+    const double Xw = X - L * floor(X / L);
+    int i = (int)floor(Xw / (L / n));
+    return i < 0 ? 0 : (i > n - 1 ? n - 1 : i);
+}
+
+__global__ void k_bin_wrap64(const double *x, const double *y, double Lx, double Ly, TruthBins tb, long long n)
+{
+    const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int b = wrap_cell(y[l], Ly, tb.nby) * tb.nbx + wrap_cell(x[l], Lx, tb.nbx);
+    tb.bin[l] = b;
+    atomicAdd(&tb.count[b], 1);
+}
+
 }  // namespace
 
 }  // namespace msd
@@ -599,23 +617,15 @@ int noalloc_max_cells() { return MS_NA_CELLS; }
 
 // Device address of the scratch array on the current device.  The address a
 // host program sees for the symbol is only a host-side placeholder; the device
-// address is looked up once per device, with that device current.
+// address is looked up on every call, with the caller's device current, so a
+// context that was torn down and created again (where the module may load at
+// another address) never gets a stale pointer.
 static cudaError_t noalloc_scratch(int **out)
 {
-    static std::mutex mu;
-    static int *addr[128] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, ms_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, ms_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = reinterpret_cast<int *>(p);
-    }
-    *out = addr[dev];
+    *out = reinterpret_cast<int *>(p);
     return cudaSuccess;
 }
 
@@ -642,7 +652,7 @@ cudaError_t noalloc_cell_moments(const Geom &g, double mass_c, double inertia_f,
     const int T = 256;
     const unsigned G = (unsigned)((n + T - 1) / T);
     e = counting_sort(b, n, [&] {
-        k_bin64<<<G, T, 0, st>>>(x, y, nullptr, g.Lx, g.Ly, b, n);
+        k_bin_wrap64<<<G, T, 0, st>>>(x, y, g.Lx, g.Ly, b, n);
     }, st);
     if (e != cudaSuccess) return e;
     k_truth_cell_moments<double><<<(nbins + 127) / 128, 128, 0, st>>>(u, v, w, r, h, fd, n, mass_c, inertia_f,

@@ -70,6 +70,42 @@ def test_noalloc_moments_match_existing_entry_points():
     m.close()
 
 
+def test_noalloc_half_open_cells_with_wrap():
+    """Floes on a cell's left edge, at X = Lx and at negative coordinates
+    (positions a caller has not wrapped) land in the cells the oracle and
+    ms_init give them: the coordinate wrapped into the periodic domain, then
+    the half-open cell (reading c23).  Two calls in a row, against the
+    oracle's moments of the same floes and against ms_moments."""
+    torch = pytest.importorskip("torch")
+    from oracle import oracle as O
+    from paper_2303_07819_gb300 import msdem as ms
+    ms.load()
+    O.build()
+    L = 4.0e4
+    dX = L / 4
+    xs = [dX, 2 * dX, L, -dX, 0.5 * dX, -L - 0.5 * dX, 2 * L + dX]
+    ys = [0.5 * dX, dX, 3 * dX, 0.5 * dX, -0.5 * dX, L, -3 * L + 2.5 * dX]
+    n = len(xs)
+    fl = {"x": np.array(xs), "y": np.array(ys), "theta": np.zeros(n), "u": np.linspace(0.1, 0.7, n),
+          "v": np.linspace(-0.2, 0.3, n), "omega": np.linspace(1e-5, 3e-5, n), "r": np.linspace(100.0, 160.0, n),
+          "h": np.linspace(1.0, 2.0, n)}
+    p = I._phys(dt=5.0)
+    p.update({"nx": 4, "ny": 4, "Lx": L, "Ly": L, "modes": np.zeros((0, 4))})
+    o = O.Model(p, fl)
+    ref = o.moments()
+    m = ms.Model(p, fl, ms.MS_FP64)
+    for _ in range(2):
+        got = _call(ms, torch, p, fl)
+        assert np.array_equal(got[:, 0], ref[:, 0]), (got[:, 0], ref[:, 0])
+        assert got[:, 0].tolist() == [0, 1, 0, 2, 0, 0, 1, 0, 0, 1, 0, 0, 2, 0, 0, 0]
+        e = rel_errors(got[:, :9], ref[:, :9], p, 1e-12)
+        assert e.max() <= TOL64, report(e)
+        e = rel_errors(got, m.moments(), p, 1e-12)
+        assert e.max() <= TOL64, report(e)
+    m.close()
+    o.close()
+
+
 def test_noalloc_rejects_oversize():
     pytest.importorskip("torch")
     from paper_2303_07819_gb300 import msdem as ms
