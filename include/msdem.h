@@ -368,8 +368,8 @@ int ms_closure_stats(ms_model *m, int64_t *out);
  * per-cell moments, window sums, coarse state and gradual-update targets, the
  * device control block (step counters, flags), dt, the launch choice, the
  * FP32 candidate lists, and the truth DEM's state and last drag.  The file
- * holds device-order raw values of this library and is read back only by
- * ms_load.  MS_ERR_STATE while a closure is attached; MS_ERR_ARG if the file
+ * holds device-order raw values of this library, each item followed by a
+ * hash of its bytes, and is read back only by ms_load.  MS_ERR_STATE while a closure is attached; MS_ERR_ARG if the file
  * cannot be written; MS_ERR_CUDA if reading the device state fails. */
 int ms_save(ms_model *m, const char *path);
 
@@ -377,11 +377,14 @@ int ms_save(ms_model *m, const char *path);
  * with the same grid, boundary, precision, number of floes and floes per
  * cell (and, for an exact resume, the same floes, forcing and laws as the
  * saved model): it then continues as the saved model would have, bit for
- * bit, and restores the saved launch choice.  MS_ERR_ARG for a file that is
- * not such a checkpoint, is truncated, or belongs to another model (after a
- * failure in the middle of the state the model's state is undefined: load
- * again or call ms_set_floes); MS_ERR_STATE while a closure is attached;
- * MS_ERR_CUDA if writing the device state fails. */
+ * bit, and restores the saved launch choice.  Every item of the file
+ * carries a 64-bit FNV-1a hash of its bytes, and the whole file is read and
+ * checked before the model changes: MS_ERR_ARG for a file that is not such a
+ * checkpoint, is truncated, has an item whose bytes do not match its hash
+ * (the message says "checksum"), or belongs to another model, and the model
+ * is then left as it was; MS_ERR_STATE while a closure is attached;
+ * MS_ERR_CUDA if writing the device state fails (the model's state is then
+ * undefined: load again or call ms_set_floes). */
 int ms_load(ms_model *m, const char *path);
 
 /* Release the model's device memory, graphs, events and stream. */

@@ -838,14 +838,30 @@ const char *ms_last_error(void) { return g_err.c_str(); }
 
 // ---------------------------------------------------------------- checkpoint
 // File layout: an 8-byte tag, then (for every item below, in this order) an
-// int64 byte count followed by the bytes.  Items: the header (precision,
+// int64 byte count, the bytes, and the 64-bit FNV-1a hash of those bytes.
+// ms_load reads and checks the whole file before it changes the model, so a
+// truncated or corrupted file (a flipped byte in a candidate list would
+// otherwise index past its cell) is refused with the model left as it was.
+// Items: the header (precision,
 // sizes, schedule counters, dt, launch choice), the cell offsets (the layout
 // the state is stored in), the msDEM state in cell order, the per-cell
 // moments, window sums, coarse state and gradual-update targets, the device
 // control block, the candidate lists (FP32), and the truth DEM's current
 // state with its last drag.
 namespace {
-constexpr char CK_TAG[8] = {'M', 'S', 'D', 'E', 'M', 'C', 'K', '1'};
+constexpr char CK_TAG[8] = {'M', 'S', 'D', 'E', 'M', 'C', 'K', '2'};
+
+// 64-bit FNV-1a (Fowler, Noll, Vo) of a byte string
+uint64_t fnv1a64(const void *p, size_t bytes)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < bytes; i++) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
 
 struct CkHeader {
     int32_t precision, nens, walls, variant, threads, persistent;
@@ -930,7 +946,9 @@ int ms_save(ms_model *m, const char *path)
     bool ok = std::fwrite(CK_TAG, 1, 8, f) == 8;
     auto put = [&](const void *p, size_t bytes) {
         const int64_t b = (int64_t)bytes;
-        ok = ok && std::fwrite(&b, sizeof(b), 1, f) == 1 && (bytes == 0 || std::fwrite(p, 1, bytes, f) == bytes);
+        const uint64_t hash = fnv1a64(p, bytes);
+        ok = ok && std::fwrite(&b, sizeof(b), 1, f) == 1 && (bytes == 0 || std::fwrite(p, 1, bytes, f) == bytes) &&
+             std::fwrite(&hash, sizeof(hash), 1, f) == 1;
     };
     put(&h, sizeof(h));
     put(m->h_off.data(), sizeof(int) * m->h_off.size());
@@ -956,16 +974,19 @@ int ms_load(ms_model *m, const char *path)
     if (!f) return fail(MS_ERR_ARG, "cannot open %s", path);
     char tag[8];
     bool ok = std::fread(tag, 1, 8, f) == 8 && std::memcmp(tag, CK_TAG, 8) == 0;
+    bool hash_ok = true;
     auto get = [&](void *p, size_t bytes) {
         int64_t b = -1;
+        uint64_t hash = 0;
         ok = ok && std::fread(&b, sizeof(b), 1, f) == 1 && b == (int64_t)bytes &&
-             (bytes == 0 || std::fread(p, 1, bytes, f) == bytes);
+             (bytes == 0 || std::fread(p, 1, bytes, f) == bytes) && std::fread(&hash, sizeof(hash), 1, f) == 1;
+        if (ok && hash != fnv1a64(p, bytes)) hash_ok = ok = false;
     };
     CkHeader h{};
     get(&h, sizeof(h));
     if (!ok) {
         std::fclose(f);
-        return fail(MS_ERR_ARG, "%s is not a checkpoint of this library", path);
+        return fail(MS_ERR_ARG, "%s is not a checkpoint of this library%s", path, hash_ok ? "" : " (checksum)");
     }
     if (h.precision != m->precision || h.nens != m->g.nens || h.walls != m->g.walls || h.n != m->n ||
         h.ncell != m->ncell) {
@@ -976,36 +997,43 @@ int ms_load(ms_model *m, const char *path)
     get(off.data(), sizeof(int) * off.size());
     if (!ok || off != m->h_off) {
         std::fclose(f);
-        return fail(MS_ERR_ARG, "checkpoint of another floe layout (the floes per cell differ)");
+        return fail(MS_ERR_ARG, "checkpoint of another floe layout (the floes per cell differ)%s",
+                    hash_ok ? "" : " or corrupted (checksum)");
     }
-    // the saved launch first (configuring a launch forgets the candidate
-    // lists; the checkpoint's lists are restored below)
+    // every item read and its hash checked before the model changes (the
+    // truth state goes into the first of its two copies)
+    const int tcur_keep = m->tcur;
+    m->tcur = 0;
+    const std::vector<CkItem> items = ck_items(m);
+    m->tcur = tcur_keep;
+    std::vector<std::vector<unsigned char>> bufs(items.size());
+    for (size_t i = 0; i < items.size() && ok; i++) {
+        bufs[i].resize(items[i].bytes);
+        get(bufs[i].data(), items[i].bytes);
+    }
+    if (ok) {   // nothing may follow the last item
+        unsigned char extra;
+        ok = std::fread(&extra, 1, 1, f) == 0;
+    }
+    std::fclose(f);
+    if (!ok)
+        return fail(MS_ERR_ARG, "%s is %s", path,
+                    hash_ok ? "truncated or of another model" : "corrupted (an item's checksum does not match)");
+    // the saved launch (configuring a launch forgets the candidate lists;
+    // the checkpoint's lists are restored below)
     CellLaunch c = m->cl;
     c.variant = h.variant;
     c.threads = h.threads;
     c.persistent = h.persistent;
     c.bin_beta = (float)h.bin_beta;
     int rc = configure_launch(m, c);
-    if (rc) {
-        std::fclose(f);
-        return rc;
-    }
+    if (rc) return rc;
     CK(cudaStreamSynchronize(m->stream));
     m->tcur = 0;   // the truth state goes into the first copy
-    std::vector<unsigned char> buf;
-    for (const CkItem &it : ck_items(m)) {
-        buf.resize(it.bytes);
-        get(buf.data(), it.bytes);
-        if (!ok) break;
-        if (it.bytes && cudaMemcpy(it.dev, buf.data(), it.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
-            std::fclose(f);
+    for (size_t i = 0; i < items.size(); i++) {
+        if (items[i].bytes &&
+            cudaMemcpy(items[i].dev, bufs[i].data(), items[i].bytes, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(MS_ERR_CUDA, "writing the checkpoint's state to the device failed");
-        }
-    }
-    std::fclose(f);
-    if (!ok) {
-        CK(invalidate_lists(m));
-        return fail(MS_ERR_ARG, "%s is truncated or of another model", path);
     }
     m->steps = h.steps;
     m->truth_steps = h.truth_steps;

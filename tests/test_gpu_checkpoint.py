@@ -91,3 +91,55 @@ def test_checkpoint_of_another_model_is_refused(ms, tmp_path):
     with pytest.raises(ms.MsError) as e:
         a.load_checkpoint(str(tmp_path / "missing.ck"))
     assert e.value.code == -1
+
+
+def _item_offsets(path):
+    """(payload offset, bytes) of every item of a checkpoint file: an 8-byte
+    tag, then per item an int64 byte count, the bytes and an 8-byte hash."""
+    data = open(path, "rb").read()
+    out, pos = [], 8
+    while pos < len(data):
+        nb = int(np.frombuffer(data[pos:pos + 8], dtype=np.int64)[0])
+        out.append((pos + 8, nb))
+        pos += 8 + nb + 8
+    assert pos == len(data)
+    return out
+
+
+@pytest.mark.parametrize("which", ["list_head", "list_tail", "state"])
+def test_corrupted_checkpoint_is_refused_and_changes_nothing(ms, tmp_path, which):
+    """A checkpoint whose bytes were altered inside an item (list entries that
+    would index past their cell, or a floe's state) is refused with
+    MS_ERR_ARG before the model changes: the refused model then continues
+    bit for bit as its untouched twin."""
+    s = I.batched_128x128(seed=11, nx=16)
+    p, fl, dt = s["params"], s["floes"], s["dt"]
+    path = str(tmp_path / "c.ck")
+    a = ms.Model(p, fl, ms.MS_FP32)
+    a.step(dt, 23)
+    a.save(path)
+    items = _item_offsets(path)
+    n = fl["x"].shape[0]
+    # items: header, offsets, 8 state arrays, moments, window, q, targets,
+    # control block, list heads, list tails, ...
+    k = {"state": 5, "list_head": 15, "list_tail": 16}[which]
+    off, nb = items[k]
+    if which == "list_head":
+        assert nb == 16 * n
+    data = bytearray(open(path, "rb").read())
+    for j in range(4):
+        data[off + (nb // 3) + j] ^= 0xA5
+    bad = str(tmp_path / "bad.ck")
+    open(bad, "wb").write(bytes(data))
+    b = ms.Model(p, fl, ms.MS_FP32)
+    b.step(dt, 23)
+    twin = ms.Model(p, fl, ms.MS_FP32)
+    twin.step(dt, 23)
+    with pytest.raises(ms.MsError) as e:
+        b.load_checkpoint(bad)
+    assert e.value.code == -1 and "checksum" in str(e.value)
+    b.step(dt, 40)
+    twin.step(dt, 40)
+    _same(b, twin)
+    for m in (a, b, twin):
+        m.close()
