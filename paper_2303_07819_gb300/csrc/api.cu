@@ -83,6 +83,8 @@ struct ms_model {
     Ctrl *d_ctrl = nullptr;
     unsigned long long *d_cmax = nullptr;   // [nens] coarse-step CFL maxima
     int2 *d_pack = nullptr;                  // [ncell] packed-warp table (at most one warp per cell)
+    int4 *d_rgroups = nullptr, *d_ritems = nullptr;   // [ncell] variant 5: groups of cells per block, cell places
+    float *d_carry = nullptr, *d_xcarry = nullptr;    // [RUN_NCARRY][n] variant 5: what a run hands to the next
     // truth
     DevState32 t32[2]{};
     DevState64 t64[2]{};
@@ -416,6 +418,9 @@ static StepCommon step_common(ms_model *m, long long i_local, double *mom, doubl
     sc.n_t = m->fc.n_t;
     sc.couple = m->fc.couple;
     sc.i_local = i_local;
+    sc.carry_in = m->d_carry;
+    sc.carry_out = m->d_carry;
+    sc.ncarry = m->n;
     return sc;
 }
 
@@ -457,6 +462,7 @@ static StepCommon cell_common(ms_model *m, long long i_local, bool scratch_out)
     StepCommon sc = step_common(m, i_local, scratch_out ? m->d_xmom : m->d_mom,
                                 scratch_out ? m->d_xwin : m->d_win);
     sc.nl = scratch_out ? m->xnl : m->nl;
+    if (scratch_out) sc.carry_out = m->d_xcarry;
     if (hybrid_on(m)) {
         sc.order = m->d_order2;
         sc.live = m->d_live;
@@ -484,7 +490,7 @@ static int64_t interval_launches(const ms_model *m)
     if (m->cl.variant == 0 || m->precision == MS_FP64) return m->interval;
     int64_t k = 0;
     for (int s = 0; s < m->cl.nseg; s++)
-        k += (m->cl.seg_kind[s] == 2 || (m->cl.variant == 3 && m->cl.seg_kind[s] == 1)) ? 1 : m->interval;
+        k += (m->cl.seg_kind[s] >= 2 || (m->cl.variant == 3 && m->cl.seg_kind[s] == 1)) ? 1 : m->interval;
     return k;
 }
 
@@ -663,6 +669,17 @@ static void fill_phys(ms_model *m)
         // by more than 1/16 cycle across one cell
         if ((std::fabs(kx) * Lcx + std::fabs(ky) * Lcy) / (2.0 * PI_D) > 1.0 / 16.0) Q.taylor = 0;
     }
+    // Variant 5 evaluates the current at a floe from its first-order Taylor
+    // expansion about a nearby centre.  The neglected term is at most
+    // 1/2 |d|^2 sum_m |A_m| |k_m|^2 per component (A_m the mode's velocity or
+    // curl amplitude), so |d| <= 2^-11.5 / k_max keeps it below 2^-24 of
+    // sum_m |A_m|, i.e. below the FP32 rounding of the mode sum itself.
+    {
+        double kmax = 0.0;
+        for (int k = 0; k < P.n_modes; k++) kmax = std::max(kmax, std::hypot(P.mKx[k], P.mKy[k]));
+        const double dmax = kmax > 0.0 ? std::pow(2.0, -11.5) / kmax : 1.0e30;
+        Q.ocean_d2 = (float)std::min(dmax * dmax, 1.0e30);
+    }
     P.drag_o = f.Cd * f.rho_o * PI_D;
     P.drag_a = f.Ca * f.rho_a * PI_D;
     P.wind_x = f.wind_x; P.wind_y = f.wind_y;
@@ -682,8 +699,11 @@ static void fill_phys(ms_model *m)
 // launched with a block size and shared memory that fit its largest cell.
 static void make_segments(ms_model *m, CellLaunch &c)
 {
-    const SizeClass *cls = c.variant == 4 ? kClassesV4 : (c.variant >= 2 ? kClassesV2 : kClassesV1);
-    const int ncls = c.variant == 4 ? (int)(sizeof(kClassesV4) / sizeof(SizeClass))
+    const SizeClass *cls = c.variant == 5   ? kClassesV5
+                           : c.variant == 4 ? kClassesV4
+                                            : (c.variant >= 2 ? kClassesV2 : kClassesV1);
+    const int ncls = c.variant == 5   ? (int)(sizeof(kClassesV5) / sizeof(SizeClass))
+                     : c.variant == 4 ? (int)(sizeof(kClassesV4) / sizeof(SizeClass))
                      : c.variant >= 2 ? (int)(sizeof(kClassesV2) / sizeof(SizeClass))
                                       : (int)(sizeof(kClassesV1) / sizeof(SizeClass));
     c.nseg = 0;
@@ -711,12 +731,128 @@ static void make_segments(ms_model *m, CellLaunch &c)
     c.ev_fork = m->ev_fork;
 }
 
+// Variant 5 keeps each floe's window sums since the last gradual update in
+// the carry between runs; before the state is replaced or another variant
+// takes over inside a coarse interval they go into the window.
+static cudaError_t fold_carry(ms_model *m)
+{
+    if (m->precision != MS_FP32 || m->cl.variant != 5 || !m->fc.couple || m->steps % m->interval == 0)
+        return cudaSuccess;
+    const StepCommon sc = step_common(m, m->steps % m->interval, m->d_mom, m->d_win);
+    return launch_carry_flush(m->s32, sc, m->d_carry, m->n, m->stream);
+}
+
+// Variant 5: the cells of the resident classes packed into the groups one
+// block takes.  A cell of more than 512 floes opens a group of 4 floes per
+// thread (1024 floes), one of more than 256 a group of 2 per thread; smaller
+// cells go, largest first, into the open group with the least room that
+// still fits them (at most RUN_GCMAX cells), else open a group of one floe
+// per thread.  Each class's groups run in decreasing order of floes.  Each
+// cell gets about sqrt(n)/beta bins per side, at most sqrt(n) (so a group's
+// bins fit its shared memory), none below 3.
+static int build_groups(ms_model *m, CellLaunch &cl)
+{
+    struct G {
+        int K, room, nf;
+        std::vector<int> cells;
+    };
+    std::vector<G> gs;
+    const int cap_max = 4 * RUN_T;
+    std::vector<std::vector<int>> by_room(cap_max + 1);   // open groups by free floes
+    auto ncount = [&](int cc) { return m->h_off[cc + 1] - m->h_off[cc]; };
+    auto place = [&](int gi, int cc) {
+        G &g = gs[gi];
+        const int n = ncount(cc);
+        g.cells.push_back(cc);
+        g.nf += n;
+        g.room -= n;
+        if ((int)g.cells.size() < RUN_GCMAX) by_room[g.room].push_back(gi);
+    };
+    int first_item = -1, end_item = -1;
+    for (int s = 0; s < cl.nseg; s++)
+        if (cl.seg_kind[s] == 3) {
+            if (first_item < 0) first_item = cl.seg_begin[s];
+            end_item = cl.seg_end[s];
+        }
+    for (int it = std::max(first_item, 0); it < end_item; it++) {
+        const int cc = m->h_order[it], n = ncount(cc);
+        if (n > RUN_T) {
+            const int K = n > 2 * RUN_T ? 4 : 2;
+            gs.push_back(G{K, K * RUN_T, 0, {}});
+            place((int)gs.size() - 1, cc);
+            continue;
+        }
+        int found = -1;
+        for (int room = n; room <= cap_max && found < 0; room++) {
+            auto &b = by_room[room];
+            while (!b.empty()) {
+                const int gi = b.back();
+                b.pop_back();
+                if (gs[gi].room == room && (int)gs[gi].cells.size() < RUN_GCMAX) {   // still current
+                    found = gi;
+                    break;
+                }
+            }
+        }
+        if (found < 0) {
+            gs.push_back(G{1, RUN_T, 0, {}});
+            found = (int)gs.size() - 1;
+        }
+        place(found, cc);
+    }
+    std::vector<int4> groups, items;
+    items.reserve(m->ncell);
+    for (int s = 0; s < cl.nseg; s++) {
+        if (cl.seg_kind[s] != 3) continue;
+        const int K = cl.seg_maxn[s] / RUN_T;
+        std::vector<int> mine;
+        for (int gi = 0; gi < (int)gs.size(); gi++)
+            if (gs[gi].K == K) mine.push_back(gi);
+        std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return gs[a].nf > gs[b].nf; });
+        const int first = (int)groups.size();
+        for (int gi : mine) {
+            int4 g = make_int4((int)items.size(), 0, 0, 0);
+            for (int cc : gs[gi].cells) {
+                const int n = ncount(cc);
+                int nb = (int)std::floor(std::sqrt((double)n) / cl.bin_beta);
+                nb = std::min(nb, (int)std::floor(std::sqrt((double)n)));
+                if (nb < 3) nb = 0;
+                items.push_back(make_int4(cc, g.z, nb, g.w));
+                g.y++;
+                g.z += n;
+                g.w += nb * nb + 1;
+            }
+            groups.push_back(g);
+        }
+        cl.rgroups[s] = m->d_rgroups + first;
+        cl.rngroups[s] = (int)groups.size() - first;
+    }
+    cl.ritems = m->d_ritems;
+    if ((long long)groups.size() > m->ncell || (long long)items.size() > m->ncell)
+        return fail(MS_ERR_STATE, "variant 5 grouping overflow");
+    if (!groups.empty())
+        CK(cudaMemcpyAsync(m->d_rgroups, groups.data(), sizeof(int4) * groups.size(), cudaMemcpyHostToDevice,
+                           m->stream));
+    if (!items.empty())
+        CK(cudaMemcpyAsync(m->d_ritems, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                           m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    return MS_OK;
+}
+
 static int configure_launch(ms_model *m, const CellLaunch &cl_in)
 {
     CellLaunch cl = cl_in;
     if (cl.variant == 0 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure needs a binned cell kernel");
+    if (cl.variant == 5 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure runs with variants 1-4");
+    if (cl.variant == 5 && m->precision != MS_FP32) return fail(MS_ERR_ARG, "variant 5 is FP32 only");
+    if (cl.variant != 5 && m->cl.variant == 5) CK(fold_carry(m));
     if (cl.variant >= 1) make_segments(m, cl);
     else cl.nseg = 0;
+    if (cl.variant == 5) {
+        const int rc = build_groups(m, cl);
+        if (rc) return rc;
+    }
     // packed warps: consecutive cells of the class, at most 32 floes and 32
     // cells per warp
     cl.pack = m->d_pack;
@@ -846,8 +982,8 @@ const char *ms_last_error(void) { return g_err.c_str(); }
 // sizes, schedule counters, dt, launch choice), the cell offsets (the layout
 // the state is stored in), the msDEM state in cell order, the per-cell
 // moments, window sums, coarse state and gradual-update targets, the device
-// control block, the candidate lists (FP32), and the truth DEM's current
-// state with its last drag.
+// control block, the candidate lists and the running window sums (FP32),
+// and the truth DEM's current state with its last drag.
 namespace {
 constexpr char CK_TAG[8] = {'M', 'S', 'D', 'E', 'M', 'C', 'K', '2'};
 
@@ -903,6 +1039,7 @@ static std::vector<CkItem> ck_items(ms_model *m)
         dev(m->nl.cstep, sizeof(long long) * nc);
         dev(m->nl.skin, sizeof(float) * nc);
     }
+    if (m->precision == MS_FP32 && m->d_carry) dev(m->d_carry, sizeof(float) * RUN_NCARRY * n);
     if (m->g.nens == 1 && m->n > 0) {
         const size_t es = m->precision == MS_FP64 ? 8 : 4;
         if (m->precision == MS_FP64) {
@@ -1224,6 +1361,11 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     } else {
         CKM(alloc32(m, m->s32, n));
         CKM(alloc_lists(m, m->nl, n, nc));
+        CKM(dalloc(m, &m->d_rgroups, nc));
+        CKM(dalloc(m, &m->d_ritems, nc));
+        CKM(dalloc(m, &m->d_carry, (size_t)RUN_NCARRY * n));
+        CKM(dalloc(m, &m->d_xcarry, (size_t)RUN_NCARRY * n));
+        CKM(cudaMemsetAsync(m->d_carry, 0, sizeof(float) * RUN_NCARRY * (size_t)n, m->stream));
         if (nens == 1) {
             CKM(alloc32(m, m->t32[0], n));
             CKM(alloc32(m, m->t32[1], n));
@@ -1468,6 +1610,7 @@ int ms_set_floes(ms_model *m, const ms_floes *floes)
             return fail(MS_ERR_ARG, "floe %lld has r <= 0 or h <= 0", l);
         }
         if (first[1] < (unsigned long long)m->n) return fail(MS_ERR_ARG, "floe %lld left its cell", (long long)first[1]);
+        CK(fold_carry(m));
         if ((rc = raw_to_state(m))) return rc;
     }
     CK(invalidate_lists(m));
@@ -1648,7 +1791,7 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
-    if (variant != 0 && !((variant >= 1 && variant <= 4) && m->precision == MS_FP32))
+    if (variant != 0 && !((variant >= 1 && variant <= 5) && m->precision == MS_FP32))
         return fail(MS_ERR_ARG, "unsupported variant %d", variant);
     if (threads != 64 && threads != 128 && threads != 256) return fail(MS_ERR_ARG, "threads must be 64, 128 or 256");
     if (!(bin_beta > 0.1 && bin_beta < 10.0)) return fail(MS_ERR_ARG, "bin_beta must be in (0.1, 10)");
@@ -1770,6 +1913,7 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
     m->hybrid_tol = tol;
     CellLaunch cl = m->cl;
     if (mode >= 0 && cl.variant == 0) cl.variant = 2;
+    if (mode >= 0 && cl.variant == 5) cl.variant = 4;     // the closure's cell selection runs on variants 1-4
     int rc = configure_launch(m, cl);
     if (rc) {
         m->hybrid_mode = prev_mode;

@@ -1,0 +1,824 @@
+// cell_run.cu -- FP32 msDEM cell steps for a whole run of fine steps in one
+// launch, every floe resident in a thread's registers (launch variant 5).
+//
+// Between two coarse steps a cell depends on nothing but itself (Sec. 3.1:
+// each coarse cell carries its own doubly periodic DEM; the gradual-update
+// increments of Algorithm 1 are fixed at the coarse step), so a block can
+// take its cells through every fine step of a run and touch global memory
+// only at the run's two ends.
+//
+// Work: the cells are packed into groups of at most 256 K floes (K = 1, 2
+// or 4 floes per thread of a 256-thread block; a group holds at most one
+// cell of more than 256 (K = 2) or 512 (K = 4) floes, and as many smaller
+// cells as fit, first fit by decreasing size).  Each K is one persistent
+// launch whose blocks take groups from a ticket queue in decreasing order of
+// work.  A floe's state, forcing and running sums stay in registers for the
+// run; per step it publishes its position and velocity to shared memory (two
+// buffers, so one barrier per step separates the step that reads a buffer
+// from the one that writes it again).
+//
+// Contacts (Eq. 2.2): a floe tests only its candidates, the floes of its
+// cell within reach at the last build: r_l G + s_l + r_j G + s_j, with G the
+// growth the cell's gradual updates can still give its radii in this
+// coarse interval and s_f the floe's own skin (its speed times a horizon of
+// steps).  A build is a counting sort of the group's floes into per-cell
+// bins (floes whose reach fits half a bin) and a per-cell list of the other,
+// "large" floes; small floes search their 3 x 3 bins and the large list
+// (recording a hit on both sides), large floes the large list.  A group
+// builds at the first step of a run and again once a floe has moved more
+// than its skin.  A list holds at most LMAX candidates; a floe whose list
+// overflowed tests every floe of its cell instead.  Each list is sorted by
+// floe index, so a floe always sums its contacts in ascending partner order
+// -- the order of the all-pairs loop over (l < j) in cell order, whatever
+// the skins, bins or build steps were.
+//
+// Ocean (Eq. 2.1c-d at the floe's global position): each floe keeps the
+// first-order Taylor expansion of the current and its curl about a centre
+// near it and evaluates that every step (6 multiply-adds instead of a sum
+// of modes).  The neglected term stays below the FP32 rounding of the mode
+// sum while the floe is within sqrt(P.ocean_d2) of the centre (the bound is
+// derived from the modes' wave numbers on the host); when a floe of a warp
+// goes farther, or wraps across its cell's edge, the whole warp expands
+// again at its floes' current positions with the modes' full sums.
+//
+// Moments (Algorithm 1): the window needs per step the cell's mass-weighted
+// mean velocity and its drag totals.  Masses change only at a gradual
+// update, so each floe sums its velocity and drag over the steps of one
+// mass (from one gradual-update step to the step before the next), and the
+// block reduces these sums once per such group of steps:
+// sum_s M u_s / M = sum_f m_f (sum_s u_f,s) / M.  A run that ends inside an
+// interval stores the floes' running sums and expansion centres (the carry)
+// and the next run picks them up, so a coarse interval gives the same result
+// bit for bit however it is split into runs.  The cell moments of the run's
+// last step (all 12 columns) are reduced once at the end.  Reductions are
+// segmented warp shuffles in a fixed tree, then a cell's warp partials in
+// order in FP64: deterministic.
+#include <cstdint>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace msd {
+
+namespace {
+
+constexpr int RT = RUN_T;          // threads per block
+constexpr int LMAX = 16;           // candidate slots per floe
+constexpr int GCMAX = RUN_GCMAX;   // cells per group
+constexpr int WT = 128;            // steps per wind table
+constexpr int NRED = 6;            // values per reduction pass
+constexpr float SKIN_STEPS = 24.0f;   // horizon of a floe's skin, in fine steps (at its build speed)
+
+template <int K>
+struct RunSm {
+    static constexpr int F = RT * K;
+    uint2 Q[2][F];                  // fixed-point position, per step buffer
+    float4 A[2][F];                 // u, v, w, r
+    float H[F];                     // thickness
+    float RE[F];                    // reach of each floe at the build: r G + s
+    unsigned short L[LMAX][F];      // candidate lists, slot-major (conflict-free by floe)
+    int LC[F];                      // list lengths (other floes append during a build)
+    unsigned short SF[F];           // floes in bin order (build)
+    unsigned short BF[F];           // bin of each floe (build)
+    int BS[F + GCMAX + 1];          // bin counts, then starts
+    int BC[F + GCMAX + 1];          // bin cursors
+    float PS[NRED][F];              // reduction partials at segment heads
+    float2 Cm[GCMAX][MAXM];         // per cell and mode: corner phase (cos, sin), or (cycles, -)
+    float rg[2][GCMAX][4];          // gradual update per cell (g, du, dv, dw), by step parity
+    float cgrow[GCMAX];             // growth the cell's radii can still take this interval
+    float2 wind[WT];
+    int cc[GCMAX], cfs[GCMAX], cn[GCMAX], cnb[GCMAX], cbb[GCMAX], cgo[GCMAX];
+    int ncg, nfl, nbin, item;
+    float vsum;
+};
+
+__host__ __device__ constexpr size_t run_smem_bytes(int K)
+{
+    return K == 1 ? sizeof(RunSm<1>) : (K == 2 ? sizeof(RunSm<2>) : sizeof(RunSm<4>));
+}
+
+// Segmented warp sum towards the head of each segment: lanes [lane, end) of
+// this warp belong to the caller's segment; after the call the segment's
+// first lane holds its total.  A fixed tree: the same order on every run.
+__device__ __forceinline__ float seg_sum(float x, int lane, int end_lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float y = __shfl_down_sync(0xffffffffu, x, d);
+        if (lane + d < end_lane) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of BS[0..nb) in place (block-wide); BC gets a copy of the
+// starts.  Ends with a barrier.
+template <int K>
+__device__ void block_scan_bins(RunSm<K> &S, int nb)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int NW = RT / 32;
+    __shared__ int wsum[NW];
+    const int per = (nb + RT - 1) / RT;
+    const int b0 = t * per, b1 = min(b0 + per, nb);
+    int s = 0;
+    for (int b = b0; b < b1; b++) s += S.BS[b];
+    int x = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int wbase = 0;
+    for (int k = 0; k < warp; k++) wbase += wsum[k];
+    int run = wbase + x - s;
+    for (int b = b0; b < b1; b++) {
+        const int c = S.BS[b];
+        S.BS[b] = run;
+        S.BC[b] = run;
+        run += c;
+    }
+    __syncthreads();
+}
+
+// Ocean current and curl, and their gradients (per metre of global X, Y),
+// at the fraction (xf, yf) of cell ci: the modes' full sums in the FP32
+// phase-split form (corner phase Cm, turn across the cell).
+struct OceanExp {
+    float u, v, z, ux, uy, vx, vy, zx, zy;
+};
+
+template <int K>
+__device__ __forceinline__ OceanExp ocean_expand(const Phys<float> &P, const RunSm<K> &S, int ci, float xf, float yf,
+                                                 float inx, float iny)
+{
+    OceanExp o;
+    o.u = P.uo_x; o.v = P.uo_y; o.z = 0.0f;
+    o.ux = o.uy = o.vx = o.vy = o.zx = o.zy = 0.0f;
+    for (int m = 0; m < P.n_modes; m++) {
+        float cs, sn;
+        if (P.taylor) {
+            float c0, s0;
+            rot_small(fmaf(P.ta[m], xf, P.tb[m] * yf), c0, s0);
+            const float2 C = S.Cm[ci][m];
+            cs = C.x * c0 - C.y * s0;
+            sn = C.y * c0 + C.x * s0;
+        } else {
+            const float cyc = S.Cm[ci][m].x + turn_x(P, m, xf, inx) + turn_y(P, m, yf, iny);
+            sincospif(2.0f * cyc, &sn, &cs);
+        }
+        // mode m: u -= Au cos(th), v += Av cos(th), curl -= Az sin(th), th = kx X + ky Y + phi
+        const float kx = P.mKx[m], ky = P.mKy[m];
+        const float au = P.mAu[m], av = P.mAv[m], az = P.mAz[m];
+        o.u -= au * cs;
+        o.v += av * cs;
+        o.z -= az * sn;
+        const float aus = au * sn, avs = av * sn, azc = az * cs;
+        o.ux += aus * kx;
+        o.uy += aus * ky;
+        o.vx -= avs * kx;
+        o.vy -= avs * ky;
+        o.zx -= azc * kx;
+        o.zy -= azc * ky;
+    }
+    return o;
+}
+
+template <int K>
+__global__ void __launch_bounds__(RT, K == 1 ? 3 : (K == 2 ? 2 : 1))
+k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, const int4 *groups, int ngroups,
+                   const int4 *items, int qslot, int nsteps)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RunSm<K> &S = *reinterpret_cast<RunSm<K> *>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31;
+    const unsigned FULL = 0xffffffffu;
+    const float dt = sc.k.dt;
+    const float sx = sc.k.sx, sy = sc.k.sy, isx = sc.k.isx, isy = sc.k.isy;
+    const float Lcmin = fminf(sc.k.Lx, sc.k.Ly);
+    const int nc = sc.ncell;
+    const long long base = sc.ctrl->base;
+    const int j0 = (int)sc.i_local;                     // steps of the interval done before this run
+    const bool have_tgt = sc.couple && sc.ctrl->have_tgt;
+    const bool win_on = sc.couple != 0;
+    const bool ends_interval = sc.couple && (j0 + nsteps == sc.N0);
+    const bool carry_in = win_on && j0 > 0;             // the run continues a previous one inside its interval
+    const bool carry_out = win_on && !ends_interval;
+    const float dtsx = dt * isx, dtsy = dt * isy;
+    const long long ncar = sc.ncarry;
+    const int nev = sc.N0 / sc.n_t;                     // gradual updates per interval
+
+    // wind of steps [js0, js0 + WT) of the run (FP64 turn, once per block
+    // for runs of up to WT steps)
+    auto wind_table = [&](int js0) {
+        if (t < WT && js0 + t < nsteps) {
+            float ua, va;
+            wind_at(P, (double)(base + j0 + js0 + t) * sc.dt, ua, va);
+            S.wind[t] = make_float2(ua, va);
+        }
+    };
+    wind_table(0);
+
+    for (;;) {
+        // ---- next group from the queue
+        __syncthreads();
+        if (t == 0) {
+            int g = (int)atomicAdd(&sc.ctrl->gq[qslot][0], 1u);
+            if (g >= ngroups) {
+                __threadfence();
+                const unsigned done = atomicAdd(&sc.ctrl->gq[qslot][1], 1u);
+                if (done == gridDim.x - 1) {     // the last block out resets the queue for the next launch
+                    sc.ctrl->gq[qslot][0] = 0u;
+                    sc.ctrl->gq[qslot][1] = 0u;
+                    __threadfence();
+                }
+            }
+            S.item = g;
+        }
+        __syncthreads();
+        const int gid = S.item;
+        if (gid >= ngroups) return;
+
+        // ---- the group's cells
+        const int4 gd = groups[gid];          // first slot, cells, floes, bins (with one large slot per cell)
+        if (t < gd.y) {
+            const int4 id = items[gd.x + t];  // cell, first floe in the group, bins per side, bin base
+            const int c = id.x;
+            S.cc[t] = c;
+            S.cfs[t] = id.y;
+            S.cn[t] = sc.off[c + 1] - sc.off[c];
+            S.cnb[t] = id.z;
+            S.cbb[t] = id.w;
+            S.cgo[t] = sc.off[c];
+        }
+        if (t == 0) {
+            S.ncg = gd.y;
+            S.nfl = gd.z;
+            S.nbin = gd.w;
+        }
+        __syncthreads();
+        const int ncg = S.ncg, nfl = S.nfl;
+        for (int idx = t; idx < ncg * P.n_modes; idx += RT) {
+            const int ci = idx / P.n_modes, m = idx - ci * P.n_modes;
+            const int c = S.cc[ci];
+            const float b = corner_phase(P, m, c % sc.g.nx, (c / sc.g.nx) % sc.g.nyr, sc.g.nx, sc.g.nyr, sc.k.inx,
+                                         sc.k.iny);
+            if (P.taylor) {
+                float sn, cs;
+                sincospif(2.0f * b, &sn, &cs);
+                S.Cm[ci][m] = make_float2(cs, sn);
+            } else {
+                S.Cm[ci][m] = make_float2(b, 0.0f);
+            }
+        }
+        // gradual update of the run's first step, if it is one
+        if (t < ncg) {
+            const int kk = j0 + 1;
+            float g = 1.0f, du = 0.0f, dv = 0.0f, dw = 0.0f;
+            if (have_tgt && kk % sc.n_t == 0) {
+                const RampCell rc = ramp_cell(sc, S.cc[t], kk / sc.n_t);
+                g = (float)rc.g; du = (float)rc.du; dv = (float)rc.dv; dw = (float)rc.dw;
+            }
+            S.rg[0][t][0] = g; S.rg[0][t][1] = du; S.rg[0][t][2] = dv; S.rg[0][t][3] = dw;
+        }
+
+        // ---- this thread's floes: p = t + k RT in group order
+        int ci[K], lc[K];
+        uint32_t xq[K], yq[K], xb[K], yb[K], x0[K], y0[K];
+        float th[K], u[K], v[K], w[K], r[K], h[K], dtm[K], dtI[K], sk2[K];
+        float su[K], sv[K], sfx[K], sfy[K], stz[K];
+        OceanExp oc[K];
+        unsigned deep = 0;
+        bool bad = false;
+        auto derived = [&](int k) {
+            const float mass = P.mass_c * r[k] * r[k] * h[k];
+            const float I = P.inertia_f * mass * r[k] * r[k];
+            dtm[k] = dt / mass;
+            dtI[k] = dt / I;
+        };
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int p = t + k * RT;
+            ci[k] = 0;
+            lc[k] = 0;
+            xq[k] = yq[k] = xb[k] = yb[k] = 0u;
+            th[k] = u[k] = v[k] = w[k] = 0.0f;
+            r[k] = 1.0f;
+            h[k] = 1.0f;
+            sk2[k] = 0.0f;
+            su[k] = sv[k] = sfx[k] = sfy[k] = stz[k] = 0.0f;
+            if (p < nfl) {
+                int c2 = 0;
+                while (c2 + 1 < ncg && S.cfs[c2 + 1] <= p) c2++;
+                ci[k] = c2;
+                const int gi = S.cgo[c2] + (p - S.cfs[c2]);
+                xq[k] = in.xq[gi]; yq[k] = in.yq[gi]; th[k] = in.th[gi];
+                u[k] = in.u[gi]; v[k] = in.v[gi]; w[k] = in.w[gi]; r[k] = in.r[gi]; h[k] = in.h[gi];
+                S.Q[0][p] = make_uint2(xq[k], yq[k]);
+                S.A[0][p] = make_float4(u[k], v[k], w[k], r[k]);
+                S.H[p] = h[k];
+            }
+            x0[k] = xq[k];
+            y0[k] = yq[k];
+            if (carry_in && p < nfl) {
+                const int gi = S.cgo[ci[k]] + (p - S.cfs[ci[k]]);
+                su[k] = sc.carry_in[gi];
+                sv[k] = sc.carry_in[ncar + gi];
+                sfx[k] = sc.carry_in[2 * ncar + gi];
+                sfy[k] = sc.carry_in[3 * ncar + gi];
+                stz[k] = sc.carry_in[4 * ncar + gi];
+                x0[k] = __float_as_uint(sc.carry_in[5 * ncar + gi]);
+                y0[k] = __float_as_uint(sc.carry_in[6 * ncar + gi]);
+            }
+            derived(k);
+        }
+        __syncthreads();   // cell phases (Cm) before the first expansion
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            oc[k] = ocean_expand(P, S, ci[k], (float)x0[k] * INV2_32F, (float)y0[k] * INV2_32F, sc.k.inx, sc.k.iny);
+
+        // ---- reduction of NV (<= NRED) per-floe values per cell: segment
+        // sums over the floes of each warp, then the cell's partials in
+        // order; thread ci < ncg gets its cell's totals in outv.  All
+        // threads call it.
+        auto reduce_cells = [&](auto nv, auto &&value, double *outv) {
+            constexpr int NV = decltype(nv)::value;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                const bool valid = p < nfl;
+                const int fs = valid ? S.cfs[ci[k]] : nfl;
+                const int fe = valid ? S.cfs[ci[k]] + S.cn[ci[k]] : RT * K;
+                const int wb = p & ~31;
+                const int end_lane = min(fe, wb + 32) - wb;
+                const int head = max(fs, wb);
+#pragma unroll
+                for (int q = 0; q < NV; q++) {
+                    float x = valid ? value(k, q) : 0.0f;
+                    x = seg_sum(x, lane, end_lane);
+                    if (p == head) S.PS[q][p] = x;
+                }
+            }
+            __syncthreads();
+            if (t < ncg) {
+                const int fs = S.cfs[t], fe = S.cfs[t] + S.cn[t];
+                for (int q = 0; q < NV; q++) {
+                    double acc = 0.0;
+                    for (int hd = fs; hd < fe; hd = (hd | 31) + 1) acc += (double)S.PS[q][hd];
+                    outv[q] = acc;
+                }
+            }
+            __syncthreads();
+        };
+        // window: the group of steps since the last flush (Algorithm 1 sums)
+        auto flush = [&]() {
+            double tot[6];
+            auto val = [&](int k, int q) -> float {
+                const float mass = P.mass_c * r[k] * r[k] * h[k];
+                switch (q) {
+                case 0: return mass;
+                case 1: return mass * su[k];
+                case 2: return mass * sv[k];
+                case 3: return sfx[k];
+                case 4: return sfy[k];
+                default: return stz[k];
+                }
+            };
+            reduce_cells(std::integral_constant<int, 6>{}, val, tot);
+            if (t < ncg) {
+                const int c = S.cc[t];
+                if (tot[0] > 0.0) {
+                    sc.win[c] += tot[1] / tot[0];
+                    sc.win[nc + c] += tot[2] / tot[0];
+                }
+                sc.win[2 * nc + c] += tot[3];
+                sc.win[3 * nc + c] += tot[4];
+                sc.win[4 * nc + c] += tot[5];
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                bad |= !(isfinite(su[k]) && isfinite(sv[k]) && isfinite(stz[k]));
+                su[k] = sv[k] = sfx[k] = sfy[k] = stz[k] = 0.0f;
+            }
+        };
+
+        // ---- candidate lists from the positions in buffer b, before step kk
+        auto build = [&](int b, int kk) {
+            // the floor of the skins: a quarter of the group's mean speed
+            float vs = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                if (t + k * RT < nfl) vs += sqrtf(u[k] * u[k] + v[k] * v[k]);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) vs += __shfl_xor_sync(FULL, vs, d);
+            if (t == 0) S.vsum = 0.0f;
+            for (int i = t; i <= S.nbin; i += RT) S.BS[i] = 0;
+            // growth the cell's radii can still take in this interval: the
+            // gradual updates bring r to r0 s at its last one, from r0 (1 +
+            // (s - 1) ev n_t/N0) after update ev
+            if (t < ncg) {
+                float gr = 1.0f;
+                if (have_tgt) {
+                    const double s = sc.tgt[S.cc[t]];
+                    const int ev = (kk - 1) / sc.n_t;       // updates already applied
+                    const double now = 1.0 + (s - 1.0) * ev / (double)nev;
+                    const double g = s / now;
+                    gr = g > 1.0 ? (float)(g * (1.0 + 1e-6)) : 1.0f;
+                }
+                S.cgrow[t] = gr;
+            }
+            __syncthreads();
+            if (lane == 0) atomicAdd(&S.vsum, vs);
+            __syncthreads();
+            const float vfloor = 0.25f * S.vsum / (float)max(nfl, 1);
+            const float horizon = SKIN_STEPS * dt;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                if (p < nfl) {
+                    const int c2 = ci[k], nb = S.cnb[c2];
+                    const float sp = sqrtf(u[k] * u[k] + v[k] * v[k]);
+                    const float skin = (1.5f * sp + vfloor) * horizon + 1.0e-3f * r[k];
+                    sk2[k] = skin * skin;
+                    const float reach = r[k] * S.cgrow[c2] + skin;
+                    S.RE[p] = reach;
+                    const bool small = nb >= 3 && reach <= 0.5f * (Lcmin / (float)nb);
+                    const int bn = S.cbb[c2] + (small ? (int)(__umulhi(yq[k], (unsigned)nb) * nb +
+                                                               __umulhi(xq[k], (unsigned)nb))
+                                                      : nb * nb);
+                    S.BF[p] = (unsigned short)bn;
+                    atomicAdd(&S.BS[bn], 1);
+                    S.LC[p] = 0;
+                }
+            }
+            __syncthreads();
+            block_scan_bins(S, S.nbin + 1);   // BS[nbin] = the group's floes
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                if (p < nfl) S.SF[atomicAdd(&S.BC[S.BF[p]], 1)] = (unsigned short)p;
+            }
+            __syncthreads();
+            // search
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                if (p >= nfl) continue;
+                const int c2 = ci[k], nb = S.cnb[c2], bb = S.cbb[c2];
+                const uint2 ql = make_uint2(xq[k], yq[k]);
+                const float rl = S.RE[p];
+                auto hit = [&](int q) {
+                    const uint2 qq = S.Q[b][q];
+                    const float dx = (float)(int)(qq.x - ql.x) * sx, dy = (float)(int)(qq.y - ql.y) * sy;
+                    const float Ssum = rl + S.RE[q];
+                    return fmaf(Ssum, Ssum, -(dx * dx + dy * dy)) > 0.0f;
+                };
+                auto add = [&](int a, int q) {
+                    const int slot = atomicAdd(&S.LC[a], 1);
+                    if (slot < LMAX) S.L[slot][a] = (unsigned short)q;
+                };
+                const int lg0 = S.BS[bb + nb * nb], lg1 = S.BS[bb + nb * nb + 1];   // the cell's large floes
+                const bool small = (int)S.BF[p] != bb + nb * nb;
+                if (small) {
+                    const int bx = (int)__umulhi(ql.x, (unsigned)nb), by = (int)__umulhi(ql.y, (unsigned)nb);
+                    for (int dyb = -1; dyb <= 1; dyb++) {
+                        int wy = by + dyb;
+                        wy = wy < 0 ? wy + nb : (wy >= nb ? wy - nb : wy);
+                        const int row = bb + wy * nb;
+                        for (int dxb = -1; dxb <= 1; dxb++) {
+                            int wx = bx + dxb;
+                            wx = wx < 0 ? wx + nb : (wx >= nb ? wx - nb : wx);
+                            const int e1 = S.BS[row + wx + 1];
+                            for (int i = S.BS[row + wx]; i < e1; i++) {
+                                const int q = S.SF[i];
+                                if (q != p && hit(q)) add(p, q);
+                            }
+                        }
+                    }
+                    for (int i = lg0; i < lg1; i++) {     // small-large pairs: both sides recorded here
+                        const int q = S.SF[i];
+                        if (hit(q)) {
+                            add(p, q);
+                            add(q, p);
+                        }
+                    }
+                } else {
+                    for (int i = lg0; i < lg1; i++) {     // large-large pairs: each side its own
+                        const int q = S.SF[i];
+                        if (q != p && hit(q)) add(p, q);
+                    }
+                }
+            }
+            __syncthreads();
+            // each list in ascending floe order; the build positions
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                if (p >= nfl) continue;
+                const int n = S.LC[p];
+                lc[k] = n;
+                if (n <= LMAX) {
+                    for (int i = 1; i < n; i++) {
+                        const unsigned short key = S.L[i][p];
+                        int j = i - 1;
+                        while (j >= 0 && S.L[j][p] > key) {
+                            S.L[j + 1][p] = S.L[j][p];
+                            j--;
+                        }
+                        S.L[j + 1][p] = key;
+                    }
+                }
+                xb[k] = xq[k];
+                yb[k] = yq[k];
+            }
+        };
+
+        if (nsteps > WT) wind_table(0);   // a previous group left a later table
+        __syncthreads();
+        int cur = 0;
+        bool need_build = true;
+        for (int js = 0; js < nsteps; js++) {
+            const int kk = j0 + js + 1;                   // step within the interval, 1-based
+            if (js > 0 && js % WT == 0) {
+                __syncthreads();
+                wind_table(js);
+                __syncthreads();
+            }
+            if (win_on && kk % sc.n_t == 0) flush();      // the steps of the previous masses
+            if (need_build) build(cur, kk);
+            __syncthreads();
+            const float2 wa = S.wind[js % WT];
+            const bool ramp = have_tgt && (kk % sc.n_t == 0);
+            const int rb = js & 1;
+            // next step's gradual update, published by the step barrier below
+            if (t < ncg && js + 1 < nsteps) {
+                const int k2 = kk + 1;
+                float g = 1.0f, du = 0.0f, dv = 0.0f, dw = 0.0f;
+                if (have_tgt && k2 % sc.n_t == 0) {
+                    const RampCell rc = ramp_cell(sc, S.cc[t], k2 / sc.n_t);
+                    g = (float)rc.g; du = (float)rc.du; dv = (float)rc.dv; dw = (float)rc.dw;
+                }
+                S.rg[rb ^ 1][t][0] = g; S.rg[rb ^ 1][t][1] = du; S.rg[rb ^ 1][t][2] = dv; S.rg[rb ^ 1][t][3] = dw;
+            }
+            const bool last = js == nsteps - 1;
+            bool far = false;
+            float Fdl[K][3];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                Fdl[k][0] = Fdl[k][1] = Fdl[k][2] = 0.0f;
+                const int p = t + k * RT;
+                const bool valid = p < nfl;
+                // the ocean expansion still holds? (whole warp expands again if not)
+                const int ix = (int)(xq[k] - x0[k]), iy = (int)(yq[k] - y0[k]);
+                const float ddx = (float)ix * sx, ddy = (float)iy * sy;
+                const bool wrapped = (xq[k] < x0[k]) != (ix < 0) || (yq[k] < y0[k]) != (iy < 0);
+                const bool stale = valid && (wrapped || ddx * ddx + ddy * ddy > P.ocean_d2);
+                float ex = ddx, ey = ddy;
+                if (__any_sync(FULL, stale)) {
+                    x0[k] = xq[k];
+                    y0[k] = yq[k];
+                    oc[k] = ocean_expand(P, S, ci[k], (float)xq[k] * INV2_32F, (float)yq[k] * INV2_32F, sc.k.inx,
+                                         sc.k.iny);
+                    ex = ey = 0.0f;
+                }
+                if (!valid) continue;
+                // contacts, ascending partner order
+                float fx = 0.0f, fy = 0.0f, tq = 0.0f;
+                unsigned dflag = 0;
+                const uint2 ql = make_uint2(xq[k], yq[k]);
+                auto pair = [&](int q) {
+                    const uint2 qq = S.Q[cur][q];
+                    const float4 aq = S.A[cur][q];
+                    const float dx = (float)(int)(qq.x - ql.x) * sx;
+                    const float dy = (float)(int)(qq.y - ql.y) * sy;
+                    contact_add(dx, dy, dx * dx + dy * dy, r[k], aq.w, h[k], S.H[q], aq.x - u[k], aq.y - v[k], w[k],
+                                aq.z, P, fx, fy, tq, dflag);
+                };
+                const int n = lc[k];
+                if (n <= LMAX) {
+                    for (int i = 0; i < n; i++) pair(S.L[i][p]);
+                } else {
+                    const int c2 = ci[k];
+                    for (int q = S.cfs[c2]; q < S.cfs[c2] + S.cn[c2]; q++)
+                        if (q != p) pair(q);
+                }
+                deep += dflag;
+                // ocean and wind drag (Eq. 2.1c-d)
+                const OceanExp &o = oc[k];
+                const float uo = fmaf(o.ux, ex, fmaf(o.uy, ey, o.u));
+                const float vo = fmaf(o.vx, ex, fmaf(o.vy, ey, o.v));
+                const float zeta = fmaf(o.zx, ex, fmaf(o.zy, ey, o.z));
+                const float r2 = r[k] * r[k];
+                const float ao = P.drag_o * r2, aa = P.drag_a * r2, bo = ao * r2;
+                const float du_o = uo - u[k], dv_o = vo - v[k];
+                const float so = sqrtf(du_o * du_o + dv_o * dv_o);
+                const float au = wa.x - u[k], av = wa.y - v[k];
+                const float sa = sqrtf(au * au + av * av);
+                const float dwo = 0.5f * zeta - w[k];
+                const float Fdx = ao * du_o * so + aa * au * sa;
+                const float Fdy = ao * dv_o * so + aa * av * sa;
+                const float Td = bo * dwo * fabsf(dwo);
+                fx += Fdx; fy += Fdy; tq += Td;
+                // forward Euler (Sec. 3.1), periodic wrap by fixed-point overflow
+                xq[k] += (uint32_t)__float2int_rn(dtsx * u[k]);
+                yq[k] += (uint32_t)__float2int_rn(dtsy * v[k]);
+                th[k] += dt * w[k];
+                u[k] += dtm[k] * fx;
+                v[k] += dtm[k] * fy;
+                w[k] += dtI[k] * tq;
+                if (ramp) {                   // gradual update (Eqs. 3.5-3.7)
+                    const float *g4 = S.rg[rb][ci[k]];
+                    r[k] *= g4[0];
+                    u[k] += g4[1];
+                    v[k] += g4[2];
+                    w[k] += g4[3];
+                    derived(k);
+                }
+                su[k] += u[k];
+                sv[k] += v[k];
+                sfx[k] += Fdx;
+                sfy[k] += Fdy;
+                stz[k] += Td;
+                Fdl[k][0] = Fdx; Fdl[k][1] = Fdy; Fdl[k][2] = Td;
+                if (!last) {
+                    S.Q[cur ^ 1][p] = make_uint2(xq[k], yq[k]);
+                    S.A[cur ^ 1][p] = make_float4(u[k], v[k], w[k], r[k]);
+                }
+                const float bx = (float)(int)(xq[k] - xb[k]) * sx, by = (float)(int)(yq[k] - yb[k]) * sy;
+                far |= bx * bx + by * by > sk2[k];
+            }
+            need_build = __syncthreads_or(far) != 0;
+            cur ^= 1;
+            if (last) {
+                // the cell moments of the run's last step (all columns)
+                double tot[NMOM];
+                auto val1 = [&](int k, int q) -> float {
+                    const float m = P.mass_c * r[k] * r[k] * h[k];
+                    const float I = P.inertia_f * m * r[k] * r[k];
+                    switch (q) {
+                    case 0: return m;
+                    case 1: return m * u[k];
+                    case 2: return m * v[k];
+                    case 3: return I;
+                    case 4: return I * w[k];
+                    default: return 3.14159265358979323846f * r[k] * r[k];
+                    }
+                };
+                auto val2 = [&](int k, int q) -> float {
+                    const float m = P.mass_c * r[k] * r[k] * h[k];
+                    switch (q) {
+                    case 0: return m * u[k] * u[k];
+                    case 1: return m * v[k] * v[k];
+                    case 2: return Fdl[k][0];
+                    case 3: return Fdl[k][1];
+                    default: return Fdl[k][2];
+                    }
+                };
+                reduce_cells(std::integral_constant<int, 6>{}, val1, tot);
+                reduce_cells(std::integral_constant<int, 5>{}, val2, tot + 6);
+                if (t < ncg) {
+                    double *mo = sc.mom + (size_t)S.cc[t] * NMOM;
+                    mo[0] = (double)S.cn[t];
+                    for (int q = 1; q < NMOM; q++) mo[q] = tot[q - 1];
+                }
+            }
+        }
+        if (ends_interval) flush();
+        // ---- back to global memory
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int p = t + k * RT;
+            if (p >= nfl) continue;
+            bad |= !(isfinite(u[k]) && isfinite(v[k]) && isfinite(w[k]));
+            const int gi = S.cgo[ci[k]] + (p - S.cfs[ci[k]]);
+            out.xq[gi] = xq[k]; out.yq[gi] = yq[k]; out.th[gi] = th[k];
+            out.u[gi] = u[k]; out.v[gi] = v[k]; out.w[gi] = w[k]; out.r[gi] = r[k];
+            if (out.h != in.h) out.h[gi] = h[k];
+            if (carry_out) {
+                sc.carry_out[gi] = su[k];
+                sc.carry_out[ncar + gi] = sv[k];
+                sc.carry_out[2 * ncar + gi] = sfx[k];
+                sc.carry_out[3 * ncar + gi] = sfy[k];
+                sc.carry_out[4 * ncar + gi] = stz[k];
+                sc.carry_out[5 * ncar + gi] = __uint_as_float(x0[k]);
+                sc.carry_out[6 * ncar + gi] = __uint_as_float(y0[k]);
+            }
+        }
+        // an empty cell of the group: zero moments
+        if (t < ncg && S.cn[t] == 0) {
+            double *mo = sc.mom + (size_t)S.cc[t] * NMOM;
+            for (int q = 0; q < NMOM; q++) mo[q] = 0.0;
+        }
+        if (__syncthreads_or(bad) && t == 0) atomicOr(&sc.ctrl->err, ERR_NONFINITE);
+        bad = false;
+        if (deep) atomicAdd(&sc.ctrl->deep, (unsigned long long)deep);
+        deep = 0;
+    }
+}
+
+// Fold the floes' running window sums into the window: a block per cell,
+// the masses of the current state, fixed-order sums; the sums are cleared
+// (the expansion centres are kept: they stay valid wherever the floes are).
+__global__ void __launch_bounds__(128) k_carry_flush(DevState32 s, StepCommon sc, float *carry, long long ncarry)
+{
+    __shared__ double red[6][128];
+    const int c = blockIdx.x, t = threadIdx.x;
+    const int o = sc.off[c], n = sc.off[c + 1] - o;
+    double a[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = t; i < n; i += 128) {
+        const long long gi = o + i;
+        const float r = s.r[gi], h = s.h[gi];
+        const double m = (double)r * (double)r * (double)h;   // rho_ice pi cancels in the mean
+        a[0] += m;
+        a[1] += m * carry[gi];
+        a[2] += m * carry[ncarry + gi];
+        a[3] += carry[2 * ncarry + gi];
+        a[4] += carry[3 * ncarry + gi];
+        a[5] += carry[4 * ncarry + gi];
+        for (int q = 0; q < 5; q++) carry[q * ncarry + gi] = 0.0f;
+    }
+    for (int q = 0; q < 6; q++) red[q][t] = a[q];
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (t < w)
+            for (int q = 0; q < 6; q++) red[q][t] += red[q][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        const int nc = sc.ncell;
+        if (red[0][0] > 0.0) {
+            sc.win[c] += red[1][0] / red[0][0];
+            sc.win[nc + c] += red[2][0] / red[0][0];
+        }
+        sc.win[2 * nc + c] += red[3][0];
+        sc.win[3 * nc + c] += red[4][0];
+        sc.win[4 * nc + c] += red[5][0];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_carry_flush(const DevState32 &s, const StepCommon &sc, float *carry, long long ncarry,
+                               cudaStream_t st)
+{
+    if (sc.ncell <= 0 || !carry) return cudaSuccess;
+    k_carry_flush<<<sc.ncell, 128, 0, st>>>(s, sc, carry, ncarry);
+    return cudaGetLastError();
+}
+
+size_t run_block_smem(int K) { return run_smem_bytes(K); }
+
+cudaError_t run_block_prepare()
+{
+    const void *kern[3] = {(const void *)k_cell_run32_block<1>, (const void *)k_cell_run32_block<2>,
+                           (const void *)k_cell_run32_block<4>};
+    const size_t sm[3] = {run_smem_bytes(1), run_smem_bytes(2), run_smem_bytes(4)};
+    for (int i = 0; i < 3; i++) {
+        cudaError_t e = cudaFuncSetAttribute(kern[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Persistent grid of one class: as many blocks as fit on the device at once
+// (at most one per group).
+static int run_block_grid(int K, int ngroups)
+{
+    static int blocks_per_sm[3] = {0, 0, 0}, nsm = 0;
+    const int ki = K == 1 ? 0 : (K == 2 ? 1 : 2);
+    if (!blocks_per_sm[ki]) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        int b = 0;
+        if (K == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cell_run32_block<1>, RT, run_smem_bytes(1));
+        else if (K == 2)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cell_run32_block<2>, RT, run_smem_bytes(2));
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cell_run32_block<4>, RT, run_smem_bytes(4));
+        blocks_per_sm[ki] = b > 0 ? b : 1;
+    }
+    const int g = blocks_per_sm[ki] * (nsm > 0 ? nsm : 1);
+    return g < ngroups ? g : ngroups;
+}
+
+cudaError_t launch_run_block(int K, const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                             const StepCommon &sc, const int4 *groups, int ngroups, const int4 *items, int qslot,
+                             int nsteps, cudaStream_t st)
+{
+    if (ngroups <= 0 || nsteps <= 0) return cudaSuccess;
+    const int grid = run_block_grid(K, ngroups);
+    if (K == 1)
+        k_cell_run32_block<1><<<grid, RT, run_smem_bytes(1), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
+                                                                    nsteps);
+    else if (K == 2)
+        k_cell_run32_block<2><<<grid, RT, run_smem_bytes(2), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
+                                                                    nsteps);
+    else
+        k_cell_run32_block<4><<<grid, RT, run_smem_bytes(4), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
+                                                                    nsteps);
+    return cudaGetLastError();
+}
+
+}  // namespace msd

@@ -18,7 +18,6 @@ namespace msd {
 
 namespace {
 
-constexpr float TWO32F = 4294967296.0f;
 
 // A large floe's search reach, capped at the cell side of its axis; NaN (a
 // diverged state) takes the whole side.  Positions lie in [0, L), so the bin
@@ -26,7 +25,6 @@ constexpr float TWO32F = 4294967296.0f;
 // integer width of the range cannot overflow, and a range narrower than the
 // cell wraps into the bin table at most once on either side.
 __device__ __forceinline__ float reach_cap(float reach, float L) { return reach < L ? reach : L; }
-constexpr float INV2_32F = 2.3283064365386963e-10f;
 
 __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -50,25 +48,6 @@ __device__ __forceinline__ StepInfo step_info(const StepCommon &sc)
     return si;
 }
 
-// Gradual update of one cell (Sec. 3.3, Eqs. 3.5-3.7).  reading: each update
-// adds n_t/N0 of (target - snapshot at the coarse step); radii follow
-// r = r0 (1 + (s - 1) ev n_t/N0), applied as the per-step ratio g.
-struct RampCell {
-    double g, du, dv, dw;
-};
-
-__device__ __forceinline__ RampCell ramp_cell(const StepCommon &sc, int c, int ev)
-{
-    const int nc = sc.ncell;
-    const double f = (double)sc.n_t / (double)sc.N0;
-    const double s = sc.tgt[c];
-    RampCell rc;
-    rc.g = (1.0 + (s - 1.0) * ev * f) / (1.0 + (s - 1.0) * (ev - 1) * f);
-    rc.du = sc.tgt[nc + c] * f;
-    rc.dv = sc.tgt[2 * nc + c] * f;
-    rc.dw = sc.tgt[3 * nc + c] * f;
-    return rc;
-}
 
 // Per-block copy of the step facts and the current cell's update, set by
 // thread 0 (its FP64 arithmetic runs once per block, not once per thread).
@@ -826,13 +805,6 @@ __device__ __forceinline__ WarpSm carve_warp(unsigned char *p, int cap, int nbma
     return w;
 }
 
-// e^{i th} for |th| <= 0.4 by its Taylor series to th^9 (error < 1e-10)
-__device__ __forceinline__ void rot_small(float th, float &c, float &s)
-{
-    const float t = th * th;
-    c = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
-    s = th * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
-}
 
 // exclusive scan of in[0..count) into out by one warp; returns the total
 __device__ __forceinline__ int warp_scan_excl(const int *in, int *out, int count, int lane)
@@ -2285,6 +2257,7 @@ int seg_nbmax(const CellLaunch &cl, int s)
 
 static size_t seg_smem(const CellLaunch &cl, int s)
 {
+    if (cl.seg_kind[s] == 3) return run_block_smem(cl.seg_maxn[s] / RUN_T);
     if (cl.seg_kind[s] == 2) return 4 * pack_region_bytes();
     if (cl.seg_kind[s] == 1 && cl.variant == 3) return 4 * run_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
     if (cl.seg_kind[s] == 1 && cl.variant == 4) return 4 * list_region_bytes(cl.seg_maxn[s], seg_nbmax(cl, s));
@@ -2302,6 +2275,11 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
     if (items <= 0) return cudaSuccess;
     const int nbm = seg_nbmax(cl, s);
     const size_t sm = seg_smem(cl, s);
+    if (cl.seg_kind[s] == 3) {   // resident blocks (variant 5): one launch for the whole run
+        const int K = cl.seg_maxn[s] / RUN_T;
+        return launch_run_block(K, in, out, P, sc0, cl.rgroups[s], cl.rngroups[s], cl.ritems,
+                                K == 1 ? 0 : (K == 2 ? 1 : 2), nsteps, st);
+    }
     if (cl.seg_kind[s] == 2) {   // resident in registers: one launch for the whole run
         if (cl.npack <= 0) return cudaSuccess;
         k_cell_run32_packed<4><<<(cl.npack + 3) / 4, 128, sm, st>>>(in, out, P, sc0, cl.pack, cl.npack, nsteps);
@@ -2332,7 +2310,7 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
                                                                 cl.seg_end[s], cl.seg_maxn[s], nbm, s);
         return cudaGetLastError();
     }
-    if (cl.variant == 4) {
+    if (cl.variant >= 4) {
         MS_T_SWITCH(cl.seg_threads[s],
                     k_cell_step32_binned<TT, true><<<items, TT, sm, st>>>(in, out, P, sc, cl.bin_beta, cl.seg_begin[s],
                                                                           cl.seg_end[s], cl.seg_maxn[s], nbm, s));
@@ -2383,6 +2361,7 @@ cudaError_t cell_step_prepare(int, const CellLaunch &, size_t smem)
             (const void *)k_cell_step32_wlist<4>, (const void *)k_cell_step32_binned<64, true>,
             (const void *)k_cell_step32_binned<128, true>, (const void *)k_cell_step32_binned<256, true>};
         limit = optin;
+        if ((e = run_block_prepare()) != cudaSuccess) return e;
         for (const void *k : kern) {
             cudaFuncAttributes fa;
             e = cudaFuncGetAttributes(&fa, k);

@@ -29,6 +29,13 @@ constexpr SizeClass kClassesV4[9] = {{1 << 30, 128, 0}, {640, 128, 1}, {512, 128
                                      {256, 128, 1},     {192, 128, 1}, {128, 128, 1}, {64, 128, 1},
                                      {32, 128, 2}};
 
+// Variant 5 keeps every cell of up to 1024 floes resident for a run of
+// steps: cells of 513-1024 floes take a block with 4 floes per thread, of
+// 257-512 floes 2 per thread, smaller cells share blocks a floe per thread
+// (kind 3, the class bound / 256 floes per thread); larger cells run the
+// block-per-cell list kernel step by step.
+constexpr SizeClass kClassesV5[4] = {{1 << 30, 128, 0}, {1024, 256, 3}, {512, 256, 3}, {256, 256, 3}};
+
 // The streams of the first kHighPriorityClasses size classes (the largest
 // cells: few blocks, each holding much shared memory, and the longest
 // launches) get the highest stream priority, so their blocks take SMs first
@@ -36,7 +43,8 @@ constexpr SizeClass kClassesV4[9] = {{1 << 30, 128, 0}, {640, 128, 1}, {512, 128
 // workload: 2-6 % less per interval than equal priorities or than priority
 // for fewer classes; graded priorities were slower).
 constexpr int kHighPriorityClasses = 4;
-static_assert(sizeof(kClassesV2) / sizeof(SizeClass) <= MAXSEG && sizeof(kClassesV4) / sizeof(SizeClass) <= MAXSEG,
+static_assert(sizeof(kClassesV2) / sizeof(SizeClass) <= MAXSEG && sizeof(kClassesV4) / sizeof(SizeClass) <= MAXSEG &&
+                  sizeof(kClassesV5) / sizeof(SizeClass) <= MAXSEG,
               "more size classes than stream slots");
 
 }  // namespace msd

@@ -32,7 +32,8 @@ struct Ctrl {
     unsigned int queue[2];        // work-queue tickets, one per step parity
     unsigned long long deep;      // contacts with overlap deeper than r_min / 2 (diagnostic)
     long long lag_mark;           // base + 1 at whose start the stored last-interval tendencies are valid
-    unsigned long long pad[2];
+    unsigned int gq[3][2];        // group queues of the resident block kernels (ticket, blocks done), by class
+    unsigned int pad[2];
 };
 
 // Physical constants in the kernel's arithmetic type.
@@ -61,6 +62,8 @@ struct Phys {
     R kcx[MAXM], kcy[MAXM];                        // FP32, real modes: the same in FP32 (turn across a cell)
     R kdx[MAXM], kdy[MAXM];                        // FP32: cycles per domain (the truth DEM's phase)
     int taylor;                                    // FP32: 1 if every mode turns by <= 1/16 cycle across a cell
+    R ocean_d2;                                    // FP32 (variant 5): squared distance (m^2) a floe may move from
+                                                   // the centre of its local ocean expansion (see cell_run.cu)
     R ta[MAXM], tb[MAXM];                          // FP32: kx Lcx, ky Lcy (radians per cell)
     R drag_o;      // Cd rho_o pi
     R drag_a;      // Ca rho_a pi
@@ -254,10 +257,17 @@ struct CellLaunch {
     int nseg;
     int seg_begin[MAXSEG], seg_end[MAXSEG], seg_maxn[MAXSEG], seg_threads[MAXSEG];
     int seg_kind[MAXSEG];   // 0: block per cell, 1: warp per cell (seg_maxn = the warp's capacity),
-                            // 2: cells of <= 32 floes packed several to a warp
+                            // 2: cells of <= 32 floes packed several to a warp, 3: resident
+                            // blocks, seg_maxn / 256 floes per thread (variant 5)
     const int2 *pack;  // kind 2: per warp (first item, cells), device
     int npack;
     int nbmax;         // bins per side at most
+    // variant 5, kind 3 segments (resident block classes): per segment the
+    // groups of cells one block takes (device) and their number; per group
+    // slot the cell and its place in the group (device)
+    const int4 *rgroups[MAXSEG];
+    int rngroups[MAXSEG];
+    const int4 *ritems;
     // segments of variant 2 run on their own streams, forked from and joined
     // back into the launching stream (concurrent branches in a graph)
     cudaStream_t side[MAXSEG];
@@ -312,7 +322,67 @@ struct StepCommon {
     double dt;
     int N0, n_t, couple;
     long long i_local;  // step within the current coarse interval (0-based)
+    // variant 5: what a run hands to the next, [RUN_NCARRY][ncarry]: the
+    // floes' running window sums (velocity u, v, drag Fx, Fy, torque since
+    // the last gradual update) and the fixed-point centre of each floe's
+    // ocean expansion; read at a run that starts inside an interval, written
+    // by one that ends inside one
+    const float *carry_in;
+    float *carry_out;
+    long long ncarry;
 };
+
+// 2^32 and 2^-32: fixed-point positions of the FP32 path (2^32 = cell side)
+constexpr float TWO32F = 4294967296.0f;
+constexpr float INV2_32F = 2.3283064365386963e-10f;
+
+// e^{i th} for |th| <= 0.4 by its Taylor series to th^9 (error < 1e-10)
+__device__ __forceinline__ void rot_small(float th, float &c, float &s)
+{
+    const float t = th * th;
+    c = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+    s = th * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+}
+
+// Gradual update of one cell (Sec. 3.3, Eqs. 3.5-3.7).  reading: each update
+// adds n_t/N0 of (target - snapshot at the coarse step); radii follow
+// r = r0 (1 + (s - 1) ev n_t/N0), applied as the per-step ratio g.
+struct RampCell {
+    double g, du, dv, dw;
+};
+
+__device__ __forceinline__ RampCell ramp_cell(const StepCommon &sc, int c, int ev)
+{
+    const int nc = sc.ncell;
+    const double f = (double)sc.n_t / (double)sc.N0;
+    const double s = sc.tgt[c];
+    RampCell rc;
+    rc.g = (1.0 + (s - 1.0) * ev * f) / (1.0 + (s - 1.0) * (ev - 1) * f);
+    rc.du = sc.tgt[nc + c] * f;
+    rc.dv = sc.tgt[2 * nc + c] * f;
+    rc.dw = sc.tgt[3 * nc + c] * f;
+    return rc;
+}
+
+constexpr int RUN_T = 256;      // threads per block of the resident block kernels (variant 5)
+constexpr int RUN_GCMAX = 32;   // cells per group of those kernels
+constexpr int RUN_NCARRY = 7;   // words per floe a run hands to the next: 5 window sums, ocean expansion centre
+
+// cell_run.cu: a run of nsteps fine steps of one block class (K floes per
+// thread) from step sc.i_local of the interval, every floe in registers
+// (launch variant 5).  groups[g] = (first slot, cells, floes, bins incl. one
+// large-floe slot per cell) in processing order; items[slot] = (cell, first
+// floe of the cell in its group, bins per side (0: none), bin base); the
+// carry is sc.carry_in / sc.carry_out; qslot = the class's queue in Ctrl.
+cudaError_t launch_run_block(int K, const DevState32 &in, const DevState32 &out, const Phys<float> &P,
+                             const StepCommon &sc, const int4 *groups, int ngroups, const int4 *items, int qslot,
+                             int nsteps, cudaStream_t st);
+size_t run_block_smem(int K);
+cudaError_t run_block_prepare();
+// fold the running window sums of a run that stopped inside a coarse interval
+// into the window (masses of the current state) and clear them
+cudaError_t launch_carry_flush(const DevState32 &s, const StepCommon &sc, float *carry, long long ncarry,
+                               cudaStream_t st);
 
 // cell_step.cu
 cudaError_t launch_cell_step32(const DevState32 &in, const DevState32 &out, const Phys<float> &P,

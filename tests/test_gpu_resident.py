@@ -1,0 +1,177 @@
+"""Launch variant 5: every cell of up to 1024 floes resident for a whole run
+of fine steps, a floe per thread (2 or 4 for cells above 256 floes),
+contacts from candidate lists summed in ascending partner order.
+
+Parity with the FP64 oracle within the FP32 tolerance on cells of every size
+class (including a cell above 1024 floes, which runs the per-step block
+kernel), contacts dense enough to overflow a list, and bitwise equality of a
+run however it is split into launches (graph intervals, single steps, odd
+runs), through coarse steps and gradual updates."""
+import numpy as np
+import pytest
+
+from paper_2303_07819_gb300 import inputs as I
+from tests.parity import rel_errors, report
+from tests.test_gpu_parity import TOL32, ragged_scenario
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    from paper_2303_07819_gb300 import msdem
+    msdem.load()
+    return msdem
+
+
+def _same(a, b):
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(a.moments(), b.moments())
+    ca, cb = a.coupling(), b.coupling()
+    for k in ("q", "targets", "window"):
+        assert np.array_equal(ca[k], cb[k]), k
+
+
+def test_every_class_matches_oracle(orc, ms):
+    """Cells of 0 to 1100 floes (empty cells, packed groups of small cells,
+    2 and 4 floes per thread, and a cell above 1024 floes on the per-step
+    block kernel), 250 steps: two coarse steps with their gradual updates;
+    moments and the coarse solution within the FP32 tolerance."""
+    s = ragged_scenario([0, 1, 3, 9, 17, 31, 33, 64, 100, 129, 200, 256, 257, 300, 511, 513, 700, 1024, 1100],
+                        L_c=25e3, seed=41)
+    p = s["params"]
+    o = orc.Model(p, s["floes"])
+    g = ms.Model(p, s["floes"], ms.MS_FP32)
+    g.set_launch(5, 128, 0, 1.3)
+    o.step(s["dt"], 250)
+    g.step(s["dt"], 250)
+    mo, mg = o.moments(), g.moments()
+    assert np.array_equal(mo[:, 0], mg[:, 0])
+    e = rel_errors(mg, mo, p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+    qo, qg = o.coupling()["q"], g.coupling()["q"]
+    for f in range(4):
+        assert np.linalg.norm(qg[f] - qo[f]) <= TOL32 * np.linalg.norm(qo[f]), f
+    assert g.info()["variant"] == 5
+
+
+def test_runs_split_anywhere_are_bitwise_equal(ms):
+    """An interval from the graph (one launch per class), the same steps one
+    launch each, and runs of odd lengths that end inside gradual-update
+    periods (the floes' running window sums carried between launches): the
+    same floes, moments, window and coarse solution bit for bit, across two
+    coarse steps."""
+    s = I.batched_128x128(seed=7, nx=16)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    models = [ms.Model(p, s["floes"], ms.MS_FP32) for _ in range(3)]
+    for m in models:
+        m.set_launch(5, 128, 0, 1.3)
+    a, b, c = models
+    total = 2 * N0 + 17
+    a.step(dt, total)
+    for _ in range(total):
+        b.step(dt, 1)
+    done = 0
+    for k in (37, 1, 62, 9, 3, 88, 17):
+        c.step(dt, k)
+        done += k
+    assert done == total
+    assert a.info()["graph_replays"] == 2 and b.info()["graph_replays"] == 0
+    _same(a, b)
+    _same(a, c)
+
+
+def test_contacts_and_list_overflow(orc, ms):
+    """A 3 km floe ringed by 60 floes of 150 m that touch it (its list of at
+    most 16 candidates overflows and it tests every floe of its cell), plus
+    loose floes: within the FP32 tolerance of the oracle over 60 steps, and
+    the same result as the neighbour-list kernel of variant 4."""
+    rng = np.random.default_rng(31)
+    L_c, nx = 25e3, 2
+    ang = 2 * np.pi * (np.arange(60) + 0.5) / 60
+    x = np.concatenate([[12.5e3], 12.5e3 + 3140.0 * np.cos(ang)])
+    y = np.concatenate([[12.5e3], 12.5e3 + 3140.0 * np.sin(ang)])
+    r = np.concatenate([[3000.0], np.full(60, 150.0)])
+    for cx, cy in ((1, 0), (0, 1), (1, 1)):
+        x = np.concatenate([x, cx * L_c + rng.uniform(2e3, 23e3, 5)])
+        y = np.concatenate([y, cy * L_c + rng.uniform(2e3, 23e3, 5)])
+        r = np.concatenate([r, np.full(5, 400.0)])
+    n = x.shape[0]
+    p = I._phys(dt=5.0)
+    p.update({"nx": nx, "ny": nx, "Lx": nx * L_c, "Ly": nx * L_c,
+              "modes": I.random_modes(rng, 4, nx * L_c, nx * L_c, 0.1)})
+    fl = I._floes(x, y, r, np.ones(n), u=rng.normal(0, 0.05, n), v=rng.normal(0, 0.05, n))
+    o = orc.Model(p, fl)
+    g = ms.Model(p, fl, ms.MS_FP32)
+    d = ms.Model(p, fl, ms.MS_FP32)
+    g.set_launch(5, 128, 0, 1.3)
+    d.set_launch(4, 128, 0, 1.3)
+    for m in (o, g, d):
+        m.step(5.0, 60)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+    e = rel_errors(g.moments(), d.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+
+
+def test_crowded_cells_match_oracle(orc, ms):
+    """Floes squeezed towards each cell's centre line (many overlaps, so
+    many contacts and list rebuilds by displacement), 40 steps: within the
+    FP32 tolerance of the oracle."""
+    s = I.batched_128x128(seed=13, nx=4)
+    p, dt = s["params"], s["dt"]
+    f = {k: v.copy() for k, v in s["floes"].items()}
+    f["x"] = f["x"] + 0.2 * (np.floor(f["x"] / 25e3) * 25e3 + 12.5e3 - f["x"])
+    o = orc.Model(p, f)
+    g = ms.Model(p, f, ms.MS_FP32)
+    g.set_launch(5, 128, 0, 1.3)
+    o.step(dt, 40)
+    g.step(dt, 40)
+    e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+    assert e.max() <= TOL32, report(e)
+    assert g.info()["deep_contacts"] >= 0
+
+
+def test_upload_inside_an_interval(ms):
+    """ms_set_floes inside a coarse interval folds the floes' running window
+    sums into the window first: the coarse solution after the interval agrees
+    with variant 4 (which adds every step to the window) within the FP32
+    tolerance (P_omega differs by about 2e-5 between two FP32 launch
+    variants, the same as between two reduction orders of one)."""
+    s = I.batched_128x128(seed=17, nx=8)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    res = []
+    for variant in (4, 5):
+        g = ms.Model(p, s["floes"], ms.MS_FP32)
+        g.set_launch(variant, 128, 0, 1.3)
+        g.step(dt, N0 + 43)
+        g.set_floes(g.floes())
+        g.step(dt, N0 - 43 + 5)
+        res.append((g.coupling()["q"], g.moments()))
+    for f in range(4):
+        a, b = res[0][0][f], res[1][0][f]
+        assert np.linalg.norm(a - b) <= TOL32 * np.linalg.norm(a), f
+    e = rel_errors(res[1][1], res[0][1], p, 1e-6)
+    assert e.max() <= 1e-4, report(e)
+
+
+def test_checkpoint_inside_an_interval(ms, tmp_path):
+    """A checkpoint written inside a gradual-update period carries the running
+    window sums: the resumed run equals the uninterrupted one bit for bit."""
+    s = I.batched_128x128(seed=11, nx=16)
+    p, dt = s["params"], s["dt"]
+    path = str(tmp_path / "v5.ck")
+    a = ms.Model(p, s["floes"], ms.MS_FP32)
+    b = ms.Model(p, s["floes"], ms.MS_FP32)
+    c = ms.Model(p, s["floes"], ms.MS_FP32)
+    for m in (a, b, c):
+        m.set_launch(5, 128, 0, 1.3)
+    a.step(dt, 235)
+    b.step(dt, 137)
+    b.save(path)
+    c.load_checkpoint(path)
+    assert c.info()["variant"] == 5
+    c.step(dt, 98)
+    _same(a, c)
