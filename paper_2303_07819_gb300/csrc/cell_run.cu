@@ -68,7 +68,8 @@ constexpr int LMAX = 16;           // candidate slots per floe
 constexpr int GCMAX = RUN_GCMAX;   // cells per group
 constexpr int WT = 128;            // steps per wind table
 constexpr int NRED = 6;            // values per reduction pass
-constexpr float SKIN_STEPS = 24.0f;   // horizon of a floe's skin, in fine steps (at its build speed)
+constexpr int NEVT = 32;           // gradual updates per interval with a precomputed radius ratio
+constexpr float SKIN_STEPS = 48.0f;   // horizon of a floe's skin, in fine steps (at its build speed)
 
 template <int K>
 struct RunSm {
@@ -86,11 +87,14 @@ struct RunSm {
     float PS[NRED][F];              // reduction partials at segment heads
     float2 Cm[GCMAX][MAXM];         // per cell and mode: corner phase (cos, sin), or (cycles, -)
     float rg[2][GCMAX][4];          // gradual update per cell (g, du, dv, dw), by step parity
-    float cgrow[GCMAX];             // growth the cell's radii can still take this interval
+    float cgrow[GCMAX][NEVT + 1];   // growth the cell's radii can still take this interval, by updates done
+    float cdv[GCMAX][NEVT + 1];     // speed the cell's gradual updates can still add, by updates done
+    double cwin[GCMAX][NWIN];       // the cells' window sums (loaded at the run's start, stored at its end)
+    float rgev[GCMAX][NEVT];        // radius ratio of each gradual update of the interval, per cell
     float2 wind[WT];
     int cc[GCMAX], cfs[GCMAX], cn[GCMAX], cnb[GCMAX], cbb[GCMAX], cgo[GCMAX];
     int ncg, nfl, nbin, item;
-    float vsum;
+    float vsum[2];                  // group speed sums of the builds, by build parity
 };
 
 __host__ __device__ constexpr size_t run_smem_bytes(int K)
@@ -141,6 +145,14 @@ __device__ void block_scan_bins(RunSm<K> &S, int nb)
         run += c;
     }
     __syncthreads();
+}
+
+// |(a, b)| from the hardware reciprocal square root (within a few ulp of
+// the correctly rounded norm; 0 for the zero vector)
+__device__ __forceinline__ float fast_norm(float a, float b)
+{
+    const float q = fmaf(a, a, b * b);
+    return q > 0.0f ? q * rsqrtf(q) : 0.0f;
 }
 
 // Ocean current and curl, and their gradients (per metre of global X, Y),
@@ -273,6 +285,33 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 S.Cm[ci][m] = make_float2(b, 0.0f);
             }
         }
+        // the window sums so far, added to in sequence and stored at the run's
+        // end (the same additions however the interval is split into runs)
+        if (t < ncg)
+            for (int q = 0; q < NWIN; q++) S.cwin[t][q] = win_on ? sc.win[(size_t)q * nc + S.cc[t]] : 0.0;
+        // per cell and gradual update of the interval (FP64, once): the
+        // update's radius ratio; and, by the updates already applied, the
+        // growth the radii can still take (r goes to r0 s at the last update
+        // from r0 (1 + (s - 1) ev n_t/N0) after update ev) and the velocity the
+        // remaining updates add (n_t/N0 of the target each)
+        const int nevt = have_tgt && nev <= NEVT ? nev : 0;
+        for (int idx = t; idx < ncg * (nevt + 1); idx += RT) {
+            const int ci = idx / (nevt + 1), ev = idx - ci * (nevt + 1);
+            const int c = S.cc[ci];
+            const double s = sc.tgt[c];
+            if (ev >= 1) S.rgev[ci][ev - 1] = (float)ramp_cell(sc, c, ev).g;
+            float gr = 1.0f, dvr = 0.0f;
+            if (nevt) {
+                const double g = s / (1.0 + (s - 1.0) * ev / (double)nev);
+                gr = g > 1.0 ? (float)(g * (1.0 + 1e-6)) : 1.0f;
+                const double du = sc.tgt[nc + c], dv = sc.tgt[2 * nc + c];
+                dvr = (float)(sqrt(du * du + dv * dv) * (nev - ev) / (double)nev);
+            }
+            S.cgrow[ci][ev] = gr;
+            S.cdv[ci][ev] = dvr;
+        }
+        if (t == 0) S.vsum[0] = S.vsum[1] = 0.0f;
+        int nbuild = 0;
         // gradual update of the run's first step, if it is one
         if (t < ncg) {
             const int kk = j0 + 1;
@@ -334,16 +373,16 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             }
             derived(k);
         }
-        __syncthreads();   // cell phases (Cm) before the first expansion
-#pragma unroll
-        for (int k = 0; k < K; k++)
-            oc[k] = ocean_expand(P, S, ci[k], (float)x0[k] * INV2_32F, (float)y0[k] * INV2_32F, sc.k.inx, sc.k.iny);
+        // the ocean expansions are made in the step loop (one call site, so
+        // every expansion rounds alike): at the first step about the centres
+        // above, later whenever a floe of the warp strays
+        bool expand_at_centre = true;
 
         // ---- reduction of NV (<= NRED) per-floe values per cell: segment
-        // sums over the floes of each warp, then the cell's partials in
-        // order; thread ci < ncg gets its cell's totals in outv.  All
-        // threads call it.
-        auto reduce_cells = [&](auto nv, auto &&value, double *outv) {
+        // sums over the floes of each warp (partials at the segment heads in
+        // PS, then a barrier); head_sum adds a cell's partials in order in
+        // FP64.  All threads call seg_partials.
+        auto seg_partials = [&](auto nv, auto &&value) {
             constexpr int NV = decltype(nv)::value;
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -362,19 +401,15 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 }
             }
             __syncthreads();
-            if (t < ncg) {
-                const int fs = S.cfs[t], fe = S.cfs[t] + S.cn[t];
-                for (int q = 0; q < NV; q++) {
-                    double acc = 0.0;
-                    for (int hd = fs; hd < fe; hd = (hd | 31) + 1) acc += (double)S.PS[q][hd];
-                    outv[q] = acc;
-                }
-            }
-            __syncthreads();
+        };
+        auto head_sum = [&](int cell, int q) {
+            const int fs = S.cfs[cell], fe = S.cfs[cell] + S.cn[cell];
+            double acc = 0.0;
+            for (int hd = fs; hd < fe; hd = (hd | 31) + 1) acc += (double)S.PS[q][hd];
+            return acc;
         };
         // window: the group of steps since the last flush (Algorithm 1 sums)
         auto flush = [&]() {
-            double tot[6];
             auto val = [&](int k, int q) -> float {
                 const float mass = P.mass_c * r[k] * r[k] * h[k];
                 switch (q) {
@@ -386,16 +421,17 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 default: return stz[k];
                 }
             };
-            reduce_cells(std::integral_constant<int, 6>{}, val, tot);
-            if (t < ncg) {
-                const int c = S.cc[t];
-                if (tot[0] > 0.0) {
-                    sc.win[c] += tot[1] / tot[0];
-                    sc.win[nc + c] += tot[2] / tot[0];
+            seg_partials(std::integral_constant<int, 6>{}, val);
+            // thread (cell, column): PS is written again only a step barrier later
+            if (t < 5 * ncg) {
+                const int cell = t / 5, q = t - 5 * cell;     // window column
+                const double x = head_sum(cell, q + 1);
+                if (q < 2) {
+                    const double M = head_sum(cell, 0);
+                    if (M > 0.0) S.cwin[cell][q] += x / M;
+                } else {
+                    S.cwin[cell][q] += x;
                 }
-                sc.win[2 * nc + c] += tot[3];
-                sc.win[3 * nc + c] += tot[4];
-                sc.win[4 * nc + c] += tot[5];
             }
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -413,36 +449,35 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 if (t + k * RT < nfl) vs += sqrtf(u[k] * u[k] + v[k] * v[k]);
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) vs += __shfl_xor_sync(FULL, vs, d);
-            if (t == 0) S.vsum = 0.0f;
             for (int i = t; i <= S.nbin; i += RT) S.BS[i] = 0;
-            // growth the cell's radii can still take in this interval: the
-            // gradual updates bring r to r0 s at its last one, from r0 (1 +
-            // (s - 1) ev n_t/N0) after update ev
-            if (t < ncg) {
-                float gr = 1.0f;
-                if (have_tgt) {
-                    const double s = sc.tgt[S.cc[t]];
-                    const int ev = (kk - 1) / sc.n_t;       // updates already applied
-                    const double now = 1.0 + (s - 1.0) * ev / (double)nev;
-                    const double g = s / now;
-                    gr = g > 1.0 ? (float)(g * (1.0 + 1e-6)) : 1.0f;
-                }
-                S.cgrow[t] = gr;
+            if (have_tgt && !nevt && t < ncg) {   // more updates per interval than the table holds
+                const int c = S.cc[t];
+                const double s = sc.tgt[c];
+                const int ev = (kk - 1) / sc.n_t;
+                const double g = s / (1.0 + (s - 1.0) * ev / (double)nev);
+                const double du = sc.tgt[nc + c], dv = sc.tgt[2 * nc + c];
+                S.cgrow[t][0] = g > 1.0 ? (float)(g * (1.0 + 1e-6)) : 1.0f;
+                S.cdv[t][0] = (float)(sqrt(du * du + dv * dv) * (nev - ev) / (double)nev);
             }
+            const int vb = nbuild & 1;
+            if (lane == 0) atomicAdd(&S.vsum[vb], vs);
+            if (t == 0) S.vsum[vb ^ 1] = 0.0f;    // for the next build
             __syncthreads();
-            if (lane == 0) atomicAdd(&S.vsum, vs);
-            __syncthreads();
-            const float vfloor = 0.25f * S.vsum / (float)max(nfl, 1);
+            // updates already applied (radius growth and velocity still to come)
+            int evd = (kk - 1) / sc.n_t;
+            if (!nevt) evd = 0;
+            const float vfloor = 0.25f * S.vsum[vb] / (float)max(nfl, 1);
+            nbuild++;
             const float horizon = SKIN_STEPS * dt;
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 const int p = t + k * RT;
                 if (p < nfl) {
                     const int c2 = ci[k], nb = S.cnb[c2];
-                    const float sp = sqrtf(u[k] * u[k] + v[k] * v[k]);
+                    const float sp = sqrtf(u[k] * u[k] + v[k] * v[k]) + S.cdv[c2][evd];
                     const float skin = (1.5f * sp + vfloor) * horizon + 1.0e-3f * r[k];
                     sk2[k] = skin * skin;
-                    const float reach = r[k] * S.cgrow[c2] + skin;
+                    const float reach = r[k] * S.cgrow[c2][evd] + skin;
                     S.RE[p] = reach;
                     const bool small = nb >= 3 && reach <= 0.5f * (Lcmin / (float)nb);
                     const int bn = S.cbb[c2] + (small ? (int)(__umulhi(yq[k], (unsigned)nb) * nb +
@@ -539,28 +574,39 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
         __syncthreads();
         int cur = 0;
         bool need_build = true;
+        int ph = (j0 + 1) % sc.n_t;                       // kk mod n_t
         for (int js = 0; js < nsteps; js++) {
             const int kk = j0 + js + 1;                   // step within the interval, 1-based
-            if (js > 0 && js % WT == 0) {
+            if (js > 0 && (js & (WT - 1)) == 0) {
                 __syncthreads();
                 wind_table(js);
                 __syncthreads();
             }
-            if (win_on && kk % sc.n_t == 0) flush();      // the steps of the previous masses
+            const bool period_end = ph == 0;
+            if (win_on && period_end) flush();            // the steps of the previous masses
             if (need_build) build(cur, kk);
             __syncthreads();
-            const float2 wa = S.wind[js % WT];
-            const bool ramp = have_tgt && (kk % sc.n_t == 0);
+            const float2 wa = S.wind[js & (WT - 1)];
+            const bool ramp = have_tgt && period_end;
             const int rb = js & 1;
+            ph = ph + 1 == sc.n_t ? 0 : ph + 1;           // next step's kk mod n_t
             // next step's gradual update, published by the step barrier below
-            if (t < ncg && js + 1 < nsteps) {
-                const int k2 = kk + 1;
-                float g = 1.0f, du = 0.0f, dv = 0.0f, dw = 0.0f;
-                if (have_tgt && k2 % sc.n_t == 0) {
-                    const RampCell rc = ramp_cell(sc, S.cc[t], k2 / sc.n_t);
-                    g = (float)rc.g; du = (float)rc.du; dv = (float)rc.dv; dw = (float)rc.dw;
+            if (have_tgt && ph == 0 && t < ncg && js + 1 < nsteps) {
+                const int ev = (kk + 1) / sc.n_t;
+                if (nev <= NEVT) {
+                    const double f = (double)sc.n_t / (double)sc.N0;
+                    const int c = S.cc[t];
+                    S.rg[rb ^ 1][t][0] = S.rgev[t][ev - 1];
+                    S.rg[rb ^ 1][t][1] = (float)(sc.tgt[nc + c] * f);
+                    S.rg[rb ^ 1][t][2] = (float)(sc.tgt[2 * nc + c] * f);
+                    S.rg[rb ^ 1][t][3] = (float)(sc.tgt[3 * nc + c] * f);
+                } else {
+                    const RampCell rc = ramp_cell(sc, S.cc[t], ev);
+                    S.rg[rb ^ 1][t][0] = (float)rc.g;
+                    S.rg[rb ^ 1][t][1] = (float)rc.du;
+                    S.rg[rb ^ 1][t][2] = (float)rc.dv;
+                    S.rg[rb ^ 1][t][3] = (float)rc.dw;
                 }
-                S.rg[rb ^ 1][t][0] = g; S.rg[rb ^ 1][t][1] = du; S.rg[rb ^ 1][t][2] = dv; S.rg[rb ^ 1][t][3] = dw;
             }
             const bool last = js == nsteps - 1;
             bool far = false;
@@ -576,12 +622,15 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 const bool wrapped = (xq[k] < x0[k]) != (ix < 0) || (yq[k] < y0[k]) != (iy < 0);
                 const bool stale = valid && (wrapped || ddx * ddx + ddy * ddy > P.ocean_d2);
                 float ex = ddx, ey = ddy;
-                if (__any_sync(FULL, stale)) {
-                    x0[k] = xq[k];
-                    y0[k] = yq[k];
-                    oc[k] = ocean_expand(P, S, ci[k], (float)xq[k] * INV2_32F, (float)yq[k] * INV2_32F, sc.k.inx,
+                const bool recentre = __any_sync(FULL, stale);
+                if (recentre || expand_at_centre) {
+                    if (recentre) {
+                        x0[k] = xq[k];
+                        y0[k] = yq[k];
+                        ex = ey = 0.0f;
+                    }
+                    oc[k] = ocean_expand(P, S, ci[k], (float)x0[k] * INV2_32F, (float)y0[k] * INV2_32F, sc.k.inx,
                                          sc.k.iny);
-                    ex = ey = 0.0f;
                 }
                 if (!valid) continue;
                 // contacts, ascending partner order
@@ -596,13 +645,13 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                     contact_add(dx, dy, dx * dx + dy * dy, r[k], aq.w, h[k], S.H[q], aq.x - u[k], aq.y - v[k], w[k],
                                 aq.z, P, fx, fy, tq, dflag);
                 };
-                const int n = lc[k];
-                if (n <= LMAX) {
-                    for (int i = 0; i < n; i++) pair(S.L[i][p]);
-                } else {
-                    const int c2 = ci[k];
-                    for (int q = S.cfs[c2]; q < S.cfs[c2] + S.cn[c2]; q++)
-                        if (q != p) pair(q);
+                // one call site for the pair law: a floe whose list overflowed
+                // walks its whole cell in the same order
+                const bool brute = lc[k] > LMAX;
+                const int cnt = brute ? S.cn[ci[k]] : lc[k], q0 = S.cfs[ci[k]];
+                for (int i = 0; i < cnt; i++) {
+                    const int q = brute ? q0 + i : (int)S.L[i][p];
+                    if (q != p) pair(q);
                 }
                 deep += dflag;
                 // ocean and wind drag (Eq. 2.1c-d)
@@ -613,9 +662,9 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 const float r2 = r[k] * r[k];
                 const float ao = P.drag_o * r2, aa = P.drag_a * r2, bo = ao * r2;
                 const float du_o = uo - u[k], dv_o = vo - v[k];
-                const float so = sqrtf(du_o * du_o + dv_o * dv_o);
+                const float so = fast_norm(du_o, dv_o);
                 const float au = wa.x - u[k], av = wa.y - v[k];
-                const float sa = sqrtf(au * au + av * av);
+                const float sa = fast_norm(au, av);
                 const float dwo = 0.5f * zeta - w[k];
                 const float Fdx = ao * du_o * so + aa * au * sa;
                 const float Fdy = ao * dv_o * so + aa * av * sa;
@@ -650,10 +699,10 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 far |= bx * bx + by * by > sk2[k];
             }
             need_build = __syncthreads_or(far) != 0;
+            expand_at_centre = false;
             cur ^= 1;
             if (last) {
                 // the cell moments of the run's last step (all columns)
-                double tot[NMOM];
                 auto val1 = [&](int k, int q) -> float {
                     const float m = P.mass_c * r[k] * r[k] * h[k];
                     const float I = P.inertia_f * m * r[k] * r[k];
@@ -676,16 +725,27 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                     default: return Fdl[k][2];
                     }
                 };
-                reduce_cells(std::integral_constant<int, 6>{}, val1, tot);
-                reduce_cells(std::integral_constant<int, 5>{}, val2, tot + 6);
-                if (t < ncg) {
-                    double *mo = sc.mom + (size_t)S.cc[t] * NMOM;
-                    mo[0] = (double)S.cn[t];
-                    for (int q = 1; q < NMOM; q++) mo[q] = tot[q - 1];
+                seg_partials(std::integral_constant<int, 6>{}, val1);
+                if (t < 6 * ncg) {
+                    const int cell = t / 6, q = t - 6 * cell;
+                    sc.mom[(size_t)S.cc[cell] * NMOM + 1 + q] = head_sum(cell, q);
                 }
+                __syncthreads();
+                seg_partials(std::integral_constant<int, 5>{}, val2);
+                if (t < 5 * ncg) {
+                    const int cell = t / 5, q = t - 5 * cell;
+                    sc.mom[(size_t)S.cc[cell] * NMOM + 7 + q] = head_sum(cell, q);
+                }
+                if (t < ncg) sc.mom[(size_t)S.cc[t] * NMOM] = (double)S.cn[t];
+                __syncthreads();
             }
         }
         if (ends_interval) flush();
+        __syncthreads();
+        if (win_on && t < ncg) {
+            const int c = S.cc[t];
+            for (int q = 0; q < NWIN; q++) sc.win[(size_t)q * nc + c] = S.cwin[t][q];
+        }
         // ---- back to global memory
 #pragma unroll
         for (int k = 0; k < K; k++) {

@@ -83,6 +83,29 @@ def test_runs_split_anywhere_are_bitwise_equal(ms):
     _same(a, c)
 
 
+def test_repeat_runs_are_bitwise_equal(ms):
+    """Builds happen at times that depend on a floating-point speed sum (a
+    shared-memory atomic, whose order varies), and floes switch between their
+    candidate list and the all-cell walk when a list overflows; neither may
+    change a result.  Two models of a crowded workload, three coarse
+    intervals from the graph, and the same steps in runs of 7: the same floes
+    and coarse solution bit for bit."""
+    s = I.batched_128x128(seed=23, nx=8)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    f = {k: v.copy() for k, v in s["floes"].items()}
+    f["x"] = f["x"] + 0.15 * (np.floor(f["x"] / 25e3) * 25e3 + 12.5e3 - f["x"])
+    ms_ = [ms.Model(p, f, ms.MS_FP32) for _ in range(3)]
+    for m in ms_:
+        m.set_launch(5, 128, 0, 1.3)
+    ms_[0].step(dt, 3 * N0)
+    ms_[1].step(dt, 3 * N0)
+    for _ in range(3 * N0 // 7):
+        ms_[2].step(dt, 7)
+    ms_[2].step(dt, 3 * N0 - 7 * (3 * N0 // 7))
+    _same(ms_[0], ms_[1])
+    _same(ms_[0], ms_[2])
+
+
 def test_contacts_and_list_overflow(orc, ms):
     """A 3 km floe ringed by 60 floes of 150 m that touch it (its list of at
     most 16 candidates overflows and it tests every floe of its cell), plus
