@@ -223,8 +223,16 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
  * r_l + r_j + skin, rebuilt by the binned search at the start of every
  * gradual-update period, whenever a floe has moved half the skin, and
  * after a list overflowed), cells of up to 640 floes warp-per-cell and
- * larger ones block-per-cell.  Variants 2-4 give the same
- * results whether an interval runs in one launch or step by step.
+ * larger ones block-per-cell; variant 5 (the default) keeps every cell of up
+ * to 1024 floes resident in registers for a whole run of steps (one launch
+ * per coarse interval on the graph path): a floe per thread of a 256-thread
+ * block that several small cells share, 2 or 4 floes per thread for cells of
+ * 257-512 or 513-1024 floes, blocks taking groups of cells from a work queue
+ * largest first; contact candidates from per-floe skins, summed in
+ * ascending partner order; larger cells run the block list kernel step by
+ * step (see ms_set_resident for its tunables).  Variants 2-5 give the same
+ * results whether an interval runs in one launch or step by step.  With a
+ * closure attached, variant 5 runs as variant 4.
  * MS_ERR_ARG for an unsupported choice. */
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
 
@@ -235,14 +243,26 @@ int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persist
  * interval's first step, no coarse step). */
 int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *mean_ms);
 
-/* Model facts, host out[16] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
+/* Tunables of launch variant 5 (the default for FP32): each floe's skin --
+ * how far it may move before its cell group searches for contact candidates
+ * again -- is its speed (plus what the coming gradual updates add) times
+ * skin_steps fine steps (1 .. 1000); cells of at most block_floes floes
+ * (32 .. 256) share a block of 256 threads, a floe per thread, up to that
+ * many floes in all.  Results do not depend on skin_steps; block_floes
+ * changes which cells share a block, and with it the order of the per-cell
+ * FP32 sums (moments differ by rounding only).  ms_autotune chooses both;
+ * ms_info entries 16 and 17 report them.  MS_ERR_ARG outside the ranges. */
+int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes);
+
+/* Model facts, host out[18] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
  * 4 kernel variant, 5 threads per block, 6 bin width (per mille of the mean
  * floe spacing), 7 cell-kernel launches per coarse interval (msDEM, whole
  * intervals, no coarse step),
  * 8 kernels per coarse step, 9 kernels per truth step, 10 steps done,
  * 11 truth steps done, 12 graph replays so far, 13 contacts seen deeper than
  * half the smaller radius, 14 persistent launch, 15 LF substeps of the last
- * coarse step. */
+ * coarse step, 16 skin horizon of variant 5 in thousandths of a fine step,
+ * 17 floes per block of small cells of variant 5. */
 int ms_info(ms_model *m, int64_t *out);
 
 /* Per-cell moments of a floe set held in the caller's device memory, computed

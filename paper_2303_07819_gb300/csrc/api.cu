@@ -665,6 +665,8 @@ static void fill_phys(ms_model *m)
         Q.mA[k] = (float)P.mA[k];
         Q.ta[k] = (float)(kx * Lcx);
         Q.tb[k] = (float)(ky * Lcy);
+        Q.mKx[k] = (float)kx;      // rad per metre: the gradient of the mode in the ocean expansion
+        Q.mKy[k] = (float)ky;
         // small-angle form of the per-floe phase: valid when no mode turns
         // by more than 1/16 cycle across one cell
         if ((std::fabs(kx) * Lcx + std::fabs(ky) * Lcy) / (2.0 * PI_D) > 1.0 / 16.0) Q.taylor = 0;
@@ -795,7 +797,7 @@ static int build_groups(ms_model *m, CellLaunch &cl)
             }
         }
         if (found < 0) {
-            gs.push_back(G{1, RUN_T, 0, {}});
+            gs.push_back(G{1, std::max(std::min(cl.run_cap1, RUN_T), n), 0, {}});
             found = (int)gs.size() - 1;
         }
         place(found, cc);
@@ -1393,9 +1395,11 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
         return rc;
     }
     CellLaunch cl{};
-    cl.variant = m->precision == MS_FP32 ? 4 : 0;
+    cl.variant = m->precision == MS_FP32 ? 5 : 0;
     cl.threads = 128;
     cl.bin_beta = 1.3f;
+    cl.run_skin = 32.0f;
+    cl.run_cap1 = RUN_T;
     cl.persistent = 0;
     cl.grid = m->sm_count * 4;
     if (cl.variant >= 1 && configure_launch(m, cl) != MS_OK) cl.variant = 0;   // cells too large to bin in shared memory
@@ -1764,6 +1768,20 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms)
                 c.bin_beta = b;
                 cand.push_back(c);
             }
+        // variant 5: bins per cell, the skin's horizon and the floes per
+        // block of small cells (how many cells share a block)
+        const float skins[4] = {16.0f, 24.0f, 32.0f, 48.0f};
+        const int caps[3] = {160, 208, RUN_T};
+        for (float b : {1.0f, 1.3f, 1.7f})
+            for (float sk : skins)
+                for (int cap : caps) {
+                    CellLaunch c = m->cl;
+                    c.variant = 5;
+                    c.bin_beta = b;
+                    c.run_skin = sk;
+                    c.run_cap1 = cap;
+                    cand.push_back(c);
+                }
     }
     // FP32: whole coarse intervals, so that variants that keep a cell
     // resident across steps are timed by what they save
@@ -1827,7 +1845,22 @@ int ms_info(ms_model *m, int64_t *out)
     out[13] = (int64_t)c.deep;
     out[14] = m->cl.persistent;
     out[15] = c.N1;
+    out[16] = (int64_t)std::lround(m->cl.run_skin * 1000.0f);
+    out[17] = m->cl.run_cap1;
     return MS_OK;
+}
+
+int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (!(skin_steps >= 1.0 && skin_steps <= 1000.0)) return fail(MS_ERR_ARG, "skin_steps must be in [1, 1000]");
+    if (block_floes < 32 || block_floes > RUN_T)
+        return fail(MS_ERR_ARG, "block_floes must be in [32, %d]", RUN_T);
+    CellLaunch c = m->cl;
+    c.run_skin = (float)skin_steps;
+    c.run_cap1 = block_floes;
+    CK(cudaStreamSynchronize(m->stream));
+    return configure_launch(m, c);
 }
 
 int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia_half, int64_t n,
@@ -1952,7 +1985,9 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
         if (e == cudaSuccess)
             e = launch_features(m->d_mom, m->d_tgt, nc, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
                                 m->d_Ylag, m->d_X, m->stream);
-        for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);
+        if (e == cudaSuccess && interval_cells(m)) e = launch_interval_cells(m, false);
+        else
+            for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);
         if (e == cudaSuccess)
             e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, nc, m->fc.N0, dT, nullptr, nullptr, m->d_ctrl,
                                        m->d_Ylag, m->d_Yc, nullptr, 0.0, nullptr, nullptr, m->stream);

@@ -63,13 +63,23 @@ namespace msd {
 
 namespace {
 
+// Tunables (measured on the 128 x 128 batched workload; see the build flags)
+#ifndef MS_RUN_LMAX
+#define MS_RUN_LMAX 16
+#endif
+#ifndef MS_RUN_K1_BLOCKS
+#define MS_RUN_K1_BLOCKS 4
+#endif
+#ifndef MS_RUN_K2_BLOCKS
+#define MS_RUN_K2_BLOCKS 2
+#endif
+
 constexpr int RT = RUN_T;          // threads per block
-constexpr int LMAX = 16;           // candidate slots per floe
+constexpr int LMAX = MS_RUN_LMAX;  // candidate slots per floe
 constexpr int GCMAX = RUN_GCMAX;   // cells per group
 constexpr int WT = 128;            // steps per wind table
 constexpr int NRED = 6;            // values per reduction pass
 constexpr int NEVT = 32;           // gradual updates per interval with a precomputed radius ratio
-constexpr float SKIN_STEPS = 48.0f;   // horizon of a floe's skin, in fine steps (at its build speed)
 
 template <int K>
 struct RunSm {
@@ -95,6 +105,7 @@ struct RunSm {
     int cc[GCMAX], cfs[GCMAX], cn[GCMAX], cnb[GCMAX], cbb[GCMAX], cgo[GCMAX];
     int ncg, nfl, nbin, item;
     float vsum[2];                  // group speed sums of the builds, by build parity
+    int cflag[3][GCMAX];            // a floe of the cell strayed from its ocean centre, by step mod 3
 };
 
 __host__ __device__ constexpr size_t run_smem_bytes(int K)
@@ -147,12 +158,17 @@ __device__ void block_scan_bins(RunSm<K> &S, int nb)
     __syncthreads();
 }
 
-// |(a, b)| from the hardware reciprocal square root (within a few ulp of
-// the correctly rounded norm; 0 for the zero vector)
-__device__ __forceinline__ float fast_norm(float a, float b)
+// Has a floe at fixed point (xq, yq) left the region where the first-order
+// expansion of the current about (x0, y0) holds (squared distance above d2),
+// or wrapped across its cell's edge since (its global position jumped by a
+// cell side while the fixed-point difference stayed small)?
+__device__ __forceinline__ bool ocean_stale(uint32_t xq, uint32_t yq, uint32_t x0, uint32_t y0, float sx, float sy,
+                                            float d2)
 {
-    const float q = fmaf(a, a, b * b);
-    return q > 0.0f ? q * rsqrtf(q) : 0.0f;
+    const int ix = (int)(xq - x0), iy = (int)(yq - y0);
+    const float dx = (float)ix * sx, dy = (float)iy * sy;
+    const bool wrapped = (xq < x0) != (ix < 0) || (yq < y0) != (iy < 0);
+    return wrapped || dx * dx + dy * dy > d2;
 }
 
 // Ocean current and curl, and their gradients (per metre of global X, Y),
@@ -199,9 +215,9 @@ __device__ __forceinline__ OceanExp ocean_expand(const Phys<float> &P, const Run
 }
 
 template <int K>
-__global__ void __launch_bounds__(RT, K == 1 ? 3 : (K == 2 ? 2 : 1))
+__global__ void __launch_bounds__(RT, K == 1 ? MS_RUN_K1_BLOCKS : (K == 2 ? MS_RUN_K2_BLOCKS : 1))
 k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, const int4 *groups, int ngroups,
-                   const int4 *items, int qslot, int nsteps)
+                   const int4 *items, int qslot, int nsteps, float skin_steps)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RunSm<K> &S = *reinterpret_cast<RunSm<K> *>(smem_raw);
@@ -270,6 +286,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             S.nfl = gd.z;
             S.nbin = gd.w;
         }
+        if (t < 3 * GCMAX) (&S.cflag[0][0])[t] = 0;
         __syncthreads();
         const int ncg = S.ncg, nfl = S.nfl;
         for (int idx = t; idx < ncg * P.n_modes; idx += RT) {
@@ -468,7 +485,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             if (!nevt) evd = 0;
             const float vfloor = 0.25f * S.vsum[vb] / (float)max(nfl, 1);
             nbuild++;
-            const float horizon = SKIN_STEPS * dt;
+            const float horizon = skin_steps * dt;
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 const int p = t + k * RT;
@@ -570,6 +587,11 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             }
         };
 
+        // the first step's recentring follows the rule of every later step:
+        // a cell whose floe strayed from its centre expands again
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            if (t + k * RT < nfl && ocean_stale(xq[k], yq[k], x0[k], y0[k], sx, sy, P.ocean_d2)) S.cflag[0][ci[k]] = 1;
         if (nsteps > WT) wind_table(0);   // a previous group left a later table
         __syncthreads();
         int cur = 0;
@@ -609,6 +631,8 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 }
             }
             const bool last = js == nsteps - 1;
+            const int fl_cur = js % 3, fl_nxt = (js + 1) % 3;
+            if (t < ncg) S.cflag[(js + 2) % 3][t] = 0;     // read two steps ago, written at the next step's end
             bool far = false;
             float Fdl[K][3];
 #pragma unroll
@@ -616,13 +640,13 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 Fdl[k][0] = Fdl[k][1] = Fdl[k][2] = 0.0f;
                 const int p = t + k * RT;
                 const bool valid = p < nfl;
-                // the ocean expansion still holds? (whole warp expands again if not)
-                const int ix = (int)(xq[k] - x0[k]), iy = (int)(yq[k] - y0[k]);
-                const float ddx = (float)ix * sx, ddy = (float)iy * sy;
-                const bool wrapped = (xq[k] < x0[k]) != (ix < 0) || (yq[k] < y0[k]) != (iy < 0);
-                const bool stale = valid && (wrapped || ddx * ddx + ddy * ddy > P.ocean_d2);
-                float ex = ddx, ey = ddy;
-                const bool recentre = __any_sync(FULL, stale);
+                // the ocean expansion: every floe of a cell expands again about
+                // its current position when one of them strayed at the last
+                // step (a decision of the cell alone, whatever shares its
+                // block); at the run's first step each floe about its centre
+                // unless it strayed from it
+                float ex = (float)(int)(xq[k] - x0[k]) * sx, ey = (float)(int)(yq[k] - y0[k]) * sy;
+                const bool recentre = valid && S.cflag[fl_cur][ci[k]] != 0;
                 if (recentre || expand_at_centre) {
                     if (recentre) {
                         x0[k] = xq[k];
@@ -662,9 +686,9 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 const float r2 = r[k] * r[k];
                 const float ao = P.drag_o * r2, aa = P.drag_a * r2, bo = ao * r2;
                 const float du_o = uo - u[k], dv_o = vo - v[k];
-                const float so = fast_norm(du_o, dv_o);
+                const float so = sqrtf(du_o * du_o + dv_o * dv_o);
                 const float au = wa.x - u[k], av = wa.y - v[k];
-                const float sa = fast_norm(au, av);
+                const float sa = sqrtf(au * au + av * av);
                 const float dwo = 0.5f * zeta - w[k];
                 const float Fdx = ao * du_o * so + aa * au * sa;
                 const float Fdy = ao * dv_o * so + aa * av * sa;
@@ -697,6 +721,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 }
                 const float bx = (float)(int)(xq[k] - xb[k]) * sx, by = (float)(int)(yq[k] - yb[k]) * sy;
                 far |= bx * bx + by * by > sk2[k];
+                if (!last && ocean_stale(xq[k], yq[k], x0[k], y0[k], sx, sy, P.ocean_d2)) S.cflag[fl_nxt][ci[k]] = 1;
             }
             need_build = __syncthreads_or(far) != 0;
             expand_at_centre = false;
@@ -865,19 +890,19 @@ static int run_block_grid(int K, int ngroups)
 
 cudaError_t launch_run_block(int K, const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                              const StepCommon &sc, const int4 *groups, int ngroups, const int4 *items, int qslot,
-                             int nsteps, cudaStream_t st)
+                             int nsteps, float skin_steps, cudaStream_t st)
 {
     if (ngroups <= 0 || nsteps <= 0) return cudaSuccess;
     const int grid = run_block_grid(K, ngroups);
     if (K == 1)
         k_cell_run32_block<1><<<grid, RT, run_smem_bytes(1), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
-                                                                    nsteps);
+                                                                    nsteps, skin_steps);
     else if (K == 2)
         k_cell_run32_block<2><<<grid, RT, run_smem_bytes(2), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
-                                                                    nsteps);
+                                                                    nsteps, skin_steps);
     else
         k_cell_run32_block<4><<<grid, RT, run_smem_bytes(4), st>>>(in, out, P, sc, groups, ngroups, items, qslot,
-                                                                    nsteps);
+                                                                    nsteps, skin_steps);
     return cudaGetLastError();
 }
 

@@ -2278,7 +2278,7 @@ static cudaError_t launch_seg32(const DevState32 &in, const DevState32 &out, con
     if (cl.seg_kind[s] == 3) {   // resident blocks (variant 5): one launch for the whole run
         const int K = cl.seg_maxn[s] / RUN_T;
         return launch_run_block(K, in, out, P, sc0, cl.rgroups[s], cl.rngroups[s], cl.ritems,
-                                K == 1 ? 0 : (K == 2 ? 1 : 2), nsteps, st);
+                                K == 1 ? 0 : (K == 2 ? 1 : 2), nsteps, cl.run_skin, st);
     }
     if (cl.seg_kind[s] == 2) {   // resident in registers: one launch for the whole run
         if (cl.npack <= 0) return cudaSuccess;

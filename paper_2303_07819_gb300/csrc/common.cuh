@@ -268,6 +268,8 @@ struct CellLaunch {
     const int4 *rgroups[MAXSEG];
     int rngroups[MAXSEG];
     const int4 *ritems;
+    float run_skin;    // variant 5: horizon of a floe's skin, fine steps at its build speed
+    int run_cap1;      // variant 5: floes per block of small cells (at most RUN_T)
     // segments of variant 2 run on their own streams, forked from and joined
     // back into the launching stream (concurrent branches in a graph)
     cudaStream_t side[MAXSEG];
@@ -376,7 +378,7 @@ constexpr int RUN_NCARRY = 7;   // words per floe a run hands to the next: 5 win
 // carry is sc.carry_in / sc.carry_out; qslot = the class's queue in Ctrl.
 cudaError_t launch_run_block(int K, const DevState32 &in, const DevState32 &out, const Phys<float> &P,
                              const StepCommon &sc, const int4 *groups, int ngroups, const int4 *items, int qslot,
-                             int nsteps, cudaStream_t st);
+                             int nsteps, float skin_steps, cudaStream_t st);
 size_t run_block_smem(int K);
 cudaError_t run_block_prepare();
 // fold the running window sums of a run that stopped inside a coarse interval

@@ -58,7 +58,7 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
-           "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm"]
+           "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm", "ms_set_resident"]
 
 
 def lib_path() -> str:
@@ -93,6 +93,7 @@ def load(path: str | None = None):
     L.ms_autotune.argtypes = [vp, C.c_double, C.c_int32, _dp]
     L.ms_time_kernel.argtypes = [vp, C.c_int32, C.c_double, C.c_int32, _dp]
     L.ms_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_double]
+    L.ms_set_resident.argtypes = [vp, C.c_double, C.c_int32]
     L.ms_info.argtypes = [vp, C.POINTER(C.c_int64)]
     L.ms_cell_moments_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int32, C.c_int64] + [vp] * 10
     L.ms_closure_attach.argtypes = [vp, vp, C.c_int32, C.c_double, C.POINTER(C.c_float)]
@@ -273,12 +274,16 @@ class Model:
         return {"closure_cell_intervals": int(out[0]), "cells": int(out[1]), "mode": int(out[2]),
                 "intervals": int(out[3])}
 
+    def set_resident(self, skin_steps: float = 32.0, block_floes: int = 256) -> None:
+        _check(load().ms_set_resident(self._h, float(skin_steps), int(block_floes)))
+
     def info(self) -> dict:
-        out = np.zeros(16, dtype=np.int64)
+        out = np.zeros(18, dtype=np.int64)
         _check(load().ms_info(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "ncell", "max_n", "precision", "variant", "threads", "bin_beta_milli",
                 "launches_per_interval", "launches_per_coarse", "launches_per_truth_step", "steps",
-                "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1"]
+                "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1", "skin_steps_milli",
+                "block_floes"]
         return {k: int(v) for k, v in zip(keys, out)}
 
 

@@ -26,24 +26,27 @@ def realizations(R=3, nx=4):
     return scens
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_ensemble_equals_separate_models(ms, precision):
+@pytest.mark.parametrize("precision, variant", [(0, 4), (1, 0)])
+def test_ensemble_equals_separate_models(ms, precision, variant):
     """Floes, moments and coarse state of the batched ensemble are those of
     the separate models through two coarse steps (graph path) and 50 single
     steps: bit for bit in FP32 (positions are fixed point of the cell, so the
     stacking offset e Ly leaves them unchanged); in FP64 the stacked y = y +
     e Ly rounds the offsets within the cell by an ulp of e Ly, so there the
-    two agree to 1e-10."""
+    two agree to 1e-10.  FP32 with the warp-per-cell kernels (variant 4),
+    whose sums over a cell do not depend on the other cells."""
     scens = realizations()
     ens = I.stack_ensemble(scens)
     dt, nsteps = ens["dt"], 250
     g = ms.Model(ens["params"], ens["floes"], precision)
+    g.set_launch(variant, 128, 0, 1.3)
     g.step(dt, nsteps)
     fe, me, qe = g.floes(), g.moments(), g.coupling()["q"]
     nc = scens[0]["params"]["nx"] * scens[0]["params"]["ny"]
     off = 0
     for e, sc in enumerate(scens):
         m = ms.Model(sc["params"], sc["floes"], precision)
+        m.set_launch(variant, 128, 0, 1.3)
         m.step(dt, nsteps)
         f = m.floes()
         n = f["x"].shape[0]
@@ -63,6 +66,43 @@ def test_ensemble_equals_separate_models(ms, precision):
             assert np.linalg.norm(q0 - q1) <= 1e-10 * np.linalg.norm(q1), e
         off += n
         m.close()
+
+
+def test_ensemble_resident_blocks(ms):
+    """The resident block kernels (variant 5, the default) pack cells of all
+    realizations into shared blocks, differently from separate models.  A
+    floe's arithmetic does not depend on its block: until the first coarse
+    step (which feeds the cells' moments back) the ensemble's floes are the
+    separate models' bit for bit.  The moments are sums over the floes of a
+    block's warps, which do follow the packing: after two coarse steps the
+    two agree within the FP32 tolerance."""
+    scens = realizations()
+    ens = I.stack_ensemble(scens)
+    dt = ens["dt"]
+    N0 = ens["params"]["N0"]
+    g = ms.Model(ens["params"], ens["floes"], 0)
+    assert g.info()["variant"] == 5
+    seps = [ms.Model(sc["params"], sc["floes"], 0) for sc in scens]
+    nc = scens[0]["params"]["nx"] * scens[0]["params"]["ny"]
+    for nsteps, exact in ((N0 - 1, True), (2 * N0 + 51, False)):
+        g.step(dt, nsteps)
+        fe, me, qe = g.floes(), g.moments(), g.coupling()["q"]
+        off = 0
+        for e, (sc, m) in enumerate(zip(scens, seps)):
+            m.step(dt, nsteps)
+            f = m.floes()
+            n = f["x"].shape[0]
+            if exact:
+                for k in f:
+                    want = f[k] + (e * sc["params"]["Ly"] if k == "y" else 0.0)
+                    assert np.array_equal(fe[k][off:off + n], want), (e, k)
+            else:
+                err = rel_errors(me[e * nc:(e + 1) * nc], m.moments(), sc["params"], 1e-6)
+                assert err.max() <= 1e-4, report(err)
+                q0, q1 = qe[:, e * nc:(e + 1) * nc], m.coupling()["q"]
+                for fld in range(4):
+                    assert np.linalg.norm(q0[fld] - q1[fld]) <= 1e-4 * np.linalg.norm(q1[fld]), (e, fld)
+            off += n
 
 
 def test_ensemble_matches_oracle(orc, ms):

@@ -63,8 +63,11 @@ def test_network_learns_translational_drag(trained):
 
 
 def _run(msdem, s, mode, tol, net, box, K):
+    """The closure's cell selection runs on the warp-per-cell kernels
+    (variant 4), so the particle-only runs here use them too."""
     p = s["params"]
     m = msdem.Model(p, s["floes"], 0)
+    m.set_launch(4, 128, 0, 1.3)
     m.step(s["dt"], p["N0"] * SPIN)
     if mode >= 0:
         m.closure_attach(net if mode == 0 else None, mode, tol, box)

@@ -201,15 +201,15 @@ def test_largest_cell_fp32(orc, ms):
 
 def test_full_size_batched_sampled_cells(orc, ms):
     """The 128 x 128 batched workload at full size (~2.0M floes, 16,384 cells)
-    on the GPU in the launch the bench times (variant 4: candidate lists
-    built at steps 1 and 11, read in between), 12 steps; the oracle
+    on the GPU in the launch the bench times (variant 5: every cell resident
+    for the run, candidate lists built at the run's start), 12 steps; the oracle
     recomputes a sample of 48 cells (the largest and random ones) from those
     cells' floes alone, since the cells' DEMs are independent until the first
     coarse step."""
     s = I.batched_128x128()
     p = s["params"]
     g = ms.Model(p, s["floes"], ms.MS_FP32)
-    assert g.info()["variant"] == 4
+    assert g.info()["variant"] == 5
     g.step(s["dt"], 12)
     mg = g.moments()
     cell = s["meta"]["cell"]
@@ -330,6 +330,8 @@ def test_autotune_keeps_results(ms):
     assert best > 0
     ib = b.info()
     a.set_launch(ib["variant"], ib["threads"], ib["persistent"], ib["bin_beta_milli"] / 1000.0)
+    a.set_resident(ib["skin_steps_milli"] / 1000.0, ib["block_floes"])
+    assert a.info()["block_floes"] == ib["block_floes"]
     a.step(s["dt"], 120)
     b.step(s["dt"], 120)
     fa, fb = a.floes(), b.floes()
@@ -385,7 +387,7 @@ def test_set_floes_roundtrip(ms):
         assert np.array_equal(f[k], f2[k]), k
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_fp32_variants_match_oracle(orc, ms, variant):
     """Brute-force, block-binned, warp-binned, resident warp-binned and
     neighbour-list pair search: each within the FP32 tolerance of the oracle
@@ -457,7 +459,7 @@ def test_fp32_variants_agree_one_step(ms):
     find the same contacts, so moments agree to FP32 summation order."""
     s = I.powerlaw_32x32(nx=16)
     res = []
-    for variant in (0, 1, 2, 3, 4):
+    for variant in (0, 1, 2, 3, 4, 5):
         g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
         g.set_launch(variant, 128, 0, 1.0)
         g.step(s["dt"], 1)

@@ -198,3 +198,42 @@ def test_checkpoint_inside_an_interval(ms, tmp_path):
     assert c.info()["variant"] == 5
     c.step(dt, 98)
     _same(a, c)
+
+
+def test_diverged_state_is_reported(ms):
+    """Every floe given 1e12 m/s (finite, so the upload accepts it): the
+    skins and reaches grow beyond the cells (every floe becomes a large one,
+    lists overflow to the all-cell walk) and then turn inf and NaN; every
+    class finishes its run, the step reports MS_ERR_UNSTABLE and the context
+    stays usable."""
+    s = ragged_scenario([0, 20, 100, 300, 700, 1000], seed=31)
+    g = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    g.set_launch(5, 128, 0, 1.3)
+    g.step(s["dt"], 3)
+    f = g.floes()
+    f["u"][:] = 1.0e12
+    g.set_floes(f)
+    with pytest.raises(ms.MsError) as e:
+        g.step(s["dt"], 30)
+    assert e.value.code == -3, str(e.value)
+    assert np.all(np.isfinite(ms.Model(s["params"], s["floes"], ms.MS_FP32).moments()))
+
+
+@pytest.mark.parametrize("scen", ["square", "powerlaw"])
+def test_ocean_expansion_is_exact_to_fp32(orc, ms, scen):
+    """The resident kernels evaluate the current from each floe's first-order
+    expansion about a nearby centre, within a radius that keeps the dropped
+    term below FP32 rounding.  Over the first 50 steps (before contacts and
+    coupling amplify rounding) the moments stay as close to the oracle as the
+    kernels that sum the modes every step (variant 4) do: within 2e-5 in
+    every column, where a missing or wrong gradient term leaves 1e-4."""
+    s = I.square_4x4() if scen == "square" else I.powerlaw_32x32(nx=4)
+    p = s["params"]
+    o = orc.Model(p, s["floes"])
+    o.step(s["dt"], 50)
+    for v in (4, 5):
+        g = ms.Model(p, s["floes"], ms.MS_FP32)
+        g.set_launch(v, 128, 0, 1.3)
+        g.step(s["dt"], 50)
+        e = rel_errors(g.moments(), o.moments(), p, 1e-6)
+        assert e.max() <= 2e-5, (v, report(e))
