@@ -42,14 +42,16 @@
 // again at its floes' current positions with the modes' full sums.
 //
 // Moments (Algorithm 1): the window needs per step the cell's mass-weighted
-// mean velocity and its drag totals.  Masses change only at a gradual
-// update, so each floe sums its velocity and drag over the steps of one
-// mass (from one gradual-update step to the step before the next), and the
-// block reduces these sums once per such group of steps:
-// sum_s M u_s / M = sum_f m_f (sum_s u_f,s) / M.  A run that ends inside an
-// interval stores the floes' running sums and expansion centres (the carry)
-// and the next run picks them up, so a coarse interval gives the same result
-// bit for bit however it is split into runs.  The cell moments of the run's
+// mean velocity and its drag totals.  A gradual update scales the radii of
+// all floes of a cell by one factor (Eq. 3.5 with reading c11) and leaves
+// thicknesses alone, so each floe's share m_f / M of its cell's mass is the
+// same at every step of a coarse interval; then sum_s (sum_f m_f u_f,s) / M
+// = sum_f (m_f / M) (sum_s u_f,s).  Each floe sums its velocity and drag
+// over the interval and the block reduces these sums once, at the
+// interval's end.  A run that ends inside an interval stores the floes'
+// running sums and expansion centres (the carry) and the next run picks
+// them up, so a coarse interval gives the same result bit for bit however
+// it is split into runs.  The cell moments of the run's
 // last step (all 12 columns) are reduced once at the end.  Reductions are
 // segmented warp shuffles in a fixed tree, then a cell's warp partials in
 // order in FP64: deterministic.
@@ -156,6 +158,14 @@ __device__ void block_scan_bins(RunSm<K> &S, int nb)
         run += c;
     }
     __syncthreads();
+}
+
+// |(a, b)| from the hardware reciprocal square root (within a few ulp of
+// the correctly rounded norm; 0 for the zero vector)
+__device__ __forceinline__ float fast_norm(float a, float b)
+{
+    const float q = fmaf(a, a, b * b);
+    return q > 0.0f ? q * rsqrtf(q) : 0.0f;
 }
 
 // Has a floe at fixed point (xq, yq) left the region where the first-order
@@ -605,7 +615,6 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 __syncthreads();
             }
             const bool period_end = ph == 0;
-            if (win_on && period_end) flush();            // the steps of the previous masses
             if (need_build) build(cur, kk);
             __syncthreads();
             const float2 wa = S.wind[js & (WT - 1)];
@@ -686,9 +695,9 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 const float r2 = r[k] * r[k];
                 const float ao = P.drag_o * r2, aa = P.drag_a * r2, bo = ao * r2;
                 const float du_o = uo - u[k], dv_o = vo - v[k];
-                const float so = sqrtf(du_o * du_o + dv_o * dv_o);
+                const float so = fast_norm(du_o, dv_o);
                 const float au = wa.x - u[k], av = wa.y - v[k];
-                const float sa = sqrtf(au * au + av * av);
+                const float sa = fast_norm(au, av);
                 const float dwo = 0.5f * zeta - w[k];
                 const float Fdx = ao * du_o * so + aa * au * sa;
                 const float Fdy = ao * dv_o * so + aa * av * sa;
