@@ -44,11 +44,22 @@ def peaks():
     return HBM_FALLBACK_GBS, "fallback", {}
 
 
-def profile_traffic():
-    """DRAM bytes per fine step of the cell-step kernels from the committed
-    ncu summary, if the kernel sources have not changed since (else None)."""
+PROFILE_SOURCES = ("cell_run.cu", "common.cuh", "classes.cuh")   # the resident kernels and their launch classes
+
+
+def sources_sha16():
     import hashlib
-    path = os.path.join(ROOT, "profiles", "cell_step32_batched128x128.txt")
+    h = hashlib.sha256()
+    for f in PROFILE_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2303_07819_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic():
+    """DRAM bytes per coarse interval of the resident cell kernels (the three
+    class launches of one interval, live caches) from the committed ncu
+    summary, if the kernel sources have not changed since (else None)."""
+    path = os.path.join(ROOT, "profiles", "cell_run32_batched128x128.txt")
     if not os.path.exists(path):
         return None, None
     rec = {}
@@ -56,12 +67,9 @@ def profile_traffic():
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    h = hashlib.sha256()
-    for f in ("cell_step.cu", "common.cuh", "classes.cuh"):   # kernels and the launch's size classes
-        h.update(open(os.path.join(ROOT, "paper_2303_07819_gb300", "csrc", f), "rb").read())
-    if h.hexdigest()[:16] != rec.get("sources_sha256_16"):
+    if sources_sha16() != rec.get("sources_sha256_16"):
         return None, rec
-    return float(rec["dram_bytes_read_per_fine_step"]) + float(rec["dram_bytes_write_per_fine_step"]), rec
+    return float(rec["dram_bytes_per_interval"]), rec
 
 
 def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
@@ -142,6 +150,41 @@ def closure_eval(msdem, s, seeds=(101,), nx_train=128, spin=15, nint=20, K=10):
     out["seconds"] = time.perf_counter() - t0
     net.close()
     return out
+
+
+def ensemble_eval(msdem, warmup=2, steps=5):
+    """The ensemble workload (16 seeded realizations of 256 x 256 cells,
+    about 8M floes, one model): device-timed coarse intervals after warm-up,
+    an L2 flush before each."""
+    import torch
+    s = load_scenario("ensemble_16x256x256")
+    p, dt, N0 = s["params"], s["dt"], int(s["params"]["N0"])
+    st = torch.cuda.Stream()
+    m = msdem.Model(p, s["floes"], msdem.MS_FP32)
+    m.set_stream(st.cuda_stream)
+    for _ in range(warmup):
+        m.step(dt, N0)
+    m.sync()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for k in range(steps):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        m.step_async(dt, N0)
+        e1.record(st)
+        st.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    m.sync()
+    n, nc = m.n, m.ncell
+    info = m.info()
+    m.close()
+    tot = sum(ms) / 1e3
+    return {"workload": workload_config(s, "flushed before every timed interval (512 MB write)")["workload"],
+            "floes": int(n), "cells": int(nc), "intervals_timed": steps, "ms_per_interval": 1e3 * tot / steps,
+            "floe_steps_per_s": n * N0 * steps / tot, "cell_steps_per_s": nc * N0 * steps / tot,
+            "launch_variant": info["variant"]}
 
 
 def load_scenario(name: str):
@@ -408,7 +451,7 @@ def main():
     if args.workload != "batched_128x128":     # the committed capture is of this workload only
         traffic, prof = None, None
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
-    kern_ms_iso = model.time_kernel(0, dt, 20)  # cell kernel alone, warm L2, out of place
+    kern_ms_interval = model.time_kernel(2, dt, 10)   # cell kernels of one interval alone, out of place
     achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
     # the FP32 side of the roofline: the FMA rate this GPU reaches (probe),
     # the FMA-pipe activity ncu measured on the cell kernels, and the issue
@@ -418,8 +461,8 @@ def main():
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     issue_frac = None
     if prof is not None and traffic is not None and clk.get("sm_mhz"):
-        wi = float(prof["warp_instructions_per_fine_step"])
-        issue_frac = wi / (kern_ms_live / 1e3) / (nsm * 4 * clk["sm_mhz"] * 1e6)
+        wi = float(prof["warp_instructions_per_interval"])
+        issue_frac = wi / (tot_ms / args.steps / 1e3) / (nsm * 4 * clk["sm_mhz"] * 1e6)
 
     line = {
         "metric": "floe-steps/s", "value": value, "unit": "floe-steps/s", "n_gpus": world,
@@ -428,10 +471,14 @@ def main():
         "data": "synthetic", "cell_steps_per_s": cell_rate,
         "config": workload_config(s, "flushed before every timed step (512 MB write); state 64 MB"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "msd::k_cell_step32", "peak_source": peak_kind,
+                     "frac": achieved / hbm,
+                     "traffic": (traffic if traffic is not None and info["variant"] == 5 else None),
+                     "traffic_per": "coarse interval (one launch of each resident class)",
+                     "kernel": "msd::k_cell_run32_block<1|2|4> (resident for a coarse interval)",
+                     "peak_source": peak_kind,
                      "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
-                     "kernel_ms_live": kern_ms_live, "kernel_ms_isolated_warm_l2": kern_ms_iso,
+                     "algorithmic_bytes_per_interval": n_floes * BYTES_PER_FLOE_STEP * N0,
+                     "kernel_ms_live": kern_ms_live, "cell_kernels_ms_per_interval_alone": kern_ms_interval,
                      "fp32_peak_tflops_probe": fp32_peak,
                      "fp32_pipe_frac_ncu": (float(prof["fp32_pipe_frac"]) if traffic is not None else None),
                      "issue_frac": issue_frac},
@@ -469,6 +516,7 @@ def main():
                                           f"{tdt:.1f} s wall, FP64, OpenMP over cells"}
         if args.workload == "batched_128x128":
             line["closure"] = closure_eval(msdem, s)
+            line["ensemble"] = ensemble_eval(msdem)
     model.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
