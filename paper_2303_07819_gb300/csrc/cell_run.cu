@@ -37,9 +37,10 @@
 // near it and evaluates that every step (6 multiply-adds instead of a sum
 // of modes).  The neglected term stays below the FP32 rounding of the mode
 // sum while the floe is within sqrt(P.ocean_d2) of the centre (the bound is
-// derived from the modes' wave numbers on the host); when a floe of a warp
-// goes farther, or wraps across its cell's edge, the whole warp expands
-// again at its floes' current positions with the modes' full sums.
+// derived from the modes' wave numbers on the host); when a floe of a cell
+// goes farther, or wraps across its cell's edge, every floe of that cell
+// expands again at its current position with the modes' full sums at the
+// next step (a decision of the cell alone, whichever cells share its block).
 //
 // Moments (Algorithm 1): the window needs per step the cell's mass-weighted
 // mean velocity and its drag totals.  A gradual update scales the radii of

@@ -28,3 +28,13 @@ def rel_errors(got: np.ndarray, ref: np.ndarray, params: dict, eps: float) -> np
 
 def report(errs: np.ndarray) -> str:
     return ", ".join(f"{n}={e:.2e}" for n, e in zip(FIELDS, errs))
+
+
+def cell_errors(got: np.ndarray, ref: np.ndarray, params: dict, eps: float) -> np.ndarray:
+    """Per moment column, the largest error of any single cell, over the
+    column's rms across cells (floored as in rel_errors): a single cell that
+    went wrong shows as an O(1) value however many cells agree."""
+    n = ref.shape[0]
+    rms = np.linalg.norm(ref, axis=0) / np.sqrt(max(n, 1))
+    den = np.maximum(rms, field_floors(ref, params, eps) / np.sqrt(max(n, 1)))
+    return np.max(np.abs(got - ref), axis=0) / den

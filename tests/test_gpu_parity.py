@@ -199,35 +199,6 @@ def test_largest_cell_fp32(orc, ms):
     assert e.max() <= 1e-5, report(e)
 
 
-def test_full_size_batched_sampled_cells(orc, ms):
-    """The 128 x 128 batched workload at full size (~2.0M floes, 16,384 cells)
-    on the GPU in the launch the bench times (variant 5: every cell resident
-    for the run, candidate lists built at the run's start), 12 steps; the oracle
-    recomputes a sample of 48 cells (the largest and random ones) from those
-    cells' floes alone, since the cells' DEMs are independent until the first
-    coarse step."""
-    s = I.batched_128x128()
-    p = s["params"]
-    g = ms.Model(p, s["floes"], ms.MS_FP32)
-    assert g.info()["variant"] == 5
-    g.step(s["dt"], 12)
-    mg = g.moments()
-    cell = s["meta"]["cell"]
-    counts = np.bincount(cell, minlength=p["nx"] * p["ny"])
-    rng = np.random.default_rng(0)
-    pick = np.unique(np.concatenate([np.argsort(-counts)[:8], rng.choice(len(counts), 40, replace=False)]))
-    sel = np.isin(cell, pick)
-    sub = {k: v[sel] for k, v in s["floes"].items()}
-    o = orc.Model(p, sub)
-    o.step(s["dt"], 12)
-    mo = o.moments()[pick]
-    e = rel_errors(mg[pick], mo, p, 1e-6)
-    assert e.max() <= TOL32, report(e)
-    # totals that hold at any size: floe counts per cell and total mass
-    assert np.array_equal(mg[:, 0], counts.astype(np.float64))
-    g.close()
-
-
 def test_graph_replay_equals_single_steps(ms):
     s = I.square_4x4()
     a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
