@@ -298,6 +298,8 @@ struct orc_model {
     int have_q, have_tgt;
     int64_t steps;
     double dt;
+    int hold_coarse;               /* stop before each coarse step (sharded runs) */
+    int coarse_pending;
 };
 
 /* copy of the parameters with both mode tables in one owned buffer */
@@ -565,6 +567,7 @@ int orc_model_step(orc_model *m, double dt, int64_t nsteps)
     if (m->dt == 0.0) m->dt = dt;
     else if (dt != m->dt) return -1;      /* the schedule needs a fixed dt */
     if (p->couple && (p->N0 <= 0 || p->n_t <= 0 || p->N0 % p->n_t != 0)) return -1;
+    if (m->coarse_pending) return -1;      /* a held coarse step has to run first */
     for (int64_t k = 0; k < nsteps; k++) {
         int64_t s = m->steps + 1;          /* index of this step, 1-based */
         double t = (double)m->steps * dt;  /* forces at t_n */
@@ -577,8 +580,52 @@ int orc_model_step(orc_model *m, double dt, int64_t nsteps)
 #endif
         for (c = 0; c < nc; c++) model_cell_step(m, c, dt, t, ramp, frac);
         m->steps = s;
-        if (p->couple && (s % p->N0) == 0) model_coarse_step(m, dt);
+        if (p->couple && (s % p->N0) == 0) {
+            if (m->hold_coarse) {
+                m->coarse_pending = 1;
+                return 0;
+            }
+            model_coarse_step(m, dt);
+        }
     }
+    return 0;
+}
+
+/* Sharded runs (a rank advances the cells it owns and the ranks exchange
+ * what the coarse step reads): with hold set, orc_model_step returns right
+ * after the last fine step of a coarse interval and leaves the coarse step
+ * pending.  The coarse step reads, per cell, the moment columns 1-5 (sum m,
+ * sum m u, sum m v, sum I, sum I omega: its initial state and the targets)
+ * and the window sums: ORC_NCI values, exported and replaced here. */
+void orc_model_set_hold(orc_model *m, int32_t hold) { m->hold_coarse = hold ? 1 : 0; }
+
+void orc_model_coarse_inputs(const orc_model *m, double *out)
+{
+    int32_t nc = m->ncell;
+    for (int32_t c = 0; c < nc; c++) {
+        for (int k = 0; k < 5; k++) out[(size_t)c * ORC_NCI + k] = m->mom[(size_t)c * ORC_NMOM + 1 + k];
+        for (int k = 0; k < ORC_NWIN; k++) out[(size_t)c * ORC_NCI + 5 + k] = m->win[(size_t)k * nc + c];
+    }
+}
+
+void orc_model_set_coarse_inputs(orc_model *m, int32_t ncells, const int32_t *cells, const double *vals)
+{
+    int32_t nc = m->ncell;
+    for (int32_t i = 0; i < ncells; i++) {
+        int32_t c = cells[i];
+        if (c < 0 || c >= nc) continue;
+        for (int k = 0; k < 5; k++) m->mom[(size_t)c * ORC_NMOM + 1 + k] = vals[(size_t)i * ORC_NCI + k];
+        for (int k = 0; k < ORC_NWIN; k++) m->win[(size_t)k * nc + c] = vals[(size_t)i * ORC_NCI + 5 + k];
+    }
+}
+
+int32_t orc_model_pending(const orc_model *m) { return m->coarse_pending; }
+
+int orc_model_coarse(orc_model *m)
+{
+    if (!m->coarse_pending) return -1;
+    model_coarse_step(m, m->dt);
+    m->coarse_pending = 0;
     return 0;
 }
 

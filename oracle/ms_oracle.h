@@ -18,6 +18,7 @@
 
 #define ORC_NMOM 12   /* moment columns, see orc_model_moments() */
 #define ORC_NWIN 5    /* window-sum columns: sum_t ubar, vbar, Fdx, Fdy, Td */
+#define ORC_NCI 10    /* coarse-step inputs per cell: moment columns 1-5, window sums */
 
 typedef struct orc_params {
     /* domain and coarse grid (one periodic DEM per coarse cell) */
@@ -108,6 +109,16 @@ orc_model *orc_model_create(const orc_params *p, int64_t n,
                             const double *r, const double *h);
 void orc_model_free(orc_model *m);
 int  orc_model_step(orc_model *m, double dt, int64_t nsteps);
+/* sharded runs: hold = 1 makes orc_model_step stop right after the last fine
+ * step of a coarse interval (the coarse step pending, further steps refused
+ * until orc_model_coarse); the coarse inputs of every cell, [ncell][ORC_NCI]
+ * = (sum m, sum m u, sum m v, sum I, sum I omega, the 5 window sums), can
+ * be read and those of listed cells replaced before it runs */
+void orc_model_set_hold(orc_model *m, int32_t hold);
+int32_t orc_model_pending(const orc_model *m);
+void orc_model_coarse_inputs(const orc_model *m, double *out);
+void orc_model_set_coarse_inputs(orc_model *m, int32_t ncells, const int32_t *cells, const double *vals);
+int  orc_model_coarse(orc_model *m);
 /* moments of the current state: [ncell][ORC_NMOM] */
 void orc_model_moments(const orc_model *m, double *out);
 /* floe state in the caller's original order, global coordinates, 8 x n:

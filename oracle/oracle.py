@@ -65,6 +65,7 @@ def lib():
         L = C.CDLL(LIB)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int64)
+        ip32 = C.POINTER(C.c_int32)
         P = C.POINTER(Params)
         L.orc_forcing.argtypes = [P, C.c_double, C.c_double, C.c_double, dp]
         L.orc_pair.argtypes = [P, C.c_double, C.c_double] + [C.c_double] * 14 + [dp]
@@ -86,6 +87,16 @@ def lib():
         L.orc_model_floes.argtypes = [C.c_void_p, dp]
         L.orc_model_coupling.argtypes = [C.c_void_p, dp, dp, dp, ip]
         L.orc_model_layout.argtypes = [C.c_void_p, ip, ip]
+        L.orc_model_set_hold.argtypes = [C.c_void_p, C.c_int32]
+        L.orc_model_set_hold.restype = None
+        L.orc_model_pending.argtypes = [C.c_void_p]
+        L.orc_model_pending.restype = C.c_int32
+        L.orc_model_coarse_inputs.argtypes = [C.c_void_p, dp]
+        L.orc_model_coarse_inputs.restype = None
+        L.orc_model_set_coarse_inputs.argtypes = [C.c_void_p, C.c_int32, ip32, dp]
+        L.orc_model_set_coarse_inputs.restype = None
+        L.orc_model_coarse.argtypes = [C.c_void_p]
+        L.orc_model_coarse.restype = C.c_int
         L.orc_truth_create.argtypes = [P, C.c_int64] + [dp] * 8
         L.orc_truth_create.restype = C.c_void_p
         L.orc_truth_free.argtypes = [C.c_void_p]
@@ -256,6 +267,31 @@ class Model(_Base):
         orig = np.zeros(max(self.n, 1), dtype=np.int64)
         lib().orc_model_layout(self._h, _ip(off), _ip(orig))
         return off, orig[: self.n]
+
+    # sharded runs: stop before each coarse step, exchange its inputs
+    NCI = 10
+
+    def set_hold(self, hold: bool) -> None:
+        lib().orc_model_set_hold(self._h, 1 if hold else 0)
+
+    def coarse_pending(self) -> bool:
+        return bool(lib().orc_model_pending(self._h))
+
+    def coarse_inputs(self) -> np.ndarray:
+        """[ncell][10]: moment columns 1-5 and the window sums of every cell."""
+        out = np.zeros((self.ncell, self.NCI))
+        lib().orc_model_coarse_inputs(self._h, _dp(out))
+        return out
+
+    def set_coarse_inputs(self, cells, vals) -> None:
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64).reshape(cells.shape[0], self.NCI)
+        lib().orc_model_set_coarse_inputs(self._h, int(cells.shape[0]), cells.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          _dp(vals))
+
+    def coarse(self) -> None:
+        if lib().orc_model_coarse(self._h) != 0:
+            raise ValueError("no coarse step is pending")
 
 
 class Truth(_Base):
