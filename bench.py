@@ -400,9 +400,17 @@ def main():
     dt = s["dt"]
     N0 = int(p["N0"])
     stream = torch.cuda.Stream()
-    model = msdem.Model(p, s["floes"], msdem.MS_FP32)
+    sharded = None
+    if world > 1:
+        # one grid split into tiles of cells, one per rank; the coarse
+        # inputs are all-gathered (NCCL) once per coarse interval
+        from paper_2303_07819_gb300 import shard
+        sharded = shard.ShardedModel(p, s["floes"], world, rank, precision=msdem.MS_FP32)
+        model = sharded.model
+    else:
+        model = msdem.Model(p, s["floes"], msdem.MS_FP32)
     model.set_stream(stream.cuda_stream)
-    n_floes, ncell = model.n, model.ncell
+    n_floes, ncell = int(s["floes"]["x"].shape[0]), model.ncell   # the whole grid's
     if args.profile:
         if args.variant >= 0:
             model.set_launch(args.variant, 128, 0)
@@ -443,8 +451,9 @@ def main():
     model.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     fine_steps = args.steps * N0
-    value, tot_ms = job_rate(n_floes * fine_steps, float(sum(step_ms)), world, dist, "cuda")
-    cell_rate = world * ncell * fine_steps / (tot_ms / 1e3)
+    # the ranks share one grid: all its floes over the slowest rank's time
+    value, tot_ms = job_rate(n_floes * fine_steps, float(sum(step_ms)), 1, dist, "cuda")
+    cell_rate = ncell * fine_steps / (tot_ms / 1e3)
 
     hbm, peak_kind, _ = peaks()
     traffic, prof = profile_traffic()
@@ -452,7 +461,8 @@ def main():
         traffic, prof = None, None
     kern_ms_live = tot_ms / fine_steps          # per fine step, incl. the coarse step's share
     kern_ms_interval = model.time_kernel(2, dt, 10)   # cell kernels of one interval alone, out of place
-    achieved = n_floes * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
+    # per GPU: this rank's floes (all of them at N = 1) over the step time
+    achieved = model.n * BYTES_PER_FLOE_STEP / (kern_ms_live / 1e3) / 1e9
     # the FP32 side of the roofline: the FMA rate this GPU reaches (probe),
     # the FMA-pipe activity ncu measured on the cell kernels, and the issue
     # rate the live step implies for ncu's instruction count (of the peak
@@ -467,7 +477,7 @@ def main():
     line = {
         "metric": "floe-steps/s", "value": value, "unit": "floe-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "cell_steps_per_s": cell_rate,
         "config": workload_config(s, "flushed before every timed step (512 MB write); state 64 MB"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -477,25 +487,26 @@ def main():
                      "kernel": "msd::k_cell_run32_block<1|2|4> (resident for a coarse interval)",
                      "peak_source": peak_kind,
                      "bytes_per_floe_step": BYTES_PER_FLOE_STEP,
-                     "algorithmic_bytes_per_interval": n_floes * BYTES_PER_FLOE_STEP * N0,
+                     "algorithmic_bytes_per_interval": model.n * BYTES_PER_FLOE_STEP * N0,
                      "kernel_ms_live": kern_ms_live, "cell_kernels_ms_per_interval_alone": kern_ms_interval,
                      "fp32_peak_tflops_probe": fp32_peak,
                      "fp32_pipe_frac_ncu": (float(prof["fp32_pipe_frac"]) if traffic is not None else None),
                      "issue_frac": issue_frac},
         "clocks": clk,
-        "gpu_launches": args.steps * (info["launches_per_interval"] + info["launches_per_coarse"]),
+        "gpu_launches": args.steps * (info["launches_per_interval"] + info["launches_per_coarse"]
+                                      + (2 if sharded else 0)),   # + pack and scatter of the exchange
         "launch": {"variant": info["variant"], "threads": info["threads"], "persistent": info["persistent"]},
         "wall_s": t_wall,
     }
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras:
         # end to end through the public API with host buffers: upload the
-        # state, one coarse interval, read the moments back.  Each step's
-        # input is the state the model holds (fetched before the timer
-        # starts), so the run continues as the device-resident one does; an
-        # older state uploaded again while the coarse solution moves on is
-        # not a state of the method, and drives it unstable within a few
-        # intervals.
+        # state, one coarse interval, read the moments back (every rank, as
+        # the interval's exchange needs them all).  Each step's input is the
+        # state the model holds (fetched before the timer starts), so the
+        # run continues as the device-resident one does; an older state
+        # uploaded again while the coarse solution moves on is not a state
+        # of the method, and drives it unstable within a few intervals.
         ke = max(1, min(args.steps, 5))
         model.set_floes(model.floes())
         model.step(dt, N0)
@@ -507,8 +518,14 @@ def main():
             model.step_async(dt, N0)
             mom = model.moments()
             te += time.perf_counter() - t0
-        line["e2e"] = {"value": world * n_floes * N0 * ke / te, "unit": "floe-steps/s",
-                       "h2d_bytes_per_step": int(64 * n_floes), "d2h_bytes_per_step": int(mom.nbytes)}
+        _, te_ms = job_rate(1, te * 1e3, 1, dist, "cuda")
+        line["e2e"] = {"value": n_floes * N0 * ke / (te_ms / 1e3), "unit": "floe-steps/s",
+                       "h2d_bytes_per_step": int(64 * n_floes), "d2h_bytes_per_step": int(world * mom.nbytes)}
+    if sharded is not None:
+        line["config"]["parallelism"] = (f"{world} tiles of cells (recursive bisection balanced by floe "
+                                         f"pairs), coarse inputs all-gathered once per coarse interval (NCCL)")
+        line["shard_floes"] = int(model.n)
+    if not args.no_extras and rank == 0:
         ncells, steps = calibrated_oracle(s, 15.0)
         rate, n, tdt, cores = oracle_sample_rate(s, ncells, steps)
         line["cpu_baseline"] = {"value": rate, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",

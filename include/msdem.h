@@ -246,15 +246,17 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
 /* Tunables of launch variant 5 (the default for FP32): each floe's skin --
  * how far it may move before its cell group searches for contact candidates
  * again -- is its speed (plus what the coming gradual updates add) times
- * skin_steps fine steps (1 .. 1000); cells of at most block_floes floes
- * (32 .. 256) share a block of 256 threads, a floe per thread, up to that
- * many floes in all.  Results do not depend on skin_steps; block_floes
- * changes which cells share a block, and with it the order of the per-cell
- * FP32 sums (moments differ by rounding only).  ms_autotune chooses both;
+ * skin_steps fine steps (1 .. 1000); cells of at most 256 floes share a
+ * block of 256 threads, a floe per thread, up to block_floes (32 .. 256)
+ * floes in all; a larger cell has a block of its own.  Floes do not depend
+ * on skin_steps, block_floes or the other cells of the model;
+ * block_floes changes which cells share a block, and with it the order of
+ * the per-cell FP32 sums (moments differ by rounding only, and through the
+ * coarse step the floes of later intervals).  ms_autotune chooses both;
  * ms_info entries 16 and 17 report them.  MS_ERR_ARG outside the ranges. */
 int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes);
 
-/* Model facts, host out[18] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
+/* Model facts, host out[21] (int64): 0 n, 1 ncell, 2 largest cell, 3 precision,
  * 4 kernel variant, 5 threads per block, 6 bin width (per mille of the mean
  * floe spacing), 7 cell-kernel launches per coarse interval (msDEM, whole
  * intervals, no coarse step),
@@ -262,8 +264,63 @@ int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes);
  * 11 truth steps done, 12 graph replays so far, 13 contacts seen deeper than
  * half the smaller radius, 14 persistent launch, 15 LF substeps of the last
  * coarse step, 16 skin horizon of variant 5 in thousandths of a fine step,
- * 17 floes per block of small cells of variant 5. */
+ * 17 floes per block of small cells of variant 5, 18 ranks of a sharded
+ * grid (0: not sharded), 19 this model's rank, 20 cells it owns. */
 int ms_info(ms_model *m, int64_t *out);
+
+/* ---- sharded grids (Sec. 3.1's processor grid of cell blocks, one rank per
+ * GPU).  Between coarse steps a cell's DEM touches only its own floes
+ * (Algorithm 1), so a rank's model holds the floes of its own cells and the
+ * ranks meet once per coarse interval: each packs the coarse inputs of its
+ * cells (MS_SHARD_NCOL doubles per cell: moment columns 1-5, then the five
+ * window sums, the only DEM data the coarse step reads), every rank gathers
+ * all ranks' rows and takes the whole grid's coarse step itself.  That step
+ * is the same computation on the same inputs on every rank, so in FP64 the
+ * floes and moments of a rank's cells equal those of the unsharded model bit
+ * for bit.  In FP32 (launch variant 5) the floes are equal bit for bit until
+ * the first coarse step; the moments are sums whose order depends on which
+ * cells share a block (ms_set_resident), so from then on the sharded model
+ * differs from the unsharded one as a repacked model does, by rounding. */
+#define MS_SHARD_NCOL 10
+
+/* The cell (j * nx + i, rows j of every realization stacked in y) that
+ * ms_init assigns each floe to: each coordinate wrapped into the periodic
+ * domain, then the half-open cell holding it.  cell_out: host, floes->n
+ * int32.  MS_ERR_ARG for a bad grid, NULL arrays or a non-finite position. */
+int ms_floe_cells(const ms_grid *grid, const ms_floes *floes, int32_t *cell_out);
+
+/* Exchange of a sharded model's coarse inputs, called by ms_step and
+ * ms_step_async on the calling thread at each coarse step, after the rank's
+ * rows have been packed into its send buffer on `stream` (the model's
+ * cudaStream_t).  It must leave every rank's send buffer in recv, rank r's
+ * rows at r * max_cells .. (see ms_shard_buffers), ordered before later work
+ * on `stream`: an all-gather enqueued on that stream (NCCL), or a
+ * synchronous copy after synchronizing it.  Returns 0, non-zero on failure. */
+typedef int (*ms_exchange_fn)(void *ctx, void *stream);
+
+/* Make m rank `rank` of `nranks` ranks: rank r owns the cells
+ * cells[rank_off[r] .. rank_off[r + 1]) (host arrays, caller-owned, copied:
+ * rank_off [nranks + 1] from 0, non-decreasing, up to the number of cells;
+ * cells a permutation of all cells).  m must hold floes of its own cells only
+ * (build it from the floes that ms_floe_cells places there; its cells may
+ * be empty).  fn(ctx, stream) is the exchange (ms_exchange_fn), called once
+ * per coarse step of a coupled model.  After a failed exchange the model
+ * stands at the end of an interval without its coarse step and ms_step
+ * returns MS_ERR_STATE from then on.  ms_moments of a sharded model: its own
+ * cells' rows; other cells hold zeros but in columns 1-5, which hold the
+ * last exchange's values.  A sharded model runs no closure
+ * (ms_closure_attach and ms_closure_collect return MS_ERR_STATE).
+ * MS_ERR_ARG: bad layout, fn NULL, a floe in a cell of another rank;
+ * MS_ERR_STATE: already sharded, or a closure attached. */
+int ms_set_shard(ms_model *m, int32_t nranks, int32_t rank, const int32_t *rank_off, const int32_t *cells,
+                 ms_exchange_fn fn, void *ctx);
+
+/* The exchange buffers of a sharded model, device memory owned by the model
+ * (valid until ms_free): send [max_cells][MS_SHARD_NCOL] FP64, rows past the
+ * rank's own cells zero; recv [nranks * max_cells][MS_SHARD_NCOL] FP64;
+ * max_cells the largest number of cells a rank owns.  Outputs may be NULL.
+ * MS_ERR_STATE if m is not sharded. */
+int ms_shard_buffers(ms_model *m, double **send, double **recv, int32_t *max_cells);
 
 /* Per-cell moments of a floe set held in the caller's device memory, computed
  * without allocating any memory.  The paper has no counterpart: this entry

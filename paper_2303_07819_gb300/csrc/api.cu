@@ -16,6 +16,7 @@
 
 #include "classes.cuh"
 #include "common.cuh"
+#include "shard.cuh"
 #include "upload.cuh"
 #include "../../include/msdem.h"
 
@@ -114,6 +115,17 @@ struct ms_model {
     double *d_mom0 = nullptr;
     unsigned long long *d_ccount = nullptr;
     long long hybrid_intervals = 0;
+    // a grid split into tiles: this model holds the floes of cells
+    // shard_cells[0 .. shard_nown) (device copy: the cells of every rank, in
+    // rank order, and their rows of the gathered buffer)
+    int shard_nranks = 0, shard_rank = 0, shard_nown = 0, shard_maxc = 0, shard_first = 0;
+    int *d_shard_cells = nullptr;
+    long long *d_shard_rows = nullptr;
+    double *d_send = nullptr, *d_recv = nullptr;
+    ms_exchange_fn exch = nullptr;
+    void *exch_ctx = nullptr;
+    bool exch_failed = false;
+    cudaGraphExec_t gexec_end = nullptr;   // sharded: the interval's coarse step after the exchange
     // host staging (pinned)
     void *h_stage = nullptr;
     size_t h_stage_bytes = 0;
@@ -196,6 +208,29 @@ static int cell_index(double X, double L, double d, int n)
     if (i < 0) i = 0;
     if (i > n - 1) i = n - 1;
     return i;
+}
+
+// the model's geometry of a grid (an ensemble stacks its realizations in y)
+static Geom grid_geom(const ms_grid *grid)
+{
+    const int nens = grid->nens > 1 ? grid->nens : 1;
+    Geom g{};
+    g.nx = grid->nx;
+    g.ny = grid->ny * nens;
+    g.nyr = grid->ny;
+    g.nens = nens;
+    g.Lx = grid->Lx;
+    g.Ly = grid->Ly * nens;
+    g.Lcx = grid->Lx / grid->nx;
+    g.Lcy = grid->Ly / grid->ny;
+    g.walls = grid->walls;
+    return g;
+}
+
+// the cell a floe at (x, y) belongs to (periodic wrap of the position first)
+static int floe_cell(const Geom &g, double x, double y)
+{
+    return cell_index(y, g.Ly, g.Lcy, g.ny) * g.nx + cell_index(x, g.Lx, g.Lcx, g.nx);
 }
 
 static uint32_t to_fix(double frac)
@@ -570,30 +605,79 @@ static cudaError_t launch_interval_start(ms_model *m)
 static void drop_graph(ms_model *m)
 {
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->gexec_end) cudaGraphExecDestroy(m->gexec_end);
     m->gexec = nullptr;
+    m->gexec_end = nullptr;
 }
 
-static cudaError_t build_graph(ms_model *m)
+// a sharded model exchanges the coarse inputs before each coarse step
+static bool sharded_coarse(const ms_model *m) { return m->shard_nranks > 0 && m->fc.couple; }
+
+// pack this rank's coarse inputs (end of an interval, before the exchange)
+static cudaError_t launch_shard_send(ms_model *m)
+{
+    return launch_shard_pack(m->d_mom, m->d_win, m->ncell, m->d_shard_cells + m->shard_first, m->shard_nown,
+                             m->d_send, m->stream);
+}
+
+// every rank's coarse inputs into the moments and window sums (after it)
+static cudaError_t launch_shard_recv(ms_model *m)
+{
+    return launch_shard_scatter(m->d_mom, m->d_win, m->ncell, m->d_shard_cells, m->d_shard_rows, m->d_recv,
+                                m->stream);
+}
+
+template <class F>
+static cudaError_t capture(ms_model *m, cudaGraphExec_t *out, F &&body)
 {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    cudaError_t le = launch_interval_start(m);
-    // FP32 size classes: one fork per interval, so that a class's next step
-    // does not wait for the other classes' current one
-    if (le == cudaSuccess && interval_cells(m)) le = launch_interval_cells(m, false);
-    else
-        for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
-    if (le == cudaSuccess) le = launch_interval_end(m);
+    const cudaError_t le = body();
     e = cudaStreamEndCapture(m->stream, &graph);
     if (le != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         return le;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    e = cudaGraphInstantiate(out, graph, 0);
     cudaGraphDestroy(graph);
     return e;
+}
+
+// One coarse interval as a graph; a sharded model's splits at the exchange
+// (gexec ends with the pack of its send rows, gexec_end is the scatter of
+// the gathered rows and the coarse step).
+static cudaError_t build_graph(ms_model *m)
+{
+    const bool split = sharded_coarse(m);
+    cudaError_t e = capture(m, &m->gexec, [&]() {
+        cudaError_t le = launch_interval_start(m);
+        // FP32 size classes: one fork per interval, so that a class's next
+        // step does not wait for the other classes' current one
+        if (le == cudaSuccess && interval_cells(m)) le = launch_interval_cells(m, false);
+        else
+            for (int i = 0; i < m->interval && le == cudaSuccess; i++) le = launch_step(m, i, false);
+        if (le == cudaSuccess) le = split ? launch_shard_send(m) : launch_interval_end(m);
+        return le;
+    });
+    if (e == cudaSuccess && split) e = capture(m, &m->gexec_end, [&]() {
+        cudaError_t le = launch_shard_recv(m);
+        return le == cudaSuccess ? launch_interval_end(m) : le;
+    });
+    if (e != cudaSuccess) drop_graph(m);
+    return e;
+}
+
+// the caller's exchange between the pack and the scatter
+static int shard_exchange(ms_model *m)
+{
+    Trace tr("msdem.shard exchange");
+    if (m->exch(m->exch_ctx, (void *)m->stream) != 0) {
+        m->exch_failed = true;
+        return fail(MS_ERR_ARG, "the exchange of the coarse inputs failed at step %lld", m->steps);
+    }
+    return MS_OK;
 }
 
 static int read_errors(ms_model *m)
@@ -768,7 +852,11 @@ static int build_groups(ms_model *m, CellLaunch &cl)
         g.cells.push_back(cc);
         g.nf += n;
         g.room -= n;
-        if ((int)g.cells.size() < RUN_GCMAX) by_room[g.room].push_back(gi);
+        // only groups of one floe per thread take further cells: a cell's
+        // floes then run the code of its own size class wherever it is
+        // packed (the 2- and 4-floe classes compile to other instruction
+        // sequences, whose rounding may differ)
+        if (g.K == 1 && (int)g.cells.size() < RUN_GCMAX) by_room[g.room].push_back(gi);
     };
     int first_item = -1, end_item = -1;
     for (int s = 0; s < cl.nseg; s++)
@@ -1261,15 +1349,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->fc.vmodes = m->vmodes.data();
     m->n = floes->n;
     m->ncell = grid->nx * grid->ny * nens;
-    m->g.nx = grid->nx;
-    m->g.ny = grid->ny * nens;
-    m->g.nyr = grid->ny;
-    m->g.nens = nens;
-    m->g.Lx = grid->Lx;
-    m->g.Ly = grid->Ly * nens;
-    m->g.Lcx = grid->Lx / grid->nx;
-    m->g.Lcy = grid->Ly / grid->ny;
-    m->g.walls = grid->walls;
+    m->g = grid_geom(grid);
     m->interval = f.couple ? f.N0 : 100;
     fill_phys(m);
 
@@ -1279,8 +1359,7 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->h_cell_of_orig.resize(n);
     m->h_off.assign(m->ncell + 1, 0);
     for (long long l = 0; l < n; l++) {
-        const int c = cell_index(floes->y[l], m->g.Ly, m->g.Lcy, m->g.ny) * m->g.nx +
-                      cell_index(floes->x[l], m->g.Lx, m->g.Lcx, m->g.nx);
+        const int c = floe_cell(m->g, floes->x[l], floes->y[l]);
         m->h_cell_of_orig[l] = c;
         m->h_off[c + 1]++;
         rmax = std::max(rmax, floes->r[l]);
@@ -1452,7 +1531,9 @@ static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
     if (nsteps < 0) return fail(MS_ERR_ARG, "nsteps < 0");
     if (m->dt == 0.0) m->dt = dt;
     else if (dt != m->dt) return fail(MS_ERR_ARG, "dt = %g differs from the model's dt = %g", dt, m->dt);
+    if (m->exch_failed) return fail(MS_ERR_STATE, "an exchange of the coarse inputs failed; the model cannot step");
     const int N = m->interval;
+    const bool split = sharded_coarse(m);
     while (nsteps > 0) {
         const long long i_local = m->steps % N;
         if (i_local == 0 && nsteps >= N && !m->graph_failed) {
@@ -1469,9 +1550,14 @@ static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
                 Trace ti("msdem.interval (graph)");
                 CK(cudaGraphLaunch(m->gexec, m->stream));
             }
-            m->replays++;
             m->steps += N;
             nsteps -= N;
+            if (split) {
+                int rc = shard_exchange(m);
+                if (rc) return rc;
+                CK(cudaGraphLaunch(m->gexec_end, m->stream));
+            }
+            m->replays++;
             continue;
         }
         if (i_local == 0) {
@@ -1486,6 +1572,12 @@ static int step_enqueue(ms_model *m, double dt, int64_t nsteps)
         nsteps--;
         if (m->steps % N == 0) {
             Trace te("msdem.interval end (coarse step)");
+            if (split) {
+                CK(launch_shard_send(m));
+                int rc = shard_exchange(m);
+                if (rc) return rc;
+                CK(launch_shard_recv(m));
+            }
             CK(launch_interval_end(m));
         }
     }
@@ -1847,6 +1939,9 @@ int ms_info(ms_model *m, int64_t *out)
     out[15] = c.N1;
     out[16] = (int64_t)std::lround(m->cl.run_skin * 1000.0f);
     out[17] = m->cl.run_cap1;
+    out[18] = m->shard_nranks;
+    out[19] = m->shard_rank;
+    out[20] = m->shard_nranks ? m->shard_nown : m->ncell;
     return MS_OK;
 }
 
@@ -1861,6 +1956,82 @@ int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes)
     c.run_cap1 = block_floes;
     CK(cudaStreamSynchronize(m->stream));
     return configure_launch(m, c);
+}
+
+int ms_floe_cells(const ms_grid *grid, const ms_floes *floes, int32_t *cell_out)
+{
+    if (!grid || !cell_out) return fail(MS_ERR_ARG, "NULL argument");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nens < 0 || grid->nens > 65536 || !(grid->Lx > 0.0) ||
+        !(grid->Ly > 0.0) || !isfin(grid->Lx) || !isfin(grid->Ly))
+        return fail(MS_ERR_ARG, "bad grid");
+    int rc = check_floe_args(floes, -1);
+    if (rc) return rc;
+    const Geom g = grid_geom(grid);
+    const long long l = host_first(floes->n, [&](long long k) { return !isfin(floes->x[k]) || !isfin(floes->y[k]); });
+    if (l < floes->n) return fail(MS_ERR_ARG, "floe %lld has a non-finite position", l);
+    host_parallel(floes->n, [&](long long b, long long e) {
+        for (long long k = b; k < e; k++) cell_out[k] = floe_cell(g, floes->x[k], floes->y[k]);
+    });
+    return MS_OK;
+}
+
+int ms_set_shard(ms_model *m, int32_t nranks, int32_t rank, const int32_t *rank_off, const int32_t *cells,
+                 ms_exchange_fn fn, void *ctx)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (m->shard_nranks) return fail(MS_ERR_STATE, "the model is already sharded");
+    if (m->hybrid_mode >= 0) return fail(MS_ERR_STATE, "a model with a closure attached cannot be sharded");
+    if (!rank_off || !cells || !fn) return fail(MS_ERR_ARG, "NULL argument");
+    if (nranks < 1 || rank < 0 || rank >= nranks) return fail(MS_ERR_ARG, "need 0 <= rank < nranks");
+    const int nc = m->ncell;
+    if (rank_off[0] != 0 || rank_off[nranks] != nc) return fail(MS_ERR_ARG, "rank_off must run from 0 to %d", nc);
+    int maxc = 0;
+    for (int r = 0; r < nranks; r++) {
+        if (rank_off[r + 1] < rank_off[r]) return fail(MS_ERR_ARG, "rank_off decreases at rank %d", r);
+        maxc = std::max(maxc, rank_off[r + 1] - rank_off[r]);
+    }
+    std::vector<int> seen(nc, -1);
+    std::vector<long long> rows(nc);
+    for (int r = 0; r < nranks; r++)
+        for (int t = rank_off[r]; t < rank_off[r + 1]; t++) {
+            const int c = cells[t];
+            if (c < 0 || c >= nc || seen[c] >= 0) return fail(MS_ERR_ARG, "cells is not a permutation of the cells");
+            seen[c] = r;
+            rows[t] = (long long)r * maxc + (t - rank_off[r]);
+        }
+    for (int c = 0; c < nc; c++)
+        if (seen[c] != rank && m->h_off[c + 1] > m->h_off[c])
+            return fail(MS_ERR_ARG, "cell %d holds floes but belongs to rank %d", c, seen[c]);
+    CK(cudaStreamSynchronize(m->stream));
+    const size_t ncol = SHARD_NCOL;
+    if (dalloc(m, &m->d_shard_cells, nc) != cudaSuccess || dalloc(m, &m->d_shard_rows, nc) != cudaSuccess ||
+        dalloc(m, &m->d_send, (size_t)std::max(maxc, 1) * ncol) != cudaSuccess ||
+        dalloc(m, &m->d_recv, (size_t)nranks * std::max(maxc, 1) * ncol) != cudaSuccess)
+        return fail(MS_ERR_CUDA, "cudaMalloc of the exchange buffers failed");
+    CK(cudaMemcpyAsync(m->d_shard_cells, cells, sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemcpyAsync(m->d_shard_rows, rows.data(), sizeof(long long) * nc, cudaMemcpyHostToDevice, m->stream));
+    CK(cudaMemsetAsync(m->d_send, 0, sizeof(double) * std::max(maxc, 1) * ncol, m->stream));
+    CK(cudaMemsetAsync(m->d_recv, 0, sizeof(double) * nranks * std::max(maxc, 1) * ncol, m->stream));
+    CK(cudaStreamSynchronize(m->stream));
+    drop_graph(m);
+    m->shard_nranks = nranks;
+    m->shard_rank = rank;
+    m->shard_first = rank_off[rank];
+    m->shard_nown = rank_off[rank + 1] - rank_off[rank];
+    m->shard_maxc = maxc;
+    m->exch = fn;
+    m->exch_ctx = ctx;
+    return MS_OK;
+}
+
+int ms_shard_buffers(ms_model *m, double **send, double **recv, int32_t *max_cells)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (!m->shard_nranks) return fail(MS_ERR_STATE, "the model is not sharded");
+    if (send) *send = m->d_send;
+    if (recv) *recv = m->d_recv;
+    if (max_cells) *max_cells = m->shard_maxc;
+    return MS_OK;
 }
 
 int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia_half, int64_t n,
@@ -1905,6 +2076,7 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
     if (mode == 0 && !mlp) return fail(MS_ERR_ARG, "mode 0 needs a network");
     if (mode >= 0 && (m->precision != MS_FP32 || !m->fc.couple))
         return fail(MS_ERR_STATE, "the closure runs on coupled FP32 models");
+    if (mode >= 0 && m->shard_nranks) return fail(MS_ERR_STATE, "a sharded model runs no closure");
     if (!(tol >= 0.0)) return fail(MS_ERR_ARG, "tol must be >= 0");
     if (mode >= 0 && m->steps % m->interval != 0) return fail(MS_ERR_STATE, "attach between coarse intervals");
     CK(cudaStreamSynchronize(m->stream));
@@ -1962,6 +2134,7 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
     if (!m || !X || !Y) return fail(MS_ERR_ARG, "NULL argument");
     if (nint < 1) return fail(MS_ERR_ARG, "nint must be >= 1");
     if (!m->fc.couple || m->precision != MS_FP32) return fail(MS_ERR_STATE, "collect runs on coupled FP32 models");
+    if (m->shard_nranks) return fail(MS_ERR_STATE, "a sharded model runs no closure");
     if (m->dt == 0.0) return fail(MS_ERR_STATE, "step the model once first (dt is not set)");
     if (m->steps % m->interval != 0) return fail(MS_ERR_STATE, "collect starts between coarse intervals");
     if (!m->d_X) {

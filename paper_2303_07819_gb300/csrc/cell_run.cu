@@ -8,9 +8,10 @@
 // only at the run's two ends.
 //
 // Work: the cells are packed into groups of at most 256 K floes (K = 1, 2
-// or 4 floes per thread of a 256-thread block; a group holds at most one
-// cell of more than 256 (K = 2) or 512 (K = 4) floes, and as many smaller
-// cells as fit, first fit by decreasing size).  Each K is one persistent
+// or 4 floes per thread of a 256-thread block): a cell of more than 256
+// (K = 2) or 512 (K = 4) floes is a group of its own, smaller cells share
+// K = 1 groups, first fit by decreasing size.  A cell's floes so always run
+// the code of its own size class, whatever else the model holds.  Each K is one persistent
 // launch whose blocks take groups from a ticket queue in decreasing order of
 // work.  A floe's state, forcing and running sums stay in registers for the
 // run; per step it publishes its position and velocity to shared memory (two

@@ -17,6 +17,7 @@
 // a fixed sequence of launches (prepare, NSUB_MAX substeps that return at once
 // past N1, targets, finish) and can be captured in a CUDA graph.
 #include "common.cuh"
+#include "shard.cuh"
 
 namespace msd {
 
@@ -148,7 +149,48 @@ __global__ void k_coarse_finish(CoarseArgs a)
 
 __global__ void k_advance(Ctrl *ctrl, int N0) { ctrl->base += N0; }
 
+// Sharded grids: the coarse step of a cell reads its moment columns 1-5 and
+// its five window sums and nothing else of the DEM (k_coarse_prepare,
+// k_coarse_targets).  A rank packs those of its own cells, row k of `send`
+// for its k-th cell, and after the exchange writes every gathered row back
+// into the cell it belongs to.
+__global__ void k_shard_pack(const double *mom, const double *win, int nc, const int *cells, int ncells,
+                             double *send)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncells) return;
+    const int c = cells[k];
+    double *o = send + (size_t)k * SHARD_NCOL;
+    for (int a = 0; a < 5; a++) o[a] = mom[(size_t)c * NMOM + 1 + a];
+    for (int a = 0; a < NWIN; a++) o[5 + a] = win[(size_t)a * nc + c];
+}
+
+__global__ void k_shard_scatter(double *mom, double *win, int nc, const int *cells, const long long *rows,
+                                const double *recv)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc) return;
+    const int c = cells[t];
+    const double *i = recv + (size_t)rows[t] * SHARD_NCOL;
+    for (int a = 0; a < 5; a++) mom[(size_t)c * NMOM + 1 + a] = i[a];
+    for (int a = 0; a < NWIN; a++) win[(size_t)a * nc + c] = i[5 + a];
+}
+
 }  // namespace
+
+cudaError_t launch_shard_pack(const double *mom, const double *win, int nc, const int *cells, int ncells,
+                              double *send, cudaStream_t st)
+{
+    if (ncells > 0) k_shard_pack<<<(ncells + 255) / 256, 256, 0, st>>>(mom, win, nc, cells, ncells, send);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_scatter(double *mom, double *win, int nc, const int *cells, const long long *rows,
+                                 const double *recv, cudaStream_t st)
+{
+    k_shard_scatter<<<(nc + 255) / 256, 256, 0, st>>>(mom, win, nc, cells, rows, recv);
+    return cudaGetLastError();
+}
 
 int coarse_launches() { return NSUB_MAX + 3; }
 

@@ -23,6 +23,10 @@ MOMENT_NAMES = ["n", "M", "Mu", "Mv", "I", "Iw", "area", "Muu", "Mvv", "Fdx", "F
 FLOE_KEYS = ("x", "y", "theta", "u", "v", "omega", "r", "h")
 
 _dp = C.POINTER(C.c_double)
+_ip32 = C.POINTER(C.c_int32)
+SHARD_NCOL = 10
+# int exchange(void *ctx, void *stream)
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p)
 
 
 class Grid(C.Structure):
@@ -58,7 +62,8 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_time_kernel", "ms_set_launch", "ms_info", "ms_free", "ms_last_error", "ms_cell_moments_noalloc",
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
-           "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm", "ms_set_resident"]
+           "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm", "ms_set_resident",
+           "ms_floe_cells", "ms_set_shard", "ms_shard_buffers"]
 
 
 def lib_path() -> str:
@@ -102,6 +107,9 @@ def load(path: str | None = None):
     L.ms_probe_fp32.argtypes = [C.c_int32, _dp]
     L.ms_save.argtypes = [vp, C.c_char_p]
     L.ms_load.argtypes = [vp, C.c_char_p]
+    L.ms_floe_cells.argtypes = [C.POINTER(Grid), C.POINTER(Floes), _ip32]
+    L.ms_set_shard.argtypes = [vp, C.c_int32, C.c_int32, _ip32, _ip32, EXCHANGE_FN, vp]
+    L.ms_shard_buffers.argtypes = [vp, C.POINTER(_dp), C.POINTER(_dp), _ip32]
     L.ms_free.argtypes = [vp]
     L.ms_free.restype = None
     L.ms_last_error.restype = C.c_char_p
@@ -148,6 +156,32 @@ def make_forcing(p: dict, precision: int):
     return f, (modes, vmodes)
 
 
+def make_grid(params: dict) -> Grid:
+    nens = max(1, int(params.get("nens", 1)))
+    return Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]), nens,
+                int(params.get("walls", 0)))
+
+
+def floe_cells(params: dict, floes: dict) -> np.ndarray:
+    """The cell ms_init assigns each floe to (int32, j * nx + i)."""
+    L = load()
+    g = make_grid(params)
+    fl, keep = make_floes(floes)
+    out = np.zeros(max(int(fl.n), 1), dtype=np.int32)
+    _check(L.ms_floe_cells(C.byref(g), C.byref(fl), out.ctypes.data_as(_ip32)))
+    return out[: int(fl.n)]
+
+
+class DeviceArray:
+    """A view of device memory the library owns, for consumers of
+    __cuda_array_interface__ (torch.as_tensor(..., device="cuda"))."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str = "<f8"):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None,
+                                         "stream": None}
+
+
 class Model:
     """One msDEM model (plus its truth DEM) on the current CUDA device."""
 
@@ -156,8 +190,7 @@ class Model:
         self.params = dict(params)
         self.precision = precision
         nens = max(1, int(params.get("nens", 1)))
-        g = Grid(int(params["nx"]), int(params["ny"]), float(params["Lx"]), float(params["Ly"]), nens,
-                 int(params.get("walls", 0)))
+        g = make_grid(params)
         fl, keep1 = make_floes(floes)
         fc, keep2 = make_forcing(params, precision)
         h = C.c_void_p()
@@ -183,11 +216,18 @@ class Model:
     def __exit__(self, *a):
         self.close()
 
+    def _step_check(self, rc: int) -> None:
+        err = getattr(self, "_exch_error", None)
+        if rc != 0 and err is not None:
+            self._exch_error = None
+            raise MsError(rc, load().ms_last_error().decode()) from err
+        _check(rc)
+
     def step(self, dt: float, nsteps: int) -> None:
-        _check(load().ms_step(self._h, float(dt), int(nsteps)))
+        self._step_check(load().ms_step(self._h, float(dt), int(nsteps)))
 
     def step_async(self, dt: float, nsteps: int) -> None:
-        _check(load().ms_step_async(self._h, float(dt), int(nsteps)))
+        self._step_check(load().ms_step_async(self._h, float(dt), int(nsteps)))
 
     def sync(self) -> None:
         _check(load().ms_sync(self._h))
@@ -277,13 +317,46 @@ class Model:
     def set_resident(self, skin_steps: float = 32.0, block_floes: int = 256) -> None:
         _check(load().ms_set_resident(self._h, float(skin_steps), int(block_floes)))
 
+    def set_shard(self, nranks: int, rank: int, rank_off, cells, exchange) -> None:
+        """Make this model rank `rank` of a sharded grid (ms_set_shard).
+        exchange(stream_handle) gathers every rank's send rows into recv
+        (shard_buffers) ordered on that stream; an exception in it fails the
+        step that called it and is re-raised from there."""
+        rank_off = np.ascontiguousarray(rank_off, dtype=np.int32)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        self._exch_error = None
+
+        def cb(ctx, stream):
+            try:
+                exchange(int(stream or 0))
+                return 0
+            except BaseException as e:  # reported through the failing step
+                self._exch_error = e
+                return 1
+
+        fn = EXCHANGE_FN(cb)
+        _check(load().ms_set_shard(self._h, int(nranks), int(rank), rank_off.ctypes.data_as(_ip32),
+                                   cells.ctypes.data_as(_ip32), fn, None))
+        self._exch_keep = (fn, rank_off, cells)
+        self._shard = (int(nranks), int(rank))
+
+    def shard_buffers(self):
+        """(send, recv, max_cells): DeviceArray views of the exchange
+        buffers, [max_cells][10] and [nranks * max_cells][10] FP64."""
+        snd, rcv, mc = _dp(), _dp(), C.c_int32()
+        _check(load().ms_shard_buffers(self._h, C.byref(snd), C.byref(rcv), C.byref(mc)))
+        nranks = self._shard[0]
+        addr = lambda p: C.cast(p, C.c_void_p).value
+        return (DeviceArray(addr(snd), (mc.value, SHARD_NCOL)),
+                DeviceArray(addr(rcv), (nranks * mc.value, SHARD_NCOL)), mc.value)
+
     def info(self) -> dict:
-        out = np.zeros(18, dtype=np.int64)
+        out = np.zeros(21, dtype=np.int64)
         _check(load().ms_info(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))))
         keys = ["n", "ncell", "max_n", "precision", "variant", "threads", "bin_beta_milli",
                 "launches_per_interval", "launches_per_coarse", "launches_per_truth_step", "steps",
                 "truth_steps", "graph_replays", "deep_contacts", "persistent", "N1", "skin_steps_milli",
-                "block_floes"]
+                "block_floes", "shard_ranks", "shard_rank", "shard_cells"]
         return {k: int(v) for k, v in zip(keys, out)}
 
 
