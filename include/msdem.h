@@ -125,9 +125,10 @@ typedef struct ms_forcing {
 
 typedef struct ms_model ms_model;
 
-/* Create a model on the current CUDA device: validates the inputs, assigns
- * floes to cells, builds the per-cell floe layout on the device (floes of a
- * cell contiguous), uploads the state and a second copy for the truth DEM.
+/* Create a model on the current CUDA device: validates the inputs, uploads
+ * them, assigns floes to cells and builds the per-cell floe layout by a
+ * counting sort on the device (floes of a cell contiguous, in the caller's
+ * order), and keeps a second copy of the state for the truth DEM.
  * Rejects (MS_ERR_ARG): nx, ny < 1; non-positive or non-finite sizes; n < 0;
  * non-finite floe values; r <= 0 or h <= 0; 2 r_max >= half the smaller cell
  * side (the periodic minimum image would be ambiguous); a cell with more than
@@ -285,9 +286,18 @@ int ms_info(ms_model *m, int64_t *out);
 
 /* The cell (j * nx + i, rows j of every realization stacked in y) that
  * ms_init assigns each floe to: each coordinate wrapped into the periodic
- * domain, then the half-open cell holding it.  cell_out: host, floes->n
- * int32.  MS_ERR_ARG for a bad grid, NULL arrays or a non-finite position. */
+ * domain, then the half-open cell holding it -- computed by ms_init's own
+ * kernel on the current CUDA device (temporary device memory, freed before
+ * returning).  floes: host arrays (only x and y are read); cell_out: host,
+ * floes->n int32.  MS_ERR_ARG for a bad grid, NULL arrays or a non-finite
+ * position; MS_ERR_CUDA if the device work fails. */
 int ms_floe_cells(const ms_grid *grid, const ms_floes *floes, int32_t *cell_out);
+
+/* The model's floe layout: off (host, ncell + 1 int32) the first stored
+ * floe of each cell (off[ncell] = n), orig (host, n int32) the caller's
+ * index of each stored floe -- the cells' floes in the caller's order.
+ * Either may be NULL. */
+int ms_layout(ms_model *m, int32_t *off, int32_t *orig);
 
 /* Exchange of a sharded model's coarse inputs, called by ms_step and
  * ms_step_async on the calling thread at each coarse step, after the rank's

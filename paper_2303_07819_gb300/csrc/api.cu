@@ -201,15 +201,6 @@ static void *stage(ms_model *m, size_t bytes)
 
 static bool isfin(double x) { return std::isfinite(x); }
 
-static int cell_index(double X, double L, double d, int n)
-{
-    double Xw = X - L * std::floor(X / L);
-    int i = (int)std::floor(Xw / d);
-    if (i < 0) i = 0;
-    if (i > n - 1) i = n - 1;
-    return i;
-}
-
 // the model's geometry of a grid (an ensemble stacks its realizations in y)
 static Geom grid_geom(const ms_grid *grid)
 {
@@ -225,12 +216,6 @@ static Geom grid_geom(const ms_grid *grid)
     g.Lcy = grid->Ly / grid->ny;
     g.walls = grid->walls;
     return g;
-}
-
-// the cell a floe at (x, y) belongs to (periodic wrap of the position first)
-static int floe_cell(const Geom &g, double x, double y)
-{
-    return cell_index(y, g.Ly, g.Lcy, g.ny) * g.nx + cell_index(x, g.Lx, g.Lcx, g.nx);
 }
 
 static uint32_t to_fix(double frac)
@@ -354,15 +339,6 @@ static int raw_to_state(ms_model *m)
     else
         CK(launch_floes_to_cells32(m->d_raw, m->d_orig, m->d_cell_of, g, m->s32, m->stream));
     return MS_OK;
-}
-
-// upload floes (already validated and assigned) into the msDEM layout
-static int upload_model_state(ms_model *m, const ms_floes *f)
-{
-    if (m->n == 0) return MS_OK;
-    Trace tr("msdem.upload");
-    const int rc = send_raw(m, f);
-    return rc ? rc : raw_to_state(m);
 }
 
 static int upload_truth_state(ms_model *m, const ms_floes *f)
@@ -1353,42 +1329,15 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     m->interval = f.couple ? f.N0 : 100;
     fill_phys(m);
 
-    // stable assignment of floes to cells; reject ambiguous minimum images
+    // reject ambiguous minimum images
     const long long n = m->n;
     double rmax = 0.0;
-    m->h_cell_of_orig.resize(n);
-    m->h_off.assign(m->ncell + 1, 0);
-    for (long long l = 0; l < n; l++) {
-        const int c = floe_cell(m->g, floes->x[l], floes->y[l]);
-        m->h_cell_of_orig[l] = c;
-        m->h_off[c + 1]++;
-        rmax = std::max(rmax, floes->r[l]);
-    }
+    for (long long l = 0; l < n; l++) rmax = std::max(rmax, floes->r[l]);
     if (n > 0 && !(2.0 * rmax < 0.5 * std::min(m->g.Lcx, m->g.Lcy))) {
         ms_free(m);
         return fail(MS_ERR_ARG, "2 r_max = %g m must be below half the cell side (%g m)", 2.0 * rmax,
                     0.5 * std::min(m->g.Lcx, m->g.Lcy));
     }
-    for (int c = 0; c < m->ncell; c++) {
-        m->max_n = std::max(m->max_n, m->h_off[c + 1]);
-        m->h_off[c + 1] += m->h_off[c];
-    }
-    const int cap = m->precision == MS_FP64 ? 2048 : 4096;
-    if (m->max_n > cap) {
-        int mx = m->max_n;
-        ms_free(m);
-        return fail(MS_ERR_ARG, "a cell holds %d floes; at most %d are supported", mx, cap);
-    }
-    m->h_orig.resize(n);
-    {
-        std::vector<int> fill(m->h_off.begin(), m->h_off.end() - 1);
-        for (long long l = 0; l < n; l++) m->h_orig[fill[m->h_cell_of_orig[l]]++] = l;
-    }
-    m->h_order.resize(m->ncell);
-    for (int c = 0; c < m->ncell; c++) m->h_order[c] = c;
-    std::stable_sort(m->h_order.begin(), m->h_order.end(), [&](int a, int b) {
-        return (m->h_off[a + 1] - m->h_off[a]) > (m->h_off[b + 1] - m->h_off[b]);
-    });
 
     int dev = 0;
     cudaError_t e;
@@ -1457,18 +1406,63 @@ int ms_init(ms_model **out, const ms_grid *grid, const ms_floes *floes, const ms
     CKM(cudaMemsetAsync(m->d_win, 0, sizeof(double) * nc * NWIN, m->stream));
     CKM(cudaMemsetAsync(m->d_q0, 0, sizeof(double) * nc * 4, m->stream));
     CKM(cudaMemsetAsync(m->d_tgt, 0, sizeof(double) * nc * 4, m->stream));
-    CKM(cudaMemcpyAsync(m->d_off, m->h_off.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, m->stream));
-    CKM(cudaMemcpyAsync(m->d_order, m->h_order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
-    {
-        const std::vector<int> orig32(m->h_orig.begin(), m->h_orig.end());
-        CKM(cudaMemcpyAsync(m->d_orig, orig32.data(), sizeof(int) * n, cudaMemcpyHostToDevice, m->stream));
-        CKM(cudaMemcpyAsync(m->d_cell_of, m->h_cell_of_orig.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
-                            m->stream));
-        CKM(cudaStreamSynchronize(m->stream));
+    // The cell of every floe, the cells' offsets and each cell's floes in the
+    // caller's order: a counting sort on the device over the raw upload
+    // (cell of each floe and counts, scan, scatter, rank sort within cells).
+    // The host keeps the offsets for the launch layout and the permutation
+    // for downloads.
+    if (n > 0 && (rc = send_raw(m, floes))) {
+        ms_free(m);
+        return rc;
     }
+    {
+        int *count = nullptr, *cursor = nullptr, *tmp = nullptr;
+        const long long ntmp = sort_scan_ints(nc + 1);
+        auto release = [&]() {
+            cudaFree(count);
+            cudaFree(cursor);
+            cudaFree(tmp);
+        };
+        e = cudaMalloc(&count, sizeof(int) * nc);
+        if (e == cudaSuccess) e = cudaMalloc(&cursor, sizeof(int) * nc);
+        if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int) * ntmp);
+        if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, sizeof(int) * nc, m->stream);
+        if (e == cudaSuccess) e = launch_cell_of(m->d_raw, up_geom(m), m->d_cell_of, count, m->stream);
+        if (e == cudaSuccess) e = sort_by_cell(m->d_cell_of, count, m->d_off, cursor, m->d_orig, tmp, nc, n, m->stream);
+        m->h_off.assign(nc + 1, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(m->h_off.data(), m->d_off, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost, m->stream);
+        std::vector<int> orig32(n);
+        m->h_cell_of_orig.resize(n);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(orig32.data(), m->d_orig, sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess && n > 0)
+            e = cudaMemcpyAsync(m->h_cell_of_orig.data(), m->d_cell_of, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                                m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        release();
+        if (e != cudaSuccess) {
+            ms_free(m);
+            return fail(MS_ERR_CUDA, "cell assignment failed: %s", cudaGetErrorString(e));
+        }
+        m->h_orig.assign(orig32.begin(), orig32.end());
+    }
+    for (int c = 0; c < nc; c++) m->max_n = std::max(m->max_n, m->h_off[c + 1] - m->h_off[c]);
+    const int cap = m->precision == MS_FP64 ? 2048 : 4096;
+    if (m->max_n > cap) {
+        const int mx = m->max_n;
+        ms_free(m);
+        return fail(MS_ERR_ARG, "a cell holds %d floes; at most %d are supported", mx, cap);
+    }
+    m->h_order.resize(nc);
+    for (int c = 0; c < nc; c++) m->h_order[c] = c;
+    std::stable_sort(m->h_order.begin(), m->h_order.end(), [&](int a, int b) {
+        return (m->h_off[a + 1] - m->h_off[a]) > (m->h_off[b + 1] - m->h_off[b]);
+    });
+    CKM(cudaMemcpyAsync(m->d_order, m->h_order.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, m->stream));
 #undef CKM
     // an ensemble has no truth DEM (each realization's truth is a model of its own)
-    if ((rc = upload_model_state(m, floes)) ||
+    if ((rc = raw_to_state(m)) ||
         (nens == 1 && ((rc = upload_truth_state(m, floes)) || (rc = setup_truth_bins(m, floes->r, rmax > 0 ? rmax : 1.0))))) {
         ms_free(m);
         return rc;
@@ -1966,12 +1960,37 @@ int ms_floe_cells(const ms_grid *grid, const ms_floes *floes, int32_t *cell_out)
         return fail(MS_ERR_ARG, "bad grid");
     int rc = check_floe_args(floes, -1);
     if (rc) return rc;
+    const long long n = floes->n;
+    const long long l = host_first(n, [&](long long k) { return !isfin(floes->x[k]) || !isfin(floes->y[k]); });
+    if (l < n) return fail(MS_ERR_ARG, "floe %lld has a non-finite position", l);
+    if (n == 0) return MS_OK;
+    // the kernel ms_init assigns cells with, on the current device
     const Geom g = grid_geom(grid);
-    const long long l = host_first(floes->n, [&](long long k) { return !isfin(floes->x[k]) || !isfin(floes->y[k]); });
-    if (l < floes->n) return fail(MS_ERR_ARG, "floe %lld has a non-finite position", l);
-    host_parallel(floes->n, [&](long long b, long long e) {
-        for (long long k = b; k < e; k++) cell_out[k] = floe_cell(g, floes->x[k], floes->y[k]);
-    });
+    UpGeom ug{n, g.nx, g.ny, g.Lx, g.Ly, g.Lcx, g.Lcy};
+    double *xy = nullptr;
+    int *cell = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&xy, sizeof(double) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&cell, sizeof(int) * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xy, floes->x, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xy + n, floes->y, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_cell_of(xy, ug, cell, nullptr, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cell_out, cell, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(xy);
+    cudaFree(cell);
+    if (st) cudaStreamDestroy(st);
+    if (e != cudaSuccess) return fail(MS_ERR_CUDA, "cell assignment failed: %s", cudaGetErrorString(e));
+    return MS_OK;
+}
+
+int ms_layout(ms_model *m, int32_t *off, int32_t *orig)
+{
+    if (!m) return fail(MS_ERR_ARG, "model is NULL");
+    if (off) std::copy(m->h_off.begin(), m->h_off.end(), off);
+    if (orig)
+        for (long long k = 0; k < m->n; k++) orig[k] = (int32_t)m->h_orig[k];
     return MS_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <climits>
 
 #include "common.cuh"
+#include "upload.cuh"
 
 namespace msd {
 
@@ -80,6 +81,8 @@ __global__ void k_scan_add(int *out, const int *bsum, int n)
     const int i = blockIdx.x * SCAN_T + threadIdx.x;
     if (i < n) out[i] += bsum[blockIdx.x];
 }
+
+__global__ void k_set_int(int *p, int v) { *p = v; }
 
 __global__ void k_scatter(const int *bin, const int *start, int *cursor, int *sorted, long long n)
 {
@@ -496,6 +499,74 @@ cudaError_t counting_sort(TruthBins &b, long long n, BinF binf, cudaStream_t st)
 
 }  // namespace
 
+// ---- the floes of a model grouped by cell (ms_init)
+
+// exclusive scan of n ints (in place allowed): per-block scans, the block
+// totals scanned the same way, then added back
+static cudaError_t scan_exclusive(const int *in, int *out, long long n, int *tmp, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long nb = (n + SCAN_T - 1) / SCAN_T;
+    k_scan_blocks<<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, tmp, (int)n);
+    if (nb > 1) {
+        const cudaError_t e = scan_exclusive(tmp, tmp, nb, tmp + nb, st);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<(unsigned)nb, SCAN_T, 0, st>>>(out, tmp, (int)n);
+    }
+    return cudaGetLastError();
+}
+
+long long sort_scan_ints(long long n)
+{
+    long long total = 1;
+    while (n > 1) {
+        n = (n + SCAN_T - 1) / SCAN_T;
+        total += n;
+    }
+    return total + 1;
+}
+
+namespace {
+
+constexpr int RANK_T = 256;
+constexpr int RANK_MAX = 4096;   // the largest cell a model takes
+
+// A block per cell: the cell's caller indices into ascending order, each
+// entry placed at its rank (the number of smaller indices; they are
+// distinct).  Cells above RANK_MAX floes are left as scattered (ms_init
+// rejects them before this runs).
+__global__ void __launch_bounds__(RANK_T) k_cell_rank_sort(const int *off, int *orig, int ncell)
+{
+    __shared__ int keys[RANK_MAX];
+    const int c = blockIdx.x;
+    if (c >= ncell) return;
+    const int s = off[c], m = off[c + 1] - s;
+    if (m <= 1 || m > RANK_MAX) return;
+    for (int i = threadIdx.x; i < m; i += RANK_T) keys[i] = orig[s + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += RANK_T) {
+        const int key = keys[i];
+        int rank = 0;
+        for (int j = 0; j < m; j++) rank += keys[j] < key ? 1 : 0;
+        orig[s + rank] = key;
+    }
+}
+
+}  // namespace
+
+cudaError_t sort_by_cell(const int *cell_of, const int *count, int *off, int *cursor, int *orig, int *tmp,
+                         int ncell, long long n, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st);
+    if (e == cudaSuccess) e = scan_exclusive(count, off, ncell, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_set_int<<<1, 1, 0, st>>>(off + ncell, (int)n);
+    const int T = 256;
+    if (n > 0) k_scatter<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(cell_of, off, cursor, orig, n);
+    if (n > 0 && ncell > 0) k_cell_rank_sort<<<ncell, RANK_T, 0, st>>>(off, orig, ncell);
+    return cudaGetLastError();
+}
+
 cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st)
 {
     const int nb = (nbins + SCAN_T - 1) / SCAN_T;
@@ -576,8 +647,6 @@ cudaError_t launch_truth_moments64(const DevState64 &s, const Phys<double> &P, c
 // time corrupt each other.
 
 namespace {
-
-__global__ void k_set_int(int *p, int v) { *p = v; }
 
 // cell of a caller's floe: each coordinate wrapped into [0, L) by
 // X - L floor(X / L), then the half-open cell floor(X / (L / n)), clamped

@@ -1,11 +1,11 @@
 // upload.cu -- the caller's floes into the cell layout, on the device.
 //
 // The host copies the eight FP64 input arrays into pinned memory (all cores)
-// and from there to the device in one transfer; these kernels check them and
-// write the stored state, one thread per floe.  The arithmetic is that of
-// the host-side assignment in ms_init, written with explicitly rounded
-// operations (no contraction into FMAs), so a floe gets the same cell and the
-// same fixed-point position on either side.
+// and from there to the device in one transfer; these kernels assign the
+// floes to cells, check them and write the stored state, one thread per
+// floe.  The arithmetic is written with explicitly rounded operations (no
+// contraction into FMAs), so the assignment is the plain IEEE evaluation of
+// X - L floor(X / L) and floor(X / d) wherever it runs.
 #include "upload.cuh"
 
 namespace msd {
@@ -96,6 +96,18 @@ __global__ void __launch_bounds__(UP_T) k_floes_to_cells64(const double *__restr
     }
 }
 
+// the cell of every caller floe (and the count of each cell)
+__global__ void __launch_bounds__(UP_T) k_cell_of(const double *__restrict__ raw, UpGeom g, int *__restrict__ cell_of,
+                                                  int *__restrict__ count)
+{
+    const long long n = g.n;
+    for (long long l = blockIdx.x * (long long)UP_T + threadIdx.x; l < n; l += (long long)gridDim.x * UP_T) {
+        const int c = cell_index_d(raw[n + l], g.Ly, g.Lcy, g.ny) * g.nx + cell_index_d(raw[l], g.Lx, g.Lcx, g.nx);
+        cell_of[l] = c;
+        if (count) atomicAdd(&count[c], 1);
+    }
+}
+
 // one thread per floe, at most 65,536 blocks (a grid-stride loop covers the rest)
 int up_blocks(long long n)
 {
@@ -104,6 +116,13 @@ int up_blocks(long long n)
 }
 
 }  // namespace
+
+cudaError_t launch_cell_of(const double *raw, UpGeom g, int *cell_of, int *count, cudaStream_t st)
+{
+    if (g.n == 0) return cudaSuccess;
+    k_cell_of<<<up_blocks(g.n), UP_T, 0, st>>>(raw, g, cell_of, count);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_check_floes(const double *raw, const int *cell_of, UpGeom g, unsigned long long *first,
                                cudaStream_t st)

@@ -63,7 +63,7 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
            "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm", "ms_set_resident",
-           "ms_floe_cells", "ms_set_shard", "ms_shard_buffers"]
+           "ms_floe_cells", "ms_set_shard", "ms_shard_buffers", "ms_layout"]
 
 
 def lib_path() -> str:
@@ -108,6 +108,7 @@ def load(path: str | None = None):
     L.ms_save.argtypes = [vp, C.c_char_p]
     L.ms_load.argtypes = [vp, C.c_char_p]
     L.ms_floe_cells.argtypes = [C.POINTER(Grid), C.POINTER(Floes), _ip32]
+    L.ms_layout.argtypes = [vp, _ip32, _ip32]
     L.ms_set_shard.argtypes = [vp, C.c_int32, C.c_int32, _ip32, _ip32, EXCHANGE_FN, vp]
     L.ms_shard_buffers.argtypes = [vp, C.POINTER(_dp), C.POINTER(_dp), _ip32]
     L.ms_free.argtypes = [vp]
@@ -316,6 +317,14 @@ class Model:
 
     def set_resident(self, skin_steps: float = 32.0, block_floes: int = 256) -> None:
         _check(load().ms_set_resident(self._h, float(skin_steps), int(block_floes)))
+
+    def layout(self):
+        """(off [ncell + 1], orig [n]): each cell's first stored floe and the
+        caller's index of every stored floe (ms_layout)."""
+        off = np.zeros(self.ncell + 1, dtype=np.int32)
+        orig = np.zeros(max(self.n, 1), dtype=np.int32)
+        _check(load().ms_layout(self._h, off.ctypes.data_as(_ip32), orig.ctypes.data_as(_ip32)))
+        return off, orig[: self.n]
 
     def set_shard(self, nranks: int, rank: int, rank_off, cells, exchange) -> None:
         """Make this model rank `rank` of a sharded grid (ms_set_shard).

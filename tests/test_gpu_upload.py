@@ -148,8 +148,8 @@ def test_uploading_the_held_state_continues_the_run(ms, precision):
 def test_half_open_cells_match_the_oracle(ms, orc, precision):
     """Floes on a cell's left edge, at X = Lx and at negative coordinates
     are assigned as the oracle assigns them (half-open cells, floor wrap):
-    by ms_init on the host, and by the device-side check of ms_set_floes,
-    which accepts the same floes again."""
+    by ms_init's counting sort on the device, by ms_floe_cells, and by the
+    device-side check of ms_set_floes, which accepts the same floes again."""
     L = 4.0e4
     dX = L / 4
     xs = [dX, 2 * dX, L, -dX, 0.5 * dX]
@@ -163,6 +163,65 @@ def test_half_open_cells_match_the_oracle(ms, orc, precision):
     o = orc.Model(p, fl)
     assert np.array_equal(g.moments()[:, 0], o.moments()[:, 0])
     assert g.moments()[:, 0].tolist() == [0, 1, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 2, 0, 0, 0]
+    assert ms.floe_cells(p, fl).tolist() == [1, 6, 12, 3, 12]
+    for a, b in zip(g.layout(), o.layout()):
+        assert np.array_equal(a, b)
     g.set_floes(fl)
     assert np.array_equal(g.moments()[:, 0], o.moments()[:, 0])
+    g.close()
+
+
+def _oracle_layout(orc, p, fl):
+    o = orc.Model(p, fl)
+    off, orig = o.layout()
+    o.close()
+    return off, orig
+
+
+@pytest.mark.parametrize("name", ["powerlaw_32x32", "batched_128x128"])
+def test_layout_is_the_oracles(ms, orc, name):
+    """The cell layout ms_init builds on the device (cell of each floe,
+    offsets, the floes of each cell in the caller's order) equals the
+    oracle's, index for index, on the full-size workloads (65k and 2M
+    floes), and ms_floe_cells gives the cells it used."""
+    s = I.WORKLOADS[name]()
+    p, fl = s["params"], s["floes"]
+    g = ms.Model(p, fl, 0)
+    off, orig = g.layout()
+    o_off, o_orig = _oracle_layout(orc, p, fl)
+    assert np.array_equal(off, o_off)
+    assert np.array_equal(orig, o_orig)
+    cell = np.repeat(np.arange(off.size - 1), np.diff(off))
+    cells_of = ms.floe_cells(p, fl)
+    assert np.array_equal(cells_of[orig], cell)
+    g.close()
+
+
+def test_layout_of_a_full_cell_in_shuffled_order(ms, orc):
+    """4096 floes in one cell (the FP32 limit) and a few in others, given in
+    a random order: each cell's floes come out in ascending caller order,
+    as the oracle stores them; an empty model has an all-zero layout."""
+    rng = np.random.default_rng(7)
+    L = 8.0e5
+    n0 = 4096
+    x = np.concatenate([rng.uniform(0.0, L / 2, n0), rng.uniform(L / 2, L, 37)])
+    y = np.concatenate([rng.uniform(0.0, L / 2, n0), rng.uniform(0.0, L, 37)])
+    perm = rng.permutation(x.size)
+    n = x.size
+    fl = {"x": x[perm], "y": y[perm], "theta": np.zeros(n), "u": np.zeros(n), "v": np.zeros(n),
+          "omega": np.zeros(n), "r": np.full(n, 10.0), "h": np.ones(n)}
+    p = I._phys(dt=5.0)
+    p.update({"nx": 2, "ny": 2, "Lx": L, "Ly": L, "modes": np.zeros((0, 4)), "couple": 0})
+    g = ms.Model(p, fl, 0)
+    off, orig = g.layout()
+    o_off, o_orig = _oracle_layout(orc, p, fl)
+    assert np.array_equal(off, o_off) and np.array_equal(orig, o_orig)
+    assert off[1] - off[0] == n0
+    for c in range(4):
+        assert (np.diff(orig[off[c]:off[c + 1]]) > 0).all()
+    g.close()
+    empty = {k: np.zeros(0) for k in fl}
+    g = ms.Model(p, empty, 0)
+    off, orig = g.layout()
+    assert not off.any() and orig.size == 0
     g.close()
