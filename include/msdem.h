@@ -233,7 +233,8 @@ int ms_autotune(ms_model *m, double dt, int32_t reps, double *best_ms);
  * ascending partner order; larger cells run the block list kernel step by
  * step (see ms_set_resident for its tunables).  Variants 2-5 give the same
  * results whether an interval runs in one launch or step by step.  With a
- * closure attached, variant 5 runs as variant 4.
+ * closure attached, the cells that take the closure for an interval hold no
+ * floes in their group for that interval (variants 2-5 skip them).
  * MS_ERR_ARG for an unsupported choice. */
 int ms_set_launch(ms_model *m, int32_t variant, int32_t threads, int32_t persistent, double bin_beta);
 
@@ -250,10 +251,10 @@ int ms_time_kernel(ms_model *m, int32_t which, double dt, int32_t reps, double *
  * skin_steps fine steps (1 .. 1000); cells of at most 256 floes share a
  * block of 256 threads, a floe per thread, up to block_floes (32 .. 256)
  * floes in all; a larger cell has a block of its own.  Floes do not depend
- * on skin_steps, block_floes or the other cells of the model;
- * block_floes changes which cells share a block, and with it the order of
- * the per-cell FP32 sums (moments differ by rounding only, and through the
- * coarse step the floes of later intervals).  ms_autotune chooses both;
+ * on skin_steps, block_floes or the other cells of the model, and
+ * neither do the moments: the per-cell sums are exact fixed-point integer
+ * sums (each value relative to the largest binary exponent of its cell and
+ * column), whichever cells share a block.  ms_autotune chooses both;
  * ms_info entries 16 and 17 report them.  MS_ERR_ARG outside the ranges. */
 int ms_set_resident(ms_model *m, double skin_steps, int32_t block_floes);
 
@@ -276,12 +277,10 @@ int ms_info(ms_model *m, int64_t *out);
  * cells (MS_SHARD_NCOL doubles per cell: moment columns 1-5, then the five
  * window sums, the only DEM data the coarse step reads), every rank gathers
  * all ranks' rows and takes the whole grid's coarse step itself.  That step
- * is the same computation on the same inputs on every rank, so in FP64 the
- * floes and moments of a rank's cells equal those of the unsharded model bit
- * for bit.  In FP32 (launch variant 5) the floes are equal bit for bit until
- * the first coarse step; the moments are sums whose order depends on which
- * cells share a block (ms_set_resident), so from then on the sharded model
- * differs from the unsharded one as a repacked model does, by rounding. */
+ * is the same computation on the same inputs on every rank, so the floes
+ * and moments of a rank's cells equal those of the unsharded model bit for
+ * bit, in FP64 and in FP32 with launch variant 5 (whose results do not
+ * depend on which cells share a block, see ms_set_resident). */
 #define MS_SHARD_NCOL 10
 
 /* The cell (j * nx + i, rows j of every realization stacked in y) that
@@ -419,8 +418,10 @@ void ms_mlp_free(ms_mlp *m);
 /* Closure plus particle fallback on a coupled FP32 model (not in the paper).
  * mode 0: at the start of each coarse interval every cell's features
  * (rho, mean u, v, omega, variances of u and v, ocean u, v, divergence and
- * curl at the cell centre, wind u, v, and the cell's four tendencies of the
- * interval before, measured by its DEM or predicted) go through `mlp`, which
+ * curl at the cell centre, wind u, v, the cell's drag per unit mass (x, y)
+ * and drag torque per unit inertia at the interval's start -- moment columns
+ * 9-11, measured by its DEM or predicted -- and the rate of change of its
+ * velocity variance over the interval before) go through `mlp`, which
  * predicts the interval-mean drag force per unit mass (x, y), drag torque per
  * unit inertia and the rate of change of the velocity variance.  A cell runs
  * the closure only when the interval before computed tendencies, its
@@ -433,8 +434,11 @@ void ms_mlp_free(ms_mlp *m);
  * every cell's DEM.  Every other cell runs the particle step (the fallback).  A closure cell skips its DEM for
  * the interval: it takes its pending coarse increments at once, its velocity
  * spread follows the predicted variance rate, and the coarse step sees the
- * predicted tendencies.  mode 1: the mean-field drag for every cell (no
- * network).  mode -1: off.  Attach between coarse intervals; `mlp` must
+ * predicted tendencies.  mode 2: as mode 0, but `mlp` predicts the
+ * tendencies less features 12-15 (the drag at the interval's start and the
+ * variance rate before), which the closure adds back (train it on
+ * Y - X[:, 12:16]).  mode 1: the
+ * mean-field drag for every cell (no network).  mode -1: off.  Attach between coarse intervals; `mlp` must
  * outlive the attachment.  Each closure cell counts as N0 cell-steps. */
 int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const float *box);
 

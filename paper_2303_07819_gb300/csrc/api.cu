@@ -519,7 +519,7 @@ static cudaError_t launch_interval_end(ms_model *m)
     if (hybrid_on(m)) {
         // the interval's tendencies (measured or predicted) become the next
         // interval's lagged features; the window is still unconsumed here
-        const bool net = m->hybrid_mode == 0;
+        const bool net = m->hybrid_mode == 0 || m->hybrid_mode == 2;
         cudaError_t e = launch_collect_targets(m->d_mom0, m->d_mom, m->d_win, m->ncell, m->fc.N0,
                                                (double)m->fc.N0 * m->dt, m->d_isc, m->d_Yuse, m->d_ctrl, m->d_Ylag,
                                                nullptr, net ? m->d_Yp : nullptr, floor_acc(m),
@@ -541,7 +541,8 @@ static cudaError_t launch_interval_start(ms_model *m)
         e = launch_features(m->d_mom, m->d_tgt, m->ncell, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
                             m->d_Ylag, m->d_X, m->stream);
     if (e != cudaSuccess) return e;
-    if (m->hybrid_mode == 0 && ms_mlp_forward_device(m->mlp, m->d_X, m->ncell, m->d_Yp, m->stream) != MS_OK)
+    if ((m->hybrid_mode == 0 || m->hybrid_mode == 2) &&
+        ms_mlp_forward_device(m->mlp, m->d_X, m->ncell, m->d_Yp, m->stream) != MS_OK)
         return cudaErrorUnknown;
     HybridArgs h{};
     h.X = m->d_X;
@@ -910,7 +911,6 @@ static int configure_launch(ms_model *m, const CellLaunch &cl_in)
 {
     CellLaunch cl = cl_in;
     if (cl.variant == 0 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure needs a binned cell kernel");
-    if (cl.variant == 5 && hybrid_on(m)) return fail(MS_ERR_STATE, "the closure runs with variants 1-4");
     if (cl.variant == 5 && m->precision != MS_FP32) return fail(MS_ERR_ARG, "variant 5 is FP32 only");
     if (cl.variant != 5 && m->cl.variant == 5) CK(fold_carry(m));
     if (cl.variant >= 1) make_segments(m, cl);
@@ -2091,8 +2091,8 @@ int ms_cell_moments_noalloc(const ms_grid *grid, double rho_ice, int32_t inertia
 int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const float *box)
 {
     if (!m) return fail(MS_ERR_ARG, "model is NULL");
-    if (mode < -1 || mode > 1) return fail(MS_ERR_ARG, "mode must be -1, 0 or 1");
-    if (mode == 0 && !mlp) return fail(MS_ERR_ARG, "mode 0 needs a network");
+    if (mode < -1 || mode > 2) return fail(MS_ERR_ARG, "mode must be -1, 0, 1 or 2");
+    if ((mode == 0 || mode == 2) && !mlp) return fail(MS_ERR_ARG, "modes 0 and 2 need a network");
     if (mode >= 0 && (m->precision != MS_FP32 || !m->fc.couple))
         return fail(MS_ERR_STATE, "the closure runs on coupled FP32 models");
     if (mode >= 0 && m->shard_nranks) return fail(MS_ERR_STATE, "a sharded model runs no closure");
@@ -2137,7 +2137,6 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
     m->hybrid_tol = tol;
     CellLaunch cl = m->cl;
     if (mode >= 0 && cl.variant == 0) cl.variant = 2;
-    if (mode >= 0 && cl.variant == 5) cl.variant = 4;     // the closure's cell selection runs on variants 1-4
     int rc = configure_launch(m, cl);
     if (rc) {
         m->hybrid_mode = prev_mode;

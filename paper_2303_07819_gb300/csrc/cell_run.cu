@@ -82,7 +82,7 @@ constexpr int RT = RUN_T;          // threads per block
 constexpr int LMAX = MS_RUN_LMAX;  // candidate slots per floe
 constexpr int GCMAX = RUN_GCMAX;   // cells per group
 constexpr int WT = 128;            // steps per wind table
-constexpr int NRED = 6;            // values per reduction pass
+constexpr int NRED = 16;           // values per reduction (moment columns 1-11, window sums)
 constexpr int NEVT = 32;           // gradual updates per interval with a precomputed radius ratio
 
 template <int K>
@@ -98,7 +98,8 @@ struct RunSm {
     unsigned short BF[F];           // bin of each floe (build)
     int BS[F + GCMAX + 1];          // bin counts, then starts
     int BC[F + GCMAX + 1];          // bin cursors
-    float PS[NRED][F];              // reduction partials at segment heads
+    unsigned long long csum[NRED][GCMAX];   // per-cell sums of a reduction, fixed point (two's complement)
+    int cexp[NRED][GCMAX];          // their binary exponents: the largest of the cell's values
     float2 Cm[GCMAX][MAXM];         // per cell and mode: corner phase (cos, sin), or (cycles, -)
     float rg[2][GCMAX][4];          // gradual update per cell (g, du, dv, dw), by step parity
     float cgrow[GCMAX][NEVT + 1];   // growth the cell's radii can still take this interval, by updates done
@@ -107,7 +108,8 @@ struct RunSm {
     float rgev[GCMAX][NEVT];        // radius ratio of each gradual update of the interval, per cell
     float2 wind[WT];
     int cc[GCMAX], cfs[GCMAX], cn[GCMAX], cnb[GCMAX], cbb[GCMAX], cgo[GCMAX];
-    int ncg, nfl, nbin, item;
+    int cskip[GCMAX];               // a closure cell: no DEM this interval (its floes stay where they are)
+    int ncg, nfl, nbin, item, allskip;
     float vsum[2];                  // group speed sums of the builds, by build parity
     int cflag[3][GCMAX];            // a floe of the cell strayed from its ocean centre, by step mod 3
 };
@@ -117,18 +119,35 @@ __host__ __device__ constexpr size_t run_smem_bytes(int K)
     return K == 1 ? sizeof(RunSm<1>) : (K == 2 ? sizeof(RunSm<2>) : sizeof(RunSm<4>));
 }
 
-// Segmented warp sum towards the head of each segment: lanes [lane, end) of
-// this warp belong to the caller's segment; after the call the segment's
-// first lane holds its total.  A fixed tree: the same order on every run.
-__device__ __forceinline__ float seg_sum(float x, int lane, int end_lane)
+// Segmented warp reductions towards the head of each segment: lanes [lane,
+// end) of this warp belong to the caller's segment; after the call the
+// segment's first lane holds its maximum or total.  Integer operations, so
+// the result does not depend on the order.
+__device__ __forceinline__ int seg_max(int x, int lane, int end_lane)
 {
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const float y = __shfl_down_sync(0xffffffffu, x, d);
+        const int y = __shfl_down_sync(0xffffffffu, x, d);
+        if (lane + d < end_lane) x = max(x, y);
+    }
+    return x;
+}
+
+__device__ __forceinline__ long long seg_sum(long long x, int lane, int end_lane)
+{
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_down_sync(0xffffffffu, x, d);
         if (lane + d < end_lane) x += y;
     }
     return x;
 }
+
+// Fixed-point per-cell sums: a value v of a cell's column whose largest
+// magnitude lies in [2^e, 2^(e + 1)) counts as round(v 2^(FIX_SHIFT - e)),
+// at most 2^50 in magnitude, so 4096 floes sum to below 2^62 exactly.
+constexpr int FIX_SHIFT = 49;
+constexpr int FIX_NONE = -30000;   // exponent of a column with no nonzero value
 
 // Exclusive scan of BS[0..nb) in place (block-wide); BC gets a copy of the
 // starts.  Ends with a barrier.
@@ -283,23 +302,40 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 
         // ---- the group's cells
         const int4 gd = groups[gid];          // first slot, cells, floes, bins (with one large slot per cell)
-        if (t < gd.y) {
-            const int4 id = items[gd.x + t];  // cell, first floe in the group, bins per side, bin base
-            const int c = id.x;
-            S.cc[t] = c;
-            S.cfs[t] = id.y;
-            S.cn[t] = sc.off[c + 1] - sc.off[c];
-            S.cnb[t] = id.z;
-            S.cbb[t] = id.w;
-            S.cgo[t] = sc.off[c];
+        if (t < 32) {                         // warp 0: a group has at most 32 cells
+            int n = 0;
+            if (t < gd.y) {
+                const int4 id = items[gd.x + t];  // cell, first floe in the group, bins per side, bin base
+                const int c = id.x;
+                const int skip = sc.skip && sc.skip[c] ? 1 : 0;
+                n = skip ? 0 : sc.off[c + 1] - sc.off[c];
+                S.cc[t] = c;
+                S.cskip[t] = skip;
+                S.cn[t] = n;
+                S.cnb[t] = id.z;
+                S.cbb[t] = id.w;
+                S.cgo[t] = sc.off[c];
+            }
+            // the group's floes packed cell after cell, closure cells holding
+            // none (without a closure: the places the grouping gave them)
+            int x = n;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, d);
+                if (lane >= d) x += y;
+            }
+            if (t < gd.y) S.cfs[t] = x - n;
+            if (t == 31) S.nfl = x;
+            const unsigned sk = __ballot_sync(FULL, t < gd.y && sc.skip && sc.skip[S.cc[t]]);
+            if (t == 0) S.allskip = __popc(sk) == gd.y;
         }
         if (t == 0) {
             S.ncg = gd.y;
-            S.nfl = gd.z;
             S.nbin = gd.w;
         }
         if (t < 3 * GCMAX) (&S.cflag[0][0])[t] = 0;
         __syncthreads();
+        if (S.allskip) continue;              // every cell of the group takes the closure this interval
         const int ncg = S.ncg, nfl = S.nfl;
         for (int idx = t; idx < ncg * P.n_modes; idx += RT) {
             const int ci = idx / P.n_modes, m = idx - ci * P.n_modes;
@@ -407,12 +443,26 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
         // above, later whenever a floe of the warp strays
         bool expand_at_centre = true;
 
-        // ---- reduction of NV (<= NRED) per-floe values per cell: segment
-        // sums over the floes of each warp (partials at the segment heads in
-        // PS, then a barrier); head_sum adds a cell's partials in order in
-        // FP64.  All threads call seg_partials.
+        // ---- reduction of NV (<= NRED) per-floe values per cell, exact and
+        // independent of where the cell's floes sit in the block: the
+        // largest binary exponent of each (cell, column), then the values in
+        // fixed point relative to it summed as integers (segments of a warp
+        // by shuffles, their heads into shared memory atomically); head_sum
+        // converts a total back.  All threads call seg_partials; it begins
+        // and ends with a barrier.
         auto seg_partials = [&](auto nv, auto &&value) {
             constexpr int NV = decltype(nv)::value;
+            for (int i = t; i < NV * GCMAX; i += RT) {
+                S.cexp[i / GCMAX][i % GCMAX] = FIX_NONE;
+                S.csum[i / GCMAX][i % GCMAX] = 0ull;
+            }
+            __syncthreads();
+            // a value counts if it is finite and nonzero (a non-finite state
+            // is reported by the run's end check)
+            auto counted = [&](int k, int q, bool valid) -> float {
+                const float x = valid ? value(k, q) : 0.0f;
+                return (x != 0.0f && isfinite(x)) ? x : 0.0f;
+            };
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 const int p = t + k * RT;
@@ -424,51 +474,36 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
                 const int head = max(fs, wb);
 #pragma unroll
                 for (int q = 0; q < NV; q++) {
-                    float x = valid ? value(k, q) : 0.0f;
-                    x = seg_sum(x, lane, end_lane);
-                    if (p == head) S.PS[q][p] = x;
+                    const float x = counted(k, q, valid);
+                    const int e = seg_max(x != 0.0f ? ilogbf(x) : FIX_NONE, lane, end_lane);
+                    if (p == head && e != FIX_NONE) atomicMax(&S.cexp[q][ci[k]], e);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int p = t + k * RT;
+                const bool valid = p < nfl;
+                const int fs = valid ? S.cfs[ci[k]] : nfl;
+                const int fe = valid ? S.cfs[ci[k]] + S.cn[ci[k]] : RT * K;
+                const int wb = p & ~31;
+                const int end_lane = min(fe, wb + 32) - wb;
+                const int head = max(fs, wb);
+#pragma unroll
+                for (int q = 0; q < NV; q++) {
+                    const float x = counted(k, q, valid);
+                    long long iv = 0;
+                    if (x != 0.0f) iv = __float2ll_rn(scalbnf(x, FIX_SHIFT - S.cexp[q][ci[k]]));
+                    iv = seg_sum(iv, lane, end_lane);
+                    if (p == head && iv != 0) atomicAdd(&S.csum[q][ci[k]], (unsigned long long)iv);
                 }
             }
             __syncthreads();
         };
-        auto head_sum = [&](int cell, int q) {
-            const int fs = S.cfs[cell], fe = S.cfs[cell] + S.cn[cell];
-            double acc = 0.0;
-            for (int hd = fs; hd < fe; hd = (hd | 31) + 1) acc += (double)S.PS[q][hd];
-            return acc;
+        auto head_sum = [&](int cell, int q) -> double {
+            const int e = S.cexp[q][cell];
+            return e == FIX_NONE ? 0.0 : ldexp((double)(long long)S.csum[q][cell], e - FIX_SHIFT);
         };
-        // window: the group of steps since the last flush (Algorithm 1 sums)
-        auto flush = [&]() {
-            auto val = [&](int k, int q) -> float {
-                const float mass = P.mass_c * r[k] * r[k] * h[k];
-                switch (q) {
-                case 0: return mass;
-                case 1: return mass * su[k];
-                case 2: return mass * sv[k];
-                case 3: return sfx[k];
-                case 4: return sfy[k];
-                default: return stz[k];
-                }
-            };
-            seg_partials(std::integral_constant<int, 6>{}, val);
-            // thread (cell, column): PS is written again only a step barrier later
-            if (t < 5 * ncg) {
-                const int cell = t / 5, q = t - 5 * cell;     // window column
-                const double x = head_sum(cell, q + 1);
-                if (q < 2) {
-                    const double M = head_sum(cell, 0);
-                    if (M > 0.0) S.cwin[cell][q] += x / M;
-                } else {
-                    S.cwin[cell][q] += x;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < K; k++) {
-                bad |= !(isfinite(su[k]) && isfinite(sv[k]) && isfinite(stz[k]));
-                su[k] = sv[k] = sfx[k] = sfy[k] = stz[k] = 0.0f;
-            }
-        };
-
         // ---- candidate lists from the positions in buffer b, before step kk
         auto build = [&](int b, int kk) {
             // the floor of the skins: a quarter of the group's mean speed
@@ -608,6 +643,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
         __syncthreads();
         int cur = 0;
         bool need_build = true;
+        float Fdl[K][3];                                  // the drag of the latest step (the moments' columns 9-11)
         int ph = (j0 + 1) % sc.n_t;                       // kk mod n_t
         for (int js = 0; js < nsteps; js++) {
             const int kk = j0 + js + 1;                   // step within the interval, 1-based
@@ -645,7 +681,6 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             const int fl_cur = js % 3, fl_nxt = (js + 1) % 3;
             if (t < ncg) S.cflag[(js + 2) % 3][t] = 0;     // read two steps ago, written at the next step's end
             bool far = false;
-            float Fdl[K][3];
 #pragma unroll
             for (int k = 0; k < K; k++) {
                 Fdl[k][0] = Fdl[k][1] = Fdl[k][2] = 0.0f;
@@ -737,48 +772,61 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             need_build = __syncthreads_or(far) != 0;
             expand_at_centre = false;
             cur ^= 1;
-            if (last) {
-                // the cell moments of the run's last step (all columns)
-                auto val1 = [&](int k, int q) -> float {
-                    const float m = P.mass_c * r[k] * r[k] * h[k];
-                    const float I = P.inertia_f * m * r[k] * r[k];
-                    switch (q) {
-                    case 0: return m;
-                    case 1: return m * u[k];
-                    case 2: return m * v[k];
-                    case 3: return I;
-                    case 4: return I * w[k];
-                    default: return 3.14159265358979323846f * r[k] * r[k];
-                    }
-                };
-                auto val2 = [&](int k, int q) -> float {
-                    const float m = P.mass_c * r[k] * r[k] * h[k];
-                    switch (q) {
-                    case 0: return m * u[k] * u[k];
-                    case 1: return m * v[k] * v[k];
-                    case 2: return Fdl[k][0];
-                    case 3: return Fdl[k][1];
-                    default: return Fdl[k][2];
-                    }
-                };
-                seg_partials(std::integral_constant<int, 6>{}, val1);
-                if (t < 6 * ncg) {
-                    const int cell = t / 6, q = t - 6 * cell;
-                    sc.mom[(size_t)S.cc[cell] * NMOM + 1 + q] = head_sum(cell, q);
+        }
+        // ---- the run's end: the cell moments of its last step (every column)
+        // and, at the interval's end, the window sums of Algorithm 1, in one
+        // exact reduction
+        {
+            auto val = [&](int k, int q) -> float {
+                const float m = P.mass_c * r[k] * r[k] * h[k];
+                const float I = P.inertia_f * m * r[k] * r[k];
+                switch (q) {
+                case 0: return m;
+                case 1: return m * u[k];
+                case 2: return m * v[k];
+                case 3: return I;
+                case 4: return I * w[k];
+                case 5: return 3.14159265358979323846f * r[k] * r[k];
+                case 6: return m * u[k] * u[k];
+                case 7: return m * v[k] * v[k];
+                case 8: return Fdl[k][0];
+                case 9: return Fdl[k][1];
+                case 10: return Fdl[k][2];
+                case 11: return m * su[k];
+                case 12: return m * sv[k];
+                case 13: return sfx[k];
+                case 14: return sfy[k];
+                default: return stz[k];
                 }
-                __syncthreads();
-                seg_partials(std::integral_constant<int, 5>{}, val2);
+            };
+            if (ends_interval) seg_partials(std::integral_constant<int, 16>{}, val);
+            else seg_partials(std::integral_constant<int, 11>{}, val);
+            // moment columns 1-11 are reduction columns 0-10
+            for (int i = t; i < 11 * ncg; i += RT) {
+                const int cell = i / 11, q = i - 11 * cell;
+                if (!S.cskip[cell]) sc.mom[(size_t)S.cc[cell] * NMOM + 1 + q] = head_sum(cell, q);
+            }
+            if (t < ncg && !S.cskip[t]) sc.mom[(size_t)S.cc[t] * NMOM] = (double)S.cn[t];
+            if (ends_interval) {
                 if (t < 5 * ncg) {
-                    const int cell = t / 5, q = t - 5 * cell;
-                    sc.mom[(size_t)S.cc[cell] * NMOM + 7 + q] = head_sum(cell, q);
+                    const int cell = t / 5, q = t - 5 * cell;     // window column
+                    const double x = head_sum(cell, 11 + q);
+                    if (q < 2) {
+                        const double M = head_sum(cell, 0);
+                        if (M > 0.0) S.cwin[cell][q] += x / M;
+                    } else {
+                        S.cwin[cell][q] += x;
+                    }
                 }
-                if (t < ncg) sc.mom[(size_t)S.cc[t] * NMOM] = (double)S.cn[t];
-                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    bad |= !(isfinite(su[k]) && isfinite(sv[k]) && isfinite(stz[k]));
+                    su[k] = sv[k] = sfx[k] = sfy[k] = stz[k] = 0.0f;
+                }
             }
         }
-        if (ends_interval) flush();
         __syncthreads();
-        if (win_on && t < ncg) {
+        if (win_on && t < ncg && !S.cskip[t]) {
             const int c = S.cc[t];
             for (int q = 0; q < NWIN; q++) sc.win[(size_t)q * nc + c] = S.cwin[t][q];
         }
@@ -803,7 +851,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             }
         }
         // an empty cell of the group: zero moments
-        if (t < ncg && S.cn[t] == 0) {
+        if (t < ncg && S.cn[t] == 0 && !S.cskip[t]) {
             double *mo = sc.mom + (size_t)S.cc[t] * NMOM;
             for (int q = 0; q < NMOM; q++) mo[q] = 0.0;
         }

@@ -475,7 +475,8 @@ cudaError_t bins_scan(TruthBins &b, int nbins, cudaStream_t st);
 
 // hybrid.cu: closure-plus-fallback intervals
 struct HybridArgs {
-    const float *X, *Yp;      // features [ncell][NFEAT], network prediction [ncell][4]
+    const float *X;           // features [ncell][NFEAT]
+    float *Yp;                // network prediction [ncell][4] (mode 2: made absolute in place)
     const float *nerr;        // [ncell] the network's drag error on the cell's last DEM interval
     const int *age;           // [ncell] closure intervals since that DEM interval
     const double *mom;

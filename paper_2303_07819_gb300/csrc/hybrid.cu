@@ -13,11 +13,11 @@
 // interval of a cell the network's prediction for that interval is compared
 // with the cell's measured drag, and only a cell whose last check passed, and
 // that has run at most CLOSURE_MAX_RUN closure intervals since, may take the
-// closure.  The features include the cell's tendencies of the
-// interval before (measured by its DEM, or predicted if it ran the closure):
-// the drag torque of a cell depends on the spread of its floes' spins, which
-// its moments do not carry but which changes slowly from one interval to the
-// next.
+// closure.  The features include the cell's drag at the interval's start
+// (the drag moment columns of the step that ended the interval before, or
+// the prediction if it ran the closure): a cell's drag depends on how its
+// floes' velocities and spins spread about the means, which the other
+// moments do not carry but which changes slowly over an interval.
 #include "common.cuh"
 
 namespace msd {
@@ -38,11 +38,14 @@ __host__ __device__ inline double ramp_mean_share(int N0, int n_t)
 }
 
 // [rho, ubar, vbar, wbar, var u, var v, u_o, v_o, div u_o, curl u_o, u_a, v_a,
-//  and the four tendencies of the interval before] (ocean at the cell centre,
-// wind at the start of the interval; the last four are zero when the
-// interval before computed none).  The mean velocity and spin are the
-// interval means the gradual updates produce: the cell's current means plus
-// the mean share of its pending increments.
+//  the cell's drag per unit mass (x, y) and drag torque per unit inertia at
+//  the interval's start (moment columns 9-11 of the step that ended the
+//  interval before; a closure cell's are its predicted ones), and the rate
+//  of change of the velocity variance over the interval before] (ocean at
+// the cell centre, wind at the start of the interval; the last four are zero
+// when the interval before computed no tendencies).  The mean velocity and
+// spin are the interval means the gradual updates produce: the cell's
+// current means plus the mean share of its pending increments.
 __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom g, Phys<double> P,
                            const Ctrl *ctrl, double dt, double share, const float *Ylag, float *X)
 {
@@ -66,7 +69,9 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
     const bool lag = ctrl->lag_mark == ctrl->base + 1;
     const double f[12] = {M / Ac, ub, vb, wb, su, sv, uo, vo, div, zeta, ua, va};
     for (int k = 0; k < 12; k++) X[(size_t)c * NF + k] = (float)f[k];
-    for (int k = 0; k < NT; k++) X[(size_t)c * NF + 12 + k] = lag ? Ylag[(size_t)c * NT + k] : 0.0f;
+    const double d[3] = {M > 0.0 ? mo[9] / M : 0.0, M > 0.0 ? mo[10] / M : 0.0, I > 0.0 ? mo[11] / I : 0.0};
+    for (int k = 0; k < 3; k++) X[(size_t)c * NF + 12 + k] = lag ? (float)d[k] : 0.0f;
+    X[(size_t)c * NF + 15] = lag ? Ylag[(size_t)c * NT + 3] : 0.0f;
 }
 
 // Targets of the interval just run: window means of the cell's total drag per
@@ -138,7 +143,7 @@ __device__ __forceinline__ void meanfield(const float *x, const double *mo, cons
 }
 
 // closure or particle for each cell; the tendencies the coarse step will see
-__global__ void k_classify(const float *X, const float *Yp, const double *mom, int ncell, Phys<double> P,
+__global__ void k_classify(const float *X, float *Yp, const double *mom, int ncell, Phys<double> P,
                            double rho_ice, const float *box, double tol, int mode, const Ctrl *ctrl,
                            const float *nerr, const int *age, int *is_closure, float *Yuse)
 {
@@ -148,6 +153,15 @@ __global__ void k_classify(const float *X, const float *Yp, const double *mom, i
     const double *mo = mom + (size_t)c * NMOM;
     double mf[4];
     meanfield(x, mo, P, rho_ice, mf);
+    if (mode == 2) {
+        // the network gives the change from features 12-15 (the drag at the
+        // interval's start, the variance rate of the interval before); from
+        // here on Yp holds the tendencies themselves (without an interval
+        // before there is nothing to add to, and nothing to check)
+        float *yp = Yp + (size_t)c * NT;
+        const bool lag = ctrl->lag_mark == ctrl->base + 1;
+        for (int k = 0; k < NT; k++) yp[k] = lag ? yp[k] + x[12 + k] : 3.0e38f;
+    }
     int closure = 0;
     float y[NT] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (ctrl->have_tgt) {

@@ -295,7 +295,9 @@ class Model:
         _check(load().ms_set_launch(self._h, int(variant), int(threads), int(persistent), float(bin_beta)))
 
     def closure_attach(self, mlp, mode: int = 0, tol: float = 0.5, box=None) -> None:
-        """mode 0: network `mlp` with fallback; 1: mean-field closure; -1: off."""
+        """mode 0: network `mlp` (predicting the tendencies) with fallback;
+        2: as 0 with `mlp` predicting their change from the interval before;
+        1: mean-field closure; -1: off."""
         self._mlp_ref = mlp
         bx = None if box is None else np.ascontiguousarray(box, dtype=np.float32).reshape(2 * NFEAT)
         self._box = bx

@@ -62,12 +62,14 @@ def test_network_learns_translational_drag(trained):
     assert r2[0] > 0.8 and r2[1] > 0.8, r2
 
 
-def _run(msdem, s, mode, tol, net, box, K):
-    """The closure's cell selection runs on the warp-per-cell kernels
-    (variant 4), so the particle-only runs here use them too."""
+def _run(msdem, s, mode, tol, net, box, K, variant=5):
+    """Spin-up, then K coarse intervals with the closure attached (mode >= 0)
+    or without; `variant` chooses the cell kernels (5, the default, or the
+    warp-per-cell kernels of variant 4)."""
     p = s["params"]
     m = msdem.Model(p, s["floes"], 0)
-    m.set_launch(4, 128, 0, 1.3)
+    if variant != 5:
+        m.set_launch(variant, 128, 0, 1.3)
     m.step(s["dt"], p["N0"] * SPIN)
     if mode >= 0:
         m.closure_attach(net if mode == 0 else None, mode, tol, box)
@@ -75,13 +77,14 @@ def _run(msdem, s, mode, tol, net, box, K):
     return m
 
 
-def test_zero_tolerance_is_the_particle_path(trained):
+@pytest.mark.parametrize("variant", [4, 5])
+def test_zero_tolerance_is_the_particle_path(trained, variant):
     """With tol = 0 every cell fails the residual check and runs the particle
     step: the floes are bitwise those of the model without the closure."""
     msdem, net, X, Y, losses, box = trained
     s = I.batched_128x128(seed=205, nx=16)
-    a = _run(msdem, s, -1, 0.0, net, box, 3)
-    b = _run(msdem, s, 0, 0.0, net, box, 3)
+    a = _run(msdem, s, -1, 0.0, net, box, 3, variant)
+    b = _run(msdem, s, 0, 0.0, net, box, 3, variant)
     assert b.closure_stats()["closure_cell_intervals"] == 0
     fa, fb = a.floes(), b.floes()
     for k in fa:
@@ -118,3 +121,36 @@ def test_fallback_fraction_follows_tolerance(trained):
         st = m.closure_stats()
         fr.append(st["closure_cell_intervals"] / (2 * st["cells"]))
     assert fr[0] <= fr[1] <= fr[2] and fr[2] > 0.5, fr
+
+
+def test_closure_cells_skip_their_dem(trained):
+    """One coarse interval with a mix of closure and particle cells (the
+    resident kernels, variant 5): a closure cell's floes do not move (its
+    DEM is skipped; the closure changed their velocities only), and every
+    particle cell's floes are bitwise those of the particle-only model --
+    cells sharing a block with skipped cells step exactly as before."""
+    msdem, net, X, Y, losses, box = trained
+    s = I.batched_128x128(seed=208, nx=16)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    a = _run(msdem, s, -1, 0.0, net, box, 2)
+    b = _run(msdem, s, 0, 0.2, net, box, 1)
+    assert b.closure_stats()["closure_cell_intervals"] == 0   # the first interval runs every DEM
+    f1 = b.floes()
+    b.step(dt, N0)
+    f2, fa = b.floes(), a.floes()
+    cells = msdem.floe_cells(p, s["floes"])
+    still = (f1["x"] == f2["x"]) & (f1["y"] == f2["y"])
+    ncell = p["nx"] * p["ny"]
+    closure = np.zeros(ncell, bool)
+    for c in range(ncell):
+        sel = cells == c
+        if sel.any() and still[sel].all():
+            closure[c] = True
+    nclos = b.closure_stats()["closure_cell_intervals"]
+    assert 0 < nclos < ncell, nclos
+    assert closure.sum() == nclos
+    part = ~closure[cells]
+    for k in fa:
+        assert np.array_equal(f2[k][part], fa[k][part]), k
+    a.close()
+    b.close()

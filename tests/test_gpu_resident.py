@@ -106,6 +106,27 @@ def test_repeat_runs_are_bitwise_equal(ms):
     _same(ms_[0], ms_[2])
 
 
+def test_packing_does_not_change_results(ms):
+    """Which cells share a block (block_floes), the skin horizon, and a
+    cell's place among the other cells of its block do not change a result:
+    its floes run the code of its own size class and its per-cell sums are
+    exact integer sums.  Three coarse intervals of the batched workload's
+    laws on 24 x 24 cells (cells of 8 to 1024 floes) under four launch
+    choices: the same floes, moments and coarse solution bit for bit."""
+    s = I.batched_128x128(seed=29, nx=24)
+    p, dt, N0 = s["params"], s["dt"], s["params"]["N0"]
+    runs = []
+    for skin, cap in ((32.0, 256), (32.0, 96), (16.0, 160), (48.0, 208)):
+        m = ms.Model(p, s["floes"], ms.MS_FP32)
+        m.set_resident(skin, cap)
+        m.step(dt, 3 * N0 + 17)
+        runs.append(m)
+    for m in runs[1:]:
+        _same(runs[0], m)
+    for m in runs:
+        m.close()
+
+
 def test_contacts_and_list_overflow(orc, ms):
     """A 3 km floe ringed by 60 floes of 150 m that touch it (its list of at
     most 16 candidates overflows and it tests every floe of its cell), plus
