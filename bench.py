@@ -73,7 +73,7 @@ def profile_traffic():
 
 
 def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=20, K=10,
-                 tols=(0.005, 0.01, 0.02, 0.05, 0.1, 0.3), target_err=1e-2, mode=2, epochs=40):
+                 tols=(0.01, 0.015, 0.02, 0.025, 0.03, 0.05, 0.1, 0.2), target_err=1e-2, mode=0, epochs=40):
     """The learned closure on the timed workload.  Training data come from the
     particle path of other seeds of the same workload (after spin-up; about
     1e6 cell-intervals); the network trains on the GPU; then K coarse

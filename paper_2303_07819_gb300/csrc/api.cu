@@ -113,6 +113,7 @@ struct ms_model {
     int *d_age = nullptr;
     int *d_isc = nullptr, *d_order2 = nullptr, *d_live = nullptr, *d_segb = nullptr, *d_sege = nullptr;
     double *d_mom0 = nullptr;
+    double *d_ocean = nullptr;      // [ncell][4] ocean at the cell centres (closure features)
     unsigned long long *d_ccount = nullptr;
     long long hybrid_intervals = 0;
     // a grid split into tiles: this model holds the floes of cells
@@ -539,7 +540,7 @@ static cudaError_t launch_interval_start(ms_model *m)
                                     m->stream);
     if (e == cudaSuccess)
         e = launch_features(m->d_mom, m->d_tgt, m->ncell, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
-                            m->d_Ylag, m->d_X, m->stream);
+                            m->d_Ylag, m->d_ocean, m->d_X, m->stream);
     if (e != cudaSuccess) return e;
     if ((m->hybrid_mode == 0 || m->hybrid_mode == 2) &&
         ms_mlp_forward_device(m->mlp, m->d_X, m->ncell, m->d_Yp, m->stream) != MS_OK)
@@ -576,6 +577,19 @@ static cudaError_t launch_interval_start(ms_model *m)
     h.tgt = m->d_tgt;
     h.N0 = m->fc.N0;
     h.n_t = m->fc.n_t;
+    // the resident classes (kind 3) skip closure cells in their own groups;
+    // the class of shared blocks keeps a group's closure all or nothing
+    h.seg_mask = 0u;
+    h.vgroups = nullptr;
+    h.vitems = m->cl.ritems;
+    h.nvgroups = 0;
+    for (int s = 0; s < m->cl.nseg; s++) {
+        if (m->cl.seg_kind[s] != 3) h.seg_mask |= 1u << s;
+        else if (m->cl.seg_maxn[s] == RUN_T) {
+            h.vgroups = m->cl.rgroups[s];
+            h.nvgroups = m->cl.rngroups[s];
+        }
+    }
     return launch_hybrid_select(h, m->stream);
 }
 
@@ -666,6 +680,7 @@ static int read_errors(ms_model *m)
     if (c.err & ERR_NONFINITE) return fail(MS_ERR_UNSTABLE, "floe state became non-finite");
     if (c.err & ERR_CFL)
         return fail(MS_ERR_UNSTABLE, "coarse step needs N1 = %d > %d Lax-Friedrichs substeps", c.N1, NSUB_MAX);
+    if (m->mlp && m->hybrid_mode >= 0) return ms_mlp_check(m->mlp);   // the closure network's own waits
     return MS_OK;
 }
 
@@ -2112,6 +2127,8 @@ int ms_closure_attach(ms_model *m, ms_mlp *mlp, int32_t mode, double tol, const 
         CK(dalloc(m, &m->d_isc, nc));
         CK(dalloc(m, &m->d_order2, nc));
         CK(dalloc(m, &m->d_live, MAXSEG));
+        CK(dalloc(m, &m->d_ocean, (size_t)nc * 4));
+        CK(launch_ocean_at_centres(nc, m->g, m->P64, m->d_ocean, m->stream));
         CK(dalloc(m, &m->d_segb, MAXSEG));
         CK(dalloc(m, &m->d_sege, MAXSEG));
         CK(dalloc(m, &m->d_mom0, (size_t)nc * NMOM));
@@ -2175,7 +2192,7 @@ int ms_closure_collect(ms_model *m, int32_t nint, float *X, float *Y)
                                         m->stream);
         if (e == cudaSuccess)
             e = launch_features(m->d_mom, m->d_tgt, nc, m->g, m->P64, m->d_ctrl, m->dt, m->fc.N0, m->fc.n_t,
-                                m->d_Ylag, m->d_X, m->stream);
+                                m->d_Ylag, m->d_ocean, m->d_X, m->stream);
         if (e == cudaSuccess && interval_cells(m)) e = launch_interval_cells(m, false);
         else
             for (int i = 0; i < m->interval && e == cudaSuccess; i++) e = launch_step(m, i, false);

@@ -62,6 +62,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "fixsum.cuh"
 
 namespace msd {
 
@@ -142,12 +143,6 @@ __device__ __forceinline__ long long seg_sum(long long x, int lane, int end_lane
     }
     return x;
 }
-
-// Fixed-point per-cell sums: a value v of a cell's column whose largest
-// magnitude lies in [2^e, 2^(e + 1)) counts as round(v 2^(FIX_SHIFT - e)),
-// at most 2^50 in magnitude, so 4096 floes sum to below 2^62 exactly.
-constexpr int FIX_SHIFT = 49;
-constexpr int FIX_NONE = -30000;   // exponent of a column with no nonzero value
 
 // Exclusive scan of BS[0..nb) in place (block-wide); BC gets a copy of the
 // starts.  Ends with a barrier.
@@ -460,8 +455,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
             // a value counts if it is finite and nonzero (a non-finite state
             // is reported by the run's end check)
             auto counted = [&](int k, int q, bool valid) -> float {
-                const float x = valid ? value(k, q) : 0.0f;
-                return (x != 0.0f && isfinite(x)) ? x : 0.0f;
+                return fix_counted(valid ? value(k, q) : 0.0f);
             };
 #pragma unroll
             for (int k = 0; k < K; k++) {
@@ -475,7 +469,7 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 #pragma unroll
                 for (int q = 0; q < NV; q++) {
                     const float x = counted(k, q, valid);
-                    const int e = seg_max(x != 0.0f ? ilogbf(x) : FIX_NONE, lane, end_lane);
+                    const int e = seg_max(fix_exp(x), lane, end_lane);
                     if (p == head && e != FIX_NONE) atomicMax(&S.cexp[q][ci[k]], e);
                 }
             }
@@ -492,17 +486,14 @@ k_cell_run32_block(DevState32 in, DevState32 out, Phys<float> P, StepCommon sc, 
 #pragma unroll
                 for (int q = 0; q < NV; q++) {
                     const float x = counted(k, q, valid);
-                    long long iv = 0;
-                    if (x != 0.0f) iv = __float2ll_rn(scalbnf(x, FIX_SHIFT - S.cexp[q][ci[k]]));
-                    iv = seg_sum(iv, lane, end_lane);
+                    const long long iv = seg_sum(fix_val(x, S.cexp[q][ci[k]]), lane, end_lane);
                     if (p == head && iv != 0) atomicAdd(&S.csum[q][ci[k]], (unsigned long long)iv);
                 }
             }
             __syncthreads();
         };
         auto head_sum = [&](int cell, int q) -> double {
-            const int e = S.cexp[q][cell];
-            return e == FIX_NONE ? 0.0 : ldexp((double)(long long)S.csum[q][cell], e - FIX_SHIFT);
+            return fix_total((long long)S.csum[q][cell], S.cexp[q][cell]);
         };
         // ---- candidate lists from the positions in buffer b, before step kk
         auto build = [&](int b, int kk) {

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "mlp_tc.cuh"
 #include "../../include/msdem.h"
 
 namespace msd {
@@ -313,6 +314,9 @@ struct ms_mlp {
          *dyt = nullptr;
     double *loss = nullptr;
     long long t = 0;           // Adam steps
+    int engine = 1;            // inference: 1 tcgen05 fused kernel, 0 tiled mma.sync GEMMs
+    int sm_count = 0;
+    int *tc_err = nullptr;     // set by the tcgen05 kernel if a wait ran out
     cudaStream_t st = nullptr;
     std::vector<void *> allocs;
     std::vector<float> hnorm;
@@ -470,8 +474,16 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         (e = mal(m, &m->sd_y, NOUT)) || (e = mal(m, &m->X, (size_t)Bp * NIN)) || (e = mal(m, &m->Y, (size_t)Bp * NOUT)) ||
         (e = mal(m, &m->yp, (size_t)Bp * NOP)) || (e = mal(m, &m->yout, (size_t)Bp * NOUT)) ||
         (e = mal(m, &m->xh, (size_t)Bp * KIN)) || (e = mal(m, &m->xht, (size_t)Bp * KIN)) ||
-        (e = mal(m, &m->dy, (size_t)Bp * NOP)) || (e = mal(m, &m->dyt, (size_t)Bp * NOP)) || (e = mal(m, &m->loss, 1)))
+        (e = mal(m, &m->dy, (size_t)Bp * NOP)) || (e = mal(m, &m->dyt, (size_t)Bp * NOP)) || (e = mal(m, &m->loss, 1)) ||
+        (e = mal(m, &m->tc_err, 1)))
         return fail_free(ck(e, "cudaMalloc"));
+    {
+        int dev = 0;
+        if ((rc = ck(cudaGetDevice(&dev), "device")) ||
+            (rc = ck(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev), "attribute")) ||
+            (rc = ck(mlp_tc_prepare(), "tcgen05 kernel attribute")))
+            return fail_free(rc);
+    }
     for (int l = 0; l < 3; l++)
         if ((e = mal(m, &m->H[l], (size_t)Bp * NH)) || (e = mal(m, &m->Ht[l], (size_t)Bp * NH)) ||
             (e = mal(m, &m->dZ[l], (size_t)Bp * NH)) || (e = mal(m, &m->dZt[l], (size_t)Bp * NH)))
@@ -535,6 +547,24 @@ void ms_mlp_free(ms_mlp *m)
 int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream)
 {
     if (!m || (n > 0 && (!X || !Y))) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (m->engine == 1) {
+        TcArgs a{};
+        a.X = X;
+        a.Y = Y;
+        a.n = n;
+        for (int l = 0; l < 4; l++) {
+            a.W[l] = m->L[l].Wb;
+            a.b[l] = m->L[l].b;
+        }
+        a.mu_x = m->mu_x;
+        a.sd_x = m->sd_x;
+        a.mu_y = m->mu_y;
+        a.sd_y = m->sd_y;
+        a.nout_pad = m->L[3].nop;
+        a.err = m->tc_err;
+        // two 107 KB CTAs fit an SM
+        return ck(launch_mlp_forward_tc(a, 2 * m->sm_count, stream ? (cudaStream_t)stream : m->st), "tcgen05 forward");
+    }
     cudaStream_t keep = m->st;
     if (stream) m->st = (cudaStream_t)stream;
     int rc = MS_OK;
@@ -559,6 +589,27 @@ int ms_mlp_predict(ms_mlp *m, const float *X, int64_t n, float *Y)
         if (rc) return rc;
         CKC(cudaMemcpyAsync(Y + s0 * NOUT, m->yout, sizeof(float) * B * NOUT, cudaMemcpyDeviceToHost, m->st));
         CKC(cudaStreamSynchronize(m->st));
+    }
+    return ms_mlp_check(m);
+}
+
+int ms_mlp_set_engine(ms_mlp *m, int32_t engine)
+{
+    if (!m) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    if (engine != 0 && engine != 1) return ms_closure_fail(MS_ERR_ARG, "engine must be 0 or 1");
+    CKC(cudaStreamSynchronize(m->st));
+    m->engine = engine;
+    return MS_OK;
+}
+
+int ms_mlp_check(ms_mlp *m)
+{
+    if (!m) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
+    int err = 0;
+    CKC(cudaMemcpy(&err, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CKC(cudaMemset(m->tc_err, 0, sizeof(int)));
+        return ms_closure_fail(MS_ERR_TIMEOUT, "a wait on the tensor cores ran out in the closure network");
     }
     return MS_OK;
 }

@@ -492,14 +492,23 @@ struct HybridArgs {
     const int *order, *seg_begin, *seg_end, *off;
     int *order2, *live;
     unsigned long long *closure_count;
+    unsigned seg_mask;        // classes whose particle cells are compacted into order2 / live
+    // groups of cells that share a block for a whole interval (resident
+    // kernels): a cell keeps the closure only if every cell with floes in its
+    // group does (device; nvgroups = 0: none)
+    const int4 *vgroups, *vitems;
+    int nvgroups;
     DevState32 st32;
     double *win, *tgt;
     double *mom_rw;
     int N0, n_t;
 };
 constexpr int NFEAT = 16;   // closure features per cell (12 from the moments and forcing, 4 lagged tendencies)
+// oc = [ncell][4] ocean u, v, divergence and curl at the cell centres
+cudaError_t launch_ocean_at_centres(int ncell, const Geom &g, const Phys<double> &P, double *oc, cudaStream_t st);
 cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
-                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, float *X, cudaStream_t st);
+                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, const double *oc,
+                            float *X, cudaStream_t st);
 cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const double *win, int ncell, int N0,
                                    double dT, const int *is_closure, const float *Yuse, Ctrl *ctrl, float *Ylag,
                                    float *Y, const float *Yp, double floor_acc, float *nerr, int *age,

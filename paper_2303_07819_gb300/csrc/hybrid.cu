@@ -19,6 +19,7 @@
 // floes' velocities and spins spread about the means, which the other
 // moments do not carry but which changes slowly over an interval.
 #include "common.cuh"
+#include "fixsum.cuh"
 
 namespace msd {
 
@@ -46,8 +47,23 @@ __host__ __device__ inline double ramp_mean_share(int N0, int n_t)
 // when the interval before computed no tendencies).  The mean velocity and
 // spin are the interval means the gradual updates produce: the cell's
 // current means plus the mean share of its pending increments.
+// The steady forcing at each cell centre: ocean u, v, divergence and curl
+// (the ocean does not change in time), computed once per attachment.
+__global__ void k_ocean_at_centres(int ncell, Geom g, Phys<double> P, double *oc)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int ix = c % g.nx, iy = (c / g.nx) % g.nyr;
+    double uo, vo, zeta;
+    ocean_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy, uo, vo, zeta);
+    oc[(size_t)c * 4] = uo;
+    oc[(size_t)c * 4 + 1] = vo;
+    oc[(size_t)c * 4 + 2] = ocean_div_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy);
+    oc[(size_t)c * 4 + 3] = zeta;
+}
+
 __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom g, Phys<double> P,
-                           const Ctrl *ctrl, double dt, double share, const float *Ylag, float *X)
+                           const Ctrl *ctrl, double dt, double share, const float *Ylag, const double *oc, float *X)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -60,12 +76,10 @@ __global__ void k_features(const double *mom, const double *tgt, int ncell, Geom
     const double sv = M > 0.0 ? fmax(mo[8] / M - vb0 * vb0, 0.0) : 0.0;
     const double sh = ctrl->have_tgt ? share : 0.0;
     const double ub = ub0 + sh * tgt[ncell + c], vb = vb0 + sh * tgt[2 * ncell + c], wb = wb0 + sh * tgt[3 * ncell + c];
-    const int ix = c % g.nx, iy = (c / g.nx) % g.nyr;
-    double uo, vo, zeta;
-    ocean_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy, uo, vo, zeta);
+    const double uo = oc[(size_t)c * 4], vo = oc[(size_t)c * 4 + 1], div = oc[(size_t)c * 4 + 2],
+                 zeta = oc[(size_t)c * 4 + 3];
     double ua, va;
     wind_at(P, (double)ctrl->base * dt, ua, va);
-    const double div = ocean_div_f64(P, (ix + 0.5) * g.Lcx, (iy + 0.5) * g.Lcy);
     const bool lag = ctrl->lag_mark == ctrl->base + 1;
     const double f[12] = {M / Ac, ub, vb, wb, su, sv, uo, vo, div, zeta, ua, va};
     for (int k = 0; k < 12; k++) X[(size_t)c * NF + k] = (float)f[k];
@@ -145,7 +159,8 @@ __device__ __forceinline__ void meanfield(const float *x, const double *mo, cons
 // closure or particle for each cell; the tendencies the coarse step will see
 __global__ void k_classify(const float *X, float *Yp, const double *mom, int ncell, Phys<double> P,
                            double rho_ice, const float *box, double tol, int mode, const Ctrl *ctrl,
-                           const float *nerr, const int *age, int *is_closure, float *Yuse)
+                           const float *nerr, const int *age, int *is_closure, float *Yuse,
+                           unsigned long long *closure_count)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -183,15 +198,18 @@ __global__ void k_classify(const float *X, float *Yp, const double *mom, int nce
     }
     is_closure[c] = closure;
     for (int k = 0; k < NT; k++) Yuse[(size_t)c * NT + k] = y[k];
+    const unsigned bal = __ballot_sync(__activemask(), closure != 0);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && bal) atomicAdd(closure_count, (unsigned long long)__popc(bal));
 }
 
 // Per size class (one block each), the particle cells of the class, in their
 // processing order, packed at the front of the class's range.
 __global__ void k_compact(const int *order, const int *seg_begin, const int *seg_end, const int *is_closure,
-                          int *order2, int *live, unsigned long long *closure_count)
+                          int *order2, int *live, unsigned seg_mask)
 {
     __shared__ int ws[33];
     const int s = blockIdx.x;
+    if (!((seg_mask >> s) & 1u)) return;       // a class whose kernels skip closure cells themselves
     const int b = seg_begin[s], e = seg_end[s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int base = 0, nclos = 0;
@@ -217,9 +235,34 @@ __global__ void k_compact(const int *order, const int *seg_begin, const int *seg
         base += ws[32];
         __syncthreads();
     }
-    for (int o = 16; o > 0; o >>= 1) nclos += __shfl_xor_sync(0xffffffffu, nclos, o);
-    if (lane == 0 && nclos) atomicAdd(closure_count, (unsigned long long)nclos);
     if (threadIdx.x == 0) live[s] = base;
+}
+
+// Cells that share a block run it for the interval's whole length, so a
+// closure cell saves time only when the cells beside it take the closure
+// too: a group keeps its closure cells only if every cell of it that holds
+// floes takes the closure.  A thread per group.
+__global__ void k_group_veto(const int4 *groups, int ngroups, const int4 *items, const int *off, int *is_closure,
+                             unsigned long long *closure_count)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngroups) return;
+    const int4 gd = groups[g];
+    bool all = true;
+    for (int i = 0; i < gd.y; i++) {
+        const int c = items[gd.x + i].x;
+        all &= off[c + 1] == off[c] || is_closure[c] != 0;
+    }
+    if (all) return;
+    unsigned long long dropped = 0;
+    for (int i = 0; i < gd.y; i++) {
+        const int c = items[gd.x + i].x;
+        if (off[c + 1] > off[c] && is_closure[c]) {
+            is_closure[c] = 0;
+            dropped++;
+        }
+    }
+    if (dropped) atomicAdd(closure_count, 0ull - dropped);
 }
 
 // A closure cell runs the interval without its DEM.  It reports to the coarse
@@ -229,14 +272,18 @@ __global__ void k_compact(const int *order, const int *seg_begin, const int *seg
 // sums.  Its floes end the interval where the particle path would take them:
 // the full increments plus dT times the predicted tendencies (uniform shifts),
 // the velocity spread scaled to the predicted variance, the radius scale
-// (bounded to [0.5, 2] for one interval) applied.
-__global__ void __launch_bounds__(128)
+// (bounded to [0.5, 2] for one interval) applied.  A warp per cell; its
+// moments are the exact fixed-point sums of the FP32 values the resident
+// cell kernels sum for a DEM cell (fixsum.cuh).
+constexpr int CA_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * CA_WARPS)
 k_closure_apply(DevState32 st, Phys<float> P, const int *off, const int *is_closure, const float *Yuse,
                 double *mom, double *win, double *tgt, int ncell, int N0, double dT, double share)
 {
-    __shared__ double red[4][NMOM];
-    const int c = blockIdx.x;
-    if (!is_closure[c]) return;
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * CA_WARPS + (threadIdx.x >> 5);
+    if (c >= ncell || !is_closure[c]) return;
     const int o = off[c], n = off[c + 1] - o;
     double *mo = mom + (size_t)c * NMOM;
     const double M = mo[1];
@@ -250,38 +297,50 @@ k_closure_apply(DevState32 st, Phys<float> P, const int *off, const int *is_clos
     const float s = (float)sc;
     const float du = (float)(dux + dT * y[0]), dv = (float)(duy + dT * y[1]), dww = (float)(dw + dT * y[2]);
     const float ubf = (float)ub, vbf = (float)vb;
-    double acc[NMOM];
-    for (int k = 0; k < NMOM; k++) acc[k] = 0.0;
-    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    for (int l = lane; l < n; l += 32) {
         const int i = o + l;
-        const float r = st.r[i] * s, h = st.h[i];
-        const float u = ubf + du + fs * (st.u[i] - ubf), v = vbf + dv + fs * (st.v[i] - vbf);
-        const float w = st.w[i] + dww;
-        st.r[i] = r;
-        st.u[i] = u;
-        st.v[i] = v;
-        st.w[i] = w;
-        const double m = (double)P.mass_c * r * r * h, I = (double)P.inertia_f * m * r * r;
-        acc[1] += m;
-        acc[2] += m * u;
-        acc[3] += m * v;
-        acc[4] += I;
-        acc[5] += I * w;
-        acc[6] += 3.14159265358979323846 * (double)r * r;
-        acc[7] += m * u * u;
-        acc[8] += m * v * v;
+        st.r[i] *= s;
+        st.u[i] = ubf + du + fs * (st.u[i] - ubf);
+        st.v[i] = vbf + dv + fs * (st.v[i] - vbf);
+        st.w[i] += dww;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = 1; k < NMOM; k++) {
-        double v = acc[k];
-        for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
-        if (lane == 0) red[warp][k] = v;
+    // moment columns 1-8 of the new state (each lane reads the floes it wrote)
+    auto val = [&](int i, int q) -> float {
+        const float r = st.r[i], h = st.h[i], m = P.mass_c * r * r * h, I = P.inertia_f * m * r * r;
+        switch (q) {
+        case 0: return m;
+        case 1: return m * st.u[i];
+        case 2: return m * st.v[i];
+        case 3: return I;
+        case 4: return I * st.w[i];
+        case 5: return 3.14159265358979323846f * r * r;
+        case 6: return m * st.u[i] * st.u[i];
+        default: return m * st.v[i] * st.v[i];
+        }
+    };
+    int e[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) e[q] = FIX_NONE;
+    for (int l = lane; l < n; l += 32)
+#pragma unroll
+        for (int q = 0; q < 8; q++) e[q] = max(e[q], fix_exp(fix_counted(val(o + l, q))));
+#pragma unroll
+    for (int q = 0; q < 8; q++) e[q] = __reduce_max_sync(0xffffffffu, e[q]);
+    long long a[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) a[q] = 0;
+    for (int l = lane; l < n; l += 32)
+#pragma unroll
+        for (int q = 0; q < 8; q++) a[q] += fix_val(fix_counted(val(o + l, q)), e[q]);
+    double t[NMOM];
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) a[q] += __shfl_xor_sync(0xffffffffu, a[q], d);
+        t[1 + q] = fix_total(a[q], e[q]);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t[NMOM];
+    if (lane == 0) {
         t[0] = n;
-        for (int k = 1; k < NMOM; k++) t[k] = red[0][k] + red[1][k] + red[2][k] + red[3][k];
         t[9] = t[1] * y[0];
         t[10] = t[1] * y[1];
         t[11] = t[4] * y[2];
@@ -299,11 +358,18 @@ k_closure_apply(DevState32 st, Phys<float> P, const int *off, const int *is_clos
 
 }  // namespace
 
+cudaError_t launch_ocean_at_centres(int ncell, const Geom &g, const Phys<double> &P, double *oc, cudaStream_t st)
+{
+    k_ocean_at_centres<<<(ncell + 127) / 128, 128, 0, st>>>(ncell, g, P, oc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_features(const double *mom, const double *tgt, int ncell, const Geom &g, const Phys<double> &P,
-                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, float *X, cudaStream_t st)
+                            const Ctrl *ctrl, double dt, int N0, int n_t, const float *Ylag, const double *oc,
+                            float *X, cudaStream_t st)
 {
     k_features<<<(ncell + 127) / 128, 128, 0, st>>>(mom, tgt, ncell, g, P, ctrl, dt, ramp_mean_share(N0, n_t), Ylag,
-                                                     X);
+                                                     oc, X);
     return cudaGetLastError();
 }
 
@@ -320,11 +386,16 @@ cudaError_t launch_collect_targets(const double *mom0, const double *mom1, const
 cudaError_t launch_hybrid_select(const HybridArgs &h, cudaStream_t st)
 {
     k_classify<<<(h.ncell + 127) / 128, 128, 0, st>>>(h.X, h.Yp, h.mom, h.ncell, h.P64, h.rho_ice, h.box, h.tol,
-                                                     h.mode, h.ctrl, h.nerr, h.age, h.is_closure, h.Yuse);
-    k_compact<<<h.nseg, 1024, 0, st>>>(h.order, h.seg_begin, h.seg_end, h.is_closure, h.order2, h.live,
-                                        h.closure_count);
-    k_closure_apply<<<h.ncell, 128, 0, st>>>(h.st32, h.P32, h.off, h.is_closure, h.Yuse, h.mom_rw, h.win, h.tgt,
-                                             h.ncell, h.N0, h.dT, ramp_mean_share(h.N0, h.n_t));
+                                                     h.mode, h.ctrl, h.nerr, h.age, h.is_closure, h.Yuse,
+                                                     h.closure_count);
+    if (h.nvgroups > 0)
+        k_group_veto<<<(h.nvgroups + 127) / 128, 128, 0, st>>>(h.vgroups, h.nvgroups, h.vitems, h.off, h.is_closure,
+                                                                h.closure_count);
+    if (h.seg_mask) k_compact<<<h.nseg, 1024, 0, st>>>(h.order, h.seg_begin, h.seg_end, h.is_closure, h.order2, h.live,
+                                                        h.seg_mask);
+    k_closure_apply<<<(h.ncell + CA_WARPS - 1) / CA_WARPS, 32 * CA_WARPS, 0, st>>>(
+        h.st32, h.P32, h.off, h.is_closure, h.Yuse, h.mom_rw, h.win, h.tgt, h.ncell, h.N0, h.dT,
+        ramp_mean_share(h.N0, h.n_t));
     return cudaGetLastError();
 }
 

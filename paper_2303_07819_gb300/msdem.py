@@ -63,7 +63,8 @@ SYMBOLS = ["ms_init", "ms_step", "ms_step_async", "ms_sync", "ms_moments", "ms_g
            "ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train", "ms_mlp_get_params",
            "ms_mlp_forward_device", "ms_mlp_free", "ms_closure_attach", "ms_closure_collect", "ms_closure_stats",
            "ms_probe_fp32", "ms_save", "ms_load", "ms_mlp_fit_norm", "ms_set_resident",
-           "ms_floe_cells", "ms_set_shard", "ms_shard_buffers", "ms_layout"]
+           "ms_floe_cells", "ms_set_shard", "ms_shard_buffers", "ms_layout", "ms_mlp_set_engine",
+           "ms_mlp_check"]
 
 
 def lib_path() -> str:
@@ -426,10 +427,13 @@ def _load_mlp():
     L.ms_mlp_get_params.argtypes = [vp, _fp]
     L.ms_mlp_forward_device.argtypes = [vp, vp, C.c_int64, vp, vp]
     L.ms_mlp_fit_norm.argtypes = [_fp, _fp, C.c_int64, _fp]
+    L.ms_mlp_set_engine.argtypes = [vp, C.c_int32]
+    L.ms_mlp_check.argtypes = [vp]
     L.ms_mlp_free.argtypes = [vp]
     L.ms_mlp_free.restype = None
     for n in ("ms_mlp_create", "ms_mlp_predict", "ms_mlp_grad", "ms_mlp_step", "ms_mlp_train",
-              "ms_mlp_get_params", "ms_mlp_forward_device", "ms_mlp_fit_norm"):
+              "ms_mlp_get_params", "ms_mlp_forward_device", "ms_mlp_fit_norm", "ms_mlp_set_engine",
+              "ms_mlp_check"):
         getattr(L, n).restype = C.c_int
     L._mlp_ready = True
     return L
@@ -476,6 +480,10 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+    def set_engine(self, engine: int) -> None:
+        """1: the tcgen05 inference kernel (default); 0: the mma.sync GEMMs."""
+        _check(_load_mlp().ms_mlp_set_engine(self._h, int(engine)))
 
     def predict(self, X) -> np.ndarray:
         X = _f32(X)

@@ -66,6 +66,40 @@ def test_forward_matches_oracle(ms):
     assert np.quantile(ez, 0.99) < 0.04, np.quantile(ez, 0.99, axis=0)
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 301, 40000])
+def test_tcgen05_forward_matches_oracle_and_mma(ms, n):
+    """The tcgen05 inference kernel (the default engine) against the FP64
+    oracle with the bounds of the tiled engine, and against the tiled
+    engine itself: both round activations to BF16 between layers, so they
+    differ only where an FP32 accumulation order flips a BF16 rounding.
+    Sizes: one cell, a tile less one, one tile, a ragged tail, many tiles
+    per CTA."""
+    X, Y = _data(1, n)
+    norm = CO.normalisation(_data(0, 301)[0], _data(0, 301)[1])
+    p = _params()
+    net = ms.MLP(p, norm, max_batch=65536)
+    got = net.predict(X)
+    net.set_engine(0)
+    mma = net.predict(X)
+    net.set_engine(1)
+    ref = CO.predict(p, X, norm)
+    ez = np.abs(got - ref) / norm["sd_y"]
+    assert ez.max() < 0.1, ez.max(0)
+    if n >= 128:
+        assert np.quantile(ez, 0.99) < 0.04, np.quantile(ez, 0.99, axis=0)
+    em = np.abs(got - mma) / norm["sd_y"]
+    assert np.median(em) < 1e-3 and em.max() < 0.05, (np.median(em), em.max())
+    net.close()
+
+
+def test_engine_choice_is_checked(ms):
+    X, Y = _data(0, 64)
+    net = ms.MLP(_params(), CO.normalisation(X, Y), max_batch=64)
+    with pytest.raises(ms.MsError):
+        net.set_engine(2)
+    net.close()
+
+
 @pytest.mark.parametrize("B", [64, 1000, 5000])
 def test_gradients_match_oracle(ms, B):
     """BF16 products with FP32 accumulation: each parameter's gradient within
