@@ -72,6 +72,33 @@ def profile_traffic():
     return float(rec["dram_bytes_per_interval"]), rec
 
 
+# FLOP per sample of the closure network (16 -> 128 -> 128 -> 128 -> 4):
+# forward 2 (16*128 + 2*128*128 + 128*4); training adds about twice that
+MLP_FWD_FLOP = 2 * (16 * 128 + 2 * 128 * 128 + 128 * 4)
+MLP_TRAIN_FLOP = 3 * MLP_FWD_FLOP
+
+
+def closure_inference_rate(net, X, n=256 * 256, reps=20):
+    """The network on a 256 x 256 grid's cells (features drawn from the
+    training set), device-timed over `reps` calls of the inference kernel."""
+    import torch
+    idx = np.random.default_rng(5).integers(0, X.shape[0], n)
+    Xd = torch.as_tensor(X[idx].astype(np.float32), device="cuda")
+    Yd = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        net.forward_device(Xd.data_ptr(), n, Yd.data_ptr(), st.cuda_stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        net.forward_device(Xd.data_ptr(), n, Yd.data_ptr(), st.cuda_stream)
+    b.record(st)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"cells": n, "ms_per_call": ms, "cells_per_s": n / (ms * 1e-3),
+            "tflops": n * MLP_FWD_FLOP / (ms * 1e-3) / 1e12, "engine": "tcgen05 (kind::f16, BF16, FP32 in TMEM)"}
+
+
 def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=20, K=10,
                  tols=(0.01, 0.015, 0.02, 0.025, 0.03, 0.05, 0.1, 0.2), target_err=1e-2, mode=0, epochs=40):
     """The learned closure on the timed workload.  Training data come from the
@@ -104,6 +131,7 @@ def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=20
     tt = time.perf_counter()
     losses = net.train(X, T, epochs=epochs, batch=1024, lr=2e-3, seed=3)
     t_train = time.perf_counter() - tt
+    infer = closure_inference_rate(net, X)
     box = np.stack([X.min(0) - 0.05 * np.abs(X.min(0)), X.max(0) + 0.05 * np.abs(X.max(0))])
     p, dt, N0 = s["params"], s["dt"], int(s["params"]["N0"])
     cells = p["nx"] * p["ny"]
@@ -147,10 +175,13 @@ def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=20
            "train": {"samples": int(X.shape[0]), "from": f"particle path, seeds {list(seeds)}, {nx_train}^2 cells, "
                                                           f"{nint} intervals after {spin} of spin-up",
                      "epochs": epochs, "seconds": t_train,
+                     "samples_per_s": epochs * int(X.shape[0]) / t_train,
+                     "tflops": epochs * int(X.shape[0]) * MLP_TRAIN_FLOP / t_train / 1e12,
                      "loss_first_last": [float(losses[0]), float(losses[-1])],
                      "mode": mode,
                      "heldout_r2_drag_x_y_torque_var": [float(v) for v in r2],
                      "heldout_r2_of_last_interval": [float(v) for v in r2_lag]},
+           "inference_256x256": infer,
            "particle": {"cell_steps_per_s": cells * N0 * K / tp}}
     qn, tn, _, _, _ = run(-1, 0.0, variant=4)
     out["noise_floor_other_reduction_order"] = {"coarse_state_rel_err": err(qn)}

@@ -400,9 +400,14 @@ int ms_mlp_grad(ms_mlp *m, const float *X, const float *Y, int64_t n, float *gra
 /* One Adam step of learning rate lr on one batch (n <= max_batch). */
 int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr);
 
-/* Train for `epochs` passes over host data (n samples) in batches of
- * `batch` (8 .. max_batch), reshuffled every epoch from `seed`;
- * loss_per_epoch (host [epochs], may be NULL) gets each epoch's mean loss. */
+/* Train for `epochs` passes over host data (n <= 2^30 samples) in batches of
+ * `batch` (8 .. max_batch; a last batch below 8 samples is left out of the
+ * epoch).  The data go to the device once; every epoch gathers them there in
+ * a new order -- a keyed permutation of [0, n) (four-round Feistel network
+ * with cycle walking, keys drawn from `seed` by SplitMix64) -- and replays one
+ * captured CUDA graph of the epoch's batches; the host waits only at the
+ * end.  loss_per_epoch (host [epochs], may be NULL) gets each epoch's mean
+ * loss.  The call allocates 80 n bytes of device memory for its duration. */
 int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, float lr,
                  uint64_t seed, double *loss_per_epoch);
 

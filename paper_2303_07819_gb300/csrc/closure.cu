@@ -261,9 +261,15 @@ struct LayerDev {
 };
 
 // Adam on one layer, then refresh its BF16 copies (both layouts)
-__global__ void k_adam(LayerDev L, float lr, float c1, float c2, float beta1, float beta2, float eps)
+// Adam's step count lives on the device (so that a captured training epoch
+// replays with the right bias corrections)
+__global__ void k_tick(long long *t) { *t += 1; }
+
+__global__ void k_adam(LayerDev L, float lr, const long long *tstep, float beta1, float beta2, float eps)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float tf = (float)*tstep;
+    const float c1 = 1.0f - powf(beta1, tf), c2 = 1.0f - powf(beta2, tf);
     const int nw = L.nout * L.nin;
     if (i < nw) {
         const int o = i / L.nin, k = i % L.nin;
@@ -287,6 +293,54 @@ __global__ void k_adam(LayerDev L, float lr, float c1, float c2, float beta1, fl
         L.b[o] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
     }
 }
+
+// ---- the training loop's shuffle: a keyed permutation of [0, n), a
+// four-round Feistel network on [0, 4^h) (4^h >= n), values past n walked
+// on through the network until they fall below n (cycle walking; the walk
+// returns to the domain because the start lies in it)
+
+// integer mixer ("lowbias32", a published 32-bit hash)
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int h, uint4 k)
+{
+    const uint32_t mask = (1u << h) - 1u;
+    uint32_t L = x >> h, R = x & mask;
+    const uint32_t key[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const uint32_t nL = R;
+        R = L ^ (mix32(R ^ key[r]) & mask);
+        L = nL;
+    }
+    return (L << h) | R;
+}
+
+// Xs[i], Ys[i] = X[p(i)], Y[p(i)] for the epoch's permutation p
+__global__ void k_gather_epoch(const float *X, const float *Y, long long n, int h, uint4 key, float *Xs, float *Ys)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t j = feistel((uint32_t)i, h, key);
+    while (j >= (uint32_t)n) j = feistel(j, h, key);
+#pragma unroll
+    for (int f = 0; f < NIN; f++) Xs[i * NIN + f] = X[(long long)j * NIN + f];
+#pragma unroll
+    for (int o = 0; o < NOUT; o++) Ys[i * NOUT + o] = Y[(long long)j * NOUT + o];
+}
+
+__global__ void k_set_epoch(int *ep, int v) { *ep = v; }
+
+// the batch's mean loss times its size into the current epoch's sum
+__global__ void k_add_loss(const double *loss, int B, const int *ep, double *eloss) { eloss[*ep] += *loss * B; }
 
 __global__ void k_cast_layer(LayerDev L)
 {
@@ -313,7 +367,9 @@ struct ms_mlp {
     bf16 *xh = nullptr, *xht = nullptr, *H[3] = {}, *Ht[3] = {}, *dZ[3] = {}, *dZt[3] = {}, *dy = nullptr,
          *dyt = nullptr;
     double *loss = nullptr;
-    long long t = 0;           // Adam steps
+    long long *d_t = nullptr;  // Adam steps (device)
+    double *d_eloss = nullptr; // per-epoch loss sums of ms_mlp_train (device)
+    int *d_ep = nullptr;       // the epoch being trained (device)
     int engine = 1;            // inference: 1 tcgen05 fused kernel, 0 tiled mma.sync GEMMs
     int sm_count = 0;
     int *tc_err = nullptr;     // set by the tcgen05 kernel if a wait ran out
@@ -475,7 +531,7 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         (e = mal(m, &m->yp, (size_t)Bp * NOP)) || (e = mal(m, &m->yout, (size_t)Bp * NOUT)) ||
         (e = mal(m, &m->xh, (size_t)Bp * KIN)) || (e = mal(m, &m->xht, (size_t)Bp * KIN)) ||
         (e = mal(m, &m->dy, (size_t)Bp * NOP)) || (e = mal(m, &m->dyt, (size_t)Bp * NOP)) || (e = mal(m, &m->loss, 1)) ||
-        (e = mal(m, &m->tc_err, 1)))
+        (e = mal(m, &m->tc_err, 1)) || (e = mal(m, &m->d_t, 1)) || (e = mal(m, &m->d_ep, 1)))
         return fail_free(ck(e, "cudaMalloc"));
     {
         int dev = 0;
@@ -674,12 +730,11 @@ static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float 
     if (e == cudaSuccess) e = backward(m, B, Bp);
     m->Y = const_cast<float *>(keepY);
     CKC(e);
-    m->t++;
     const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.0f - std::pow(b1, (float)m->t), c2 = 1.0f - std::pow(b2, (float)m->t);
+    k_tick<<<1, 1, 0, m->st>>>(m->d_t);
     for (int l = 0; l < 4; l++) {
         const int tot = m->L[l].nout * m->L[l].nin + m->L[l].nout;
-        k_adam<<<(tot + 255) / 256, 256, 0, m->st>>>(m->L[l], lr, c1, c2, b1, b2, 1e-8f);
+        k_adam<<<(tot + 255) / 256, 256, 0, m->st>>>(m->L[l], lr, m->d_t, b1, b2, 1e-8f);
     }
     return ck(cudaGetLastError(), "adam");
 }
@@ -702,58 +757,89 @@ int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t e
     if (!m || !X || !Y) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
     if (n < 1 || epochs < 0 || batch < 8 || batch > m->max_batch || !(lr > 0.0f))
         return ms_closure_fail(MS_ERR_ARG, "need n >= 1, epochs >= 0, 8 <= batch <= max_batch, lr > 0");
-    // the whole training set on the device, shuffled per epoch on the host
+    if (n > (int64_t)1 << 30) return ms_closure_fail(MS_ERR_ARG, "at most 2^30 samples");
+    // the training set on the device once; each epoch gathers it in the
+    // epoch's order on the device and replays one captured graph of its
+    // batches; the per-epoch losses stay on the device until the end
     float *Xd = nullptr, *Yd = nullptr, *Xs = nullptr, *Ys = nullptr;
+    double *el = nullptr;
     std::vector<void *> loc;
-    auto dm = [&](float **p, size_t cnt) {
-        cudaError_t e = cudaMalloc(p, sizeof(float) * cnt);
+    auto dm = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaMalloc(p, bytes);
         if (e == cudaSuccess) loc.push_back(*p);
         return e;
     };
-    auto cleanup = [&]() { for (void *p : loc) cudaFree(p); };
+    cudaGraphExec_t gexec = nullptr;
+    auto cleanup = [&]() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (void *p : loc) cudaFree(p);
+    };
     cudaError_t e;
-    if ((e = dm(&Xd, (size_t)n * NIN)) || (e = dm(&Yd, (size_t)n * NOUT)) || (e = dm(&Xs, (size_t)n * NIN)) ||
-        (e = dm(&Ys, (size_t)n * NOUT))) {
+    if ((e = dm((void **)&Xd, sizeof(float) * n * NIN)) || (e = dm((void **)&Yd, sizeof(float) * n * NOUT)) ||
+        (e = dm((void **)&Xs, sizeof(float) * n * NIN)) || (e = dm((void **)&Ys, sizeof(float) * n * NOUT)) ||
+        (e = dm((void **)&el, sizeof(double) * (epochs > 0 ? epochs : 1)))) {
         cleanup();
         return ck(e, "cudaMalloc");
     }
-    std::vector<float> hx(X, X + n * NIN), hy(Y, Y + n * NOUT), sx((size_t)n * NIN), sy((size_t)n * NOUT);
-    std::vector<int64_t> perm(n);
-    for (int64_t i = 0; i < n; i++) perm[i] = i;
-    uint64_t st = seed ? seed : 0x9E3779B97F4A7C15ull;
-    auto next = [&]() {   // SplitMix64
-        st += 0x9E3779B97F4A7C15ull;
-        uint64_t z = st;
+    int rc = MS_OK;
+    auto run = [&](cudaError_t x, const char *what) {
+        if (rc == MS_OK) rc = ck(x, what);
+    };
+    run(cudaMemcpyAsync(Xd, X, sizeof(float) * n * NIN, cudaMemcpyHostToDevice, m->st), "copy");
+    run(cudaMemcpyAsync(Yd, Y, sizeof(float) * n * NOUT, cudaMemcpyHostToDevice, m->st), "copy");
+    run(cudaMemsetAsync(el, 0, sizeof(double) * (epochs > 0 ? epochs : 1), m->st), "memset");
+    // Feistel domain 4^h >= n
+    int h = 1;
+    while (((int64_t)1 << (2 * h)) < n) h++;
+    uint64_t sm = seed ? seed : 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {   // SplitMix64: the epochs' keys
+        sm += 0x9E3779B97F4A7C15ull;
+        uint64_t z = sm;
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         return z ^ (z >> 31);
     };
-    int rc = MS_OK;
-    for (int ep = 0; ep < epochs && rc == MS_OK; ep++) {
-        for (int64_t i = n - 1; i > 0; i--) std::swap(perm[i], perm[(int64_t)(next() % (uint64_t)(i + 1))]);
-        for (int64_t i = 0; i < n; i++) {
-            std::memcpy(&sx[(size_t)i * NIN], &hx[(size_t)perm[i] * NIN], sizeof(float) * NIN);
-            std::memcpy(&sy[(size_t)i * NOUT], &hy[(size_t)perm[i] * NOUT], sizeof(float) * NOUT);
-        }
-        if ((rc = ck(cudaMemcpyAsync(Xs, sx.data(), sizeof(float) * sx.size(), cudaMemcpyHostToDevice, m->st), "copy")))
-            break;
-        if ((rc = ck(cudaMemcpyAsync(Ys, sy.data(), sizeof(float) * sy.size(), cudaMemcpyHostToDevice, m->st), "copy")))
-            break;
-        double lsum = 0.0;
-        int64_t nb = 0;
-        for (int64_t s0 = 0; s0 < n && rc == MS_OK; s0 += batch) {
+    // one epoch's batches (a ragged last batch below 8 samples is dropped)
+    int64_t used = 0;
+    auto batches = [&]() -> int {
+        used = 0;
+        for (int64_t s0 = 0; s0 < n; s0 += batch) {
             const int B = (int)std::min<int64_t>(batch, n - s0);
-            if (B < 8) break;   // a ragged last batch below one tile row group is dropped this epoch
-            rc = train_step(m, Xs + s0 * NIN, Ys + s0 * NOUT, B, lr);
-            if (rc == MS_OK && loss_per_epoch) {
-                double l = 0.0;
-                rc = ck(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st), "copy");
-                if (rc == MS_OK) rc = ck(cudaStreamSynchronize(m->st), "sync");
-                lsum += l * B;
-                nb += B;
-            }
+            if (B < 8) break;
+            const int r = train_step(m, Xs + s0 * NIN, Ys + s0 * NOUT, B, lr);
+            if (r) return r;
+            if (loss_per_epoch) k_add_loss<<<1, 1, 0, m->st>>>(m->loss, B, m->d_ep, el);
+            used += B;
         }
-        if (loss_per_epoch && nb) loss_per_epoch[ep] = lsum / nb;
+        return ck(cudaGetLastError(), "batch");
+    };
+    if (rc == MS_OK && epochs > 0) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int r = batches();
+            const cudaError_t ee = cudaStreamEndCapture(m->st, &g);
+            if (r == MS_OK && ee == cudaSuccess && g && cudaGraphInstantiate(&gexec, g, 0) != cudaSuccess)
+                gexec = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();   // a capture that failed leaves the direct launches below
+    }
+    for (int ep = 0; ep < epochs && rc == MS_OK; ep++) {
+        const uint64_t k1 = next(), k2 = next();
+        const uint4 key = make_uint4((uint32_t)k1, (uint32_t)(k1 >> 32), (uint32_t)k2, (uint32_t)(k2 >> 32));
+        k_gather_epoch<<<(unsigned)((n + 255) / 256), 256, 0, m->st>>>(Xd, Yd, n, h, key, Xs, Ys);
+        k_set_epoch<<<1, 1, 0, m->st>>>(m->d_ep, ep);
+        run(cudaGetLastError(), "gather");
+        if (rc) break;
+        if (gexec) run(cudaGraphLaunch(gexec, m->st), "epoch graph");
+        else rc = batches();
+    }
+    if (rc == MS_OK && loss_per_epoch && epochs > 0) {
+        std::vector<double> hl(epochs);
+        run(cudaMemcpyAsync(hl.data(), el, sizeof(double) * epochs, cudaMemcpyDeviceToHost, m->st), "copy");
+        run(cudaStreamSynchronize(m->st), "sync");
+        if (rc == MS_OK)
+            for (int ep = 0; ep < epochs; ep++) loss_per_epoch[ep] = used ? hl[ep] / (double)used : 0.0;
     }
     if (rc == MS_OK) rc = ck(cudaStreamSynchronize(m->st), "sync");
     cleanup();

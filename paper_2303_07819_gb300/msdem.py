@@ -481,6 +481,12 @@ class MLP:
         except Exception:
             pass
 
+    def forward_device(self, x_ptr: int, n: int, y_ptr: int, stream: int | None = None) -> None:
+        """Device X[n][16] -> device Y[n][4] (addresses as ints) on `stream`,
+        without waiting (ms_mlp_forward_device)."""
+        _check(_load_mlp().ms_mlp_forward_device(self._h, C.c_void_p(x_ptr), int(n), C.c_void_p(y_ptr),
+                                                 C.c_void_p(stream) if stream else None))
+
     def set_engine(self, engine: int) -> None:
         """1: the tcgen05 inference kernel (default); 0: the mma.sync GEMMs."""
         _check(_load_mlp().ms_mlp_set_engine(self._h, int(engine)))

@@ -142,3 +142,21 @@ def test_training_on_gpu_reduces_loss(ms):
     assert losses[-1] < 0.1 * losses[0], losses
     ref = CO.loss_and_grads(net.params(), X, Y, norm)[0]
     assert abs(ref - losses[-1]) < 0.5 * losses[-1] + 1e-3
+
+
+def test_every_epoch_visits_every_sample_once(ms):
+    """The device shuffle is a permutation: with a learning rate too small to
+    move the weights, each epoch's mean loss is the loss of the whole set,
+    to double rounding, although the set is gathered in a new order every
+    epoch.  The samples' residuals span many magnitudes, so a sample seen
+    twice or missed would move the mean far beyond that."""
+    n = 8192
+    X, Y = _data(9, n)
+    norm = CO.normalisation(X, Y)
+    Y = Y.copy()
+    Y[:, 0] += norm["sd_y"][0] * np.geomspace(1e-3, 30.0, n)[np.random.default_rng(2).permutation(n)]
+    net = ms.MLP(_params(), norm, max_batch=n)
+    full = net.grad(X, Y)[0]
+    losses = net.train(X, Y, epochs=3, batch=1024, lr=1e-30, seed=17)
+    assert np.allclose(losses, full, rtol=1e-9, atol=0.0), (losses, full)
+    net.close()
