@@ -422,6 +422,9 @@ def main():
                     help="the truth DEM of --workload alone: run N steps and exit (for ncu captures), "
                          "or with --truth-time time it")
     ap.add_argument("--truth-time", action="store_true", help="print the truth DEM's time per step")
+    ap.add_argument("--closure-infer", type=int, default=0,
+                    help="the closure network's inference kernel alone on N cells of synthetic features "
+                         "(random-init weights): time it and exit (for ncu captures)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -440,6 +443,16 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     msdem.load()
+    if args.closure_infer:
+        from paper_2303_07819_gb300 import inputs as I
+        rng = np.random.default_rng(3)
+        X = rng.normal(size=(4096, 16)).astype(np.float32)
+        Y = rng.normal(size=(4096, 4)).astype(np.float32)
+        net = msdem.MLP(I.mlp_init(), msdem.fit_norm(X, Y), max_batch=4096)
+        out = closure_inference_rate(net, X, n=args.closure_infer, reps=5)
+        net.close()
+        print(json.dumps(out), flush=True)
+        return
     if args.truth:
         tp = dict(s["params"], couple=0)
         tm = msdem.Model(tp, s["floes"], msdem.MS_FP32)
