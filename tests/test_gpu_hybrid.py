@@ -154,3 +154,41 @@ def test_closure_cells_skip_their_dem(trained):
         assert np.array_equal(f2[k][part], fa[k][part]), k
     a.close()
     b.close()
+
+
+def test_ensemble_with_switching_closure_against_oracle(trained, orc):
+    """Ensemble plus closure: two realizations of 32 x 32 cells (the batched
+    workload's laws, about 98k floes each) in one model, the network
+    attached after two coarse intervals, three more intervals in which cells
+    switch between the closure and the particle path.  Each realization's
+    coarse state against the FP64 oracle run of that realization alone
+    (particle path only): mass within 1e-3, momentum and angular momentum
+    within the closure's error scale; the same ensemble without the closure
+    is within the FP32 tolerance."""
+    msdem, net, X, Y, losses, box = trained
+    scens = [I.batched_128x128(seed=301 + e, nx=32) for e in range(2)]
+    for sc in scens[1:]:
+        sc["params"]["modes"] = scens[0]["params"]["modes"]
+    ens = I.stack_ensemble(scens)
+    dt, N0 = ens["dt"], ens["params"]["N0"]
+    nc = 32 * 32
+    qs = {}
+    for tol in (0.0, 0.1):
+        g = msdem.Model(ens["params"], ens["floes"], 0)
+        g.step(dt, 2 * N0)
+        g.closure_attach(net, 0, tol, box)
+        g.step(dt, 3 * N0)
+        st = g.closure_stats()
+        qs[tol] = (g.coupling()["q"], st["closure_cell_intervals"] / (2 * nc * 3))
+        g.close()
+    assert qs[0.0][1] == 0.0
+    assert 0.0 < qs[0.1][1] < 1.0, qs[0.1][1]
+    for e, sc in enumerate(scens):
+        o = orc.Model(sc["params"], sc["floes"])
+        o.step(dt, 5 * N0)
+        qo = o.coupling()["q"]
+        o.close()
+        for tol, bounds in ((0.0, (1e-5, 1e-2, 1e-2, 1e-2)), (0.1, (1e-3, 0.15, 0.15, 0.3))):
+            q = qs[tol][0][:, e * nc:(e + 1) * nc]
+            err = [np.linalg.norm(q[f] - qo[f]) / np.linalg.norm(qo[f]) for f in range(4)]
+            assert all(a <= b for a, b in zip(err, bounds)), (e, tol, err)
