@@ -258,6 +258,7 @@ struct LayerDev {
     float *mW, *vW, *mb, *vb;  // Adam moments
     float *gW, *gb;            // gradients [nop][kin] (padded), [nout]
     bf16 *Wb, *Wt;             // BF16 copies [nop][kin] and [kin][nop]
+    bf16 *Wc;                  // BF16 image of the tcgen05 inference kernel (tc_core_index layout)
 };
 
 // Adam on one layer, then refresh its BF16 copies (both layouts)
@@ -283,6 +284,7 @@ __global__ void k_adam(LayerDev L, float lr, const long long *tstep, float beta1
         const bf16 wb = __float2bfloat16_rn(w);
         L.Wb[o * L.kin + k] = wb;
         L.Wt[k * L.nop + o] = wb;
+        L.Wc[tc_core_index(o, k, L.kin)] = wb;
     } else if (i < nw + L.nout) {
         const int o = i - nw;
         const float g = L.gb[o];
@@ -351,6 +353,7 @@ __global__ void k_cast_layer(LayerDev L)
     const bf16 wb = __float2bfloat16_rn(w);
     L.Wb[i] = wb;
     L.Wt[k * L.nop + o] = wb;
+    L.Wc[tc_core_index(o, k, L.kin)] = wb;
 }
 
 }  // namespace
@@ -515,7 +518,8 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         if ((e = mal(m, &L.W, nw)) || (e = mal(m, &L.b, L.nout)) || (e = mal(m, &L.mW, nw)) ||
             (e = mal(m, &L.vW, nw)) || (e = mal(m, &L.mb, L.nout)) || (e = mal(m, &L.vb, L.nout)) ||
             (e = mal(m, &L.gW, (size_t)L.nop * L.kin)) || (e = mal(m, &L.gb, L.nout)) ||
-            (e = mal(m, &L.Wb, (size_t)L.nop * L.kin)) || (e = mal(m, &L.Wt, (size_t)L.nop * L.kin)))
+            (e = mal(m, &L.Wb, (size_t)L.nop * L.kin)) || (e = mal(m, &L.Wt, (size_t)L.nop * L.kin)) ||
+            (e = mal(m, &L.Wc, (size_t)tc_image_rows(l) * L.kin)))
             return fail_free(ck(e, "cudaMalloc"));
         if ((rc = ck(cudaMemcpyAsync(L.W, params + off, sizeof(float) * nw, cudaMemcpyHostToDevice, m->st), "copy")))
             return fail_free(rc);
@@ -609,14 +613,13 @@ int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *
         a.Y = Y;
         a.n = n;
         for (int l = 0; l < 4; l++) {
-            a.W[l] = m->L[l].Wb;
+            a.W[l] = m->L[l].Wc;
             a.b[l] = m->L[l].b;
         }
         a.mu_x = m->mu_x;
         a.sd_x = m->sd_x;
         a.mu_y = m->mu_y;
         a.sd_y = m->sd_y;
-        a.nout_pad = m->L[3].nop;
         a.err = m->tc_err;
         // two 107 KB CTAs fit an SM
         return ck(launch_mlp_forward_tc(a, 2 * m->sm_count, stream ? (cudaStream_t)stream : m->st), "tcgen05 forward");

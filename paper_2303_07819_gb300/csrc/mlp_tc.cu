@@ -18,8 +18,10 @@
 // byte offset (next core matrix along K) is 128 and its stride byte offset
 // (next 8 rows) is 16 K.
 //
-// Every wait on the mbarrier is bounded: a wait that runs out sets the error
-// word, waits once more (bounded) for the chain in flight, and the CTA frees
+// The weights arrive by four cp.async.bulk copies of their images (kept in
+// global memory in this layout by the trainer) completing on an mbarrier.
+// Every wait on an mbarrier is bounded: a wait that runs out sets the error
+// word, waits once more (bounded) for the work in flight, and the CTA frees
 // its tensor memory and stops.
 #include <cuda_bf16.h>
 #include <cstdint>
@@ -49,6 +51,7 @@ struct TcSmem {
     float b[3][TC_NH], b3[TC_NO];
     float mux[TC_KIN], sdx[TC_KIN], muy[4], sdy[4];
     unsigned long long bar;        // mbarrier of the MMA chains
+    unsigned long long wbar;       // mbarrier of the weights' bulk copies
     uint32_t tbase;                // tensor-memory address from tcgen05.alloc
 };
 
@@ -128,16 +131,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// one global [R][Kg] row-major BF16 matrix into shared memory, core-matrix
-// layout of R x K (rows past Rg and columns past Kg zero), 16-byte pieces
-__device__ void load_weights(bf16 *dst, const bf16 *src, int Rg, int Kg, int R, int K)
+// one bulk copy global -> shared, completing on the mbarrier's transaction
+// count (addresses 16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    for (int c = threadIdx.x; c < R * (K / 8); c += TC_T) {
-        const int r = c / (K / 8), j = c % (K / 8);
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (r < Rg && 8 * j < Kg) v = *reinterpret_cast<const uint4 *>(src + (size_t)r * Kg + 8 * j);
-        *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(dst) + core_off(r, 8 * j, K)) = v;
-    }
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
 __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
@@ -145,10 +144,19 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
     extern __shared__ __align__(128) unsigned char tc_raw[];
     TcSmem &S = *reinterpret_cast<TcSmem *>(tc_raw);
     const int t = threadIdx.x, warp = t >> 5;
-    load_weights(S.W0, a.W[0], TC_NH, TC_KIN, TC_NH, TC_KIN);
-    load_weights(S.W1, a.W[1], TC_NH, TC_NH, TC_NH, TC_NH);
-    load_weights(S.W2, a.W[2], TC_NH, TC_NH, TC_NH, TC_NH);
-    load_weights(S.W3, a.W[3], a.nout_pad, TC_NH, TC_NO, TC_NH);
+    // the weight images by four bulk copies on their own mbarrier
+    const uint32_t wbar = smem_u32(&S.wbar);
+    constexpr uint32_t wbytes[4] = {TC_NH * TC_KIN * 2, TC_NH * TC_NH * 2, TC_NH * TC_NH * 2, TC_NO * TC_NH * 2};
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(wbar), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(wbar), "r"(wbytes[0] + wbytes[1] + wbytes[2] + wbytes[3]) : "memory");
+        bulk_g2s(smem_u32(S.W0), a.W[0], wbytes[0], wbar);
+        bulk_g2s(smem_u32(S.W1), a.W[1], wbytes[1], wbar);
+        bulk_g2s(smem_u32(S.W2), a.W[2], wbytes[2], wbar);
+        bulk_g2s(smem_u32(S.W3), a.W[3], wbytes[3], wbar);
+    }
     for (int i = t; i < 3 * TC_NH; i += TC_T) S.b[i / TC_NH][i % TC_NH] = a.b[i / TC_NH][i % TC_NH];
     if (t < TC_NO) S.b3[t] = t < 4 ? a.b[3][t] : 0.0f;
     if (t < TC_KIN) {
@@ -173,11 +181,13 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
     fence_before();
     __syncthreads();
     fence_after();
+    // the weights in shared memory (every thread waits; the same verdict for all)
+    bool ok = __syncthreads_and(bar_wait(wbar, 0u) ? 1 : 0) != 0;
     const uint32_t tmem = S.tbase;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
     const uint32_t sA = smem_u32(S.A), sW[4] = {smem_u32(S.W0), smem_u32(S.W1), smem_u32(S.W2), smem_u32(S.W3)};
     uint32_t phase = 0;
-    bool ok = true;
+    const bool weights_ok = ok;
     const int ntiles = (a.n + TC_T - 1) / TC_T;
     unsigned char *Ab = reinterpret_cast<unsigned char *>(S.A);
 
@@ -242,7 +252,8 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
     }
     if (!ok) {
         if (t == 0) atomicOr(a.err, 1);
-        bar_wait(bar, phase);      // the chain in flight, if it still completes
+        if (weights_ok) bar_wait(bar, phase);   // the chain in flight, if it still completes
+        else bar_wait(wbar, 0u);                // the copies in flight, if they still complete
     }
     fence_before();
     __syncthreads();
