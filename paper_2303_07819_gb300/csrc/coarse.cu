@@ -13,11 +13,18 @@
 // cell (rho, rho v_y, P_omega equal; rho v_x and <v_x> of opposite sign), so
 // no mass crosses the wall.
 //
-// N1 is chosen on the device (it depends on the window data), so the step is
-// a fixed sequence of launches (prepare, NSUB_MAX substeps that return at once
-// past N1, targets, finish) and can be captured in a CUDA graph.
+// N1 is chosen on the device (it depends on the window data).  The step is
+// one cooperative launch whose blocks pass each phase (prepare, the N1
+// substeps, targets, finish) together with grid-wide barriers between them,
+// so it fits a CUDA graph as a single node; a device that cannot hold the
+// cooperative grid takes the phases as a fixed sequence of launches (NSUB_MAX
+// substeps that return at once past N1).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "shard.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace msd {
 
@@ -32,11 +39,9 @@ __device__ __forceinline__ int n_sub(const CoarseArgs &a, int e)
     return N1 < 1 ? 1 : N1;
 }
 
-__global__ void k_coarse_prepare(CoarseArgs a)
+__device__ __forceinline__ void coarse_prepare_cell(const CoarseArgs &a, int c)
 {
     const int nc = a.nx * a.ny;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
     const double *mo = a.mom + (size_t)c * NMOM;
     if (!a.ctrl->have_q) {
         // initialise the coarse model from the DEM data (Sec. 3.2)
@@ -59,11 +64,9 @@ __global__ void k_coarse_prepare(CoarseArgs a)
     atomicMax(&a.cmax[c / (a.nx * a.nyr)], (unsigned long long)__double_as_longlong(cc));
 }
 
-__global__ void k_coarse_lf(CoarseArgs a, int k)
+__device__ __forceinline__ void coarse_lf_cell(const CoarseArgs &a, int k, int c)
 {
     const int nx = a.nx, ny = a.nyr, nc = nx * a.ny;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
     const int e = c / (nx * ny);
     const int N1 = n_sub(a, e);
     if (k >= N1) return;
@@ -99,11 +102,9 @@ __global__ void k_coarse_lf(CoarseArgs a, int k)
 // Targets of the gradual update (Sec. 3.3).  reading: the radius scale s
 // makes the cell mass equal rho* A_c; the uniform velocity and spin increments
 // make the scaled cell's momentum and angular momentum equal the coarse ones.
-__global__ void k_coarse_targets(CoarseArgs a)
+__device__ __forceinline__ void coarse_targets_cell(const CoarseArgs &a, int c)
 {
     const int nc = a.nx * a.ny;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
     const int N1 = n_sub(a, c / (a.nx * a.nyr));
     const double *q = ((N1 < NSUB_MAX ? N1 : NSUB_MAX) & 1) ? a.q1 : a.q0;
     double qc[4];
@@ -131,7 +132,7 @@ __global__ void k_coarse_targets(CoarseArgs a)
     a.tgt[3 * nc + c] = dw;
 }
 
-__global__ void k_coarse_finish(CoarseArgs a)
+__device__ __forceinline__ void coarse_finish(const CoarseArgs &a)
 {
     int N1 = 1;
     for (int e = 0; e < a.nens; e++) {
@@ -145,6 +146,59 @@ __global__ void k_coarse_finish(CoarseArgs a)
     ctrl->have_q = 1;
     ctrl->have_tgt = 1;
     ctrl->base += a.N0;
+}
+
+// the phases as separate launches (a thread per cell)
+__global__ void k_coarse_prepare(CoarseArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < a.nx * a.ny) coarse_prepare_cell(a, c);
+}
+
+__global__ void k_coarse_lf(CoarseArgs a, int k)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < a.nx * a.ny) coarse_lf_cell(a, k, c);
+}
+
+__global__ void k_coarse_targets(CoarseArgs a)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < a.nx * a.ny) coarse_targets_cell(a, c);
+}
+
+__global__ void k_coarse_finish(CoarseArgs a) { coarse_finish(a); }
+
+// The whole coarse step in one cooperative launch: every block runs each
+// phase over a grid-stride share of the cells, with a grid-wide barrier
+// between phases (each substep reads the neighbours the one before wrote),
+// and the substeps stop at the largest N1 of the realizations.
+constexpr int CF_T = 256;
+
+__global__ void __launch_bounds__(CF_T) k_coarse_fused(CoarseArgs a)
+{
+    cg::grid_group grid = cg::this_grid();
+    const int nc = a.nx * a.ny;
+    const int c0 = blockIdx.x * blockDim.x + threadIdx.x, cs = gridDim.x * blockDim.x;
+    for (int c = c0; c < nc; c += cs) coarse_prepare_cell(a, c);
+    grid.sync();
+    // the largest substep count over the realizations (every block the same)
+    __shared__ int n1s[CF_T / 32];
+    int n1 = 1;
+    for (int e = threadIdx.x; e < a.nens; e += CF_T) n1 = max(n1, n_sub(a, e));
+    for (int d = 16; d > 0; d >>= 1) n1 = max(n1, __shfl_xor_sync(0xffffffffu, n1, d));
+    if ((threadIdx.x & 31) == 0) n1s[threadIdx.x >> 5] = n1;
+    __syncthreads();
+    int n1max = 1;
+    for (int w = 0; w < CF_T / 32; w++) n1max = max(n1max, n1s[w]);
+    n1max = min(n1max, NSUB_MAX);
+    for (int k = 0; k < n1max; k++) {
+        for (int c = c0; c < nc; c += cs) coarse_lf_cell(a, k, c);
+        grid.sync();
+    }
+    for (int c = c0; c < nc; c += cs) coarse_targets_cell(a, c);
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) coarse_finish(a);
 }
 
 __global__ void k_advance(Ctrl *ctrl, int N0) { ctrl->base += N0; }
@@ -192,11 +246,33 @@ cudaError_t launch_shard_scatter(double *mom, double *win, int nc, const int *ce
     return cudaGetLastError();
 }
 
-int coarse_launches() { return NSUB_MAX + 3; }
+int coarse_launches() { return 1; }
+
+// grid of the fused coarse step: as many blocks as the device holds at once
+// (a cooperative launch needs them all resident), at most one per 256 cells
+static int coarse_fused_grid(int nc)
+{
+    static int per_sm = -1, nsm = 0;
+    if (per_sm < 0) {
+        int dev = 0, b = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_coarse_fused, CF_T, 0) != cudaSuccess) b = 0;
+        per_sm = b;
+    }
+    const int need = (nc + CF_T - 1) / CF_T, most = per_sm * nsm;
+    return need < most ? need : most;
+}
 
 cudaError_t launch_coarse_step(const CoarseArgs &a, cudaStream_t st)
 {
     const int nc = a.nx * a.ny;
+    const int G = coarse_fused_grid(nc);
+    if (G > 0) {
+        void *args[] = {const_cast<CoarseArgs *>(&a)};
+        return cudaLaunchCooperativeKernel((const void *)k_coarse_fused, dim3(G), dim3(CF_T), args, 0, st);
+    }
+    // the phases launch by launch (a device that cannot hold a cooperative grid)
     const int T = 256, B = (nc + T - 1) / T;
     k_coarse_prepare<<<B, T, 0, st>>>(a);
     for (int k = 0; k < NSUB_MAX; k++) k_coarse_lf<<<B, T, 0, st>>>(a, k);

@@ -423,7 +423,7 @@ struct CoarseArgs {
     double *tgt;        // [4][ncell]
     Ctrl *ctrl;
 };
-cudaError_t launch_coarse_step(const CoarseArgs &a, cudaStream_t st);   // NSUB_MAX + 3 launches
+cudaError_t launch_coarse_step(const CoarseArgs &a, cudaStream_t st);   // one cooperative launch
 cudaError_t fma_probe(int reps, double *tflops);                          // probe.cu
 cudaError_t launch_advance(Ctrl *ctrl, int N0, cudaStream_t st);       // base += N0
 int coarse_launches();
