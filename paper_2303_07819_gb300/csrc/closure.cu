@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "mlp_tc.cuh"
+#include "tc_ptx.cuh"
 #include "../../include/msdem.h"
 
 namespace msd {
@@ -170,6 +171,232 @@ k_gemm(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda, con
         }
 }
 
+// The same product on the tcgen05 tensor cores: a CTA of 128 threads takes
+// a 128 x 64 tile of C (rows past M and columns past N are not written; the
+// MMA's N is the tile's columns padded to a multiple of 16) over the k-slice
+// of blockIdx.z.  The threads stage 64-wide k chunks of A and B into shared
+// memory in the core-matrix layout, two buffers deep, and one thread issues
+// one tcgen05.mma (K = 16) per 16 k of the chunk into a 64-column FP32
+// accumulator in tensor memory; a chunk's commit to its buffer's mbarrier
+// frees that buffer, so staging chunk c + 1 overlaps the MMAs of chunk c.
+// The epilogue reads a row per thread (tcgen05.ld) and applies the same EPI
+// as k_gemm, with 16-byte row stores and four-wide atomic adds.  A wait that
+// runs out sets *err; the CTA then waits (bounded) for the MMAs in flight,
+// frees its tensor memory and stops.  49 KB of shared memory per CTA keeps at
+// most four CTAs (256 of the 512 tensor-memory columns) on an SM.
+constexpr int TCG_T = 128, TCG_BK = 64, TCG_NT = 64;
+
+struct TcgSmem {
+    bf16 A[2][TCG_T * TCG_BK];       // 128 x 64 per buffer, core-matrix layout
+    bf16 B[2][TCG_NT * TCG_BK];      // 64 x 64
+    unsigned long long bar[2];       // MMA chunk done, per buffer
+    uint32_t tbase;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(TCG_T)
+k_gemm_tc(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
+          EpiArgs ea, int *err)
+{
+    using namespace tcx;
+    extern __shared__ __align__(128) unsigned char tcg_raw[];
+    TcgSmem &S = *reinterpret_cast<TcgSmem *>(tcg_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int m0 = blockIdx.x * TCG_T, n0 = blockIdx.y * TCG_NT;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int nch = kend > kbeg ? (kend - kbeg + TCG_BK - 1) / TCG_BK : 0;
+    const int Nt = min(TCG_NT, N - n0), Np = (Nt + 15) / 16 * 16;
+    const uint32_t bar0 = smem_u32(&S.bar[0]), bar1 = smem_u32(&S.bar[1]);
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar0), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar1), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&S.tbase)), "r"(TCG_NT));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tbase;
+    // per buffer: the phase of its next commit and whether one is unwaited
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool pend0 = false, pend1 = false;
+    bool ok = true;
+    for (int c = 0; c < nch && ok; c++) {
+        const int b = c & 1, k0 = kbeg + c * TCG_BK;
+        const uint32_t bar = b ? bar1 : bar0;
+        if (b ? pend1 : pend0) {
+            // buffer b is free once chunk c - 2's MMAs are done
+            const uint32_t ph = b ? ph1 : ph0;
+            ok = __syncthreads_and(bar_wait(bar, ph) ? 1 : 0) != 0;
+            if (!ok) break;
+            if (b) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
+            fence_after();
+        }
+        unsigned char *Ab = reinterpret_cast<unsigned char *>(S.A[b]), *Bb = reinterpret_cast<unsigned char *>(S.B[b]);
+        // 16-byte pieces, all loads first: rows past M (N) and k past the slice read as zero
+        constexpr int PA = TCG_T * (TCG_BK / 8) / TCG_T, PB = TCG_NT * (TCG_BK / 8) / TCG_T;
+        uint4 va[PA], vb[PB];
+#pragma unroll
+        for (int i = 0; i < PA; i++) {
+            const int q = t + i * TCG_T, r = q / (TCG_BK / 8), gk = k0 + 8 * (q % (TCG_BK / 8));
+            va[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (m0 + r < M && gk < kend) va[i] = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + gk);
+        }
+#pragma unroll
+        for (int i = 0; i < PB; i++) {
+            const int q = t + i * TCG_T, r = q / (TCG_BK / 8), gk = k0 + 8 * (q % (TCG_BK / 8));
+            vb[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (r < Nt && gk < kend) vb[i] = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + gk);
+        }
+#pragma unroll
+        for (int i = 0; i < PA; i++) {
+            const int q = t + i * TCG_T;
+            *reinterpret_cast<uint4 *>(Ab + core_off(q / (TCG_BK / 8), 8 * (q % (TCG_BK / 8)), TCG_BK)) = va[i];
+        }
+#pragma unroll
+        for (int i = 0; i < PB; i++) {
+            const int q = t + i * TCG_T;
+            *reinterpret_cast<uint4 *>(Bb + core_off(q / (TCG_BK / 8), 8 * (q % (TCG_BK / 8)), TCG_BK)) = vb[i];
+        }
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (t == 0) {
+            const uint32_t id = idesc_bf16(TCG_T, Np), sA = smem_u32(S.A[b]), sB = smem_u32(S.B[b]);
+            const int nk = min(TCG_BK / 16, (kend - k0 + 15) / 16);   // k past the slice is zero
+            for (int kk = 0; kk < nk; kk++)
+                mma_issue(tmem, sdesc(sA + kk * 256, 128, 16 * TCG_BK), sdesc(sB + kk * 256, 128, 16 * TCG_BK), id,
+                          (c > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(bar);
+        }
+        if (b) pend1 = true; else pend0 = true;
+    }
+    if (ok && nch > 0) {
+        // the last chunk's commit covers every MMA before it
+        const int b = (nch - 1) & 1;
+        ok = __syncthreads_and(bar_wait(b ? bar1 : bar0, b ? ph1 : ph0) ? 1 : 0) != 0;
+        if (ok) pend0 = pend1 = false;
+        fence_after();
+    }
+    if (ok && nch > 0) {
+        const int m = m0 + t;
+        const bool row = m < M;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c0 = 0; c0 < Np; c0 += 16) {
+            float v[16];
+            tmem_ld16(lane_addr + c0, v);
+            const int nb = n0 + c0;
+            const bool full = nb + 16 <= N;
+            if (EPI == EPI_TANH || EPI == EPI_DZ) {
+                float cs[16];
+                __align__(16) bf16 o[16];
+                if (row) {
+                    if (EPI == EPI_DZ && full) {
+                        __align__(16) bf16 hh[16];
+                        const uint4 *hp = reinterpret_cast<const uint4 *>(ea.h + (size_t)m * ea.ldo + nb);
+                        reinterpret_cast<uint4 *>(hh)[0] = hp[0];
+                        reinterpret_cast<uint4 *>(hh)[1] = hp[1];
+#pragma unroll
+                        for (int i = 0; i < 16; i++) {
+                            const float h = __bfloat162float(hh[i]);
+                            cs[i] = v[i] * (1.0f - h * h);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const int n = nb + i;
+                        if (EPI == EPI_TANH) {
+                            cs[i] = 0.0f;
+                            o[i] = __float2bfloat16_rn(n < N ? tanhf(v[i] + ea.bias[n]) : 0.0f);
+                        } else {
+                            if (!full) {
+                                const float h = n < N ? __bfloat162float(ea.h[(size_t)m * ea.ldo + n]) : 0.0f;
+                                cs[i] = n < N ? v[i] * (1.0f - h * h) : 0.0f;
+                            }
+                            o[i] = __float2bfloat16_rn(cs[i]);
+                        }
+                    }
+                    if (full) {
+                        uint4 *op = reinterpret_cast<uint4 *>(ea.out + (size_t)m * ea.ldo + nb);
+                        op[0] = reinterpret_cast<const uint4 *>(o)[0];
+                        op[1] = reinterpret_cast<const uint4 *>(o)[1];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        const int n = nb + i;
+                        if (n < N) {
+                            if (!full) ea.out[(size_t)m * ea.ldo + n] = o[i];
+                            ea.outT[(size_t)n * ea.ldt + m] = o[i];
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++) cs[i] = 0.0f;
+                }
+                if (EPI == EPI_DZ) {
+                    // bias gradient: each column over the warp's 32 rows, one atomic per column
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        float x = cs[i];
+#pragma unroll
+                        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+                        if (lane == 0 && nb + i < N) atomicAdd(&ea.bgrad[nb + i], x);
+                    }
+                }
+            } else if (row) {
+                float *p = ea.f32 + (size_t)m * ea.ldf + nb;
+                if (EPI == EPI_LIN) {
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        if (nb + i < N) p[i] = v[i] + (nb + i < ea.n_real ? ea.bias[nb + i] : 0.0f);
+                } else if (full) {
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4) {
+                        const float4 x = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                        if (ea.atomic) atomicAdd(reinterpret_cast<float4 *>(p + i), x);
+                        else *reinterpret_cast<float4 *>(p + i) = x;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; i++)
+                        if (nb + i < N) {
+                            if (ea.atomic) atomicAdd(p + i, v[i]);
+                            else p[i] = v[i];
+                        }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(err, 1);
+        // the MMAs in flight, if they still complete (at most one commit per buffer)
+        if (pend0) bar_wait(bar0, ph0);
+        if (pend1) bar_wait(bar1, ph1);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCG_NT));
+}
+
+cudaError_t gemm_tc_prepare()
+{
+    const int sz = (int)sizeof(TcgSmem);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_gemm_tc<EPI_TANH>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
+        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
+        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
+        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)))
+        return e;
+    return cudaSuccess;
+}
+
 // raw features -> z-scored BF16, [B][KIN] and [KIN][B] (padding columns 0)
 __global__ void k_prep_input(const float *X, int B, int Bp, const float *mu, const float *sd, bf16 *xh, bf16 *xht)
 {
@@ -185,12 +412,13 @@ __global__ void k_prep_input(const float *X, int B, int Bp, const float *mu, con
 }
 
 // z-scored residual of the outputs: loss sum, dL/dy in both layouts, output
-// bias gradient
+// bias gradient (summed over the warp first: one atomic per warp and output)
 __global__ void k_loss_grad(const float *yp, const float *Y, int B, int Bp, const float *mu, const float *sd,
                             bf16 *dy, bf16 *dyt, float *b4grad, double *loss)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
+    float gs[NOUT] = {};
     if (s < Bp) {
         for (int o = 0; o < NOP; o++) {
             float g = 0.0f;
@@ -198,7 +426,7 @@ __global__ void k_loss_grad(const float *yp, const float *Y, int B, int Bp, cons
                 const float r = yp[(size_t)s * NOP + o] - (Y[(size_t)s * NOUT + o] - mu[o]) / sd[o];
                 l += (double)r * r;
                 g = 2.0f * r / (4.0f * (float)B);
-                atomicAdd(&b4grad[o], g);
+                gs[o] = g;
             }
             const bf16 b = __float2bfloat16_rn(g);
             dy[(size_t)s * NOP + o] = b;
@@ -206,7 +434,15 @@ __global__ void k_loss_grad(const float *yp, const float *Y, int B, int Bp, cons
         }
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l / (4.0 * B));
+#pragma unroll
+    for (int q = 0; q < NOUT; q++)
+        for (int o = 16; o > 0; o >>= 1) gs[q] += __shfl_xor_sync(0xffffffffu, gs[q], o);
+    if ((threadIdx.x & 31) == 0) {
+        if (l != 0.0) atomicAdd(loss, l / (4.0 * B));
+#pragma unroll
+        for (int q = 0; q < NOUT; q++)
+            if (gs[q] != 0.0f) atomicAdd(&b4grad[q], gs[q]);
+    }
 }
 
 // z-scored outputs -> physical units
@@ -373,7 +609,7 @@ struct ms_mlp {
     long long *d_t = nullptr;  // Adam steps (device)
     double *d_eloss = nullptr; // per-epoch loss sums of ms_mlp_train (device)
     int *d_ep = nullptr;       // the epoch being trained (device)
-    int engine = 1;            // inference: 1 tcgen05 fused kernel, 0 tiled mma.sync GEMMs
+    int engine = 1;            // 1: tcgen05 (fused inference kernel, training GEMMs), 0: mma.sync tiles
     int sm_count = 0;
     int *tc_err = nullptr;     // set by the tcgen05 kernel if a wait ran out
     cudaStream_t st = nullptr;
@@ -397,9 +633,29 @@ static cudaError_t mal(ms_mlp *m, T **p, size_t n)
     return cudaMemsetAsync(q, 0, sizeof(T) * (n ? n : 1), m->st);
 }
 
-static cudaError_t gemm(int epi, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb, const EpiArgs &ea,
-                        cudaStream_t st, int ksplit = 1)
+// C = A B^T with epilogue epi on the MLP's stream: the tcgen05 kernel when
+// the MLP's engine is 1, else the mma.sync tiles
+static cudaError_t gemm(const ms_mlp *m, int epi, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
+                        const EpiArgs &ea, int ksplit = 1)
 {
+    cudaStream_t st = m->st;
+    if (m->engine == 1) {
+        const int tiles = ((M + TCG_T - 1) / TCG_T) * ((N + TCG_NT - 1) / TCG_NT);
+        if (ksplit > 1) {
+            // split k until the grid covers the SMs, a 64-wide chunk at least per slice
+            ksplit = std::max(1, std::min((K + TCG_BK - 1) / TCG_BK, (m->sm_count + tiles - 1) / tiles));
+        }
+        const int kchunk = ((K + ksplit - 1) / ksplit + TCG_BK - 1) / TCG_BK * TCG_BK;
+        dim3 grid((M + TCG_T - 1) / TCG_T, (N + TCG_NT - 1) / TCG_NT, (K + kchunk - 1) / kchunk);
+        const size_t sm = sizeof(TcgSmem);
+        switch (epi) {
+        case EPI_TANH: k_gemm_tc<EPI_TANH><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
+        case EPI_LIN: k_gemm_tc<EPI_LIN><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
+        case EPI_DZ: k_gemm_tc<EPI_DZ><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
+        default: k_gemm_tc<EPI_F32><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
+        }
+        return cudaGetLastError();
+    }
     const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, (K + kchunk - 1) / kchunk);
     switch (epi) {
@@ -424,7 +680,7 @@ static cudaError_t forward(ms_mlp *m, int Bp)
         ea.outT = m->Ht[l];
         ea.ldo = NH;
         ea.ldt = Bp;
-        if ((e = gemm(EPI_TANH, Bp, NH, LKIN[l], in, ldin, m->L[l].Wb, LKIN[l], ea, m->st)) != cudaSuccess) return e;
+        if ((e = gemm(m, EPI_TANH, Bp, NH, LKIN[l], in, ldin, m->L[l].Wb, LKIN[l], ea)) != cudaSuccess) return e;
         in = m->H[l];
         ldin = NH;
     }
@@ -433,7 +689,7 @@ static cudaError_t forward(ms_mlp *m, int Bp)
     ea.f32 = m->yp;
     ea.ldf = NOP;
     ea.n_real = NOUT;
-    return gemm(EPI_LIN, Bp, NOP, NH, in, NH, m->L[3].Wb, NH, ea, m->st);
+    return gemm(m, EPI_LIN, Bp, NOP, NH, in, NH, m->L[3].Wb, NH, ea);
 }
 
 // gradients of the batch loss (z-scored units) into the layers' gW, gb
@@ -457,7 +713,7 @@ static cudaError_t backward(ms_mlp *m, int B, int Bp)
         eg.f32 = m->L[l].gW;
         eg.ldf = LKIN[l];
         eg.atomic = ks > 1;
-        if ((e = gemm(EPI_F32, LOUT[l], LKIN[l], Bp, dzt, Bp, xt, Bp, eg, m->st, ks)) != cudaSuccess) return e;
+        if ((e = gemm(m, EPI_F32, LOUT[l], LKIN[l], Bp, dzt, Bp, xt, Bp, eg, ks)) != cudaSuccess) return e;
         if (l == 0) break;
         // dH_{l} = dz W_l -> dZ_{l-1} = dH (1 - h^2), plus its bias gradient
         EpiArgs ed{};
@@ -467,7 +723,7 @@ static cudaError_t backward(ms_mlp *m, int B, int Bp)
         ed.ldo = NH;
         ed.ldt = Bp;
         ed.bgrad = m->L[l - 1].gb;
-        if ((e = gemm(EPI_DZ, Bp, NH, LNOP[l], dz, ldz, m->L[l].Wt, LNOP[l], ed, m->st)) != cudaSuccess) return e;
+        if ((e = gemm(m, EPI_DZ, Bp, NH, LNOP[l], dz, ldz, m->L[l].Wt, LNOP[l], ed)) != cudaSuccess) return e;
         dz = m->dZ[l - 1];
         dzt = m->dZt[l - 1];
         ldz = NH;
@@ -541,7 +797,8 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         int dev = 0;
         if ((rc = ck(cudaGetDevice(&dev), "device")) ||
             (rc = ck(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev), "attribute")) ||
-            (rc = ck(mlp_tc_prepare(), "tcgen05 kernel attribute")))
+            (rc = ck(mlp_tc_prepare(), "tcgen05 kernel attribute")) ||
+            (rc = ck(gemm_tc_prepare(), "tcgen05 kernel attribute")))
             return fail_free(rc);
     }
     for (int l = 0; l < 3; l++)
@@ -703,7 +960,8 @@ int ms_mlp_grad(ms_mlp *m, const float *X, const float *Y, int64_t n, float *gra
     CKC(backward(m, B, Bp));
     if (loss) CKC(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     CKC(cudaStreamSynchronize(m->st));
-    return gather_grads(m, grads);
+    const int rc = gather_grads(m, grads);
+    return rc ? rc : ms_mlp_check(m);
 }
 
 int ms_mlp_get_params(ms_mlp *m, float *params)
@@ -751,7 +1009,7 @@ int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr)
     int rc = train_step(m, m->X, m->Y, (int)n, lr);
     if (rc) return rc;
     CKC(cudaStreamSynchronize(m->st));
-    return MS_OK;
+    return ms_mlp_check(m);
 }
 
 int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, float lr,
@@ -846,7 +1104,7 @@ int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t e
     }
     if (rc == MS_OK) rc = ck(cudaStreamSynchronize(m->st), "sync");
     cleanup();
-    return rc;
+    return rc == MS_OK ? ms_mlp_check(m) : rc;
 }
 
 }  // extern "C"

@@ -1,5 +1,7 @@
 """The closure network's BF16 tensor-core forward, backward and Adam kernels
-against the FP64 oracle (oracle/closure_oracle.py)."""
+against the FP64 oracle (oracle/closure_oracle.py).  Training runs on either
+engine: the tcgen05 GEMMs (engine 1, the default) or the mma.sync tiles
+(engine 0); the training tests run on both."""
 import numpy as np
 import pytest
 
@@ -100,14 +102,21 @@ def test_engine_choice_is_checked(ms):
     net.close()
 
 
-@pytest.mark.parametrize("B", [64, 1000, 5000])
-def test_gradients_match_oracle(ms, B):
+ENGINES = pytest.mark.parametrize("engine", [1, 0], ids=["tcgen05", "mma"])
+
+
+@ENGINES
+@pytest.mark.parametrize("B", [8, 64, 1000, 5000])
+def test_gradients_match_oracle(ms, B, engine):
     """BF16 products with FP32 accumulation: each parameter's gradient within
-    2e-2 of the FP64 gradient (normwise)."""
+    2e-2 of the FP64 gradient (normwise).  Batches below one 128-row tile,
+    several tiles with a ragged tail, and split over k (5000 samples: 32
+    slices of the weight-gradient products, added atomically)."""
     X, Y = _data(1, B)
     norm = CO.normalisation(X, Y)
     p = _params()
     net = ms.MLP(p, norm, max_batch=8192)
+    net.set_engine(engine)
     loss, g = net.grad(X, Y)
     lref, gref = CO.loss_and_grads(p, X, Y, norm)
     assert abs(loss - lref) <= 2e-2 * lref
@@ -116,13 +125,32 @@ def test_gradients_match_oracle(ms, B):
         assert e < 2e-2, (k, e)
 
 
-def test_adam_first_step(ms):
+def test_gradients_of_the_two_engines_agree(ms):
+    """Both engines round the same FP32 accumulations to BF16 between
+    layers; they differ where the order of the FP32 sums flips a rounding:
+    each gradient within 5e-3 of the other normwise."""
+    X, Y = _data(6, 3001)
+    norm = CO.normalisation(X, Y)
+    net = ms.MLP(_params(), norm, max_batch=4096)
+    l1, g1 = net.grad(X, Y)
+    net.set_engine(0)
+    l0, g0 = net.grad(X, Y)
+    assert abs(l1 - l0) <= 1e-3 * l0
+    for k in CO.NAMES:
+        e = np.linalg.norm(g1[k] - g0[k]) / np.linalg.norm(g0[k])
+        assert e < 5e-3, (k, e)
+    net.close()
+
+
+@ENGINES
+def test_adam_first_step(ms, engine):
     """The first Adam step moves each parameter by lr * g / (|g| + eps): the
     same as the oracle's wherever the two gradients agree in sign."""
     X, Y = _data(2, 512)
     norm = CO.normalisation(X, Y)
     p = _params()
     net = ms.MLP(p, norm)
+    net.set_engine(engine)
     _, gref = CO.loss_and_grads(p, X, Y, norm)
     net.step(X, Y, 1e-3)
     q = net.params()
@@ -134,17 +162,20 @@ def test_adam_first_step(ms):
         assert np.mean(d < 1e-6) > 0.97, (k, np.mean(d < 1e-6))
 
 
-def test_training_on_gpu_reduces_loss(ms):
+@ENGINES
+def test_training_on_gpu_reduces_loss(ms, engine):
     X, Y = _data(3, 20000)
     norm = CO.normalisation(X, Y)
     net = ms.MLP(I.mlp_init(), norm, max_batch=4096)
+    net.set_engine(engine)
     losses = net.train(X, Y, epochs=25, batch=1024, lr=2e-3, seed=7)
     assert losses[-1] < 0.1 * losses[0], losses
     ref = CO.loss_and_grads(net.params(), X, Y, norm)[0]
     assert abs(ref - losses[-1]) < 0.5 * losses[-1] + 1e-3
 
 
-def test_every_epoch_visits_every_sample_once(ms):
+@ENGINES
+def test_every_epoch_visits_every_sample_once(ms, engine):
     """The device shuffle is a permutation: with a learning rate too small to
     move the weights, each epoch's mean loss is the loss of the whole set,
     to double rounding, although the set is gathered in a new order every
@@ -156,6 +187,7 @@ def test_every_epoch_visits_every_sample_once(ms):
     Y = Y.copy()
     Y[:, 0] += norm["sd_y"][0] * np.geomspace(1e-3, 30.0, n)[np.random.default_rng(2).permutation(n)]
     net = ms.MLP(_params(), norm, max_batch=n)
+    net.set_engine(engine)
     full = net.grad(X, Y)[0]
     losses = net.train(X, Y, epochs=3, batch=1024, lr=1e-30, seed=17)
     assert np.allclose(losses, full, rtol=1e-9, atol=0.0), (losses, full)
