@@ -20,7 +20,6 @@
 
 #include "common.cuh"
 #include "mlp_tc.cuh"
-#include "tc_ptx.cuh"
 #include "../../include/msdem.h"
 
 namespace msd {
@@ -171,232 +170,6 @@ k_gemm(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda, con
         }
 }
 
-// The same product on the tcgen05 tensor cores: a CTA of 128 threads takes
-// a 128 x 64 tile of C (rows past M and columns past N are not written; the
-// MMA's N is the tile's columns padded to a multiple of 16) over the k-slice
-// of blockIdx.z.  The threads stage 64-wide k chunks of A and B into shared
-// memory in the core-matrix layout, two buffers deep, and one thread issues
-// one tcgen05.mma (K = 16) per 16 k of the chunk into a 64-column FP32
-// accumulator in tensor memory; a chunk's commit to its buffer's mbarrier
-// frees that buffer, so staging chunk c + 1 overlaps the MMAs of chunk c.
-// The epilogue reads a row per thread (tcgen05.ld) and applies the same EPI
-// as k_gemm, with 16-byte row stores and four-wide atomic adds.  A wait that
-// runs out sets *err; the CTA then waits (bounded) for the MMAs in flight,
-// frees its tensor memory and stops.  49 KB of shared memory per CTA keeps at
-// most four CTAs (256 of the 512 tensor-memory columns) on an SM.
-constexpr int TCG_T = 128, TCG_BK = 64, TCG_NT = 64;
-
-struct TcgSmem {
-    bf16 A[2][TCG_T * TCG_BK];       // 128 x 64 per buffer, core-matrix layout
-    bf16 B[2][TCG_NT * TCG_BK];      // 64 x 64
-    unsigned long long bar[2];       // MMA chunk done, per buffer
-    uint32_t tbase;
-};
-
-template <int EPI>
-__global__ void __launch_bounds__(TCG_T)
-k_gemm_tc(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb,
-          EpiArgs ea, int *err)
-{
-    using namespace tcx;
-    extern __shared__ __align__(128) unsigned char tcg_raw[];
-    TcgSmem &S = *reinterpret_cast<TcgSmem *>(tcg_raw);
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int m0 = blockIdx.x * TCG_T, n0 = blockIdx.y * TCG_NT;
-    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-    const int nch = kend > kbeg ? (kend - kbeg + TCG_BK - 1) / TCG_BK : 0;
-    const int Nt = min(TCG_NT, N - n0), Np = (Nt + 15) / 16 * 16;
-    const uint32_t bar0 = smem_u32(&S.bar[0]), bar1 = smem_u32(&S.bar[1]);
-    if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar0), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar1), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&S.tbase)), "r"(TCG_NT));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = S.tbase;
-    // per buffer: the phase of its next commit and whether one is unwaited
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool pend0 = false, pend1 = false;
-    bool ok = true;
-    for (int c = 0; c < nch && ok; c++) {
-        const int b = c & 1, k0 = kbeg + c * TCG_BK;
-        const uint32_t bar = b ? bar1 : bar0;
-        if (b ? pend1 : pend0) {
-            // buffer b is free once chunk c - 2's MMAs are done
-            const uint32_t ph = b ? ph1 : ph0;
-            ok = __syncthreads_and(bar_wait(bar, ph) ? 1 : 0) != 0;
-            if (!ok) break;
-            if (b) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
-            fence_after();
-        }
-        unsigned char *Ab = reinterpret_cast<unsigned char *>(S.A[b]), *Bb = reinterpret_cast<unsigned char *>(S.B[b]);
-        // 16-byte pieces, all loads first: rows past M (N) and k past the slice read as zero
-        constexpr int PA = TCG_T * (TCG_BK / 8) / TCG_T, PB = TCG_NT * (TCG_BK / 8) / TCG_T;
-        uint4 va[PA], vb[PB];
-#pragma unroll
-        for (int i = 0; i < PA; i++) {
-            const int q = t + i * TCG_T, r = q / (TCG_BK / 8), gk = k0 + 8 * (q % (TCG_BK / 8));
-            va[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (m0 + r < M && gk < kend) va[i] = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + gk);
-        }
-#pragma unroll
-        for (int i = 0; i < PB; i++) {
-            const int q = t + i * TCG_T, r = q / (TCG_BK / 8), gk = k0 + 8 * (q % (TCG_BK / 8));
-            vb[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (r < Nt && gk < kend) vb[i] = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + gk);
-        }
-#pragma unroll
-        for (int i = 0; i < PA; i++) {
-            const int q = t + i * TCG_T;
-            *reinterpret_cast<uint4 *>(Ab + core_off(q / (TCG_BK / 8), 8 * (q % (TCG_BK / 8)), TCG_BK)) = va[i];
-        }
-#pragma unroll
-        for (int i = 0; i < PB; i++) {
-            const int q = t + i * TCG_T;
-            *reinterpret_cast<uint4 *>(Bb + core_off(q / (TCG_BK / 8), 8 * (q % (TCG_BK / 8)), TCG_BK)) = vb[i];
-        }
-        fence_async_smem();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (t == 0) {
-            const uint32_t id = idesc_bf16(TCG_T, Np), sA = smem_u32(S.A[b]), sB = smem_u32(S.B[b]);
-            const int nk = min(TCG_BK / 16, (kend - k0 + 15) / 16);   // k past the slice is zero
-            for (int kk = 0; kk < nk; kk++)
-                mma_issue(tmem, sdesc(sA + kk * 256, 128, 16 * TCG_BK), sdesc(sB + kk * 256, 128, 16 * TCG_BK), id,
-                          (c > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(bar);
-        }
-        if (b) pend1 = true; else pend0 = true;
-    }
-    if (ok && nch > 0) {
-        // the last chunk's commit covers every MMA before it
-        const int b = (nch - 1) & 1;
-        ok = __syncthreads_and(bar_wait(b ? bar1 : bar0, b ? ph1 : ph0) ? 1 : 0) != 0;
-        if (ok) pend0 = pend1 = false;
-        fence_after();
-    }
-    if (ok && nch > 0) {
-        const int m = m0 + t;
-        const bool row = m < M;
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c0 = 0; c0 < Np; c0 += 16) {
-            float v[16];
-            tmem_ld16(lane_addr + c0, v);
-            const int nb = n0 + c0;
-            const bool full = nb + 16 <= N;
-            if (EPI == EPI_TANH || EPI == EPI_DZ) {
-                float cs[16];
-                __align__(16) bf16 o[16];
-                if (row) {
-                    if (EPI == EPI_DZ && full) {
-                        __align__(16) bf16 hh[16];
-                        const uint4 *hp = reinterpret_cast<const uint4 *>(ea.h + (size_t)m * ea.ldo + nb);
-                        reinterpret_cast<uint4 *>(hh)[0] = hp[0];
-                        reinterpret_cast<uint4 *>(hh)[1] = hp[1];
-#pragma unroll
-                        for (int i = 0; i < 16; i++) {
-                            const float h = __bfloat162float(hh[i]);
-                            cs[i] = v[i] * (1.0f - h * h);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const int n = nb + i;
-                        if (EPI == EPI_TANH) {
-                            cs[i] = 0.0f;
-                            o[i] = __float2bfloat16_rn(n < N ? tanhf(v[i] + ea.bias[n]) : 0.0f);
-                        } else {
-                            if (!full) {
-                                const float h = n < N ? __bfloat162float(ea.h[(size_t)m * ea.ldo + n]) : 0.0f;
-                                cs[i] = n < N ? v[i] * (1.0f - h * h) : 0.0f;
-                            }
-                            o[i] = __float2bfloat16_rn(cs[i]);
-                        }
-                    }
-                    if (full) {
-                        uint4 *op = reinterpret_cast<uint4 *>(ea.out + (size_t)m * ea.ldo + nb);
-                        op[0] = reinterpret_cast<const uint4 *>(o)[0];
-                        op[1] = reinterpret_cast<const uint4 *>(o)[1];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const int n = nb + i;
-                        if (n < N) {
-                            if (!full) ea.out[(size_t)m * ea.ldo + n] = o[i];
-                            ea.outT[(size_t)n * ea.ldt + m] = o[i];
-                        }
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; i++) cs[i] = 0.0f;
-                }
-                if (EPI == EPI_DZ) {
-                    // bias gradient: each column over the warp's 32 rows, one atomic per column
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        float x = cs[i];
-#pragma unroll
-                        for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
-                        if (lane == 0 && nb + i < N) atomicAdd(&ea.bgrad[nb + i], x);
-                    }
-                }
-            } else if (row) {
-                float *p = ea.f32 + (size_t)m * ea.ldf + nb;
-                if (EPI == EPI_LIN) {
-#pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        if (nb + i < N) p[i] = v[i] + (nb + i < ea.n_real ? ea.bias[nb + i] : 0.0f);
-                } else if (full) {
-#pragma unroll
-                    for (int i = 0; i < 16; i += 4) {
-                        const float4 x = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-                        if (ea.atomic) atomicAdd(reinterpret_cast<float4 *>(p + i), x);
-                        else *reinterpret_cast<float4 *>(p + i) = x;
-                    }
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; i++)
-                        if (nb + i < N) {
-                            if (ea.atomic) atomicAdd(p + i, v[i]);
-                            else p[i] = v[i];
-                        }
-                }
-            }
-        }
-    }
-    if (!ok) {
-        if (t == 0) atomicOr(err, 1);
-        // the MMAs in flight, if they still complete (at most one commit per buffer)
-        if (pend0) bar_wait(bar0, ph0);
-        if (pend1) bar_wait(bar1, ph1);
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCG_NT));
-}
-
-cudaError_t gemm_tc_prepare()
-{
-    const int sz = (int)sizeof(TcgSmem);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_gemm_tc<EPI_TANH>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
-        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
-        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_DZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)) ||
-        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sz)))
-        return e;
-    return cudaSuccess;
-}
-
 // raw features -> z-scored BF16, [B][KIN] and [KIN][B] (padding columns 0)
 __global__ void k_prep_input(const float *X, int B, int Bp, const float *mu, const float *sd, bf16 *xh, bf16 *xht)
 {
@@ -494,23 +267,37 @@ struct LayerDev {
     float *mW, *vW, *mb, *vb;  // Adam moments
     float *gW, *gb;            // gradients [nop][kin] (padded), [nout]
     bf16 *Wb, *Wt;             // BF16 copies [nop][kin] and [kin][nop]
-    bf16 *Wc;                  // BF16 image of the tcgen05 inference kernel (tc_core_index layout)
+    bf16 *Wc;                  // BF16 image of W for the tcgen05 kernels (tc_core_index layout, [rows][kin])
+    bf16 *Wtc;                 // BF16 image of W^T for the tcgen05 backward pass ([128][tk])
+    int tk;                    // K of the W^T image (tc_timage_k)
 };
 
-// Adam on one layer, then refresh its BF16 copies (both layouts)
-// Adam's step count lives on the device (so that a captured training epoch
-// replays with the right bias corrections)
+// Adam on every layer in one launch, then refresh each layer's BF16 copies
+// (all layouts); each gradient entry is zeroed once read, so the next batch's
+// atomic sums start from zero.  Adam's step count lives on the device (so
+// that a captured training epoch replays with the right bias corrections).
 __global__ void k_tick(long long *t) { *t += 1; }
 
-__global__ void k_adam(LayerDev L, float lr, const long long *tstep, float beta1, float beta2, float eps)
+struct AdamAll {
+    LayerDev L[4];
+    int off[5];                // thread ranges: layer l takes [off[l], off[l+1])
+};
+
+__global__ void k_adam(AdamAll A, float lr, const long long *tstep, float beta1, float beta2, float eps)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.off[4]) return;
+    int l = 0;
+    while (i >= A.off[l + 1]) l++;
+    const LayerDev &L = A.L[l];
+    i -= A.off[l];
     const float tf = (float)*tstep;
     const float c1 = 1.0f - powf(beta1, tf), c2 = 1.0f - powf(beta2, tf);
     const int nw = L.nout * L.nin;
     if (i < nw) {
         const int o = i / L.nin, k = i % L.nin;
         const float g = L.gW[o * L.kin + k];
+        L.gW[o * L.kin + k] = 0.0f;
         const float m = beta1 * L.mW[i] + (1.0f - beta1) * g;
         const float v = beta2 * L.vW[i] + (1.0f - beta2) * g * g;
         L.mW[i] = m;
@@ -521,9 +308,11 @@ __global__ void k_adam(LayerDev L, float lr, const long long *tstep, float beta1
         L.Wb[o * L.kin + k] = wb;
         L.Wt[k * L.nop + o] = wb;
         L.Wc[tc_core_index(o, k, L.kin)] = wb;
+        L.Wtc[tc_core_index(k, o, L.tk)] = wb;
     } else if (i < nw + L.nout) {
         const int o = i - nw;
         const float g = L.gb[o];
+        L.gb[o] = 0.0f;
         const float m = beta1 * L.mb[o] + (1.0f - beta1) * g;
         const float v = beta2 * L.vb[o] + (1.0f - beta2) * g * g;
         L.mb[o] = m;
@@ -578,7 +367,12 @@ __global__ void k_gather_epoch(const float *X, const float *Y, long long n, int 
 __global__ void k_set_epoch(int *ep, int v) { *ep = v; }
 
 // the batch's mean loss times its size into the current epoch's sum
-__global__ void k_add_loss(const double *loss, int B, const int *ep, double *eloss) { eloss[*ep] += *loss * B; }
+// the batch's loss into its epoch's sum; the batch sum restarts from zero
+__global__ void k_add_loss(double *loss, int B, const int *ep, double *eloss)
+{
+    eloss[*ep] += *loss * B;
+    *loss = 0.0;
+}
 
 __global__ void k_cast_layer(LayerDev L)
 {
@@ -590,6 +384,7 @@ __global__ void k_cast_layer(LayerDev L)
     L.Wb[i] = wb;
     L.Wt[k * L.nop + o] = wb;
     L.Wc[tc_core_index(o, k, L.kin)] = wb;
+    if (o < L.tk) L.Wtc[tc_core_index(k, o, L.tk)] = wb;
 }
 
 }  // namespace
@@ -633,29 +428,11 @@ static cudaError_t mal(ms_mlp *m, T **p, size_t n)
     return cudaMemsetAsync(q, 0, sizeof(T) * (n ? n : 1), m->st);
 }
 
-// C = A B^T with epilogue epi on the MLP's stream: the tcgen05 kernel when
-// the MLP's engine is 1, else the mma.sync tiles
+// C = A B^T with epilogue epi on the MLP's stream (the mma.sync tiles)
 static cudaError_t gemm(const ms_mlp *m, int epi, int M, int N, int K, const bf16 *A, int lda, const bf16 *B, int ldb,
                         const EpiArgs &ea, int ksplit = 1)
 {
     cudaStream_t st = m->st;
-    if (m->engine == 1) {
-        const int tiles = ((M + TCG_T - 1) / TCG_T) * ((N + TCG_NT - 1) / TCG_NT);
-        if (ksplit > 1) {
-            // split k until the grid covers the SMs, a 64-wide chunk at least per slice
-            ksplit = std::max(1, std::min((K + TCG_BK - 1) / TCG_BK, (m->sm_count + tiles - 1) / tiles));
-        }
-        const int kchunk = ((K + ksplit - 1) / ksplit + TCG_BK - 1) / TCG_BK * TCG_BK;
-        dim3 grid((M + TCG_T - 1) / TCG_T, (N + TCG_NT - 1) / TCG_NT, (K + kchunk - 1) / kchunk);
-        const size_t sm = sizeof(TcgSmem);
-        switch (epi) {
-        case EPI_TANH: k_gemm_tc<EPI_TANH><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
-        case EPI_LIN: k_gemm_tc<EPI_LIN><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
-        case EPI_DZ: k_gemm_tc<EPI_DZ><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
-        default: k_gemm_tc<EPI_F32><<<grid, TCG_T, sm, st>>>(M, N, K, kchunk, A, lda, B, ldb, ea, m->tc_err); break;
-        }
-        return cudaGetLastError();
-    }
     const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
     dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, (K + kchunk - 1) / kchunk);
     switch (epi) {
@@ -692,15 +469,11 @@ static cudaError_t forward(ms_mlp *m, int Bp)
     return gemm(m, EPI_LIN, Bp, NOP, NH, in, NH, m->L[3].Wb, NH, ea);
 }
 
-// gradients of the batch loss (z-scored units) into the layers' gW, gb
+// gradients of the batch loss (z-scored units) added to the layers' gW, gb (zero
+// at entry: Adam zeroes them once read) and the loss added to m->loss
 static cudaError_t backward(ms_mlp *m, int B, int Bp)
 {
     cudaError_t e;
-    for (int l = 0; l < 4; l++) {
-        if ((e = cudaMemsetAsync(m->L[l].gW, 0, sizeof(float) * LNOP[l] * LKIN[l], m->st)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(m->L[l].gb, 0, sizeof(float) * LOUT[l], m->st)) != cudaSuccess) return e;
-    }
-    if ((e = cudaMemsetAsync(m->loss, 0, sizeof(double), m->st)) != cudaSuccess) return e;
     k_loss_grad<<<(Bp + 255) / 256, 256, 0, m->st>>>(m->yp, m->Y, B, Bp, m->mu_y, m->sd_y, m->dy, m->dyt, m->L[3].gb,
                                                      m->loss);
     const int ks = Bp >= 4096 ? 32 : (Bp >= 512 ? 8 : 1);
@@ -768,14 +541,14 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
     size_t off = 0;
     for (int l = 0; l < 4; l++) {
         LayerDev &L = m->L[l];
-        L.nin = LIN[l]; L.nout = LOUT[l]; L.kin = LKIN[l]; L.nop = LNOP[l];
+        L.nin = LIN[l]; L.nout = LOUT[l]; L.kin = LKIN[l]; L.nop = LNOP[l]; L.tk = tc_timage_k(l);
         const size_t nw = (size_t)L.nout * L.nin;
         cudaError_t e;
         if ((e = mal(m, &L.W, nw)) || (e = mal(m, &L.b, L.nout)) || (e = mal(m, &L.mW, nw)) ||
             (e = mal(m, &L.vW, nw)) || (e = mal(m, &L.mb, L.nout)) || (e = mal(m, &L.vb, L.nout)) ||
             (e = mal(m, &L.gW, (size_t)L.nop * L.kin)) || (e = mal(m, &L.gb, L.nout)) ||
             (e = mal(m, &L.Wb, (size_t)L.nop * L.kin)) || (e = mal(m, &L.Wt, (size_t)L.nop * L.kin)) ||
-            (e = mal(m, &L.Wc, (size_t)tc_image_rows(l) * L.kin)))
+            (e = mal(m, &L.Wc, (size_t)tc_image_rows(l) * L.kin)) || (e = mal(m, &L.Wtc, (size_t)NH * L.tk)))
             return fail_free(ck(e, "cudaMalloc"));
         if ((rc = ck(cudaMemcpyAsync(L.W, params + off, sizeof(float) * nw, cudaMemcpyHostToDevice, m->st), "copy")))
             return fail_free(rc);
@@ -798,7 +571,7 @@ int ms_mlp_create(ms_mlp **out, const float *params, const float *norm, int32_t 
         if ((rc = ck(cudaGetDevice(&dev), "device")) ||
             (rc = ck(cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, dev), "attribute")) ||
             (rc = ck(mlp_tc_prepare(), "tcgen05 kernel attribute")) ||
-            (rc = ck(gemm_tc_prepare(), "tcgen05 kernel attribute")))
+            (rc = ck(mlp_train_tc_prepare(), "tcgen05 kernel attribute")))
             return fail_free(rc);
     }
     for (int l = 0; l < 3; l++)
@@ -930,6 +703,75 @@ int ms_mlp_check(ms_mlp *m)
     return MS_OK;
 }
 
+// the gradients of the batch (X, Y) already on the device into the layers'
+// gW, gb (which hold zeros) and its loss added to m->loss: on engine 1 the
+// two tcgen05 kernels, on engine 0 the mma.sync GEMMs
+static cudaError_t batch_grads(ms_mlp *m, const float *Xd, const float *Yd, int B, bool tick)
+{
+    const int Bp = pad8(B);
+    if (m->engine == 1) {
+        TrainArgs a{};
+        a.X = Xd;
+        a.Y = Yd;
+        a.B = B;
+        a.Bp = Bp;
+        for (int l = 0; l < 4; l++) {
+            a.W[l] = m->L[l].Wc;
+            a.Wt[l] = m->L[l].Wtc;
+            a.b[l] = m->L[l].b;
+        }
+        a.mu_x = m->mu_x;
+        a.sd_x = m->sd_x;
+        a.mu_y = m->mu_y;
+        a.sd_y = m->sd_y;
+        a.xt = m->xht;
+        for (int l = 0; l < 3; l++) {
+            a.Ht[l] = m->Ht[l];
+            a.dZt[l] = m->dZt[l];
+        }
+        a.dyt = m->dyt;
+        a.loss = m->loss;
+        a.tick = tick ? m->d_t : nullptr;
+        a.err = m->tc_err;
+        cudaError_t e = launch_train_tile_tc(a, m->sm_count, m->st);
+        if (e != cudaSuccess) return e;
+        WgradArgs w{};
+        w.njob = 4;
+        w.K = Bp;
+        w.err = m->tc_err;
+        for (int l = 0; l < 4; l++) {
+            WgradJob &J = w.job[l];
+            J.M = LOUT[l];
+            J.nin = LIN[l];
+            J.ldw = LKIN[l];
+            J.A = l == 3 ? m->dyt : m->dZt[l];
+            J.B = l == 0 ? m->xht : m->Ht[l - 1];
+            J.gW = m->L[l].gW;
+            J.gb = m->L[l].gb;
+        }
+        return launch_wgrad_tc(w, m->sm_count, m->st);
+    }
+    k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(Xd, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
+    const float *keepY = m->Y;
+    m->Y = const_cast<float *>(Yd);
+    cudaError_t e = forward(m, Bp);
+    if (e == cudaSuccess) e = backward(m, B, Bp);
+    m->Y = const_cast<float *>(keepY);
+    if (e == cudaSuccess && tick) k_tick<<<1, 1, 0, m->st>>>(m->d_t);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// gradients, loss and Adam's step count back to zero
+static cudaError_t zero_grads(ms_mlp *m)
+{
+    cudaError_t e = cudaMemsetAsync(m->loss, 0, sizeof(double), m->st);
+    for (int l = 0; l < 4 && e == cudaSuccess; l++) {
+        e = cudaMemsetAsync(m->L[l].gW, 0, sizeof(float) * m->L[l].nop * m->L[l].kin, m->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->L[l].gb, 0, sizeof(float) * m->L[l].nout, m->st);
+    }
+    return e;
+}
+
 static int gather_grads(ms_mlp *m, float *grads)
 {
     size_t off = 0;
@@ -952,15 +794,15 @@ int ms_mlp_grad(ms_mlp *m, const float *X, const float *Y, int64_t n, float *gra
 {
     if (!m || !X || !Y || !grads) return ms_closure_fail(MS_ERR_ARG, "NULL argument");
     if (n < 1 || n > m->max_batch) return ms_closure_fail(MS_ERR_ARG, "n must be in [1, max_batch]");
-    const int B = (int)n, Bp = pad8(B);
+    const int B = (int)n;
     CKC(cudaMemcpyAsync(m->X, X, sizeof(float) * B * NIN, cudaMemcpyHostToDevice, m->st));
     CKC(cudaMemcpyAsync(m->Y, Y, sizeof(float) * B * NOUT, cudaMemcpyHostToDevice, m->st));
-    k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(m->X, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
-    CKC(forward(m, Bp));
-    CKC(backward(m, B, Bp));
+    CKC(zero_grads(m));
+    CKC(batch_grads(m, m->X, m->Y, B, false));
     if (loss) CKC(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->st));
     CKC(cudaStreamSynchronize(m->st));
-    const int rc = gather_grads(m, grads);
+    int rc = gather_grads(m, grads);
+    if (rc == MS_OK) rc = ck(zero_grads(m), "memset");
     return rc ? rc : ms_mlp_check(m);
 }
 
@@ -983,20 +825,14 @@ int ms_mlp_get_params(ms_mlp *m, float *params)
 // one Adam step on the gradients of the batch (X, Y) already on the device
 static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float lr)
 {
-    const int Bp = pad8(B);
-    k_prep_input<<<(Bp + 255) / 256, 256, 0, m->st>>>(Xd, B, Bp, m->mu_x, m->sd_x, m->xh, m->xht);
-    const float *keepY = m->Y;
-    m->Y = const_cast<float *>(Yd);
-    cudaError_t e = forward(m, Bp);
-    if (e == cudaSuccess) e = backward(m, B, Bp);
-    m->Y = const_cast<float *>(keepY);
-    CKC(e);
-    const float b1 = 0.9f, b2 = 0.999f;
-    k_tick<<<1, 1, 0, m->st>>>(m->d_t);
+    CKC(batch_grads(m, Xd, Yd, B, true));
+    AdamAll A{};
+    A.off[0] = 0;
     for (int l = 0; l < 4; l++) {
-        const int tot = m->L[l].nout * m->L[l].nin + m->L[l].nout;
-        k_adam<<<(tot + 255) / 256, 256, 0, m->st>>>(m->L[l], lr, m->d_t, b1, b2, 1e-8f);
+        A.L[l] = m->L[l];
+        A.off[l + 1] = A.off[l] + m->L[l].nout * m->L[l].nin + m->L[l].nout;
     }
+    k_adam<<<(A.off[4] + 255) / 256, 256, 0, m->st>>>(A, lr, m->d_t, 0.9f, 0.999f, 1e-8f);
     return ck(cudaGetLastError(), "adam");
 }
 
@@ -1006,6 +842,7 @@ int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr)
     if (n < 1 || n > m->max_batch) return ms_closure_fail(MS_ERR_ARG, "n must be in [1, max_batch]");
     CKC(cudaMemcpyAsync(m->X, X, sizeof(float) * n * NIN, cudaMemcpyHostToDevice, m->st));
     CKC(cudaMemcpyAsync(m->Y, Y, sizeof(float) * n * NOUT, cudaMemcpyHostToDevice, m->st));
+    CKC(zero_grads(m));
     int rc = train_step(m, m->X, m->Y, (int)n, lr);
     if (rc) return rc;
     CKC(cudaStreamSynchronize(m->st));
@@ -1049,6 +886,7 @@ int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t e
     run(cudaMemcpyAsync(Xd, X, sizeof(float) * n * NIN, cudaMemcpyHostToDevice, m->st), "copy");
     run(cudaMemcpyAsync(Yd, Y, sizeof(float) * n * NOUT, cudaMemcpyHostToDevice, m->st), "copy");
     run(cudaMemsetAsync(el, 0, sizeof(double) * (epochs > 0 ? epochs : 1), m->st), "memset");
+    run(zero_grads(m), "memset");
     // Feistel domain 4^h >= n
     int h = 1;
     while (((int64_t)1 << (2 * h)) < n) h++;

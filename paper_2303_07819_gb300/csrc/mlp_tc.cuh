@@ -15,6 +15,9 @@ __host__ __device__ inline int tc_core_index(int r, int k, int K)
 }
 // rows of each layer's image: 128, 128, 128 and the output layer padded to 16
 __host__ __device__ inline int tc_image_rows(int layer) { return layer == 3 ? 16 : 128; }
+// The backward pass's image of W_l^T (l = 1, 2, 3): 128 rows (the layer's
+// inputs) by K = the layer's outputs, the output layer's 4 padded to 16.
+__host__ __device__ inline int tc_timage_k(int layer) { return layer == 3 ? 16 : 128; }
 
 struct TcArgs {
     const float *X;                  // [n][16] raw features (device)
@@ -26,9 +29,49 @@ struct TcArgs {
     int *err;                        // set to 1 if a wait on the tensor cores ran out
 };
 
+// One training batch, forward and backward through the hidden layers, per
+// 128-sample tile (k_train_tile_tc).  The buffers have Bp rows (the batch
+// rounded up to 8); rows B .. Bp - 1 are padding (zero inputs, zero dL/dy).
+struct TrainArgs {
+    const float *X, *Y;              // the batch: [B][16] raw features, [B][4] raw targets (device)
+    int B, Bp;
+    const __nv_bfloat16 *W[4];       // forward images, as TcArgs::W
+    const __nv_bfloat16 *Wt[4];      // backward images of W_l^T for l = 1, 2, 3 (tc_timage_k); Wt[0] unused
+    const float *b[4];
+    const float *mu_x, *sd_x, *mu_y, *sd_y;
+    __nv_bfloat16 *xt;               // out: [16][Bp] z-scored inputs, transposed
+    __nv_bfloat16 *Ht[3];            // out: [128][Bp] hidden activations, transposed
+    __nv_bfloat16 *dyt;              // out: rows 0-3 of [8][Bp], dL/dy transposed
+    __nv_bfloat16 *dZt[3];           // out: [128][Bp] dL/dz of the hidden layers' pre-activations, transposed
+    double *loss;                    // += the batch's mean squared error (z-scored outputs)
+    long long *tick;                 // += 1 (Adam's step count) unless null
+    int *err;                        // set to 1 if a wait on the tensor cores ran out
+};
+
+// Weight and bias gradients of the batch: for each job, gW[m][n] += sum_k
+// A[m][k] B[n][k] over m < M, n < nin, and gb[m] += sum_k A[m][k]
+// (k_wgrad_tc; A = dL/dz transposed, B = the layer's input transposed, both
+// with K = Bp columns).
+struct WgradJob {
+    int M, nin, ldw;
+    const __nv_bfloat16 *A, *B;
+    float *gW, *gb;
+};
+struct WgradArgs {
+    WgradJob job[4];
+    int njob, K;
+    int *err;
+};
+
 size_t mlp_tc_smem();
 cudaError_t mlp_tc_prepare();
 // a persistent grid of at most sm_count CTAs, 128 cells per tile
 cudaError_t launch_mlp_forward_tc(const TcArgs &a, int sm_count, cudaStream_t st);
+
+cudaError_t mlp_train_tc_prepare();
+// one CTA per SM at most (178 KB of shared memory), 128 samples per tile
+cudaError_t launch_train_tile_tc(const TrainArgs &a, int sm_count, cudaStream_t st);
+// the jobs' 64-column tiles times k slices of at least 64, about 2 CTAs per SM
+cudaError_t launch_wgrad_tc(const WgradArgs &a, int sm_count, cudaStream_t st);
 
 }  // namespace msd
