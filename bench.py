@@ -78,6 +78,29 @@ MLP_FWD_FLOP = 2 * (16 * 128 + 2 * 128 * 128 + 128 * 4)
 MLP_TRAIN_FLOP = 3 * MLP_FWD_FLOP
 
 
+def closure_training_rate(msdem, batch, n=65536, epochs=4):
+    """Adam epochs over n synthetic samples at `batch` on each engine (one
+    epoch of warm-up, then `epochs` timed by the host around ms_mlp_train,
+    which waits for the device once at its end)."""
+    from paper_2303_07819_gb300 import inputs as I
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(n, 16)).astype(np.float32)
+    Y = np.stack([np.sin(X[:, 0]), 0.1 * X[:, 1], np.tanh(X[:, 3]), 0.01 * X[:, 4] ** 2], 1).astype(np.float32)
+    norm = msdem.fit_norm(X, Y)
+    out = {"samples": n, "batch": batch, "epochs": epochs}
+    for eng, name in ((1, "tcgen05"), (0, "mma_sync")):
+        net = msdem.MLP(I.mlp_init(), norm, max_batch=batch)
+        net.set_engine(eng)
+        net.train(X, Y, epochs=1, batch=batch, lr=1e-3, seed=1)
+        t = time.perf_counter()
+        net.train(X, Y, epochs=epochs, batch=batch, lr=1e-3, seed=2)
+        dt = time.perf_counter() - t
+        net.close()
+        out[name] = {"samples_per_s": epochs * n / dt, "tflops": epochs * n * MLP_TRAIN_FLOP / dt / 1e12,
+                     "us_per_batch": dt / (epochs * (n // batch)) * 1e6}
+    return out
+
+
 def closure_inference_rate(net, X, n=256 * 256, reps=20):
     """The network on a 256 x 256 grid's cells (features drawn from the
     training set), device-timed over `reps` calls of the inference kernel."""
@@ -422,6 +445,9 @@ def main():
                     help="the truth DEM of --workload alone: run N steps and exit (for ncu captures), "
                          "or with --truth-time time it")
     ap.add_argument("--truth-time", action="store_true", help="print the truth DEM's time per step")
+    ap.add_argument("--closure-train", type=int, default=0,
+                    help="the closure network's training alone at batch B on 65,536 synthetic samples "
+                         "(random-init weights), each engine: time it and exit (for ncu captures)")
     ap.add_argument("--closure-infer", type=int, default=0,
                     help="the closure network's inference kernel alone on N cells of synthetic features "
                          "(random-init weights): time it and exit (for ncu captures)")
@@ -443,6 +469,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     msdem.load()
+    if args.closure_train:
+        print(json.dumps(closure_training_rate(msdem, args.closure_train)), flush=True)
+        return
     if args.closure_infer:
         from paper_2303_07819_gb300 import inputs as I
         rng = np.random.default_rng(3)

@@ -10,7 +10,8 @@
 // shared memory, D the FP32 accumulator in tensor memory (128 lanes = the
 // tile's cells, one column per unit).  A commit to an mbarrier marks the
 // chain done; every thread then reads its cell's row with tcgen05.ld, adds
-// the bias, applies tanh and writes the next layer's BF16 operand in place.
+// the bias, applies tanh (the special-function unit's tanh.approx) and writes
+// the next layer's BF16 operand in place.
 //
 // Shared-memory operands use the canonical K-major layout without swizzle:
 // 8 x 16-byte "core matrices" (8 rows, 8 BF16 along K), core matrix (i, j)
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
                     tmem_ld16(lane_addr + c0, v);
                     __align__(16) bf16 h[16];
 #pragma unroll
-                    for (int e = 0; e < 16; e++) h[e] = __float2bfloat16_rn(tanhf(v[e] + S.b[l][c0 + e]));
+                    for (int e = 0; e < 16; e++) h[e] = __float2bfloat16_rn(tanh_sfu(v[e] + S.b[l][c0 + e]));
                     *reinterpret_cast<uint4 *>(Ab + core_off(t, c0, TC_NH)) = *reinterpret_cast<const uint4 *>(h);
                     *reinterpret_cast<uint4 *>(Ab + core_off(t, c0 + 8, TC_NH)) =
                         *reinterpret_cast<const uint4 *>(h + 8);

@@ -69,7 +69,7 @@ cudaError_t mlp_tc_prepare();
 cudaError_t launch_mlp_forward_tc(const TcArgs &a, int sm_count, cudaStream_t st);
 
 cudaError_t mlp_train_tc_prepare();
-// one CTA per SM at most (178 KB of shared memory), 128 samples per tile
+// one CTA per SM (210 KB of shared memory, all 512 tensor-memory columns), 128 samples per tile
 cudaError_t launch_train_tile_tc(const TrainArgs &a, int sm_count, cudaStream_t st);
 // the jobs' 64-column tiles times k slices of at least 64, about 2 CTAs per SM
 cudaError_t launch_wgrad_tc(const WgradArgs &a, int sm_count, cudaStream_t st);

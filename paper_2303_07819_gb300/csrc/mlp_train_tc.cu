@@ -1,19 +1,22 @@
 // mlp_train_tc.cu -- one Adam batch of the closure network on the tcgen05
 // tensor cores in two kernels (the Adam update is a third, in closure.cu).
 //
-// k_train_tile_tc: a persistent CTA of 128 threads per SM keeps the four
+// k_train_tile_tc: a persistent CTA of 256 threads per SM keeps the four
 // forward weight images and the three transposed ones of the backward pass
 // in shared memory (140 KB, staged by seven cp.async.bulk copies) and takes
-// tiles of 128 samples, a thread per sample.  For each tile it runs seven
+// tiles of 128 samples, two threads per sample (each takes half of a layer's
+// units in the epilogues).  For each tile it runs seven
 // tcgen05.mma chains, each into the same 128-column FP32 accumulator in
 // tensor memory:
 //   forward   h_l = tanh(W_l h_{l-1} + b_l), l = 0, 1, 2;  y = W_3 h_2 + b_3
 //   loss      r = y - (target - mu_y) / sd_y,  dL/dy = 2 r / (4 B)
 //   backward  dz_{l-1} = (W_l^T dz_l) (1 - h_{l-1}^2), l = 3, 2, 1 (dz_3 = dL/dy)
 // Each chain's epilogue reads the sample's row (tcgen05.ld) and writes the
-// next chain's BF16 operand over the last one in shared memory.  The
-// transposed activations and dz go to global memory for the weight gradients
-// (h_{l-1} is read back from there for the tanh derivative).
+// next chain's BF16 operand over the last one in shared memory.  The hidden
+// activations also stay in tensor memory for the tanh derivative of the
+// backward pass (all 512 columns: one CTA per SM), and the transposed
+// activations and dz go to global memory for the weight gradients, staged in
+// shared memory and written while the next chain's MMAs run.
 //
 // k_wgrad_tc: the weight gradients dz_l^T h_{l-1} of the four layers as one
 // launch of 128 x 64 tcgen05 tiles (tc_gemm.cuh) over k slices of the batch,
@@ -37,11 +40,12 @@ namespace {
 using namespace tcx;
 typedef __nv_bfloat16 bf16;
 
-constexpr int TR_T = 128;          // threads = samples per tile = MMA M
+constexpr int TR_T = 128;          // samples per tile = MMA M = tensor-memory lanes
+constexpr int TR_THREADS = 256;    // two threads per sample: warps w and w + 4 share lanes 32 (w % 4) ..
 constexpr int TR_NH = 128;         // hidden width
 constexpr int TR_KIN = 16;         // input features
 constexpr int TR_NO = 16;          // output layer padded to the smallest N (forward) and K (backward)
-constexpr int TR_COLS = 128;       // tensor-memory columns held
+constexpr int TR_COLS = 512;       // tensor-memory columns: the accumulator, then h_0, h_1, h_2 (FP32)
 
 struct TrSmem {
     bf16 W0[TR_NH * TR_KIN];       // forward images [out][in]: 128 x 16
@@ -52,19 +56,22 @@ struct TrSmem {
     bf16 T2[TR_NH * TR_NH];
     bf16 T3[TR_NH * TR_NO];        // 128 x 16, columns 4-15 zero
     bf16 A[TR_T * TR_NH];          // the tile's operand, [128][K] for K = 16 or 128
+    bf16 Tr[TR_NH * TR_T];         // a layer's output transposed, [unit][sample], on its way to global memory
     float b[3][TR_NH], b3[TR_NO];
     float mux[TR_KIN], sdx[TR_KIN], muy[4], sdy[4];
-    double lsum[TR_T / 32];
+    double lsum[TR_THREADS / 32];
     unsigned long long bar;        // mbarrier of the MMA chains
     unsigned long long wbar;       // mbarrier of the weights' bulk copies
     uint32_t tbase;
 };
 
-__global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
+__global__ void __launch_bounds__(TR_THREADS) k_train_tile_tc(TrainArgs a)
 {
     extern __shared__ __align__(128) unsigned char tr_raw[];
     TrSmem &S = *reinterpret_cast<TrSmem *>(tr_raw);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // this thread's sample (tensor-memory lane) and half of the units
+    const int r = 32 * (warp & 3) + lane, half = warp >> 2;
     const uint32_t wbar = smem_u32(&S.wbar);
     constexpr uint32_t SQ = TR_NH * TR_NH * 2, SM16 = TR_NH * TR_KIN * 2;   // bytes of the images
     if (t == 0) {
@@ -80,7 +87,7 @@ __global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
         bulk_g2s(smem_u32(S.T2), a.Wt[2], SQ, wbar);
         bulk_g2s(smem_u32(S.T3), a.Wt[3], SM16, wbar);
     }
-    for (int i = t; i < 3 * TR_NH; i += TR_T) S.b[i / TR_NH][i % TR_NH] = a.b[i / TR_NH][i % TR_NH];
+    for (int i = t; i < 3 * TR_NH; i += TR_THREADS) S.b[i / TR_NH][i % TR_NH] = a.b[i / TR_NH][i % TR_NH];
     if (t < TR_NO) S.b3[t] = t < 4 ? a.b[3][t] : 0.0f;
     if (t < TR_KIN) {
         S.mux[t] = a.mu_x[t];
@@ -107,13 +114,32 @@ __global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
     bool ok = __syncthreads_and(bar_wait(wbar, 0u) ? 1 : 0) != 0;
     const bool weights_ok = ok;
     const uint32_t tmem = S.tbase;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const uint32_t sA = smem_u32(S.A);
     unsigned char *Ab = reinterpret_cast<unsigned char *>(S.A);
     uint32_t phase = 0;
+    const size_t Bp = (size_t)a.Bp;
+    const int cbeg = half * (TR_NH / 2), cend = cbeg + TR_NH / 2;   // this thread's units
 
-    // one chain D = A B^T (M = 128, N, K) into the accumulator; the same
-    // verdict in every thread
+    // S.Tr -> rows of a transposed [units][Bp] array from column m0 on (its
+    // samples below Bp), 16-byte pieces
+    bf16 *tr_dst = nullptr;
+    int tr_m0 = 0;
+    auto flush_tr = [&]() {
+        if (!tr_dst) return;
+#pragma unroll 4
+        for (int i = 0; i < TR_NH * TR_T / 8 / TR_THREADS; i++) {
+            const int q = t + i * TR_THREADS, n = q / (TR_T / 8), j = q % (TR_T / 8);
+            if (tr_m0 + 8 * j < a.Bp)
+                *reinterpret_cast<uint4 *>(tr_dst + (size_t)n * Bp + tr_m0 + 8 * j) =
+                    *reinterpret_cast<const uint4 *>(&S.Tr[n * TR_T + 8 * j]);
+        }
+        tr_dst = nullptr;
+    };
+
+    // one chain D = A B^T (M = 128, N, K) into the accumulator; the previous
+    // layer's transposed output goes to global memory while the MMAs run.
+    // The same verdict in every thread.
     auto chain = [&](uint32_t sB, int K, int N) -> bool {
         fence_async_smem();
         fence_before();
@@ -126,81 +152,99 @@ __global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
                           kk > 0 ? 1u : 0u);
             mma_commit(bar);
         }
-        const bool r = __syncthreads_and(bar_wait(bar, phase) ? 1 : 0) != 0;
-        if (r) {
+        flush_tr();
+        const bool ok2 = __syncthreads_and(bar_wait(bar, phase) ? 1 : 0) != 0;
+        if (ok2) {
             phase ^= 1u;
             fence_after();
         }
-        return r;
+        return ok2;
     };
 
     const int ntiles = (a.Bp + TR_T - 1) / TR_T;
-    const size_t Bp = (size_t)a.Bp;
     const float inv4B = 1.0f / (4.0f * (float)a.B);
     double lsum = 0.0;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const int m = tile * TR_T + t;
+        const int m0 = tile * TR_T, m = m0 + r;
         const bool inB = m < a.B, inBp = m < a.Bp;
-        // z-scored inputs: the first operand (K = 16) and their transpose
+        // z-scored inputs: the first operand (K = 16) and their transpose;
+        // each half of the threads takes 8 features
         {
-            float x[TR_KIN];
+            const int f0 = 8 * half;
+            float x[8];
+            if (inB) {
+                const float4 *xp = reinterpret_cast<const float4 *>(a.X + (size_t)m * TR_KIN + f0);
+                const float4 u0 = xp[0], u1 = xp[1];
+                x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
+                x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
 #pragma unroll
-            for (int f = 0; f < TR_KIN; f++) x[f] = inB ? (a.X[(size_t)m * TR_KIN + f] - S.mux[f]) / S.sdx[f] : 0.0f;
+                for (int e = 0; e < 8; e++) x[e] = (x[e] - S.mux[f0 + e]) / S.sdx[f0 + e];
+            } else {
 #pragma unroll
-            for (int j = 0; j < TR_KIN / 8; j++) {
-                __align__(16) bf16 h[8];
-#pragma unroll
-                for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(x[8 * j + e]);
-                *reinterpret_cast<uint4 *>(Ab + core_off(t, 8 * j, TR_KIN)) = *reinterpret_cast<const uint4 *>(h);
-                if (inBp)
-#pragma unroll
-                    for (int e = 0; e < 8; e++) a.xt[(size_t)(8 * j + e) * Bp + m] = h[e];
+                for (int e = 0; e < 8; e++) x[e] = 0.0f;
             }
+            __align__(16) bf16 h[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(x[e]);
+            *reinterpret_cast<uint4 *>(Ab + core_off(r, f0, TR_KIN)) = *reinterpret_cast<const uint4 *>(h);
+            if (inBp)
+#pragma unroll
+                for (int e = 0; e < 8; e++) a.xt[(size_t)(f0 + e) * Bp + m] = h[e];
         }
-        // hidden layers
+        // hidden layers: h_l to the next operand, to tensor memory (FP32 of
+        // the BF16 value, for the backward pass) and transposed to S.Tr
         const uint32_t sW[3] = {smem_u32(S.W0), smem_u32(S.W1), smem_u32(S.W2)};
         for (int l = 0; l < 3 && ok; l++) {
             ok = chain(sW[l], l == 0 ? TR_KIN : TR_NH, TR_NH);
             if (!ok) break;
-            bf16 *Ht = a.Ht[l];
 #pragma unroll 1
-            for (int c0 = 0; c0 < TR_NH; c0 += 16) {
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float v[16];
                 tmem_ld16(lane_addr + c0, v);
                 __align__(16) bf16 h[16];
 #pragma unroll
-                for (int e = 0; e < 16; e++) h[e] = __float2bfloat16_rn(tanhf(v[e] + S.b[l][c0 + e]));
-                *reinterpret_cast<uint4 *>(Ab + core_off(t, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(h);
-                *reinterpret_cast<uint4 *>(Ab + core_off(t, c0 + 8, TR_NH)) = *reinterpret_cast<const uint4 *>(h + 8);
-                if (inBp)
-#pragma unroll
-                    for (int e = 0; e < 16; e++) Ht[(size_t)(c0 + e) * Bp + m] = h[e];
+                for (int e = 0; e < 16; e++) {
+                    h[e] = __float2bfloat16_rn(tanh_sfu(v[e] + S.b[l][c0 + e]));
+                    v[e] = __bfloat162float(h[e]);
+                    S.Tr[(c0 + e) * TR_T + r] = h[e];
+                }
+                tmem_st16(lane_addr + (uint32_t)(TR_NH * (l + 1) + c0), v);
+                *reinterpret_cast<uint4 *>(Ab + core_off(r, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(h);
+                *reinterpret_cast<uint4 *>(Ab + core_off(r, c0 + 8, TR_NH)) = *reinterpret_cast<const uint4 *>(h + 8);
             }
+            tmem_st_wait();
+            tr_dst = a.Ht[l];
+            tr_m0 = m0;
             fence_before();
         }
         if (!ok) break;
-        // output layer and the loss: dL/dy is the first backward operand (K = 16)
+        // output layer and the loss: dL/dy is the first backward operand
+        // (K = 16), written by the first half of the threads
         ok = chain(smem_u32(S.W3), TR_NH, TR_NO);
         if (!ok) break;
         {
             float v[16];
             tmem_ld16(lane_addr, v);
-            __align__(16) bf16 g[16];
+            if (half == 0) {
+                __align__(16) bf16 g[16];
 #pragma unroll
-            for (int e = 0; e < 16; e++) g[e] = __float2bfloat16_rn(0.0f);
-            if (inB) {
+                for (int e = 0; e < 16; e++) g[e] = __float2bfloat16_rn(0.0f);
+                if (inB) {
+                    const float4 y = *reinterpret_cast<const float4 *>(a.Y + (size_t)m * 4);
+                    const float yv[4] = {y.x, y.y, y.z, y.w};
 #pragma unroll
-                for (int o = 0; o < 4; o++) {
-                    const float r = v[o] + S.b3[o] - (a.Y[(size_t)m * 4 + o] - S.muy[o]) / S.sdy[o];
-                    lsum += (double)r * r;
-                    g[o] = __float2bfloat16_rn(2.0f * r * inv4B);
+                    for (int o = 0; o < 4; o++) {
+                        const float res = v[o] + S.b3[o] - (yv[o] - S.muy[o]) / S.sdy[o];
+                        lsum += (double)res * res;
+                        g[o] = __float2bfloat16_rn(2.0f * res * inv4B);
+                    }
                 }
-            }
-            *reinterpret_cast<uint4 *>(Ab + core_off(t, 0, TR_NO)) = *reinterpret_cast<const uint4 *>(g);
-            *reinterpret_cast<uint4 *>(Ab + core_off(t, 8, TR_NO)) = *reinterpret_cast<const uint4 *>(g + 8);
-            if (inBp)
+                *reinterpret_cast<uint4 *>(Ab + core_off(r, 0, TR_NO)) = *reinterpret_cast<const uint4 *>(g);
+                *reinterpret_cast<uint4 *>(Ab + core_off(r, 8, TR_NO)) = *reinterpret_cast<const uint4 *>(g + 8);
+                if (inBp)
 #pragma unroll
-                for (int o = 0; o < 4; o++) a.dyt[(size_t)o * Bp + m] = g[o];
+                    for (int o = 0; o < 4; o++) a.dyt[(size_t)o * Bp + m] = g[o];
+            }
             fence_before();
         }
         // backward through layers 3, 2, 1: dz of the hidden layers 2, 1, 0
@@ -208,29 +252,30 @@ __global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
         for (int l = 3; l >= 1 && ok; l--) {
             ok = chain(sT[l], l == 3 ? TR_NO : TR_NH, TR_NH);
             if (!ok) break;
-            const bf16 *Hp = a.Ht[l - 1];
-            bf16 *dZ = a.dZt[l - 1];
 #pragma unroll 1
-            for (int c0 = 0; c0 < TR_NH; c0 += 16) {
-                float v[16];
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                float v[16], h[16];
                 tmem_ld16(lane_addr + c0, v);
+                tmem_ld16(lane_addr + (uint32_t)(TR_NH * l + c0), h);   // h_{l-1}
                 __align__(16) bf16 d[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++) {
-                    const float h = inBp ? __bfloat162float(Hp[(size_t)(c0 + e) * Bp + m]) : 0.0f;
-                    d[e] = __float2bfloat16_rn(v[e] * (1.0f - h * h));
+                    d[e] = __float2bfloat16_rn(v[e] * (1.0f - h[e] * h[e]));
+                    S.Tr[(c0 + e) * TR_T + r] = d[e];
                 }
                 if (l > 1) {
-                    *reinterpret_cast<uint4 *>(Ab + core_off(t, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(d);
-                    *reinterpret_cast<uint4 *>(Ab + core_off(t, c0 + 8, TR_NH)) =
+                    *reinterpret_cast<uint4 *>(Ab + core_off(r, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(d);
+                    *reinterpret_cast<uint4 *>(Ab + core_off(r, c0 + 8, TR_NH)) =
                         *reinterpret_cast<const uint4 *>(d + 8);
                 }
-                if (inBp)
-#pragma unroll
-                    for (int e = 0; e < 16; e++) dZ[(size_t)(c0 + e) * Bp + m] = d[e];
             }
+            tr_dst = a.dZt[l - 1];
+            tr_m0 = m0;
             fence_before();
         }
+        // dz_0 is the tile's last output: to global memory before S.Tr is reused
+        __syncthreads();
+        flush_tr();
     }
     // the loss: one atomic per CTA
 #pragma unroll
@@ -239,7 +284,7 @@ __global__ void __launch_bounds__(TR_T) k_train_tile_tc(TrainArgs a)
     __syncthreads();
     if (t == 0) {
         double s = 0.0;
-        for (int w = 0; w < TR_T / 32; w++) s += S.lsum[w];
+        for (int w = 0; w < TR_THREADS / 32; w++) s += S.lsum[w];
         if (s != 0.0) atomicAdd(a.loss, s / (4.0 * (double)a.B));
         if (blockIdx.x == 0 && a.tick) *a.tick += 1;
     }
@@ -317,7 +362,7 @@ cudaError_t launch_train_tile_tc(const TrainArgs &a, int sm_count, cudaStream_t 
     if (a.Bp <= 0) return cudaSuccess;
     const int ntiles = (a.Bp + TR_T - 1) / TR_T;
     const int grid = ntiles < sm_count ? ntiles : sm_count;
-    k_train_tile_tc<<<grid, TR_T, sizeof(TrSmem), st>>>(a);
+    k_train_tile_tc<<<grid, TR_THREADS, sizeof(TrSmem), st>>>(a);
     return cudaGetLastError();
 }
 
