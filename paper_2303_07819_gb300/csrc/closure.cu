@@ -261,64 +261,31 @@ __global__ void __launch_bounds__(256) k_col_stats(const float *A, long long n, 
     }
 }
 
-struct LayerDev {
-    int nin, nout, kin, nop;   // logical and padded sizes
-    float *W, *b;              // FP32 master [nout][nin], [nout]
-    float *mW, *vW, *mb, *vb;  // Adam moments
-    float *gW, *gb;            // gradients [nop][kin] (padded), [nout]
-    bf16 *Wb, *Wt;             // BF16 copies [nop][kin] and [kin][nop]
-    bf16 *Wc;                  // BF16 image of W for the tcgen05 kernels (tc_core_index layout, [rows][kin])
-    bf16 *Wtc;                 // BF16 image of W^T for the tcgen05 backward pass ([128][tk])
-    int tk;                    // K of the W^T image (tc_timage_k)
-};
-
-// Adam on every layer in one launch, then refresh each layer's BF16 copies
-// (all layouts); each gradient entry is zeroed once read, so the next batch's
-// atomic sums start from zero.  Adam's step count lives on the device (so
-// that a captured training epoch replays with the right bias corrections).
+// Adam on every layer in one launch.  Adam's step count lives on the device
+// (so that a captured training epoch replays with the right bias
+// corrections).
 __global__ void k_tick(long long *t) { *t += 1; }
 
 struct AdamAll {
     LayerDev L[4];
     int off[5];                // thread ranges: layer l takes [off[l], off[l+1])
+    double *loss, *eloss;      // if eloss: the batch loss times B into eloss[*ep], the loss zeroed
+    const int *ep;
+    int B;
 };
 
-__global__ void k_adam(AdamAll A, float lr, const long long *tstep, float beta1, float beta2, float eps)
+__global__ void k_adam(AdamAll A, AdamHyper h)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && A.eloss) {
+        A.eloss[*A.ep] += *A.loss * A.B;
+        *A.loss = 0.0;
+    }
     if (i >= A.off[4]) return;
     int l = 0;
     while (i >= A.off[l + 1]) l++;
-    const LayerDev &L = A.L[l];
-    i -= A.off[l];
-    const float tf = (float)*tstep;
-    const float c1 = 1.0f - powf(beta1, tf), c2 = 1.0f - powf(beta2, tf);
-    const int nw = L.nout * L.nin;
-    if (i < nw) {
-        const int o = i / L.nin, k = i % L.nin;
-        const float g = L.gW[o * L.kin + k];
-        L.gW[o * L.kin + k] = 0.0f;
-        const float m = beta1 * L.mW[i] + (1.0f - beta1) * g;
-        const float v = beta2 * L.vW[i] + (1.0f - beta2) * g * g;
-        L.mW[i] = m;
-        L.vW[i] = v;
-        const float w = L.W[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
-        L.W[i] = w;
-        const bf16 wb = __float2bfloat16_rn(w);
-        L.Wb[o * L.kin + k] = wb;
-        L.Wt[k * L.nop + o] = wb;
-        L.Wc[tc_core_index(o, k, L.kin)] = wb;
-        L.Wtc[tc_core_index(k, o, L.tk)] = wb;
-    } else if (i < nw + L.nout) {
-        const int o = i - nw;
-        const float g = L.gb[o];
-        L.gb[o] = 0.0f;
-        const float m = beta1 * L.mb[o] + (1.0f - beta1) * g;
-        const float v = beta2 * L.vb[o] + (1.0f - beta2) * g * g;
-        L.mb[o] = m;
-        L.vb[o] = v;
-        L.b[o] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
-    }
+    const float tf = (float)*h.tstep;
+    adam_entry(A.L[l], i - A.off[l], h, 1.0f - powf(h.beta1, tf), 1.0f - powf(h.beta2, tf));
 }
 
 // ---- the training loop's shuffle: a keyed permutation of [0, n), a
@@ -367,12 +334,6 @@ __global__ void k_gather_epoch(const float *X, const float *Y, long long n, int 
 __global__ void k_set_epoch(int *ep, int v) { *ep = v; }
 
 // the batch's mean loss times its size into the current epoch's sum
-// the batch's loss into its epoch's sum; the batch sum restarts from zero
-__global__ void k_add_loss(double *loss, int B, const int *ep, double *eloss)
-{
-    eloss[*ep] += *loss * B;
-    *loss = 0.0;
-}
 
 __global__ void k_cast_layer(LayerDev L)
 {
@@ -703,6 +664,17 @@ int ms_mlp_check(ms_mlp *m)
     return MS_OK;
 }
 
+static AdamHyper adam_hyper(const ms_mlp *m, float lr)
+{
+    AdamHyper h;
+    h.lr = lr;
+    h.beta1 = 0.9f;
+    h.beta2 = 0.999f;
+    h.eps = 1e-8f;
+    h.tstep = m->d_t;
+    return h;
+}
+
 // the gradients of the batch (X, Y) already on the device into the layers'
 // gW, gb (which hold zeros) and its loss added to m->loss: on engine 1 the
 // two tcgen05 kernels, on engine 0 the mma.sync GEMMs
@@ -761,7 +733,7 @@ static cudaError_t batch_grads(ms_mlp *m, const float *Xd, const float *Yd, int 
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// gradients, loss and Adam's step count back to zero
+// gradients and loss back to zero
 static cudaError_t zero_grads(ms_mlp *m)
 {
     cudaError_t e = cudaMemsetAsync(m->loss, 0, sizeof(double), m->st);
@@ -822,8 +794,9 @@ int ms_mlp_get_params(ms_mlp *m, float *params)
     return MS_OK;
 }
 
-// one Adam step on the gradients of the batch (X, Y) already on the device
-static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float lr)
+// one Adam step on the gradients of the batch (X, Y) already on the device;
+// the batch's loss (times B) into eloss[*d_ep] if eloss is not null
+static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float lr, double *eloss)
 {
     CKC(batch_grads(m, Xd, Yd, B, true));
     AdamAll A{};
@@ -832,7 +805,11 @@ static int train_step(ms_mlp *m, const float *Xd, const float *Yd, int B, float 
         A.L[l] = m->L[l];
         A.off[l + 1] = A.off[l] + m->L[l].nout * m->L[l].nin + m->L[l].nout;
     }
-    k_adam<<<(A.off[4] + 255) / 256, 256, 0, m->st>>>(A, lr, m->d_t, 0.9f, 0.999f, 1e-8f);
+    A.loss = m->loss;
+    A.eloss = eloss;
+    A.ep = m->d_ep;
+    A.B = B;
+    k_adam<<<(A.off[4] + 255) / 256, 256, 0, m->st>>>(A, adam_hyper(m, lr));
     return ck(cudaGetLastError(), "adam");
 }
 
@@ -843,7 +820,7 @@ int ms_mlp_step(ms_mlp *m, const float *X, const float *Y, int64_t n, float lr)
     CKC(cudaMemcpyAsync(m->X, X, sizeof(float) * n * NIN, cudaMemcpyHostToDevice, m->st));
     CKC(cudaMemcpyAsync(m->Y, Y, sizeof(float) * n * NOUT, cudaMemcpyHostToDevice, m->st));
     CKC(zero_grads(m));
-    int rc = train_step(m, m->X, m->Y, (int)n, lr);
+    int rc = train_step(m, m->X, m->Y, (int)n, lr, nullptr);
     if (rc) return rc;
     CKC(cudaStreamSynchronize(m->st));
     return ms_mlp_check(m);
@@ -905,9 +882,8 @@ int ms_mlp_train(ms_mlp *m, const float *X, const float *Y, int64_t n, int32_t e
         for (int64_t s0 = 0; s0 < n; s0 += batch) {
             const int B = (int)std::min<int64_t>(batch, n - s0);
             if (B < 8) break;
-            const int r = train_step(m, Xs + s0 * NIN, Ys + s0 * NOUT, B, lr);
+            const int r = train_step(m, Xs + s0 * NIN, Ys + s0 * NOUT, B, lr, loss_per_epoch ? el : nullptr);
             if (r) return r;
-            if (loss_per_epoch) k_add_loss<<<1, 1, 0, m->st>>>(m->loss, B, m->d_ep, el);
             used += B;
         }
         return ck(cudaGetLastError(), "batch");

@@ -19,6 +19,60 @@ __host__ __device__ inline int tc_image_rows(int layer) { return layer == 3 ? 16
 // inputs) by K = the layer's outputs, the output layer's 4 padded to 16.
 __host__ __device__ inline int tc_timage_k(int layer) { return layer == 3 ? 16 : 128; }
 
+// One layer of the closure network on the device: FP32 master weights and
+// biases, Adam's moments, the batch's gradients (zero between batches), and
+// the BF16 copies each engine reads.
+struct LayerDev {
+    int nin, nout, kin, nop;       // logical and padded sizes
+    float *W, *b;                  // FP32 master [nout][nin], [nout]
+    float *mW, *vW, *mb, *vb;      // Adam moments
+    float *gW, *gb;                // gradients [nop][kin] (padded), [nout]
+    __nv_bfloat16 *Wb, *Wt;        // BF16 copies [nop][kin] and [kin][nop] (mma.sync engine)
+    __nv_bfloat16 *Wc;             // BF16 image of W for the tcgen05 kernels (tc_core_index layout, [rows][kin])
+    __nv_bfloat16 *Wtc;            // BF16 image of W^T for the tcgen05 backward pass ([128][tk])
+    int tk;                        // K of the W^T image (tc_timage_k)
+};
+
+struct AdamHyper {
+    float lr, beta1, beta2, eps;
+    const long long *tstep;        // Adam's step count (device), already advanced for this step
+};
+
+// Adam on entry i of layer L (weight i < nout * nin, row-major, else bias
+// i - nout * nin), then the entry's BF16 copies in every layout; the
+// gradient is read through L2 (other CTAs added to it atomically) and zeroed
+// so that the next batch's sums start from zero.  c1, c2: the bias
+// corrections 1 - beta^t.
+__device__ inline void adam_entry(const LayerDev &L, int i, const AdamHyper &h, float c1, float c2)
+{
+    const int nw = L.nout * L.nin;
+    if (i < nw) {
+        const int o = i / L.nin, k = i % L.nin;
+        const float g = __ldcg(&L.gW[o * L.kin + k]);
+        L.gW[o * L.kin + k] = 0.0f;
+        const float m = h.beta1 * L.mW[i] + (1.0f - h.beta1) * g;
+        const float v = h.beta2 * L.vW[i] + (1.0f - h.beta2) * g * g;
+        L.mW[i] = m;
+        L.vW[i] = v;
+        const float w = L.W[i] - h.lr * (m / c1) / (sqrtf(v / c2) + h.eps);
+        L.W[i] = w;
+        const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+        L.Wb[o * L.kin + k] = wb;
+        L.Wt[k * L.nop + o] = wb;
+        L.Wc[tc_core_index(o, k, L.kin)] = wb;
+        L.Wtc[tc_core_index(k, o, L.tk)] = wb;
+    } else if (i < nw + L.nout) {
+        const int o = i - nw;
+        const float g = __ldcg(&L.gb[o]);
+        L.gb[o] = 0.0f;
+        const float m = h.beta1 * L.mb[o] + (1.0f - h.beta1) * g;
+        const float v = h.beta2 * L.vb[o] + (1.0f - h.beta2) * g * g;
+        L.mb[o] = m;
+        L.vb[o] = v;
+        L.b[o] -= h.lr * (m / c1) / (sqrtf(v / c2) + h.eps);
+    }
+}
+
 struct TcArgs {
     const float *X;                  // [n][16] raw features (device)
     float *Y;                        // [n][4] tendencies in physical units (device)
