@@ -418,20 +418,25 @@ int ms_mlp_get_params(ms_mlp *m, float *params);
  * waiting. */
 int ms_mlp_forward_device(ms_mlp *m, const float *X, int64_t n, float *Y, void *stream);
 
-/* Inference engine of ms_mlp_predict and ms_mlp_forward_device: 1 (the
- * default) one persistent kernel on the tcgen05 tensor cores -- a CTA keeps
- * the BF16 weights in shared memory and runs 128 cells per tile through all
- * four layers, each layer a chain of tcgen05.mma with the FP32 accumulator in
+/* Engine of every later call on m: 1 (the default) the tcgen05 tensor
+ * cores -- inference is one persistent kernel whose CTAs keep the BF16
+ * weights in shared memory and run 128 cells per tile through all four
+ * layers, each layer a chain of tcgen05.mma with the FP32 accumulator in
  * tensor memory (about 107 KB of shared memory and 128 tensor-memory columns
- * per CTA); 0: the tiled mma.sync GEMMs that training uses.  Both round the
- * activations to BF16 between layers; their outputs differ by the order of
- * the FP32 accumulation.  MS_ERR_ARG for another value. */
+ * per CTA); a training batch is three kernels: forward, loss and backward per
+ * 128-sample tile (210 KB of shared memory and all 512 tensor-memory columns
+ * of its SM), the weight and bias gradients as tcgen05 tiles over slices of
+ * the batch, and Adam.  0: the tiled mma.sync GEMMs.  Both round the
+ * activations to BF16 between layers; their results differ by the order of
+ * the FP32 accumulation and by tanh (tanh.approx.f32 on engine 1, tanhf on
+ * engine 0, about 2^-11 apart).  Waits for m's work; MS_ERR_ARG for another
+ * value. */
 int ms_mlp_set_engine(ms_mlp *m, int32_t engine);
 
-/* MS_ERR_TIMEOUT if a bounded wait of the tcgen05 kernel on its tensor-core
+/* MS_ERR_TIMEOUT if a bounded wait of a tcgen05 kernel on its tensor-core
  * work ran out since the last check (the affected outputs are not written;
- * the flag is cleared), else MS_OK.  ms_mlp_predict and the model's step
- * check it. */
+ * the flag is cleared), else MS_OK.  ms_mlp_predict, ms_mlp_grad,
+ * ms_mlp_step, ms_mlp_train and the model's step check it. */
 int ms_mlp_check(ms_mlp *m);
 
 void ms_mlp_free(ms_mlp *m);

@@ -488,7 +488,7 @@ class MLP:
                                                  C.c_void_p(stream) if stream else None))
 
     def set_engine(self, engine: int) -> None:
-        """1: the tcgen05 inference kernel (default); 0: the mma.sync GEMMs."""
+        """1: the tcgen05 kernels for inference and training (default); 0: the mma.sync GEMMs."""
         _check(_load_mlp().ms_mlp_set_engine(self._h, int(engine)))
 
     def predict(self, X) -> np.ndarray:

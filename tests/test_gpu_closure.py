@@ -125,6 +125,28 @@ def test_gradients_match_oracle(ms, B, engine):
         assert e < 2e-2, (k, e)
 
 
+def test_gradients_with_several_tiles_per_cta(ms):
+    """40,000 samples are 313 tiles of 128, more than the SMs: the persistent
+    tile kernel takes two or three tiles per CTA, and the weight-gradient
+    kernel cuts the batch into 30 slices of 21 chunks of 64 samples.
+    Within the oracle's 2e-2 and within 5e-3 of the mma.sync engine."""
+    X, Y = _data(8, 40000)
+    norm = CO.normalisation(X, Y)
+    p = _params()
+    net = ms.MLP(p, norm, max_batch=40000)
+    l1, g1 = net.grad(X, Y)
+    net.set_engine(0)
+    l0, g0 = net.grad(X, Y)
+    lref, gref = CO.loss_and_grads(p, X, Y, norm)
+    assert abs(l1 - lref) <= 2e-2 * lref
+    for k in CO.NAMES:
+        e = np.linalg.norm(g1[k] - gref[k]) / np.linalg.norm(gref[k])
+        assert e < 2e-2, (k, e)
+        e = np.linalg.norm(g1[k] - g0[k]) / np.linalg.norm(g0[k])
+        assert e < 5e-3, (k, e)
+    net.close()
+
+
 def test_gradients_of_the_two_engines_agree(ms):
     """Both engines round the same FP32 accumulations to BF16 between
     layers; they differ where the order of the FP32 sums flips a rounding:
