@@ -167,9 +167,11 @@ int ms_get_floes(ms_model *m, double *out);
 
 /* Replace the msDEM floe state (same n, every floe in the cell it started
  * in; MS_ERR_ARG otherwise) from host arrays.  The coupling state is kept.
- * The arrays are copied (all host cores) into pinned memory, sent to the
- * device in one transfer (64 bytes per floe), and checked and converted to
- * the cell layout there: a non-finite value, r <= 0 or h <= 0, or a floe
+ * The arrays go to the device (64 bytes per floe) -- straight from the
+ * caller's memory when all eight are page-locked (cudaHostAlloc,
+ * cudaHostRegister), else copied (all host cores) into pinned memory array by
+ * array, each array's transfer overlapping the next one's copy -- and are
+ * checked and converted to the cell layout there: a non-finite value, r <= 0 or h <= 0, or a floe
  * outside its cell fails with MS_ERR_ARG naming the smallest such index (the
  * value checks first), and the model's state is then left as it was.  The
  * caller's arrays are only read, and not used after the call returns. */

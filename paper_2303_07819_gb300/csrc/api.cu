@@ -317,16 +317,41 @@ static UpGeom up_geom(const ms_model *m)
 
 // the caller's eight arrays into the pinned stage (all host cores), then to
 // the device's raw copy in one transfer (queued on the model's stream)
+// true if p lies in page-locked host memory of this process (cudaHostAlloc,
+// cudaHostRegister)
+static bool host_pinned(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// the caller's eight floe arrays into d_raw on the model's stream: straight
+// from the caller's memory when every array is page-locked, else through the
+// pinned staging buffer array by array (the transfer of one array overlaps
+// the host copy of the next)
 static int send_raw(ms_model *m, const ms_floes *f)
 {
     const long long n = m->n;
+    const double *src[8] = {f->x, f->y, f->theta, f->u, f->v, f->omega, f->r, f->h};
+    bool pinned = true;
+    for (int a = 0; a < 8 && pinned; a++) pinned = host_pinned(src[a]);
+    if (pinned) {
+        for (int a = 0; a < 8; a++)
+            CK(cudaMemcpyAsync(m->d_raw + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
+        return MS_OK;
+    }
     double *st = (double *)stage(m, sizeof(double) * 8 * n);
     if (!st) return fail(MS_ERR_CUDA, "cudaMallocHost of %lld bytes failed", (long long)(64 * n));
-    const double *src[8] = {f->x, f->y, f->theta, f->u, f->v, f->omega, f->r, f->h};
-    host_parallel(n, [&](long long k0, long long k1) {
-        for (int a = 0; a < 8; a++) std::memcpy(st + a * n + k0, src[a] + k0, sizeof(double) * (k1 - k0));
-    });
-    CK(cudaMemcpyAsync(m->d_raw, st, sizeof(double) * 8 * n, cudaMemcpyHostToDevice, m->stream));
+    for (int a = 0; a < 8; a++) {
+        host_parallel(n, [&](long long k0, long long k1) {
+            std::memcpy(st + a * n + k0, src[a] + k0, sizeof(double) * (k1 - k0));
+        });
+        CK(cudaMemcpyAsync(m->d_raw + a * n, st + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, m->stream));
+    }
     return MS_OK;
 }
 

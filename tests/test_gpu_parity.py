@@ -358,6 +358,35 @@ def test_set_floes_roundtrip(ms):
         assert np.array_equal(f[k], f2[k]), k
 
 
+def test_set_floes_from_page_locked_memory(ms):
+    """ms_set_floes sends page-locked arrays without a host copy and others
+    through its staging buffer: the same state either way, then the same
+    steps; a bad value in page-locked memory is still refused."""
+    torch = pytest.importorskip("torch")
+    s = I.powerlaw_32x32(nx=8)
+    a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
+    a.step(s["dt"], 30)
+    f = a.floes()
+    pinned = torch.empty((8, a.n), dtype=torch.float64).pin_memory().numpy()
+    fp = {k: pinned[i] for i, k in enumerate(ms.FLOE_KEYS)}
+    for k in f:
+        fp[k][:] = f[k]
+    a.set_floes(fp)
+    b.set_floes(f)
+    for m in (a, b):
+        m.step(s["dt"], 120)
+    fa, fb = a.floes(), b.floes()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(a.moments(), b.moments())
+    fp["h"][17] = -1.0
+    with pytest.raises(ms.MsError, match="floe 17"):
+        a.set_floes(fp)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_fp32_variants_match_oracle(orc, ms, variant):
     """Brute-force, block-binned, warp-binned, resident warp-binned and
