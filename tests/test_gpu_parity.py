@@ -366,7 +366,8 @@ def test_set_floes_from_page_locked_memory(ms):
     s = I.powerlaw_32x32(nx=8)
     a = ms.Model(s["params"], s["floes"], ms.MS_FP32)
     b = ms.Model(s["params"], s["floes"], ms.MS_FP32)
-    a.step(s["dt"], 30)
+    for m in (a, b):                 # the same coupling state in both
+        m.step(s["dt"], 30)
     f = a.floes()
     pinned = torch.empty((8, a.n), dtype=torch.float64).pin_memory().numpy()
     fp = {k: pinned[i] for i, k in enumerate(ms.FLOE_KEYS)}
