@@ -122,12 +122,13 @@ def closure_inference_rate(net, X, n=256 * 256, reps=20):
             "tflops": n * MLP_FWD_FLOP / (ms * 1e-3) / 1e12, "engine": "tcgen05 (kind::f16, BF16, FP32 in TMEM)"}
 
 
-def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=20, K=10,
+def closure_eval(msdem, s, seeds=(101, 102, 103), nx_train=128, spin=15, nint=21, K=10,
                  tols=(0.01, 0.015, 0.02, 0.025, 0.03, 0.05, 0.1, 0.2), target_err=1e-2, mode=0, epochs=40):
     """The learned closure on the timed workload.  Training data come from the
-    particle path of other seeds of the same workload (after spin-up; about
-    1e6 cell-intervals); the network trains on the GPU; then K coarse
-    intervals of the particle-only model are compared with the
+    particle path of other seeds of the same workload (after spin-up;
+    1.03e6 cell-intervals: 3 seeds x 21 intervals x 16,384 cells); the
+    network trains on the GPU; then K coarse intervals of the particle-only
+    model are compared with the
     closure-plus-fallback model at a sweep of bounds on the network's checked
     error, the mean-field closure, and, as the noise floor, the particle path
     with another reduction order (the warp-per-cell kernels), all from the
