@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
     fence_before();
     __syncthreads();
     fence_after();
-    // the weights in shared memory (every thread waits; the same verdict for all)
+    // the weights in shared memory (every thread waits; the same outcome for all)
     bool ok = __syncthreads_and(bar_wait(wbar, 0u) ? 1 : 0) != 0;
     const uint32_t tmem = S.tbase;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
                               kk > 0 ? 1u : 0u);
                 mma_commit(bar);
             }
-            // the same verdict in every thread, so that all leave together
+            // the same outcome in every thread, so that all leave together
             ok = __syncthreads_and(bar_wait(bar, phase) ? 1 : 0) != 0;
             if (!ok) break;
             phase ^= 1u;

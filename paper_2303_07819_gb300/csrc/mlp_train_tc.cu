@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(TR_THREADS) k_train_tile_tc(TrainArgs a)
 
     // one chain D = A B^T (M = 128, N, K) into the accumulator; the previous
     // layer's transposed output goes to global memory while the MMAs run.
-    // The same verdict in every thread.
+    // The same outcome in every thread.
     auto chain = [&](uint32_t sB, int K, int N) -> bool {
         fence_async_smem();
         fence_before();

@@ -61,7 +61,7 @@ __device__ __forceinline__ uint32_t tcg_init(TcgSmem &S)
 }
 
 // The tile's MMAs; true when the accumulator holds the tile (false if a wait
-// ran out: the same verdict in every thread).  Every thread calls it.
+// ran out: the same outcome in every thread).  Every thread calls it.
 __device__ __forceinline__ bool tcg_mainloop(TcgSmem &S, uint32_t tmem, TcgState &st, int M, int N, int kbeg, int kend,
                                              int m0, int n0, const __nv_bfloat16 *__restrict__ A, int lda,
                                              const __nv_bfloat16 *__restrict__ B, int ldb, int ones_row)
