@@ -197,14 +197,21 @@ __global__ void __launch_bounds__(TR_THREADS) k_train_tile_tc(TrainArgs a)
         for (int l = 0; l < 3 && ok; l++) {
             ok = chain(sW[l], l == 0 ? TR_KIN : TR_NH, TR_NH);
             if (!ok) break;
-#pragma unroll 1
-            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            // this thread's 64 columns: four loads in flight, one wait
+            uint32_t acc[4][16];
+            __syncwarp();
+#pragma unroll
+            for (int g = 0; g < 4; g++) tmem_ld16_issue(lane_addr + (uint32_t)(cbeg + 16 * g), acc[g]);
+#pragma unroll
+            for (int g = 0; g < 4; g++) tmem_ld_wait(acc[g]);
+#pragma unroll
+            for (int g = 0; g < 4; g++) {
+                const int c0 = cbeg + 16 * g;
                 float v[16];
-                tmem_ld16(lane_addr + c0, v);
                 __align__(16) bf16 h[16];
 #pragma unroll
                 for (int e = 0; e < 16; e++) {
-                    h[e] = __float2bfloat16_rn(tanh_sfu(v[e] + S.b[l][c0 + e]));
+                    h[e] = __float2bfloat16_rn(tanh_sfu(__uint_as_float(acc[g][e]) + S.b[l][c0 + e]));
                     v[e] = __bfloat162float(h[e]);
                     S.Tr[(c0 + e) * TR_T + r] = h[e];
                 }
@@ -253,20 +260,35 @@ __global__ void __launch_bounds__(TR_THREADS) k_train_tile_tc(TrainArgs a)
             ok = chain(sT[l], l == 3 ? TR_NO : TR_NH, TR_NH);
             if (!ok) break;
 #pragma unroll 1
-            for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                float v[16], h[16];
-                tmem_ld16(lane_addr + c0, v);
-                tmem_ld16(lane_addr + (uint32_t)(TR_NH * l + c0), h);   // h_{l-1}
-                __align__(16) bf16 d[16];
+            for (int c1 = cbeg; c1 < cend; c1 += 32) {
+                // two groups of 16 columns and their h_{l-1}: four loads in flight, one wait
+                uint32_t acc[2][16], hh[2][16];
+                __syncwarp();
 #pragma unroll
-                for (int e = 0; e < 16; e++) {
-                    d[e] = __float2bfloat16_rn(v[e] * (1.0f - h[e] * h[e]));
-                    S.Tr[(c0 + e) * TR_T + r] = d[e];
+                for (int g = 0; g < 2; g++) {
+                    tmem_ld16_issue(lane_addr + (uint32_t)(c1 + 16 * g), acc[g]);
+                    tmem_ld16_issue(lane_addr + (uint32_t)(TR_NH * l + c1 + 16 * g), hh[g]);
                 }
-                if (l > 1) {
-                    *reinterpret_cast<uint4 *>(Ab + core_off(r, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(d);
-                    *reinterpret_cast<uint4 *>(Ab + core_off(r, c0 + 8, TR_NH)) =
-                        *reinterpret_cast<const uint4 *>(d + 8);
+#pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    tmem_ld_wait(acc[g]);
+                    tmem_ld_wait(hh[g]);
+                }
+#pragma unroll
+                for (int g = 0; g < 2; g++) {
+                    const int c0 = c1 + 16 * g;
+                    __align__(16) bf16 d[16];
+#pragma unroll
+                    for (int e = 0; e < 16; e++) {
+                        const float h = __uint_as_float(hh[g][e]);
+                        d[e] = __float2bfloat16_rn(__uint_as_float(acc[g][e]) * (1.0f - h * h));
+                        S.Tr[(c0 + e) * TR_T + r] = d[e];
+                    }
+                    if (l > 1) {
+                        *reinterpret_cast<uint4 *>(Ab + core_off(r, c0, TR_NH)) = *reinterpret_cast<const uint4 *>(d);
+                        *reinterpret_cast<uint4 *>(Ab + core_off(r, c0 + 8, TR_NH)) =
+                            *reinterpret_cast<const uint4 *>(d + 8);
+                    }
                 }
             }
             tr_dst = a.dZt[l - 1];
