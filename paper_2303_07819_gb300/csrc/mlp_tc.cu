@@ -147,15 +147,25 @@ __global__ void __launch_bounds__(TC_T) k_mlp_forward_tc(TcArgs a)
             if (l < 3) {
                 // bias, tanh, BF16: the next layer's operand (K = 128), in place
 #pragma unroll 1
-                for (int c0 = 0; c0 < TC_NH; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(lane_addr + c0, v);
-                    __align__(16) bf16 h[16];
+                for (int c1 = 0; c1 < TC_NH; c1 += 64) {
+                    // four loads of 16 columns in flight, one wait
+                    uint32_t acc[4][16];
+                    __syncwarp();
 #pragma unroll
-                    for (int e = 0; e < 16; e++) h[e] = __float2bfloat16_rn(tanh_sfu(v[e] + S.b[l][c0 + e]));
-                    *reinterpret_cast<uint4 *>(Ab + core_off(t, c0, TC_NH)) = *reinterpret_cast<const uint4 *>(h);
-                    *reinterpret_cast<uint4 *>(Ab + core_off(t, c0 + 8, TC_NH)) =
-                        *reinterpret_cast<const uint4 *>(h + 8);
+                    for (int g = 0; g < 4; g++) tmem_ld16_issue(lane_addr + (uint32_t)(c1 + 16 * g), acc[g]);
+#pragma unroll
+                    for (int g = 0; g < 4; g++) tmem_ld_wait(acc[g]);
+#pragma unroll
+                    for (int g = 0; g < 4; g++) {
+                        const int c0 = c1 + 16 * g;
+                        __align__(16) bf16 h[16];
+#pragma unroll
+                        for (int e = 0; e < 16; e++)
+                            h[e] = __float2bfloat16_rn(tanh_sfu(__uint_as_float(acc[g][e]) + S.b[l][c0 + e]));
+                        *reinterpret_cast<uint4 *>(Ab + core_off(t, c0, TC_NH)) = *reinterpret_cast<const uint4 *>(h);
+                        *reinterpret_cast<uint4 *>(Ab + core_off(t, c0 + 8, TC_NH)) =
+                            *reinterpret_cast<const uint4 *>(h + 8);
+                    }
                 }
                 fence_before();
             } else {
