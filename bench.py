@@ -333,12 +333,12 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_sample_rate(s, ncells: int, steps: int, seed: int = 0):
-    """Floe-steps/s of the FP64 oracle (all host cores) on `ncells` random
-    cells of the workload for `steps` fine steps."""
+def oracle_sample_rate(s, ncells: int, steps: int, seed: int = 0, threads: int | None = None):
+    """Floe-steps/s of the FP64 oracle (all host cores, or `threads`) on
+    `ncells` random cells of the workload for `steps` fine steps."""
     from oracle import oracle as O
     O.build()
-    cores = len(os.sched_getaffinity(0))
+    cores = threads if threads else len(os.sched_getaffinity(0))
     O.set_threads(cores)
     p = dict(s["params"], nens=1)           # an ensemble: cells of its first realization
     fl = s["floes"]
@@ -634,9 +634,17 @@ def main():
     if not args.no_extras and rank == 0:
         ncells, steps = calibrated_oracle(s, 15.0)
         rate, n, tdt, cores = oracle_sample_rate(s, ncells, steps)
+        # the same oracle on one thread, a 32nd of the cells (about the same wall time)
+        n1cells = max(8, ncells // 32)
+        rate1, n1, tdt1, _ = oracle_sample_rate(s, n1cells, steps, seed=2, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "floe-steps/s", "cores": cores, "kind": "oracle",
+                                "cell_steps_per_s": ncells * steps / tdt,
                                 "sample": f"{ncells} random cells ({n} floes) x {steps} fine steps, "
-                                          f"{tdt:.1f} s wall, FP64, OpenMP over cells"}
+                                          f"{tdt:.1f} s wall, FP64, OpenMP over cells",
+                                "one_thread": {"value": rate1, "unit": "floe-steps/s",
+                                               "cell_steps_per_s": n1cells * steps / tdt1,
+                                               "sample": f"{n1cells} random cells ({n1} floes) x {steps} "
+                                                         f"fine steps, {tdt1:.1f} s wall"}}
         if args.workload == "batched_128x128":
             line["closure"] = closure_eval(msdem, s)
             line["ensemble"] = ensemble_eval(msdem)
